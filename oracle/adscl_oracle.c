@@ -1,0 +1,388 @@
+/*
+ * adscl_oracle.c -- plain, sequential FP64 reference of the AdS4 Einstein-Klein-Gordon
+ * method-of-lines scheme (Liebling & Khanna, arXiv:1706.07413, Sec. II).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or call this
+ * file: only the tests, the package's smoke check and the CPU-baseline leg of the bench
+ * use it.  It shares no code, header, table or constant generator with the CUDA library.
+ *
+ * Everything here is written for a reader checking it against the paper by eye: no
+ * blocking, no fusion, no reordering.  Radial integrations run sequentially, exactly as
+ * the paper describes the constraint solve (Sec. II, after Eq. (eq:delta)).
+ *
+ * Notation (Sec. II, Eq. (metric)): grid x_i = i h, i = 0..N-1, h = pi/(2(N-1));
+ * rho = Phi^2 + Pi^2; s(x) = sin x cos x; F = A exp(-delta).
+ *
+ * Readings of the paper used here (the paper is silent on them; both implementations use
+ * the same reading):
+ *  - node-centred grid with x_0 = 0 and x_{N-1} = pi/2;
+ *  - parity ghosts: Phi odd / Pi even at x = 0; Phi even / Pi odd at x = pi/2;
+ *    f = F Pi follows Pi, g = F Phi follows Phi;
+ *  - midpoint values by the 4-point Lagrange formula (-u_{i-1}+9u_i+9u_{i+1}-u_{i+2})/16;
+ *  - delta: Simpson's rule per cell, summed from x = pi/2 inwards (Eq. (eq:delta), delta(pi/2)=0);
+ *  - A: the Hamiltonian constraint Eq. (eq:aprime) rewritten for the mass function
+ *    m = (1-A) sin x / cos^3 x, which obeys m' = tan^2 x rho - sin x cos x rho m, m(0)=0,
+ *    integrated cell by cell outwards with classic RK4 (midpoint data interpolated);
+ *  - RHS: Eqs. (eq:phi), (eq:pi) with 4th-order centred differences; Eq. (eq:pi) kept in the
+ *    paper's form tan^{-2}(tan^2 g)'; Pi-dot at x=0 by L'Hopital (3 D g); boundary rows
+ *    Phi-dot(0) = Phi-dot(pi/2) = Pi-dot(pi/2) = 0;
+ *  - Kreiss-Oliger dissipation sigma/(64h) (u_{i-3}-6u_{i-2}+15u_{i-1}-20u_i+15u_{i+1}-6u_{i+2}+u_{i+3})
+ *    on every non-boundary row (not in the paper);
+ *  - classic RK4 in time with the constraint solve at every stage;
+ *  - collapse: the first step after which min_i A < theta; t_c by linear interpolation.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* instance status codes (same meaning as the library's per-instance status) */
+enum { ORC_RUNNING = 0, ORC_DONE = 1, ORC_COLLAPSED = 2, ORC_NONFINITE = 3 };
+
+/* ------------------------------------------------------------------ grid helpers */
+
+static double grid_h(int N) { return 0.5 * ORC_PI / (double)(N - 1); }
+
+/* value of u at index i in [-3, N+2], using the parity rule:
+ * u_{-k} = p0 * u_k and u_{N-1+k} = p1 * u_{N-1-k}. */
+static double with_ghost(const double *u, int N, int i, double p0, double p1)
+{
+    if (i < 0) return p0 * u[-i];
+    if (i > N - 1) return p1 * u[2 * (N - 1) - i];
+    return u[i];
+}
+
+/* ------------------------------------------------------------------ constraints */
+
+/*
+ * Solve the two constraints (Eqs. (eq:aprime) and (eq:delta)) on one time slice.
+ * Inputs Phi, Pi (length N).  Outputs A, delta (length N); m (length N, optional);
+ * *mass = m(pi/2) = integral of tan^2 x A rho dx (the paper's mass, Sec. II).
+ */
+void orc_constraints(int N, const double *Phi, const double *Pi, double *A, double *delta,
+                     double *m_out, double *mass)
+{
+    const double h = grid_h(N);
+    double *rho = (double *)malloc(sizeof(double) * N);
+    double *rhom = (double *)malloc(sizeof(double) * N);
+    double *m = (double *)malloc(sizeof(double) * N);
+    int i, c;
+
+    for (i = 0; i < N; ++i) rho[i] = Phi[i] * Phi[i] + Pi[i] * Pi[i];
+
+    /* rho at cell midpoints x_{c+1/2} from interpolated Phi and Pi */
+    for (c = 0; c < N - 1; ++c) {
+        double phm = (-with_ghost(Phi, N, c - 1, -1.0, 1.0) + 9.0 * Phi[c] + 9.0 * Phi[c + 1]
+                      - with_ghost(Phi, N, c + 2, -1.0, 1.0)) / 16.0;
+        double pim = (-with_ghost(Pi, N, c - 1, 1.0, -1.0) + 9.0 * Pi[c] + 9.0 * Pi[c + 1]
+                      - with_ghost(Pi, N, c + 2, 1.0, -1.0)) / 16.0;
+        rhom[c] = phm * phm + pim * pim;
+    }
+
+    /* delta' = -sin x cos x rho, delta(pi/2) = 0: Simpson per cell, inward */
+    delta[N - 1] = 0.0;
+    for (c = N - 2; c >= 0; --c) {
+        double x0 = c * h, xm = (c + 0.5) * h, x1 = (c + 1) * h;
+        double s0 = sin(x0) * cos(x0), sm = sin(xm) * cos(xm), s1 = sin(x1) * cos(x1);
+        delta[c] = delta[c + 1] + h / 6.0 * (s0 * rho[c] + 4.0 * sm * rhom[c] + s1 * rho[c + 1]);
+    }
+
+    /* m' = a - b m, a = tan^2 x rho, b = sin x cos x rho, m(0) = 0: RK4 per cell, outward */
+    m[0] = 0.0;
+    for (c = 0; c < N - 1; ++c) {
+        double x0 = c * h, xm = (c + 0.5) * h, x1 = (c + 1) * h;
+        double a0 = tan(x0) * tan(x0) * rho[c];
+        double am = tan(xm) * tan(xm) * rhom[c];
+        double a1 = (c + 1 == N - 1) ? 0.0 : tan(x1) * tan(x1) * rho[c + 1];
+        double b0 = sin(x0) * cos(x0) * rho[c];
+        double bm = sin(xm) * cos(xm) * rhom[c];
+        double b1 = sin(x1) * cos(x1) * rho[c + 1];
+        double y = m[c];
+        double k1 = a0 - b0 * y;
+        double k2 = am - bm * (y + 0.5 * h * k1);
+        double k3 = am - bm * (y + 0.5 * h * k2);
+        double k4 = a1 - b1 * (y + h * k3);
+        m[c + 1] = y + h / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+    }
+
+    /* A = 1 - m cos^3 x / sin x, with A = 1 at both ends (Sec. II boundary conditions) */
+    A[0] = 1.0;
+    A[N - 1] = 1.0;
+    for (i = 1; i < N - 1; ++i) {
+        double x = i * h;
+        A[i] = 1.0 - m[i] * cos(x) * cos(x) * cos(x) / sin(x);
+    }
+    if (mass) *mass = m[N - 1];
+    if (m_out) memcpy(m_out, m, sizeof(double) * N);
+    free(rho);
+    free(rhom);
+    free(m);
+}
+
+/* ------------------------------------------------------------------ right-hand side */
+
+/* Kreiss-Oliger term at row i for field u with ghost parities p0, p1 */
+static double ko_term(const double *u, int N, int i, double p0, double p1, double sigma, double h)
+{
+    double d6 = with_ghost(u, N, i - 3, p0, p1) - 6.0 * with_ghost(u, N, i - 2, p0, p1)
+              + 15.0 * with_ghost(u, N, i - 1, p0, p1) - 20.0 * u[i]
+              + 15.0 * with_ghost(u, N, i + 1, p0, p1) - 6.0 * with_ghost(u, N, i + 2, p0, p1)
+              + with_ghost(u, N, i + 3, p0, p1);
+    return sigma / (64.0 * h) * d6;
+}
+
+/* 4th-order centred first derivative at row i with ghost parities p0, p1 */
+static double d1(const double *u, int N, int i, double p0, double p1, double h)
+{
+    return (with_ghost(u, N, i - 2, p0, p1) - 8.0 * with_ghost(u, N, i - 1, p0, p1)
+            + 8.0 * with_ghost(u, N, i + 1, p0, p1) - with_ghost(u, N, i + 2, p0, p1)) / (12.0 * h);
+}
+
+/*
+ * Time derivatives of Phi and Pi (Eqs. (eq:phi), (eq:pi)) given the constraint solution
+ * A, delta on the same slice.  Eq. (eq:pi) is discretised in the form the paper writes it,
+ * Pi-dot = tan^{-2} x (tan^2 x F Phi)': the 4th-order difference of u = tan^2 x g divided by
+ * tan^2 x (the expanded form g' + 2g/(sin x cos x) is unstable at both ends of the grid).
+ * u is odd about x = 0 and even about x = pi/2, where its finite limit is taken from the
+ * even extrapolation u_{N-1} = (4 u_{N-2} - u_{N-3}) / 3.
+ */
+void orc_rhs(int N, double sigma, const double *Phi, const double *Pi, const double *A,
+             const double *delta, double *dPhi, double *dPi)
+{
+    const double h = grid_h(N);
+    double *f = (double *)malloc(sizeof(double) * N);
+    double *g = (double *)malloc(sizeof(double) * N);
+    double *u = (double *)malloc(sizeof(double) * N);
+    int i;
+    for (i = 0; i < N; ++i) {
+        double F = A[i] * exp(-delta[i]);
+        f[i] = F * Pi[i];
+        g[i] = F * Phi[i];
+    }
+    for (i = 0; i < N - 1; ++i) u[i] = tan(i * h) * tan(i * h) * g[i];
+    u[N - 1] = (4.0 * u[N - 2] - u[N - 3]) / 3.0;
+    /* x = 0: Phi stays 0; Pi-dot = 3 (F Phi)'(0) (limit of Eq. (eq:pi)) */
+    dPhi[0] = 0.0;
+    dPi[0] = 3.0 * d1(g, N, 0, -1.0, 1.0, h) + ko_term(Pi, N, 0, 1.0, -1.0, sigma, h);
+    for (i = 1; i < N - 1; ++i) {
+        double x = i * h;
+        dPhi[i] = d1(f, N, i, 1.0, -1.0, h) + ko_term(Phi, N, i, -1.0, 1.0, sigma, h);
+        dPi[i] = d1(u, N, i, -1.0, 1.0, h) / (tan(x) * tan(x))
+               + ko_term(Pi, N, i, 1.0, -1.0, sigma, h);
+    }
+    /* x = pi/2: Phi = Pi = 0 held fixed */
+    dPhi[N - 1] = 0.0;
+    dPi[N - 1] = 0.0;
+    free(f);
+    free(g);
+    free(u);
+}
+
+/* ------------------------------------------------------------------ time stepping */
+
+/*
+ * One classic RK4 step of size dt (Sec. II: Runge-Kutta method of lines), constraints solved
+ * at every stage.  Phi, Pi are updated in place.
+ */
+void orc_rk4_step(int N, double dt, double sigma, double *Phi, double *Pi)
+{
+    size_t bytes = sizeof(double) * N;
+    double *A = (double *)malloc(bytes), *dl = (double *)malloc(bytes);
+    double *sPhi = (double *)malloc(bytes), *sPi = (double *)malloc(bytes);
+    double *kPhi = (double *)malloc(bytes), *kPi = (double *)malloc(bytes);
+    double *aPhi = (double *)malloc(bytes), *aPi = (double *)malloc(bytes);
+    const double cstage[4] = {0.0, 0.5, 0.5, 1.0};
+    const double wstage[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    int i, st;
+    memcpy(sPhi, Phi, bytes);
+    memcpy(sPi, Pi, bytes);
+    memcpy(aPhi, Phi, bytes);
+    memcpy(aPi, Pi, bytes);
+    for (st = 0; st < 4; ++st) {
+        if (st > 0) {
+            for (i = 0; i < N; ++i) {
+                sPhi[i] = Phi[i] + cstage[st] * dt * kPhi[i];
+                sPi[i] = Pi[i] + cstage[st] * dt * kPi[i];
+            }
+        }
+        orc_constraints(N, sPhi, sPi, A, dl, NULL, NULL);
+        orc_rhs(N, sigma, sPhi, sPi, A, dl, kPhi, kPi);
+        for (i = 0; i < N; ++i) {
+            aPhi[i] += wstage[st] * dt * kPhi[i];
+            aPi[i] += wstage[st] * dt * kPi[i];
+        }
+    }
+    memcpy(Phi, aPhi, bytes);
+    memcpy(Pi, aPi, bytes);
+    free(A); free(dl); free(sPhi); free(sPi); free(kPhi); free(kPi); free(aPhi); free(aPi);
+}
+
+static double min_of(const double *u, int N)
+{
+    double v = u[0];
+    int i;
+    for (i = 1; i < N; ++i)
+        if (u[i] < v) v = u[i];
+    return v;
+}
+
+/*
+ * Evolve one instance from step index n0 (time n0*dt) by at most nsteps RK4 steps, stopping
+ * early at collapse (Sec. II: the code stops when min A falls to a small threshold theta and
+ * records that time) or at a non-finite slice.
+ *
+ *   minA_in    min A of the starting slice (pass NaN to have it recomputed here)
+ *   out[0..6]  t_reached, t_collapse (+inf if none), mass at the last slice, min A at the last
+ *              slice, steps taken, status (ORC_*), delta(0) at the last slice
+ *   mass_hist, minA_hist  optional, length nsteps+1: values at every slice visited
+ * Phi, Pi are updated in place; A, delta receive the constraint solution of the last slice.
+ */
+int orc_evolve(int N, double dt, long n0, long nsteps, double sigma, double theta, double minA_in,
+               double *Phi, double *Pi, double *A, double *delta, double *out,
+               double *mass_hist, double *minA_hist)
+{
+    double mass = 0.0, minA, t_c = INFINITY;
+    long n;
+    int status = ORC_DONE;
+    orc_constraints(N, Phi, Pi, A, delta, NULL, &mass);
+    minA = isnan(minA_in) ? min_of(A, N) : minA_in;
+    if (mass_hist) mass_hist[0] = mass;
+    if (minA_hist) minA_hist[0] = minA;
+    for (n = 0; n < nsteps; ++n) {
+        double minA_new;
+        orc_rk4_step(N, dt, sigma, Phi, Pi);
+        orc_constraints(N, Phi, Pi, A, delta, NULL, &mass);
+        minA_new = min_of(A, N);
+        if (mass_hist) mass_hist[n + 1] = mass;
+        if (minA_hist) minA_hist[n + 1] = minA_new;
+        if (!isfinite(mass) || !isfinite(delta[0]) || !isfinite(minA_new)) {
+            status = ORC_NONFINITE;
+            minA = minA_new;
+            ++n;
+            break;
+        }
+        if (minA_new < theta) {
+            /* linear interpolation of min A between t_n and t_{n+1} */
+            double tn = (double)(n0 + n) * dt;
+            t_c = tn + dt * (minA - theta) / (minA - minA_new);
+            status = ORC_COLLAPSED;
+            minA = minA_new;
+            ++n;
+            break;
+        }
+        minA = minA_new;
+    }
+    out[0] = (double)(n0 + n) * dt;
+    out[1] = t_c;
+    out[2] = mass;
+    out[3] = minA;
+    out[4] = (double)n;
+    out[5] = (double)status;
+    out[6] = delta[0];
+    return status;
+}
+
+/* ------------------------------------------------------------------ AdS eigenbasis */
+
+/* Jacobi polynomial P_n^{(a,b)}(y) by the standard three-term recurrence in n */
+static double jacobi_p(int n, double a, double b, double y)
+{
+    double p0 = 1.0, p1, p2;
+    int k;
+    if (n == 0) return p0;
+    p1 = 0.5 * ((a + b + 2.0) * y + (a - b));
+    for (k = 2; k <= n; ++k) {
+        double c = 2.0 * k + a + b;
+        double lhs = 2.0 * k * (k + a + b) * (c - 2.0);
+        double r1 = (c - 1.0) * (c * (c - 2.0) * y + a * a - b * b);
+        double r2 = 2.0 * (k + a - 1.0) * (k + b - 1.0) * c;
+        p2 = (r1 * p1 - r2 * p0) / lhs;
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+/*
+ * Linear normal modes of the scalar on AdS4 (the spectrum of Sec. II; the paper gives no
+ * formula, this is the standard result of the works it cites):
+ *   e_j(x) = d_j cos^3 x P_j^{(1/2,3/2)}(cos 2x),  omega_j = 3 + 2j,
+ *   d_j = 2 sqrt(j! (j+2)!) / Gamma(j + 3/2),  so that  int_0^{pi/2} e_i e_j tan^2 x dx = delta_ij.
+ * Derivative via dP_n^{(a,b)}/dy = (n+a+b+1)/2 P_{n-1}^{(a+1,b+1)}.
+ * Outputs e[j*nx + i], de[j*nx + i] at the points x[i].
+ */
+void orc_eigen_at(int J, int nx, const double *x, double *e, double *de)
+{
+    int j, i;
+    for (j = 0; j < J; ++j) {
+        double dj = 2.0 * exp(0.5 * (lgamma(j + 1.0) + lgamma(j + 3.0)) - lgamma(j + 1.5));
+        for (i = 0; i < nx; ++i) {
+            double c = cos(x[i]), s = sin(x[i]), y = cos(2.0 * x[i]);
+            double P = jacobi_p(j, 0.5, 1.5, y);
+            double dP = (j == 0) ? 0.0 : 0.5 * (j + 3.0) * jacobi_p(j - 1, 1.5, 2.5, y);
+            e[(size_t)j * nx + i] = dj * c * c * c * P;
+            /* d/dx [cos^3 x P(cos 2x)] = -3 cos^2 x sin x P - 2 sin 2x cos^3 x P'(y) */
+            de[(size_t)j * nx + i] = dj * (-3.0 * c * c * s * P - 4.0 * s * c * c * c * c * dP);
+        }
+    }
+}
+
+/* the same on the evolution grid x_i = i h */
+void orc_eigen(int N, int J, double *e, double *de)
+{
+    double *x = (double *)malloc(sizeof(double) * N);
+    const double h = grid_h(N);
+    int i;
+    for (i = 0; i < N; ++i) x[i] = i * h;
+    orc_eigen_at(J, N, x, e, de);
+    free(x);
+}
+
+/*
+ * Mode energies: Pi_j = (sqrt(A) Pi, e_j), Phi_j = (sqrt(A) Phi, e_j'),
+ * E_j = Pi_j^2 + Phi_j^2 / omega_j^2, with (u, v) = int_0^{pi/2} u v tan^2 x dx by the
+ * trapezoid rule on the grid (the integrand vanishes at both ends).
+ * Also returns the projections themselves if Pij/Phij are non-NULL.
+ */
+void orc_spectrum(int N, int J, const double *Phi, const double *Pi, const double *A, double *E,
+                  double *Pij, double *Phij)
+{
+    const double h = grid_h(N);
+    double *e = (double *)malloc(sizeof(double) * (size_t)N * J);
+    double *de = (double *)malloc(sizeof(double) * (size_t)N * J);
+    int j, i;
+    orc_eigen(N, J, e, de);
+    for (j = 0; j < J; ++j) {
+        double pj = 0.0, fj = 0.0, om = 3.0 + 2.0 * j;
+        for (i = 1; i < N - 1; ++i) {
+            double x = i * h, t2 = tan(x) * tan(x), sa = sqrt(A[i]);
+            pj += h * t2 * sa * Pi[i] * e[(size_t)j * N + i];
+            fj += h * t2 * sa * Phi[i] * de[(size_t)j * N + i];
+        }
+        E[j] = pj * pj + fj * fj / (om * om);
+        if (Pij) Pij[j] = pj;
+        if (Phij) Phij[j] = fj;
+    }
+    free(e);
+    free(de);
+}
+
+/* Pi(x,0) = sum_j a_j e_j(x), Phi(x,0) = 0, with the boundary values of Sec. II imposed */
+void orc_synthesize(int N, int K, const double *a, double *Phi, double *Pi)
+{
+    double *e = (double *)malloc(sizeof(double) * (size_t)N * K);
+    double *de = (double *)malloc(sizeof(double) * (size_t)N * K);
+    int j, i;
+    orc_eigen(N, K, e, de);
+    for (i = 0; i < N; ++i) {
+        double v = 0.0;
+        for (j = 0; j < K; ++j) v += a[j] * e[(size_t)j * N + i];
+        Pi[i] = v;
+        Phi[i] = 0.0;
+    }
+    Pi[N - 1] = 0.0;
+    free(e);
+    free(de);
+}
