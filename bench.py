@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched FP64 AdS4 collapse evolution (one JSON line on stdout).
+
+Workload: the amplitude scan -- B = 256 Gaussian pulses Pi(x,0) = (2 eps/pi) exp(-4 tan^2 x /
+(pi^2 sigma^2)), sigma = 1/16, eps log-uniform in [5, 80] (seed 0), N = 4097 grid points each,
+RK4 with dt ~ 0.5 dx, constraints solved in every RK stage, per-instance stop when min A < 2^-7.
+One bench step = one persistent launch that advances every running instance by STEP_RK RK4
+steps.  Metric: FP64 RK4 point-substeps per second (sum over instances of N x 4 x RK4 steps
+actually taken, over the device time of the timed launches).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank evolves its own batch (seed = rank): weak scaling, no collective on
+the data path; rank 0 prints the max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1706_07413_b300 import workloads as W  # noqa: E402
+
+METRIC = "batched FP64 RK4 point-substeps/s"
+UNIT = "point-substeps/s"
+STEP_RK = 128             # RK4 steps per bench step (one persistent launch)
+B_DEFAULT, N_DEFAULT = 256, 4097
+THETA = 2.0 ** -7
+SIGMA_KO = 0.5
+# FP64 flops (FMA = 2) per point-substep of the evolution kernel, tallied from its source:
+# constraint cell data 48, thread/warp scans 6.75, local pass 9 + exp 14, RHS 32, RK4 7.
+FLOPS_PER_POINT_SUBSTEP = 116.75
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def oracle_rate(insts, nsteps, threads):
+    """The CPU oracle, as it stands, on a bounded sample: point-substeps/s with `threads` host
+    threads (one instance per thread at a time; the ctypes call releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    oracle.build()
+
+    def run(it):
+        N = it.N
+        dt = oracle.dt_for(N)
+        r = oracle.evolve(np.zeros(N), W.gaussian_pi(N, it.eps, it.sigma), dt, nsteps,
+                          sigma=SIGMA_KO, theta=THETA)
+        return N * 4 * r.steps
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        work = sum(ex.map(run, insts))
+    el = time.perf_counter() - t0
+    return work / el, el, work
+
+
+def run_reference(args):
+    """The reference arm: the sequential FP64 CPU oracle on the host cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    threads = min(os.cpu_count() or 1, 16)
+    insts = W.amp_scan()[: 2 * threads]
+    nsteps = 24
+    for _ in range(args.warmup):
+        oracle_rate(insts[:threads], 4, threads)
+    rates, total_t, total_w = [], 0.0, 0
+    for _ in range(args.steps):
+        r, el, w = oracle_rate(insts, nsteps, threads)
+        rates.append(r)
+        total_t += el
+        total_w += w
+    value = total_w / total_t
+    sample = f"{len(insts)} of the 256 N=4097 pulses x {nsteps} RK4 steps per bench step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "amplitude scan, B=256 Gaussian pulses, N=4097, sigma=1/16, "
+                               "eps log-uniform [5,80], theta=2^-7 (bounded sample)",
+                   "oracle": "sequential FP64 C, one instance per host thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_1706_07413_b300 import adscl
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    stream = torch.cuda.Stream()
+    insts = W.amp_scan(B=B_DEFAULT, N=N_DEFAULT, seed=rank)
+    B, N = len(insts), insts[0].N
+    Pi0 = W.packed([W.gaussian_pi(N, it.eps, it.sigma) for it in insts])
+    Phi0 = np.zeros_like(Pi0)
+
+    tflops_peak = adscl.probe_fp64(local, stream.cuda_stream)
+
+    sol = adscl.Solver([N] * B, ko_sigma=SIGMA_KO, collapse_threshold=THETA, device=local,
+                       stream=stream.cuda_stream)
+    sol.set_initial(Phi0, Pi0)
+    dt, _ = sol.clock()
+    dstep = STEP_RK * dt[0]
+    outs = [torch.empty(B, dtype=torch.float64, device="cuda") for _ in range(3)] + \
+        [torch.empty(B, dtype=torch.int32, device="cuda")]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    t = 0.0
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            t += dstep
+            sol.evolve(t, out=outs)
+    torch.cuda.synchronize()
+    _, step0 = sol.clock()
+    launches0 = sol.launch_count()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.zero_()                    # L2 flush, outside the timed interval
+                evs[k][0].record(stream)
+                t += dstep
+                sol.evolve(t, out=outs)
+                evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = sol.launch_count() - launches0
+    _, step1 = sol.clock()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    dev_s = sum(ms) / 1e3
+    work = float(np.sum((step1 - step0) * sol.N.astype(np.float64) * 4.0))
+    tr, tc, m, st = sol.evolve(t)   # (already there: reads statuses only)
+    collapsed = int(np.sum(st == adscl.COLLAPSED))
+
+    if dist is not None:
+        tt = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ww = torch.tensor([work], dtype=torch.float64, device="cuda")
+        dist.all_reduce(ww, op=dist.ReduceOp.SUM)
+        dev_s, work_all = float(tt.item()), float(ww.item())
+    else:
+        work_all = work
+    value = work_all / dev_s
+
+    # roofline of the evolution kernel (it is >99% of each timed launch)
+    achieved_tflops = (work * FLOPS_PER_POINT_SUBSTEP) / dev_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": tflops_peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / tflops_peak, "traffic": None,
+                "peak_source": "measured FP64 FMA-chain probe on this GPU (FMA = 2 flops)",
+                "flops_per_point_substep": FLOPS_PER_POINT_SUBSTEP}
+
+    # one instance per launch, same workload, for the batched-vs-one-per-launch comparison
+    opl = None
+    if rank == 0:
+        nopl = 4
+        s1 = adscl.Solver([N] * nopl, ko_sigma=SIGMA_KO, collapse_threshold=THETA, device=local,
+                          one_per_launch=True, stream=stream.cuda_stream)
+        s1.set_initial(Phi0[: nopl * N].copy(), Pi0[: nopl * N].copy())
+        with torch.cuda.stream(stream):
+            s1.evolve(dstep / 4, out=[o[:nopl] for o in outs])
+            torch.cuda.synchronize()
+            _, sa = s1.clock()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s1.evolve(dstep / 4 + dstep / 2, out=[o[:nopl] for o in outs])
+            e1.record(stream)
+        torch.cuda.synchronize()
+        _, sb = s1.clock()
+        w1 = float(np.sum((sb - sa) * N * 4.0))
+        opl = w1 / (e0.elapsed_time(e1) / 1e3)
+        s1.close()
+
+    # end to end through the public API with host buffers: upload a fresh batch of initial
+    # data from pinned memory, solve, evolve one bench step, read the per-instance results
+    e2e = None
+    if not args.no_e2e:
+        hPhi = torch.from_numpy(Phi0).pin_memory().numpy()
+        hPi = torch.from_numpy(Pi0).pin_memory().numpy()
+        res = [torch.empty(B, dtype=torch.float64).pin_memory().numpy() for _ in range(3)] + \
+            [torch.empty(B, dtype=torch.int32).pin_memory().numpy()]
+        sol_e = adscl.Solver([N] * B, ko_sigma=SIGMA_KO, collapse_threshold=THETA, device=local,
+                             stream=stream.cuda_stream)
+        ne = max(3, args.steps // 4)
+        tot, work_e = 0.0, 0.0
+        for k in range(ne + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sol_e.set_initial(hPhi, hPi)
+            st = sol_e.lib.adscl_evolve(sol_e.ctx, dstep, res[0].ctypes.data, res[1].ctypes.data,
+                                        res[2].ctypes.data, res[3].ctypes.data, 0)
+            el = time.perf_counter() - t0
+            assert st == 0
+            if k > 0:   # first one is a warm-up
+                tot += el
+                _, se = sol_e.clock()
+                work_e += float(np.sum(se * N * 4.0))
+        sol_e.close()
+        h2d = 2 * B * N * 8
+        d2h = B * (3 * 8 + 4)
+        e2e_v = work_e / tot
+        if dist is not None:
+            tt = torch.tensor([e2e_v * ws], dtype=torch.float64, device="cuda")
+            e2e_v = float(tt.item())
+        e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        threads = min(os.cpu_count() or 1, 16)
+        sample_insts = W.amp_scan()[: 2 * threads]
+        rate, el, _ = oracle_rate(sample_insts, 24, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{len(sample_insts)} of the 256 N=4097 pulses x 24 RK4 steps "
+                         f"({el:.1f} s wall)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"amplitude scan: B={B} Gaussian pulses per GPU, N={N}, "
+                                   "sigma=1/16, eps log-uniform [5,80], RK4 dt=0.5dx, "
+                                   "constraints every substep, early exit at min A < 2^-7",
+                       "step": f"one persistent launch = {STEP_RK} RK4 steps of every running "
+                               "instance",
+                       "window_t": [round(args.warmup * dstep, 6),
+                                    round((args.warmup + args.steps) * dstep, 6)],
+                       "collapsed_in_window": collapsed,
+                       "l2": "flushed (512 MB write) before every timed launch",
+                       "parallelism": f"instances sharded over {ws} GPU(s), no collective"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "one_per_launch": {"value": opl, "unit": UNIT, "instances": 4,
+                               "batched_over_one_per_launch": (value / ws) / opl if opl else None},
+            "adjoint_forward_ratio": None,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

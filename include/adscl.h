@@ -1,0 +1,142 @@
+/*
+ * adscl.h -- C ABI of the B300 (sm_103a) solver for spherically symmetric scalar-field
+ * collapse in AdS4: the Einstein-Klein-Gordon system in the variables Phi, Pi, A, delta of
+ * Liebling & Khanna, arXiv:1706.07413, Sec. II, Eqs. (metric), (eq:phi)-(eq:delta).
+ *
+ * The solver evolves batches of independent instances ("instances" = one radial grid and its
+ * fields each) by the method of lines: 4th-order centred differences, Kreiss-Oliger
+ * dissipation and classic RK4, with the two constraints (eq:aprime) and (eq:delta) solved on
+ * the GPU inside every RK stage.  Grid of one instance: x_i = i h, i = 0..N-1,
+ * h = pi / (2 (N - 1)), so x_0 = 0 and x_{N-1} = pi/2.
+ *
+ * Conventions shared by every entry point:
+ *  - Fields of a batch are packed instance after instance: instance b occupies the N_b
+ *    doubles starting at offset sum_{c<b} N_c ("packed layout").
+ *  - The caller owns every buffer it passes.  The library owns its device state and copies
+ *    in and out on the context's stream.
+ *  - ptr_is_device = 1: the pointers are device pointers and the call is asynchronous on the
+ *    context's stream.  ptr_is_device = 0: host pointers; the call returns after the stream
+ *    has finished the work.
+ *  - No entry point throws or aborts.  Each returns an adscl_status; on failure the context
+ *    keeps a message readable with adscl_last_error.  Per-instance outcomes (collapse,
+ *    non-finite fields) are reported in inst_status and the call itself returns ADSCL_OK.
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef ADSCL_H
+#define ADSCL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct adscl_ctx adscl_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    ADSCL_OK = 0,
+    ADSCL_EINVAL = 1,       /* bad argument or configuration; nothing was launched */
+    ADSCL_ENOMEM = 2,       /* a device or host allocation failed */
+    ADSCL_ECUDA = 3,        /* a CUDA runtime call failed (message names it) */
+    ADSCL_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
+    ADSCL_ENONFINITE = 5,   /* input fields contain NaN or Inf */
+    ADSCL_EUNSUPPORTED = 6  /* valid request this build does not provide */
+} adscl_status;
+
+typedef enum {
+    ADSCL_INST_RUNNING = 0,   /* can be evolved further */
+    ADSCL_INST_DONE = 1,      /* reached the requested time in the last adscl_evolve call */
+    ADSCL_INST_COLLAPSED = 2, /* min_x A fell below the collapse threshold (Sec. II) */
+    ADSCL_INST_NONFINITE = 3, /* a slice produced NaN or Inf; the instance stopped */
+    ADSCL_INST_TIMEOUT = 4    /* a bounded device wait gave up for this instance */
+} adscl_inst_status;
+
+typedef struct {
+    int32_t num_instances;       /* B >= 1 */
+    const int32_t *N;            /* host array of B grid sizes; each N >= 17 with (N - 1) a
+                                    multiple of 8 and N <= adscl_max_points() */
+    double cfl;                  /* lambda: dt <= lambda h; 0 selects 0.5 */
+    double ko_sigma;             /* Kreiss-Oliger strength sigma >= 0 (not in the paper) */
+    double collapse_threshold;   /* theta: an instance collapses when min A < theta (the paper
+                                    uses 0.01, Sec. II) */
+    double out_dt;               /* cadence D: dt = D / ceil(D / (lambda h)) so that steps land
+                                    on multiples of D; 0 selects 1.0 */
+    int32_t spec_J;              /* number of modes of the spectrum diagnostic (<= 64); 0 = 64 */
+    int32_t ckpt_every;          /* adjoint checkpoint interval in steps; 0 = 256 */
+    int64_t max_device_iters;    /* iteration limit of any device-side wait; 0 = default */
+    int32_t device;              /* CUDA device ordinal */
+    int32_t one_per_launch;      /* 0: all instances in one persistent launch (CUDA graph);
+                                    1: one kernel launch per instance (comparison mode) */
+    void *stream;                /* cudaStream_t for all work; NULL = the legacy default stream */
+} adscl_config;
+
+/* Largest grid size N one instance may use in this build. */
+int32_t adscl_max_points(void);
+
+/* Create a context: validates cfg (ADSCL_EINVAL before any allocation or launch), builds the
+ * geometry tables of every distinct N, allocates the device state.  *out receives the
+ * context, or NULL on failure. */
+adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out);
+
+/* Set the initial slice t = 0 of every instance from packed Phi(x,0), Pi(x,0) and solve the
+ * constraints (eq:aprime), (eq:delta) for A and delta on it (Sec. II: "one must define Phi(x,0)
+ * and Pi(x,0) and solve ...").  The boundary values Phi(0) = Phi(pi/2) = Pi(pi/2) = 0 are
+ * imposed.  Resets every instance to step 0 with status RUNNING (or COLLAPSED at t = 0 if
+ * min A already lies below the threshold).  ADSCL_ENONFINITE if an input is NaN/Inf. */
+adscl_status adscl_set_initial(adscl_ctx *ctx, const double *Phi, const double *Pi, int ptr_is_device);
+
+/* Same, with Phi(x,0) = 0 and Pi(x,0) = sum_{j<K} a_j e_j(x), e_j the AdS4 normal modes
+ * (Sec. II, "We can use these normal modes to define initial data").  a: B x K row-major,
+ * K <= 64. */
+adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *a, int32_t K, int ptr_is_device);
+
+/* Evolve every RUNNING instance until t >= t_end (its step count n with n dt >= t_end - 1e-9 dt)
+ * or until it collapses (min A < theta; Sec. II) or turns non-finite.  Outputs, each of
+ * length B (any may be NULL): t_reached (time of the last slice), t_collapse (linear
+ * interpolation of min A across theta, +inf if none), mass (M = m(pi/2) of the last slice,
+ * the paper's mass), inst_status (adscl_inst_status). */
+adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, double *t_collapse,
+                          double *mass, int32_t *inst_status, int ptr_is_device);
+
+/* Mode-energy spectrum E_j, j < J, of every instance's current slice: B x J row-major.
+ * precision: ADSCL_PREC_FP64, ADSCL_PREC_BF16X3 or ADSCL_PREC_TF32X3 (tensor cores). */
+enum { ADSCL_PREC_FP64 = 0, ADSCL_PREC_BF16X3 = 1, ADSCL_PREC_TF32X3 = 2 };
+adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E, int ptr_is_device);
+
+/* Gradient of J = sum_{j<64}(E_j(T) - E_j(0))^2 with respect to the initial mode amplitudes
+ * a (B x K) by the discrete adjoint of the whole scheme. */
+adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, double *J_out,
+                        double *dJda, int ptr_is_device);
+
+/* Copy out one instance's current slice: Phi, Pi and the constraint solution A, delta on it
+ * (each length N_inst; any may be NULL). */
+adscl_status adscl_get_state(adscl_ctx *ctx, int32_t inst, double *Phi, double *Pi, double *A,
+                             double *delta, int ptr_is_device);
+
+/* Replace one instance's slice by host arrays Phi, Pi at step index `step` (time step*dt);
+ * its status becomes RUNNING and the constraints are re-solved. */
+adscl_status adscl_set_state(adscl_ctx *ctx, int32_t inst, const double *Phi, const double *Pi,
+                             int64_t step);
+
+/* Per-instance time step dt and current step index (host outputs, length B, may be NULL). */
+adscl_status adscl_get_clock(adscl_ctx *ctx, double *dt, int64_t *step);
+
+/* Kernel launches issued by this context since creation (for launch accounting). */
+int64_t adscl_launch_count(const adscl_ctx *ctx);
+
+/* Measured FP64 throughput of `device` in TFLOP/s (a fused multiply-add counts 2 flops):
+ * independent FMA chains on every SM, best of three timed launches on `stream` (a
+ * cudaStream_t or NULL).  It is the ceiling of the FP64-bound evolution kernels. */
+adscl_status adscl_probe_fp64(int32_t device, void *stream, double *tflops);
+
+/* Message of the last failure on this context ("" if none).  Valid until the next call. */
+const char *adscl_last_error(const adscl_ctx *ctx);
+
+/* Free every resource of the context (NULL is ignored). */
+void adscl_destroy(adscl_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADSCL_H */

@@ -1,0 +1,440 @@
+// adscl.cu -- host side of the C ABI declared in include/adscl.h: configuration checks,
+// geometry tables, device state, launches.  Every CUDA runtime call is checked; failures are
+// returned as adscl_status with a message, never thrown across the ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "adscl.h"
+#include "evolve.cuh"
+
+using namespace adscl;
+
+namespace {
+
+constexpr int kP = 8;      // grid nodes per thread
+constexpr int kNT = 512;   // threads per CTA
+constexpr int kMaxPoints = kP * kNT + 1;  // 4097
+
+}  // namespace
+
+struct adscl_ctx {
+    int B = 0;
+    std::vector<int32_t> N;
+    std::vector<int64_t> off;
+    int64_t total = 0;
+    int Nmax = 0;
+    double cfl = 0.5, sigma = 0.0, theta = 0.0, out_dt = 1.0;
+    int spec_J = 64, ckpt = 256;
+    int64_t max_iters = 0;
+    int device = 0, one_per_launch = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+
+    std::vector<InstDesc> h_desc;
+    std::vector<int32_t> h_order;
+    double *d_geo_block = nullptr;
+    GeoTab *d_geo = nullptr;
+    InstDesc *d_desc = nullptr;
+    InstState *d_st = nullptr;
+    double *d_Phi = nullptr, *d_Pi = nullptr, *d_aPhi = nullptr, *d_aPi = nullptr;
+    double *d_scratchA = nullptr, *d_scratchD = nullptr;
+    int32_t *d_order = nullptr, *d_queue = nullptr;
+    double *d_out = nullptr;      // 3 B doubles: t_reached, t_c, mass
+    int32_t *d_outs = nullptr;    // B statuses
+    int stride = 0;
+    size_t smem = 0;
+
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+adscl_status fail(adscl_ctx *c, adscl_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(ctx, ADSCL_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+// Geometry factors of one grid size (host libm, FP64); layout: ws, wt, K, T, iT12 (N each),
+// wsm, wtm (N-1 each).
+std::vector<double> make_geometry(int N)
+{
+    const double h = 0.5 * M_PI / (double)(N - 1);
+    std::vector<double> t((size_t)7 * N, 0.0);
+    double *ws = t.data(), *wt = ws + N, *K = wt + N, *T = K + N, *iT12 = T + N, *wsm = iT12 + N,
+           *wtm = wsm + N;
+    for (int i = 0; i < N; ++i) {
+        const double x = i * h, s = std::sin(x), c = std::cos(x);
+        ws[i] = h * s * c / 6.0;
+        if (i < N - 1) {
+            const double tn = std::tan(x);
+            T[i] = tn * tn;
+            wt[i] = h * T[i] / 6.0;
+        }
+        if (i > 0 && i < N - 1) {
+            K[i] = c * c * c / s;
+            iT12[i] = 1.0 / (12.0 * h * T[i]);
+        }
+    }
+    for (int c = 0; c < N - 1; ++c) {
+        const double x = (c + 0.5) * h, s = std::sin(x), co = std::cos(x), tn = std::tan(x);
+        wsm[c] = h * s * co / (6.0 * 256.0);
+        wtm[c] = h * tn * tn / (6.0 * 256.0);
+    }
+    return t;
+}
+
+double step_for(int N, double cfl, double cadence)
+{
+    const double h = 0.5 * M_PI / (double)(N - 1);
+    return cadence / std::ceil(cadence / (cfl * h));
+}
+
+adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, const int32_t *order_dev,
+                           int nwork, double *outA, double *outD)
+{
+    if (nwork <= 0) return ADSCL_OK;
+    EvolveArgs a{};
+    a.desc = ctx->d_desc;
+    a.st = ctx->d_st;
+    a.geo = ctx->d_geo;
+    a.Phi = ctx->d_Phi;
+    a.Pi = ctx->d_Pi;
+    a.aPhi = ctx->d_aPhi;
+    a.aPi = ctx->d_aPi;
+    a.order = order_dev;
+    a.nwork = nwork;
+    a.queue = ctx->d_queue;
+    a.t_end = t_end;
+    a.theta = ctx->theta;
+    a.outA = outA;
+    a.outDelta = outD;
+    a.mode = mode;
+    CK(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int32_t), ctx->stream));
+    const int grid = std::min(nwork, ctx->num_sms);
+    evolve_kernel<kP, kNT><<<grid, kNT, ctx->smem, ctx->stream>>>(a, ctx->stride);
+    CK(cudaGetLastError());
+    ctx->launches += 1;
+    return ADSCL_OK;
+}
+
+adscl_status check_ctx(adscl_ctx *ctx)
+{
+    if (!ctx) return ADSCL_EINVAL;
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    return ADSCL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t adscl_max_points(void) { return kMaxPoints; }
+
+adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
+{
+    if (out) *out = nullptr;
+    if (!cfg || !out || cfg->num_instances < 1 || !cfg->N) return ADSCL_EINVAL;
+    for (int b = 0; b < cfg->num_instances; ++b) {
+        const int n = cfg->N[b];
+        if (n < 17 || (n - 1) % kP != 0 || n > kMaxPoints) return ADSCL_EINVAL;
+    }
+    const double cfl = cfg->cfl == 0.0 ? 0.5 : cfg->cfl;
+    const double cad = cfg->out_dt == 0.0 ? 1.0 : cfg->out_dt;
+    if (!(cfl > 0.0 && cfl <= 2.0) || !(cfg->ko_sigma >= 0.0 && cfg->ko_sigma < 10.0) ||
+        !std::isfinite(cfg->collapse_threshold) || !(cad > 0.0) || cfg->spec_J < 0 ||
+        cfg->spec_J > 64 || cfg->ckpt_every < 0 || cfg->max_device_iters < 0)
+        return ADSCL_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
+        return ADSCL_EINVAL;
+
+    adscl_ctx *ctx = new adscl_ctx();
+    ctx->B = cfg->num_instances;
+    ctx->N.assign(cfg->N, cfg->N + ctx->B);
+    ctx->cfl = cfl;
+    ctx->sigma = cfg->ko_sigma;
+    ctx->theta = cfg->collapse_threshold;
+    ctx->out_dt = cad;
+    ctx->spec_J = cfg->spec_J ? cfg->spec_J : 64;
+    ctx->ckpt = cfg->ckpt_every ? cfg->ckpt_every : 256;
+    ctx->max_iters = cfg->max_device_iters ? cfg->max_device_iters : (int64_t)1 << 24;
+    ctx->device = cfg->device;
+    ctx->one_per_launch = cfg->one_per_launch;
+    ctx->stream = (cudaStream_t)cfg->stream;
+    *out = ctx;
+
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+
+    ctx->off.resize(ctx->B);
+    for (int b = 0; b < ctx->B; ++b) {
+        ctx->off[b] = ctx->total;
+        ctx->total += ctx->N[b];
+        ctx->Nmax = std::max(ctx->Nmax, ctx->N[b]);
+    }
+
+    // geometry tables, one per distinct N
+    std::map<int, int> geo_of;
+    std::vector<int> geoN;
+    for (int n : ctx->N)
+        if (!geo_of.count(n)) {
+            geo_of[n] = (int)geoN.size();
+            geoN.push_back(n);
+        }
+    size_t geo_doubles = 0;
+    for (int n : geoN) geo_doubles += (size_t)7 * n;
+    CK(cudaMalloc(&ctx->d_geo_block, geo_doubles * sizeof(double)));
+    std::vector<GeoTab> h_geo;
+    {
+        size_t pos = 0;
+        for (int n : geoN) {
+            std::vector<double> t = make_geometry(n);
+            CK(cudaMemcpy(ctx->d_geo_block + pos, t.data(), t.size() * sizeof(double),
+                          cudaMemcpyHostToDevice));
+            const double *base = ctx->d_geo_block + pos;
+            GeoTab g;
+            g.ws = base;
+            g.wt = base + n;
+            g.K = base + 2 * (size_t)n;
+            g.T = base + 3 * (size_t)n;
+            g.iT12 = base + 4 * (size_t)n;
+            g.wsm = base + 5 * (size_t)n;
+            g.wtm = base + 6 * (size_t)n;
+            h_geo.push_back(g);
+            pos += t.size();
+        }
+    }
+    CK(cudaMalloc(&ctx->d_geo, h_geo.size() * sizeof(GeoTab)));
+    CK(cudaMemcpy(ctx->d_geo, h_geo.data(), h_geo.size() * sizeof(GeoTab), cudaMemcpyHostToDevice));
+
+    ctx->h_desc.resize(ctx->B);
+    for (int b = 0; b < ctx->B; ++b) {
+        InstDesc &d = ctx->h_desc[b];
+        const int n = ctx->N[b];
+        const double h = 0.5 * M_PI / (double)(n - 1);
+        d.N = n;
+        d.geo = geo_of[n];
+        d.off = ctx->off[b];
+        d.dt = step_for(n, cfl, cad);
+        d.dt2 = 0.5 * d.dt;
+        d.dt3 = d.dt / 3.0;
+        d.dt6 = d.dt / 6.0;
+        d.c12 = 1.0 / (12.0 * h);
+        d.c3 = 3.0 / (12.0 * h);
+        d.cko = ctx->sigma / (64.0 * h);
+    }
+    CK(cudaMalloc(&ctx->d_desc, ctx->B * sizeof(InstDesc)));
+    CK(cudaMemcpy(ctx->d_desc, ctx->h_desc.data(), ctx->B * sizeof(InstDesc), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_st, ctx->B * sizeof(InstState)));
+    CK(cudaMemset(ctx->d_st, 0, ctx->B * sizeof(InstState)));
+
+    const size_t fb = (size_t)ctx->total * sizeof(double);
+    CK(cudaMalloc(&ctx->d_Phi, fb));
+    CK(cudaMalloc(&ctx->d_Pi, fb));
+    CK(cudaMalloc(&ctx->d_aPhi, fb));
+    CK(cudaMalloc(&ctx->d_aPi, fb));
+    CK(cudaMemset(ctx->d_Phi, 0, fb));
+    CK(cudaMemset(ctx->d_Pi, 0, fb));
+    CK(cudaMalloc(&ctx->d_scratchA, fb));
+    CK(cudaMalloc(&ctx->d_scratchD, fb));
+
+    // work order: largest grids first (longest work first in the queue)
+    ctx->h_order.resize(ctx->B);
+    std::iota(ctx->h_order.begin(), ctx->h_order.end(), 0);
+    std::stable_sort(ctx->h_order.begin(), ctx->h_order.end(),
+                     [&](int x, int y) { return ctx->N[x] > ctx->N[y]; });
+    CK(cudaMalloc(&ctx->d_order, (ctx->B + 1) * sizeof(int32_t)));
+    CK(cudaMemcpy(ctx->d_order, ctx->h_order.data(), ctx->B * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_queue, sizeof(int32_t)));
+    CK(cudaMalloc(&ctx->d_out, 3 * (size_t)ctx->B * sizeof(double)));
+    CK(cudaMalloc(&ctx->d_outs, (size_t)ctx->B * sizeof(int32_t)));
+
+    ctx->stride = ((ctx->Nmax + 2 * kG) + 1) & ~1;
+    ctx->smem = (size_t)4 * ctx->stride * sizeof(double);
+    // the attribute is per kernel, not per context: always raise it to the largest grid
+    const size_t smem_max = (size_t)4 * (((kMaxPoints + 2 * kG) + 1) & ~1) * sizeof(double);
+    CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_max));
+    return ADSCL_OK;
+}
+
+adscl_status adscl_set_initial(adscl_ctx *ctx, const double *Phi, const double *Pi, int ptr_is_device)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    if (!Phi || !Pi) return fail(ctx, ADSCL_EINVAL, "null field pointer");
+    const size_t fb = (size_t)ctx->total * sizeof(double);
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ctx->d_Phi, Phi, fb, kind, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_Pi, Pi, fb, kind, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_st, 0, ctx->B * sizeof(InstState), ctx->stream));
+    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->B, nullptr, nullptr);
+    if (s != ADSCL_OK) return s;
+    if (!ptr_is_device) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        std::vector<InstState> st(ctx->B);
+        CK(cudaMemcpy(st.data(), ctx->d_st, ctx->B * sizeof(InstState), cudaMemcpyDeviceToHost));
+        for (int b = 0; b < ctx->B; ++b)
+            if (st[b].status == kNonfinite)
+                return fail(ctx, ADSCL_ENONFINITE, "instance %d: non-finite initial fields", b);
+    }
+    return ADSCL_OK;
+}
+
+adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *, int32_t, int)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    return fail(ctx, ADSCL_EUNSUPPORTED, "adscl_set_initial_modes is not available in this build");
+}
+
+adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, double *t_collapse,
+                          double *mass, int32_t *inst_status, int ptr_is_device)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    if (!std::isfinite(t_end) || t_end < 0.0) return fail(ctx, ADSCL_EINVAL, "bad t_end");
+    if (ctx->one_per_launch) {
+        for (int q = 0; q < ctx->B; ++q) {
+            s = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order + q, 1, nullptr, nullptr);
+            if (s != ADSCL_OK) return s;
+        }
+    } else {
+        s = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order, ctx->B, nullptr, nullptr);
+        if (s != ADSCL_OK) return s;
+    }
+    const int B = ctx->B;
+    double *o = ctx->d_out;
+    gather_kernel<<<(B + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_desc, ctx->d_st, B, t_end, 1, o,
+                                                           o + B, o + 2 * B, ctx->d_outs);
+    CK(cudaGetLastError());
+    ctx->launches += 1;
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (t_reached) CK(cudaMemcpyAsync(t_reached, o, B * sizeof(double), kind, ctx->stream));
+    if (t_collapse) CK(cudaMemcpyAsync(t_collapse, o + B, B * sizeof(double), kind, ctx->stream));
+    if (mass) CK(cudaMemcpyAsync(mass, o + 2 * B, B * sizeof(double), kind, ctx->stream));
+    if (inst_status) CK(cudaMemcpyAsync(inst_status, ctx->d_outs, B * sizeof(int32_t), kind, ctx->stream));
+    if (!ptr_is_device) CK(cudaStreamSynchronize(ctx->stream));
+    return ADSCL_OK;
+}
+
+adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t, int, double *, int)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    return fail(ctx, ADSCL_EUNSUPPORTED, "adscl_spectrum is not available in this build");
+}
+
+adscl_status adscl_grad(adscl_ctx *ctx, const double *, int32_t, double, double *, double *, int)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    return fail(ctx, ADSCL_EUNSUPPORTED, "adscl_grad is not available in this build");
+}
+
+adscl_status adscl_get_state(adscl_ctx *ctx, int32_t inst, double *Phi, double *Pi, double *A,
+                             double *delta, int ptr_is_device)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    if (inst < 0 || inst >= ctx->B) return fail(ctx, ADSCL_EINVAL, "instance %d out of range", inst);
+    const int64_t off = ctx->off[inst];
+    const size_t nb = (size_t)ctx->N[inst] * sizeof(double);
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (A || delta) {
+        // one constraint solve of this instance's slice (no state change)
+        CK(cudaMemcpyAsync(ctx->d_order + ctx->B, &inst, sizeof(int32_t), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        s = launch_evolve(ctx, kModeSolve, 0.0, ctx->d_order + ctx->B, 1, ctx->d_scratchA,
+                          ctx->d_scratchD);
+        if (s != ADSCL_OK) return s;
+        if (A) CK(cudaMemcpyAsync(A, ctx->d_scratchA + off, nb, kind, ctx->stream));
+        if (delta) CK(cudaMemcpyAsync(delta, ctx->d_scratchD + off, nb, kind, ctx->stream));
+    }
+    if (Phi) CK(cudaMemcpyAsync(Phi, ctx->d_Phi + off, nb, kind, ctx->stream));
+    if (Pi) CK(cudaMemcpyAsync(Pi, ctx->d_Pi + off, nb, kind, ctx->stream));
+    // the host copy of inst above must stay alive until the copy ran: always synchronise
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ADSCL_OK;
+}
+
+adscl_status adscl_set_state(adscl_ctx *ctx, int32_t inst, const double *Phi, const double *Pi,
+                             int64_t step)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    if (inst < 0 || inst >= ctx->B || !Phi || !Pi || step < 0)
+        return fail(ctx, ADSCL_EINVAL, "bad set_state arguments");
+    const int64_t off = ctx->off[inst];
+    const size_t nb = (size_t)ctx->N[inst] * sizeof(double);
+    InstState st{};
+    st.step = step;
+    CK(cudaMemcpyAsync(ctx->d_Phi + off, Phi, nb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_Pi + off, Pi, nb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_st + inst, &st, sizeof st, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_order + ctx->B, &inst, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order + ctx->B, 1, nullptr, nullptr);
+    if (s != ADSCL_OK) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ADSCL_OK;
+}
+
+adscl_status adscl_get_clock(adscl_ctx *ctx, double *dt, int64_t *step)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    if (dt)
+        for (int b = 0; b < ctx->B; ++b) dt[b] = ctx->h_desc[b].dt;
+    if (step) {
+        std::vector<InstState> st(ctx->B);
+        CK(cudaMemcpyAsync(st.data(), ctx->d_st, ctx->B * sizeof(InstState), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int b = 0; b < ctx->B; ++b) step[b] = st[b].step;
+    }
+    return ADSCL_OK;
+}
+
+int64_t adscl_launch_count(const adscl_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+const char *adscl_last_error(const adscl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void adscl_destroy(adscl_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    void *ptrs[] = {ctx->d_geo_block, ctx->d_geo, ctx->d_desc, ctx->d_st, ctx->d_Phi, ctx->d_Pi,
+                    ctx->d_aPhi, ctx->d_aPi, ctx->d_scratchA, ctx->d_scratchD, ctx->d_order,
+                    ctx->d_queue, ctx->d_out, ctx->d_outs};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete ctx;
+}
+
+}  // extern "C"

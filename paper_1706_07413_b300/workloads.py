@@ -118,3 +118,26 @@ def qp_seeds(N: int = 8193, K: int = 32) -> list:
             for eps in (0.05, 0.1):
                 out.append(Instance(N=N, kind="modes", coeffs=approx_qp_coefficients(kd, mu, eps, K)))
     return out
+
+
+def smooth_random(N: int, seed: int, amp: float = 1.0, terms: int = 5):
+    """A smooth random slice with the boundary parities of the fields:
+    Pi = amp cos^3 x sum_k c_k sin^{2k} x,  Phi = amp sin x cos^2 x sum_k d_k sin^{2k} x,
+    c_k, d_k ~ N(0, 1) / (k + 1).  Returns (Phi, Pi)."""
+    rng = np.random.default_rng(seed)
+    x = grid(N)
+    s2 = np.sin(x) ** 2
+    c = rng.standard_normal(terms) / (1.0 + np.arange(terms))
+    dd = rng.standard_normal(terms) / (1.0 + np.arange(terms))
+    poly_c = sum(c[k] * s2 ** k for k in range(terms))
+    poly_d = sum(dd[k] * s2 ** k for k in range(terms))
+    Pi = amp * np.cos(x) ** 3 * poly_c
+    Phi = amp * np.sin(x) * np.cos(x) ** 2 * poly_d
+    Pi[-1] = 0.0
+    Phi[0] = Phi[-1] = 0.0
+    return Phi, Pi
+
+
+def packed(fields):
+    """Concatenate per-instance arrays into the packed layout of the C ABI."""
+    return np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.float64) for f in fields]))

@@ -1,0 +1,169 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element on the
+same seeded inputs.  Tolerances: the constraint scans and the RK4 step reorder FP64 sums, so
+single slices agree to ~1e-12 of the field scale; evolved states to <= 1e-9 max-abs before
+collapse (the solver's stated bound), and collapse times to 0.1 %."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1706_07413_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ad():
+    from paper_1706_07413_b300 import adscl
+    adscl.load()
+    return adscl
+
+
+def _solver(ad, Ns, **kw):
+    kw.setdefault("ko_sigma", 0.5)
+    kw.setdefault("collapse_threshold", 2.0 ** -7)
+    return ad.Solver(Ns, **kw)
+
+
+def test_static_ads_stays_exact(ad):
+    s = _solver(ad, [17, 129])
+    s.set_initial(np.zeros(s.total), np.zeros(s.total))
+    tr, tc, m, st = s.evolve(0.5)
+    assert np.all(st == ad.DONE) and np.all(m == 0.0) and np.all(np.isinf(tc))
+    for b in range(2):
+        Phi, Pi, A, dl = s.get_state(b)
+        assert np.all(Phi == 0) and np.all(Pi == 0) and np.all(A == 1.0) and np.all(dl == 0.0)
+
+
+@pytest.mark.parametrize("N", [17, 33, 129, 1025, 4097])
+def test_constraints_match_oracle(ad, orc, N):
+    Phi, Pi = W.smooth_random(N, seed=N, amp=3.0)
+    s = _solver(ad, [N])
+    s.set_initial(Phi, Pi)
+    _, _, A, dl = s.get_state(0)
+    Ao, dlo, _, Mo = orc.constraints(Phi, Pi)
+    assert np.abs(A - Ao).max() < 1e-12 * max(1.0, np.abs(Ao).max())
+    assert np.abs(dl - dlo).max() < 1e-12 * max(1.0, np.abs(dlo).max())
+    _, _, m, _ = s.evolve(0.0)
+    assert abs(m[0] - Mo) <= 1e-12 * abs(Mo)
+
+
+@pytest.mark.parametrize("N", [17, 129, 4097])
+def test_single_rk4_step_matches_oracle(ad, orc, N):
+    Phi, Pi = W.smooth_random(N, seed=7 * N, amp=2.0)
+    s = _solver(ad, [N])
+    s.set_initial(Phi, Pi)
+    dt, _ = s.clock()
+    s.evolve(dt[0])
+    gPhi, gPi, gA, gd = s.get_state(0)
+    oPhi, oPi = orc.rk4_step(Phi, Pi, dt[0], sigma=0.5)
+    scale = max(np.abs(oPhi).max(), np.abs(oPi).max())
+    assert np.abs(gPhi - oPhi).max() < 1e-13 * scale
+    assert np.abs(gPi - oPi).max() < 1e-13 * scale
+    assert gPhi[0] == 0.0 and gPhi[-1] == 0.0 and gPi[-1] == 0.0
+
+
+def test_single_gaussian_pulse_parity(ad, orc):
+    """N = 1025, eps = 40, sigma = 1/16, RK4 with dt ~ 0.5 dx: fields agree to 1e-9 max-abs
+    before collapse; the collapse (min A < 0.01) time agrees to 0.1 %."""
+    N, theta = 1025, 0.01
+    Pi0 = W.gaussian_pi(N, 40.0)
+    Phi0 = np.zeros(N)
+    s = _solver(ad, [N], collapse_threshold=theta)
+    s.set_initial(Phi0, Pi0)
+    dt, _ = s.clock()
+    t1 = 4.0
+    n1 = int(round(t1 / dt[0]))
+    tr, tc, m, st = s.evolve(t1)
+    assert st[0] == ad.DONE and abs(tr[0] - n1 * dt[0]) < 1e-12
+    r = orc.evolve(Phi0, Pi0, dt[0], n1, sigma=0.5, theta=theta)
+    gPhi, gPi, gA, gd = s.get_state(0)
+    for g, o in ((gPhi, r.Phi), (gPi, r.Pi), (gA, r.A), (gd, r.delta)):
+        assert np.abs(g - o).max() <= 1e-9
+    assert abs(m[0] - r.mass) <= 1e-10 * abs(r.mass)
+    # continue to collapse
+    tr, tc, m, st = s.evolve(10.0)
+    r2 = orc.evolve(r.Phi, r.Pi, dt[0], int(round(10.0 / dt[0])) - n1, sigma=0.5, theta=theta,
+                    n0=n1, minA_in=r.minA)
+    assert r2.status == orc.COLLAPSED and st[0] == ad.COLLAPSED
+    assert abs(tc[0] / r2.t_collapse - 1) < 1e-3
+
+
+def test_batched_uneven_equals_single_bitwise(ad):
+    Ns = [4097, 17, 1025, 129, 2049, 33]
+    fields = [W.smooth_random(n, seed=100 + i, amp=4.0) for i, n in enumerate(Ns)]
+    s = _solver(ad, Ns)
+    s.set_initial(W.packed([f[0] for f in fields]), W.packed([f[1] for f in fields]))
+    tb = s.evolve(0.05)
+    for i, n in enumerate(Ns):
+        one = _solver(ad, [n])
+        one.set_initial(fields[i][0], fields[i][1])
+        t1 = one.evolve(0.05)
+        a, b = s.get_state(i), one.get_state(0)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+        assert tb[2][i] == t1[2][0] and tb[0][i] == t1[0][0]
+
+
+def test_one_per_launch_equals_batched(ad):
+    Ns = [129, 257, 129]
+    fields = [W.smooth_random(n, seed=200 + i, amp=2.0) for i, n in enumerate(Ns)]
+    res = []
+    for opl in (False, True):
+        s = _solver(ad, Ns, one_per_launch=opl)
+        s.set_initial(W.packed([f[0] for f in fields]), W.packed([f[1] for f in fields]))
+        s.evolve(0.1)
+        res.append([s.get_state(i) for i in range(len(Ns))])
+    for a, b in zip(*res):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def test_restart_is_bitwise(ad):
+    N = 257
+    Phi, Pi = W.smooth_random(N, seed=5, amp=3.0)
+    a = _solver(ad, [N]); a.set_initial(Phi, Pi); a.evolve(0.3)
+    b = _solver(ad, [N]); b.set_initial(Phi, Pi); b.evolve(0.1); b.evolve(0.3)
+    for x, y in zip(a.get_state(0), b.get_state(0)):
+        assert np.array_equal(x, y)
+    # set_state round trip at a step boundary
+    dt, step = a.clock()
+    P1, Q1, _, _ = a.get_state(0)
+    c = _solver(ad, [N]); c.set_state(0, P1, Q1, step[0]); a.evolve(0.5); c.evolve(0.5)
+    for x, y in zip(a.get_state(0), c.get_state(0)):
+        assert np.array_equal(x, y)
+
+
+def test_nonfinite_instance_is_isolated(ad):
+    Ns = [129, 129, 129]
+    fields = [W.smooth_random(129, seed=300 + i, amp=2.0) for i in range(3)]
+    bad = [f[1].copy() for f in fields]
+    bad[1][40] = np.nan
+    s = _solver(ad, Ns)
+    with pytest.raises(ad.AdsclError):
+        s.set_initial(W.packed([f[0] for f in fields]), W.packed(bad))
+    tr, tc, m, st = s.evolve(0.2)
+    assert list(st) == [ad.DONE, ad.NONFINITE, ad.DONE]
+    ref = _solver(ad, [129]); ref.set_initial(fields[2][0], fields[2][1]); ref.evolve(0.2)
+    for x, y in zip(s.get_state(2), ref.get_state(0)):
+        assert np.array_equal(x, y)
+
+
+def test_amp_scan_full_size_sampled(ad, orc):
+    """The 256-instance, N = 4097 amplitude scan in the bench's launch configuration: sampled
+    instances agree with the oracle after 40 RK4 steps."""
+    insts = W.amp_scan()
+    N = insts[0].N
+    s = _solver(ad, [N] * len(insts))
+    Pi = W.packed([W.gaussian_pi(N, it.eps, it.sigma) for it in insts])
+    s.set_initial(np.zeros_like(Pi), Pi)
+    dt, _ = s.clock()
+    s.evolve(40 * dt[0])
+    for b in (0, 77, 255):
+        r = orc.evolve(np.zeros(N), W.gaussian_pi(N, insts[b].eps, insts[b].sigma), dt[b], 40, sigma=0.5)
+        gPhi, gPi, gA, gd = s.get_state(b)
+        scale = max(1.0, np.abs(r.Pi).max())
+        assert np.abs(gPhi - r.Phi).max() <= 1e-11 * scale
+        assert np.abs(gPi - r.Pi).max() <= 1e-11 * scale
+        assert np.abs(gA - r.A).max() <= 1e-11
+        assert np.abs(gd - r.delta).max() <= 1e-11 * max(1.0, np.abs(r.delta).max())
