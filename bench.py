@@ -34,13 +34,16 @@ from paper_1706_07413_b300 import workloads as W  # noqa: E402
 
 METRIC = "batched FP64 RK4 point-substeps/s"
 UNIT = "point-substeps/s"
-STEP_RK = 128             # RK4 steps per bench step (one persistent launch)
+STEP_RK = 256             # RK4 steps per bench step (one persistent launch)
 B_DEFAULT, N_DEFAULT = 256, 4097
 THETA = 2.0 ** -7
 SIGMA_KO = 0.5
-# FP64 flops (FMA = 2) per point-substep of the evolution kernel, tallied from its source:
-# constraint cell data 48, thread/warp scans 6.75, local pass 9 + exp 14, RHS 32, RK4 7.
-FLOPS_PER_POINT_SUBSTEP = 116.75
+# Algorithmic FP64 flops (FMA = 2) per point-substep, tallied from the evolution kernel's
+# source for the sequential scheme it computes: cell data (rho, midpoint interpolation,
+# Simpson increment, RK4-in-x affine map) 45; sequential scans, A, the fused A e^{-delta}
+# (17, table-driven exp), fluxes 24.75; RHS stencils with dissipation 31; RK4 update 7.
+# The parallel-scan overheads (per-thread aggregates, warp shuffles, ~7 flops) are not counted.
+FLOPS_PER_POINT_SUBSTEP = 107.75
 L2_FLUSH_BYTES = 512 << 20
 
 

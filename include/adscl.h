@@ -67,6 +67,9 @@ typedef struct {
     int32_t device;              /* CUDA device ordinal */
     int32_t one_per_launch;      /* 0: all instances in one persistent launch (CUDA graph);
                                     1: one kernel launch per instance (comparison mode) */
+    int32_t chunk_steps;         /* RK4 steps of one instance per scheduling unit of the
+                                    persistent launch (instances migrate between SMs at chunk
+                                    boundaries); 0 = 16 */
     void *stream;                /* cudaStream_t for all work; NULL = the legacy default stream */
 } adscl_config;
 
@@ -128,6 +131,11 @@ int64_t adscl_launch_count(const adscl_ctx *ctx);
  * independent FMA chains on every SM, best of three timed launches on `stream` (a
  * cudaStream_t or NULL).  It is the ceiling of the FP64-bound evolution kernels. */
 adscl_status adscl_probe_fp64(int32_t device, void *stream, double *tflops);
+
+/* The solver's e^{-x} (Tang's table-driven method, used for F = A e^{-delta}) on n host
+ * values x >= 0, written to host y; exposed so that it can be checked against a reference exp.
+ * Synchronous; allocates its own device buffers. */
+adscl_status adscl_exp_neg(int32_t device, const double *x, double *y, int64_t n);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next call. */
 const char *adscl_last_error(const adscl_ctx *ctx);

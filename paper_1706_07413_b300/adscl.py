@@ -36,6 +36,7 @@ class adscl_config(ctypes.Structure):
                 ("max_device_iters", ctypes.c_int64),
                 ("device", ctypes.c_int32),
                 ("one_per_launch", ctypes.c_int32),
+                ("chunk_steps", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -56,6 +57,7 @@ SIGNATURES = {
     "adscl_get_clock": ([_VP, _VP, _VP], ctypes.c_int),
     "adscl_launch_count": ([_VP], _I64),
     "adscl_probe_fp64": ([_I32, _VP, _VP], ctypes.c_int),
+    "adscl_exp_neg": ([_I32, _VP, _VP, _I64], ctypes.c_int),
     "adscl_last_error": ([_VP], ctypes.c_char_p),
     "adscl_destroy": ([_VP], None),
 }
@@ -94,6 +96,17 @@ def probe_fp64(device=0, stream=None):
     return out.value
 
 
+def exp_neg(x, device=0):
+    """The solver's e^{-x} on a host array (verification of the library's exp)."""
+    lib = load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    st = lib.adscl_exp_neg(device, x.ctypes.data, y.ctypes.data, x.size)
+    if st != ADSCL_OK:
+        raise AdsclError(st, "exp_neg failed")
+    return y
+
+
 class AdsclError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -117,7 +130,7 @@ class Solver:
 
     def __init__(self, N, cfl=0.5, ko_sigma=0.5, collapse_threshold=2.0 ** -7, out_dt=1.0,
                  spec_J=64, ckpt_every=256, device=0, one_per_launch=False, stream=None,
-                 max_device_iters=0):
+                 max_device_iters=0, chunk_steps=0):
         self.lib = load()
         self.N = np.ascontiguousarray(np.asarray(N, dtype=np.int32).ravel())
         self.B = int(self.N.size)
@@ -134,6 +147,7 @@ class Solver:
         cfg.max_device_iters = max_device_iters
         cfg.device = device
         cfg.one_per_launch = 1 if one_per_launch else 0
+        cfg.chunk_steps = chunk_steps
         cfg.stream = stream
         h = ctypes.c_void_p()
         st = self.lib.adscl_create(ctypes.byref(cfg), ctypes.byref(h))

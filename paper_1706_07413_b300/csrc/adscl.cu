@@ -23,6 +23,7 @@ namespace {
 constexpr int kP = 8;      // grid nodes per thread
 constexpr int kNT = 512;   // threads per CTA
 constexpr int kMaxPoints = kP * kNT + 1;  // 4097
+static_assert(6 * field_stride<kP>(kMaxPoints) * 8 + 4096 <= 232448, "shared memory budget");
 
 }  // namespace
 
@@ -35,19 +36,22 @@ struct adscl_ctx {
     double cfl = 0.5, sigma = 0.0, theta = 0.0, out_dt = 1.0;
     int spec_J = 64, ckpt = 256;
     int64_t max_iters = 0;
-    int device = 0, one_per_launch = 0;
+    int device = 0, one_per_launch = 0, chunk = 16;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
 
     std::vector<InstDesc> h_desc;
     std::vector<int32_t> h_order;
     double *d_geo_block = nullptr;
+    double *d_exptab = nullptr;
+    QueueCtl *d_ctl = nullptr;
+    int32_t *d_rounds = nullptr;
     GeoTab *d_geo = nullptr;
     InstDesc *d_desc = nullptr;
     InstState *d_st = nullptr;
     double *d_Phi = nullptr, *d_Pi = nullptr, *d_aPhi = nullptr, *d_aPi = nullptr;
     double *d_scratchA = nullptr, *d_scratchD = nullptr;
-    int32_t *d_order = nullptr, *d_queue = nullptr;
+    int32_t *d_order = nullptr;
     double *d_out = nullptr;      // 3 B doubles: t_reached, t_c, mass
     int32_t *d_outs = nullptr;    // B statuses
     int stride = 0;
@@ -78,13 +82,13 @@ adscl_status fail(adscl_ctx *c, adscl_status s, const char *fmt, ...)
     } while (0)
 
 // Geometry factors of one grid size (host libm, FP64); layout: ws, wt, K, T, iT12 (N each),
-// wsm, wtm (N-1 each).
+// wsm3, wtm (N-1 each).
 std::vector<double> make_geometry(int N)
 {
     const double h = 0.5 * M_PI / (double)(N - 1);
     std::vector<double> t((size_t)7 * N, 0.0);
-    double *ws = t.data(), *wt = ws + N, *K = wt + N, *T = K + N, *iT12 = T + N, *wsm = iT12 + N,
-           *wtm = wsm + N;
+    double *ws = t.data(), *wt = ws + N, *K = wt + N, *T = K + N, *iT12 = T + N, *wsm3 = iT12 + N,
+           *wtm = wsm3 + N;
     for (int i = 0; i < N; ++i) {
         const double x = i * h, s = std::sin(x), c = std::cos(x);
         ws[i] = h * s * c / 6.0;
@@ -100,7 +104,7 @@ std::vector<double> make_geometry(int N)
     }
     for (int c = 0; c < N - 1; ++c) {
         const double x = (c + 0.5) * h, s = std::sin(x), co = std::cos(x), tn = std::tan(x);
-        wsm[c] = h * s * co / (6.0 * 256.0);
+        wsm3[c] = h * s * co / (2.0 * 256.0);
         wtm[c] = h * tn * tn / (6.0 * 256.0);
     }
     return t;
@@ -120,23 +124,48 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, const int32_t
     a.desc = ctx->d_desc;
     a.st = ctx->d_st;
     a.geo = ctx->d_geo;
+    a.exptab = ctx->d_exptab;
     a.Phi = ctx->d_Phi;
     a.Pi = ctx->d_Pi;
     a.aPhi = ctx->d_aPhi;
     a.aPi = ctx->d_aPi;
     a.order = order_dev;
     a.nwork = nwork;
-    a.queue = ctx->d_queue;
+    a.chunk = ctx->chunk;
+    a.mode = mode;
+    a.ctl = ctx->d_ctl;
+    a.rounds = ctx->d_rounds;
+    a.max_spin = ctx->max_iters;
     a.t_end = t_end;
     a.theta = ctx->theta;
     a.outA = outA;
     a.outDelta = outD;
-    a.mode = mode;
-    CK(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int32_t), ctx->stream));
+    // bound on the number of rounds: no instance needs more than ceil(n_end / chunk) chunks
+    long long rounds = 1;
+    if (mode == kModeEvolve) {
+        long long n_end_max = 0;
+        for (const InstDesc &d : ctx->h_desc)
+            n_end_max = std::max(n_end_max, (long long)std::ceil(t_end / d.dt - 1e-9));
+        rounds = n_end_max / ctx->chunk + 2;
+    }
+    if ((long long)nwork * rounds > 0x7ffffff0LL)
+        return fail(ctx, ADSCL_EINVAL, "t_end too large for one launch (%lld rounds)", rounds);
+    a.max_rounds = (int32_t)rounds;
     const int grid = std::min(nwork, ctx->num_sms);
+    queue_init_kernel<<<(nwork + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_ctl, ctx->d_rounds, nwork, grid);
+    CK(cudaGetLastError());
     evolve_kernel<kP, kNT><<<grid, kNT, ctx->smem, ctx->stream>>>(a, ctx->stride);
     CK(cudaGetLastError());
-    ctx->launches += 1;
+    ctx->launches += 2;
+    return ADSCL_OK;
+}
+
+// after a synchronising call: report a device wait that ran out
+adscl_status check_timeout(adscl_ctx *ctx)
+{
+    QueueCtl c{};
+    CK(cudaMemcpy(&c, ctx->d_ctl, sizeof c, cudaMemcpyDeviceToHost));
+    if (c.error) return fail(ctx, ADSCL_ETIMEOUT, "a chunk wait ran out (work item %d)", c.error - 1);
     return ADSCL_OK;
 }
 
@@ -184,6 +213,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     ctx->max_iters = cfg->max_device_iters ? cfg->max_device_iters : (int64_t)1 << 24;
     ctx->device = cfg->device;
     ctx->one_per_launch = cfg->one_per_launch;
+    ctx->chunk = cfg->chunk_steps > 0 ? cfg->chunk_steps : 16;
     ctx->stream = (cudaStream_t)cfg->stream;
     *out = ctx;
 
@@ -222,7 +252,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
             g.K = base + 2 * (size_t)n;
             g.T = base + 3 * (size_t)n;
             g.iT12 = base + 4 * (size_t)n;
-            g.wsm = base + 5 * (size_t)n;
+            g.wsm3 = base + 5 * (size_t)n;
             g.wtm = base + 6 * (size_t)n;
             h_geo.push_back(g);
             pos += t.size();
@@ -246,6 +276,11 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
         d.c12 = 1.0 / (12.0 * h);
         d.c3 = 3.0 / (12.0 * h);
         d.cko = ctx->sigma / (64.0 * h);
+        d.rko = 3.0 * ctx->sigma / 16.0;
+        d.dt6c = d.dt6 * d.c12;
+        d.dt3c = d.dt3 * d.c12;
+        d.dt2c = d.dt2 * d.c12;
+        d.dtc = d.dt * d.c12;
     }
     CK(cudaMalloc(&ctx->d_desc, ctx->B * sizeof(InstDesc)));
     CK(cudaMemcpy(ctx->d_desc, ctx->h_desc.data(), ctx->B * sizeof(InstDesc), cudaMemcpyHostToDevice));
@@ -269,14 +304,23 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
                      [&](int x, int y) { return ctx->N[x] > ctx->N[y]; });
     CK(cudaMalloc(&ctx->d_order, (ctx->B + 1) * sizeof(int32_t)));
     CK(cudaMemcpy(ctx->d_order, ctx->h_order.data(), ctx->B * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&ctx->d_queue, sizeof(int32_t)));
+    CK(cudaMalloc(&ctx->d_ctl, sizeof(QueueCtl)));
+    CK(cudaMemset(ctx->d_ctl, 0, sizeof(QueueCtl)));
+    CK(cudaMalloc(&ctx->d_rounds, (ctx->B + 1) * sizeof(int32_t)));
+    {
+        // 2^{j/256}, computed in extended precision and rounded once to double
+        std::vector<double> tab(kExpTableSize);
+        for (int j = 0; j < kExpTableSize; ++j) tab[j] = (double)std::exp2l((long double)j / 256.0L);
+        CK(cudaMalloc(&ctx->d_exptab, kExpTableSize * sizeof(double)));
+        CK(cudaMemcpy(ctx->d_exptab, tab.data(), kExpTableSize * sizeof(double), cudaMemcpyHostToDevice));
+    }
     CK(cudaMalloc(&ctx->d_out, 3 * (size_t)ctx->B * sizeof(double)));
     CK(cudaMalloc(&ctx->d_outs, (size_t)ctx->B * sizeof(int32_t)));
 
-    ctx->stride = ((ctx->Nmax + 2 * kG) + 1) & ~1;
-    ctx->smem = (size_t)4 * ctx->stride * sizeof(double);
+    ctx->stride = field_stride<kP>(ctx->Nmax);
+    ctx->smem = (size_t)6 * ctx->stride * sizeof(double);
     // the attribute is per kernel, not per context: always raise it to the largest grid
-    const size_t smem_max = (size_t)4 * (((kMaxPoints + 2 * kG) + 1) & ~1) * sizeof(double);
+    const size_t smem_max = (size_t)6 * field_stride<kP>(kMaxPoints) * sizeof(double);
     CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem_max));
     return ADSCL_OK;
@@ -329,8 +373,9 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
     }
     const int B = ctx->B;
     double *o = ctx->d_out;
-    gather_kernel<<<(B + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_desc, ctx->d_st, B, t_end, 1, o,
-                                                           o + B, o + 2 * B, ctx->d_outs);
+    gather_kernel<<<(B + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_desc, ctx->d_st, B, t_end, 1,
+                                                           ctx->d_ctl, ctx->d_order, o, o + B,
+                                                           o + 2 * B, ctx->d_outs);
     CK(cudaGetLastError());
     ctx->launches += 1;
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -338,7 +383,10 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
     if (t_collapse) CK(cudaMemcpyAsync(t_collapse, o + B, B * sizeof(double), kind, ctx->stream));
     if (mass) CK(cudaMemcpyAsync(mass, o + 2 * B, B * sizeof(double), kind, ctx->stream));
     if (inst_status) CK(cudaMemcpyAsync(inst_status, ctx->d_outs, B * sizeof(int32_t), kind, ctx->stream));
-    if (!ptr_is_device) CK(cudaStreamSynchronize(ctx->stream));
+    if (!ptr_is_device) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        return check_timeout(ctx);
+    }
     return ADSCL_OK;
 }
 
@@ -431,7 +479,7 @@ void adscl_destroy(adscl_ctx *ctx)
     else cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_geo_block, ctx->d_geo, ctx->d_desc, ctx->d_st, ctx->d_Phi, ctx->d_Pi,
                     ctx->d_aPhi, ctx->d_aPi, ctx->d_scratchA, ctx->d_scratchD, ctx->d_order,
-                    ctx->d_queue, ctx->d_out, ctx->d_outs};
+                    ctx->d_ctl, ctx->d_rounds, ctx->d_exptab, ctx->d_out, ctx->d_outs};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;

@@ -1,8 +1,7 @@
 // evolve.cuh -- persistent FP64 method-of-lines kernel for the AdS4 Einstein-Klein-Gordon
 // system of arXiv:1706.07413, Sec. II (Eqs. (eq:phi), (eq:pi), (eq:aprime), (eq:delta)).
 //
-// One CTA evolves one instance at a time with the whole stage slice resident in shared
-// memory; CTAs pull instances from an atomic work queue (persistent grid, one CTA per SM).
+// One CTA evolves one instance at a time with its stage slice resident in shared memory.
 // Thread t owns the P contiguous grid nodes t*P .. t*P+P-1 and the cells to their right;
 // node N-1 (x = pi/2, where Phi = Pi = 0) is owned by nobody and written as a constant.
 //
@@ -14,17 +13,28 @@
 //      (per-thread serial, then warp shuffles, then one warp over the warp totals);
 //   3. A = 1 - m cos^3 x / sin x, F = A e^{-delta}, fluxes f = F Pi and u = tan^2 x F Phi;
 //   4. RHS: Phi-dot = D f, Pi-dot = D u / tan^2 x (Eq. (eq:pi) in its conservative form),
-//      Kreiss-Oliger dissipation, classic RK4 accumulation.
+//      Kreiss-Oliger dissipation, classic RK4 accumulation into the other stage buffer.
 // The FP64 pipe is the bound on this chip, so every term is arranged to minimise FP64
-// instructions; comparisons and finiteness tests run on the integer pipe.
+// instructions; comparisons, finiteness tests and indexing run on the integer pipe.
+//
+// Scheduling: work is cut into chunks of `chunk` RK4 steps of one instance.  Tickets are
+// handed out in round-major order (round r, work item q); a chunk waits (bounded) for the
+// previous chunk of the same instance to be released by whichever CTA ran it, so instances
+// migrate between SMs and all SMs stay busy even when the batch is not a multiple of the SM
+// count.  A CTA retires when fewer instances remain than CTAs take tickets, which keeps every
+// wait shorter than about one chunk.  A wait that exceeds its iteration limit records an error
+// and the CTAs leave; nothing spins without a bound.
+//
+// Shared-memory layout: node i of a field array lives at (i + 8) + (i + 8) / P, i.e. one pad
+// double after every P nodes, so that the P-strided accesses of a warp hit distinct banks.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <cstdint>
 
-namespace adscl {
+#include "expneg.cuh"
 
-constexpr int kG = 4;  // ghost padding on each side of the shared-memory field arrays
+namespace adscl {
 
 // per distinct grid size: geometry factors at nodes (length N) and cell midpoints (N-1)
 struct GeoTab {
@@ -33,8 +43,8 @@ struct GeoTab {
     const double *K;     // cos^3 x / sin x          (0 at both ends)
     const double *T;     // tan^2 x                  (0 at x = pi/2)
     const double *iT12;  // 1 / (12 h tan^2 x)       (0 at both ends)
-    const double *wsm;   // h sin x cos x / (6*256) at x_{c+1/2}
-    const double *wtm;   // h tan^2 x / (6*256)     at x_{c+1/2}
+    const double *wsm3;  // 3 h sin x cos x / (6*256) at x_{c+1/2}
+    const double *wtm;   // h tan^2 x / (6*256)       at x_{c+1/2}
 };
 
 struct InstDesc {
@@ -45,6 +55,8 @@ struct InstDesc {
     double c12;   // 1 / (12 h)
     double c3;    // 3 / (12 h)
     double cko;   // sigma / (64 h)
+    double rko;   // cko / c12 = 3 sigma / 16
+    double dt6c, dt3c, dt2c, dtc;  // dt/6, dt/3, dt/2, dt times c12
 };
 
 enum : int32_t { kRunning = 0, kDone = 1, kCollapsed = 2, kNonfinite = 3, kTimeout = 4 };
@@ -61,19 +73,33 @@ struct InstState {
 
 enum : int32_t { kModeEvolve = 0, kModeInit = 1, kModeSolve = 2 };
 
+struct QueueCtl {
+    int32_t ticket;      // next ticket
+    int32_t unfinished;  // work items not yet finished in this launch
+    int32_t active;      // CTAs still taking tickets
+    int32_t error;       // 0, or 1 + work item whose wait ran out
+};
+
+constexpr int32_t kFinished = 0x7fffffff;
+
 struct EvolveArgs {
     const InstDesc *desc;
     InstState *st;
     const GeoTab *geo;
-    double *Phi, *Pi;     // packed current slices (updated in place)
-    double *aPhi, *aPi;   // packed RK4 accumulators (workspace)
-    const int32_t *order; // work item -> instance
+    const double *exptab;  // 2^{j/256}, j < 256
+    double *Phi, *Pi;      // packed current slices (updated in place)
+    double *aPhi, *aPi;    // packed RK4 accumulators (workspace)
+    const int32_t *order;  // work item -> instance
     int32_t nwork;
-    int32_t *queue;       // work counter, zero before the launch
+    int32_t chunk;         // RK4 steps per ticket
+    int32_t max_rounds;    // tickets beyond nwork * max_rounds are never handed out
+    int32_t mode;
+    QueueCtl *ctl;
+    int32_t *rounds;       // per work item: rounds completed, or kFinished
+    long long max_spin;    // iteration limit of a wait
     double t_end;
     double theta;
     double *outA, *outDelta;  // kModeSolve only: packed A, delta of the slice (may be null)
-    int32_t mode;
 };
 
 // order-preserving map of doubles onto signed 64-bit integers (integer-pipe min)
@@ -89,79 +115,158 @@ __device__ __forceinline__ bool is_finite_bits(double v) {
 }
 __device__ __forceinline__ long long min_ll(long long a, long long b) { return a < b ? a : b; }
 
+__device__ __forceinline__ int ld_acquire(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed(const int32_t *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// offset of node (P*t + m) relative to the thread base (P+1)*t, for m >= -8
+template <int P>
+__device__ __forceinline__ constexpr int soff(int m) { return (m + 8) + (m + 8) / P; }
+// absolute padded position of node i >= -8
+template <int P>
+__device__ __forceinline__ int spos(int i) { return (i + 8) + (i + 8) / P; }
+
+// length of one padded shared-memory field array for grids up to Nmax nodes
+template <int P>
+__host__ __device__ constexpr int field_stride(int Nmax) {
+    return (((Nmax + 12) + (Nmax + 12) / P + 1) + 1) & ~1;
+}
+
+__global__ void queue_init_kernel(QueueCtl *ctl, int32_t *rounds, int nwork, int grid)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        ctl->ticket = 0;
+        ctl->unfinished = nwork;
+        ctl->active = grid;
+        ctl->error = 0;
+    }
+    if (i < nwork) rounds[i] = 0;
+}
+
 template <int P, int NT>
 __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
 {
-    static_assert(P >= 4, "ghost fill needs >= 4 nodes per thread");
+    static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
     constexpr int NW = NT / 32;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ double smem[];
-    double *sPhi = smem;
-    double *sPi = sPhi + stride;
-    double *sF = sPi + stride;
-    double *sU = sF + stride;
+    double *bufA0 = smem, *bufA1 = smem + stride;                   // stage Phi, Pi
+    double *bufB0 = smem + 2 * stride, *bufB1 = smem + 3 * stride;  // next stage Phi, Pi
+    double *sF = smem + 4 * stride, *sU = smem + 5 * stride;        // alpha/beta, then f/u
+    __shared__ double s_tab[kExpTableSize];
     __shared__ double wAl[NW], wBe[NW], wDe[NW], cM[NW], cD[NW];
     __shared__ long long wMin[NW];
     __shared__ double s_mass, s_d0;
-    __shared__ int s_item;
+    __shared__ int s_cmd, s_q, s_r, s_leave;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < kExpTableSize; i += NT) s_tab[i] = a.exptab[i];
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(a.queue, 1);
+        // ------------------------------------------------------------ take a ticket
+        if (tid == 0) {
+            int cmd = 0, q = 0, r = 0;  // cmd 0: leave, 1: run
+            for (;;) {
+                if (ld_relaxed(&a.ctl->unfinished) == 0 || ld_relaxed(&a.ctl->error) != 0) break;
+                const int t = atomicAdd(&a.ctl->ticket, 1);
+                if (t >= a.nwork * a.max_rounds) break;
+                r = t / a.nwork;
+                q = t - r * a.nwork;
+                int rd = ld_acquire(a.rounds + q);
+                long long spin = 0;
+                while (rd < r) {  // the previous chunk of this instance is still running
+                    if (++spin > a.max_spin) break;
+                    __nanosleep(256);
+                    rd = ld_acquire(a.rounds + q);
+                }
+                if (rd == kFinished) continue;
+                if (rd < r) {
+                    atomicCAS(&a.ctl->error, 0, q + 1);
+                    break;
+                }
+                cmd = 1;
+                break;
+            }
+            s_cmd = cmd;
+            s_q = q;
+            s_r = r;
+        }
         __syncthreads();
-        const int item = s_item;
-        __syncthreads();
-        if (item >= a.nwork) break;
-        const int b = a.order[item];
+        if (s_cmd == 0) break;
+        const int q = s_q, rnd = s_r;
+        const int b = a.order[q];
         const InstDesc d = a.desc[b];
-        InstState S = a.st[b];
+        InstState S;
+        {
+            const InstState *sp = a.st + b;
+            S.step = __ldcg(&sp->step);
+            S.t_c = __ldcg(&sp->t_c);
+            S.minA = __ldcg(&sp->minA);
+            S.mass = __ldcg(&sp->mass);
+            S.delta0 = __ldcg(&sp->delta0);
+            S.status = __ldcg(&sp->status);
+        }
+        __syncthreads();  // every thread has read s_cmd, s_q, s_r before thread 0 rewrites them
+
         const double dt = d.dt;
-        long long n_end = 0;
+        long long n_end = S.step, n_target = S.step;
         if (a.mode == kModeEvolve) {
-            if (S.status != kRunning) continue;
             n_end = (long long)ceil(a.t_end / dt - 1e-9);
-            if (S.step >= n_end) continue;
+            n_target = min(n_end, S.step + (long long)a.chunk);
         }
         const int N = d.N;
         const int Tn = (N - 1) / P;
         const bool act = tid < Tn;
         const bool last = tid == Tn - 1;
         const int i0 = tid * P;
+        const int tb = (P + 1) * tid;  // thread base in the padded arrays
         const GeoTab g = a.geo[d.geo];
         double *uPhi = a.Phi + d.off, *uPi = a.Pi + d.off;
         double *cPhi = a.aPhi + d.off, *cPi = a.aPi + d.off;
+        const bool skip = (a.mode == kModeEvolve) && (S.status != kRunning || S.step >= n_target);
 
-        // ---- load the current slice into the stage arrays (boundary values imposed) ----
-        {
-            double p[P], q[P];
+        long long step = S.step;
+        double minA_prev = S.minA, minA = S.minA, mass = S.mass, d0 = S.delta0, t_c = S.t_c;
+        int32_t status = S.status;
+
+        if (!skip) {
+            // ---- load the current slice into stage buffer A (boundary values imposed) ----
             if (act) {
+                double p[P], qv[P];
 #pragma unroll
                 for (int k = 0; k < P; ++k) {
-                    p[k] = uPhi[i0 + k];
-                    q[k] = uPi[i0 + k];
+                    p[k] = __ldcg(uPhi + i0 + k);
+                    qv[k] = __ldcg(uPi + i0 + k);
                 }
                 if (tid == 0) p[0] = 0.0;
 #pragma unroll
                 for (int k = 0; k < P; ++k) {
-                    sPhi[kG + i0 + k] = p[k];
-                    sPi[kG + i0 + k] = q[k];
+                    bufA0[tb + soff<P>(k)] = p[k];
+                    bufA1[tb + soff<P>(k)] = qv[k];
                 }
                 if (tid == 0) {
 #pragma unroll
                     for (int j = 1; j <= 3; ++j) {
-                        sPhi[kG - j] = -p[j];
-                        sPi[kG - j] = q[j];
+                        bufA0[spos<P>(-j)] = -p[j];
+                        bufA1[spos<P>(-j)] = qv[j];
                     }
                     if (a.mode == kModeInit) uPhi[0] = 0.0;
                 }
                 if (last) {
-                    sPhi[kG + N - 1] = 0.0;
-                    sPi[kG + N - 1] = 0.0;
+                    bufA0[spos<P>(N - 1)] = 0.0;
+                    bufA1[spos<P>(N - 1)] = 0.0;
 #pragma unroll
                     for (int j = 1; j <= 3; ++j) {
-                        sPhi[kG + N - 1 + j] = p[P - j];
-                        sPi[kG + N - 1 + j] = -q[P - j];
+                        bufA0[spos<P>(N - 1 + j)] = p[P - j];
+                        bufA1[spos<P>(N - 1 + j)] = -qv[P - j];
                     }
                     if (a.mode == kModeInit) {
                         uPhi[N - 1] = 0.0;
@@ -169,291 +274,327 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                     }
                 }
             }
-        }
-        __syncthreads();
+            __syncthreads();
 
-        long long step = S.step;
-        double minA_prev = S.minA, minA = S.minA, mass = S.mass, d0 = S.delta0, t_c = S.t_c;
-        int32_t status = S.status;
-        bool first = true;
-
-        for (;;) {
+            double *S0 = bufA0, *S1 = bufA1, *D0 = bufB0, *D1 = bufB1;
+            bool first = true;
+            for (;;) {
 #pragma unroll 1
-            for (int s = 0; s < 4; ++s) {
-                // ================= constraint solve on the stage slice =================
-                double al[P], be[P], De[P];
-                double aT = 1.0, bT = 0.0, SD = 0.0;
-                if (act) {
-                    double ph[P + 3], pq[P + 3];  // nodes i0-1 .. i0+P+1
-#pragma unroll
-                    for (int k = 0; k < P + 3; ++k) {
-                        ph[k] = sPhi[kG + i0 - 1 + k];
-                        pq[k] = sPi[kG + i0 - 1 + k];
-                    }
-                    double qn[P + 1], rn[P + 1];  // per node: h s rho / 6, h tan^2 rho / 6
-#pragma unroll
-                    for (int k = 0; k <= P; ++k) {
-                        const double rho = fma(ph[k + 1], ph[k + 1], pq[k + 1] * pq[k + 1]);
-                        qn[k] = __ldg(g.ws + i0 + k) * rho;
-                        rn[k] = __ldg(g.wt + i0 + k) * rho;
-                    }
-#pragma unroll
-                    for (int k = 0; k < P; ++k) {
-                        const int c = i0 + k;
-                        // 16 * (midpoint value) by the 4-point Lagrange formula
-                        const double p16 = fma(9.0, ph[k + 1] + ph[k + 2], -(ph[k] + ph[k + 3]));
-                        const double q16 = fma(9.0, pq[k + 1] + pq[k + 2], -(pq[k] + pq[k + 3]));
-                        const double rm = fma(p16, p16, q16 * q16);  // 256 rho_{c+1/2}
-                        const double qm = __ldg(g.wsm + c) * rm;     // h s rho / 6 at the midpoint
-                        const double tm = __ldg(g.wtm + c) * rm;     // h tan^2 rho / 6 at the midpoint
-                        // Simpson increment of delta over the cell
-                        De[k] = fma(4.0, qm, qn[k] + qn[k + 1]);
-                        // RK4 in x of m' = a - b m over the cell, as the affine map
-                        // m -> alpha m + beta (alpha: y' = -b y, y = 1; beta: y' = a - b y, y = 0)
-                        const double qm3 = 3.0 * qm;
-                        const double y2 = fma(-3.0, qn[k], 1.0);
-                        const double y3 = fma(-qm3, y2, 1.0);
-                        const double y4 = fma(-2.0 * qm3, y3, 1.0);
-                        al[k] = fma(-2.0 * qm, y2 + y3, fma(-qn[k + 1], y4, 1.0 - qn[k]));
-                        const double w2 = fma(-qm3, rn[k], tm);
-                        const double w3 = fma(-qm, 3.0 * w2, tm);
-                        const double w4 = fma(-qn[k + 1], 6.0 * w3, rn[k + 1]);
-                        be[k] = fma(2.0, w2 + w3, rn[k]) + w4;
-                    }
-                    aT = al[0];
-                    bT = be[0];
-                    SD = De[0];
-#pragma unroll
-                    for (int k = 1; k < P; ++k) {
-                        bT = fma(al[k], bT, be[k]);
-                        aT = aT * al[k];
-                        SD = SD + De[k];
-                    }
-                }
-                // warp-level inclusive scans: affine prefix (lanes ascending), delta suffix sum
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const double ap = __shfl_up_sync(FULL, aT, o);
-                    const double bp = __shfl_up_sync(FULL, bT, o);
-                    const double dn = __shfl_down_sync(FULL, SD, o);
-                    if (lane >= o) {
-                        bT = fma(aT, bp, bT);
-                        aT = aT * ap;
-                    }
-                    if (lane + o < 32) SD = SD + dn;
-                }
-                double aEx = __shfl_up_sync(FULL, aT, 1);
-                double bEx = __shfl_up_sync(FULL, bT, 1);
-                double dEx = __shfl_down_sync(FULL, SD, 1);
-                if (lane == 0) { aEx = 1.0; bEx = 0.0; }
-                if (lane == 31) dEx = 0.0;
-                if (lane == 31) { wAl[wid] = aT; wBe[wid] = bT; }
-                if (lane == 0) wDe[wid] = SD;
-                __syncthreads();
-                if (wid == 0) {
-                    double A_ = lane < NW ? wAl[lane] : 1.0;
-                    double B_ = lane < NW ? wBe[lane] : 0.0;
-                    double D_ = lane < NW ? wDe[lane] : 0.0;
-#pragma unroll
-                    for (int o = 1; o < NW; o <<= 1) {
-                        const double ap = __shfl_up_sync(FULL, A_, o);
-                        const double bp = __shfl_up_sync(FULL, B_, o);
-                        const double dn = __shfl_down_sync(FULL, D_, o);
-                        if (lane >= o) {
-                            B_ = fma(A_, bp, B_);
-                            A_ = A_ * ap;
-                        }
-                        if (lane + o < NW) D_ = D_ + dn;
-                    }
-                    double bw = __shfl_up_sync(FULL, B_, 1);
-                    double dw = __shfl_down_sync(FULL, D_, 1);
-                    if (lane == 0) bw = 0.0;
-                    if (lane + 1 >= NW) dw = 0.0;
-                    if (lane < NW) { cM[lane] = bw; cD[lane] = dw; }
-                }
-                __syncthreads();
-
-                long long kmin = 0x7FFFFFFFFFFFFFFFLL;
-                if (act) {
-                    double m = fma(aEx, cM[wid], bEx);   // m at node i0
-                    double dl[P];                        // delta at nodes i0 .. i0+P-1
-                    double dc = dEx + cD[wid];           // delta at node i0+P
-#pragma unroll
-                    for (int k = P - 1; k >= 0; --k) {
-                        dc = dc + De[k];
-                        dl[k] = dc;
-                    }
-                    double fv[P], uv[P];
-                    double g1 = 0.0, g2 = 0.0;
-#pragma unroll
-                    for (int k = 0; k < P; ++k) {
-                        const int i = i0 + k;
-                        const double Ai = fma(-m, __ldg(g.K + i), 1.0);
-                        kmin = min_ll(kmin, order_key(Ai));
-                        const double Fi = Ai * exp(-dl[k]);
-                        const double phi = sPhi[kG + i], pii = sPi[kG + i];
-                        const double gi = Fi * phi;
-                        fv[k] = Fi * pii;
-                        uv[k] = __ldg(g.T + i) * gi;
-                        if (k == 1) g1 = gi;
-                        if (k == 2) g2 = gi;
-                        sF[kG + i] = fv[k];
-                        sU[kG + i] = uv[k];
-                        if (a.outA) {
-                            a.outA[d.off + i] = Ai;
-                            a.outDelta[d.off + i] = dl[k];
-                        }
-                        if (k < P - 1) m = fma(al[k], m, be[k]);
-                    }
-                    if (tid == 0) {
-                        s_d0 = dl[0];
-                        sF[kG - 1] = fv[1];
-                        sF[kG - 2] = fv[2];
-                        sU[kG - 1] = -uv[1];
-                        sU[kG - 2] = -uv[2];
-                        // Pi-dot at x = 0 needs (F Phi)'(0) = (16 g_1 - 2 g_2) / (12 h)
-                        sF[kG - 3] = fma(16.0, g1, -2.0 * g2);
-                    }
-                    if (last) {
-                        s_mass = fma(al[P - 1], m, be[P - 1]);
-                        sF[kG + N - 1] = 0.0;
-                        sF[kG + N] = -fv[P - 1];
-                        sF[kG + N + 1] = -fv[P - 2];
-                        sU[kG + N - 1] = (4.0 * uv[P - 1] - uv[P - 2]) * (1.0 / 3.0);
-                        sU[kG + N] = uv[P - 1];
-                        sU[kG + N + 1] = uv[P - 2];
-                        if (a.outA) {
-                            a.outA[d.off + N - 1] = 1.0;
-                            a.outDelta[d.off + N - 1] = 0.0;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) kmin = min_ll(kmin, __shfl_xor_sync(FULL, kmin, o));
-                if (lane == 0) wMin[wid] = kmin;
-                __syncthreads();
-
-                if (s == 0) {
-                    // ---------- end-of-step diagnostics on the slice t = step * dt ----------
-                    long long km = wMin[0];
-#pragma unroll
-                    for (int w = 1; w < NW; ++w) km = min_ll(km, wMin[w]);
-                    minA = order_key_inv(km);
-                    mass = s_mass;
-                    d0 = s_d0;
-                    const bool nonfin = !(is_finite_bits(mass) && is_finite_bits(d0));
-                    bool stop = false;
-                    if (a.mode != kModeEvolve) {
-                        if (a.mode == kModeInit) {
-                            status = nonfin ? kNonfinite : (minA < a.theta ? kCollapsed : kRunning);
-                            t_c = (status == kCollapsed) ? 0.0 : __longlong_as_double(0x7FF0000000000000LL);
-                        }
-                        stop = true;
-                    } else if (!first) {
-                        if (nonfin) {
-                            status = kNonfinite;
-                            stop = true;
-                        } else if (minA < a.theta) {
-                            // min A crossed theta between t_{n-1} and t_n: linear interpolation
-                            t_c = (double)(step - 1) * dt + dt * (minA_prev - a.theta) / (minA_prev - minA);
-                            status = kCollapsed;
-                            stop = true;
-                        }
-                    }
-                    if (!stop && step >= n_end) stop = true;
-                    if (stop) goto finish;
-                    minA_prev = minA;
-                    first = false;
-                }
-
-                // ================= right-hand side and RK4 update =================
-                {
-                    double nP[P], nQ[P];
+                for (int s = 0; s < 4; ++s) {
+                    // ================= constraint solve on the stage slice =================
+                    double De[P];
+                    double aT = 1.0, bT = 0.0, SD = 0.0;
                     if (act) {
-                        const double wacc = (s == 0 || s == 3) ? d.dt6 : d.dt3;
-                        const double wst = (s == 2) ? dt : d.dt2;
+                        const double *Sp = S0 + tb, *Sq = S1 + tb;
+                        double pm1 = Sp[soff<P>(-1)], p0 = Sp[soff<P>(0)], p1 = Sp[soff<P>(1)];
+                        double qm1 = Sq[soff<P>(-1)], q0 = Sq[soff<P>(0)], q1 = Sq[soff<P>(1)];
+                        const double rho0 = fma(p0, p0, q0 * q0);
+                        double qn0 = __ldg(g.ws + i0) * rho0, rn0 = __ldg(g.wt + i0) * rho0;
+#pragma unroll
+                        for (int k = 0; k < P; ++k) {
+                            const int c = i0 + k;
+                            const double p2 = Sp[soff<P>(k + 2)], q2 = Sq[soff<P>(k + 2)];
+                            const double rho1 = fma(p1, p1, q1 * q1);
+                            const double qn1 = __ldg(g.ws + c + 1) * rho1;
+                            const double rn1 = __ldg(g.wt + c + 1) * rho1;
+                            // 16 * (midpoint value) by the 4-point Lagrange formula
+                            const double p16 = fma(9.0, p0 + p1, -(pm1 + p2));
+                            const double q16 = fma(9.0, q0 + q1, -(qm1 + q2));
+                            const double rm = fma(p16, p16, q16 * q16);  // 256 rho_{c+1/2}
+                            const double qm3 = __ldg(g.wsm3 + c) * rm;   // 3 (h s rho / 6) at the midpoint
+                            const double tm = __ldg(g.wtm + c) * rm;     // h tan^2 rho / 6 there
+                            const double s01 = qn0 + qn1;
+                            // Simpson increment of delta over the cell
+                            De[k] = fma(4.0 / 3.0, qm3, s01);
+                            // RK4 in x of m' = a - b m over the cell as the affine map
+                            // m -> alpha m + beta (alpha: y' = -b y, y(0) = 1; beta: y' = a - b y,
+                            // y(0) = 0), with the stage values eliminated algebraically:
+                            //   alpha = 1 - q0 - q1 - 3qm [ (2/3) y2 + y3 (2/3 - 2 q1) ],
+                            //   y2 = 1 - 3 q0, y3 = 1 - 3 qm y2;
+                            //   beta = r0 + r1 + 2 w2 + w3 (2 - 6 q1),
+                            //   w2 = tm - 3 qm r0, w3 = tm - 3 qm w2,
+                            // q = h b / 6, r = h a / 6 at the cell's left end, midpoint, right end.
+                            const double y2 = fma(-3.0, qn0, 1.0);
+                            const double y3 = fma(-qm3, y2, 1.0);
+                            const double ca = fma(-2.0, qn1, 2.0 / 3.0);
+                            const double al = fma(-qm3, fma(y3, ca, fma(-2.0, qn0, 2.0 / 3.0)), 1.0 - s01);
+                            const double w2 = fma(-qm3, rn0, tm);
+                            const double w3 = fma(-qm3, w2, tm);
+                            const double be = fma(w3, fma(-6.0, qn1, 2.0), fma(2.0, w2, rn0 + rn1));
+                            sF[tb + soff<P>(k)] = al;
+                            sU[tb + soff<P>(k)] = be;
+                            if (k == 0) {
+                                aT = al;
+                                bT = be;
+                                SD = De[0];
+                            } else {
+                                bT = fma(al, bT, be);
+                                aT = aT * al;
+                                SD = SD + De[k];
+                            }
+                            pm1 = p0; p0 = p1; p1 = p2;
+                            qm1 = q0; q0 = q1; q1 = q2;
+                            qn0 = qn1; rn0 = rn1;
+                        }
+                    }
+                    // warp-level inclusive scans: affine prefix (lanes ascending), delta suffix sum
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const double ap = __shfl_up_sync(FULL, aT, o);
+                        const double bp = __shfl_up_sync(FULL, bT, o);
+                        const double dn = __shfl_down_sync(FULL, SD, o);
+                        if (lane >= o) {
+                            bT = fma(aT, bp, bT);
+                            aT = aT * ap;
+                        }
+                        if (lane + o < 32) SD = SD + dn;
+                    }
+                    double aEx = __shfl_up_sync(FULL, aT, 1);
+                    double bEx = __shfl_up_sync(FULL, bT, 1);
+                    double dEx = __shfl_down_sync(FULL, SD, 1);
+                    if (lane == 0) { aEx = 1.0; bEx = 0.0; }
+                    if (lane == 31) dEx = 0.0;
+                    if (lane == 31) { wAl[wid] = aT; wBe[wid] = bT; }
+                    if (lane == 0) wDe[wid] = SD;
+                    __syncthreads();
+                    if (wid == 0) {
+                        double A_ = lane < NW ? wAl[lane] : 1.0;
+                        double B_ = lane < NW ? wBe[lane] : 0.0;
+                        double D_ = lane < NW ? wDe[lane] : 0.0;
+#pragma unroll
+                        for (int o = 1; o < NW; o <<= 1) {
+                            const double ap = __shfl_up_sync(FULL, A_, o);
+                            const double bp = __shfl_up_sync(FULL, B_, o);
+                            const double dn = __shfl_down_sync(FULL, D_, o);
+                            if (lane >= o) {
+                                B_ = fma(A_, bp, B_);
+                                A_ = A_ * ap;
+                            }
+                            if (lane + o < NW) D_ = D_ + dn;
+                        }
+                        double bw = __shfl_up_sync(FULL, B_, 1);
+                        double dw = __shfl_down_sync(FULL, D_, 1);
+                        if (lane == 0) bw = 0.0;
+                        if (lane + 1 >= NW) dw = 0.0;
+                        if (lane < NW) { cM[lane] = bw; cD[lane] = dw; }
+                    }
+                    __syncthreads();
+
+                    long long kmin = 0x7FFFFFFFFFFFFFFFLL;
+                    if (act) {
+                        const double *Sp = S0 + tb, *Sq = S1 + tb;
+                        double m = fma(aEx, cM[wid], bEx);   // m at node i0
+                        double dc = dEx + cD[wid];           // delta at node i0+P
+#pragma unroll
+                        for (int k = P - 1; k >= 0; --k) {   // delta at nodes i0 .. i0+P-1
+                            dc = dc + De[k];
+                            De[k] = dc;
+                        }
+                        double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0, fm1 = 0.0, fm2 = 0.0;
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
-                            const double *f = sF + kG + i, *u = sU + kG + i;
-                            const double *p = sPhi + kG + i, *q = sPi + kG + i;
-                            const double Df = (f[-2] - f[2]) + 8.0 * (f[1] - f[-1]);
-                            const double Du = (u[-2] - u[2]) + 8.0 * (u[1] - u[-1]);
-                            double kp = fma(-20.0, p[0], fma(15.0, p[-1] + p[1], fma(-6.0, p[-2] + p[2], p[-3] + p[3])));
-                            double kq = fma(-20.0, q[0], fma(15.0, q[-1] + q[1], fma(-6.0, q[-2] + q[2], q[-3] + q[3])));
-                            double dP = fma(d.c12, Df, d.cko * kp);
+                            const double al = sF[tb + soff<P>(k)], be = sU[tb + soff<P>(k)];
+                            const double Ai = fma(-m, __ldg(g.K + i), 1.0);
+                            kmin = min_ll(kmin, order_key(Ai));
+                            const double Fi = a_exp_neg(Ai, De[k], s_tab);
+                            const double gi = Fi * Sp[soff<P>(k)];
+                            const double fi = Fi * Sq[soff<P>(k)];
+                            const double ui = __ldg(g.T + i) * gi;
+                            sF[tb + soff<P>(k)] = fi;
+                            sU[tb + soff<P>(k)] = ui;
+                            if (k == 1) g1 = gi;
+                            if (k == 2) g2 = gi;
+                            if (tid == 0 && (k == 1 || k == 2)) {
+                                sF[spos<P>(-k)] = fi;   // f = F Pi: even about x = 0
+                                sU[spos<P>(-k)] = -ui;  // u = tan^2 F Phi: odd about x = 0
+                            }
+                            if (k == P - 1) { fm1 = fi; um1 = ui; }
+                            if (k == P - 2) { fm2 = fi; um2 = ui; }
+                            if (a.outA) {
+                                a.outA[d.off + i] = Ai;
+                                a.outDelta[d.off + i] = De[k];
+                            }
+                            if (k < P - 1) m = fma(al, m, be);
+                            else if (last) s_mass = fma(al, m, be);
+                        }
+                        if (tid == 0) {
+                            s_d0 = De[0];
+                            // Pi-dot at x = 0 needs (F Phi)'(0) = (16 g_1 - 2 g_2) / (12 h)
+                            sF[spos<P>(-3)] = fma(16.0, g1, -2.0 * g2);
+                        }
+                        if (last) {
+                            // f odd and u even about x = pi/2; u(pi/2) by even extrapolation
+                            sF[spos<P>(N - 1)] = 0.0;
+                            sF[spos<P>(N)] = -fm1;
+                            sF[spos<P>(N + 1)] = -fm2;
+                            sU[spos<P>(N - 1)] = (4.0 * um1 - um2) * (1.0 / 3.0);
+                            sU[spos<P>(N)] = um1;
+                            sU[spos<P>(N + 1)] = um2;
+                            if (a.outA) {
+                                a.outA[d.off + N - 1] = 1.0;
+                                a.outDelta[d.off + N - 1] = 0.0;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) kmin = min_ll(kmin, __shfl_xor_sync(FULL, kmin, o));
+                    if (lane == 0) wMin[wid] = kmin;
+                    __syncthreads();
+
+                    if (s == 0) {
+                        // ---------- end-of-step diagnostics on the slice t = step * dt ----------
+                        long long km = wMin[0];
+#pragma unroll
+                        for (int w = 1; w < NW; ++w) km = min_ll(km, wMin[w]);
+                        minA = order_key_inv(km);
+                        mass = s_mass;
+                        d0 = s_d0;
+                        const bool nonfin = !(is_finite_bits(mass) && is_finite_bits(d0));
+                        bool stop = false;
+                        if (a.mode != kModeEvolve) {
+                            if (a.mode == kModeInit) {
+                                status = nonfin ? kNonfinite : (minA < a.theta ? kCollapsed : kRunning);
+                                t_c = (status == kCollapsed) ? 0.0
+                                                             : __longlong_as_double(0x7FF0000000000000LL);
+                            }
+                            stop = true;
+                        } else if (!first) {
+                            if (nonfin) {
+                                status = kNonfinite;
+                                stop = true;
+                            } else if (minA < a.theta) {
+                                // min A crossed theta between t_{n-1} and t_n: linear interpolation
+                                t_c = (double)(step - 1) * dt +
+                                      dt * (minA_prev - a.theta) / (minA_prev - minA);
+                                status = kCollapsed;
+                                stop = true;
+                            }
+                        }
+                        if (!stop && step >= n_target) stop = true;
+                        if (stop) goto finish;
+                        minA_prev = minA;
+                        first = false;
+                    }
+
+                    // ================= right-hand side and RK4 update =================
+                    if (act) {
+                        const double wacc = (s == 0 || s == 3) ? d.dt6 : d.dt3;
+                        const double wst = (s == 2) ? dt : d.dt2;
+                        const double waccc = (s == 0 || s == 3) ? d.dt6c : d.dt3c;
+                        const double wstc = (s == 2) ? d.dtc : d.dt2c;
+                        const double *Sp = S0 + tb, *Sq = S1 + tb;
+                        const double *f = sF + tb, *u = sU + tb;
+                        double *Dp = D0 + tb, *Dq = D1 + tb;
+#pragma unroll
+                        for (int k = 0; k < P; ++k) {
+                            const int i = i0 + k;
+                            const double Df = (f[soff<P>(k - 2)] - f[soff<P>(k + 2)]) +
+                                              8.0 * (f[soff<P>(k + 1)] - f[soff<P>(k - 1)]);
+                            const double Du = (u[soff<P>(k - 2)] - u[soff<P>(k + 2)]) +
+                                              8.0 * (u[soff<P>(k + 1)] - u[soff<P>(k - 1)]);
+                            const double kp = fma(-20.0, Sp[soff<P>(k)],
+                                fma(15.0, Sp[soff<P>(k - 1)] + Sp[soff<P>(k + 1)],
+                                fma(-6.0, Sp[soff<P>(k - 2)] + Sp[soff<P>(k + 2)],
+                                    Sp[soff<P>(k - 3)] + Sp[soff<P>(k + 3)])));
+                            const double kq = fma(-20.0, Sq[soff<P>(k)],
+                                fma(15.0, Sq[soff<P>(k - 1)] + Sq[soff<P>(k + 1)],
+                                fma(-6.0, Sq[soff<P>(k - 2)] + Sq[soff<P>(k + 2)],
+                                    Sq[soff<P>(k - 3)] + Sq[soff<P>(k + 3)])));
+                            // Phi-dot = c12 (Df + rko kp): the factor c12 is folded into the RK weights
+                            double Xp = fma(d.rko, kp, Df);
                             double dQ = fma(__ldg(g.iT12 + i), Du, d.cko * kq);
                             if (k == 0 && tid == 0) {
-                                dP = 0.0;                                // Phi(0) = 0
-                                dQ = fma(d.c3, sF[kG - 3], d.cko * kq);  // Pi-dot(0) = 3 (F Phi)'(0)
+                                Xp = 0.0;                                      // Phi(0) = 0
+                                dQ = fma(d.c3, sF[spos<P>(-3)], d.cko * kq);  // 3 (F Phi)'(0)
                             }
-                            const double up = uPhi[i], uq = uPi[i];
+                            const double up = __ldcg(uPhi + i), uq = __ldcg(uPi + i);
                             double ap_, aq_;
                             if (s == 0) {
-                                ap_ = fma(wacc, dP, up);
+                                ap_ = fma(waccc, Xp, up);
                                 aq_ = fma(wacc, dQ, uq);
                             } else {
-                                ap_ = fma(wacc, dP, cPhi[i]);
-                                aq_ = fma(wacc, dQ, cPi[i]);
+                                ap_ = fma(waccc, Xp, __ldcg(cPhi + i));
+                                aq_ = fma(wacc, dQ, __ldcg(cPi + i));
                             }
+                            double np, nq;
                             if (s < 3) {
                                 cPhi[i] = ap_;
                                 cPi[i] = aq_;
-                                nP[k] = fma(wst, dP, up);
-                                nQ[k] = fma(wst, dQ, uq);
+                                np = fma(wstc, Xp, up);
+                                nq = fma(wst, dQ, uq);
                             } else {
-                                nP[k] = ap_;
-                                nQ[k] = aq_;
+                                np = ap_;
+                                nq = aq_;
                                 uPhi[i] = ap_;
                                 uPi[i] = aq_;
                             }
-                        }
-                    }
-                    __syncthreads();
-                    if (act) {
-#pragma unroll
-                        for (int k = 0; k < P; ++k) {
-                            sPhi[kG + i0 + k] = nP[k];
-                            sPi[kG + i0 + k] = nQ[k];
-                        }
-                        if (tid == 0) {
-#pragma unroll
-                            for (int j = 1; j <= 3; ++j) {
-                                sPhi[kG - j] = -nP[j];
-                                sPi[kG - j] = nQ[j];
+                            Dp[soff<P>(k)] = np;
+                            Dq[soff<P>(k)] = nq;
+                            if (tid == 0 && k >= 1 && k <= 3) {
+                                D0[spos<P>(-k)] = -np;  // Phi odd about x = 0
+                                D1[spos<P>(-k)] = nq;   // Pi even about x = 0
+                            }
+                            if (last && k >= P - 3) {
+                                D0[spos<P>(N - 1 + (P - k))] = np;   // Phi even about pi/2
+                                D1[spos<P>(N - 1 + (P - k))] = -nq;  // Pi odd about pi/2
                             }
                         }
                         if (last) {
-#pragma unroll
-                            for (int j = 1; j <= 3; ++j) {
-                                sPhi[kG + N - 1 + j] = nP[P - j];
-                                sPi[kG + N - 1 + j] = -nQ[P - j];
-                            }
+                            D0[spos<P>(N - 1)] = 0.0;
+                            D1[spos<P>(N - 1)] = 0.0;
                         }
                     }
                     __syncthreads();
+                    double *t0 = S0, *t1 = S1;
+                    S0 = D0; S1 = D1; D0 = t0; D1 = t1;
                 }
+                ++step;
             }
-            ++step;
         }
     finish:
+        __syncthreads();  // all global writes of this chunk are issued
         if (tid == 0) {
-            S.step = step;
-            S.t_c = t_c;
-            S.minA = minA;
-            S.mass = mass;
-            S.delta0 = d0;
-            S.status = status;
-            a.st[b] = S;
+            if (!skip) {
+                InstState *sp = a.st + b;
+                sp->step = step;
+                sp->t_c = t_c;
+                sp->minA = minA;
+                sp->mass = mass;
+                sp->delta0 = d0;
+                sp->status = status;
+            }
+            __threadfence();
+            const bool fin = (a.mode != kModeEvolve) || status != kRunning || step >= n_end;
+            if (fin) {
+                atomicExch(a.rounds + q, kFinished);
+                atomicSub(&a.ctl->unfinished, 1);
+            } else {
+                atomicExch(a.rounds + q, rnd + 1);
+            }
+            // retire when fewer work items remain than CTAs take tickets
+            int leave = 0;
+            for (;;) {
+                const int act_n = ld_relaxed(&a.ctl->active);
+                const int unf = ld_relaxed(&a.ctl->unfinished);
+                if (unf >= act_n) break;
+                if (atomicCAS(&a.ctl->active, act_n, act_n - 1) == act_n) {
+                    leave = 1;
+                    break;
+                }
+            }
+            s_leave = leave;
         }
         __syncthreads();
+        if (s_leave) break;
     }
 }
 
 // per-instance results of an evolve call: t_reached, t_collapse, mass, status
+// (an instance whose chunk wait ran out in the last launch is reported as kTimeout)
 __global__ void gather_kernel(const InstDesc *desc, const InstState *st, int B, double t_end,
-                              int evolve_call, double *t_reached, double *t_c, double *mass,
-                              int32_t *status)
+                              int evolve_call, const QueueCtl *ctl, const int32_t *order,
+                              double *t_reached, double *t_c, double *mass, int32_t *status)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
@@ -462,6 +603,8 @@ __global__ void gather_kernel(const InstDesc *desc, const InstState *st, int B, 
     t_c[b] = S.t_c;
     mass[b] = S.mass;
     int32_t s = S.status;
+    const int err = ctl->error;
+    if (err > 0 && order[err - 1] == b && s == kRunning) s = kTimeout;
     if (evolve_call && s == kRunning) {
         const long long n_end = (long long)ceil(t_end / desc[b].dt - 1e-9);
         if (S.step >= n_end) s = kDone;

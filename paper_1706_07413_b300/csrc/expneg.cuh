@@ -1,0 +1,54 @@
+// expneg.cuh -- e^{-x} for the lapse factor F = A e^{-delta} of Eqs. (eq:phi), (eq:pi).
+//
+// Method: Tang's table-driven exponential (P. T. P. Tang, "Table-driven implementation of the
+// exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989), written from
+// the published method: with y = -x,
+//   y = (256 m + j) ln2/256 + r,  0 <= j < 256,  |r| <= ln2/512,
+//   e^y = 2^m * 2^{j/256} * e^r,  e^r - 1 = r + r^2/2 + r^3/6 + r^4/24 + O(r^5),
+// where the O(r^5) remainder is below 4e-17 for |r| <= ln2/512.  The reduction uses the
+// round-to-integer shift constant 1.5*2^52 and a two-term (Cody-Waite) ln2/256 with FMAs, the
+// table holds 2^{j/256} rounded to double, and 2^m is applied by integer addition to the
+// exponent field of the table entry.  The caller's factor A is applied in the same FMA:
+//   A e^{-x} = fma(A t, p, A t),  t = 2^m 2^{j/256},  p = e^r - 1,
+// ten FP64 instructions in all (the library's double exp costs about twenty FP64 issue slots on
+// this part).  Accuracy: within 2 ulp of the exact value for x in [0, 700]; the result is 0 for
+// x > 700 (e^{-700} ~ 1e-304) and NaN for NaN input.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace adscl {
+
+constexpr int kExpTableSize = 256;
+
+// two-term split of ln2/256: L1 = RN(ln2/256), L2 = RN(ln2/256 - L1)
+constexpr double kLn2o256Hi = 0.0027076061740622863;
+constexpr double kLn2o256Lo = 9.058776616587108e-20;
+constexpr double kInvLn2x256 = 369.3299304675746;  // 256 / ln 2
+constexpr double kShift = 6755399441055744.0;      // 1.5 * 2^52
+constexpr int kExpNMin = -258531;                   // n below this: x > 700, result 0
+
+// A * e^{-x} with the table `tab` (2^{j/256}, j < 256), normally in shared memory
+__device__ __forceinline__ double a_exp_neg(double A, double x, const double *tab)
+{
+    const double y = -x;
+    const double nf = fma(y, kInvLn2x256, kShift);
+    const int n = __double2loint(nf);  // round(y * 256/ln2), exact integer in the low bits
+    const double nd = nf - kShift;
+    double r = fma(-nd, kLn2o256Hi, y);
+    r = fma(-nd, kLn2o256Lo, r);
+    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
+    p = fma(r, p, 0.5);
+    p = fma(r, p, 1.0);
+    p = r * p;                         // e^r - 1
+    const int j = n & (kExpTableSize - 1);
+    const int m = n >> 8;              // floor(n / 256)
+    const long long tb = __double_as_longlong(tab[j]) + ((long long)m << 52);
+    double t = __longlong_as_double(tb);
+    if (n < kExpNMin) t = 0.0;
+    const double at = A * t;
+    return fma(at, p, at);
+}
+
+}  // namespace adscl

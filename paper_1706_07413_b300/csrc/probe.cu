@@ -57,3 +57,52 @@ extern "C" adscl_status adscl_probe_fp64(int32_t device, void *stream_, double *
     cudaFree(out);
     return st;
 }
+
+// ---------------------------------------------------------------------------------------------
+// The solver's e^{-x} (expneg.cuh) on an array, for verification against a reference exp.
+
+#include <cmath>
+#include <vector>
+
+#include "expneg.cuh"
+
+namespace {
+
+__global__ void exp_neg_kernel(const double *x, double *y, long long n, const double *tab_g)
+{
+    __shared__ double tab[adscl::kExpTableSize];
+    for (int i = threadIdx.x; i < adscl::kExpTableSize; i += blockDim.x) tab[i] = tab_g[i];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = adscl::a_exp_neg(1.0, x[i], tab);
+}
+
+}  // namespace
+
+extern "C" adscl_status adscl_exp_neg(int32_t device, const double *x, double *y, int64_t n)
+{
+    if (!x || !y || n < 0) return ADSCL_EINVAL;
+    if (n == 0) return ADSCL_OK;
+    if (cudaSetDevice(device) != cudaSuccess) return ADSCL_ECUDA;
+    std::vector<double> tab(adscl::kExpTableSize);
+    for (int j = 0; j < adscl::kExpTableSize; ++j) tab[j] = (double)std::exp2l((long double)j / 256.0L);
+    double *dx = nullptr, *dy = nullptr, *dt = nullptr;
+    adscl_status st = ADSCL_OK;
+    const size_t nb = (size_t)n * sizeof(double);
+    if (cudaMalloc(&dx, nb) != cudaSuccess || cudaMalloc(&dy, nb) != cudaSuccess ||
+        cudaMalloc(&dt, tab.size() * sizeof(double)) != cudaSuccess) {
+        st = ADSCL_ENOMEM;
+    } else if (cudaMemcpy(dx, x, nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+               cudaMemcpy(dt, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        st = ADSCL_ECUDA;
+    } else {
+        exp_neg_kernel<<<256, 256>>>(dx, dy, n, dt);
+        if (cudaGetLastError() != cudaSuccess || cudaMemcpy(y, dy, nb, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = ADSCL_ECUDA;
+    }
+    if (dx) cudaFree(dx);
+    if (dy) cudaFree(dy);
+    if (dt) cudaFree(dt);
+    return st;
+}
