@@ -40,7 +40,8 @@ typedef enum {
     ADSCL_ECUDA = 3,        /* a CUDA runtime call failed (message names it) */
     ADSCL_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
     ADSCL_ENONFINITE = 5,   /* input fields contain NaN or Inf */
-    ADSCL_EUNSUPPORTED = 6  /* valid request this build does not provide */
+    ADSCL_EUNSUPPORTED = 6, /* valid request this build does not provide */
+    ADSCL_ECAPACITY = 7     /* request larger than the fixed capacity of adscl_evolve_noalloc */
 } adscl_status;
 
 typedef enum {
@@ -136,6 +137,41 @@ adscl_status adscl_probe_fp64(int32_t device, void *stream, double *tflops);
  * values x >= 0, written to host y; exposed so that it can be checked against a reference exp.
  * Synchronous; allocates its own device buffers. */
 adscl_status adscl_exp_neg(int32_t device, const double *x, double *y, int64_t n);
+
+/* ---- evolution without device allocation ----------------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers of the library.
+ *
+ * adscl_evolve_noalloc runs the same computation as adscl_create + adscl_set_initial +
+ * adscl_evolve(t_end) (+ adscl_get_state for the fields) for one batch of B instances of one
+ * grid size N, but allocates no device memory at all.  It is meant for callers that cannot
+ * allocate: programs that give the whole GPU memory to their own pool when they start and
+ * forbid allocations outside it, code in latency-critical loops that cannot afford the
+ * device-wide synchronisation of cudaMalloc/cudaFree, and plug-ins running inside another
+ * framework that owns every allocation.
+ *
+ * The caller provides, as device pointers: Phi and Pi (packed B x N doubles; on entry the
+ * initial slice Phi(x,0), Pi(x,0); on return the slice at t_reached), and four outputs of
+ * length B (t_reached, t_collapse, mass, inst_status) with the meaning of adscl_evolve.
+ * cfl, ko_sigma and collapse_threshold as in adscl_config (out_dt is 1).  All other working
+ * storage is one fixed array in device memory that the library holds on every GPU where it is
+ * loaded (about 1.3 MB, until the process exits), hence the limits: B <= 64 instances,
+ * N <= 4097, B * N <= 65552 (16 instances of N = 4097); larger requests return
+ * ADSCL_ECAPACITY and launch nothing.
+ *
+ * The work is queued on `stream` (a cudaStream_t, NULL = legacy default) and the call returns
+ * without waiting; read the outputs after synchronising that stream.  The first call on a
+ * device also looks up the fixed array's device address and sets the kernel's shared-memory
+ * attribute; make that first call before any stream capture.  Every call uses the same fixed
+ * array (the previous call's contents stay in it until overwritten; each call re-initialises
+ * what it needs), so calls whose GPU work overlaps -- on two streams, or from two threads --
+ * race with each other: serialise them.  Returns ADSCL_EINVAL for bad arguments and
+ * ADSCL_ECUDA if a CUDA call fails. */
+#define ADSCL_NOALLOC_MAX_INSTANCES 64
+#define ADSCL_NOALLOC_MAX_POINTS 65552
+adscl_status adscl_evolve_noalloc(int32_t device, void *stream, int32_t B, int32_t N,
+                                  double *Phi, double *Pi, double t_end, double cfl,
+                                  double ko_sigma, double collapse_threshold, double *t_reached,
+                                  double *t_collapse, double *mass, int32_t *inst_status);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next call. */
 const char *adscl_last_error(const adscl_ctx *ctx);

@@ -16,12 +16,14 @@ import numpy as np
 from . import build as _build
 
 ADSCL_OK, ADSCL_EINVAL, ADSCL_ENOMEM, ADSCL_ECUDA, ADSCL_ETIMEOUT, ADSCL_ENONFINITE, \
-    ADSCL_EUNSUPPORTED = range(7)
+    ADSCL_EUNSUPPORTED, ADSCL_ECAPACITY = range(8)
 RUNNING, DONE, COLLAPSED, NONFINITE, TIMEOUT = range(5)
 PREC_FP64, PREC_BF16X3, PREC_TF32X3 = range(3)
 
 STATUS_NAMES = {0: "ADSCL_OK", 1: "ADSCL_EINVAL", 2: "ADSCL_ENOMEM", 3: "ADSCL_ECUDA",
-                4: "ADSCL_ETIMEOUT", 5: "ADSCL_ENONFINITE", 6: "ADSCL_EUNSUPPORTED"}
+                4: "ADSCL_ETIMEOUT", 5: "ADSCL_ENONFINITE", 6: "ADSCL_EUNSUPPORTED",
+                7: "ADSCL_ECAPACITY"}
+NOALLOC_MAX_INSTANCES, NOALLOC_MAX_POINTS = 64, 65552
 
 
 class adscl_config(ctypes.Structure):
@@ -58,6 +60,8 @@ SIGNATURES = {
     "adscl_launch_count": ([_VP], _I64),
     "adscl_probe_fp64": ([_I32, _VP, _VP], ctypes.c_int),
     "adscl_exp_neg": ([_I32, _VP, _VP, _I64], ctypes.c_int),
+    "adscl_evolve_noalloc": ([_I32, _VP, _I32, _I32, _VP, _VP, _F, _F, _F, _F, _VP, _VP, _VP, _VP],
+                             ctypes.c_int),
     "adscl_last_error": ([_VP], ctypes.c_char_p),
     "adscl_destroy": ([_VP], None),
 }
@@ -105,6 +109,19 @@ def exp_neg(x, device=0):
     if st != ADSCL_OK:
         raise AdsclError(st, "exp_neg failed")
     return y
+
+
+def evolve_noalloc(Phi, Pi, N, t_end, t_reached, t_collapse, mass, status, cfl=0.5,
+                   ko_sigma=0.5, collapse_threshold=2.0 ** -7, device=0, stream=None):
+    """adscl_evolve_noalloc on CUDA torch tensors that the caller allocated: Phi, Pi (packed
+    B x N, updated in place) and the four length-B outputs.  Asynchronous on `stream`; returns
+    the status code (no exception, so that the capacity limit can be probed)."""
+    lib = load()
+    B = Phi.numel() // N
+    return lib.adscl_evolve_noalloc(device, stream, B, N, Phi.data_ptr(), Pi.data_ptr(),
+                                    float(t_end), cfl, ko_sigma, collapse_threshold,
+                                    t_reached.data_ptr(), t_collapse.data_ptr(), mass.data_ptr(),
+                                    status.data_ptr())
 
 
 class AdsclError(RuntimeError):
