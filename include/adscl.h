@@ -102,8 +102,13 @@ adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *a, int32_t K,
 adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, double *t_collapse,
                           double *mass, int32_t *inst_status, int ptr_is_device);
 
-/* Mode-energy spectrum E_j, j < J, of every instance's current slice: B x J row-major.
- * precision: ADSCL_PREC_FP64, ADSCL_PREC_BF16X3 or ADSCL_PREC_TF32X3 (tensor cores). */
+/* Mode-energy spectrum of every instance's current slice (Sec. II: "the current numerical
+ * solution can be decomposed into a spectrum of normal modes"): E_j = Pi_j^2 + Phi_j^2/omega_j^2,
+ * Pi_j = (sqrt(A) Pi, e_j), Phi_j = (sqrt(A) Phi, e_j'), (u, w) = int_0^{pi/2} u w tan^2 x dx by
+ * the trapezoid rule on the grid, e_j the AdS4 normal modes (omega_j = 3 + 2j), j < J <= 64.
+ * Output E: B x J row-major.  A is recomputed from the current slice (no state change).
+ * precision: ADSCL_PREC_FP64 (FP64 CUDA cores), ADSCL_PREC_BF16X3 or ADSCL_PREC_TF32X3
+ * (tensor-core projection with split operands, FP32 accumulation; see its accuracy note). */
 enum { ADSCL_PREC_FP64 = 0, ADSCL_PREC_BF16X3 = 1, ADSCL_PREC_TF32X3 = 2 };
 adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E, int ptr_is_device);
 

@@ -15,6 +15,7 @@
 
 #include "adscl.h"
 #include "evolve.cuh"
+#include "spectrum.cuh"
 
 using namespace adscl;
 
@@ -51,6 +52,11 @@ struct adscl_ctx {
     InstState *d_st = nullptr;
     double *d_Phi = nullptr, *d_Pi = nullptr, *d_aPhi = nullptr, *d_aPi = nullptr;
     double *d_scratchA = nullptr, *d_scratchD = nullptr;
+    std::vector<int> geoN;             // grid size of each geometry table
+    double *d_eig_block = nullptr;     // normal modes e_j, e_j' per grid size
+    EigTab *d_eig = nullptr;
+    double *d_modes = nullptr;         // B x kMaxModes mode coefficients (set_initial_modes)
+    double *d_E = nullptr;             // B x kMaxModes mode energies
     int32_t *d_order = nullptr;
     double *d_out = nullptr;      // 3 B doubles: t_reached, t_c, mass
     int32_t *d_outs = nullptr;    // B statuses
@@ -169,6 +175,56 @@ adscl_status check_timeout(adscl_ctx *ctx)
     return ADSCL_OK;
 }
 
+// Normal modes on the grid of size N (see spectrum.cuh): e_j(x_i), e_j'(x_i), j < kMaxModes,
+// by the orthonormal three-term recurrence of p_n for the weight (1-y)^{1/2}(1+y)^{3/2}.
+void make_modes(int N, double *e, double *de)
+{
+    const double h = 0.5 * M_PI / (double)(N - 1);
+    auto an = [](int n) { return std::sqrt((double)n * (n + 2)) / (2.0 * (n + 1)); };
+    auto bn = [](int n) { return 1.0 / (2.0 * (n + 1) * (n + 2)); };
+    for (int i = 0; i < N; ++i) {
+        const double x = i * h, c = std::cos(x), s = std::sin(x), y = std::cos(2.0 * x);
+        double pm = 0.0, p = std::sqrt(2.0 / M_PI), dpm = 0.0, dp = 0.0;
+        for (int j = 0; j < kMaxModes; ++j) {
+            e[(size_t)j * N + i] = 4.0 * c * c * c * p;
+            de[(size_t)j * N + i] = 4.0 * (-3.0 * c * c * s * p - 4.0 * s * c * c * c * c * dp);
+            if (j + 1 < kMaxModes) {
+                const double a1 = an(j + 1), a0 = an(j), b0 = bn(j);
+                const double pn = ((y - b0) * p - a0 * pm) / a1;
+                const double dpn = ((y - b0) * dp + p - a0 * dpm) / a1;
+                pm = p;
+                p = pn;
+                dpm = dp;
+                dp = dpn;
+            }
+        }
+    }
+}
+
+adscl_status ensure_modes(adscl_ctx *ctx)
+{
+    if (ctx->d_eig) return ADSCL_OK;
+    size_t total = 0;
+    for (int n : ctx->geoN) total += (size_t)2 * kMaxModes * n;
+    CK(cudaMalloc(&ctx->d_eig_block, total * sizeof(double)));
+    std::vector<EigTab> tabs;
+    size_t pos = 0;
+    for (int n : ctx->geoN) {
+        std::vector<double> e((size_t)kMaxModes * n), de((size_t)kMaxModes * n);
+        make_modes(n, e.data(), de.data());
+        double *pe = ctx->d_eig_block + pos, *pd = pe + (size_t)kMaxModes * n;
+        CK(cudaMemcpy(pe, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(pd, de.data(), de.size() * sizeof(double), cudaMemcpyHostToDevice));
+        tabs.push_back(EigTab{pe, pd});
+        pos += (size_t)2 * kMaxModes * n;
+    }
+    CK(cudaMalloc(&ctx->d_eig, tabs.size() * sizeof(EigTab)));
+    CK(cudaMemcpy(ctx->d_eig, tabs.data(), tabs.size() * sizeof(EigTab), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_modes, (size_t)ctx->B * kMaxModes * sizeof(double)));
+    CK(cudaMalloc(&ctx->d_E, (size_t)ctx->B * kMaxModes * sizeof(double)));
+    return ADSCL_OK;
+}
+
 adscl_status check_ctx(adscl_ctx *ctx)
 {
     if (!ctx) return ADSCL_EINVAL;
@@ -229,7 +285,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
 
     // geometry tables, one per distinct N
     std::map<int, int> geo_of;
-    std::vector<int> geoN;
+    std::vector<int> &geoN = ctx->geoN;
     for (int n : ctx->N)
         if (!geo_of.count(n)) {
             geo_of[n] = (int)geoN.size();
@@ -349,11 +405,31 @@ adscl_status adscl_set_initial(adscl_ctx *ctx, const double *Phi, const double *
     return ADSCL_OK;
 }
 
-adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *, int32_t, int)
+adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *a, int32_t K, int ptr_is_device)
 {
     adscl_status s = check_ctx(ctx);
     if (s != ADSCL_OK) return s;
-    return fail(ctx, ADSCL_EUNSUPPORTED, "adscl_set_initial_modes is not available in this build");
+    if (!a || K < 1 || K > kMaxModes) return fail(ctx, ADSCL_EINVAL, "need 1 <= K <= %d modes", kMaxModes);
+    s = ensure_modes(ctx);
+    if (s != ADSCL_OK) return s;
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ctx->d_modes, a, (size_t)ctx->B * K * sizeof(double), kind, ctx->stream));
+    synth_kernel<<<ctx->B, 256, 0, ctx->stream>>>(ctx->d_desc, ctx->d_eig, ctx->d_modes, K, ctx->d_Phi,
+                                                  ctx->d_Pi);
+    CK(cudaGetLastError());
+    ctx->launches += 1;
+    CK(cudaMemsetAsync(ctx->d_st, 0, ctx->B * sizeof(InstState), ctx->stream));
+    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->B, nullptr, nullptr);
+    if (s != ADSCL_OK) return s;
+    if (!ptr_is_device) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        std::vector<InstState> st(ctx->B);
+        CK(cudaMemcpy(st.data(), ctx->d_st, ctx->B * sizeof(InstState), cudaMemcpyDeviceToHost));
+        for (int b = 0; b < ctx->B; ++b)
+            if (st[b].status == kNonfinite)
+                return fail(ctx, ADSCL_ENONFINITE, "instance %d: non-finite initial fields", b);
+    }
+    return ADSCL_OK;
 }
 
 adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, double *t_collapse,
@@ -390,11 +466,31 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
     return ADSCL_OK;
 }
 
-adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t, int, double *, int)
+adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E, int ptr_is_device)
 {
     adscl_status s = check_ctx(ctx);
     if (s != ADSCL_OK) return s;
-    return fail(ctx, ADSCL_EUNSUPPORTED, "adscl_spectrum is not available in this build");
+    if (!E || J < 1 || J > kMaxModes) return fail(ctx, ADSCL_EINVAL, "need 1 <= J <= %d", kMaxModes);
+    if (precision != ADSCL_PREC_FP64)
+        return fail(ctx, ADSCL_EUNSUPPORTED, "precision %d is not available in this build", precision);
+    s = ensure_modes(ctx);
+    if (s != ADSCL_OK) return s;
+    // A on the current slices (one constraint solve of every instance, no state change)
+    s = launch_evolve(ctx, kModeSolve, 0.0, ctx->d_order, ctx->B, ctx->d_scratchA, ctx->d_scratchD);
+    if (s != ADSCL_OK) return s;
+    // u = w Pi and v = w Phi overwrite the scratch arrays (A is consumed in the same kernel)
+    spectrum_weights_kernel<<<ctx->B, 256, 0, ctx->stream>>>(ctx->d_desc, ctx->d_geo, ctx->d_Phi,
+                                                             ctx->d_Pi, ctx->d_scratchA,
+                                                             ctx->d_scratchA, ctx->d_scratchD);
+    CK(cudaGetLastError());
+    spectrum_fp64_kernel<<<ctx->B, 256, 0, ctx->stream>>>(ctx->d_desc, ctx->d_eig, ctx->d_scratchA,
+                                                          ctx->d_scratchD, J, ctx->d_E);
+    CK(cudaGetLastError());
+    ctx->launches += 2;
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(E, ctx->d_E, (size_t)ctx->B * J * sizeof(double), kind, ctx->stream));
+    if (!ptr_is_device) CK(cudaStreamSynchronize(ctx->stream));
+    return ADSCL_OK;
 }
 
 adscl_status adscl_grad(adscl_ctx *ctx, const double *, int32_t, double, double *, double *, int)
@@ -479,7 +575,8 @@ void adscl_destroy(adscl_ctx *ctx)
     else cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_geo_block, ctx->d_geo, ctx->d_desc, ctx->d_st, ctx->d_Phi, ctx->d_Pi,
                     ctx->d_aPhi, ctx->d_aPi, ctx->d_scratchA, ctx->d_scratchD, ctx->d_order,
-                    ctx->d_ctl, ctx->d_rounds, ctx->d_exptab, ctx->d_out, ctx->d_outs};
+                    ctx->d_ctl, ctx->d_rounds, ctx->d_exptab, ctx->d_out, ctx->d_outs,
+                    ctx->d_eig_block, ctx->d_eig, ctx->d_modes, ctx->d_E};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;

@@ -1,0 +1,72 @@
+"""GPU parity of the normal-mode machinery (mode-sum initial data, FP64 mode-energy spectrum)
+with the CPU oracle, and the paper's printed temperatures through the GPU path."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1706_07413_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ad():
+    from paper_1706_07413_b300 import adscl
+    adscl.load()
+    return adscl
+
+
+def test_mode_sum_initial_data_matches_oracle(ad, orc):
+    Ns = [129, 1025, 4097]
+    rng = np.random.default_rng(3)
+    a = np.zeros((3, 64))
+    a[:, :24] = rng.uniform(-1, 1, (3, 24)) * np.exp(-np.arange(24) / 5.0)
+    s = ad.Solver(Ns)
+    s.set_initial_modes(np.ascontiguousarray(a[:, :24]))
+    for b, N in enumerate(Ns):
+        Phi, Pi, A, dl = s.get_state(b)
+        oPhi, oPi = orc.synthesize(N, a[b, :24])
+        oA, odl, _, _ = orc.constraints(oPhi, oPi)
+        assert np.all(Phi == 0.0)
+        assert np.abs(Pi - oPi).max() < 1e-11 * max(1.0, np.abs(oPi).max())
+        assert np.abs(A - oA).max() < 1e-11 and np.abs(dl - odl).max() < 1e-11
+
+
+@pytest.mark.parametrize("kind", ["random", "gauss"])
+def test_fp64_spectrum_matches_oracle(ad, orc, kind):
+    Ns = [257, 2049, 4097]
+    if kind == "random":
+        fields = [W.smooth_random(n, seed=60 + i, amp=2.0) for i, n in enumerate(Ns)]
+    else:
+        fields = [(np.zeros(n), W.gaussian_pi(n, 8.0, sigma=0.25)) for n in Ns]
+    s = ad.Solver(Ns)
+    s.set_initial(W.packed([f[0] for f in fields]), W.packed([f[1] for f in fields]))
+    if kind == "gauss":
+        s.evolve(0.3)          # a slice with both Phi and Pi populated
+    E = s.spectrum(64)
+    for b, N in enumerate(Ns):
+        Phi, Pi, A, _ = s.get_state(b)
+        oA, _, _, M = orc.constraints(Phi, Pi)
+        Eo, _, _ = orc.spectrum(Phi, Pi, oA, 64)
+        assert np.abs(E[b] - Eo).max() <= 1e-12 * M, (b, np.abs(E[b] - Eo).max(), M)
+
+
+def test_paper_temperatures_through_the_gpu_path(ad):
+    """Approximate QP data (Eq. (eq:approxQP)) synthesised on the GPU and projected back by the
+    GPU spectrum give the temperatures printed in the paper (Sec. II)."""
+    gold = json.load(open(os.path.join(GOLDEN, "qp_temperatures.json")))
+    N = 2049
+    cases = gold["cases"]
+    a = np.stack([W.approx_qp_coefficients(c["kd"], c["mu"], eps=1e-4, K=32) for c in cases])
+    s = ad.Solver([N] * len(cases))
+    s.set_initial_modes(np.ascontiguousarray(a))
+    E = s.spectrum(40)
+    w = 3.0 + 2.0 * np.arange(40)
+    for b, c in enumerate(cases):
+        T = E[b].sum() / (E[b] / w).sum()
+        tol = 0.5 * 10 ** (math.floor(math.log10(c["T"])) - c["digits"] + 1)
+        assert abs(T - c["T"]) <= tol, (c, T)
