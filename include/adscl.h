@@ -107,8 +107,12 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
  * Pi_j = (sqrt(A) Pi, e_j), Phi_j = (sqrt(A) Phi, e_j'), (u, w) = int_0^{pi/2} u w tan^2 x dx by
  * the trapezoid rule on the grid, e_j the AdS4 normal modes (omega_j = 3 + 2j), j < J <= 64.
  * Output E: B x J row-major.  A is recomputed from the current slice (no state change).
- * precision: ADSCL_PREC_FP64 (FP64 CUDA cores), ADSCL_PREC_BF16X3 or ADSCL_PREC_TF32X3
- * (tensor-core projection with split operands, FP32 accumulation; see its accuracy note). */
+ * precision: ADSCL_PREC_FP64 (FP64 CUDA cores), ADSCL_PREC_BF16X3 or ADSCL_PREC_TF32X3: the
+ * projections on the tensor cores (tcgen05) with each operand split into a rounded high part
+ * and a rounded remainder (BF16 or TF32), three products hi*hi + hi*lo + lo*hi, FP32
+ * accumulation.  Accuracy: max_j |E_j - E_j(FP64)| <= 5e-5 M (measured ~1e-5 M); small E_j are
+ * not relatively accurate.  ADSCL_ETIMEOUT if a bounded wait of the tensor-core kernel ran out
+ * (host pointers only). */
 enum { ADSCL_PREC_FP64 = 0, ADSCL_PREC_BF16X3 = 1, ADSCL_PREC_TF32X3 = 2 };
 adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E, int ptr_is_device);
 

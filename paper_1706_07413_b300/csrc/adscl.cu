@@ -16,6 +16,7 @@
 #include "adscl.h"
 #include "evolve.cuh"
 #include "spectrum.cuh"
+#include "spectrum_tc.cuh"
 
 using namespace adscl;
 
@@ -57,6 +58,18 @@ struct adscl_ctx {
     EigTab *d_eig = nullptr;
     double *d_modes = nullptr;         // B x kMaxModes mode coefficients (set_initial_modes)
     double *d_E = nullptr;             // B x kMaxModes mode energies
+    // tensor-core spectrum (built on first use)
+    int tc_tiles = 0;                  // 128-row tiles over all grid-size groups
+    std::vector<int> tc_tile_geo;      // grid-size group of each tile
+    int64_t *d_tc_rowoff = nullptr;    // per tile row: offset of its instance's fields
+    int32_t *d_tc_rowinst = nullptr;   // per tile row: instance index or -1
+    int64_t *d_tc_modeoff = nullptr;   // 0, N, 2N, ... (rows of the mode tables)
+    char *d_tc_ops = nullptr;          // U, V (hi, lo) per tile and mode tables (hi, lo) per group
+    size_t tc_ops_bytes = 0;
+    int tc_built_prec = -1;            // precision of the mode tables currently in d_tc_ops
+    float *d_tc_D = nullptr;           // 2 x tiles x 128 x 64 projections
+    TcTask *d_tc_tasks = nullptr;
+    int *d_tc_err = nullptr;
     int32_t *d_order = nullptr;
     double *d_out = nullptr;      // 3 B doubles: t_reached, t_c, mass
     int32_t *d_outs = nullptr;    // B statuses
@@ -222,6 +235,141 @@ adscl_status ensure_modes(adscl_ctx *ctx)
     CK(cudaMemcpy(ctx->d_eig, tabs.data(), tabs.size() * sizeof(EigTab), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_modes, (size_t)ctx->B * kMaxModes * sizeof(double)));
     CK(cudaMalloc(&ctx->d_E, (size_t)ctx->B * kMaxModes * sizeof(double)));
+    return ADSCL_OK;
+}
+
+int kpad_of(int N) { return (N + kTcKC - 1) / kTcKC * kTcKC; }
+
+__global__ void tc_energy_kernel(const float *Dp, const float *Df, const int32_t *rowinst, int rows,
+                                 int J, double *E)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int b = rowinst[r];
+    if (b < 0) return;
+    for (int j = 0; j < J; ++j) {
+        const double p = Dp[(size_t)r * kTcN + j], f = Df[(size_t)r * kTcN + j];
+        const double w = 3.0 + 2.0 * j;
+        E[(size_t)b * J + j] = fma(p, p, f * f / (w * w));
+    }
+}
+
+// operand layout in d_tc_ops (element size 4 bytes reserved for both precisions):
+// per tile: U hi, U lo, V hi, V lo (128 x Kpad each); per group: e hi, e lo, e' hi, e' lo (64 x Kpad)
+adscl_status tc_prepare(adscl_ctx *ctx, int precision)
+{
+    const bool tf32 = precision == ADSCL_PREC_TF32X3;
+    const size_t ES = 4;
+    const int G = (int)ctx->geoN.size();
+    if (!ctx->d_tc_ops) {
+        std::vector<std::vector<int>> members(G);
+        for (int b = 0; b < ctx->B; ++b) members[ctx->h_desc[b].geo].push_back(b);
+        std::vector<int64_t> rowoff;
+        std::vector<int32_t> rowinst;
+        for (int g = 0; g < G; ++g) {
+            const int cnt = (int)members[g].size();
+            for (int t0 = 0; t0 < cnt; t0 += kTcM) {
+                ctx->tc_tile_geo.push_back(g);
+                for (int r = 0; r < kTcM; ++r) {
+                    const int k = t0 + r;
+                    rowoff.push_back(k < cnt ? ctx->off[members[g][k]] : 0);
+                    rowinst.push_back(k < cnt ? members[g][k] : -1);
+                }
+            }
+        }
+        ctx->tc_tiles = (int)ctx->tc_tile_geo.size();
+        size_t bytes = 0;
+        for (int t = 0; t < ctx->tc_tiles; ++t) bytes += 4 * (size_t)kTcM * kpad_of(ctx->geoN[ctx->tc_tile_geo[t]]) * ES;
+        for (int g = 0; g < G; ++g) bytes += 4 * (size_t)kTcN * kpad_of(ctx->geoN[g]) * ES;
+        CK(cudaMalloc(&ctx->d_tc_ops, bytes));
+        ctx->tc_ops_bytes = bytes;
+        CK(cudaMalloc(&ctx->d_tc_rowoff, rowoff.size() * sizeof(int64_t)));
+        CK(cudaMemcpy(ctx->d_tc_rowoff, rowoff.data(), rowoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&ctx->d_tc_rowinst, rowinst.size() * sizeof(int32_t)));
+        CK(cudaMemcpy(ctx->d_tc_rowinst, rowinst.data(), rowinst.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        std::vector<int64_t> moff(kTcN);
+        CK(cudaMalloc(&ctx->d_tc_modeoff, (size_t)G * kTcN * sizeof(int64_t)));
+        for (int g = 0; g < G; ++g) {
+            for (int j = 0; j < kTcN; ++j) moff[j] = (int64_t)j * ctx->geoN[g];
+            CK(cudaMemcpy(ctx->d_tc_modeoff + (size_t)g * kTcN, moff.data(), kTcN * sizeof(int64_t),
+                          cudaMemcpyHostToDevice));
+        }
+        CK(cudaMalloc(&ctx->d_tc_D, 2 * (size_t)ctx->tc_tiles * kTcM * kTcN * sizeof(float)));
+        CK(cudaMalloc(&ctx->d_tc_tasks, 2 * (size_t)ctx->tc_tiles * sizeof(TcTask)));
+        CK(cudaMalloc(&ctx->d_tc_err, sizeof(int)));
+        const int smem = 2 * (kTcM + kTcN) * kTcKC * 4;
+        CK(cudaFuncSetAttribute(spectrum_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        CK(cudaFuncSetAttribute(spectrum_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    }
+    // operand pointers
+    std::vector<char *> tileU(ctx->tc_tiles), grpB(G);
+    char *p = ctx->d_tc_ops;
+    for (int t = 0; t < ctx->tc_tiles; ++t) {
+        tileU[t] = p;
+        p += 4 * (size_t)kTcM * kpad_of(ctx->geoN[ctx->tc_tile_geo[t]]) * ES;
+    }
+    for (int g = 0; g < G; ++g) {
+        grpB[g] = p;
+        p += 4 * (size_t)kTcN * kpad_of(ctx->geoN[g]) * ES;
+    }
+    const size_t esz = tf32 ? 4 : 2;
+    // mode tables of every group, split once per precision
+    if (ctx->tc_built_prec != precision) {
+        for (int g = 0; g < G; ++g) {
+            const int n = ctx->geoN[g], kp = kpad_of(n);
+            const size_t part = (size_t)kTcN * kp * esz;
+            const double *e = ctx->d_eig_block, *de;
+            size_t pos = 0;
+            for (int h = 0; h < g; ++h) pos += (size_t)2 * kMaxModes * ctx->geoN[h];
+            e = ctx->d_eig_block + pos;
+            de = e + (size_t)kMaxModes * n;
+            const dim3 grid((kp + 255) / 256, kTcN);
+            const int64_t *mo = ctx->d_tc_modeoff + (size_t)g * kTcN;
+            if (tf32) {
+                split_rows_kernel<true><<<grid, 256, 0, ctx->stream>>>(e, mo, kTcN, n, kp, grpB[g], grpB[g] + part);
+                split_rows_kernel<true><<<grid, 256, 0, ctx->stream>>>(de, mo, kTcN, n, kp, grpB[g] + 2 * part, grpB[g] + 3 * part);
+            } else {
+                split_rows_kernel<false><<<grid, 256, 0, ctx->stream>>>(e, mo, kTcN, n, kp, grpB[g], grpB[g] + part);
+                split_rows_kernel<false><<<grid, 256, 0, ctx->stream>>>(de, mo, kTcN, n, kp, grpB[g] + 2 * part, grpB[g] + 3 * part);
+            }
+            CK(cudaGetLastError());
+            ctx->launches += 2;
+        }
+        ctx->tc_built_prec = precision;
+    }
+    // field operands of every tile, and the task list
+    std::vector<TcTask> tasks(2 * (size_t)ctx->tc_tiles);
+    for (int t = 0; t < ctx->tc_tiles; ++t) {
+        const int g = ctx->tc_tile_geo[t], n = ctx->geoN[g], kp = kpad_of(n);
+        const size_t part = (size_t)kTcM * kp * esz, bpart = (size_t)kTcN * kp * esz;
+        char *U = tileU[t];
+        const dim3 grid((kp + 255) / 256, kTcM);
+        const int64_t *ro = ctx->d_tc_rowoff + (size_t)t * kTcM;
+        // rows of padding carry offset 0 but are zeroed by nrows: count real rows of this tile
+        int nrows = 0;
+        {
+            int seen = 0;
+            for (int q = 0; q < t; ++q) seen += (ctx->tc_tile_geo[q] == g) ? kTcM : 0;
+            int cnt = 0;
+            for (int b = 0; b < ctx->B; ++b) cnt += ctx->h_desc[b].geo == g;
+            nrows = std::min(kTcM, cnt - seen);
+        }
+        if (tf32) {
+            split_rows_kernel<true><<<grid, 256, 0, ctx->stream>>>(ctx->d_scratchA, ro, nrows, n, kp, U, U + part);
+            split_rows_kernel<true><<<grid, 256, 0, ctx->stream>>>(ctx->d_scratchD, ro, nrows, n, kp, U + 2 * part, U + 3 * part);
+        } else {
+            split_rows_kernel<false><<<grid, 256, 0, ctx->stream>>>(ctx->d_scratchA, ro, nrows, n, kp, U, U + part);
+            split_rows_kernel<false><<<grid, 256, 0, ctx->stream>>>(ctx->d_scratchD, ro, nrows, n, kp, U + 2 * part, U + 3 * part);
+        }
+        CK(cudaGetLastError());
+        ctx->launches += 2;
+        char *Bg = grpB[g];
+        tasks[2 * t] = TcTask{U, U + part, Bg, Bg + bpart, kp, ctx->d_tc_D + (size_t)t * kTcM * kTcN};
+        tasks[2 * t + 1] = TcTask{U + 2 * part, U + 3 * part, Bg + 2 * bpart, Bg + 3 * bpart, kp,
+                                  ctx->d_tc_D + ((size_t)ctx->tc_tiles + t) * kTcM * kTcN};
+    }
+    CK(cudaMemcpyAsync(ctx->d_tc_tasks, tasks.data(), tasks.size() * sizeof(TcTask), cudaMemcpyHostToDevice,
+                       ctx->stream));
     return ADSCL_OK;
 }
 
@@ -471,8 +619,8 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
     adscl_status s = check_ctx(ctx);
     if (s != ADSCL_OK) return s;
     if (!E || J < 1 || J > kMaxModes) return fail(ctx, ADSCL_EINVAL, "need 1 <= J <= %d", kMaxModes);
-    if (precision != ADSCL_PREC_FP64)
-        return fail(ctx, ADSCL_EUNSUPPORTED, "precision %d is not available in this build", precision);
+    if (precision != ADSCL_PREC_FP64 && precision != ADSCL_PREC_BF16X3 && precision != ADSCL_PREC_TF32X3)
+        return fail(ctx, ADSCL_EINVAL, "unknown precision %d", precision);
     s = ensure_modes(ctx);
     if (s != ADSCL_OK) return s;
     // A on the current slices (one constraint solve of every instance, no state change)
@@ -483,13 +631,38 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
                                                              ctx->d_Pi, ctx->d_scratchA,
                                                              ctx->d_scratchA, ctx->d_scratchD);
     CK(cudaGetLastError());
-    spectrum_fp64_kernel<<<ctx->B, 256, 0, ctx->stream>>>(ctx->d_desc, ctx->d_eig, ctx->d_scratchA,
-                                                          ctx->d_scratchD, J, ctx->d_E);
-    CK(cudaGetLastError());
-    ctx->launches += 2;
+    ctx->launches += 1;
+    if (precision == ADSCL_PREC_FP64) {
+        spectrum_fp64_kernel<<<ctx->B, 256, 0, ctx->stream>>>(ctx->d_desc, ctx->d_eig, ctx->d_scratchA,
+                                                              ctx->d_scratchD, J, ctx->d_E);
+        CK(cudaGetLastError());
+        ctx->launches += 1;
+    } else {
+        s = tc_prepare(ctx, precision);
+        if (s != ADSCL_OK) return s;
+        CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), ctx->stream));
+        const int smem = 2 * (kTcM + kTcN) * kTcKC * (precision == ADSCL_PREC_TF32X3 ? 4 : 2);
+        if (precision == ADSCL_PREC_TF32X3)
+            spectrum_tc_kernel<true><<<2 * ctx->tc_tiles, 128, smem, ctx->stream>>>(ctx->d_tc_tasks, ctx->d_tc_err);
+        else
+            spectrum_tc_kernel<false><<<2 * ctx->tc_tiles, 128, smem, ctx->stream>>>(ctx->d_tc_tasks, ctx->d_tc_err);
+        CK(cudaGetLastError());
+        const int rows = ctx->tc_tiles * kTcM;
+        tc_energy_kernel<<<(rows + 127) / 128, 128, 0, ctx->stream>>>(
+            ctx->d_tc_D, ctx->d_tc_D + (size_t)rows * kTcN, ctx->d_tc_rowinst, rows, J, ctx->d_E);
+        CK(cudaGetLastError());
+        ctx->launches += 2;
+    }
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CK(cudaMemcpyAsync(E, ctx->d_E, (size_t)ctx->B * J * sizeof(double), kind, ctx->stream));
-    if (!ptr_is_device) CK(cudaStreamSynchronize(ctx->stream));
+    if (!ptr_is_device) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (precision != ADSCL_PREC_FP64) {
+            int err = 0;
+            CK(cudaMemcpy(&err, ctx->d_tc_err, sizeof err, cudaMemcpyDeviceToHost));
+            if (err) return fail(ctx, ADSCL_ETIMEOUT, "tensor-core projection: a wait ran out");
+        }
+    }
     return ADSCL_OK;
 }
 
@@ -576,7 +749,9 @@ void adscl_destroy(adscl_ctx *ctx)
     void *ptrs[] = {ctx->d_geo_block, ctx->d_geo, ctx->d_desc, ctx->d_st, ctx->d_Phi, ctx->d_Pi,
                     ctx->d_aPhi, ctx->d_aPi, ctx->d_scratchA, ctx->d_scratchD, ctx->d_order,
                     ctx->d_ctl, ctx->d_rounds, ctx->d_exptab, ctx->d_out, ctx->d_outs,
-                    ctx->d_eig_block, ctx->d_eig, ctx->d_modes, ctx->d_E};
+                    ctx->d_eig_block, ctx->d_eig, ctx->d_modes, ctx->d_E, ctx->d_tc_rowoff,
+                    ctx->d_tc_rowinst, ctx->d_tc_modeoff, ctx->d_tc_ops, ctx->d_tc_D,
+                    ctx->d_tc_tasks, ctx->d_tc_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
