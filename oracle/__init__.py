@@ -66,6 +66,16 @@ def lib():
         _lib.orc_spectrum.restype = None
         _lib.orc_synthesize.argtypes = [I, I, D, D, D]
         _lib.orc_synthesize.restype = None
+        _lib.orc_constraints_vjp.argtypes = [I, D, D, D, D, D, D]
+        _lib.orc_constraints_vjp.restype = None
+        _lib.orc_rhs_vjp.argtypes = [I, F, D, D, D, D, D, D, D, D, D, D]
+        _lib.orc_rhs_vjp.restype = None
+        _lib.orc_rk4_step_vjp.argtypes = [I, F, F, D, D, D, D]
+        _lib.orc_rk4_step_vjp.restype = None
+        _lib.orc_spectrum_vjp.argtypes = [I, I, D, D, D, D, D]
+        _lib.orc_spectrum_vjp.restype = None
+        _lib.orc_grad.argtypes = [I, I, D, L, F, F, I, D, D]
+        _lib.orc_grad.restype = None
     return _lib
 
 
@@ -177,6 +187,62 @@ def synthesize(N, a):
     Phi, Pi = np.empty(N), np.empty(N)
     lib().orc_synthesize(N, a.size, _p(a), _p(Phi), _p(Pi))
     return Phi, Pi
+
+
+def constraints_vjp(Phi, Pi, Abar, dbar):
+    """Sensitivities to (Phi, Pi) of sum(Abar*A + dbar*delta): transpose of constraints()."""
+    Phi, Pi, Abar, dbar = map(_f64, (Phi, Pi, Abar, dbar))
+    N = Phi.size
+    gP, gQ = np.zeros(N), np.zeros(N)
+    lib().orc_constraints_vjp(N, _p(Phi), _p(Pi), _p(Abar), _p(dbar), _p(gP), _p(gQ))
+    return gP, gQ
+
+
+def rhs_vjp(Phi, Pi, A, delta, vP, vQ, sigma=0.0):
+    """Sensitivities to (Phi, Pi, A, delta) of sum(vP*dPhi + vQ*dPi) at fixed A, delta."""
+    Phi, Pi, A, delta, vP, vQ = map(_f64, (Phi, Pi, A, delta, vP, vQ))
+    N = Phi.size
+    out = [np.zeros(N) for _ in range(4)]
+    lib().orc_rhs_vjp(N, sigma, _p(Phi), _p(Pi), _p(A), _p(delta), _p(vP), _p(vQ), *map(_p, out))
+    return tuple(out)
+
+
+def rk4_step_vjp(Phi, Pi, lP, lQ, dt, sigma=0.0):
+    """Transpose of one RK4 step at the input (Phi, Pi): sensitivity to the input."""
+    Phi, Pi = _f64(Phi), _f64(Pi)
+    lP, lQ = _f64(lP).copy(), _f64(lQ).copy()
+    lib().orc_rk4_step_vjp(Phi.size, dt, sigma, _p(Phi), _p(Pi), _p(lP), _p(lQ))
+    return lP, lQ
+
+
+def spectrum_vjp(Phi, Pi, Ebar):
+    """Sensitivities to (Phi, Pi) of sum(Ebar*E) (E with A from the same slice)."""
+    Phi, Pi, Ebar = map(_f64, (Phi, Pi, Ebar))
+    N = Phi.size
+    gP, gQ = np.zeros(N), np.zeros(N)
+    lib().orc_spectrum_vjp(N, Ebar.size, _p(Phi), _p(Pi), _p(Ebar), _p(gP), _p(gQ))
+    return gP, gQ
+
+
+def grad(a, N, nsteps, dt, sigma=0.5, Jm=32):
+    """J = sum_{j<Jm}(E_j(T) - E_j(0))^2 for Pi(x,0) = sum a_k e_k and dJ/da (discrete adjoint)."""
+    a = _f64(a)
+    out = np.zeros(1)
+    g = np.zeros(a.size)
+    lib().orc_grad(N, a.size, _p(a), nsteps, dt, sigma, Jm, _p(out), _p(g))
+    return float(out[0]), g
+
+
+def functional(a, N, nsteps, dt, sigma=0.5, Jm=32):
+    """J alone, by the forward routines only (for finite-difference checks)."""
+    Phi, Pi = synthesize(N, a)
+    A, _, _, _ = constraints(Phi, Pi)
+    E0, _, _ = spectrum(Phi, Pi, A, Jm)
+    for _ in range(nsteps):
+        Phi, Pi = rk4_step(Phi, Pi, dt, sigma)
+    A, _, _, _ = constraints(Phi, Pi)
+    ET, _, _ = spectrum(Phi, Pi, A, Jm)
+    return float(np.sum((ET - E0) ** 2))
 
 
 def temperature_from_energies(E):

@@ -386,3 +386,347 @@ void orc_synthesize(int N, int K, const double *a, double *Phi, double *Pi)
     free(e);
     free(de);
 }
+
+/* ==================================================================================== */
+/* Discrete adjoint (reverse mode) of the scheme above.  Every routine below transposes */
+/* the corresponding forward routine line by line: given the sensitivity of a scalar    */
+/* functional to the outputs, it accumulates (+=) the sensitivity to the inputs.        */
+/* ==================================================================================== */
+
+/* w_bar[mirror(j)] += p * val for a stencil entry that read with_ghost(w, N, j, p0, p1) */
+static void scatter_ghost(double *wbar, int N, int j, double p0, double p1, double val)
+{
+    if (j < 0) wbar[-j] += p0 * val;
+    else if (j > N - 1) wbar[2 * (N - 1) - j] += p1 * val;
+    else wbar[j] += val;
+}
+
+/*
+ * Transpose of orc_constraints: given Abar (length N) and dbar (length N), the sensitivities
+ * to A and delta, accumulate the sensitivities to Phi and Pi.  A_0, A_{N-1} and delta_{N-1}
+ * are constants and their bars are ignored.
+ */
+void orc_constraints_vjp(int N, const double *Phi, const double *Pi, const double *Abar,
+                         const double *dbar_in, double *Phibar, double *Pibar)
+{
+    const double h = grid_h(N);
+    double *rho = (double *)calloc(N, sizeof(double)), *rhom = (double *)calloc(N, sizeof(double));
+    double *phm = (double *)calloc(N, sizeof(double)), *pim = (double *)calloc(N, sizeof(double));
+    double *m = (double *)calloc(N, sizeof(double)), *mbar = (double *)calloc(N, sizeof(double));
+    double *rhobar = (double *)calloc(N, sizeof(double)), *rhombar = (double *)calloc(N, sizeof(double));
+    double *dbar = (double *)calloc(N, sizeof(double));
+    int i, c;
+
+    /* forward values needed by the transpose */
+    for (i = 0; i < N; ++i) rho[i] = Phi[i] * Phi[i] + Pi[i] * Pi[i];
+    for (c = 0; c < N - 1; ++c) {
+        phm[c] = (-with_ghost(Phi, N, c - 1, -1.0, 1.0) + 9.0 * Phi[c] + 9.0 * Phi[c + 1]
+                  - with_ghost(Phi, N, c + 2, -1.0, 1.0)) / 16.0;
+        pim[c] = (-with_ghost(Pi, N, c - 1, 1.0, -1.0) + 9.0 * Pi[c] + 9.0 * Pi[c + 1]
+                  - with_ghost(Pi, N, c + 2, 1.0, -1.0)) / 16.0;
+        rhom[c] = phm[c] * phm[c] + pim[c] * pim[c];
+    }
+    m[0] = 0.0;
+    for (c = 0; c < N - 1; ++c) {
+        double x0 = c * h, xm = (c + 0.5) * h, x1 = (c + 1) * h;
+        double a0 = tan(x0) * tan(x0) * rho[c], am = tan(xm) * tan(xm) * rhom[c];
+        double a1 = (c + 1 == N - 1) ? 0.0 : tan(x1) * tan(x1) * rho[c + 1];
+        double b0 = sin(x0) * cos(x0) * rho[c], bm = sin(xm) * cos(xm) * rhom[c];
+        double b1 = sin(x1) * cos(x1) * rho[c + 1];
+        double y = m[c];
+        double k1 = a0 - b0 * y;
+        double k2 = am - bm * (y + 0.5 * h * k1);
+        double k3 = am - bm * (y + 0.5 * h * k2);
+        double k4 = a1 - b1 * (y + h * k3);
+        m[c + 1] = y + h / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+    }
+
+    /* A_i = 1 - m_i cos^3 x_i / sin x_i */
+    for (i = 1; i < N - 1; ++i) {
+        double x = i * h;
+        mbar[i] += -Abar[i] * cos(x) * cos(x) * cos(x) / sin(x);
+    }
+    /* the outward RK4 recurrence for m, transposed (cells in reverse order) */
+    for (c = N - 2; c >= 0; --c) {
+        double x0 = c * h, xm = (c + 0.5) * h, x1 = (c + 1) * h;
+        double t0 = tan(x0) * tan(x0), tm = tan(xm) * tan(xm), t1 = tan(x1) * tan(x1);
+        double s0 = sin(x0) * cos(x0), sm = sin(xm) * cos(xm), s1 = sin(x1) * cos(x1);
+        double a0 = t0 * rho[c], am = tm * rhom[c], a1 = (c + 1 == N - 1) ? 0.0 : t1 * rho[c + 1];
+        double b0 = s0 * rho[c], bm = sm * rhom[c], b1 = s1 * rho[c + 1];
+        double y = m[c];
+        double k1 = a0 - b0 * y;
+        double k2 = am - bm * (y + 0.5 * h * k1);
+        double k3 = am - bm * (y + 0.5 * h * k2);
+        double mb = mbar[c + 1];
+        double yb = mb, k1b = h / 6.0 * mb, k2b = h / 3.0 * mb, k3b = h / 3.0 * mb, k4b = h / 6.0 * mb;
+        double a0b = 0, amb = 0, a1b = 0, b0b = 0, bmb = 0, b1b = 0;
+        /* k4 = a1 - b1 (y + h k3) */
+        a1b += k4b;
+        b1b -= k4b * (y + h * k3);
+        yb -= k4b * b1;
+        k3b -= k4b * b1 * h;
+        /* k3 = am - bm (y + h/2 k2) */
+        amb += k3b;
+        bmb -= k3b * (y + 0.5 * h * k2);
+        yb -= k3b * bm;
+        k2b -= k3b * bm * 0.5 * h;
+        /* k2 = am - bm (y + h/2 k1) */
+        amb += k2b;
+        bmb -= k2b * (y + 0.5 * h * k1);
+        yb -= k2b * bm;
+        k1b -= k2b * bm * 0.5 * h;
+        /* k1 = a0 - b0 y */
+        a0b += k1b;
+        b0b -= k1b * y;
+        yb -= k1b * b0;
+        mbar[c] += yb;
+        rhobar[c] += t0 * a0b + s0 * b0b;
+        rhombar[c] += tm * amb + sm * bmb;
+        if (c + 1 != N - 1) rhobar[c + 1] += t1 * a1b;
+        rhobar[c + 1] += s1 * b1b;
+    }
+    /* delta_c = delta_{c+1} + h/6 (s0 rho_c + 4 sm rhom_c + s1 rho_{c+1}), transposed */
+    for (i = 0; i < N; ++i) dbar[i] = dbar_in[i];
+    dbar[N - 1] = 0.0;
+    for (c = 0; c < N - 1; ++c) {
+        double x0 = c * h, xm = (c + 0.5) * h, x1 = (c + 1) * h;
+        double s0 = sin(x0) * cos(x0), sm = sin(xm) * cos(xm), s1 = sin(x1) * cos(x1);
+        double db = dbar[c];
+        if (c + 1 < N - 1) dbar[c + 1] += db;
+        rhobar[c] += h / 6.0 * s0 * db;
+        rhombar[c] += h / 6.0 * 4.0 * sm * db;
+        rhobar[c + 1] += h / 6.0 * s1 * db;
+    }
+    /* rho at midpoints from the interpolated fields */
+    for (c = 0; c < N - 1; ++c) {
+        double pb = 2.0 * phm[c] * rhombar[c] / 16.0, qb = 2.0 * pim[c] * rhombar[c] / 16.0;
+        scatter_ghost(Phibar, N, c - 1, -1.0, 1.0, -pb);
+        Phibar[c] += 9.0 * pb;
+        Phibar[c + 1] += 9.0 * pb;
+        scatter_ghost(Phibar, N, c + 2, -1.0, 1.0, -pb);
+        scatter_ghost(Pibar, N, c - 1, 1.0, -1.0, -qb);
+        Pibar[c] += 9.0 * qb;
+        Pibar[c + 1] += 9.0 * qb;
+        scatter_ghost(Pibar, N, c + 2, 1.0, -1.0, -qb);
+    }
+    for (i = 0; i < N; ++i) {
+        Phibar[i] += 2.0 * Phi[i] * rhobar[i];
+        Pibar[i] += 2.0 * Pi[i] * rhobar[i];
+    }
+    free(rho); free(rhom); free(phm); free(pim); free(m); free(mbar); free(rhobar); free(rhombar);
+    free(dbar);
+}
+
+/* transposed stencils: scatter val * (KO stencil at row i) and val * (D stencil at row i) */
+static void ko_term_vjp(double *wbar, int N, int i, double p0, double p1, double sigma, double h, double val)
+{
+    double s = sigma / (64.0 * h) * val;
+    scatter_ghost(wbar, N, i - 3, p0, p1, s);
+    scatter_ghost(wbar, N, i - 2, p0, p1, -6.0 * s);
+    scatter_ghost(wbar, N, i - 1, p0, p1, 15.0 * s);
+    wbar[i] += -20.0 * s;
+    scatter_ghost(wbar, N, i + 1, p0, p1, 15.0 * s);
+    scatter_ghost(wbar, N, i + 2, p0, p1, -6.0 * s);
+    scatter_ghost(wbar, N, i + 3, p0, p1, s);
+}
+
+static void d1_vjp(double *wbar, int N, int i, double p0, double p1, double h, double val)
+{
+    double s = val / (12.0 * h);
+    scatter_ghost(wbar, N, i - 2, p0, p1, s);
+    scatter_ghost(wbar, N, i - 1, p0, p1, -8.0 * s);
+    scatter_ghost(wbar, N, i + 1, p0, p1, 8.0 * s);
+    scatter_ghost(wbar, N, i + 2, p0, p1, -s);
+}
+
+/*
+ * Transpose of orc_rhs: given vP, vQ (sensitivities to dPhi/dt, dPi/dt), accumulate the
+ * sensitivities to Phi, Pi, A and delta.
+ */
+void orc_rhs_vjp(int N, double sigma, const double *Phi, const double *Pi, const double *A,
+                 const double *delta, const double *vP, const double *vQ, double *Phibar,
+                 double *Pibar, double *Abar, double *dbar)
+{
+    const double h = grid_h(N);
+    double *F = (double *)calloc(N, sizeof(double));
+    double *fb = (double *)calloc(N, sizeof(double)), *gb = (double *)calloc(N, sizeof(double));
+    double *ub = (double *)calloc(N, sizeof(double));
+    int i;
+    for (i = 0; i < N; ++i) F[i] = A[i] * exp(-delta[i]);
+    /* row 0: dPi = 3 d1(g, 0) + KO(Pi, 0) */
+    d1_vjp(gb, N, 0, -1.0, 1.0, h, 3.0 * vQ[0]);
+    ko_term_vjp(Pibar, N, 0, 1.0, -1.0, sigma, h, vQ[0]);
+    for (i = 1; i < N - 1; ++i) {
+        double x = i * h;
+        d1_vjp(fb, N, i, 1.0, -1.0, h, vP[i]);
+        ko_term_vjp(Phibar, N, i, -1.0, 1.0, sigma, h, vP[i]);
+        d1_vjp(ub, N, i, -1.0, 1.0, h, vQ[i] / (tan(x) * tan(x)));
+        ko_term_vjp(Pibar, N, i, 1.0, -1.0, sigma, h, vQ[i]);
+    }
+    /* u_{N-1} = (4 u_{N-2} - u_{N-3}) / 3 */
+    ub[N - 2] += 4.0 / 3.0 * ub[N - 1];
+    ub[N - 3] += -1.0 / 3.0 * ub[N - 1];
+    ub[N - 1] = 0.0;
+    for (i = 0; i < N - 1; ++i) gb[i] += tan(i * h) * tan(i * h) * ub[i];
+    for (i = 0; i < N; ++i) {
+        double Fb = fb[i] * Pi[i] + gb[i] * Phi[i];
+        Pibar[i] += fb[i] * F[i];
+        Phibar[i] += gb[i] * F[i];
+        Abar[i] += Fb * exp(-delta[i]);
+        dbar[i] += -Fb * F[i];
+    }
+    free(F); free(fb); free(gb); free(ub);
+}
+
+/* transpose of the full right-hand side R(y) = rhs(y, constraints(y)) */
+static void rhs_full_vjp(int N, double sigma, const double *Phi, const double *Pi, const double *vP,
+                         const double *vQ, double *Phibar, double *Pibar)
+{
+    size_t bytes = sizeof(double) * N;
+    double *A = (double *)malloc(bytes), *dl = (double *)malloc(bytes);
+    double *Ab = (double *)calloc(N, sizeof(double)), *db = (double *)calloc(N, sizeof(double));
+    orc_constraints(N, Phi, Pi, A, dl, NULL, NULL);
+    orc_rhs_vjp(N, sigma, Phi, Pi, A, dl, vP, vQ, Phibar, Pibar, Ab, db);
+    orc_constraints_vjp(N, Phi, Pi, Ab, db, Phibar, Pibar);
+    free(A); free(dl); free(Ab); free(db);
+}
+
+/*
+ * Transpose of orc_rk4_step at the state (Phi, Pi) (the step's input): given lP, lQ (the
+ * sensitivity to the step's output), overwrite them with the sensitivity to its input.
+ */
+void orc_rk4_step_vjp(int N, double dt, double sigma, const double *Phi, const double *Pi,
+                      double *lP, double *lQ)
+{
+    size_t bytes = sizeof(double) * N;
+    double *yP[4], *yQ[4], *kP = (double *)malloc(bytes), *kQ = (double *)malloc(bytes);
+    double *A = (double *)malloc(bytes), *dl = (double *)malloc(bytes);
+    double *kbP = (double *)malloc(bytes), *kbQ = (double *)malloc(bytes);
+    double *ybP = (double *)malloc(bytes), *ybQ = (double *)malloc(bytes);
+    double *inP = (double *)malloc(bytes), *inQ = (double *)malloc(bytes);
+    const double cstage[4] = {0.0, 0.5, 0.5, 1.0};
+    const double wstage[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    int st, i;
+    /* recompute the stage inputs y_s exactly as the forward step does */
+    for (st = 0; st < 4; ++st) {
+        yP[st] = (double *)malloc(bytes);
+        yQ[st] = (double *)malloc(bytes);
+        if (st == 0) {
+            memcpy(yP[0], Phi, bytes);
+            memcpy(yQ[0], Pi, bytes);
+        } else {
+            for (i = 0; i < N; ++i) {
+                yP[st][i] = Phi[i] + cstage[st] * dt * kP[i];
+                yQ[st][i] = Pi[i] + cstage[st] * dt * kQ[i];
+            }
+        }
+        orc_constraints(N, yP[st], yQ[st], A, dl, NULL, NULL);
+        orc_rhs(N, sigma, yP[st], yQ[st], A, dl, kP, kQ);
+    }
+    /* reverse: kbar_s = w_s dt lambda + c_{s+1} dt ybar_{s+1};  ybar_s = R'(y_s)^T kbar_s */
+    memcpy(inP, lP, bytes);
+    memcpy(inQ, lQ, bytes);
+    for (i = 0; i < N; ++i) { ybP[i] = 0.0; ybQ[i] = 0.0; }
+    for (st = 3; st >= 0; --st) {
+        for (i = 0; i < N; ++i) {
+            kbP[i] = wstage[st] * dt * inP[i] + (st < 3 ? cstage[st + 1] * dt * ybP[i] : 0.0);
+            kbQ[i] = wstage[st] * dt * inQ[i] + (st < 3 ? cstage[st + 1] * dt * ybQ[i] : 0.0);
+            ybP[i] = 0.0;
+            ybQ[i] = 0.0;
+        }
+        rhs_full_vjp(N, sigma, yP[st], yQ[st], kbP, kbQ, ybP, ybQ);
+        for (i = 0; i < N; ++i) {
+            lP[i] += ybP[i];
+            lQ[i] += ybQ[i];
+        }
+    }
+    for (st = 0; st < 4; ++st) { free(yP[st]); free(yQ[st]); }
+    free(kP); free(kQ); free(A); free(dl); free(kbP); free(kbQ); free(ybP); free(ybQ);
+    free(inP); free(inQ);
+}
+
+/*
+ * Transpose of orc_spectrum (with A from orc_constraints of the same slice): given Ebar
+ * (length J), accumulate the sensitivities to Phi and Pi.
+ */
+void orc_spectrum_vjp(int N, int J, const double *Phi, const double *Pi, const double *Ebar,
+                      double *Phibar, double *Pibar)
+{
+    const double h = grid_h(N);
+    double *A = (double *)malloc(sizeof(double) * N), *dl = (double *)malloc(sizeof(double) * N);
+    double *Ab = (double *)calloc(N, sizeof(double)), *db = (double *)calloc(N, sizeof(double));
+    double *e = (double *)malloc(sizeof(double) * (size_t)N * J);
+    double *de = (double *)malloc(sizeof(double) * (size_t)N * J);
+    int j, i;
+    orc_constraints(N, Phi, Pi, A, dl, NULL, NULL);
+    orc_eigen(N, J, e, de);
+    for (j = 0; j < J; ++j) {
+        double pj = 0.0, fj = 0.0, om = 3.0 + 2.0 * j, pb, fb;
+        for (i = 1; i < N - 1; ++i) {
+            double x = i * h, t2 = tan(x) * tan(x), sa = sqrt(A[i]);
+            pj += h * t2 * sa * Pi[i] * e[(size_t)j * N + i];
+            fj += h * t2 * sa * Phi[i] * de[(size_t)j * N + i];
+        }
+        pb = 2.0 * pj * Ebar[j];
+        fb = 2.0 * fj * Ebar[j] / (om * om);
+        for (i = 1; i < N - 1; ++i) {
+            double x = i * h, t2 = tan(x) * tan(x), sa = sqrt(A[i]);
+            Pibar[i] += pb * h * t2 * sa * e[(size_t)j * N + i];
+            Phibar[i] += fb * h * t2 * sa * de[(size_t)j * N + i];
+            Ab[i] += (pb * h * t2 * Pi[i] * e[(size_t)j * N + i]
+                      + fb * h * t2 * Phi[i] * de[(size_t)j * N + i]) / (2.0 * sa);
+        }
+    }
+    orc_constraints_vjp(N, Phi, Pi, Ab, db, Phibar, Pibar);
+    free(A); free(dl); free(Ab); free(db); free(e); free(de);
+}
+
+/*
+ * The mode-energy drift functional J = sum_{j<Jm} (E_j(T) - E_j(0))^2 of an evolution from
+ * Pi(x,0) = sum_{k<K} a_k e_k, Phi(x,0) = 0 over nsteps RK4 steps of size dt (no collapse
+ * stop), and its gradient dJ/da by the discrete adjoint: states stored every step, one
+ * backward sweep.  out[0] = J; dJda has length K.
+ */
+void orc_grad(int N, int K, const double *a, long nsteps, double dt, double sigma, int Jm,
+              double *out, double *dJda)
+{
+    size_t bytes = sizeof(double) * N;
+    double *P = (double *)malloc(bytes * (nsteps + 1)), *Q = (double *)malloc(bytes * (nsteps + 1));
+    double *A = (double *)malloc(bytes), *dl = (double *)malloc(bytes);
+    double *E0 = (double *)malloc(sizeof(double) * Jm), *ET = (double *)malloc(sizeof(double) * Jm);
+    double *Eb = (double *)malloc(sizeof(double) * Jm);
+    double *lP = (double *)calloc(N, sizeof(double)), *lQ = (double *)calloc(N, sizeof(double));
+    double *e = (double *)malloc(sizeof(double) * (size_t)N * K);
+    double *de = (double *)malloc(sizeof(double) * (size_t)N * K);
+    double Jv = 0.0;
+    long n;
+    int j, i;
+    orc_synthesize(N, K, a, P, Q);
+    for (n = 0; n < nsteps; ++n) {
+        memcpy(P + (n + 1) * N, P + n * N, bytes);
+        memcpy(Q + (n + 1) * N, Q + n * N, bytes);
+        orc_rk4_step(N, dt, sigma, P + (n + 1) * N, Q + (n + 1) * N);
+    }
+    orc_constraints(N, P, Q, A, dl, NULL, NULL);
+    orc_spectrum(N, Jm, P, Q, A, E0, NULL, NULL);
+    orc_constraints(N, P + nsteps * N, Q + nsteps * N, A, dl, NULL, NULL);
+    orc_spectrum(N, Jm, P + nsteps * N, Q + nsteps * N, A, ET, NULL, NULL);
+    for (j = 0; j < Jm; ++j) Jv += (ET[j] - E0[j]) * (ET[j] - E0[j]);
+    out[0] = Jv;
+    /* J through E(T) */
+    for (j = 0; j < Jm; ++j) Eb[j] = 2.0 * (ET[j] - E0[j]);
+    orc_spectrum_vjp(N, Jm, P + nsteps * N, Q + nsteps * N, Eb, lP, lQ);
+    for (n = nsteps - 1; n >= 0; --n) orc_rk4_step_vjp(N, dt, sigma, P + n * N, Q + n * N, lP, lQ);
+    /* J through E(0) */
+    for (j = 0; j < Jm; ++j) Eb[j] = -2.0 * (ET[j] - E0[j]);
+    orc_spectrum_vjp(N, Jm, P, Q, Eb, lP, lQ);
+    /* Pi(x,0) = sum_k a_k e_k with Pi_{N-1} = 0 imposed; Phi(x,0) = 0 does not depend on a */
+    orc_eigen(N, K, e, de);
+    for (j = 0; j < K; ++j) {
+        double s = 0.0;
+        for (i = 0; i < N - 1; ++i) s += lQ[i] * e[(size_t)j * N + i];
+        dJda[j] = s;
+    }
+    free(P); free(Q); free(A); free(dl); free(E0); free(ET); free(Eb); free(lP); free(lQ);
+    free(e); free(de);
+}
