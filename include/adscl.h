@@ -116,8 +116,16 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
 enum { ADSCL_PREC_FP64 = 0, ADSCL_PREC_BF16X3 = 1, ADSCL_PREC_TF32X3 = 2 };
 adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E, int ptr_is_device);
 
-/* Gradient of J = sum_{j<64}(E_j(T) - E_j(0))^2 with respect to the initial mode amplitudes
- * a (B x K) by the discrete adjoint of the whole scheme. */
+/* Discrete-adjoint gradient of the mode-energy drift functional (Sec. II spectrum; the
+ * functional and the adjoint are not in the paper):  for every instance, with
+ * Pi(x,0) = sum_{k<K} a_k e_k(x), Phi(x,0) = 0 (a: B x K row-major, K <= 64),
+ *   J = sum_{j<spec_J} (E_j(T) - E_j(0))^2,
+ * evolved without the collapse stop for n = ceil(T/dt) RK4 steps (the same n for every
+ * instance, N <= 4097).  Outputs J_out (B) and dJda (B x K).  The forward pass keeps
+ * (Phi, Pi) every ckpt_every steps; each segment is recomputed once with every stage stored in
+ * device memory (B * ckpt_every * 24 * N doubles) and swept backwards through the exact
+ * transpose of the discrete step (constraint scans included).  Replaces the context's state by
+ * the final slice. */
 adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, double *J_out,
                         double *dJda, int ptr_is_device);
 

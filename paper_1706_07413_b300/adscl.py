@@ -243,5 +243,15 @@ class Solver:
         self._check(self.lib.adscl_spectrum(self.ctx, J, precision, E.ctypes.data, 0))
         return E
 
+    def grad(self, a, T):
+        """(J, dJ/da) of J = sum_{j<spec_J} (E_j(T) - E_j(0))^2 for Pi(x,0) = sum_k a_k e_k."""
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        K = a.shape[-1]
+        J = np.empty(self.B)
+        g = np.empty((self.B, K))
+        self._check(self.lib.adscl_grad(self.ctx, a.ctypes.data, K, float(T), J.ctypes.data,
+                                        g.ctypes.data, 0))
+        return J, g
+
     def launch_count(self):
         return int(self.lib.adscl_launch_count(self.ctx))

@@ -1,0 +1,714 @@
+// adjoint.cuh -- discrete adjoint (reverse mode) of the evolution of evolve.cuh: the transpose of
+// one RK4 step of the method-of-lines scheme of arXiv:1706.07413, Sec. II, including the
+// constraint solve inside every stage, and the transpose of the sqrt(A)-weighted mode
+// projection of spectrum.cuh.  Used for gradients of mode-energy functionals with respect to
+// initial data.
+//
+// Work unit: one CTA (512 threads, 8 nodes per thread, the layout of evolve.cuh) per instance
+// and checkpoint segment.
+//   Phase F: from the segment's first slice, recompute its steps with the same discrete map as
+//     evolve.cuh (affine-map scan for m, suffix sum for delta, table-driven exp) and store, for
+//     every stage of every step, the stage input (Phi, Pi) and the stage's m, e^{-delta}, F and
+//     alpha in HBM; nothing is recomputed later.
+//   Phase B: run the steps backwards.  With lambda' the sensitivity to a step's output,
+//     kbar_s = w_s dt lambda' + c_{s+1} dt ybar_{s+1},  ybar_s = R'(y_s)^T kbar_s,
+//     lambda = lambda' + sum_s ybar_s,
+//   where R'(y)^T applies, in this order: the transposed stencils of the right-hand side (gather
+//   form on the ghost-extended index range, ghost values folded back onto the nodes they
+//   mirror), the flux products, A = 1 - m K and F = A e^{-delta}, the m recurrence transposed
+//   into a suffix affine scan mu_c = alpha_c mu_{c+1} + mbar_c, the delta suffix sum transposed
+//   into a prefix sum, the derivatives of the per-cell RK4 maps (alpha, beta) and of the
+//   Simpson increment, and the midpoint interpolation and rho = Phi^2 + Pi^2.
+// Neighbour values go through CTA-private global scratch arrays and __syncthreads (the kernel is
+// bound by FP64 issue, not by memory).  Instances are taken from an atomic counter; no CTA waits
+// on another.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "evolve.cuh"
+#include "spectrum.cuh"
+
+namespace adscl {
+
+constexpr int kAP = 8;          // nodes per thread
+constexpr int kANT = 512;       // threads per CTA
+constexpr int kANW = kANT / 32;
+constexpr int kStageArrays = 6;  // stored per stage: yP, yQ, M, E, F, AL
+constexpr int kScrArrays = 20;   // CTA scratch arrays of length Nmax
+
+enum : int32_t { kAdjSegment = 0, kAdjSpectrum = 1, kAdjProject = 2 };
+
+struct AdjArgs {
+    const InstDesc *desc;
+    const GeoTab *geo;
+    const EigTab *eig;
+    const double *exptab;
+    const int32_t *order;
+    int32_t nwork;
+    int32_t *queue;
+    int32_t mode;
+    // segment mode
+    const double *ckP, *ckQ;  // packed slices at the segment start
+    int32_t nsteps;           // steps of this segment
+    double *stage;            // per work item: nsteps_cap * 4 stages * kStageArrays * Nmax
+    int32_t nsteps_cap;
+    double *lamP, *lamQ;      // packed adjoint state, updated in place
+    double *scratch;          // per CTA: kScrArrays * Nmax
+    int32_t Nmax;
+    // spectrum mode: lambda += d(sum_j Ebar_j E_j)/d(slice)
+    const double *Ebar;       // B x J
+    int32_t J;
+    const double *sP, *sQ;    // packed slice
+    // projection mode: dJda[b, j] = sum_{i < N-1} lamQ_i e_j(x_i), j < J
+    double *dJda;
+};
+
+// value at index i in [-8, N+7] with the parity rule (u_{-k} = p0 u_k, u_{N-1+k} = p1 u_{N-1-k})
+__device__ __forceinline__ double gv(const double *u, int N, int i, double p0, double p1) {
+    if (i < 0) return p0 * u[-i];
+    if (i > N - 1) return p1 * u[2 * (N - 1) - i];
+    return u[i];
+}
+// value of a row-restricted array on the extended range (zero outside [0, N-1])
+__device__ __forceinline__ double rv(const double *v, int N, int i) {
+    return (i < 0 || i > N - 1) ? 0.0 : v[i];
+}
+
+// ------------------------------------------------------------------ block scans (512 threads)
+struct ScanShared {
+    double a[kANW], b[kANW], c[kANW], d[kANW];
+};
+
+// exclusive prefix composition of affine maps x -> a x + b over threads (ascending), applied to
+// 0 at the block start: returns the b part.  Threads' own maps are (a, b).
+__device__ double scan_affine_prefix(double a, double b, ScanShared &sh)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double ap = __shfl_up_sync(FULL, a, o), bp = __shfl_up_sync(FULL, b, o);
+        if (lane >= o) { b = fma(a, bp, b); a = a * ap; }
+    }
+    double aEx = __shfl_up_sync(FULL, a, 1), bEx = __shfl_up_sync(FULL, b, 1);
+    if (lane == 0) { aEx = 1.0; bEx = 0.0; }
+    if (lane == 31) { sh.a[wid] = a; sh.b[wid] = b; }
+    __syncthreads();
+    if (wid == 0) {
+        double A = lane < kANW ? sh.a[lane] : 1.0, B = lane < kANW ? sh.b[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < kANW; o <<= 1) {
+            const double ap = __shfl_up_sync(FULL, A, o), bp = __shfl_up_sync(FULL, B, o);
+            if (lane >= o) { B = fma(A, bp, B); A = A * ap; }
+        }
+        double bw = __shfl_up_sync(FULL, B, 1);
+        if (lane == 0) bw = 0.0;
+        if (lane < kANW) sh.c[lane] = bw;
+    }
+    __syncthreads();
+    const double r = fma(aEx, sh.c[wid], bEx);
+    __syncthreads();
+    return r;
+}
+
+// exclusive suffix composition (threads descending): the thread's map is x_left = a x_right + b;
+// returns the b part of the composition of all later threads applied to 0 at the block end
+__device__ double scan_affine_suffix(double a, double b, ScanShared &sh)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double an = __shfl_down_sync(FULL, a, o), bn = __shfl_down_sync(FULL, b, o);
+        if (lane + o < 32) { b = fma(a, bn, b); a = a * an; }
+    }
+    double aEx = __shfl_down_sync(FULL, a, 1), bEx = __shfl_down_sync(FULL, b, 1);
+    if (lane == 31) { aEx = 1.0; bEx = 0.0; }
+    if (lane == 0) { sh.a[wid] = a; sh.b[wid] = b; }
+    __syncthreads();
+    if (wid == 0) {
+        double A = lane < kANW ? sh.a[lane] : 1.0, B = lane < kANW ? sh.b[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < kANW; o <<= 1) {
+            const double an = __shfl_down_sync(FULL, A, o), bn = __shfl_down_sync(FULL, B, o);
+            if (lane + o < kANW) { B = fma(A, bn, B); A = A * an; }
+        }
+        double bw = __shfl_down_sync(FULL, B, 1);
+        if (lane + 1 >= kANW) bw = 0.0;
+        if (lane < kANW) sh.c[lane] = bw;
+    }
+    __syncthreads();
+    const double r = fma(aEx, sh.c[wid], bEx);
+    __syncthreads();
+    return r;
+}
+
+// exclusive sums over threads: prefix (threads ascending) and suffix (descending)
+template <bool kSuffix>
+__device__ double scan_sum(double x, ScanShared &sh)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        if (kSuffix) {
+            const double n = __shfl_down_sync(FULL, x, o);
+            if (lane + o < 32) x += n;
+        } else {
+            const double n = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += n;
+        }
+    }
+    double ex = kSuffix ? __shfl_down_sync(FULL, x, 1) : __shfl_up_sync(FULL, x, 1);
+    if (kSuffix ? lane == 31 : lane == 0) ex = 0.0;
+    if (kSuffix ? lane == 0 : lane == 31) sh.d[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        double X = lane < kANW ? sh.d[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < kANW; o <<= 1) {
+            if (kSuffix) {
+                const double n = __shfl_down_sync(FULL, X, o);
+                if (lane + o < kANW) X += n;
+            } else {
+                const double n = __shfl_up_sync(FULL, X, o);
+                if (lane >= o) X += n;
+            }
+        }
+        double w = kSuffix ? __shfl_down_sync(FULL, X, 1) : __shfl_up_sync(FULL, X, 1);
+        if (kSuffix ? lane + 1 >= kANW : lane == 0) w = 0.0;
+        if (lane < kANW) sh.c[lane] = w;
+    }
+    __syncthreads();
+    const double r = ex + sh.c[wid];
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------------------ per-cell RK4 map of m
+struct CellFwd {
+    double qn0, qn1, rn0, rn1, p16, q16, qm3, tm, y2, y3, ca, w2, w3, al, be, De;
+};
+
+// forward cell data of cell c from the stage slice (yP, yQ) (ghost-extended reads)
+__device__ __forceinline__ CellFwd cell_fwd(const double *yP, const double *yQ, const GeoTab &g, int N, int c)
+{
+    CellFwd r;
+    const double pm1 = gv(yP, N, c - 1, -1.0, 1.0), p0 = yP[c], p1 = yP[c + 1], p2 = gv(yP, N, c + 2, -1.0, 1.0);
+    const double qm1 = gv(yQ, N, c - 1, 1.0, -1.0), q0 = yQ[c], q1 = yQ[c + 1], q2 = gv(yQ, N, c + 2, 1.0, -1.0);
+    const double rho0 = fma(p0, p0, q0 * q0), rho1 = fma(p1, p1, q1 * q1);
+    r.qn0 = __ldg(g.ws + c) * rho0;
+    r.rn0 = __ldg(g.wt + c) * rho0;
+    r.qn1 = __ldg(g.ws + c + 1) * rho1;
+    r.rn1 = __ldg(g.wt + c + 1) * rho1;
+    r.p16 = fma(9.0, p0 + p1, -(pm1 + p2));
+    r.q16 = fma(9.0, q0 + q1, -(qm1 + q2));
+    const double rm = fma(r.p16, r.p16, r.q16 * r.q16);
+    r.qm3 = __ldg(g.wsm3 + c) * rm;
+    r.tm = __ldg(g.wtm + c) * rm;
+    const double s01 = r.qn0 + r.qn1;
+    r.De = fma(4.0 / 3.0, r.qm3, s01);
+    r.y2 = fma(-3.0, r.qn0, 1.0);
+    r.y3 = fma(-r.qm3, r.y2, 1.0);
+    r.ca = fma(-2.0, r.qn1, 2.0 / 3.0);
+    r.al = fma(-r.qm3, fma(r.y3, r.ca, fma(-2.0, r.qn0, 2.0 / 3.0)), 1.0 - s01);
+    r.w2 = fma(-r.qm3, r.rn0, r.tm);
+    r.w3 = fma(-r.qm3, r.w2, r.tm);
+    r.be = fma(r.w3, fma(-6.0, r.qn1, 2.0), fma(2.0, r.w2, r.rn0 + r.rn1));
+    return r;
+}
+
+// transpose of cell_fwd from (alpha_bar, beta_bar, Delta_bar) to the node and midpoint
+// sensitivities: rho_bar at node c (n0) and c+1 (n1), and (p16_bar, q16_bar)
+__device__ __forceinline__ void cell_bwd(const CellFwd &f, const GeoTab &g, int c, double alb, double beb,
+                                         double Deb, double &n0, double &n1, double &p16b, double &q16b)
+{
+    double q0b = 0.0, q1b = 0.0, qm3b = 0.0, r0b = 0.0, r1b = 0.0, tmb = 0.0;
+    // beta = w3 (2 - 6 q1) + 2 w2 + r0 + r1
+    const double cb = fma(-6.0, f.qn1, 2.0);
+    double w3b = beb * cb, w2b = 2.0 * beb;
+    q1b += -6.0 * beb * f.w3;
+    r0b += beb;
+    r1b += beb;
+    // w3 = tm - qm3 w2
+    tmb += w3b;
+    qm3b -= w3b * f.w2;
+    w2b -= w3b * f.qm3;
+    // w2 = tm - qm3 r0
+    tmb += w2b;
+    qm3b -= w2b * f.rn0;
+    r0b -= w2b * f.qm3;
+    // alpha = (1 - q0 - q1) - qm3 [ (2/3 - 2 q0) + y3 ca ]
+    const double I = fma(f.y3, f.ca, fma(-2.0, f.qn0, 2.0 / 3.0));
+    qm3b -= alb * I;
+    const double Ib = -alb * f.qm3;
+    q0b -= alb;
+    q1b -= alb;
+    q0b -= 2.0 * Ib;
+    const double y3b = Ib * f.ca;
+    q1b -= 2.0 * Ib * f.y3;        // ca = 2/3 - 2 q1
+    qm3b -= y3b * f.y2;            // y3 = 1 - qm3 y2
+    q0b -= 3.0 * (-y3b * f.qm3);   // y2 = 1 - 3 q0
+    // Delta = 4/3 qm3 + q0 + q1
+    qm3b += (4.0 / 3.0) * Deb;
+    q0b += Deb;
+    q1b += Deb;
+    n0 = fma(__ldg(g.ws + c), q0b, __ldg(g.wt + c) * r0b);
+    n1 = fma(__ldg(g.ws + c + 1), q1b, __ldg(g.wt + c + 1) * r1b);
+    const double rmb = fma(__ldg(g.wsm3 + c), qm3b, __ldg(g.wtm + c) * tmb);
+    p16b = 2.0 * f.p16 * rmb;
+    q16b = 2.0 * f.q16 * rmb;
+}
+
+// ------------------------------------------------------------------ CTA scratch layout
+struct Scr {
+    double *uP, *uQ;     // current slice u_n (phase F)
+    double *aP, *aQ;     // RK4 accumulator (phase F)
+    double *f, *u;       // fluxes F Pi, tan^2 F Phi (phase F)
+    double *vP, *vQ;     // kbar restricted to rows (phase B)
+    double *fb, *ub;     // fbar, ubar on nodes (phase B)
+    double *r1, *pb, *qb;  // per cell: rho_bar of its right node, p16_bar, q16_bar
+    double *lo, *lq;     // lambda' (sensitivity to the step output)
+    double *ybP, *ybQ;   // ybar of the previous (later) stage
+    double *mb;          // mbar, then mu
+    double *dlb;         // delta_bar
+};
+
+__device__ __forceinline__ Scr scratch_of(double *base, int Nmax)
+{
+    Scr s;
+    double *p = base;
+    s.uP = p; p += Nmax; s.uQ = p; p += Nmax; s.aP = p; p += Nmax; s.aQ = p; p += Nmax;
+    s.f = p; p += Nmax; s.u = p; p += Nmax; s.vP = p; p += Nmax; s.vQ = p; p += Nmax;
+    s.fb = p; p += Nmax; s.ub = p; p += Nmax; s.r1 = p; p += Nmax; s.pb = p; p += Nmax;
+    s.qb = p; p += Nmax; s.lo = p; p += Nmax; s.lq = p; p += Nmax; s.ybP = p; p += Nmax;
+    s.ybQ = p; p += Nmax; s.mb = p; p += Nmax; s.dlb = p;
+    return s;
+}
+
+// ------------------------------------------------------------------ stage forward
+// Constraint solve on the stage slice (yP, yQ) (node N-1 and all nodes written, zero at N-1);
+// stores M, E = e^{-delta}, F = A E on nodes and AL = alpha on cells; computes the fluxes into
+// scr.f, scr.u and, if kP != nullptr, the stage derivative (kP, kQ) on the thread's nodes.
+__device__ void stage_forward(const double *yP, const double *yQ, double *M, double *E, double *F, double *AL,
+                              const Scr &scr, double *kP, double *kQ, const InstDesc &d, const GeoTab &g,
+                              const double *tab, ScanShared &sh, bool with_rhs)
+{
+    const int N = d.N, Tn = (N - 1) / kAP, tid = threadIdx.x;
+    const bool act = tid < Tn, last = tid == Tn - 1;
+    const int i0 = tid * kAP;
+    double De[kAP], al[kAP], be[kAP];
+    double aT = 1.0, bT = 0.0, SD = 0.0;
+    if (act) {
+#pragma unroll
+        for (int k = 0; k < kAP; ++k) {
+            const CellFwd cf = cell_fwd(yP, yQ, g, N, i0 + k);
+            De[k] = cf.De;
+            al[k] = cf.al;
+            be[k] = cf.be;
+            AL[i0 + k] = cf.al;
+            if (k == 0) { aT = cf.al; bT = cf.be; SD = cf.De; }
+            else { bT = fma(cf.al, bT, cf.be); aT *= cf.al; SD += cf.De; }
+        }
+    }
+    const double mstart = scan_affine_prefix(aT, bT, sh);
+    const double dend = scan_sum<true>(SD, sh);
+    double g1 = 0.0, g2 = 0.0;
+    if (act) {
+        double dc = dend;
+#pragma unroll
+        for (int k = kAP - 1; k >= 0; --k) { dc += De[k]; De[k] = dc; }
+        double m = mstart;
+#pragma unroll
+        for (int k = 0; k < kAP; ++k) {
+            const int i = i0 + k;
+            const double A = fma(-m, __ldg(g.K + i), 1.0);
+            const double Ei = a_exp_neg(1.0, De[k], tab);
+            const double Fi = A * Ei;
+            M[i] = m;
+            E[i] = Ei;
+            F[i] = Fi;
+            const double gi = Fi * yP[i];
+            scr.f[i] = Fi * yQ[i];
+            scr.u[i] = __ldg(g.T + i) * gi;
+            if (k == 1) g1 = gi;
+            if (k == 2) g2 = gi;
+            m = fma(al[k], m, be[k]);
+        }
+        if (last) {
+            M[N - 1] = m;
+            E[N - 1] = 1.0;
+            F[N - 1] = 1.0;
+            scr.f[N - 1] = 0.0;
+        }
+    }
+    __syncthreads();
+    if (act && last) scr.u[N - 1] = (4.0 * scr.u[N - 2] - scr.u[N - 3]) * (1.0 / 3.0);
+    __syncthreads();
+    if (!with_rhs || !act) return;
+#pragma unroll
+    for (int k = 0; k < kAP; ++k) {
+        const int i = i0 + k;
+        const double Df = (gv(scr.f, N, i - 2, 1.0, -1.0) - gv(scr.f, N, i + 2, 1.0, -1.0)) +
+                          8.0 * (gv(scr.f, N, i + 1, 1.0, -1.0) - gv(scr.f, N, i - 1, 1.0, -1.0));
+        const double Du = (gv(scr.u, N, i - 2, -1.0, 1.0) - gv(scr.u, N, i + 2, -1.0, 1.0)) +
+                          8.0 * (gv(scr.u, N, i + 1, -1.0, 1.0) - gv(scr.u, N, i - 1, -1.0, 1.0));
+        const double kp = fma(-20.0, yP[i], fma(15.0, gv(yP, N, i - 1, -1, 1) + gv(yP, N, i + 1, -1, 1),
+                          fma(-6.0, gv(yP, N, i - 2, -1, 1) + gv(yP, N, i + 2, -1, 1),
+                              gv(yP, N, i - 3, -1, 1) + gv(yP, N, i + 3, -1, 1))));
+        const double kq = fma(-20.0, yQ[i], fma(15.0, gv(yQ, N, i - 1, 1, -1) + gv(yQ, N, i + 1, 1, -1),
+                          fma(-6.0, gv(yQ, N, i - 2, 1, -1) + gv(yQ, N, i + 2, 1, -1),
+                              gv(yQ, N, i - 3, 1, -1) + gv(yQ, N, i + 3, 1, -1))));
+        double dP = fma(d.c12, Df, d.cko * kp);
+        double dQ = fma(__ldg(g.iT12 + i), Du, d.cko * kq);
+        if (i == 0) {
+            dP = 0.0;
+            dQ = fma(d.c3, fma(16.0, g1, -2.0 * g2), d.cko * kq);
+        }
+        kP[i] = dP;
+        kQ[i] = dQ;
+    }
+}
+
+// ------------------------------------------------------------------ constraint transpose
+// Given Abar-derived mbar (scr.mb, nodes) and delta_bar (scr.dlb, nodes), accumulate into
+// (yb P, yb Q) += d/d(yP, yQ) on the thread's nodes.
+__device__ void constraint_backward(const double *yP, const double *yQ, const double *M, const double *AL,
+                                    const Scr &scr, double *ybP, double *ybQ, const InstDesc &d,
+                                    const GeoTab &g, ScanShared &sh)
+{
+    const int N = d.N, Tn = (N - 1) / kAP, tid = threadIdx.x;
+    const bool act = tid < Tn;
+    const int i0 = tid * kAP;
+    // mu_c = alpha_c mu_{c+1} + mbar_c, mu_{N-1} = 0: suffix affine scan
+    double aT = 1.0, bT = 0.0, SP = 0.0;
+    if (act) {
+#pragma unroll
+        for (int k = kAP - 1; k >= 0; --k) {
+            const int c = i0 + k;
+            const double a = AL[c];
+            bT = fma(a, bT, scr.mb[c]);
+            aT *= a;
+        }
+#pragma unroll
+        for (int k = 0; k < kAP; ++k) SP += scr.dlb[i0 + k];
+    }
+    const double mu_end = scan_affine_suffix(aT, bT, sh);   // mu at node i0 + P
+    const double dpre = scan_sum<false>(SP, sh);             // sum of delta_bar over nodes < i0
+    if (act) {
+        double mu = mu_end;
+        double mun[kAP];   // mu at node c+1 for each own cell
+#pragma unroll
+        for (int k = kAP - 1; k >= 0; --k) {
+            mun[k] = mu;
+            mu = fma(AL[i0 + k], mu, scr.mb[i0 + k]);
+        }
+        double Db = dpre;
+        double n0s[kAP];
+#pragma unroll
+        for (int k = 0; k < kAP; ++k) {
+            const int c = i0 + k;
+            Db += scr.dlb[c];                         // Delta_bar_c = sum_{i <= c} delta_bar_i
+            const CellFwd cf = cell_fwd(yP, yQ, g, N, c);
+            double n0, n1, pb, qb;
+            cell_bwd(cf, g, c, mun[k] * M[c], mun[k], Db, n0, n1, pb, qb);
+            n0s[k] = n0;
+            scr.r1[c] = n1;
+            scr.pb[c] = pb;
+            scr.qb[c] = qb;
+        }
+        // keep the node parts in the scratch f/u slots (free in phase B)
+#pragma unroll
+        for (int k = 0; k < kAP; ++k) scr.fb[i0 + k] = n0s[k];
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int k = 0; k < kAP; ++k) {
+            const int j = i0 + k;
+            const double rb = scr.fb[j] + (j >= 1 ? scr.r1[j - 1] : 0.0);
+            // transpose of p16_c = 9 (w_c + w_{c+1}) - (w_{c-1} + w_{c+2}), cells 0 .. N-2
+            auto itp = [&](const double *b, int x) {
+                return 9.0 * (rv(b, N - 1, x) + rv(b, N - 1, x - 1)) - (rv(b, N - 1, x + 1) + rv(b, N - 1, x - 2));
+            };
+            double pP = itp(scr.pb, j), pQ = itp(scr.qb, j);
+            if (j == 1) { pP += -itp(scr.pb, -1); pQ += itp(scr.qb, -1); }                    // ghost -1
+            if (j == N - 2) { pP += itp(scr.pb, N); pQ += -itp(scr.qb, N); }                  // ghost N
+            ybP[j] += fma(2.0 * yP[j], rb, pP);
+            ybQ[j] += fma(2.0 * yQ[j], rb, pQ);
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ stage backward
+// ybar = R'(y)^T kbar with kbar in (scr.vP, scr.vQ) (already restricted to rows), written to
+// (ybP, ybQ) (overwritten) on the thread's nodes.
+__device__ void stage_backward(const double *yP, const double *yQ, const double *M, const double *E,
+                               const double *F, const double *AL, const Scr &scr, double *ybP, double *ybQ,
+                               const InstDesc &d, const GeoTab &g, ScanShared &sh)
+{
+    const int N = d.N, Tn = (N - 1) / kAP, tid = threadIdx.x;
+    const bool act = tid < Tn, last = tid == Tn - 1;
+    const int i0 = tid * kAP;
+    const double *vP = scr.vP, *vQ = scr.vQ;
+    if (act) {
+        // iT12-weighted Pi-dot sensitivities for the u stencil (zero at rows 0 and N-1)
+#pragma unroll
+        for (int k = 0; k < kAP; ++k) scr.pb[i0 + k] = __ldg(g.iT12 + i0 + k) * vQ[i0 + k];
+        if (last) scr.pb[N - 1] = 0.0;
+    }
+    __syncthreads();
+    const double *v2 = scr.pb;
+    auto Dr = [&](const double *v, int x) {   // raw 4th-order difference of a row-restricted array
+        return (rv(v, N, x - 2) - rv(v, N, x + 2)) + 8.0 * (rv(v, N, x + 1) - rv(v, N, x - 1));
+    };
+    auto KOr = [&](const double *v, int x) {  // raw dissipation stencil of a row-restricted array
+        return fma(-20.0, rv(v, N, x), fma(15.0, rv(v, N, x - 1) + rv(v, N, x + 1),
+               fma(-6.0, rv(v, N, x - 2) + rv(v, N, x + 2), rv(v, N, x - 3) + rv(v, N, x + 3))));
+    };
+    if (act) {
+        const double vQ0 = vQ[0];
+#pragma unroll
+        for (int k = 0; k < kAP; ++k) {
+            const int j = i0 + k;
+            // transposed stencils on the extended range, ghosts folded back (parities:
+            // f even/odd, u odd/even, Phi odd/even, Pi even/odd about 0 / pi/2)
+            double fbx = -Dr(vP, j), ubx = -Dr(v2, j), kpx = KOr(vP, j), kqx = KOr(vQ, j);
+            if (j >= 1 && j <= 3) {
+                fbx += -Dr(vP, -j);
+                ubx -= -Dr(v2, -j);
+                kpx -= KOr(vP, -j);
+                kqx += KOr(vQ, -j);
+            }
+            if (j >= N - 4 && j <= N - 2) {
+                const int x = 2 * (N - 1) - j;
+                fbx -= -Dr(vP, x);
+                ubx += -Dr(v2, x);
+                kpx += KOr(vP, x);
+                kqx -= KOr(vQ, x);
+            }
+            if (j == N - 2) ubx += (4.0 / 3.0) * (-Dr(v2, N - 1));   // u(pi/2) extrapolation
+            if (j == N - 3) ubx += (-1.0 / 3.0) * (-Dr(v2, N - 1));
+            const double fb = d.c12 * fbx;
+            double gb = __ldg(g.T + j) * ubx;
+            if (j == 1) gb = fma(16.0 * d.c3, vQ0, gb);             // Pi-dot(0) = 3 (F Phi)'(0)
+            if (j == 2) gb = fma(-2.0 * d.c3, vQ0, gb);
+            const double Fj = F[j];
+            const double Fb = fma(fb, yQ[j], gb * yP[j]);
+            ybQ[j] = fma(fb, Fj, d.cko * kqx);
+            ybP[j] = fma(gb, Fj, d.cko * kpx);
+            const double Ab = Fb * E[j];
+            scr.dlb[j] = -Fb * Fj;
+            scr.mb[j] = -Ab * __ldg(g.K + j);
+        }
+        if (last) { scr.dlb[N - 1] = 0.0; scr.mb[N - 1] = 0.0; }
+    }
+    __syncthreads();
+    constraint_backward(yP, yQ, M, AL, scr, ybP, ybQ, d, g, sh);
+}
+
+// ------------------------------------------------------------------ the kernel
+__global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
+{
+    __shared__ ScanShared sh;
+    __shared__ double s_tab[kExpTableSize];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kExpTableSize; i += kANT) s_tab[i] = a.exptab[i];
+    const Scr scr = scratch_of(a.scratch + (size_t)blockIdx.x * kScrArrays * a.Nmax, a.Nmax);
+    const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+    const double wst[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int q = s_item;
+        __syncthreads();
+        if (q >= a.nwork) break;
+        const int b = a.order[q];
+        const InstDesc d = a.desc[b];
+        const GeoTab g = a.geo[d.geo];
+        const int N = d.N, Tn = (N - 1) / kAP;
+        const bool act = tid < Tn;
+        const int i0 = tid * kAP;
+        double *lamP = a.lamP + d.off, *lamQ = a.lamQ + d.off;
+
+        if (a.mode == kAdjProject) {
+            const EigTab t = a.eig[d.geo];
+            const int lane = tid & 31, warp = tid >> 5;
+            for (int j = warp; j < a.J; j += kANW) {
+                double s = 0.0;
+                for (int i = lane; i < N - 1; i += 32) s = fma(lamQ[i], __ldg(t.e + (size_t)j * N + i), s);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) a.dJda[(size_t)b * a.J + j] = s;
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // per-stage storage of this work item
+        const size_t stN = (size_t)a.Nmax;
+        double *stage_base = a.stage + (size_t)q * a.nsteps_cap * 4 * kStageArrays * stN;
+        auto slot = [&](int n, int s, int arr) { return stage_base + (((size_t)n * 4 + s) * kStageArrays + arr) * stN; };
+
+        if (a.mode == kAdjSpectrum) {
+            // constraint solve of the slice, projections, then the transpose into lambda
+            const double *sP = a.sP + d.off, *sQ = a.sQ + d.off;
+            double *yP = slot(0, 0, 0), *yQ = slot(0, 0, 1), *M = slot(0, 0, 2), *E = slot(0, 0, 3),
+                   *F = slot(0, 0, 4), *AL = slot(0, 0, 5);
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < kAP; ++k) { yP[i0 + k] = sP[i0 + k]; yQ[i0 + k] = sQ[i0 + k]; }
+                if (tid == Tn - 1) { yP[N - 1] = 0.0; yQ[N - 1] = 0.0; }
+            }
+            __syncthreads();
+            stage_forward(yP, yQ, M, E, F, AL, scr, nullptr, nullptr, d, g, s_tab, sh, false);
+            // A = F / E on interior nodes; weights h tan^2 sqrt(A); projections per mode
+            const EigTab t = a.eig[d.geo];
+            const double h = 1.0 / (12.0 * d.c12);
+            const int lane = tid & 31, warp = tid >> 5;
+            for (int j = warp; j < a.J; j += kANW) {
+                double sp = 0.0, sf = 0.0;
+                for (int i = 1 + lane; i < N - 1; i += 32) {
+                    const double A = fma(-M[i], __ldg(g.K + i), 1.0);
+                    const double w = h * __ldg(g.T + i) * sqrt(A);
+                    sp = fma(w * yQ[i], __ldg(t.e + (size_t)j * N + i), sp);
+                    sf = fma(w * yP[i], __ldg(t.de + (size_t)j * N + i), sf);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sp += __shfl_xor_sync(0xffffffffu, sp, o);
+                    sf += __shfl_xor_sync(0xffffffffu, sf, o);
+                }
+                if (lane == 0) {
+                    const double om = 3.0 + 2.0 * j, Eb = a.Ebar[(size_t)b * a.J + j];
+                    scr.vP[j] = 2.0 * sp * Eb;              // Pi_j bar
+                    scr.vQ[j] = 2.0 * sf * Eb / (om * om);  // Phi_j bar
+                }
+            }
+            __syncthreads();
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < kAP; ++k) {
+                    const int i = i0 + k;
+                    double cP = 0.0, cQ = 0.0, Ab = 0.0, dlb = 0.0;
+                    if (i >= 1 && i < N - 1) {
+                        double se = 0.0, sd = 0.0;
+                        for (int j = 0; j < a.J; ++j) {
+                            se = fma(scr.vP[j], __ldg(t.e + (size_t)j * N + i), se);
+                            sd = fma(scr.vQ[j], __ldg(t.de + (size_t)j * N + i), sd);
+                        }
+                        const double A = fma(-M[i], __ldg(g.K + i), 1.0);
+                        const double sa = sqrt(A), ht = h * __ldg(g.T + i);
+                        cQ = ht * sa * se;
+                        cP = ht * sa * sd;
+                        Ab = ht * (yQ[i] * se + yP[i] * sd) / (2.0 * sa);
+                    }
+                    scr.ybP[i] = cP;
+                    scr.ybQ[i] = cQ;
+                    scr.mb[i] = -Ab * __ldg(g.K + i);
+                    scr.dlb[i] = dlb;
+                }
+                if (tid == Tn - 1) { scr.mb[N - 1] = 0.0; scr.dlb[N - 1] = 0.0; }
+            }
+            __syncthreads();
+            constraint_backward(yP, yQ, M, AL, scr, scr.ybP, scr.ybQ, d, g, sh);
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < kAP; ++k) {
+                    lamP[i0 + k] += scr.ybP[i0 + k];
+                    lamQ[i0 + k] += scr.ybQ[i0 + k];
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // ================= segment: phase F (recompute and store every stage) =================
+        const double *ckP = a.ckP + d.off, *ckQ = a.ckQ + d.off;
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < kAP; ++k) { scr.uP[i0 + k] = ckP[i0 + k]; scr.uQ[i0 + k] = ckQ[i0 + k]; }
+        }
+        __syncthreads();
+        for (int n = 0; n < a.nsteps; ++n) {
+            for (int s = 0; s < 4; ++s) {
+                double *yP = slot(n, s, 0), *yQ = slot(n, s, 1);
+                if (s == 0 && act) {
+#pragma unroll
+                    for (int k = 0; k < kAP; ++k) { yP[i0 + k] = scr.uP[i0 + k]; yQ[i0 + k] = scr.uQ[i0 + k]; }
+                }
+                if (act && tid == Tn - 1) { yP[N - 1] = 0.0; yQ[N - 1] = 0.0; }
+                __syncthreads();
+                double *kP = scr.vP, *kQ = scr.vQ;   // stage derivative (phase F use of the slots)
+                stage_forward(yP, yQ, slot(n, s, 2), slot(n, s, 3), slot(n, s, 4), slot(n, s, 5), scr, kP, kQ,
+                              d, g, s_tab, sh, true);
+                if (act) {
+#pragma unroll
+                    for (int k = 0; k < kAP; ++k) {
+                        const int i = i0 + k;
+                        const double up = scr.uP[i], uq = scr.uQ[i];
+                        const double ap = (s == 0) ? fma(wst[0] * d.dt, kP[i], up) : fma(wst[s] * d.dt, kP[i], scr.aP[i]);
+                        const double aq = (s == 0) ? fma(wst[0] * d.dt, kQ[i], uq) : fma(wst[s] * d.dt, kQ[i], scr.aQ[i]);
+                        scr.aP[i] = ap;
+                        scr.aQ[i] = aq;
+                        if (s < 3) {
+                            slot(n, s + 1, 0)[i] = fma(cst[s + 1] * d.dt, kP[i], up);
+                            slot(n, s + 1, 1)[i] = fma(cst[s + 1] * d.dt, kQ[i], uq);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < kAP; ++k) { scr.uP[i0 + k] = scr.aP[i0 + k]; scr.uQ[i0 + k] = scr.aQ[i0 + k]; }
+            }
+            __syncthreads();
+        }
+
+        // ================= segment: phase B (steps backwards) =================
+        for (int n = a.nsteps - 1; n >= 0; --n) {
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < kAP; ++k) {
+                    scr.lo[i0 + k] = lamP[i0 + k];
+                    scr.lq[i0 + k] = lamQ[i0 + k];
+                }
+            }
+            for (int s = 3; s >= 0; --s) {
+                if (act) {
+#pragma unroll
+                    for (int k = 0; k < kAP; ++k) {
+                        const int i = i0 + k;
+                        double kb = wst[s] * d.dt * scr.lo[i], kq = wst[s] * d.dt * scr.lq[i];
+                        if (s < 3) {
+                            kb = fma(cst[s + 1] * d.dt, scr.ybP[i], kb);
+                            kq = fma(cst[s + 1] * d.dt, scr.ybQ[i], kq);
+                        }
+                        scr.vP[i] = (i == 0) ? 0.0 : kb;   // Phi-dot(0) is identically zero
+                        scr.vQ[i] = kq;
+                    }
+                    if (tid == Tn - 1) { scr.vP[N - 1] = 0.0; scr.vQ[N - 1] = 0.0; }
+                }
+                __syncthreads();
+                stage_backward(slot(n, s, 0), slot(n, s, 1), slot(n, s, 2), slot(n, s, 3), slot(n, s, 4),
+                               slot(n, s, 5), scr, scr.ybP, scr.ybQ, d, g, sh);
+                if (act) {
+#pragma unroll
+                    for (int k = 0; k < kAP; ++k) {
+                        lamP[i0 + k] += scr.ybP[i0 + k];
+                        lamQ[i0 + k] += scr.ybQ[i0 + k];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+}  // namespace adscl

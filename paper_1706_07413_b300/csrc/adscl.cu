@@ -17,6 +17,7 @@
 #include "evolve.cuh"
 #include "spectrum.cuh"
 #include "spectrum_tc.cuh"
+#include "adjoint.cuh"
 
 using namespace adscl;
 
@@ -70,6 +71,15 @@ struct adscl_ctx {
     float *d_tc_D = nullptr;           // 2 x tiles x 128 x 64 projections
     TcTask *d_tc_tasks = nullptr;
     int *d_tc_err = nullptr;
+    // adjoint (built on first use)
+    double *d_lam = nullptr;           // packed lambda: Phi part, then Pi part
+    double *d_adj_scr = nullptr;       // per CTA scratch
+    double *d_adj_stage = nullptr;     // stored stages of one segment, per instance
+    size_t adj_stage_doubles = 0;
+    double *d_ck = nullptr;            // checkpoints (Phi, Pi) at segment starts
+    size_t ck_doubles = 0;
+    double *d_adj_small = nullptr;     // E0, ET, Ebar (B x J each), J (B), dJda (B x 64)
+    int32_t *d_adj_queue = nullptr;
     int32_t *d_order = nullptr;
     double *d_out = nullptr;      // 3 B doubles: t_reached, t_c, mass
     int32_t *d_outs = nullptr;    // B statuses
@@ -666,11 +676,147 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
     return ADSCL_OK;
 }
 
-adscl_status adscl_grad(adscl_ctx *ctx, const double *, int32_t, double, double *, double *, int)
+namespace {
+
+__global__ void drift_kernel(const double *E0, const double *ET, int B, int J, double *Jout, double *EbT,
+                             double *Eb0)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double s = 0.0;
+    for (int j = 0; j < J; ++j) {
+        const double dE = ET[(size_t)b * J + j] - E0[(size_t)b * J + j];
+        s = fma(dE, dE, s);
+        EbT[(size_t)b * J + j] = 2.0 * dE;
+        Eb0[(size_t)b * J + j] = -2.0 * dE;
+    }
+    Jout[b] = s;
+}
+
+adscl_status launch_adjoint(adscl_ctx *ctx, AdjArgs &a)
+{
+    const int grid = std::min(ctx->B, ctx->num_sms);
+    CK(cudaMemsetAsync(ctx->d_adj_queue, 0, sizeof(int32_t), ctx->stream));
+    a.queue = ctx->d_adj_queue;
+    adjoint_kernel<<<grid, kANT, 0, ctx->stream>>>(a);
+    CK(cudaGetLastError());
+    ctx->launches += 1;
+    return ADSCL_OK;
+}
+
+}  // namespace
+
+adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, double *J_out, double *dJda,
+                        int ptr_is_device)
 {
     adscl_status s = check_ctx(ctx);
     if (s != ADSCL_OK) return s;
-    return fail(ctx, ADSCL_EUNSUPPORTED, "adscl_grad is not available in this build");
+    if (!a || K < 1 || K > kMaxModes || !(T >= 0.0) || !std::isfinite(T))
+        return fail(ctx, ADSCL_EINVAL, "bad grad arguments");
+    for (int n : ctx->N)
+        if ((n - 1) / kAP > kANT) return fail(ctx, ADSCL_EUNSUPPORTED, "grad supports N <= %d", kAP * kANT + 1);
+    const int B = ctx->B, Jm = ctx->spec_J, seg = ctx->ckpt;
+    const size_t total = (size_t)ctx->total;
+    long long nT = 0;
+    for (const InstDesc &d : ctx->h_desc) nT = std::max(nT, (long long)std::ceil(T / d.dt - 1e-9));
+    for (const InstDesc &d : ctx->h_desc)
+        if ((long long)std::ceil(T / d.dt - 1e-9) != nT)
+            return fail(ctx, ADSCL_EUNSUPPORTED, "grad needs the same number of steps for every instance");
+    const long long nseg = (nT + seg - 1) / seg;
+    // buffers (grown on demand)
+    if (!ctx->d_lam) {
+        CK(cudaMalloc(&ctx->d_lam, 2 * total * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_adj_scr, (size_t)std::min(B, ctx->num_sms) * kScrArrays * ctx->Nmax * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_adj_small, ((size_t)B * (5 * kMaxModes + 1)) * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_adj_queue, sizeof(int32_t)));
+    }
+    const size_t stage_need = (size_t)B * std::max(seg, 1) * 4 * kStageArrays * ctx->Nmax;
+    if (ctx->adj_stage_doubles < stage_need) {
+        if (ctx->d_adj_stage) CK(cudaFree(ctx->d_adj_stage));
+        ctx->d_adj_stage = nullptr;
+        if (cudaMalloc(&ctx->d_adj_stage, stage_need * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->adj_stage_doubles = 0;
+            return fail(ctx, ADSCL_ENOMEM, "adjoint stage storage (%zu MB)", stage_need * 8 >> 20);
+        }
+        ctx->adj_stage_doubles = stage_need;
+    }
+    const size_t ck_need = (size_t)std::max(nseg, 1LL) * 2 * total;
+    if (ctx->ck_doubles < ck_need) {
+        if (ctx->d_ck) CK(cudaFree(ctx->d_ck));
+        ctx->d_ck = nullptr;
+        CK(cudaMalloc(&ctx->d_ck, ck_need * sizeof(double)));
+        ctx->ck_doubles = ck_need;
+    }
+    double *E0 = ctx->d_adj_small, *ET = E0 + (size_t)B * kMaxModes, *EbT = ET + (size_t)B * kMaxModes;
+    double *Eb0 = EbT + (size_t)B * kMaxModes, *Jd = Eb0 + (size_t)B * kMaxModes;
+    double *dJ = Jd + B;
+    (void)dJ;
+
+    // forward: initial data, E(0), checkpoints every `seg` steps, E(T); no collapse stop
+    const double theta = ctx->theta;
+    ctx->theta = -INFINITY;
+    s = adscl_set_initial_modes(ctx, a, K, ptr_is_device);
+    if (s == ADSCL_OK) s = adscl_spectrum(ctx, Jm, ADSCL_PREC_FP64, E0, 1);
+    for (long long g = 0; g < nseg && s == ADSCL_OK; ++g) {
+        double *ck = ctx->d_ck + (size_t)g * 2 * total;
+        CK(cudaMemcpyAsync(ck, ctx->d_Phi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ck + total, ctx->d_Pi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        const long long n1 = std::min(nT, (g + 1) * seg);
+        s = launch_evolve(ctx, kModeEvolve, (double)n1 * ctx->h_desc[0].dt, ctx->d_order, B, nullptr, nullptr);
+    }
+    ctx->theta = theta;
+    if (s != ADSCL_OK) return s;
+    s = adscl_spectrum(ctx, Jm, ADSCL_PREC_FP64, ET, 1);
+    if (s != ADSCL_OK) return s;
+    drift_kernel<<<(B + 127) / 128, 128, 0, ctx->stream>>>(E0, ET, B, Jm, Jd, EbT, Eb0);
+    CK(cudaGetLastError());
+
+    // backward
+    AdjArgs aa{};
+    aa.desc = ctx->d_desc;
+    aa.geo = ctx->d_geo;
+    aa.eig = ctx->d_eig;
+    aa.exptab = ctx->d_exptab;
+    aa.order = ctx->d_order;
+    aa.nwork = B;
+    aa.stage = ctx->d_adj_stage;
+    aa.nsteps_cap = std::max(seg, 1);
+    aa.lamP = ctx->d_lam;
+    aa.lamQ = ctx->d_lam + total;
+    aa.scratch = ctx->d_adj_scr;
+    aa.Nmax = ctx->Nmax;
+    aa.J = Jm;
+    CK(cudaMemsetAsync(ctx->d_lam, 0, 2 * total * sizeof(double), ctx->stream));
+    aa.mode = kAdjSpectrum;
+    aa.Ebar = EbT;
+    aa.sP = ctx->d_Phi;
+    aa.sQ = ctx->d_Pi;
+    s = launch_adjoint(ctx, aa);
+    for (long long g = nseg - 1; g >= 0 && s == ADSCL_OK; --g) {
+        aa.mode = kAdjSegment;
+        aa.ckP = ctx->d_ck + (size_t)g * 2 * total;
+        aa.ckQ = aa.ckP + total;
+        aa.nsteps = (int32_t)(std::min(nT, (g + 1) * seg) - g * seg);
+        s = launch_adjoint(ctx, aa);
+    }
+    if (s != ADSCL_OK) return s;
+    aa.mode = kAdjSpectrum;
+    aa.Ebar = Eb0;
+    aa.sP = ctx->d_ck;
+    aa.sQ = ctx->d_ck + total;
+    s = launch_adjoint(ctx, aa);
+    if (s != ADSCL_OK) return s;
+    aa.mode = kAdjProject;
+    aa.J = K;
+    aa.dJda = dJ;
+    s = launch_adjoint(ctx, aa);
+    if (s != ADSCL_OK) return s;
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (J_out) CK(cudaMemcpyAsync(J_out, Jd, B * sizeof(double), kind, ctx->stream));
+    if (dJda) CK(cudaMemcpyAsync(dJda, dJ, (size_t)B * K * sizeof(double), kind, ctx->stream));
+    if (!ptr_is_device) CK(cudaStreamSynchronize(ctx->stream));
+    return ADSCL_OK;
 }
 
 adscl_status adscl_get_state(adscl_ctx *ctx, int32_t inst, double *Phi, double *Pi, double *A,
@@ -751,7 +897,8 @@ void adscl_destroy(adscl_ctx *ctx)
                     ctx->d_ctl, ctx->d_rounds, ctx->d_exptab, ctx->d_out, ctx->d_outs,
                     ctx->d_eig_block, ctx->d_eig, ctx->d_modes, ctx->d_E, ctx->d_tc_rowoff,
                     ctx->d_tc_rowinst, ctx->d_tc_modeoff, ctx->d_tc_ops, ctx->d_tc_D,
-                    ctx->d_tc_tasks, ctx->d_tc_err};
+                    ctx->d_tc_tasks, ctx->d_tc_err, ctx->d_lam, ctx->d_adj_scr, ctx->d_adj_stage,
+                    ctx->d_ck, ctx->d_adj_small, ctx->d_adj_queue};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;

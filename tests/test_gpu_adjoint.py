@@ -1,0 +1,48 @@
+"""GPU discrete adjoint (adscl_grad) against the CPU oracle's adjoint and against central
+differences of the GPU forward functional."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ad():
+    from paper_1706_07413_b300 import adscl
+    adscl.load()
+    return adscl
+
+
+@pytest.mark.parametrize("N,nsteps,ckpt", [(129, 40, 16), (1025, 24, 8)])
+def test_grad_matches_oracle_adjoint(ad, orc, N, nsteps, ckpt):
+    B, K, Jm = 3, 6, 8
+    rng = np.random.default_rng(N)
+    a = rng.uniform(0.0, 0.8, (B, K)) * np.exp(-np.arange(K) / 2.0)
+    s = ad.Solver([N] * B, ko_sigma=0.5, spec_J=Jm, ckpt_every=ckpt)
+    dt, _ = s.clock()
+    J, g = s.grad(a, nsteps * dt[0])
+    for b in range(B):
+        Jo, go = orc.grad(a[b], N, nsteps, dt[0], sigma=0.5, Jm=Jm)
+        assert abs(J[b] - Jo) <= 1e-10 * abs(Jo), (b, J[b], Jo)
+        big = np.abs(go) > 1e-3 * np.abs(go).max()
+        assert np.all(np.abs(g[b] - go)[big] <= 1e-9 * np.abs(go)[big]), (b, g[b], go)
+
+
+def test_grad_against_central_differences_of_gpu_forward(ad):
+    N, nsteps, K, Jm = 257, 30, 5, 8
+    rng = np.random.default_rng(7)
+    a0 = rng.uniform(0.1, 0.6, K) * np.exp(-np.arange(K) / 2.0)
+    s = ad.Solver([N], ko_sigma=0.5, spec_J=Jm, ckpt_every=7)
+    dt, _ = s.clock()
+    T = nsteps * dt[0]
+    J, g = s.grad(a0[None, :], T)
+    eps = 1e-6
+    for k in range(K):
+        ap, am = a0.copy(), a0.copy()
+        ap[k] += eps
+        am[k] -= eps
+        Jp, _ = s.grad(ap[None, :], T)
+        Jm_, _ = s.grad(am[None, :], T)
+        fd = (Jp[0] - Jm_[0]) / (2 * eps)
+        if abs(g[0, k]) > 1e-3 * np.abs(g).max():
+            assert abs(fd - g[0, k]) <= 1e-5 * abs(g[0, k]), (k, fd, g[0, k])
