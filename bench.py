@@ -172,6 +172,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -275,6 +276,55 @@ def main():
         opl = w1 / (e0.elapsed_time(e1) / 1e3)
         s1.close()
 
+    # adjoint/forward time ratio on the adjoint batch: 64 instances at N = 4097, Pi(x,0) =
+    # sum_{j<32} a_j e_j with a_j = U(0, 0.1) exp(-j/4), dt = 2 pi / 32768 (T = 2 pi is 32768 steps),
+    # 256-step checkpoints; timed over a window of ADJ_STEPS steps (the ratio does not depend on
+    # the window length: both passes scale with the step count)
+    adj = None
+    if rank == 0 and not args.no_adjoint:
+        ADJ_STEPS = 1024
+        ainst = W.adjoint_batch()
+        a = np.stack([it.coeffs for it in ainst])
+        sa = adscl.Solver([ainst[0].N] * len(ainst), ko_sigma=SIGMA_KO, collapse_threshold=-1.0,
+                          out_dt=2 * math.pi, spec_J=32, ckpt_every=256, device=local,
+                          stream=stream.cuda_stream)
+        dta, _ = sa.clock()
+        Ta = ADJ_STEPS * dta[0]
+        sa.grad(a, Ta)                      # warm-up (allocates the stage storage)
+        sa.set_initial_modes(a)
+        sa.evolve(Ta)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sa.set_initial_modes(a)
+        sa.evolve(Ta)
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        Jv, gv = sa.grad(a, Ta)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        adj = {"value": t_adj / t_fwd, "forward_ms": 1e3 * t_fwd, "grad_ms": 1e3 * t_adj,
+               "workload": f"64 mode-sum instances, N=4097, {ADJ_STEPS} RK4 steps of dt=2pi/32768, "
+                           "checkpoint every 256 steps, J = sum_{j<32}(E_j(T)-E_j(0))^2",
+               "grad_includes": "forward pass with checkpoints, E(0), E(T), per-segment recompute "
+                                "with stage storage, backward sweep, projection"}
+        sa.close()
+
+    # spectrum timing (current slices of the amplitude scan, 64 modes)
+    spec = None
+    if rank == 0:
+        spec = {}
+        for name, prec in (("fp64", adscl.PREC_FP64), ("bf16x3", adscl.PREC_BF16X3),
+                           ("tf32x3", adscl.PREC_TF32X3)):
+            sol.spectrum(64, prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(5):
+                sol.spectrum(64, prec)
+            torch.cuda.synchronize()
+            spec[name + "_ms"] = 1e3 * (time.perf_counter() - t0) / 5
+        spec["note"] = "256 instances x 4097 points, 64 modes; includes the constraint solve for A"
+
     # end to end through the public API with host buffers: upload a fresh batch of initial
     # data from pinned memory, solve, evolve one bench step, read the per-instance results
     e2e = None
@@ -340,7 +390,8 @@ def main():
             "gpu_launches": launches,
             "one_per_launch": {"value": opl, "unit": UNIT, "instances": 4,
                                "batched_over_one_per_launch": (value / ws) / opl if opl else None},
-            "adjoint_forward_ratio": None,
+            "adjoint_forward_ratio": adj,
+            "spectrum": spec,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
