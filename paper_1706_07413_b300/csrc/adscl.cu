@@ -25,8 +25,9 @@ namespace {
 
 constexpr int kP = 8;      // grid nodes per thread
 constexpr int kNT = 512;   // threads per CTA
-constexpr int kMaxPoints = kP * kNT + 1;  // 4097
-static_assert(6 * field_stride<kP>(kMaxPoints) * 8 + 4096 <= 232448, "shared memory budget");
+constexpr int kMaxPoints1 = kP * kNT + 1;      // 4097: one CTA per instance
+constexpr int kMaxPoints = 2 * kP * kNT + 1;   // 8193: a 2-CTA cluster per instance
+static_assert(6 * field_stride<kP>(kMaxPoints1) * 8 + 4096 <= 232448, "shared memory budget");
 
 }  // namespace
 
@@ -145,10 +146,15 @@ double step_for(int N, double cfl, double cadence)
     return cadence / std::ceil(cadence / (cfl * h));
 }
 
+// Launch the evolution kernel on the work list order_dev[0 .. nwork) (host copy order_host):
+// instances with N > 4097 (first in the list, which is sorted by N, largest first) run on 2-CTA
+// clusters with queue control ctl[1], the others on single CTAs with ctl[0].
 adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, const int32_t *order_dev,
-                           int nwork, double *outA, double *outD)
+                           const int32_t *order_host, int nwork, double *outA, double *outD)
 {
     if (nwork <= 0) return ADSCL_OK;
+    int nbig = 0;
+    while (nbig < nwork && ctx->N[order_host[nbig]] > kMaxPoints1) ++nbig;
     EvolveArgs a{};
     a.desc = ctx->d_desc;
     a.st = ctx->d_st;
@@ -158,12 +164,8 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, const int32_t
     a.Pi = ctx->d_Pi;
     a.aPhi = ctx->d_aPhi;
     a.aPi = ctx->d_aPi;
-    a.order = order_dev;
-    a.nwork = nwork;
     a.chunk = ctx->chunk;
     a.mode = mode;
-    a.ctl = ctx->d_ctl;
-    a.rounds = ctx->d_rounds;
     a.max_spin = ctx->max_iters;
     a.t_end = t_end;
     a.theta = ctx->theta;
@@ -180,21 +182,61 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, const int32_t
     if ((long long)nwork * rounds > 0x7ffffff0LL)
         return fail(ctx, ADSCL_EINVAL, "t_end too large for one launch (%lld rounds)", rounds);
     a.max_rounds = (int32_t)rounds;
-    const int grid = std::min(nwork, ctx->num_sms);
-    queue_init_kernel<<<(nwork + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_ctl, ctx->d_rounds, nwork, grid);
-    CK(cudaGetLastError());
-    evolve_kernel<kP, kNT><<<grid, kNT, ctx->smem, ctx->stream>>>(a, ctx->stride);
-    CK(cudaGetLastError());
-    ctx->launches += 2;
+    if (nbig > 0) {
+        const int clusters = std::min(nbig, ctx->num_sms / 2);
+        a.order = order_dev;
+        a.nwork = nbig;
+        a.ctl = ctx->d_ctl + 1;
+        a.rounds = ctx->d_rounds + (ctx->B + 1);
+        queue_init_kernel<<<(nbig + 255) / 256, 256, 0, ctx->stream>>>(a.ctl, a.rounds, nbig, clusters);
+        CK(cudaGetLastError());
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(2 * clusters, 1, 1);
+        cfg.blockDim = dim3(kNT, 1, 1);
+        cfg.dynamicSmemBytes = ctx->smem;
+        cfg.stream = ctx->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, evolve_kernel<kP, kNT, 2>, a, ctx->stride));
+        ctx->launches += 2;
+    }
+    if (nwork - nbig > 0) {
+        const int grid = std::min(nwork - nbig, ctx->num_sms);
+        a.order = order_dev + nbig;
+        a.nwork = nwork - nbig;
+        a.ctl = ctx->d_ctl;
+        a.rounds = ctx->d_rounds;
+        queue_init_kernel<<<(a.nwork + 255) / 256, 256, 0, ctx->stream>>>(a.ctl, a.rounds, a.nwork, grid);
+        CK(cudaGetLastError());
+        evolve_kernel<kP, kNT, 1><<<grid, kNT, ctx->smem, ctx->stream>>>(a, ctx->stride);
+        CK(cudaGetLastError());
+        ctx->launches += 2;
+    }
     return ADSCL_OK;
+}
+
+// status kTimeout for the instance whose chunk wait ran out in the last cluster launch
+__global__ void mark_timeout_kernel(const QueueCtl *ctl, const int32_t *order, const InstState *st,
+                                    int32_t *status)
+{
+    const int err = ctl->error;
+    if (err > 0) {
+        const int b = order[err - 1];
+        if (st[b].status == kRunning) status[b] = kTimeout;
+    }
 }
 
 // after a synchronising call: report a device wait that ran out
 adscl_status check_timeout(adscl_ctx *ctx)
 {
-    QueueCtl c{};
-    CK(cudaMemcpy(&c, ctx->d_ctl, sizeof c, cudaMemcpyDeviceToHost));
-    if (c.error) return fail(ctx, ADSCL_ETIMEOUT, "a chunk wait ran out (work item %d)", c.error - 1);
+    QueueCtl c[2]{};
+    CK(cudaMemcpy(c, ctx->d_ctl, sizeof c, cudaMemcpyDeviceToHost));
+    if (c[0].error || c[1].error) return fail(ctx, ADSCL_ETIMEOUT, "a chunk wait ran out");
     return ADSCL_OK;
 }
 
@@ -518,9 +560,9 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
                      [&](int x, int y) { return ctx->N[x] > ctx->N[y]; });
     CK(cudaMalloc(&ctx->d_order, (ctx->B + 1) * sizeof(int32_t)));
     CK(cudaMemcpy(ctx->d_order, ctx->h_order.data(), ctx->B * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&ctx->d_ctl, sizeof(QueueCtl)));
-    CK(cudaMemset(ctx->d_ctl, 0, sizeof(QueueCtl)));
-    CK(cudaMalloc(&ctx->d_rounds, (ctx->B + 1) * sizeof(int32_t)));
+    CK(cudaMalloc(&ctx->d_ctl, 2 * sizeof(QueueCtl)));
+    CK(cudaMemset(ctx->d_ctl, 0, 2 * sizeof(QueueCtl)));
+    CK(cudaMalloc(&ctx->d_rounds, 2 * (ctx->B + 1) * sizeof(int32_t)));
     {
         // 2^{j/256}, computed in extended precision and rounded once to double
         std::vector<double> tab(kExpTableSize);
@@ -531,11 +573,14 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     CK(cudaMalloc(&ctx->d_out, 3 * (size_t)ctx->B * sizeof(double)));
     CK(cudaMalloc(&ctx->d_outs, (size_t)ctx->B * sizeof(int32_t)));
 
-    ctx->stride = field_stride<kP>(ctx->Nmax);
+    // a CTA never holds more than 4096 nodes of one instance (larger grids use 2-CTA clusters)
+    ctx->stride = field_stride<kP>(std::min(ctx->Nmax, kMaxPoints1));
     ctx->smem = (size_t)6 * ctx->stride * sizeof(double);
     // the attribute is per kernel, not per context: always raise it to the largest grid
-    const size_t smem_max = (size_t)6 * field_stride<kP>(kMaxPoints) * sizeof(double);
-    CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem_max = (size_t)6 * field_stride<kP>(kMaxPoints1) * sizeof(double);
+    CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_max));
+    CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem_max));
     return ADSCL_OK;
 }
@@ -550,7 +595,7 @@ adscl_status adscl_set_initial(adscl_ctx *ctx, const double *Phi, const double *
     CK(cudaMemcpyAsync(ctx->d_Phi, Phi, fb, kind, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_Pi, Pi, fb, kind, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_st, 0, ctx->B * sizeof(InstState), ctx->stream));
-    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->B, nullptr, nullptr);
+    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, nullptr, nullptr);
     if (s != ADSCL_OK) return s;
     if (!ptr_is_device) {
         CK(cudaStreamSynchronize(ctx->stream));
@@ -577,7 +622,7 @@ adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *a, int32_t K,
     CK(cudaGetLastError());
     ctx->launches += 1;
     CK(cudaMemsetAsync(ctx->d_st, 0, ctx->B * sizeof(InstState), ctx->stream));
-    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->B, nullptr, nullptr);
+    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, nullptr, nullptr);
     if (s != ADSCL_OK) return s;
     if (!ptr_is_device) {
         CK(cudaStreamSynchronize(ctx->stream));
@@ -598,20 +643,25 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
     if (!std::isfinite(t_end) || t_end < 0.0) return fail(ctx, ADSCL_EINVAL, "bad t_end");
     if (ctx->one_per_launch) {
         for (int q = 0; q < ctx->B; ++q) {
-            s = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order + q, 1, nullptr, nullptr);
+            s = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order + q, ctx->h_order.data() + q, 1, nullptr, nullptr);
             if (s != ADSCL_OK) return s;
         }
     } else {
-        s = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order, ctx->B, nullptr, nullptr);
+        s = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order, ctx->h_order.data(), ctx->B, nullptr, nullptr);
         if (s != ADSCL_OK) return s;
     }
     const int B = ctx->B;
     double *o = ctx->d_out;
+    int nbig = 0;
+    for (int n : ctx->N) nbig += n > kMaxPoints1;
+    // single-CTA work list (after the cluster list in d_order), then the cluster list's timeouts
     gather_kernel<<<(B + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_desc, ctx->d_st, B, t_end, 1,
-                                                           ctx->d_ctl, ctx->d_order, o, o + B,
+                                                           ctx->d_ctl, ctx->d_order + nbig, o, o + B,
                                                            o + 2 * B, ctx->d_outs);
     CK(cudaGetLastError());
-    ctx->launches += 1;
+    mark_timeout_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl + 1, ctx->d_order, ctx->d_st, ctx->d_outs);
+    CK(cudaGetLastError());
+    ctx->launches += 2;
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (t_reached) CK(cudaMemcpyAsync(t_reached, o, B * sizeof(double), kind, ctx->stream));
     if (t_collapse) CK(cudaMemcpyAsync(t_collapse, o + B, B * sizeof(double), kind, ctx->stream));
@@ -634,7 +684,7 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
     s = ensure_modes(ctx);
     if (s != ADSCL_OK) return s;
     // A on the current slices (one constraint solve of every instance, no state change)
-    s = launch_evolve(ctx, kModeSolve, 0.0, ctx->d_order, ctx->B, ctx->d_scratchA, ctx->d_scratchD);
+    s = launch_evolve(ctx, kModeSolve, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, ctx->d_scratchA, ctx->d_scratchD);
     if (s != ADSCL_OK) return s;
     // u = w Pi and v = w Phi overwrite the scratch arrays (A is consumed in the same kernel)
     spectrum_weights_kernel<<<ctx->B, 256, 0, ctx->stream>>>(ctx->d_desc, ctx->d_geo, ctx->d_Phi,
@@ -763,7 +813,7 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         CK(cudaMemcpyAsync(ck, ctx->d_Phi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ck + total, ctx->d_Pi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         const long long n1 = std::min(nT, (g + 1) * seg);
-        s = launch_evolve(ctx, kModeEvolve, (double)n1 * ctx->h_desc[0].dt, ctx->d_order, B, nullptr, nullptr);
+        s = launch_evolve(ctx, kModeEvolve, (double)n1 * ctx->h_desc[0].dt, ctx->d_order, ctx->h_order.data(), B, nullptr, nullptr);
     }
     ctx->theta = theta;
     if (s != ADSCL_OK) return s;
@@ -832,7 +882,7 @@ adscl_status adscl_get_state(adscl_ctx *ctx, int32_t inst, double *Phi, double *
         // one constraint solve of this instance's slice (no state change)
         CK(cudaMemcpyAsync(ctx->d_order + ctx->B, &inst, sizeof(int32_t), cudaMemcpyHostToDevice,
                            ctx->stream));
-        s = launch_evolve(ctx, kModeSolve, 0.0, ctx->d_order + ctx->B, 1, ctx->d_scratchA,
+        s = launch_evolve(ctx, kModeSolve, 0.0, ctx->d_order + ctx->B, &inst, 1, ctx->d_scratchA,
                           ctx->d_scratchD);
         if (s != ADSCL_OK) return s;
         if (A) CK(cudaMemcpyAsync(A, ctx->d_scratchA + off, nb, kind, ctx->stream));
@@ -860,7 +910,7 @@ adscl_status adscl_set_state(adscl_ctx *ctx, int32_t inst, const double *Phi, co
     CK(cudaMemcpyAsync(ctx->d_Pi + off, Pi, nb, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_st + inst, &st, sizeof st, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_order + ctx->B, &inst, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
-    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order + ctx->B, 1, nullptr, nullptr);
+    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order + ctx->B, &inst, 1, nullptr, nullptr);
     if (s != ADSCL_OK) return s;
     CK(cudaStreamSynchronize(ctx->stream));
     return ADSCL_OK;

@@ -151,10 +151,45 @@ __global__ void queue_init_kernel(QueueCtl *ctl, int32_t *rounds, int nwork, int
     if (i < nwork) rounds[i] = 0;
 }
 
-template <int P, int NT>
+// cluster-wide barrier for CL = 2 (both CTAs execute every barrier in the same order: all their
+// control decisions are taken from data exchanged between them), CTA barrier for CL = 1
+template <int CL>
+__device__ __forceinline__ void csync() {
+    if constexpr (CL == 2)
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    else
+        __syncthreads();
+}
+__device__ __forceinline__ int cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+// stores into the same shared-memory location of the other CTA of a 2-CTA cluster
+__device__ __forceinline__ uint32_t peer_addr(const void *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(1u - (uint32_t)cluster_rank()));
+    return r;
+}
+__device__ __forceinline__ void st_peer(double *p, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" :: "r"(peer_addr(p)), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_peer(long long *p, long long v) {
+    asm volatile("st.shared::cluster.b64 [%0], %1;" :: "r"(peer_addr(p)), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_peer(int *p, int v) {
+    asm volatile("st.shared::cluster.b32 [%0], %1;" :: "r"(peer_addr(p)), "r"(v) : "memory");
+}
+
+// CL = 1: one CTA per instance.  CL = 2: a cluster of two CTAs per instance, each owning half of
+// the threads' node blocks; halos, scan carries and the step-end diagnostics cross between the
+// two CTAs through distributed shared memory.
+template <int P, int NT, int CL = 1>
 __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
 {
     static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
+    static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
     constexpr int NW = NT / 32;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ double smem[];
@@ -162,17 +197,22 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
     double *bufB0 = smem + 2 * stride, *bufB1 = smem + 3 * stride;  // next stage Phi, Pi
     double *sF = smem + 4 * stride, *sU = smem + 5 * stride;        // alpha/beta, then f/u
     __shared__ double s_tab[kExpTableSize];
-    __shared__ double wAl[NW], wBe[NW], wDe[NW], cM[NW], cD[NW];
-    __shared__ long long wMin[NW];
-    __shared__ double s_mass, s_d0;
+    __shared__ double wAl[NW], wBe[NW], wDe[NW], cM[NW], cMa[NW], cD[NW];
+    __shared__ long long wMin[NW], wMinP[NW];
+    __shared__ double s_mass, s_d0, s_cA, s_cB, s_cD;
     __shared__ int s_cmd, s_q, s_r, s_leave;
+    __shared__ long long s_step;
+    __shared__ double s_tc, s_minA, s_massS, s_d0S;
+    __shared__ int s_status;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int rank = 0;
+    if constexpr (CL == 2) rank = cluster_rank();
     for (int i = tid; i < kExpTableSize; i += NT) s_tab[i] = a.exptab[i];
 
     for (;;) {
         // ------------------------------------------------------------ take a ticket
-        if (tid == 0) {
+        if (tid == 0 && rank == 0) {
             int cmd = 0, q = 0, r = 0;  // cmd 0: leave, 1: run
             for (;;) {
                 if (ld_relaxed(&a.ctl->unfinished) == 0 || ld_relaxed(&a.ctl->error) != 0) break;
@@ -195,26 +235,49 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                 cmd = 1;
                 break;
             }
+            InstState S{};
+            if (cmd) {
+                const InstState *sp = a.st + a.order[q];
+                S.step = __ldcg(&sp->step);
+                S.t_c = __ldcg(&sp->t_c);
+                S.minA = __ldcg(&sp->minA);
+                S.mass = __ldcg(&sp->mass);
+                S.delta0 = __ldcg(&sp->delta0);
+                S.status = __ldcg(&sp->status);
+            }
             s_cmd = cmd;
             s_q = q;
             s_r = r;
+            s_step = S.step;
+            s_tc = S.t_c;
+            s_minA = S.minA;
+            s_massS = S.mass;
+            s_d0S = S.delta0;
+            s_status = S.status;
+            if constexpr (CL == 2) {
+                st_peer(&s_cmd, cmd);
+                st_peer(&s_q, q);
+                st_peer(&s_r, r);
+                st_peer(&s_step, (long long)S.step);
+                st_peer(&s_tc, S.t_c);
+                st_peer(&s_minA, S.minA);
+                st_peer(&s_massS, S.mass);
+                st_peer(&s_d0S, S.delta0);
+                st_peer(&s_status, (int)S.status);
+            }
         }
-        __syncthreads();
+        csync<CL>();
         if (s_cmd == 0) break;
         const int q = s_q, rnd = s_r;
         const int b = a.order[q];
         const InstDesc d = a.desc[b];
         InstState S;
-        {
-            const InstState *sp = a.st + b;
-            S.step = __ldcg(&sp->step);
-            S.t_c = __ldcg(&sp->t_c);
-            S.minA = __ldcg(&sp->minA);
-            S.mass = __ldcg(&sp->mass);
-            S.delta0 = __ldcg(&sp->delta0);
-            S.status = __ldcg(&sp->status);
-        }
-        __syncthreads();  // every thread has read s_cmd, s_q, s_r before thread 0 rewrites them
+        S.step = s_step;
+        S.t_c = s_tc;
+        S.minA = s_minA;
+        S.mass = s_massS;
+        S.delta0 = s_d0S;
+        S.status = s_status;
 
         const double dt = d.dt;
         long long n_end = S.step, n_target = S.step;
@@ -223,11 +286,19 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
             n_target = min(n_end, S.step + (long long)a.chunk);
         }
         const int N = d.N;
-        const int Tn = (N - 1) / P;
+        const int TnAll = (N - 1) / P;
+        const int Tn0 = (CL == 2) ? (TnAll + 1) / 2 : TnAll;   // node blocks of CTA rank 0
+        const int Tn = (rank == 0) ? Tn0 : TnAll - Tn0;         // node blocks of this CTA
+        const int gb = (rank == 0) ? 0 : Tn0 * P;               // first node of this CTA
+        const int NL0 = Tn0 * P;                                // nodes of CTA rank 0
         const bool act = tid < Tn;
-        const bool last = tid == Tn - 1;
-        const int i0 = tid * P;
-        const int tb = (P + 1) * tid;  // thread base in the padded arrays
+        const bool tfirst = rank == 0 && tid == 0;              // owns node 0
+        const bool last = (rank == CL - 1) && tid == Tn - 1;    // owns node N-2
+        const bool hl = (CL == 2) && rank == 0 && tid == Tn - 1;  // pushes the halo of rank 1
+        const bool hr = (CL == 2) && rank == 1 && tid == 0;       // pushes the halo of rank 0
+        const int i0 = gb + tid * P;       // global node of the thread's first node
+        const int tb = (P + 1) * tid;      // thread base in the padded arrays (local nodes)
+        const int Nl = N - gb;             // local index of node N (boundary ghosts: Nl - 1 + j)
         const GeoTab g = a.geo[d.geo];
         double *uPhi = a.Phi + d.off, *uPi = a.Pi + d.off;
         double *cPhi = a.aPhi + d.off, *cPi = a.aPi + d.off;
@@ -246,13 +317,13 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                     p[k] = __ldcg(uPhi + i0 + k);
                     qv[k] = __ldcg(uPi + i0 + k);
                 }
-                if (tid == 0) p[0] = 0.0;
+                if (tfirst) p[0] = 0.0;
 #pragma unroll
                 for (int k = 0; k < P; ++k) {
                     bufA0[tb + soff<P>(k)] = p[k];
                     bufA1[tb + soff<P>(k)] = qv[k];
                 }
-                if (tid == 0) {
+                if (tfirst) {
 #pragma unroll
                     for (int j = 1; j <= 3; ++j) {
                         bufA0[spos<P>(-j)] = -p[j];
@@ -261,20 +332,36 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                     if (a.mode == kModeInit) uPhi[0] = 0.0;
                 }
                 if (last) {
-                    bufA0[spos<P>(N - 1)] = 0.0;
-                    bufA1[spos<P>(N - 1)] = 0.0;
+                    bufA0[spos<P>(Nl - 1)] = 0.0;
+                    bufA1[spos<P>(Nl - 1)] = 0.0;
 #pragma unroll
                     for (int j = 1; j <= 3; ++j) {
-                        bufA0[spos<P>(N - 1 + j)] = p[P - j];
-                        bufA1[spos<P>(N - 1 + j)] = -qv[P - j];
+                        bufA0[spos<P>(Nl - 1 + j)] = p[P - j];
+                        bufA1[spos<P>(Nl - 1 + j)] = -qv[P - j];
                     }
                     if (a.mode == kModeInit) {
                         uPhi[N - 1] = 0.0;
                         uPi[N - 1] = 0.0;
                     }
                 }
+                if constexpr (CL == 2) {
+                    if (hl) {   // last 3 nodes of rank 0 -> left halo of rank 1
+#pragma unroll
+                        for (int j = 1; j <= 3; ++j) {
+                            st_peer(bufA0 + spos<P>(-j), p[P - j]);
+                            st_peer(bufA1 + spos<P>(-j), qv[P - j]);
+                        }
+                    }
+                    if (hr) {   // first 3 nodes of rank 1 -> right halo of rank 0
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            st_peer(bufA0 + spos<P>(NL0 + j), p[j]);
+                            st_peer(bufA1 + spos<P>(NL0 + j), qv[j]);
+                        }
+                    }
+                }
             }
-            __syncthreads();
+            csync<CL>();
 
             double *S0 = bufA0, *S1 = bufA1, *D0 = bufB0, *D1 = bufB1;
             bool first = true;
@@ -377,20 +464,39 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                         if (lane == 0) bw = 0.0;
                         if (lane + 1 >= NW) dw = 0.0;
                         if (lane < NW) { cM[lane] = bw; cD[lane] = dw; }
+                        if constexpr (CL == 2) {
+                            double aw = __shfl_up_sync(FULL, A_, 1);
+                            if (lane == 0) aw = 1.0;
+                            if (lane < NW) cMa[lane] = aw;
+                            // block totals to the other CTA: the m map of rank 0, the delta sum of rank 1
+                            if (rank == 0 && lane == NW - 1) {
+                                st_peer(&s_cA, A_);
+                                st_peer(&s_cB, B_);
+                            }
+                            if (rank == 1 && lane == 0) st_peer(&s_cD, D_);
+                        }
                     }
-                    __syncthreads();
+                    csync<CL>();
 
                     long long kmin = 0x7FFFFFFFFFFFFFFFLL;
                     if (act) {
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
-                        double m = fma(aEx, cM[wid], bEx);   // m at node i0
-                        double dc = dEx + cD[wid];           // delta at node i0+P
+                        double m, dc;
+                        if constexpr (CL == 2) {
+                            const double cm = (rank == 1) ? fma(cMa[wid], s_cB, cM[wid]) : cM[wid];
+                            m = fma(aEx, cm, bEx);                          // m at node i0
+                            dc = dEx + cD[wid] + ((rank == 0) ? s_cD : 0.0);  // delta at node i0+P
+                        } else {
+                            m = fma(aEx, cM[wid], bEx);
+                            dc = dEx + cD[wid];
+                        }
 #pragma unroll
                         for (int k = P - 1; k >= 0; --k) {   // delta at nodes i0 .. i0+P-1
                             dc = dc + De[k];
                             De[k] = dc;
                         }
                         double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0, fm1 = 0.0, fm2 = 0.0;
+                        double f0 = 0.0, f1 = 0.0, u0 = 0.0, u1 = 0.0;
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
@@ -403,9 +509,10 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                             const double ui = __ldg(g.T + i) * gi;
                             sF[tb + soff<P>(k)] = fi;
                             sU[tb + soff<P>(k)] = ui;
-                            if (k == 1) g1 = gi;
+                            if (k == 0) { f0 = fi; u0 = ui; }
+                            if (k == 1) { g1 = gi; f1 = fi; u1 = ui; }
                             if (k == 2) g2 = gi;
-                            if (tid == 0 && (k == 1 || k == 2)) {
+                            if (tfirst && (k == 1 || k == 2)) {
                                 sF[spos<P>(-k)] = fi;   // f = F Pi: even about x = 0
                                 sU[spos<P>(-k)] = -ui;  // u = tan^2 F Phi: odd about x = 0
                             }
@@ -418,35 +525,58 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                             if (k < P - 1) m = fma(al, m, be);
                             else if (last) s_mass = fma(al, m, be);
                         }
-                        if (tid == 0) {
+                        if (tfirst) {
                             s_d0 = De[0];
                             // Pi-dot at x = 0 needs (F Phi)'(0) = (16 g_1 - 2 g_2) / (12 h)
                             sF[spos<P>(-3)] = fma(16.0, g1, -2.0 * g2);
+                            if constexpr (CL == 2) st_peer(&s_d0, De[0]);
                         }
                         if (last) {
                             // f odd and u even about x = pi/2; u(pi/2) by even extrapolation
-                            sF[spos<P>(N - 1)] = 0.0;
-                            sF[spos<P>(N)] = -fm1;
-                            sF[spos<P>(N + 1)] = -fm2;
-                            sU[spos<P>(N - 1)] = (4.0 * um1 - um2) * (1.0 / 3.0);
-                            sU[spos<P>(N)] = um1;
-                            sU[spos<P>(N + 1)] = um2;
+                            sF[spos<P>(Nl - 1)] = 0.0;
+                            sF[spos<P>(Nl)] = -fm1;
+                            sF[spos<P>(Nl + 1)] = -fm2;
+                            sU[spos<P>(Nl - 1)] = (4.0 * um1 - um2) * (1.0 / 3.0);
+                            sU[spos<P>(Nl)] = um1;
+                            sU[spos<P>(Nl + 1)] = um2;
                             if (a.outA) {
                                 a.outA[d.off + N - 1] = 1.0;
                                 a.outDelta[d.off + N - 1] = 0.0;
+                            }
+                            if constexpr (CL == 2) st_peer(&s_mass, s_mass);
+                        }
+                        if constexpr (CL == 2) {
+                            if (hl) {   // f, u at the last 2 nodes of rank 0 -> rank 1
+                                st_peer(sF + spos<P>(-1), fm1);
+                                st_peer(sF + spos<P>(-2), fm2);
+                                st_peer(sU + spos<P>(-1), um1);
+                                st_peer(sU + spos<P>(-2), um2);
+                            }
+                            if (hr) {   // f, u at the first 2 nodes of rank 1 -> rank 0
+                                st_peer(sF + spos<P>(NL0), f0);
+                                st_peer(sF + spos<P>(NL0 + 1), f1);
+                                st_peer(sU + spos<P>(NL0), u0);
+                                st_peer(sU + spos<P>(NL0 + 1), u1);
                             }
                         }
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) kmin = min_ll(kmin, __shfl_xor_sync(FULL, kmin, o));
-                    if (lane == 0) wMin[wid] = kmin;
-                    __syncthreads();
+                    if (lane == 0) {
+                        wMin[wid] = kmin;
+                        if constexpr (CL == 2) st_peer(wMinP + wid, kmin);
+                    }
+                    csync<CL>();
 
                     if (s == 0) {
                         // ---------- end-of-step diagnostics on the slice t = step * dt ----------
                         long long km = wMin[0];
 #pragma unroll
                         for (int w = 1; w < NW; ++w) km = min_ll(km, wMin[w]);
+                        if constexpr (CL == 2) {
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) km = min_ll(km, wMinP[w]);
+                        }
                         minA = order_key_inv(km);
                         mass = s_mass;
                         d0 = s_d0;
@@ -504,7 +634,7 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                             // Phi-dot = c12 (Df + rko kp): the factor c12 is folded into the RK weights
                             double Xp = fma(d.rko, kp, Df);
                             double dQ = fma(__ldg(g.iT12 + i), Du, d.cko * kq);
-                            if (k == 0 && tid == 0) {
+                            if (k == 0 && tfirst) {
                                 Xp = 0.0;                                      // Phi(0) = 0
                                 dQ = fma(d.c3, sF[spos<P>(-3)], d.cko * kq);  // 3 (F Phi)'(0)
                             }
@@ -531,21 +661,31 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                             }
                             Dp[soff<P>(k)] = np;
                             Dq[soff<P>(k)] = nq;
-                            if (tid == 0 && k >= 1 && k <= 3) {
+                            if (tfirst && k >= 1 && k <= 3) {
                                 D0[spos<P>(-k)] = -np;  // Phi odd about x = 0
                                 D1[spos<P>(-k)] = nq;   // Pi even about x = 0
                             }
                             if (last && k >= P - 3) {
-                                D0[spos<P>(N - 1 + (P - k))] = np;   // Phi even about pi/2
-                                D1[spos<P>(N - 1 + (P - k))] = -nq;  // Pi odd about pi/2
+                                D0[spos<P>(Nl - 1 + (P - k))] = np;   // Phi even about pi/2
+                                D1[spos<P>(Nl - 1 + (P - k))] = -nq;  // Pi odd about pi/2
+                            }
+                            if constexpr (CL == 2) {
+                                if (hl && k >= P - 3) {      // -> left halo of rank 1
+                                    st_peer(D0 + spos<P>(-(P - k)), np);
+                                    st_peer(D1 + spos<P>(-(P - k)), nq);
+                                }
+                                if (hr && k < 3) {           // -> right halo of rank 0
+                                    st_peer(D0 + spos<P>(NL0 + k), np);
+                                    st_peer(D1 + spos<P>(NL0 + k), nq);
+                                }
                             }
                         }
                         if (last) {
-                            D0[spos<P>(N - 1)] = 0.0;
-                            D1[spos<P>(N - 1)] = 0.0;
+                            D0[spos<P>(Nl - 1)] = 0.0;
+                            D1[spos<P>(Nl - 1)] = 0.0;
                         }
                     }
-                    __syncthreads();
+                    csync<CL>();
                     double *t0 = S0, *t1 = S1;
                     S0 = D0; S1 = D1; D0 = t0; D1 = t1;
                 }
@@ -553,8 +693,8 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
             }
         }
     finish:
-        __syncthreads();  // all global writes of this chunk are issued
-        if (tid == 0) {
+        csync<CL>();  // all global writes of this chunk are issued, by both CTAs
+        if (tid == 0 && rank == 0) {
             if (!skip) {
                 InstState *sp = a.st + b;
                 sp->step = step;
@@ -572,7 +712,7 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
             } else {
                 atomicExch(a.rounds + q, rnd + 1);
             }
-            // retire when fewer work items remain than CTAs take tickets
+            // retire when fewer work items remain than CTAs (clusters) take tickets
             int leave = 0;
             for (;;) {
                 const int act_n = ld_relaxed(&a.ctl->active);
@@ -584,8 +724,9 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                 }
             }
             s_leave = leave;
+            if constexpr (CL == 2) st_peer(&s_leave, leave);
         }
-        __syncthreads();
+        csync<CL>();
         if (s_leave) break;
     }
 }
