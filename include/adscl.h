@@ -66,11 +66,14 @@ typedef struct {
     int32_t ckpt_every;          /* adjoint checkpoint interval in steps; 0 = 256 */
     int64_t max_device_iters;    /* iteration limit of any device-side wait; 0 = default */
     int32_t device;              /* CUDA device ordinal */
-    int32_t one_per_launch;      /* 0: all instances in one persistent launch (CUDA graph);
+    int32_t one_per_launch;      /* 0: all instances in one persistent launch;
                                     1: one kernel launch per instance (comparison mode) */
     int32_t chunk_steps;         /* RK4 steps of one instance per scheduling unit of the
                                     persistent launch (instances migrate between SMs at chunk
                                     boundaries); 0 = 16 */
+    int32_t direct_launch;       /* 0: adscl_evolve replays a cached CUDA graph of its launches
+                                    (recaptured each call on a private stream, updated in
+                                    place); 1: it issues the launches one by one */
     void *stream;                /* cudaStream_t for all work; NULL = the legacy default stream */
 } adscl_config;
 
@@ -98,7 +101,12 @@ adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *a, int32_t K,
  * or until it collapses (min A < theta; Sec. II) or turns non-finite.  Outputs, each of
  * length B (any may be NULL): t_reached (time of the last slice), t_collapse (linear
  * interpolation of min A across theta, +inf if none), mass (M = m(pi/2) of the last slice,
- * the paper's mass), inst_status (adscl_inst_status). */
+ * the paper's mass), inst_status (adscl_inst_status).
+ * The launches (queue set-up, the persistent kernels, the gather of the outputs) run as one
+ * CUDA graph launch on the context's stream unless cfg.direct_launch is set.  If the caller is
+ * capturing the context's stream, they are issued directly so that the caller's graph records
+ * them (with ptr_is_device = 1 the call is then capturable; a replay evolves to the same
+ * t_end). */
 adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, double *t_collapse,
                           double *mass, int32_t *inst_status, int ptr_is_device);
 

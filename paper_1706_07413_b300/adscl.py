@@ -39,6 +39,7 @@ class adscl_config(ctypes.Structure):
                 ("device", ctypes.c_int32),
                 ("one_per_launch", ctypes.c_int32),
                 ("chunk_steps", ctypes.c_int32),
+                ("direct_launch", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -147,7 +148,7 @@ class Solver:
 
     def __init__(self, N, cfl=0.5, ko_sigma=0.5, collapse_threshold=2.0 ** -7, out_dt=1.0,
                  spec_J=64, ckpt_every=256, device=0, one_per_launch=False, stream=None,
-                 max_device_iters=0, chunk_steps=0):
+                 max_device_iters=0, chunk_steps=0, direct_launch=False):
         self.lib = load()
         self.N = np.ascontiguousarray(np.asarray(N, dtype=np.int32).ravel())
         self.B = int(self.N.size)
@@ -165,6 +166,7 @@ class Solver:
         cfg.device = device
         cfg.one_per_launch = 1 if one_per_launch else 0
         cfg.chunk_steps = chunk_steps
+        cfg.direct_launch = 1 if direct_launch else 0
         cfg.stream = stream
         h = ctypes.c_void_p()
         st = self.lib.adscl_create(ctypes.byref(cfg), ctypes.byref(h))

@@ -40,8 +40,10 @@ struct adscl_ctx {
     double cfl = 0.5, sigma = 0.0, theta = 0.0, out_dt = 1.0;
     int spec_J = 64, ckpt = 256;
     int64_t max_iters = 0;
-    int device = 0, one_per_launch = 0, chunk = 16;
+    int device = 0, one_per_launch = 0, chunk = 16, direct_launch = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;     // private stream on which evolve launches are captured
+    cudaGraphExec_t evo_exec = nullptr;    // cached executable graph of adscl_evolve's launches
     int num_sms = 0;
 
     std::vector<InstDesc> h_desc;
@@ -150,7 +152,8 @@ double step_for(int N, double cfl, double cadence)
 // instances with N > 4097 (first in the list, which is sorted by N, largest first) run on 2-CTA
 // clusters with queue control ctl[1], the others on single CTAs with ctl[0].
 adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, const int32_t *order_dev,
-                           const int32_t *order_host, int nwork, double *outA, double *outD)
+                           const int32_t *order_host, int nwork, double *outA, double *outD,
+                           cudaStream_t sm)
 {
     if (nwork <= 0) return ADSCL_OK;
     int nbig = 0;
@@ -188,13 +191,13 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, const int32_t
         a.nwork = nbig;
         a.ctl = ctx->d_ctl + 1;
         a.rounds = ctx->d_rounds + (ctx->B + 1);
-        queue_init_kernel<<<(nbig + 255) / 256, 256, 0, ctx->stream>>>(a.ctl, a.rounds, nbig, clusters);
+        queue_init_kernel<<<(nbig + 255) / 256, 256, 0, sm>>>(a.ctl, a.rounds, nbig, clusters);
         CK(cudaGetLastError());
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(2 * clusters, 1, 1);
         cfg.blockDim = dim3(kNT, 1, 1);
         cfg.dynamicSmemBytes = ctx->smem;
-        cfg.stream = ctx->stream;
+        cfg.stream = sm;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = 2;
@@ -211,9 +214,9 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, const int32_t
         a.nwork = nwork - nbig;
         a.ctl = ctx->d_ctl;
         a.rounds = ctx->d_rounds;
-        queue_init_kernel<<<(a.nwork + 255) / 256, 256, 0, ctx->stream>>>(a.ctl, a.rounds, a.nwork, grid);
+        queue_init_kernel<<<(a.nwork + 255) / 256, 256, 0, sm>>>(a.ctl, a.rounds, a.nwork, grid);
         CK(cudaGetLastError());
-        evolve_kernel<kP, kNT, 1><<<grid, kNT, ctx->smem, ctx->stream>>>(a, ctx->stride);
+        evolve_kernel<kP, kNT, 1><<<grid, kNT, ctx->smem, sm>>>(a, ctx->stride);
         CK(cudaGetLastError());
         ctx->launches += 2;
     }
@@ -433,6 +436,51 @@ adscl_status check_ctx(adscl_ctx *ctx)
     return ADSCL_OK;
 }
 
+// Run the launches that issue(stream) enqueues as one CUDA graph on the context's stream: they
+// are captured on a private stream (nothing executes there), the cached executable graph is
+// updated in place when only kernel parameters changed (re-instantiated otherwise), and the graph
+// is launched.  If the context's stream is itself being captured by the caller, or graphs are
+// switched off, the launches are issued on the context's stream directly.
+template <class Issue>
+adscl_status run_graph(adscl_ctx *ctx, cudaGraphExec_t &exec, Issue issue)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(ctx->stream, &cs));
+    if (ctx->direct_launch || cs != cudaStreamCaptureStatusNone) return issue(ctx->stream);
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t launches0 = ctx->launches;
+    const adscl_status s = issue(ctx->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (s != ADSCL_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        ctx->launches = launches0;
+        if (s != ADSCL_OK) return s;
+        return fail(ctx, ADSCL_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    }
+    if (exec) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(exec, g, &info) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+    }
+    if (!exec) {
+        const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+        if (ei != cudaSuccess) {
+            exec = nullptr;
+            cudaGraphDestroy(g);
+            return fail(ctx, ADSCL_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+        }
+    }
+    cudaGraphDestroy(g);
+    CK(cudaGraphLaunch(exec, ctx->stream));
+    return ADSCL_OK;
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -470,6 +518,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     ctx->device = cfg->device;
     ctx->one_per_launch = cfg->one_per_launch;
     ctx->chunk = cfg->chunk_steps > 0 ? cfg->chunk_steps : 16;
+    ctx->direct_launch = cfg->direct_launch;
     ctx->stream = (cudaStream_t)cfg->stream;
     *out = ctx;
 
@@ -595,7 +644,7 @@ adscl_status adscl_set_initial(adscl_ctx *ctx, const double *Phi, const double *
     CK(cudaMemcpyAsync(ctx->d_Phi, Phi, fb, kind, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_Pi, Pi, fb, kind, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_st, 0, ctx->B * sizeof(InstState), ctx->stream));
-    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, nullptr, nullptr);
+    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, nullptr, nullptr, ctx->stream);
     if (s != ADSCL_OK) return s;
     if (!ptr_is_device) {
         CK(cudaStreamSynchronize(ctx->stream));
@@ -622,7 +671,7 @@ adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *a, int32_t K,
     CK(cudaGetLastError());
     ctx->launches += 1;
     CK(cudaMemsetAsync(ctx->d_st, 0, ctx->B * sizeof(InstState), ctx->stream));
-    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, nullptr, nullptr);
+    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, nullptr, nullptr, ctx->stream);
     if (s != ADSCL_OK) return s;
     if (!ptr_is_device) {
         CK(cudaStreamSynchronize(ctx->stream));
@@ -641,27 +690,32 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
     adscl_status s = check_ctx(ctx);
     if (s != ADSCL_OK) return s;
     if (!std::isfinite(t_end) || t_end < 0.0) return fail(ctx, ADSCL_EINVAL, "bad t_end");
-    if (ctx->one_per_launch) {
-        for (int q = 0; q < ctx->B; ++q) {
-            s = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order + q, ctx->h_order.data() + q, 1, nullptr, nullptr);
-            if (s != ADSCL_OK) return s;
-        }
-    } else {
-        s = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order, ctx->h_order.data(), ctx->B, nullptr, nullptr);
-        if (s != ADSCL_OK) return s;
-    }
     const int B = ctx->B;
     double *o = ctx->d_out;
-    int nbig = 0;
-    for (int n : ctx->N) nbig += n > kMaxPoints1;
-    // single-CTA work list (after the cluster list in d_order), then the cluster list's timeouts
-    gather_kernel<<<(B + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_desc, ctx->d_st, B, t_end, 1,
-                                                           ctx->d_ctl, ctx->d_order + nbig, o, o + B,
-                                                           o + 2 * B, ctx->d_outs);
-    CK(cudaGetLastError());
-    mark_timeout_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl + 1, ctx->d_order, ctx->d_st, ctx->d_outs);
-    CK(cudaGetLastError());
-    ctx->launches += 2;
+    s = run_graph(ctx, ctx->evo_exec, [&](cudaStream_t sm) -> adscl_status {
+        adscl_status r = ADSCL_OK;
+        if (ctx->one_per_launch) {
+            for (int q = 0; q < B && r == ADSCL_OK; ++q)
+                r = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order + q, ctx->h_order.data() + q, 1,
+                                  nullptr, nullptr, sm);
+        } else {
+            r = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order, ctx->h_order.data(), B, nullptr,
+                              nullptr, sm);
+        }
+        if (r != ADSCL_OK) return r;
+        int nbig = 0;
+        for (int n : ctx->N) nbig += n > kMaxPoints1;
+        // single-CTA work list (after the cluster list in d_order), then the cluster list's timeouts
+        gather_kernel<<<(B + 127) / 128, 128, 0, sm>>>(ctx->d_desc, ctx->d_st, B, t_end, 1, ctx->d_ctl,
+                                                       ctx->d_order + nbig, o, o + B, o + 2 * B,
+                                                       ctx->d_outs);
+        CK(cudaGetLastError());
+        mark_timeout_kernel<<<1, 1, 0, sm>>>(ctx->d_ctl + 1, ctx->d_order, ctx->d_st, ctx->d_outs);
+        CK(cudaGetLastError());
+        ctx->launches += 2;
+        return ADSCL_OK;
+    });
+    if (s != ADSCL_OK) return s;
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (t_reached) CK(cudaMemcpyAsync(t_reached, o, B * sizeof(double), kind, ctx->stream));
     if (t_collapse) CK(cudaMemcpyAsync(t_collapse, o + B, B * sizeof(double), kind, ctx->stream));
@@ -684,7 +738,7 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
     s = ensure_modes(ctx);
     if (s != ADSCL_OK) return s;
     // A on the current slices (one constraint solve of every instance, no state change)
-    s = launch_evolve(ctx, kModeSolve, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, ctx->d_scratchA, ctx->d_scratchD);
+    s = launch_evolve(ctx, kModeSolve, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, ctx->d_scratchA, ctx->d_scratchD, ctx->stream);
     if (s != ADSCL_OK) return s;
     // u = w Pi and v = w Phi overwrite the scratch arrays (A is consumed in the same kernel)
     spectrum_weights_kernel<<<ctx->B, 256, 0, ctx->stream>>>(ctx->d_desc, ctx->d_geo, ctx->d_Phi,
@@ -813,7 +867,7 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         CK(cudaMemcpyAsync(ck, ctx->d_Phi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ck + total, ctx->d_Pi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         const long long n1 = std::min(nT, (g + 1) * seg);
-        s = launch_evolve(ctx, kModeEvolve, (double)n1 * ctx->h_desc[0].dt, ctx->d_order, ctx->h_order.data(), B, nullptr, nullptr);
+        s = launch_evolve(ctx, kModeEvolve, (double)n1 * ctx->h_desc[0].dt, ctx->d_order, ctx->h_order.data(), B, nullptr, nullptr, ctx->stream);
     }
     ctx->theta = theta;
     if (s != ADSCL_OK) return s;
@@ -883,7 +937,7 @@ adscl_status adscl_get_state(adscl_ctx *ctx, int32_t inst, double *Phi, double *
         CK(cudaMemcpyAsync(ctx->d_order + ctx->B, &inst, sizeof(int32_t), cudaMemcpyHostToDevice,
                            ctx->stream));
         s = launch_evolve(ctx, kModeSolve, 0.0, ctx->d_order + ctx->B, &inst, 1, ctx->d_scratchA,
-                          ctx->d_scratchD);
+                          ctx->d_scratchD, ctx->stream);
         if (s != ADSCL_OK) return s;
         if (A) CK(cudaMemcpyAsync(A, ctx->d_scratchA + off, nb, kind, ctx->stream));
         if (delta) CK(cudaMemcpyAsync(delta, ctx->d_scratchD + off, nb, kind, ctx->stream));
@@ -910,7 +964,7 @@ adscl_status adscl_set_state(adscl_ctx *ctx, int32_t inst, const double *Phi, co
     CK(cudaMemcpyAsync(ctx->d_Pi + off, Pi, nb, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_st + inst, &st, sizeof st, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_order + ctx->B, &inst, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
-    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order + ctx->B, &inst, 1, nullptr, nullptr);
+    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order + ctx->B, &inst, 1, nullptr, nullptr, ctx->stream);
     if (s != ADSCL_OK) return s;
     CK(cudaStreamSynchronize(ctx->stream));
     return ADSCL_OK;
@@ -951,6 +1005,8 @@ void adscl_destroy(adscl_ctx *ctx)
                     ctx->d_ck, ctx->d_adj_small, ctx->d_adj_queue};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (ctx->evo_exec) cudaGraphExecDestroy(ctx->evo_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
 }
 

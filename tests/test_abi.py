@@ -64,3 +64,20 @@ def test_invalid_configs_rejected_before_device_work():
     assert lib.adscl_launch_count(None) == 0
     assert lib.adscl_last_error(None) == b"null context"
     lib.adscl_destroy(None)
+
+
+def test_config_struct_layout_matches_header(tmp_path):
+    """The binding's adscl_config has the C compiler's size and field offsets."""
+    from paper_1706_07413_b300 import adscl
+    fields = [f[0] for f in adscl.adscl_config._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join(f'    printf("{f} %zu\\n", offsetof(adscl_config, {f}));\n' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "adscl.h"\nint main(void) {\n'
+                   f'{body}    printf("sizeof %zu\\n", sizeof(adscl_config));\n    return 0;\n}}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    for f in fields:
+        assert int(got[f]) == getattr(adscl.adscl_config, f).offset, f
+    assert int(got["sizeof"]) == ctypes.sizeof(adscl.adscl_config)
