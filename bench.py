@@ -45,6 +45,19 @@ SIGMA_KO = 0.5
 # The parallel-scan overheads (per-thread aggregates, warp shuffles, ~7 flops) are not counted.
 FLOPS_PER_POINT_SUBSTEP = 107.75
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one timed evolve_kernel launch of the amplitude scan, from an ncu
+# capture of this script (profiles/evolve_kernel_amp_scan.md); reported only while the kernel
+# source is the one the counters were taken on.
+TRAFFIC = {"kernel_sha256": None, "dram_bytes_per_launch": None}
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("evolve.cuh", "expneg.cuh"):
+        with open(os.path.join(ROOT, "paper_1706_07413_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def _dist():
@@ -131,6 +144,69 @@ def oracle_rate(insts, nsteps, threads):
     return work / el, el, work
 
 
+def batch_fields(insts, sol):
+    """Set the initial slices of `insts` on solver `sol`: mode sums through the library's own
+    synthesis, Gaussian pulses uploaded (Phi = 0)."""
+    B = len(insts)
+    modes = [it for it in insts if it.kind == "modes"]
+    if modes:
+        K = max(len(it.coeffs) for it in modes)
+        a = np.zeros((B, K))
+        for b, it in enumerate(insts):
+            if it.kind == "modes":
+                a[b, : len(it.coeffs)] = it.coeffs
+        sol.set_initial_modes(a)
+        for b, it in enumerate(insts):
+            if it.kind == "gauss":
+                sol.set_state(b, np.zeros(it.N), W.gaussian_pi(it.N, it.eps, it.sigma), 0)
+    else:
+        Pi0 = W.packed([W.gaussian_pi(it.N, it.eps, it.sigma) for it in insts])
+        sol.set_initial(np.zeros_like(Pi0), Pi0)
+
+
+def workload_insts(name, rank):
+    if name == "amp_scan":
+        return W.amp_scan(B=B_DEFAULT, N=N_DEFAULT, seed=rank), (
+            f"amplitude scan: B={B_DEFAULT} Gaussian pulses per GPU, N={N_DEFAULT}, sigma=1/16, "
+            "eps log-uniform [5,80], RK4 dt=0.5dx, constraints every substep, early exit at "
+            "min A < 2^-7")
+    if name == "large":
+        return W.large(seed=3 + rank), (
+            "large grids: B=148 per GPU at N=8193 (2-CTA clusters), half Gaussian pulses "
+            "(sigma U[1/32,1/8], eps log-uniform [5,80]), half two-mode data, early exit at "
+            "min A < 2^-7")
+    if name == "uneven":
+        return W.uneven(seed=1 + rank), (
+            "uneven batch: B=192 per GPU, N uniform in {2049, 4097, 8193}, "
+            "Pi = sum_{j<16} eps e^{-j/3}(1+0.05 N(0,1)) e_j, eps U[0.05,0.2]")
+    raise ValueError(name)
+
+
+def side_rate(insts, stream, local, rk_steps, flush):
+    """Point-substeps/s of one persistent launch of rk_steps RK4 steps on another batch."""
+    import torch
+    from paper_1706_07413_b300 import adscl
+    sol = adscl.Solver([it.N for it in insts], ko_sigma=SIGMA_KO, collapse_threshold=THETA,
+                       device=local, stream=stream.cuda_stream)
+    batch_fields(insts, sol)
+    dt, _ = sol.clock()
+    T = rk_steps * float(dt.max())
+    sol.evolve(T / 8)
+    torch.cuda.synchronize()
+    _, s0 = sol.clock()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        sol.evolve(T / 8 + T)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    _, s1 = sol.clock()
+    work = float(np.sum((s1 - s0) * sol.N.astype(np.float64) * 4.0))
+    sol.close()
+    return work / (e0.elapsed_time(e1) / 1e3)
+
+
 def run_reference(args):
     """The reference arm: the sequential FP64 CPU oracle on the host cores."""
     ws, rank, _ = _dist()
@@ -173,6 +249,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-others", action="store_true")
+    ap.add_argument("--workload", default="amp_scan", choices=["amp_scan", "large", "uneven"],
+                    help="batch to time (the metric's workload is amp_scan)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -189,18 +268,20 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     stream = torch.cuda.Stream()
-    insts = W.amp_scan(B=B_DEFAULT, N=N_DEFAULT, seed=rank)
-    B, N = len(insts), insts[0].N
-    Pi0 = W.packed([W.gaussian_pi(N, it.eps, it.sigma) for it in insts])
-    Phi0 = np.zeros_like(Pi0)
+    insts, wl_desc = workload_insts(args.workload, rank)
+    B = len(insts)
+    N = insts[0].N
+    amp = args.workload == "amp_scan"
+    Pi0 = W.packed([W.gaussian_pi(N, it.eps, it.sigma) for it in insts]) if amp else None
+    Phi0 = np.zeros_like(Pi0) if amp else None
 
     tflops_peak = adscl.probe_fp64(local, stream.cuda_stream)
 
-    sol = adscl.Solver([N] * B, ko_sigma=SIGMA_KO, collapse_threshold=THETA, device=local,
-                       stream=stream.cuda_stream)
-    sol.set_initial(Phi0, Pi0)
+    sol = adscl.Solver([it.N for it in insts], ko_sigma=SIGMA_KO, collapse_threshold=THETA,
+                       device=local, stream=stream.cuda_stream)
+    batch_fields(insts, sol)
     dt, _ = sol.clock()
-    dstep = STEP_RK * dt[0]
+    dstep = STEP_RK * float(dt.max())
     outs = [torch.empty(B, dtype=torch.float64, device="cuda") for _ in range(3)] + \
         [torch.empty(B, dtype=torch.int32, device="cuda")]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -250,14 +331,26 @@ def main():
 
     # roofline of the evolution kernel (it is >99% of each timed launch)
     achieved_tflops = (work * FLOPS_PER_POINT_SUBSTEP) / dev_s / 1e12
+    traffic = None
+    if amp and args.steps > 0 and kernel_digest() == TRAFFIC["kernel_sha256"]:
+        traffic = TRAFFIC["dram_bytes_per_launch"]
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": tflops_peak, "unit": "TFLOP/s",
-                "frac": achieved_tflops / tflops_peak, "traffic": None,
+                "frac": achieved_tflops / tflops_peak, "traffic": traffic,
                 "peak_source": "measured FP64 FMA-chain probe on this GPU (FMA = 2 flops)",
                 "flops_per_point_substep": FLOPS_PER_POINT_SUBSTEP}
 
+    # the other two batch shapes, one launch of 128 RK4 steps each (default workload only)
+    others = None
+    if rank == 0 and amp and not args.no_others:
+        others = {}
+        for name in ("large", "uneven"):
+            oi, od = workload_insts(name, 0)
+            others[name] = {"value": side_rate(oi, stream, local, 128, flush), "unit": UNIT,
+                            "workload": od, "rk_steps": 128}
+
     # one instance per launch, same workload, for the batched-vs-one-per-launch comparison
     opl = None
-    if rank == 0:
+    if rank == 0 and amp:
         nopl = 4
         s1 = adscl.Solver([N] * nopl, ko_sigma=SIGMA_KO, collapse_threshold=THETA, device=local,
                           one_per_launch=True, stream=stream.cuda_stream)
@@ -281,7 +374,7 @@ def main():
     # 256-step checkpoints; timed over a window of ADJ_STEPS steps (the ratio does not depend on
     # the window length: both passes scale with the step count)
     adj = None
-    if rank == 0 and not args.no_adjoint:
+    if rank == 0 and amp and not args.no_adjoint:
         ADJ_STEPS = 1024
         ainst = W.adjoint_batch()
         a = np.stack([it.coeffs for it in ainst])
@@ -312,7 +405,7 @@ def main():
 
     # spectrum timing (current slices of the amplitude scan, 64 modes)
     spec = None
-    if rank == 0:
+    if rank == 0 and amp:
         spec = {}
         for name, prec in (("fp64", adscl.PREC_FP64), ("bf16x3", adscl.PREC_BF16X3),
                            ("tf32x3", adscl.PREC_TF32X3)):
@@ -328,7 +421,7 @@ def main():
     # end to end through the public API with host buffers: upload a fresh batch of initial
     # data from pinned memory, solve, evolve one bench step, read the per-instance results
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and amp:
         hPhi = torch.from_numpy(Phi0).pin_memory().numpy()
         hPi = torch.from_numpy(Pi0).pin_memory().numpy()
         res = [torch.empty(B, dtype=torch.float64).pin_memory().numpy() for _ in range(3)] + \
@@ -360,7 +453,7 @@ def main():
         e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and amp and not args.no_cpu_baseline:
         threads = min(os.cpu_count() or 1, 16)
         sample_insts = W.amp_scan()[: 2 * threads]
         rate, el, _ = oracle_rate(sample_insts, 24, threads)
@@ -374,9 +467,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"amplitude scan: B={B} Gaussian pulses per GPU, N={N}, "
-                                   "sigma=1/16, eps log-uniform [5,80], RK4 dt=0.5dx, "
-                                   "constraints every substep, early exit at min A < 2^-7",
+            "config": {"workload": wl_desc,
                        "step": f"one persistent launch = {STEP_RK} RK4 steps of every running "
                                "instance",
                        "window_t": [round(args.warmup * dstep, 6),
@@ -392,6 +483,7 @@ def main():
                                "batched_over_one_per_launch": (value / ws) / opl if opl else None},
             "adjoint_forward_ratio": adj,
             "spectrum": spec,
+            "other_workloads": others,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

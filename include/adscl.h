@@ -77,7 +77,9 @@ typedef struct {
     void *stream;                /* cudaStream_t for all work; NULL = the legacy default stream */
 } adscl_config;
 
-/* Largest grid size N one instance may use in this build. */
+/* Largest grid size N one instance may use in this build: 32769.  Grids up to 4097 run on one
+ * CTA (one SM) per instance, larger ones on a thread-block cluster of 2, 4 or 8 CTAs sharing
+ * the instance through distributed shared memory. */
 int32_t adscl_max_points(void);
 
 /* Create a context: validates cfg (ADSCL_EINVAL before any allocation or launch), builds the

@@ -26,7 +26,17 @@ namespace {
 constexpr int kP = 8;      // grid nodes per thread
 constexpr int kNT = 512;   // threads per CTA
 constexpr int kMaxPoints1 = kP * kNT + 1;      // 4097: one CTA per instance
-constexpr int kMaxPoints = 2 * kP * kNT + 1;   // 8193: a 2-CTA cluster per instance
+constexpr int kMaxCluster = 8;                 // larger grids: clusters of 2, 4 or 8 CTAs
+constexpr int kMaxPoints = kMaxCluster * kP * kNT + 1;   // 32769
+
+// CTAs per instance of grid size N: the smallest power of two whose CTAs hold the N - 1 cells
+int cluster_of(int N)
+{
+    int cl = 1;
+    while (N > cl * kP * kNT + 1) cl *= 2;
+    return cl;
+}
+int cl_index(int cl) { return cl == 1 ? 0 : cl == 2 ? 1 : cl == 4 ? 2 : 3; }
 static_assert(6 * field_stride<kP>(kMaxPoints1) * 8 + 4096 <= 232448, "shared memory budget");
 
 }  // namespace
@@ -43,8 +53,11 @@ struct adscl_ctx {
     int device = 0, one_per_launch = 0, chunk = 16, direct_launch = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;     // private stream on which evolve launches are captured
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};   // side streams of concurrent launch groups
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t evo_exec = nullptr;    // cached executable graph of adscl_evolve's launches
     int num_sms = 0;
+    int max_units[4] = {0, 0, 0, 0};   // co-resident CTAs / clusters of 2, 4, 8 of the evolve kernel
 
     std::vector<InstDesc> h_desc;
     std::vector<int32_t> h_order;
@@ -148,16 +161,40 @@ double step_for(int N, double cfl, double cadence)
     return cadence / std::ceil(cadence / (cfl * h));
 }
 
-// Launch the evolution kernel on the work list order_dev[0 .. nwork) (host copy order_host):
-// instances with N > 4097 (first in the list, which is sorted by N, largest first) run on 2-CTA
-// clusters with queue control ctl[1], the others on single CTAs with ctl[0].
-adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, const int32_t *order_dev,
+template <int CL>
+adscl_status launch_group(adscl_ctx *ctx, const EvolveArgs &a, int units, cudaStream_t sm)
+{
+    if constexpr (CL == 1) {
+        evolve_kernel<kP, kNT, 1><<<units, kNT, ctx->smem, sm>>>(a, ctx->stride);
+        CK(cudaGetLastError());
+    } else {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(CL * units, 1, 1);
+        cfg.blockDim = dim3(kNT, 1, 1);
+        cfg.dynamicSmemBytes = ctx->smem;
+        cfg.stream = sm;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, evolve_kernel<kP, kNT, CL>, a, ctx->stride));
+    }
+    return ADSCL_OK;
+}
+
+// Launch the evolution kernel on the work list d_order[first .. first + nwork) (host copy
+// order_host[0 .. nwork)).  The list is sorted by N, largest first, so the instances that need
+// clusters of 8, 4 and 2 CTAs and those that fit one CTA form consecutive groups; each group is
+// one persistent launch with the queue control and round counters of its first list position
+// (d_ctl[first + i], d_rounds[first + i ..]), so no two launches of one call share them.
+adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
                            const int32_t *order_host, int nwork, double *outA, double *outD,
                            cudaStream_t sm)
 {
     if (nwork <= 0) return ADSCL_OK;
-    int nbig = 0;
-    while (nbig < nwork && ctx->N[order_host[nbig]] > kMaxPoints1) ++nbig;
     EvolveArgs a{};
     a.desc = ctx->d_desc;
     a.st = ctx->d_st;
@@ -185,51 +222,66 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, const int32_t
     if ((long long)nwork * rounds > 0x7ffffff0LL)
         return fail(ctx, ADSCL_EINVAL, "t_end too large for one launch (%lld rounds)", rounds);
     a.max_rounds = (int32_t)rounds;
-    if (nbig > 0) {
-        const int clusters = std::min(nbig, ctx->num_sms / 2);
-        a.order = order_dev;
-        a.nwork = nbig;
-        a.ctl = ctx->d_ctl + 1;
-        a.rounds = ctx->d_rounds + (ctx->B + 1);
-        queue_init_kernel<<<(nbig + 255) / 256, 256, 0, sm>>>(a.ctl, a.rounds, nbig, clusters);
+    // the groups (at most four) run concurrently: the first on sm, the others on side streams
+    // forked from sm and joined back into it; the block scheduler gives the SMs a group frees to
+    // the CTAs of the others still waiting to start (no group waits on another)
+    int starts[5], ng = 0;
+    for (int i = 0; i < nwork;) {
+        const int cl = cluster_of(ctx->N[order_host[i]]);
+        int j = i + 1;
+        while (j < nwork && cluster_of(ctx->N[order_host[j]]) == cl) ++j;
+        starts[ng++] = i;
+        i = j;
+    }
+    starts[ng] = nwork;
+    if (ng > 1) {
+        for (int g = 0; g < ng - 1; ++g)
+            if (!ctx->aux[g]) CK(cudaStreamCreateWithFlags(&ctx->aux[g], cudaStreamNonBlocking));
+        if (!ctx->ev_fork) {
+            CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+            for (int g = 0; g < 3; ++g) CK(cudaEventCreateWithFlags(&ctx->ev_join[g], cudaEventDisableTiming));
+        }
+        CK(cudaEventRecord(ctx->ev_fork, sm));
+        for (int g = 0; g < ng - 1; ++g) CK(cudaStreamWaitEvent(ctx->aux[g], ctx->ev_fork, 0));
+    }
+    for (int g = 0; g < ng; ++g) {
+        const int i = starts[g], j = starts[g + 1];
+        const int cl = cluster_of(ctx->N[order_host[i]]);
+        const cudaStream_t gs = (g == 0) ? sm : ctx->aux[g - 1];
+        const int units = std::min(j - i, ctx->max_units[cl_index(cl)]);
+        a.order = ctx->d_order + first + i;
+        a.nwork = j - i;
+        a.ctl = ctx->d_ctl + first + i;
+        a.rounds = ctx->d_rounds + first + i;
+        queue_init_kernel<<<(a.nwork + 255) / 256, 256, 0, gs>>>(a.ctl, a.rounds, a.nwork, units);
         CK(cudaGetLastError());
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(2 * clusters, 1, 1);
-        cfg.blockDim = dim3(kNT, 1, 1);
-        cfg.dynamicSmemBytes = ctx->smem;
-        cfg.stream = sm;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        CK(cudaLaunchKernelEx(&cfg, evolve_kernel<kP, kNT, 2>, a, ctx->stride));
+        adscl_status s = ADSCL_OK;
+        switch (cl) {
+        case 1: s = launch_group<1>(ctx, a, units, gs); break;
+        case 2: s = launch_group<2>(ctx, a, units, gs); break;
+        case 4: s = launch_group<4>(ctx, a, units, gs); break;
+        default: s = launch_group<8>(ctx, a, units, gs); break;
+        }
+        if (s != ADSCL_OK) return s;
         ctx->launches += 2;
     }
-    if (nwork - nbig > 0) {
-        const int grid = std::min(nwork - nbig, ctx->num_sms);
-        a.order = order_dev + nbig;
-        a.nwork = nwork - nbig;
-        a.ctl = ctx->d_ctl;
-        a.rounds = ctx->d_rounds;
-        queue_init_kernel<<<(a.nwork + 255) / 256, 256, 0, sm>>>(a.ctl, a.rounds, a.nwork, grid);
-        CK(cudaGetLastError());
-        evolve_kernel<kP, kNT, 1><<<grid, kNT, ctx->smem, sm>>>(a, ctx->stride);
-        CK(cudaGetLastError());
-        ctx->launches += 2;
+    for (int g = 0; g < ng - 1; ++g) {
+        CK(cudaEventRecord(ctx->ev_join[g], ctx->aux[g]));
+        CK(cudaStreamWaitEvent(sm, ctx->ev_join[g], 0));
     }
     return ADSCL_OK;
 }
 
-// status kTimeout for the instance whose chunk wait ran out in the last cluster launch
-__global__ void mark_timeout_kernel(const QueueCtl *ctl, const int32_t *order, const InstState *st,
-                                    int32_t *status)
+// status kTimeout for every instance whose chunk wait ran out in a launch of this call: the
+// launch whose list starts at position i records 1 + (list index) in ctl[i].error
+__global__ void mark_timeout_kernel(const QueueCtl *ctl, const int32_t *order, int n,
+                                    const InstState *st, int32_t *status)
 {
-    const int err = ctl->error;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int err = ctl[i].error;
     if (err > 0) {
-        const int b = order[err - 1];
+        const int b = order[i + err - 1];
         if (st[b].status == kRunning) status[b] = kTimeout;
     }
 }
@@ -237,9 +289,10 @@ __global__ void mark_timeout_kernel(const QueueCtl *ctl, const int32_t *order, c
 // after a synchronising call: report a device wait that ran out
 adscl_status check_timeout(adscl_ctx *ctx)
 {
-    QueueCtl c[2]{};
-    CK(cudaMemcpy(c, ctx->d_ctl, sizeof c, cudaMemcpyDeviceToHost));
-    if (c[0].error || c[1].error) return fail(ctx, ADSCL_ETIMEOUT, "a chunk wait ran out");
+    std::vector<QueueCtl> c(ctx->B + 1);
+    CK(cudaMemcpy(c.data(), ctx->d_ctl, c.size() * sizeof(QueueCtl), cudaMemcpyDeviceToHost));
+    for (const QueueCtl &q : c)
+        if (q.error) return fail(ctx, ADSCL_ETIMEOUT, "a chunk wait ran out");
     return ADSCL_OK;
 }
 
@@ -609,9 +662,9 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
                      [&](int x, int y) { return ctx->N[x] > ctx->N[y]; });
     CK(cudaMalloc(&ctx->d_order, (ctx->B + 1) * sizeof(int32_t)));
     CK(cudaMemcpy(ctx->d_order, ctx->h_order.data(), ctx->B * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&ctx->d_ctl, 2 * sizeof(QueueCtl)));
-    CK(cudaMemset(ctx->d_ctl, 0, 2 * sizeof(QueueCtl)));
-    CK(cudaMalloc(&ctx->d_rounds, 2 * (ctx->B + 1) * sizeof(int32_t)));
+    CK(cudaMalloc(&ctx->d_ctl, (ctx->B + 1) * sizeof(QueueCtl)));
+    CK(cudaMemset(ctx->d_ctl, 0, (ctx->B + 1) * sizeof(QueueCtl)));
+    CK(cudaMalloc(&ctx->d_rounds, (ctx->B + 1) * sizeof(int32_t)));
     {
         // 2^{j/256}, computed in extended precision and rounded once to double
         std::vector<double> tab(kExpTableSize);
@@ -622,7 +675,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     CK(cudaMalloc(&ctx->d_out, 3 * (size_t)ctx->B * sizeof(double)));
     CK(cudaMalloc(&ctx->d_outs, (size_t)ctx->B * sizeof(int32_t)));
 
-    // a CTA never holds more than 4096 nodes of one instance (larger grids use 2-CTA clusters)
+    // a CTA never holds more than 4096 nodes of one instance (larger grids use clusters)
     ctx->stride = field_stride<kP>(std::min(ctx->Nmax, kMaxPoints1));
     ctx->smem = (size_t)6 * ctx->stride * sizeof(double);
     // the attribute is per kernel, not per context: always raise it to the largest grid
@@ -631,6 +684,36 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
                             (int)smem_max));
     CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem_max));
+    CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_max));
+    CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_max));
+    // persistent grid sizes: one CTA per SM, and as many clusters as can be co-resident
+    ctx->max_units[0] = ctx->num_sms;
+    for (int cl = 2; cl <= kMaxCluster; cl *= 2) {
+        bool used = false;
+        for (int n : ctx->N) used |= cluster_of(n) == cl;
+        if (!used) continue;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(cl * (ctx->num_sms / cl), 1, 1);
+        cfg.blockDim = dim3(kNT, 1, 1);
+        cfg.dynamicSmemBytes = ctx->smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        cudaError_t e = cl == 2 ? cudaOccupancyMaxActiveClusters(&nc, evolve_kernel<kP, kNT, 2>, &cfg)
+                      : cl == 4 ? cudaOccupancyMaxActiveClusters(&nc, evolve_kernel<kP, kNT, 4>, &cfg)
+                                : cudaOccupancyMaxActiveClusters(&nc, evolve_kernel<kP, kNT, 8>, &cfg);
+        if (e != cudaSuccess || nc < 1)
+            return fail(ctx, ADSCL_EUNSUPPORTED, "no %d-CTA cluster of the evolve kernel fits (%s)", cl,
+                        cudaGetErrorString(e));
+        ctx->max_units[cl_index(cl)] = nc;
+    }
     return ADSCL_OK;
 }
 
@@ -644,7 +727,7 @@ adscl_status adscl_set_initial(adscl_ctx *ctx, const double *Phi, const double *
     CK(cudaMemcpyAsync(ctx->d_Phi, Phi, fb, kind, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_Pi, Pi, fb, kind, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_st, 0, ctx->B * sizeof(InstState), ctx->stream));
-    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, nullptr, nullptr, ctx->stream);
+    s = launch_evolve(ctx, kModeInit, 0.0, 0, ctx->h_order.data(), ctx->B, nullptr, nullptr, ctx->stream);
     if (s != ADSCL_OK) return s;
     if (!ptr_is_device) {
         CK(cudaStreamSynchronize(ctx->stream));
@@ -671,7 +754,7 @@ adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *a, int32_t K,
     CK(cudaGetLastError());
     ctx->launches += 1;
     CK(cudaMemsetAsync(ctx->d_st, 0, ctx->B * sizeof(InstState), ctx->stream));
-    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, nullptr, nullptr, ctx->stream);
+    s = launch_evolve(ctx, kModeInit, 0.0, 0, ctx->h_order.data(), ctx->B, nullptr, nullptr, ctx->stream);
     if (s != ADSCL_OK) return s;
     if (!ptr_is_device) {
         CK(cudaStreamSynchronize(ctx->stream));
@@ -694,23 +777,20 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
     double *o = ctx->d_out;
     s = run_graph(ctx, ctx->evo_exec, [&](cudaStream_t sm) -> adscl_status {
         adscl_status r = ADSCL_OK;
+        CK(cudaMemsetAsync(ctx->d_ctl, 0, (B + 1) * sizeof(QueueCtl), sm));   // no stale wait errors
         if (ctx->one_per_launch) {
             for (int q = 0; q < B && r == ADSCL_OK; ++q)
-                r = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order + q, ctx->h_order.data() + q, 1,
-                                  nullptr, nullptr, sm);
+                r = launch_evolve(ctx, kModeEvolve, t_end, q, ctx->h_order.data() + q, 1, nullptr,
+                                  nullptr, sm);
         } else {
-            r = launch_evolve(ctx, kModeEvolve, t_end, ctx->d_order, ctx->h_order.data(), B, nullptr,
-                              nullptr, sm);
+            r = launch_evolve(ctx, kModeEvolve, t_end, 0, ctx->h_order.data(), B, nullptr, nullptr, sm);
         }
         if (r != ADSCL_OK) return r;
-        int nbig = 0;
-        for (int n : ctx->N) nbig += n > kMaxPoints1;
-        // single-CTA work list (after the cluster list in d_order), then the cluster list's timeouts
-        gather_kernel<<<(B + 127) / 128, 128, 0, sm>>>(ctx->d_desc, ctx->d_st, B, t_end, 1, ctx->d_ctl,
-                                                       ctx->d_order + nbig, o, o + B, o + 2 * B,
-                                                       ctx->d_outs);
+        gather_kernel<<<(B + 127) / 128, 128, 0, sm>>>(ctx->d_desc, ctx->d_st, B, t_end, 1, nullptr,
+                                                       nullptr, o, o + B, o + 2 * B, ctx->d_outs);
         CK(cudaGetLastError());
-        mark_timeout_kernel<<<1, 1, 0, sm>>>(ctx->d_ctl + 1, ctx->d_order, ctx->d_st, ctx->d_outs);
+        mark_timeout_kernel<<<(B + 127) / 128, 128, 0, sm>>>(ctx->d_ctl, ctx->d_order, B, ctx->d_st,
+                                                            ctx->d_outs);
         CK(cudaGetLastError());
         ctx->launches += 2;
         return ADSCL_OK;
@@ -738,7 +818,7 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
     s = ensure_modes(ctx);
     if (s != ADSCL_OK) return s;
     // A on the current slices (one constraint solve of every instance, no state change)
-    s = launch_evolve(ctx, kModeSolve, 0.0, ctx->d_order, ctx->h_order.data(), ctx->B, ctx->d_scratchA, ctx->d_scratchD, ctx->stream);
+    s = launch_evolve(ctx, kModeSolve, 0.0, 0, ctx->h_order.data(), ctx->B, ctx->d_scratchA, ctx->d_scratchD, ctx->stream);
     if (s != ADSCL_OK) return s;
     // u = w Pi and v = w Phi overwrite the scratch arrays (A is consumed in the same kernel)
     spectrum_weights_kernel<<<ctx->B, 256, 0, ctx->stream>>>(ctx->d_desc, ctx->d_geo, ctx->d_Phi,
@@ -867,7 +947,7 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         CK(cudaMemcpyAsync(ck, ctx->d_Phi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ck + total, ctx->d_Pi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         const long long n1 = std::min(nT, (g + 1) * seg);
-        s = launch_evolve(ctx, kModeEvolve, (double)n1 * ctx->h_desc[0].dt, ctx->d_order, ctx->h_order.data(), B, nullptr, nullptr, ctx->stream);
+        s = launch_evolve(ctx, kModeEvolve, (double)n1 * ctx->h_desc[0].dt, 0, ctx->h_order.data(), B, nullptr, nullptr, ctx->stream);
     }
     ctx->theta = theta;
     if (s != ADSCL_OK) return s;
@@ -936,8 +1016,8 @@ adscl_status adscl_get_state(adscl_ctx *ctx, int32_t inst, double *Phi, double *
         // one constraint solve of this instance's slice (no state change)
         CK(cudaMemcpyAsync(ctx->d_order + ctx->B, &inst, sizeof(int32_t), cudaMemcpyHostToDevice,
                            ctx->stream));
-        s = launch_evolve(ctx, kModeSolve, 0.0, ctx->d_order + ctx->B, &inst, 1, ctx->d_scratchA,
-                          ctx->d_scratchD, ctx->stream);
+        s = launch_evolve(ctx, kModeSolve, 0.0, ctx->B, &inst, 1, ctx->d_scratchA, ctx->d_scratchD,
+                          ctx->stream);
         if (s != ADSCL_OK) return s;
         if (A) CK(cudaMemcpyAsync(A, ctx->d_scratchA + off, nb, kind, ctx->stream));
         if (delta) CK(cudaMemcpyAsync(delta, ctx->d_scratchD + off, nb, kind, ctx->stream));
@@ -964,7 +1044,7 @@ adscl_status adscl_set_state(adscl_ctx *ctx, int32_t inst, const double *Phi, co
     CK(cudaMemcpyAsync(ctx->d_Pi + off, Pi, nb, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_st + inst, &st, sizeof st, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_order + ctx->B, &inst, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
-    s = launch_evolve(ctx, kModeInit, 0.0, ctx->d_order + ctx->B, &inst, 1, nullptr, nullptr, ctx->stream);
+    s = launch_evolve(ctx, kModeInit, 0.0, ctx->B, &inst, 1, nullptr, nullptr, ctx->stream);
     if (s != ADSCL_OK) return s;
     CK(cudaStreamSynchronize(ctx->stream));
     return ADSCL_OK;
@@ -1007,6 +1087,11 @@ void adscl_destroy(adscl_ctx *ctx)
         if (p) cudaFree(p);
     if (ctx->evo_exec) cudaGraphExecDestroy(ctx->evo_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (int g = 0; g < 3; ++g) {
+        if (ctx->aux[g]) cudaStreamDestroy(ctx->aux[g]);
+        if (ctx->ev_join[g]) cudaEventDestroy(ctx->ev_join[g]);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     delete ctx;
 }
 

@@ -151,11 +151,12 @@ __global__ void queue_init_kernel(QueueCtl *ctl, int32_t *rounds, int nwork, int
     if (i < nwork) rounds[i] = 0;
 }
 
-// cluster-wide barrier for CL = 2 (both CTAs execute every barrier in the same order: all their
-// control decisions are taken from data exchanged between them), CTA barrier for CL = 1
+// cluster-wide barrier for CL > 1 (every CTA of the cluster executes every barrier in the same
+// order: all control decisions are taken by rank 0 and pushed to the others), CTA barrier for
+// CL = 1
 template <int CL>
 __device__ __forceinline__ void csync() {
-    if constexpr (CL == 2)
+    if constexpr (CL > 1)
         asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
     else
         __syncthreads();
@@ -165,31 +166,41 @@ __device__ __forceinline__ int cluster_rank() {
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return (int)r;
 }
-// stores into the same shared-memory location of the other CTA of a 2-CTA cluster
-__device__ __forceinline__ uint32_t peer_addr(const void *p) {
+// stores into the same shared-memory location of CTA `dst` of the cluster
+__device__ __forceinline__ uint32_t peer_addr(const void *p, int dst) {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
     uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(1u - (uint32_t)cluster_rank()));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"((uint32_t)dst));
     return r;
 }
-__device__ __forceinline__ void st_peer(double *p, double v) {
-    asm volatile("st.shared::cluster.f64 [%0], %1;" :: "r"(peer_addr(p)), "d"(v) : "memory");
+__device__ __forceinline__ void st_peer(double *p, double v, int dst) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" :: "r"(peer_addr(p, dst)), "d"(v) : "memory");
 }
-__device__ __forceinline__ void st_peer(long long *p, long long v) {
-    asm volatile("st.shared::cluster.b64 [%0], %1;" :: "r"(peer_addr(p)), "l"(v) : "memory");
+__device__ __forceinline__ void st_peer(long long *p, long long v, int dst) {
+    asm volatile("st.shared::cluster.b64 [%0], %1;" :: "r"(peer_addr(p, dst)), "l"(v) : "memory");
 }
-__device__ __forceinline__ void st_peer(int *p, int v) {
-    asm volatile("st.shared::cluster.b32 [%0], %1;" :: "r"(peer_addr(p)), "r"(v) : "memory");
+__device__ __forceinline__ void st_peer(int *p, int v, int dst) {
+    asm volatile("st.shared::cluster.b32 [%0], %1;" :: "r"(peer_addr(p, dst)), "r"(v) : "memory");
 }
+// the same value into every other CTA of a CL-CTA cluster
+template <int CL, class T>
+__device__ __forceinline__ void st_others(T *p, T v, int rank) {
+#pragma unroll
+    for (int j = 1; j < CL; ++j) st_peer(p, v, (rank + j) % CL);
+}
+// first node block of cluster rank r when T node blocks are split over CL ranks
+template <int CL>
+__device__ __forceinline__ int block_start(int r, int T) { return (r * T + CL - 1) / CL; }
 
-// CL = 1: one CTA per instance.  CL = 2: a cluster of two CTAs per instance, each owning half of
-// the threads' node blocks; halos, scan carries and the step-end diagnostics cross between the
-// two CTAs through distributed shared memory.
+// CL = 1: one CTA per instance.  CL = 2, 4, 8: a cluster of CL CTAs per instance, rank r owning
+// the node blocks block_start(r) .. block_start(r+1)-1 (at least NT/2 blocks each, so P >= 3
+// halo nodes always come from the neighbouring rank); halos, scan carries and the step-end
+// diagnostics cross between the CTAs through distributed shared memory.
 template <int P, int NT, int CL = 1>
 __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
 {
     static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
-    static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
+    static_assert(CL == 1 || CL == 2 || CL == 4 || CL == 8, "cluster of 1, 2, 4 or 8 CTAs");
     constexpr int NW = NT / 32;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ double smem[];
@@ -198,8 +209,8 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
     double *sF = smem + 4 * stride, *sU = smem + 5 * stride;        // alpha/beta, then f/u
     __shared__ double s_tab[kExpTableSize];
     __shared__ double wAl[NW], wBe[NW], wDe[NW], cM[NW], cMa[NW], cD[NW];
-    __shared__ long long wMin[NW], wMinP[NW];
-    __shared__ double s_mass, s_d0, s_cA, s_cB, s_cD;
+    __shared__ long long wMin[NW], wMinP[CL * NW];
+    __shared__ double s_mass, s_d0, s_cA[CL], s_cB[CL], s_cD[CL];
     __shared__ int s_cmd, s_q, s_r, s_leave;
     __shared__ long long s_step;
     __shared__ double s_tc, s_minA, s_massS, s_d0S;
@@ -207,7 +218,7 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int rank = 0;
-    if constexpr (CL == 2) rank = cluster_rank();
+    if constexpr (CL > 1) rank = cluster_rank();
     for (int i = tid; i < kExpTableSize; i += NT) s_tab[i] = a.exptab[i];
 
     for (;;) {
@@ -254,16 +265,16 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
             s_massS = S.mass;
             s_d0S = S.delta0;
             s_status = S.status;
-            if constexpr (CL == 2) {
-                st_peer(&s_cmd, cmd);
-                st_peer(&s_q, q);
-                st_peer(&s_r, r);
-                st_peer(&s_step, (long long)S.step);
-                st_peer(&s_tc, S.t_c);
-                st_peer(&s_minA, S.minA);
-                st_peer(&s_massS, S.mass);
-                st_peer(&s_d0S, S.delta0);
-                st_peer(&s_status, (int)S.status);
+            if constexpr (CL > 1) {
+                st_others<CL>(&s_cmd, cmd, 0);
+                st_others<CL>(&s_q, q, 0);
+                st_others<CL>(&s_r, r, 0);
+                st_others<CL>(&s_step, (long long)S.step, 0);
+                st_others<CL>(&s_tc, S.t_c, 0);
+                st_others<CL>(&s_minA, S.minA, 0);
+                st_others<CL>(&s_massS, S.mass, 0);
+                st_others<CL>(&s_d0S, S.delta0, 0);
+                st_others<CL>(&s_status, (int)S.status, 0);
             }
         }
         csync<CL>();
@@ -287,15 +298,15 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
         }
         const int N = d.N;
         const int TnAll = (N - 1) / P;
-        const int Tn0 = (CL == 2) ? (TnAll + 1) / 2 : TnAll;   // node blocks of CTA rank 0
-        const int Tn = (rank == 0) ? Tn0 : TnAll - Tn0;         // node blocks of this CTA
-        const int gb = (rank == 0) ? 0 : Tn0 * P;               // first node of this CTA
-        const int NL0 = Tn0 * P;                                // nodes of CTA rank 0
+        const int bs = block_start<CL>(rank, TnAll);
+        const int Tn = block_start<CL>(rank + 1, TnAll) - bs;  // node blocks of this CTA
+        const int gb = bs * P;                                  // first node of this CTA
+        const int NLp = (rank > 0) ? (bs - block_start<CL>(rank - 1, TnAll)) * P : 0;  // nodes of rank-1
         const bool act = tid < Tn;
         const bool tfirst = rank == 0 && tid == 0;              // owns node 0
         const bool last = (rank == CL - 1) && tid == Tn - 1;    // owns node N-2
-        const bool hl = (CL == 2) && rank == 0 && tid == Tn - 1;  // pushes the halo of rank 1
-        const bool hr = (CL == 2) && rank == 1 && tid == 0;       // pushes the halo of rank 0
+        const bool hl = (CL > 1) && rank < CL - 1 && tid == Tn - 1;  // pushes the left halo of rank+1
+        const bool hr = (CL > 1) && rank > 0 && tid == 0;            // pushes the right halo of rank-1
         const int i0 = gb + tid * P;       // global node of the thread's first node
         const int tb = (P + 1) * tid;      // thread base in the padded arrays (local nodes)
         const int Nl = N - gb;             // local index of node N (boundary ghosts: Nl - 1 + j)
@@ -344,19 +355,19 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                         uPi[N - 1] = 0.0;
                     }
                 }
-                if constexpr (CL == 2) {
-                    if (hl) {   // last 3 nodes of rank 0 -> left halo of rank 1
+                if constexpr (CL > 1) {
+                    if (hl) {   // last 3 nodes -> left halo of rank+1
 #pragma unroll
                         for (int j = 1; j <= 3; ++j) {
-                            st_peer(bufA0 + spos<P>(-j), p[P - j]);
-                            st_peer(bufA1 + spos<P>(-j), qv[P - j]);
+                            st_peer(bufA0 + spos<P>(-j), p[P - j], rank + 1);
+                            st_peer(bufA1 + spos<P>(-j), qv[P - j], rank + 1);
                         }
                     }
-                    if (hr) {   // first 3 nodes of rank 1 -> right halo of rank 0
+                    if (hr) {   // first 3 nodes -> right halo of rank-1
 #pragma unroll
                         for (int j = 0; j < 3; ++j) {
-                            st_peer(bufA0 + spos<P>(NL0 + j), p[j]);
-                            st_peer(bufA1 + spos<P>(NL0 + j), qv[j]);
+                            st_peer(bufA0 + spos<P>(NLp + j), p[j], rank - 1);
+                            st_peer(bufA1 + spos<P>(NLp + j), qv[j], rank - 1);
                         }
                     }
                 }
@@ -464,16 +475,21 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                         if (lane == 0) bw = 0.0;
                         if (lane + 1 >= NW) dw = 0.0;
                         if (lane < NW) { cM[lane] = bw; cD[lane] = dw; }
-                        if constexpr (CL == 2) {
+                        if constexpr (CL > 1) {
                             double aw = __shfl_up_sync(FULL, A_, 1);
                             if (lane == 0) aw = 1.0;
                             if (lane < NW) cMa[lane] = aw;
-                            // block totals to the other CTA: the m map of rank 0, the delta sum of rank 1
-                            if (rank == 0 && lane == NW - 1) {
-                                st_peer(&s_cA, A_);
-                                st_peer(&s_cB, B_);
+                            // block totals to the other ranks: the m map to higher ranks, the delta
+                            // sum to lower ranks (slot = the sender's rank)
+                            if (lane == NW - 1) {
+                                for (int j = rank + 1; j < CL; ++j) {
+                                    st_peer(s_cA + rank, A_, j);
+                                    st_peer(s_cB + rank, B_, j);
+                                }
                             }
-                            if (rank == 1 && lane == 0) st_peer(&s_cD, D_);
+                            if (lane == 0) {
+                                for (int j = 0; j < rank; ++j) st_peer(s_cD + rank, D_, j);
+                            }
                         }
                     }
                     csync<CL>();
@@ -482,10 +498,16 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                     if (act) {
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
                         double m, dc;
-                        if constexpr (CL == 2) {
-                            const double cm = (rank == 1) ? fma(cMa[wid], s_cB, cM[wid]) : cM[wid];
-                            m = fma(aEx, cm, bEx);                          // m at node i0
-                            dc = dEx + cD[wid] + ((rank == 0) ? s_cD : 0.0);  // delta at node i0+P
+                        if constexpr (CL > 1) {
+                            // m at this rank's first node: the maps of ranks 0 .. rank-1 applied to m = 0
+                            double mr = 0.0;
+                            for (int j = 0; j < rank; ++j) mr = (j == 0) ? s_cB[0] : fma(s_cA[j], mr, s_cB[j]);
+                            // delta carried in from the ranks to the right
+                            double dr = 0.0;
+                            for (int j = CL - 1; j > rank; --j) dr = (j == CL - 1) ? s_cD[j] : dr + s_cD[j];
+                            const double cm = (rank > 0) ? fma(cMa[wid], mr, cM[wid]) : cM[wid];
+                            m = fma(aEx, cm, bEx);                                   // m at node i0
+                            dc = dEx + cD[wid] + ((rank < CL - 1) ? dr : 0.0);      // delta at node i0+P
                         } else {
                             m = fma(aEx, cM[wid], bEx);
                             dc = dEx + cD[wid];
@@ -529,7 +551,7 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                             s_d0 = De[0];
                             // Pi-dot at x = 0 needs (F Phi)'(0) = (16 g_1 - 2 g_2) / (12 h)
                             sF[spos<P>(-3)] = fma(16.0, g1, -2.0 * g2);
-                            if constexpr (CL == 2) st_peer(&s_d0, De[0]);
+                            if constexpr (CL > 1) st_others<CL>(&s_d0, De[0], 0);
                         }
                         if (last) {
                             // f odd and u even about x = pi/2; u(pi/2) by even extrapolation
@@ -543,20 +565,20 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                                 a.outA[d.off + N - 1] = 1.0;
                                 a.outDelta[d.off + N - 1] = 0.0;
                             }
-                            if constexpr (CL == 2) st_peer(&s_mass, s_mass);
+                            if constexpr (CL > 1) st_others<CL>(&s_mass, s_mass, CL - 1);
                         }
-                        if constexpr (CL == 2) {
-                            if (hl) {   // f, u at the last 2 nodes of rank 0 -> rank 1
-                                st_peer(sF + spos<P>(-1), fm1);
-                                st_peer(sF + spos<P>(-2), fm2);
-                                st_peer(sU + spos<P>(-1), um1);
-                                st_peer(sU + spos<P>(-2), um2);
+                        if constexpr (CL > 1) {
+                            if (hl) {   // f, u at the last 2 nodes -> left halo of rank+1
+                                st_peer(sF + spos<P>(-1), fm1, rank + 1);
+                                st_peer(sF + spos<P>(-2), fm2, rank + 1);
+                                st_peer(sU + spos<P>(-1), um1, rank + 1);
+                                st_peer(sU + spos<P>(-2), um2, rank + 1);
                             }
-                            if (hr) {   // f, u at the first 2 nodes of rank 1 -> rank 0
-                                st_peer(sF + spos<P>(NL0), f0);
-                                st_peer(sF + spos<P>(NL0 + 1), f1);
-                                st_peer(sU + spos<P>(NL0), u0);
-                                st_peer(sU + spos<P>(NL0 + 1), u1);
+                            if (hr) {   // f, u at the first 2 nodes -> right halo of rank-1
+                                st_peer(sF + spos<P>(NLp), f0, rank - 1);
+                                st_peer(sF + spos<P>(NLp + 1), f1, rank - 1);
+                                st_peer(sU + spos<P>(NLp), u0, rank - 1);
+                                st_peer(sU + spos<P>(NLp + 1), u1, rank - 1);
                             }
                         }
                     }
@@ -564,7 +586,7 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                     for (int o = 16; o > 0; o >>= 1) kmin = min_ll(kmin, __shfl_xor_sync(FULL, kmin, o));
                     if (lane == 0) {
                         wMin[wid] = kmin;
-                        if constexpr (CL == 2) st_peer(wMinP + wid, kmin);
+                        if constexpr (CL > 1) st_others<CL>(wMinP + rank * NW + wid, kmin, rank);
                     }
                     csync<CL>();
 
@@ -573,9 +595,12 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                         long long km = wMin[0];
 #pragma unroll
                         for (int w = 1; w < NW; ++w) km = min_ll(km, wMin[w]);
-                        if constexpr (CL == 2) {
+                        if constexpr (CL > 1) {
+                            for (int j = 1; j < CL; ++j) {
+                                const long long *wp = wMinP + ((rank + j) % CL) * NW;
 #pragma unroll
-                            for (int w = 0; w < NW; ++w) km = min_ll(km, wMinP[w]);
+                                for (int w = 0; w < NW; ++w) km = min_ll(km, wp[w]);
+                            }
                         }
                         minA = order_key_inv(km);
                         mass = s_mass;
@@ -669,14 +694,14 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                                 D0[spos<P>(Nl - 1 + (P - k))] = np;   // Phi even about pi/2
                                 D1[spos<P>(Nl - 1 + (P - k))] = -nq;  // Pi odd about pi/2
                             }
-                            if constexpr (CL == 2) {
-                                if (hl && k >= P - 3) {      // -> left halo of rank 1
-                                    st_peer(D0 + spos<P>(-(P - k)), np);
-                                    st_peer(D1 + spos<P>(-(P - k)), nq);
+                            if constexpr (CL > 1) {
+                                if (hl && k >= P - 3) {      // -> left halo of rank+1
+                                    st_peer(D0 + spos<P>(-(P - k)), np, rank + 1);
+                                    st_peer(D1 + spos<P>(-(P - k)), nq, rank + 1);
                                 }
-                                if (hr && k < 3) {           // -> right halo of rank 0
-                                    st_peer(D0 + spos<P>(NL0 + k), np);
-                                    st_peer(D1 + spos<P>(NL0 + k), nq);
+                                if (hr && k < 3) {           // -> right halo of rank-1
+                                    st_peer(D0 + spos<P>(NLp + k), np, rank - 1);
+                                    st_peer(D1 + spos<P>(NLp + k), nq, rank - 1);
                                 }
                             }
                         }
@@ -693,7 +718,7 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
             }
         }
     finish:
-        csync<CL>();  // all global writes of this chunk are issued, by both CTAs
+        csync<CL>();  // all global writes of this chunk are issued, by every CTA of the cluster
         if (tid == 0 && rank == 0) {
             if (!skip) {
                 InstState *sp = a.st + b;
@@ -724,7 +749,7 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
                 }
             }
             s_leave = leave;
-            if constexpr (CL == 2) st_peer(&s_leave, leave);
+            if constexpr (CL > 1) st_others<CL>(&s_leave, leave, 0);
         }
         csync<CL>();
         if (s_leave) break;
@@ -732,7 +757,7 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
 }
 
 // per-instance results of an evolve call: t_reached, t_collapse, mass, status
-// (an instance whose chunk wait ran out in the last launch is reported as kTimeout)
+// (with ctl given, the instance whose chunk wait ran out in that launch is reported as kTimeout)
 __global__ void gather_kernel(const InstDesc *desc, const InstState *st, int B, double t_end,
                               int evolve_call, const QueueCtl *ctl, const int32_t *order,
                               double *t_reached, double *t_c, double *mass, int32_t *status)
@@ -744,7 +769,7 @@ __global__ void gather_kernel(const InstDesc *desc, const InstState *st, int B, 
     t_c[b] = S.t_c;
     mass[b] = S.mass;
     int32_t s = S.status;
-    const int err = ctl->error;
+    const int err = ctl ? ctl->error : 0;
     if (err > 0 && order[err - 1] == b && s == kRunning) s = kTimeout;
     if (evolve_call && s == kRunning) {
         const long long n_end = (long long)ceil(t_end / desc[b].dt - 1e-9);
