@@ -58,6 +58,7 @@ struct adscl_ctx {
     cudaGraphExec_t evo_exec = nullptr;    // cached executable graph of adscl_evolve's launches
     int num_sms = 0;
     int max_units[4] = {0, 0, 0, 0};   // co-resident CTAs / clusters of 2, 4, 8 of the evolve kernel
+    double t_prev = 0.0;               // t_end of the last evolve call since the initial data
 
     std::vector<InstDesc> h_desc;
     std::vector<int32_t> h_order;
@@ -234,6 +235,50 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
         i = j;
     }
     starts[ng] = nwork;
+    // SMs per group: in proportion to the group's estimated work (N times the RK4 steps to
+    // t_end, counted from the previous call's t_end), but no more than its instances can use,
+    // so that the groups finish together
+    int units_of[4];
+    {
+        double W[4] = {0, 0, 0, 0};
+        int cap[4], cls[4];
+        for (int g = 0; g < ng; ++g) {
+            cls[g] = cluster_of(ctx->N[order_host[starts[g]]]);
+            cap[g] = std::min(starts[g + 1] - starts[g], ctx->max_units[cl_index(cls[g])]) * cls[g];
+            for (int i = starts[g]; i < starts[g + 1]; ++i) {
+                const int b = order_host[i];
+                double steps = 1.0;
+                if (mode == kModeEvolve) {
+                    const double dtb = ctx->h_desc[b].dt;
+                    steps = std::max(1.0, std::ceil(t_end / dtb - 1e-9) - std::ceil(ctx->t_prev / dtb - 1e-9));
+                }
+                W[g] += (double)ctx->N[b] * steps;
+            }
+        }
+        double sms[4] = {0, 0, 0, 0};
+        bool sat[4] = {false, false, false, false};
+        double left = ctx->num_sms;
+        for (int it = 0; it < ng; ++it) {   // water-filling: saturated groups keep their cap
+            double wsum = 0.0;
+            for (int g = 0; g < ng; ++g)
+                if (!sat[g]) wsum += W[g];
+            if (wsum <= 0.0) break;
+            bool changed = false;
+            for (int g = 0; g < ng; ++g) {
+                if (sat[g]) continue;
+                sms[g] = left * W[g] / wsum;
+                if (sms[g] >= cap[g]) {
+                    sms[g] = cap[g];
+                    sat[g] = true;
+                    left -= cap[g];
+                    changed = true;
+                }
+            }
+            if (!changed) break;
+        }
+        for (int g = 0; g < ng; ++g)
+            units_of[g] = std::max(1, std::min(cap[g], (int)(sms[g] + 0.5)) / cls[g]);
+    }
     if (ng > 1) {
         for (int g = 0; g < ng - 1; ++g)
             if (!ctx->aux[g]) CK(cudaStreamCreateWithFlags(&ctx->aux[g], cudaStreamNonBlocking));
@@ -248,7 +293,7 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
         const int i = starts[g], j = starts[g + 1];
         const int cl = cluster_of(ctx->N[order_host[i]]);
         const cudaStream_t gs = (g == 0) ? sm : ctx->aux[g - 1];
-        const int units = std::min(j - i, ctx->max_units[cl_index(cl)]);
+        const int units = (ng > 1) ? units_of[g] : std::min(j - i, ctx->max_units[cl_index(cl)]);
         a.order = ctx->d_order + first + i;
         a.nwork = j - i;
         a.ctl = ctx->d_ctl + first + i;
@@ -727,6 +772,7 @@ adscl_status adscl_set_initial(adscl_ctx *ctx, const double *Phi, const double *
     CK(cudaMemcpyAsync(ctx->d_Phi, Phi, fb, kind, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_Pi, Pi, fb, kind, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_st, 0, ctx->B * sizeof(InstState), ctx->stream));
+    ctx->t_prev = 0.0;
     s = launch_evolve(ctx, kModeInit, 0.0, 0, ctx->h_order.data(), ctx->B, nullptr, nullptr, ctx->stream);
     if (s != ADSCL_OK) return s;
     if (!ptr_is_device) {
@@ -754,6 +800,7 @@ adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *a, int32_t K,
     CK(cudaGetLastError());
     ctx->launches += 1;
     CK(cudaMemsetAsync(ctx->d_st, 0, ctx->B * sizeof(InstState), ctx->stream));
+    ctx->t_prev = 0.0;
     s = launch_evolve(ctx, kModeInit, 0.0, 0, ctx->h_order.data(), ctx->B, nullptr, nullptr, ctx->stream);
     if (s != ADSCL_OK) return s;
     if (!ptr_is_device) {
@@ -796,6 +843,7 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
         return ADSCL_OK;
     });
     if (s != ADSCL_OK) return s;
+    ctx->t_prev = t_end;
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (t_reached) CK(cudaMemcpyAsync(t_reached, o, B * sizeof(double), kind, ctx->stream));
     if (t_collapse) CK(cudaMemcpyAsync(t_collapse, o + B, B * sizeof(double), kind, ctx->stream));
