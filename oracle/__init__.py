@@ -76,6 +76,14 @@ def lib():
         _lib.orc_spectrum_vjp.restype = None
         _lib.orc_grad.argtypes = [I, I, D, L, F, F, I, D, D]
         _lib.orc_grad.restype = None
+        _lib.orc_adot.argtypes = [I, D, D, D, D, D]
+        _lib.orc_adot.restype = None
+        _lib.orc_mass_simpson.argtypes = [I, D, D, D]
+        _lib.orc_mass_simpson.restype = F
+        _lib.orc_ea_step.argtypes = [I, I, F, F, D, D, D]
+        _lib.orc_ea_step.restype = None
+        _lib.orc_ea_evolve.argtypes = [I, I, I, F, L, L, F, F, F, D, D, D, D, D]
+        _lib.orc_ea_evolve.restype = I
     return _lib
 
 
@@ -151,6 +159,45 @@ def evolve(Phi, Pi, dt, nsteps, sigma=0.5, theta=2.0 ** -7, n0=0, minA_in=float(
         r.mass_hist, r.minA_hist = mh[: r.steps + 1], ah[: r.steps + 1]
     else:
         r.mass_hist = r.minA_hist = None
+    return r
+
+
+def adot(Phi, Pi, A, delta):
+    """A-dot of Eq. (eq:adot) on one slice."""
+    Phi, Pi, A, delta = map(_f64, (Phi, Pi, A, delta))
+    dA = np.empty(Phi.size)
+    lib().orc_adot(Phi.size, _p(Phi), _p(Pi), _p(A), _p(delta), _p(dA))
+    return dA
+
+
+def mass_simpson(Phi, Pi, A):
+    """The paper's mass integral by the composite Simpson rule on the nodes."""
+    Phi, Pi, A = map(_f64, (Phi, Pi, A))
+    return lib().orc_mass_simpson(Phi.size, _p(Phi), _p(Pi), _p(A))
+
+
+def ea_step(Phi, Pi, A, dt, order=3, sigma=0.0):
+    """One SSP Runge-Kutta step (order 2 or 3) of the evolved-A scheme."""
+    Phi, Pi, A = _f64(Phi).copy(), _f64(Pi).copy(), _f64(A).copy()
+    lib().orc_ea_step(Phi.size, order, dt, sigma, _p(Phi), _p(Pi), _p(A))
+    return Phi, Pi, A
+
+
+def ea_evolve(Phi, Pi, A, dt, nsteps, order=3, reint=0, sigma=0.5, theta=2.0 ** -7, n0=0,
+              minA_in=float("nan")):
+    """Evolve one instance with the evolved-A scheme (A given; re-integrated every `reint`
+    steps when reint > 0).  Returns an EvolveResult (mass = Simpson mass)."""
+    Phi, Pi, A = _f64(Phi).copy(), _f64(Pi).copy(), _f64(A).copy()
+    N = Phi.size
+    dl = np.empty(N)
+    out = np.empty(7)
+    lib().orc_ea_evolve(N, order, reint, dt, n0, nsteps, sigma, theta, minA_in, _p(Phi), _p(Pi),
+                        _p(A), _p(dl), _p(out))
+    r = EvolveResult()
+    r.Phi, r.Pi, r.A, r.delta = Phi, Pi, A, dl
+    r.t_reached, r.t_collapse, r.mass, r.minA = out[0], out[1], out[2], out[3]
+    r.steps, r.status, r.delta0 = int(out[4]), int(out[5]), out[6]
+    r.mass_hist = r.minA_hist = None
     return r
 
 

@@ -284,6 +284,148 @@ int orc_evolve(int N, double dt, long n0, long nsteps, double sigma, double thet
     return status;
 }
 
+/* ==================================================================================== */
+/* The paper's production variant (Sec. II): A is evolved with Eq. (eq:adot) instead of  */
+/* being integrated from Eq. (eq:aprime) at every stage, and re-integrated from          */
+/* Eq. (eq:aprime) only periodically; delta is still integrated at every stage; the time */
+/* integrator is a Runge-Kutta method of second or third order (the paper's runs use     */
+/* third order).  Readings: the strong-stability-preserving Runge-Kutta methods of       */
+/* Shu and Osher (order 2: Heun's method; order 3: the three-stage SSP scheme), no       */
+/* dissipation on A, A = 1 at both ends, and the mass by the composite Simpson rule of   */
+/* M = int tan^2 x A rho dx on the nodes.                                                 */
+/* ==================================================================================== */
+
+/* A-dot of Eq. (eq:adot): -2 sin x cos x A^2 e^{-delta} Phi Pi; zero at both ends */
+void orc_adot(int N, const double *Phi, const double *Pi, const double *A, const double *delta,
+              double *dA)
+{
+    const double h = grid_h(N);
+    int i;
+    dA[0] = 0.0;
+    dA[N - 1] = 0.0;
+    for (i = 1; i < N - 1; ++i) {
+        double x = i * h;
+        dA[i] = -2.0 * sin(x) * cos(x) * A[i] * A[i] * exp(-delta[i]) * Phi[i] * Pi[i];
+    }
+}
+
+/* M = int_0^{pi/2} tan^2 x A (Phi^2 + Pi^2) dx (Sec. II) by the composite Simpson rule on the
+ * nodes (N - 1 is even); the integrand vanishes at x = 0 and tends to 0 at x = pi/2 */
+double orc_mass_simpson(int N, const double *Phi, const double *Pi, const double *A)
+{
+    const double h = grid_h(N);
+    double sum = 0.0;
+    int i;
+    for (i = 1; i < N - 1; ++i) {
+        double x = i * h;
+        double w = (i % 2 == 1) ? 4.0 : 2.0;
+        sum += w * tan(x) * tan(x) * A[i] * (Phi[i] * Phi[i] + Pi[i] * Pi[i]);
+    }
+    return h / 3.0 * sum;
+}
+
+/* right-hand side L(Phi, Pi, A) of the evolved-A scheme: delta from the slice's Phi, Pi
+ * (Eq. (eq:delta)), Phi-dot and Pi-dot as in orc_rhs with the slice's own A, A-dot by
+ * Eq. (eq:adot) */
+static void ea_rhs(int N, double sigma, const double *Phi, const double *Pi, const double *A,
+                   double *dPhi, double *dPi, double *dA)
+{
+    size_t bytes = sizeof(double) * N;
+    double *Ac = (double *)malloc(bytes), *dl = (double *)malloc(bytes);
+    orc_constraints(N, Phi, Pi, Ac, dl, NULL, NULL);   /* only delta is used */
+    orc_rhs(N, sigma, Phi, Pi, A, dl, dPhi, dPi);
+    orc_adot(N, Phi, Pi, A, dl, dA);
+    free(Ac);
+    free(dl);
+}
+
+/*
+ * One step of the evolved-A scheme with the Shu-Osher SSP Runge-Kutta method of order 2 or 3:
+ *   order 2:  y1 = y + dt L(y);  y_new = y/2 + (y1 + dt L(y1))/2
+ *   order 3:  y1 = y + dt L(y);  y2 = 3y/4 + (y1 + dt L(y1))/4;  y_new = y/3 + 2(y2 + dt L(y2))/3
+ * y = (Phi, Pi, A), updated in place.
+ */
+void orc_ea_step(int N, int order, double dt, double sigma, double *Phi, double *Pi, double *A)
+{
+    size_t bytes = sizeof(double) * N;
+    double *sP = (double *)malloc(bytes), *sQ = (double *)malloc(bytes), *sA = (double *)malloc(bytes);
+    double *kP = (double *)malloc(bytes), *kQ = (double *)malloc(bytes), *kA = (double *)malloc(bytes);
+    /* y^{(s+1)} = a_s y_n + b_s (y^{(s)} + dt L(y^{(s)})) */
+    const double a2[2] = {0.0, 0.5}, b2[2] = {1.0, 0.5};
+    const double a3[3] = {0.0, 0.75, 1.0 / 3.0}, b3[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double *a = (order == 2) ? a2 : a3, *b = (order == 2) ? b2 : b3;
+    int st, i;
+    memcpy(sP, Phi, bytes);
+    memcpy(sQ, Pi, bytes);
+    memcpy(sA, A, bytes);
+    for (st = 0; st < order; ++st) {
+        ea_rhs(N, sigma, sP, sQ, sA, kP, kQ, kA);
+        for (i = 0; i < N; ++i) {
+            sP[i] = a[st] * Phi[i] + b[st] * (sP[i] + dt * kP[i]);
+            sQ[i] = a[st] * Pi[i] + b[st] * (sQ[i] + dt * kQ[i]);
+            sA[i] = a[st] * A[i] + b[st] * (sA[i] + dt * kA[i]);
+        }
+    }
+    memcpy(Phi, sP, bytes);
+    memcpy(Pi, sQ, bytes);
+    memcpy(A, sA, bytes);
+    free(sP); free(sQ); free(sA); free(kP); free(kQ); free(kA);
+}
+
+/*
+ * Evolve one instance with the evolved-A scheme from step index n0 by at most nsteps steps.
+ * The slice at step index n has A re-integrated from Eq. (eq:aprime) when reint > 0 and
+ * n % reint == 0 (A is given as state otherwise).  Diagnostics of a slice: min A of its A,
+ * the Simpson mass, delta(0).  Collapse and the outputs as in orc_evolve (out[2] = Simpson
+ * mass).  Phi, Pi, A are the state (updated in place); delta receives the last slice's delta.
+ */
+int orc_ea_evolve(int N, int order, int reint, double dt, long n0, long nsteps, double sigma,
+                  double theta, double minA_in, double *Phi, double *Pi, double *A, double *delta,
+                  double *out)
+{
+    size_t bytes = sizeof(double) * N;
+    double *Ac = (double *)malloc(bytes);
+    double mass, minA, t_c = INFINITY;
+    long n;
+    int status = ORC_DONE;
+    orc_constraints(N, Phi, Pi, Ac, delta, NULL, NULL);
+    if (reint > 0 && n0 % reint == 0) memcpy(A, Ac, bytes);
+    mass = orc_mass_simpson(N, Phi, Pi, A);
+    minA = isnan(minA_in) ? min_of(A, N) : minA_in;
+    for (n = 0; n < nsteps; ++n) {
+        double minA_new;
+        orc_ea_step(N, order, dt, sigma, Phi, Pi, A);
+        orc_constraints(N, Phi, Pi, Ac, delta, NULL, NULL);
+        if (reint > 0 && (n0 + n + 1) % reint == 0) memcpy(A, Ac, bytes);
+        mass = orc_mass_simpson(N, Phi, Pi, A);
+        minA_new = min_of(A, N);
+        if (!isfinite(mass) || !isfinite(delta[0]) || !isfinite(minA_new)) {
+            status = ORC_NONFINITE;
+            minA = minA_new;
+            ++n;
+            break;
+        }
+        if (minA_new < theta) {
+            double tn = (double)(n0 + n) * dt;
+            t_c = tn + dt * (minA - theta) / (minA - minA_new);
+            status = ORC_COLLAPSED;
+            minA = minA_new;
+            ++n;
+            break;
+        }
+        minA = minA_new;
+    }
+    out[0] = (double)(n0 + n) * dt;
+    out[1] = t_c;
+    out[2] = mass;
+    out[3] = minA;
+    out[4] = (double)n;
+    out[5] = (double)status;
+    out[6] = delta[0];
+    free(Ac);
+    return status;
+}
+
 /* ------------------------------------------------------------------ AdS eigenbasis */
 
 /* Jacobi polynomial P_n^{(a,b)}(y) by the standard three-term recurrence in n */
