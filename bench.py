@@ -44,6 +44,15 @@ SIGMA_KO = 0.5
 # (17, table-driven exp), fluxes 24.75; RHS stencils with dissipation 31; RK4 update 7.
 # The parallel-scan overheads (per-thread aggregates, warp shuffles, ~7 flops) are not counted.
 FLOPS_PER_POINT_SUBSTEP = 107.75
+# The same tally for the evolved-A schemes (A from Eq. (eq:adot), SSP Runge-Kutta), per stage:
+# delta cell data 20, delta scan 1, fused A e^{-delta} 17, fluxes 3, A-dot 3 and the A update
+# (SSP-RK3: 4 on average over the stages), slice mass 2 (once per step), RHS 31, Phi/Pi update
+# (SSP-RK3: 8 on average); the re-integration of A every 64 steps adds < 0.2 and is not counted.
+SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A re-integration)
+    "rk4": (0, 4, FLOPS_PER_POINT_SUBSTEP, 0),
+    "evolved_a_rk3": (1, 3, 89.0, 64),
+    "evolved_a_rk2": (2, 2, 88.5, 64),
+}
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one timed evolve_kernel launch of the amplitude scan, from an ncu
 # capture of this script (profiles/evolve_kernel_amp_scan.md); reported only while the kernel
@@ -182,12 +191,13 @@ def workload_insts(name, rank):
     raise ValueError(name)
 
 
-def side_rate(insts, stream, local, rk_steps, flush):
-    """Point-substeps/s of one persistent launch of rk_steps RK4 steps on another batch."""
+def side_rate(insts, stream, local, rk_steps, flush, substeps=4, **kw):
+    """Point-substeps/s of one persistent launch of rk_steps time steps on another batch
+    (substeps: Runge-Kutta stages per step of the scheme selected by kw)."""
     import torch
     from paper_1706_07413_b300 import adscl
     sol = adscl.Solver([it.N for it in insts], ko_sigma=SIGMA_KO, collapse_threshold=THETA,
-                       device=local, stream=stream.cuda_stream)
+                       device=local, stream=stream.cuda_stream, **kw)
     batch_fields(insts, sol)
     dt, _ = sol.clock()
     T = rk_steps * float(dt.max())
@@ -202,7 +212,7 @@ def side_rate(insts, stream, local, rk_steps, flush):
         e1.record(stream)
     torch.cuda.synchronize()
     _, s1 = sol.clock()
-    work = float(np.sum((s1 - s0) * sol.N.astype(np.float64) * 4.0))
+    work = float(np.sum((s1 - s0) * sol.N.astype(np.float64) * substeps))
     sol.close()
     return work / (e0.elapsed_time(e1) / 1e3)
 
@@ -252,6 +262,8 @@ def main():
     ap.add_argument("--no-others", action="store_true")
     ap.add_argument("--workload", default="amp_scan", choices=["amp_scan", "large", "uneven"],
                     help="batch to time (the metric's workload is amp_scan)")
+    ap.add_argument("--scheme", default="rk4", choices=sorted(SCHEMES),
+                    help="time-stepping scheme (the metric's scheme is rk4)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -271,14 +283,16 @@ def main():
     insts, wl_desc = workload_insts(args.workload, rank)
     B = len(insts)
     N = insts[0].N
-    amp = args.workload == "amp_scan"
+    amp = args.workload == "amp_scan" and args.scheme == "rk4"
     Pi0 = W.packed([W.gaussian_pi(N, it.eps, it.sigma) for it in insts]) if amp else None
     Phi0 = np.zeros_like(Pi0) if amp else None
 
     tflops_peak = adscl.probe_fp64(local, stream.cuda_stream)
 
+    scheme_id, stages, flops_pps, reint = SCHEMES[args.scheme]
     sol = adscl.Solver([it.N for it in insts], ko_sigma=SIGMA_KO, collapse_threshold=THETA,
-                       device=local, stream=stream.cuda_stream)
+                       device=local, stream=stream.cuda_stream, scheme=scheme_id,
+                       a_reint_every=reint)
     batch_fields(insts, sol)
     dt, _ = sol.clock()
     dstep = STEP_RK * float(dt.max())
@@ -315,7 +329,7 @@ def main():
     _, step1 = sol.clock()
     ms = [a.elapsed_time(b) for a, b in evs]
     dev_s = sum(ms) / 1e3
-    work = float(np.sum((step1 - step0) * sol.N.astype(np.float64) * 4.0))
+    work = float(np.sum((step1 - step0) * sol.N.astype(np.float64) * stages))
     tr, tc, m, st = sol.evolve(t)   # (already there: reads statuses only)
     collapsed = int(np.sum(st == adscl.COLLAPSED))
 
@@ -330,14 +344,14 @@ def main():
     value = work_all / dev_s
 
     # roofline of the evolution kernel (it is >99% of each timed launch)
-    achieved_tflops = (work * FLOPS_PER_POINT_SUBSTEP) / dev_s / 1e12
+    achieved_tflops = (work * flops_pps) / dev_s / 1e12
     traffic = None
-    if amp and args.steps > 0 and kernel_digest() == TRAFFIC["kernel_sha256"]:
+    if amp and args.scheme == "rk4" and kernel_digest() == TRAFFIC["kernel_sha256"]:
         traffic = TRAFFIC["dram_bytes_per_launch"]
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": tflops_peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / tflops_peak, "traffic": traffic,
                 "peak_source": "measured FP64 FMA-chain probe on this GPU (FMA = 2 flops)",
-                "flops_per_point_substep": FLOPS_PER_POINT_SUBSTEP}
+                "flops_per_point_substep": flops_pps}
 
     # the other two batch shapes, one launch of 128 RK4 steps each (default workload only)
     others = None
@@ -347,6 +361,16 @@ def main():
             oi, od = workload_insts(name, 0)
             others[name] = {"value": side_rate(oi, stream, local, 128, flush), "unit": UNIT,
                             "workload": od, "rk_steps": 128}
+        # the paper's production scheme on the amplitude scan: A evolved with Eq. (eq:adot),
+        # re-integrated every 64 steps, SSP-RK3 (3 substeps per step)
+        oi, od = workload_insts("amp_scan", 0)
+        v = side_rate(oi, stream, local, 128, flush, substeps=3, scheme=adscl.SCHEME_EVOLVED_A_RK3,
+                      a_reint_every=64)
+        others["amp_scan_evolved_A_rk3"] = {
+            "value": v, "unit": UNIT, "rk_steps": 128,
+            "workload": od + "; evolved-A scheme, SSP-RK3, A re-integrated every 64 steps",
+            "rk_steps_per_s": v / (3.0 * N_DEFAULT * B_DEFAULT),
+            "rk4_steps_per_s_same_batch": value / (4.0 * N_DEFAULT * B_DEFAULT)}
 
     # one instance per launch, same workload, for the batched-vs-one-per-launch comparison
     opl = None
@@ -470,6 +494,7 @@ def main():
             "config": {"workload": wl_desc,
                        "step": f"one persistent launch = {STEP_RK} RK4 steps of every running "
                                "instance",
+                       "scheme": args.scheme,
                        "window_t": [round(args.warmup * dstep, 6),
                                     round((args.warmup + args.steps) * dstep, 6)],
                        "collapsed_in_window": collapsed,

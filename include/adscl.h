@@ -33,6 +33,9 @@ extern "C" {
 
 typedef struct adscl_ctx adscl_ctx; /* opaque, owned by the library */
 
+/* time-stepping schemes (adscl_config.scheme) */
+enum { ADSCL_SCHEME_RK4 = 0, ADSCL_SCHEME_EVOLVED_A_RK3 = 1, ADSCL_SCHEME_EVOLVED_A_RK2 = 2 };
+
 typedef enum {
     ADSCL_OK = 0,
     ADSCL_EINVAL = 1,       /* bad argument or configuration; nothing was launched */
@@ -74,6 +77,13 @@ typedef struct {
     int32_t direct_launch;       /* 0: adscl_evolve replays a cached CUDA graph of its launches
                                     (recaptured each call on a private stream, updated in
                                     place); 1: it issues the launches one by one */
+    int32_t scheme;              /* ADSCL_SCHEME_*: 0 = classic RK4 with A integrated from
+                                    Eq. (eq:aprime) at every stage (default); 1 / 2 = the
+                                    paper's production variant (Sec. II): A evolved with
+                                    Eq. (eq:adot), SSP Runge-Kutta of order 3 / 2; N <= 4097 */
+    int32_t a_reint_every;       /* schemes 1, 2: re-integrate A from Eq. (eq:aprime) on slices
+                                    whose step index is a multiple of this (0: never; the
+                                    initial slice always takes the constraint solution) */
     void *stream;                /* cudaStream_t for all work; NULL = the legacy default stream */
 } adscl_config;
 
@@ -102,8 +112,9 @@ adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *a, int32_t K,
 /* Evolve every RUNNING instance until t >= t_end (its step count n with n dt >= t_end - 1e-9 dt)
  * or until it collapses (min A < theta; Sec. II) or turns non-finite.  Outputs, each of
  * length B (any may be NULL): t_reached (time of the last slice), t_collapse (linear
- * interpolation of min A across theta, +inf if none), mass (M = m(pi/2) of the last slice,
- * the paper's mass), inst_status (adscl_inst_status).
+ * interpolation of min A across theta, +inf if none), mass (the paper's mass M = int tan^2 x A
+ * rho dx of the last slice: m(pi/2) of the mass function under ADSCL_SCHEME_RK4, the composite
+ * Simpson rule on the nodes under the evolved-A schemes), inst_status (adscl_inst_status).
  * The launches (queue set-up, the persistent kernels, the gather of the outputs) run as one
  * CUDA graph launch on the context's stream unless cfg.direct_launch is set.  If the caller is
  * capturing the context's stream, they are issued directly so that the caller's graph records

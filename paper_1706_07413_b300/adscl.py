@@ -19,6 +19,7 @@ ADSCL_OK, ADSCL_EINVAL, ADSCL_ENOMEM, ADSCL_ECUDA, ADSCL_ETIMEOUT, ADSCL_ENONFIN
     ADSCL_EUNSUPPORTED, ADSCL_ECAPACITY = range(8)
 RUNNING, DONE, COLLAPSED, NONFINITE, TIMEOUT = range(5)
 PREC_FP64, PREC_BF16X3, PREC_TF32X3 = range(3)
+SCHEME_RK4, SCHEME_EVOLVED_A_RK3, SCHEME_EVOLVED_A_RK2 = range(3)
 
 STATUS_NAMES = {0: "ADSCL_OK", 1: "ADSCL_EINVAL", 2: "ADSCL_ENOMEM", 3: "ADSCL_ECUDA",
                 4: "ADSCL_ETIMEOUT", 5: "ADSCL_ENONFINITE", 6: "ADSCL_EUNSUPPORTED",
@@ -40,6 +41,8 @@ class adscl_config(ctypes.Structure):
                 ("one_per_launch", ctypes.c_int32),
                 ("chunk_steps", ctypes.c_int32),
                 ("direct_launch", ctypes.c_int32),
+                ("scheme", ctypes.c_int32),
+                ("a_reint_every", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -148,7 +151,8 @@ class Solver:
 
     def __init__(self, N, cfl=0.5, ko_sigma=0.5, collapse_threshold=2.0 ** -7, out_dt=1.0,
                  spec_J=64, ckpt_every=256, device=0, one_per_launch=False, stream=None,
-                 max_device_iters=0, chunk_steps=0, direct_launch=False):
+                 max_device_iters=0, chunk_steps=0, direct_launch=False, scheme=0,
+                 a_reint_every=0):
         self.lib = load()
         self.N = np.ascontiguousarray(np.asarray(N, dtype=np.int32).ravel())
         self.B = int(self.N.size)
@@ -167,6 +171,8 @@ class Solver:
         cfg.one_per_launch = 1 if one_per_launch else 0
         cfg.chunk_steps = chunk_steps
         cfg.direct_launch = 1 if direct_launch else 0
+        cfg.scheme = scheme
+        cfg.a_reint_every = a_reint_every
         cfg.stream = stream
         h = ctypes.c_void_p()
         st = self.lib.adscl_create(ctypes.byref(cfg), ctypes.byref(h))

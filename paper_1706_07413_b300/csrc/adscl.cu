@@ -18,6 +18,7 @@
 #include "spectrum.cuh"
 #include "spectrum_tc.cuh"
 #include "adjoint.cuh"
+#include "evolve_ea.cuh"
 
 using namespace adscl;
 
@@ -59,6 +60,10 @@ struct adscl_ctx {
     int num_sms = 0;
     int max_units[4] = {0, 0, 0, 0};   // co-resident CTAs / clusters of 2, 4, 8 of the evolve kernel
     double t_prev = 0.0;               // t_end of the last evolve call since the initial data
+    int scheme = 0, reint = 0;         // ADSCL_SCHEME_*, A re-integration interval (evolved A)
+    double *d_A = nullptr;             // packed evolved A (evolved-A schemes)
+    double *d_ea_block = nullptr;      // K2, wsim per grid size (evolved-A schemes)
+    EaGeo *d_eageo = nullptr;
 
     std::vector<InstDesc> h_desc;
     std::vector<int32_t> h_order;
@@ -223,6 +228,25 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
     if ((long long)nwork * rounds > 0x7ffffff0LL)
         return fail(ctx, ADSCL_EINVAL, "t_end too large for one launch (%lld rounds)", rounds);
     a.max_rounds = (int32_t)rounds;
+    if (ctx->scheme != ADSCL_SCHEME_RK4) {   // evolved A: one CTA per instance (N <= 4097)
+        EaArgs ea{};
+        ea.e = a;
+        ea.e.order = ctx->d_order + first;
+        ea.e.nwork = nwork;
+        ea.e.ctl = ctx->d_ctl + first;
+        ea.e.rounds = ctx->d_rounds + first;
+        ea.eg = ctx->d_eageo;
+        ea.A = ctx->d_A;
+        ea.order = (ctx->scheme == ADSCL_SCHEME_EVOLVED_A_RK2) ? 2 : 3;
+        ea.reint = ctx->reint;
+        const int units = std::min(nwork, ctx->max_units[0]);
+        queue_init_kernel<<<(nwork + 255) / 256, 256, 0, sm>>>(ea.e.ctl, ea.e.rounds, nwork, units);
+        CK(cudaGetLastError());
+        evolve_ea_kernel<kP, kNT><<<units, kNT, ctx->smem, sm>>>(ea, ctx->stride);
+        CK(cudaGetLastError());
+        ctx->launches += 2;
+        return ADSCL_OK;
+    }
     // the groups (at most four) run concurrently: the first on sm, the others on side streams
     // forked from sm and joined back into it; the block scheduler gives the SMs a group frees to
     // the CTAs of the others still waiting to start (no group waits on another)
@@ -597,7 +621,8 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     const double cad = cfg->out_dt == 0.0 ? 1.0 : cfg->out_dt;
     if (!(cfl > 0.0 && cfl <= 2.0) || !(cfg->ko_sigma >= 0.0 && cfg->ko_sigma < 10.0) ||
         !std::isfinite(cfg->collapse_threshold) || !(cad > 0.0) || cfg->spec_J < 0 ||
-        cfg->spec_J > 64 || cfg->ckpt_every < 0 || cfg->max_device_iters < 0)
+        cfg->spec_J > 64 || cfg->ckpt_every < 0 || cfg->max_device_iters < 0 ||
+        cfg->scheme < ADSCL_SCHEME_RK4 || cfg->scheme > ADSCL_SCHEME_EVOLVED_A_RK2 || cfg->a_reint_every < 0)
         return ADSCL_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
@@ -617,6 +642,8 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     ctx->one_per_launch = cfg->one_per_launch;
     ctx->chunk = cfg->chunk_steps > 0 ? cfg->chunk_steps : 16;
     ctx->direct_launch = cfg->direct_launch;
+    ctx->scheme = cfg->scheme;
+    ctx->reint = cfg->a_reint_every;
     ctx->stream = (cudaStream_t)cfg->stream;
     *out = ctx;
 
@@ -629,6 +656,9 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
         ctx->total += ctx->N[b];
         ctx->Nmax = std::max(ctx->Nmax, ctx->N[b]);
     }
+
+    if (ctx->scheme != ADSCL_SCHEME_RK4 && ctx->Nmax > kMaxPoints1)
+        return fail(ctx, ADSCL_EUNSUPPORTED, "the evolved-A schemes support N <= %d", kMaxPoints1);
 
     // geometry tables, one per distinct N
     std::map<int, int> geo_of;
@@ -663,6 +693,29 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     }
     CK(cudaMalloc(&ctx->d_geo, h_geo.size() * sizeof(GeoTab)));
     CK(cudaMemcpy(ctx->d_geo, h_geo.data(), h_geo.size() * sizeof(GeoTab), cudaMemcpyHostToDevice));
+    if (ctx->scheme != ADSCL_SCHEME_RK4) {
+        // node factors of the evolved-A schemes: K2 = -2 sin x cos x (A-dot of Eq. (eq:adot)) and
+        // the composite-Simpson mass weights (h/3) w_i tan^2 x_i (0 at both ends)
+        size_t tot = 0;
+        for (int n : geoN) tot += (size_t)2 * n;
+        CK(cudaMalloc(&ctx->d_ea_block, tot * sizeof(double)));
+        std::vector<EaGeo> h_eg;
+        size_t pos2 = 0;
+        for (int n : geoN) {
+            const double h = 0.5 * M_PI / (double)(n - 1);
+            std::vector<double> t((size_t)2 * n, 0.0);
+            for (int i = 1; i < n - 1; ++i) {
+                const double x = i * h, tn = std::tan(x);
+                t[i] = -2.0 * std::sin(x) * std::cos(x);
+                t[n + i] = h / 3.0 * ((i % 2) ? 4.0 : 2.0) * tn * tn;
+            }
+            CK(cudaMemcpy(ctx->d_ea_block + pos2, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+            h_eg.push_back(EaGeo{ctx->d_ea_block + pos2, ctx->d_ea_block + pos2 + n});
+            pos2 += t.size();
+        }
+        CK(cudaMalloc(&ctx->d_eageo, h_eg.size() * sizeof(EaGeo)));
+        CK(cudaMemcpy(ctx->d_eageo, h_eg.data(), h_eg.size() * sizeof(EaGeo), cudaMemcpyHostToDevice));
+    }
 
     ctx->h_desc.resize(ctx->B);
     for (int b = 0; b < ctx->B; ++b) {
@@ -699,6 +752,10 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     CK(cudaMemset(ctx->d_Pi, 0, fb));
     CK(cudaMalloc(&ctx->d_scratchA, fb));
     CK(cudaMalloc(&ctx->d_scratchD, fb));
+    if (ctx->scheme != ADSCL_SCHEME_RK4) {
+        CK(cudaMalloc(&ctx->d_A, fb));
+        CK(cudaMemset(ctx->d_A, 0, fb));
+    }
 
     // work order: largest grids first (longest work first in the queue)
     ctx->h_order.resize(ctx->B);
@@ -732,6 +789,8 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem_max));
     CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_max));
+    CK(cudaFuncSetAttribute(evolve_ea_kernel<kP, kNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem_max));
     // persistent grid sizes: one CTA per SM, and as many clusters as can be co-resident
     ctx->max_units[0] = ctx->num_sms;
@@ -945,6 +1004,8 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     if (s != ADSCL_OK) return s;
     if (!a || K < 1 || K > kMaxModes || !(T >= 0.0) || !std::isfinite(T))
         return fail(ctx, ADSCL_EINVAL, "bad grad arguments");
+    if (ctx->scheme != ADSCL_SCHEME_RK4)
+        return fail(ctx, ADSCL_EUNSUPPORTED, "grad differentiates the classic RK4 scheme only");
     for (int n : ctx->N)
         if ((n - 1) / kAP > kANT) return fail(ctx, ADSCL_EUNSUPPORTED, "grad supports N <= %d", kAP * kANT + 1);
     const int B = ctx->B, Jm = ctx->spec_J, seg = ctx->ckpt;
@@ -1130,7 +1191,8 @@ void adscl_destroy(adscl_ctx *ctx)
                     ctx->d_eig_block, ctx->d_eig, ctx->d_modes, ctx->d_E, ctx->d_tc_rowoff,
                     ctx->d_tc_rowinst, ctx->d_tc_modeoff, ctx->d_tc_ops, ctx->d_tc_D,
                     ctx->d_tc_tasks, ctx->d_tc_err, ctx->d_lam, ctx->d_adj_scr, ctx->d_adj_stage,
-                    ctx->d_ck, ctx->d_adj_small, ctx->d_adj_queue};
+                    ctx->d_ck, ctx->d_adj_small, ctx->d_adj_queue, ctx->d_A, ctx->d_ea_block,
+                    ctx->d_eageo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ctx->evo_exec) cudaGraphExecDestroy(ctx->evo_exec);

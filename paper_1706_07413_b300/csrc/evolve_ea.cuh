@@ -1,0 +1,498 @@
+// evolve_ea.cuh -- persistent FP64 kernel of the paper's production variant of the scheme
+// (arXiv:1706.07413, Sec. II): A is evolved with Eq. (eq:adot) instead of being integrated from
+// Eq. (eq:aprime) at every stage, and re-integrated from Eq. (eq:aprime) only every `reint`
+// steps; delta is integrated from Eq. (eq:delta) at every stage; time stepping by the
+// strong-stability-preserving Runge-Kutta methods of Shu and Osher of order 2 or 3,
+//   y^{(s+1)} = a_s y_n + b_s (y^{(s)} + dt L(y^{(s)})),
+//   order 2: (a, b) = (0, 1), (1/2, 1/2);  order 3: (0, 1), (3/4, 1/4), (1/3, 2/3).
+//
+// One CTA per instance (N <= P * NT + 1), the layout and the ticket queue of evolve_kernel.
+// Per stage:
+//   1. cell data: the Simpson increments of delta (and, at a re-integration slice, the affine
+//      maps of the mass function, as in evolve_kernel);
+//   2. block suffix scan of delta (and the affine prefix scan at a re-integration slice);
+//   3. F = A e^{-delta} with the stage's A, fluxes f = F Pi, u = tan^2 x F Phi, and
+//      A-dot = -2 sin x cos x A F Phi Pi pointwise, which updates A at once (A has no spatial
+//      derivative, so its stage value lives in an L2-resident global buffer, not in shared
+//      memory);
+//   4. Phi-dot, Pi-dot with dissipation as in evolve_kernel, Shu-Osher update.
+// The state is (Phi, Pi, A) in global memory; the slice's diagnostics are min A, the mass
+// M = int tan^2 x A rho dx by the composite Simpson rule on the nodes, and delta(0).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "evolve.cuh"
+
+namespace adscl {
+
+// per distinct grid size: the extra node factors of this scheme
+struct EaGeo {
+    const double *K2;    // -2 sin x cos x                          (0 at both ends)
+    const double *wsim;  // (h/3) w_i tan^2 x_i, w = Simpson weights (0 at both ends)
+};
+
+struct EaArgs {
+    EvolveArgs e;        // e.aPhi: stage A buffer (packed like the fields); e.aPi unused
+    const EaGeo *eg;
+    double *A;           // packed evolved A (state)
+    int32_t order;       // 2 or 3
+    int32_t reint;       // re-integrate A from Eq. (eq:aprime) at slices n % reint == 0 (0: never)
+};
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
+{
+    static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
+    constexpr int NW = NT / 32;
+    constexpr unsigned FULL = 0xffffffffu;
+    const EvolveArgs &a = ea.e;
+    extern __shared__ double smem[];
+    double *bufA0 = smem, *bufA1 = smem + stride;                   // stage Phi, Pi
+    double *bufB0 = smem + 2 * stride, *bufB1 = smem + 3 * stride;  // next stage Phi, Pi
+    double *sF = smem + 4 * stride, *sU = smem + 5 * stride;        // alpha/beta, then f/u
+    __shared__ double s_tab[kExpTableSize];
+    __shared__ double wAl[NW], wBe[NW], wDe[NW], cM[NW], cD[NW], wMs[NW];
+    __shared__ long long wMin[NW];
+    __shared__ double s_d0;
+    __shared__ int s_cmd, s_q, s_r, s_leave;
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < kExpTableSize; i += NT) s_tab[i] = a.exptab[i];
+
+    for (;;) {
+        // ------------------------------------------------------------ take a ticket
+        if (tid == 0) {
+            int cmd = 0, q = 0, r = 0;
+            for (;;) {
+                if (ld_relaxed(&a.ctl->unfinished) == 0 || ld_relaxed(&a.ctl->error) != 0) break;
+                const int t = atomicAdd(&a.ctl->ticket, 1);
+                if (t >= a.nwork * a.max_rounds) break;
+                r = t / a.nwork;
+                q = t - r * a.nwork;
+                int rd = ld_acquire(a.rounds + q);
+                long long spin = 0;
+                while (rd < r) {
+                    if (++spin > a.max_spin) break;
+                    __nanosleep(256);
+                    rd = ld_acquire(a.rounds + q);
+                }
+                if (rd == kFinished) continue;
+                if (rd < r) {
+                    atomicCAS(&a.ctl->error, 0, q + 1);
+                    break;
+                }
+                cmd = 1;
+                break;
+            }
+            s_cmd = cmd;
+            s_q = q;
+            s_r = r;
+        }
+        __syncthreads();
+        if (s_cmd == 0) break;
+        const int q = s_q, rnd = s_r;
+        const int b = a.order[q];
+        const InstDesc d = a.desc[b];
+        const InstState *sp = a.st + b;
+        InstState S;
+        S.step = __ldcg(&sp->step);
+        S.t_c = __ldcg(&sp->t_c);
+        S.minA = __ldcg(&sp->minA);
+        S.mass = __ldcg(&sp->mass);
+        S.delta0 = __ldcg(&sp->delta0);
+        S.status = __ldcg(&sp->status);
+
+        const double dt = d.dt;
+        long long n_end = S.step, n_target = S.step;
+        if (a.mode == kModeEvolve) {
+            n_end = (long long)ceil(a.t_end / dt - 1e-9);
+            n_target = min(n_end, S.step + (long long)a.chunk);
+        }
+        const int N = d.N;
+        const int Tn = (N - 1) / P;
+        const bool act = tid < Tn;
+        const bool tfirst = tid == 0;
+        const bool last = tid == Tn - 1;
+        const int i0 = tid * P;
+        const int tb = (P + 1) * tid;
+        const GeoTab g = a.geo[d.geo];
+        const EaGeo eg = ea.eg[d.geo];
+        double *uPhi = a.Phi + d.off, *uPi = a.Pi + d.off, *uA = ea.A + d.off;
+        double *sA = a.aPhi + d.off;   // stage A
+        const bool skip = (a.mode == kModeEvolve) && (S.status != kRunning || S.step >= n_target);
+        const int R = ea.order;
+
+        long long step = S.step;
+        double minA_prev = S.minA, minA = S.minA, mass = S.mass, d0 = S.delta0, t_c = S.t_c;
+        int32_t status = S.status;
+
+        if (!skip) {
+            if (act) {
+                double p[P], qv[P];
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    p[k] = __ldcg(uPhi + i0 + k);
+                    qv[k] = __ldcg(uPi + i0 + k);
+                }
+                if (tfirst) p[0] = 0.0;
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    bufA0[tb + soff<P>(k)] = p[k];
+                    bufA1[tb + soff<P>(k)] = qv[k];
+                }
+                if (tfirst) {
+#pragma unroll
+                    for (int j = 1; j <= 3; ++j) {
+                        bufA0[spos<P>(-j)] = -p[j];
+                        bufA1[spos<P>(-j)] = qv[j];
+                    }
+                    if (a.mode == kModeInit) uPhi[0] = 0.0;
+                }
+                if (last) {
+                    bufA0[spos<P>(N - 1)] = 0.0;
+                    bufA1[spos<P>(N - 1)] = 0.0;
+#pragma unroll
+                    for (int j = 1; j <= 3; ++j) {
+                        bufA0[spos<P>(N - 1 + j)] = p[P - j];
+                        bufA1[spos<P>(N - 1 + j)] = -qv[P - j];
+                    }
+                    if (a.mode == kModeInit) {
+                        uPhi[N - 1] = 0.0;
+                        uPi[N - 1] = 0.0;
+                        uA[N - 1] = 1.0;
+                    }
+                }
+            }
+            __syncthreads();
+
+            double *S0 = bufA0, *S1 = bufA1, *D0 = bufB0, *D1 = bufB1;
+            bool first = true;
+            for (;;) {
+#pragma unroll 1
+                for (int s = 0; s < R; ++s) {
+                    // the initial slice always takes A from the constraint
+                    const bool reint = (s == 0) && (a.mode == kModeInit ||
+                                                    (ea.reint > 0 && step % ea.reint == 0));
+                    const double wa = (s == 0) ? 0.0 : (R == 2 ? 0.5 : (s == 1 ? 0.75 : 1.0 / 3.0));
+                    const double wb = (s == 0) ? 1.0 : (R == 2 ? 0.5 : (s == 1 ? 0.25 : 2.0 / 3.0));
+                    // ================= delta (and, at a re-integration slice, m) =================
+                    double De[P];
+                    double aT = 1.0, bT = 0.0, SD = 0.0;
+                    if (act) {
+                        const double *Sp = S0 + tb, *Sq = S1 + tb;
+                        double pm1 = Sp[soff<P>(-1)], p0 = Sp[soff<P>(0)], p1 = Sp[soff<P>(1)];
+                        double qm1 = Sq[soff<P>(-1)], q0 = Sq[soff<P>(0)], q1 = Sq[soff<P>(1)];
+                        const double rho0 = fma(p0, p0, q0 * q0);
+                        double qn0 = __ldg(g.ws + i0) * rho0, rn0 = __ldg(g.wt + i0) * rho0;
+#pragma unroll
+                        for (int k = 0; k < P; ++k) {
+                            const int c = i0 + k;
+                            const double p2 = Sp[soff<P>(k + 2)], q2 = Sq[soff<P>(k + 2)];
+                            const double rho1 = fma(p1, p1, q1 * q1);
+                            const double qn1 = __ldg(g.ws + c + 1) * rho1;
+                            const double p16 = fma(9.0, p0 + p1, -(pm1 + p2));
+                            const double q16 = fma(9.0, q0 + q1, -(qm1 + q2));
+                            const double rm = fma(p16, p16, q16 * q16);
+                            const double qm3 = __ldg(g.wsm3 + c) * rm;
+                            const double s01 = qn0 + qn1;
+                            De[k] = fma(4.0 / 3.0, qm3, s01);
+                            SD = (k == 0) ? De[0] : SD + De[k];
+                            if (reint) {
+                                // the affine map of the mass function over the cell (evolve_kernel)
+                                const double rn1 = __ldg(g.wt + c + 1) * rho1;
+                                const double tm = __ldg(g.wtm + c) * rm;
+                                const double y2 = fma(-3.0, qn0, 1.0);
+                                const double y3 = fma(-qm3, y2, 1.0);
+                                const double ca = fma(-2.0, qn1, 2.0 / 3.0);
+                                const double al = fma(-qm3, fma(y3, ca, fma(-2.0, qn0, 2.0 / 3.0)), 1.0 - s01);
+                                const double w2 = fma(-qm3, rn0, tm);
+                                const double w3 = fma(-qm3, w2, tm);
+                                const double be = fma(w3, fma(-6.0, qn1, 2.0), fma(2.0, w2, rn0 + rn1));
+                                sF[tb + soff<P>(k)] = al;
+                                sU[tb + soff<P>(k)] = be;
+                                if (k == 0) {
+                                    aT = al;
+                                    bT = be;
+                                } else {
+                                    bT = fma(al, bT, be);
+                                    aT = aT * al;
+                                }
+                                rn0 = rn1;
+                            }
+                            pm1 = p0; p0 = p1; p1 = p2;
+                            qm1 = q0; q0 = q1; q1 = q2;
+                            qn0 = qn1;
+                        }
+                    }
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const double dn = __shfl_down_sync(FULL, SD, o);
+                        if (lane + o < 32) SD = SD + dn;
+                    }
+                    if (reint) {
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const double ap = __shfl_up_sync(FULL, aT, o);
+                            const double bp = __shfl_up_sync(FULL, bT, o);
+                            if (lane >= o) {
+                                bT = fma(aT, bp, bT);
+                                aT = aT * ap;
+                            }
+                        }
+                    }
+                    double aEx = __shfl_up_sync(FULL, aT, 1);
+                    double bEx = __shfl_up_sync(FULL, bT, 1);
+                    double dEx = __shfl_down_sync(FULL, SD, 1);
+                    if (lane == 0) { aEx = 1.0; bEx = 0.0; }
+                    if (lane == 31) dEx = 0.0;
+                    if (lane == 31) { wAl[wid] = aT; wBe[wid] = bT; }
+                    if (lane == 0) wDe[wid] = SD;
+                    __syncthreads();
+                    if (wid == 0) {
+                        double A_ = lane < NW ? wAl[lane] : 1.0;
+                        double B_ = lane < NW ? wBe[lane] : 0.0;
+                        double D_ = lane < NW ? wDe[lane] : 0.0;
+#pragma unroll
+                        for (int o = 1; o < NW; o <<= 1) {
+                            const double ap = __shfl_up_sync(FULL, A_, o);
+                            const double bp = __shfl_up_sync(FULL, B_, o);
+                            const double dn = __shfl_down_sync(FULL, D_, o);
+                            if (lane >= o) {
+                                B_ = fma(A_, bp, B_);
+                                A_ = A_ * ap;
+                            }
+                            if (lane + o < NW) D_ = D_ + dn;
+                        }
+                        double bw = __shfl_up_sync(FULL, B_, 1);
+                        double dw = __shfl_down_sync(FULL, D_, 1);
+                        if (lane == 0) bw = 0.0;
+                        if (lane + 1 >= NW) dw = 0.0;
+                        if (lane < NW) { cM[lane] = bw; cD[lane] = dw; }
+                    }
+                    __syncthreads();
+
+                    // ============ fluxes, A-dot and the A update; diagnostics of the slice ============
+                    long long kmin = 0x7FFFFFFFFFFFFFFFLL;
+                    double msum = 0.0;
+                    if (act) {
+                        const double *Sp = S0 + tb, *Sq = S1 + tb;
+                        double m = fma(aEx, cM[wid], bEx);
+                        double dc = dEx + cD[wid];
+#pragma unroll
+                        for (int k = P - 1; k >= 0; --k) {
+                            dc = dc + De[k];
+                            De[k] = dc;
+                        }
+                        double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0, fm1 = 0.0, fm2 = 0.0;
+#pragma unroll
+                        for (int k = 0; k < P; ++k) {
+                            const int i = i0 + k;
+                            const double ph = Sp[soff<P>(k)], pi = Sq[soff<P>(k)];
+                            double Ai;
+                            if (reint) {
+                                const double al = sF[tb + soff<P>(k)], be = sU[tb + soff<P>(k)];
+                                Ai = fma(-m, __ldg(g.K + i), 1.0);
+                                uA[i] = Ai;   // the slice's A is the constraint solution
+                                if (k < P - 1) m = fma(al, m, be);
+                            } else {
+                                Ai = (s == 0) ? __ldcg(uA + i) : __ldcg(sA + i);
+                            }
+                            const double Fi = a_exp_neg(Ai, De[k], s_tab);
+                            const double gi = Fi * ph;
+                            const double fi = Fi * pi;
+                            const double ui = __ldg(g.T + i) * gi;
+                            // A-dot = -2 sin x cos x A (A e^{-delta} Phi) Pi, and the stage update
+                            const double dA = __ldg(eg.K2 + i) * Ai * gi * pi;
+                            const double An = (s == 0) ? fma(dt, dA, Ai)
+                                                       : fma(wb, fma(dt, dA, Ai), wa * __ldcg(uA + i));
+                            if (s < R - 1) sA[i] = An;
+                            else uA[i] = An;
+                            if (s == 0) {
+                                kmin = min_ll(kmin, order_key(Ai));
+                                msum = fma(__ldg(eg.wsim + i) * Ai, fma(ph, ph, pi * pi), msum);
+                            }
+                            sF[tb + soff<P>(k)] = fi;
+                            sU[tb + soff<P>(k)] = ui;
+                            if (k == 1) g1 = gi;
+                            if (k == 2) g2 = gi;
+                            if (tfirst && (k == 1 || k == 2)) {
+                                sF[spos<P>(-k)] = fi;
+                                sU[spos<P>(-k)] = -ui;
+                            }
+                            if (k == P - 1) { fm1 = fi; um1 = ui; }
+                            if (k == P - 2) { fm2 = fi; um2 = ui; }
+                            if (a.outA) {
+                                a.outA[d.off + i] = Ai;
+                                a.outDelta[d.off + i] = De[k];
+                            }
+                        }
+                        if (tfirst) {
+                            s_d0 = De[0];
+                            sF[spos<P>(-3)] = fma(16.0, g1, -2.0 * g2);
+                        }
+                        if (last) {
+                            sF[spos<P>(N - 1)] = 0.0;
+                            sF[spos<P>(N)] = -fm1;
+                            sF[spos<P>(N + 1)] = -fm2;
+                            sU[spos<P>(N - 1)] = (4.0 * um1 - um2) * (1.0 / 3.0);
+                            sU[spos<P>(N)] = um1;
+                            sU[spos<P>(N + 1)] = um2;
+                            if (a.outA) {
+                                a.outA[d.off + N - 1] = 1.0;
+                                a.outDelta[d.off + N - 1] = 0.0;
+                            }
+                        }
+                    }
+                    if (s == 0) {
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            kmin = min_ll(kmin, __shfl_xor_sync(FULL, kmin, o));
+                            msum += __shfl_xor_sync(FULL, msum, o);
+                        }
+                        if (lane == 0) {
+                            wMin[wid] = kmin;
+                            wMs[wid] = msum;
+                        }
+                    }
+                    __syncthreads();
+
+                    if (s == 0) {
+                        long long km = wMin[0];
+                        double ms = wMs[0];
+#pragma unroll
+                        for (int w = 1; w < NW; ++w) {
+                            km = min_ll(km, wMin[w]);
+                            ms += wMs[w];
+                        }
+                        minA = order_key_inv(km);
+                        mass = ms;
+                        d0 = s_d0;
+                        const bool nonfin = !(is_finite_bits(mass) && is_finite_bits(d0) && is_finite_bits(minA));
+                        bool stop = false;
+                        if (a.mode != kModeEvolve) {
+                            if (a.mode == kModeInit) {
+                                status = nonfin ? kNonfinite : (minA < a.theta ? kCollapsed : kRunning);
+                                t_c = (status == kCollapsed) ? 0.0
+                                                             : __longlong_as_double(0x7FF0000000000000LL);
+                            }
+                            stop = true;
+                        } else if (!first) {
+                            if (nonfin) {
+                                status = kNonfinite;
+                                stop = true;
+                            } else if (minA < a.theta) {
+                                t_c = (double)(step - 1) * dt +
+                                      dt * (minA_prev - a.theta) / (minA_prev - minA);
+                                status = kCollapsed;
+                                stop = true;
+                            }
+                        }
+                        if (!stop && step >= n_target) stop = true;
+                        if (stop) goto finish;
+                        minA_prev = minA;
+                        first = false;
+                    }
+
+                    // ================= Phi-dot, Pi-dot and the Shu-Osher update =================
+                    if (act) {
+                        const double wbdc = wb * d.dtc, wbd = wb * dt;
+                        const double *Sp = S0 + tb, *Sq = S1 + tb;
+                        const double *f = sF + tb, *u = sU + tb;
+                        double *Dp = D0 + tb, *Dq = D1 + tb;
+#pragma unroll
+                        for (int k = 0; k < P; ++k) {
+                            const int i = i0 + k;
+                            const double Df = (f[soff<P>(k - 2)] - f[soff<P>(k + 2)]) +
+                                              8.0 * (f[soff<P>(k + 1)] - f[soff<P>(k - 1)]);
+                            const double Du = (u[soff<P>(k - 2)] - u[soff<P>(k + 2)]) +
+                                              8.0 * (u[soff<P>(k + 1)] - u[soff<P>(k - 1)]);
+                            const double kp = fma(-20.0, Sp[soff<P>(k)],
+                                fma(15.0, Sp[soff<P>(k - 1)] + Sp[soff<P>(k + 1)],
+                                fma(-6.0, Sp[soff<P>(k - 2)] + Sp[soff<P>(k + 2)],
+                                    Sp[soff<P>(k - 3)] + Sp[soff<P>(k + 3)])));
+                            const double kq = fma(-20.0, Sq[soff<P>(k)],
+                                fma(15.0, Sq[soff<P>(k - 1)] + Sq[soff<P>(k + 1)],
+                                fma(-6.0, Sq[soff<P>(k - 2)] + Sq[soff<P>(k + 2)],
+                                    Sq[soff<P>(k - 3)] + Sq[soff<P>(k + 3)])));
+                            double Xp = fma(d.rko, kp, Df);   // Phi-dot / c12
+                            double dQ = fma(__ldg(g.iT12 + i), Du, d.cko * kq);
+                            if (k == 0 && tfirst) {
+                                Xp = 0.0;
+                                dQ = fma(d.c3, sF[spos<P>(-3)], d.cko * kq);
+                            }
+                            double np, nq;
+                            if (s == 0) {
+                                np = fma(d.dtc, Xp, Sp[soff<P>(k)]);
+                                nq = fma(dt, dQ, Sq[soff<P>(k)]);
+                            } else {
+                                np = fma(wbdc, Xp, fma(wb, Sp[soff<P>(k)], wa * __ldcg(uPhi + i)));
+                                nq = fma(wbd, dQ, fma(wb, Sq[soff<P>(k)], wa * __ldcg(uPi + i)));
+                            }
+                            if (k == 0 && tfirst) np = 0.0;
+                            if (s == R - 1) {
+                                uPhi[i] = np;
+                                uPi[i] = nq;
+                            }
+                            Dp[soff<P>(k)] = np;
+                            Dq[soff<P>(k)] = nq;
+                            if (tfirst && k >= 1 && k <= 3) {
+                                D0[spos<P>(-k)] = -np;
+                                D1[spos<P>(-k)] = nq;
+                            }
+                            if (last && k >= P - 3) {
+                                D0[spos<P>(N - 1 + (P - k))] = np;
+                                D1[spos<P>(N - 1 + (P - k))] = -nq;
+                            }
+                        }
+                        if (last) {
+                            D0[spos<P>(N - 1)] = 0.0;
+                            D1[spos<P>(N - 1)] = 0.0;
+                        }
+                    }
+                    __syncthreads();
+                    double *t0 = S0, *t1 = S1;
+                    S0 = D0; S1 = D1; D0 = t0; D1 = t1;
+                }
+                ++step;
+            }
+        }
+    finish:
+        __syncthreads();
+        if (tid == 0) {
+            if (!skip) {
+                InstState *spw = a.st + b;
+                spw->step = step;
+                spw->t_c = t_c;
+                spw->minA = minA;
+                spw->mass = mass;
+                spw->delta0 = d0;
+                spw->status = status;
+            }
+            __threadfence();
+            const bool fin = (a.mode != kModeEvolve) || status != kRunning || step >= n_end;
+            if (fin) {
+                atomicExch(a.rounds + q, kFinished);
+                atomicSub(&a.ctl->unfinished, 1);
+            } else {
+                atomicExch(a.rounds + q, rnd + 1);
+            }
+            int leave = 0;
+            for (;;) {
+                const int act_n = ld_relaxed(&a.ctl->active);
+                const int unf = ld_relaxed(&a.ctl->unfinished);
+                if (unf >= act_n) break;
+                if (atomicCAS(&a.ctl->active, act_n, act_n - 1) == act_n) {
+                    leave = 1;
+                    break;
+                }
+            }
+            s_leave = leave;
+        }
+        __syncthreads();
+        if (s_leave) break;
+    }
+}
+
+}  // namespace adscl

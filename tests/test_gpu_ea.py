@@ -1,0 +1,91 @@
+"""GPU parity of the evolved-A schemes (the paper's production variant, Sec. II: A evolved with
+Eq. (eq:adot), periodically re-integrated from Eq. (eq:aprime), SSP Runge-Kutta of order 3 or
+2) against the oracle's evolved-A scheme, through the C ABI."""
+import numpy as np
+import pytest
+
+from paper_1706_07413_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ad():
+    from paper_1706_07413_b300 import adscl
+    adscl.load()
+    return adscl
+
+
+def _close(gpu, ref, rel):
+    scale = max(1.0, np.abs(ref).max())
+    return np.abs(gpu - ref).max() <= rel * scale
+
+
+@pytest.mark.parametrize("N,scheme,reint,steps", [(1025, 1, 0, 40), (4097, 1, 7, 30),
+                                                  (513, 2, 5, 40), (129, 1, 1, 25)])
+def test_evolution_matches_oracle(ad, orc, N, scheme, reint, steps):
+    order = 3 if scheme == 1 else 2
+    Phi, Pi = W.smooth_random(N, seed=N + reint, amp=2.5)
+    s = ad.Solver([N], scheme=scheme, a_reint_every=reint)
+    s.set_initial(Phi, Pi)
+    _, _, A0, _ = s.get_state(0)
+    Ac = orc.constraints(Phi, Pi)[0]
+    assert _close(A0, Ac, 1e-12)
+    dt, _ = s.clock()
+    tr, tc, m, st = s.evolve(steps * dt[0])
+    r = orc.ea_evolve(Phi, Pi, Ac, dt[0], steps, order=order, reint=reint, sigma=0.5)
+    gP, gQ, gA, gd = s.get_state(0)
+    assert _close(gP, r.Phi, 1e-11) and _close(gQ, r.Pi, 1e-11)
+    assert _close(gA, r.A, 1e-11) and _close(gd, r.delta, 1e-11)
+    assert abs(m[0] - r.mass) <= 1e-11 * max(1.0, r.mass)
+    assert st[0] == ad.DONE and tr[0] == pytest.approx(steps * dt[0], rel=0, abs=1e-12)
+
+
+def test_collapse_time_matches_oracle(ad, orc):
+    N = 513
+    Pi0 = W.gaussian_pi(N, 20.0, sigma=1.0 / 8)
+    z = np.zeros(N)
+    s = ad.Solver([N], scheme=1, a_reint_every=16, collapse_threshold=0.05)
+    s.set_initial(z, Pi0)
+    dt, _ = s.clock()
+    tr, tc, m, st = s.evolve(10.0)
+    r = orc.ea_evolve(z, Pi0, orc.constraints(z, Pi0)[0], dt[0], 4000, order=3, reint=16,
+                      theta=0.05)
+    assert st[0] == ad.COLLAPSED and r.status == orc.COLLAPSED
+    assert abs(tc[0] / r.t_collapse - 1) < 1e-9
+
+
+def test_batch_chunks_and_restarts_are_bit_identical(ad):
+    Ns = [4097, 1025, 129, 2049, 4097, 513]
+    fields = [W.smooth_random(n, seed=300 + i, amp=2.0) for i, n in enumerate(Ns)]
+    Phi, Pi = W.packed([f[0] for f in fields]), W.packed([f[1] for f in fields])
+    runs = []
+    for chunk, t_ends in ((3, (0.02,)), (64, (0.005, 0.013, 0.02))):
+        s = ad.Solver(Ns, scheme=1, a_reint_every=5, chunk_steps=chunk)
+        s.set_initial(Phi, Pi)
+        for t in t_ends:
+            out = s.evolve(t)
+        runs.append((out, [s.get_state(b) for b in range(len(Ns))]))
+        s.close()
+    for x, y in zip(runs[0][0], runs[1][0]):
+        assert np.array_equal(x, y)
+    for a, b in zip(runs[0][1], runs[1][1]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    for i, n in enumerate(Ns):   # batched = single instance
+        one = ad.Solver([n], scheme=1, a_reint_every=5)
+        one.set_initial(fields[i][0], fields[i][1])
+        one.evolve(0.02)
+        for x, y in zip(one.get_state(0), runs[0][1][i]):
+            assert np.array_equal(x, y)
+
+
+def test_unsupported_requests_fail_cleanly(ad):
+    with pytest.raises(ad.AdsclError) as e:
+        ad.Solver([8193], scheme=1)
+    assert e.value.status == ad.ADSCL_EUNSUPPORTED
+    s = ad.Solver([257] * 2, scheme=1)
+    s.set_initial_modes(np.full((2, 4), 0.01))
+    with pytest.raises(ad.AdsclError) as e:
+        s.grad(np.full((2, 4), 0.01), 0.1)
+    assert e.value.status == ad.ADSCL_EUNSUPPORTED
