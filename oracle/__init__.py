@@ -84,6 +84,8 @@ def lib():
         _lib.orc_ea_step.restype = None
         _lib.orc_ea_evolve.argtypes = [I, I, I, F, L, L, F, F, F, D, D, D, D, D]
         _lib.orc_ea_evolve.restype = I
+        _lib.orc_fixed_step.argtypes = [I, I, F, F, D, D]
+        _lib.orc_fixed_step.restype = None
     return _lib
 
 
@@ -199,6 +201,14 @@ def ea_evolve(Phi, Pi, A, dt, nsteps, order=3, reint=0, sigma=0.5, theta=2.0 ** 
     r.steps, r.status, r.delta0 = int(out[4]), int(out[5]), out[6]
     r.mass_hist = r.minA_hist = None
     return r
+
+
+def fixed_evolve(Phi, Pi, dt, nsteps, order=3, sigma=0.5):
+    """nsteps SSP Runge-Kutta steps of the fixed-metric case (A = 1, delta = 0)."""
+    Phi, Pi = _f64(Phi).copy(), _f64(Pi).copy()
+    for _ in range(nsteps):
+        lib().orc_fixed_step(Phi.size, order, dt, sigma, _p(Phi), _p(Pi))
+    return Phi, Pi
 
 
 def eigen_at(J, x):

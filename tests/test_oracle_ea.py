@@ -107,3 +107,22 @@ def test_evolved_scheme_collapses_like_the_constraint_scheme(orc):
     r4 = orc.evolve(z, Pi0, dt, 4000, theta=0.05)
     assert r3.status == orc.COLLAPSED and r4.status == orc.COLLAPSED
     assert abs(r3.t_collapse / r4.t_collapse - 1) < 1.5e-3
+
+
+@pytest.mark.parametrize("j", [0, 3])
+def test_fixed_metric_normal_mode_is_exact(orc, j):
+    """Fixed metric (A = 1, delta = 0; the paper's Table II case): Eqs. (eq:phi), (eq:pi) are
+    linear and Pi = cos(w t) e_j, Phi = sin(w t) e_j' / w, w = 3 + 2j, solves them exactly.  The
+    SSP-RK3 solution converges to it at third order (time error dominant)."""
+    errs = []
+    T = 1.0
+    for N in (129, 257, 513):
+        e, de = orc.eigen(N, j + 1)
+        w = 3.0 + 2.0 * j
+        n = 160 * (N - 1) // 128
+        P, Q = orc.fixed_evolve(np.zeros(N), e[j], T / n, n, order=3, sigma=0.5)
+        errs.append(max(np.abs(P - np.sin(w * T) * de[j] / w).max(),
+                        np.abs(Q - np.cos(w * T) * e[j]).max()))
+    for k in range(2):
+        assert 2.8 < math.log2(errs[k] / errs[k + 1]) < 3.6
+    assert errs[-1] < (1e-7 if j == 0 else 3e-5)
