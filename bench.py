@@ -54,10 +54,13 @@ SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A
     "evolved_a_rk2": (2, 2, 88.5, 64),
 }
 L2_FLUSH_BYTES = 512 << 20
+CPU_SAMPLE_STEPS = 800    # oracle sample of the cpu_baseline leg: ~10 s on 16 host threads
+REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
 # DRAM bytes (read + write) of one timed evolve_kernel launch of the amplitude scan, from an ncu
 # capture of this script (profiles/evolve_kernel_amp_scan.md); reported only while the kernel
 # source is the one the counters were taken on.
-TRAFFIC = {"kernel_sha256": None, "dram_bytes_per_launch": None}
+TRAFFIC = {"kernel_sha256": "8bf7461a8865258a2ac0b61bd9888b067a060b3c6953a770a8f6d2f9a31fb134",
+           "dram_bytes_per_launch": 17826560 + 205086464}
 
 
 def kernel_digest():
@@ -224,7 +227,7 @@ def run_reference(args):
         return
     threads = min(os.cpu_count() or 1, 16)
     insts = W.amp_scan()[: 2 * threads]
-    nsteps = 24
+    nsteps = REF_SAMPLE_STEPS
     for _ in range(args.warmup):
         oracle_rate(insts[:threads], 4, threads)
     rates, total_t, total_w = [], 0.0, 0
@@ -480,10 +483,10 @@ def main():
     if rank == 0 and ws == 1 and amp and not args.no_cpu_baseline:
         threads = min(os.cpu_count() or 1, 16)
         sample_insts = W.amp_scan()[: 2 * threads]
-        rate, el, _ = oracle_rate(sample_insts, 24, threads)
+        rate, el, _ = oracle_rate(sample_insts, CPU_SAMPLE_STEPS, threads)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{len(sample_insts)} of the 256 N=4097 pulses x 24 RK4 steps "
-                         f"({el:.1f} s wall)"}
+               "sample": f"{len(sample_insts)} of the 256 N=4097 pulses x {CPU_SAMPLE_STEPS} RK4 "
+                         f"steps ({el:.1f} s wall)"}
 
     if rank == 0:
         line = {

@@ -34,7 +34,8 @@ extern "C" {
 typedef struct adscl_ctx adscl_ctx; /* opaque, owned by the library */
 
 /* time-stepping schemes (adscl_config.scheme) */
-enum { ADSCL_SCHEME_RK4 = 0, ADSCL_SCHEME_EVOLVED_A_RK3 = 1, ADSCL_SCHEME_EVOLVED_A_RK2 = 2 };
+enum { ADSCL_SCHEME_RK4 = 0, ADSCL_SCHEME_EVOLVED_A_RK3 = 1, ADSCL_SCHEME_EVOLVED_A_RK2 = 2,
+       ADSCL_SCHEME_FIXED_METRIC_RK3 = 3 };
 
 typedef enum {
     ADSCL_OK = 0,
@@ -80,7 +81,9 @@ typedef struct {
     int32_t scheme;              /* ADSCL_SCHEME_*: 0 = classic RK4 with A integrated from
                                     Eq. (eq:aprime) at every stage (default); 1 / 2 = the
                                     paper's production variant (Sec. II): A evolved with
-                                    Eq. (eq:adot), SSP Runge-Kutta of order 3 / 2; N <= 4097 */
+                                    Eq. (eq:adot), SSP Runge-Kutta of order 3 / 2; 3 = A = 1 and
+                                    delta = 0 held fixed (the paper's Table II case, the linear
+                                    wave equation on AdS4), SSP-RK3; schemes 1-3: N <= 4097 */
     int32_t a_reint_every;       /* schemes 1, 2: re-integrate A from Eq. (eq:aprime) on slices
                                     whose step index is a multiple of this (0: never; the
                                     initial slice always takes the constraint solution) */

@@ -19,7 +19,7 @@ ADSCL_OK, ADSCL_EINVAL, ADSCL_ENOMEM, ADSCL_ECUDA, ADSCL_ETIMEOUT, ADSCL_ENONFIN
     ADSCL_EUNSUPPORTED, ADSCL_ECAPACITY = range(8)
 RUNNING, DONE, COLLAPSED, NONFINITE, TIMEOUT = range(5)
 PREC_FP64, PREC_BF16X3, PREC_TF32X3 = range(3)
-SCHEME_RK4, SCHEME_EVOLVED_A_RK3, SCHEME_EVOLVED_A_RK2 = range(3)
+SCHEME_RK4, SCHEME_EVOLVED_A_RK3, SCHEME_EVOLVED_A_RK2, SCHEME_FIXED_METRIC_RK3 = range(4)
 
 STATUS_NAMES = {0: "ADSCL_OK", 1: "ADSCL_EINVAL", 2: "ADSCL_ENOMEM", 3: "ADSCL_ECUDA",
                 4: "ADSCL_ETIMEOUT", 5: "ADSCL_ENONFINITE", 6: "ADSCL_EUNSUPPORTED",

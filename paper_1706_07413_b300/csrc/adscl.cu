@@ -242,7 +242,10 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
         const int units = std::min(nwork, ctx->max_units[0]);
         queue_init_kernel<<<(nwork + 255) / 256, 256, 0, sm>>>(ea.e.ctl, ea.e.rounds, nwork, units);
         CK(cudaGetLastError());
-        evolve_ea_kernel<kP, kNT><<<units, kNT, ctx->smem, sm>>>(ea, ctx->stride);
+        if (ctx->scheme == ADSCL_SCHEME_FIXED_METRIC_RK3)
+            evolve_ea_kernel<kP, kNT, true><<<units, kNT, ctx->smem, sm>>>(ea, ctx->stride);
+        else
+            evolve_ea_kernel<kP, kNT, false><<<units, kNT, ctx->smem, sm>>>(ea, ctx->stride);
         CK(cudaGetLastError());
         ctx->launches += 2;
         return ADSCL_OK;
@@ -622,7 +625,8 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     if (!(cfl > 0.0 && cfl <= 2.0) || !(cfg->ko_sigma >= 0.0 && cfg->ko_sigma < 10.0) ||
         !std::isfinite(cfg->collapse_threshold) || !(cad > 0.0) || cfg->spec_J < 0 ||
         cfg->spec_J > 64 || cfg->ckpt_every < 0 || cfg->max_device_iters < 0 ||
-        cfg->scheme < ADSCL_SCHEME_RK4 || cfg->scheme > ADSCL_SCHEME_EVOLVED_A_RK2 || cfg->a_reint_every < 0)
+        cfg->scheme < ADSCL_SCHEME_RK4 || cfg->scheme > ADSCL_SCHEME_FIXED_METRIC_RK3 ||
+        cfg->a_reint_every < 0)
         return ADSCL_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
@@ -658,7 +662,8 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     }
 
     if (ctx->scheme != ADSCL_SCHEME_RK4 && ctx->Nmax > kMaxPoints1)
-        return fail(ctx, ADSCL_EUNSUPPORTED, "the evolved-A schemes support N <= %d", kMaxPoints1);
+        return fail(ctx, ADSCL_EUNSUPPORTED, "the evolved-A and fixed-metric schemes support N <= %d",
+                    kMaxPoints1);
 
     // geometry tables, one per distinct N
     std::map<int, int> geo_of;
@@ -790,7 +795,9 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
                             (int)smem_max));
     CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem_max));
-    CK(cudaFuncSetAttribute(evolve_ea_kernel<kP, kNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CK(cudaFuncSetAttribute(evolve_ea_kernel<kP, kNT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_max));
+    CK(cudaFuncSetAttribute(evolve_ea_kernel<kP, kNT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem_max));
     // persistent grid sizes: one CTA per SM, and as many clusters as can be co-resident
     ctx->max_units[0] = ctx->num_sms;

@@ -89,3 +89,25 @@ def test_unsupported_requests_fail_cleanly(ad):
     with pytest.raises(ad.AdsclError) as e:
         s.grad(np.full((2, 4), 0.01), 0.1)
     assert e.value.status == ad.ADSCL_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("N,j", [(1025, 0), (2049, 5)])
+def test_fixed_metric_matches_oracle_and_exact_mode(ad, orc, N, j):
+    """Scheme 3 (A = 1, delta = 0; the paper's Table II case): a normal mode e_j, synthesised on
+    the device, evolves as Pi = cos(w t) e_j, Phi = sin(w t) e_j' / w."""
+    a = np.zeros((1, j + 1))
+    a[0, j] = 1.0
+    s = ad.Solver([N], scheme=ad.SCHEME_FIXED_METRIC_RK3)
+    s.set_initial_modes(a)
+    dt, _ = s.clock()
+    n = 200
+    tr, tc, m, st = s.evolve(n * dt[0])
+    gP, gQ, gA, gd = s.get_state(0)
+    e, de = orc.eigen(N, j + 1)
+    oP, oQ = orc.fixed_evolve(np.zeros(N), e[j], dt[0], n, order=3, sigma=0.5)
+    assert np.abs(gP - oP).max() < 1e-11 and np.abs(gQ - oQ).max() < 1e-11
+    w, T = 3.0 + 2.0 * j, n * dt[0]
+    err = max(np.abs(gP - np.sin(w * T) * de[j] / w).max(), np.abs(gQ - np.cos(w * T) * e[j]).max())
+    assert err < (1e-7 if j == 0 else 1e-5)
+    assert np.all(gA == 1.0) and np.all(gd == 0.0)
+    assert st[0] == ad.DONE
