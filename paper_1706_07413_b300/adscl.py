@@ -174,6 +174,7 @@ class Solver:
         cfg.scheme = scheme
         cfg.a_reint_every = a_reint_every
         cfg.stream = stream
+        self.stream = stream
         h = ctypes.c_void_p()
         st = self.lib.adscl_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != ADSCL_OK:
