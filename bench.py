@@ -220,6 +220,53 @@ def side_rate(insts, stream, local, rk_steps, flush, substeps=4, **kw):
     return work / (e0.elapsed_time(e1) / 1e3)
 
 
+def autotune_report(stream, local):
+    """Default kernel shape against the autotuned one on the two latency-bound cases: the single
+    pulse (one instance, N = 1025, eps = 40, sigma = 1/16) and a batch smaller than the SM count
+    (64 pulses at N = 4097); plus the single pulse run to t = 10 (or collapse) with the tuned
+    shape."""
+    import torch
+    from paper_1706_07413_b300 import adscl
+    out = {}
+    cases = (("single_N1025", W.single(), 400), ("batch64_N4097", W.amp_scan(B=64), 64))
+    for name, insts, steps in cases:
+        res = {}
+        for tuned in (False, True):
+            sol = adscl.Solver([it.N for it in insts], ko_sigma=SIGMA_KO, collapse_threshold=THETA,
+                               device=local, stream=stream.cuda_stream)
+            batch_fields(insts, sol)
+            shapes = sol.autotune(8) if tuned else sol.shapes()
+            dt, _ = sol.clock()
+            T = steps * float(dt.max())
+            sol.evolve(T / 8)
+            torch.cuda.synchronize()
+            _, s0 = sol.clock()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                sol.evolve(T / 8 + T)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            _, s1 = sol.clock()
+            ms = e0.elapsed_time(e1)
+            work = float(np.sum((s1 - s0) * sol.N.astype(np.float64) * 4.0))
+            res["tuned" if tuned else "default"] = {
+                "shape_P_NT_CL": list(shapes[insts[0].N]), "value": work / (ms / 1e3),
+                "unit": UNIT, "us_per_rk4_step": 1e3 * ms / max(1, int(np.max(s1 - s0)))}
+            if tuned and name == "single_N1025":
+                sol.set_initial(np.zeros(insts[0].N), W.gaussian_pi(insts[0].N, insts[0].eps,
+                                                                     insts[0].sigma))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                tr, tc, m, st = sol.evolve(10.0)
+                res["to_t10"] = {"wall_s": time.perf_counter() - t0, "t_reached": float(tr[0]),
+                                 "t_collapse": float(tc[0]), "rk4_steps": int(sol.clock()[1][0]),
+                                 "theta": THETA}
+            sol.close()
+        out[name] = res
+    return out
+
+
 def run_reference(args):
     """The reference arm: the sequential FP64 CPU oracle on the host cores."""
     ws, rank, _ = _dist()
@@ -369,6 +416,7 @@ def main():
         oi, od = workload_insts("amp_scan", 0)
         v = side_rate(oi, stream, local, 128, flush, substeps=3, scheme=adscl.SCHEME_EVOLVED_A_RK3,
                       a_reint_every=64)
+        others["autotune"] = autotune_report(stream, local)
         others["amp_scan_evolved_A_rk3"] = {
             "value": v, "unit": UNIT, "rk_steps": 128,
             "workload": od + "; evolved-A scheme, SSP-RK3, A re-integrated every 64 steps",

@@ -166,6 +166,24 @@ adscl_status adscl_set_state(adscl_ctx *ctx, int32_t inst, const double *Phi, co
 /* Per-instance time step dt and current step index (host outputs, length B, may be NULL). */
 adscl_status adscl_get_clock(adscl_ctx *ctx, double *dt, int64_t *step);
 
+/* Autotuner (classic RK4 scheme): for every grid size N of the context, time each kernel shape
+ * that fits N -- P grid nodes per thread, NT threads per CTA (so 512 / NT CTAs per SM), CL CTAs
+ * (a thread-block cluster) per instance -- on the context's own instances of that N for
+ * trial_steps RK4 steps (0 = 8) from their current slices, keep the fastest, and restore the
+ * state (the call changes no instance's slice, step or status).  Results are cached for the
+ * process by (GPU name, SM count, N, number of instances of that N); a cached entry is reused
+ * without timing.  Synchronous.  No-op for the evolved-A and fixed-metric schemes (one shape).
+ * Different shapes associate the radial scans differently, so results agree with the default
+ * shape to rounding, not bit for bit. */
+adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps);
+
+/* The kernel shape (P, NT, CL) instance `inst` runs with (any output may be NULL). */
+adscl_status adscl_get_shape(adscl_ctx *ctx, int32_t inst, int32_t *P, int32_t *NT, int32_t *CL);
+
+/* Run every instance of grid size N with shape (P, NT, CL); ADSCL_EINVAL if the library is not
+ * built with that shape, it does not fit N, or no instance has that N. */
+adscl_status adscl_set_shape(adscl_ctx *ctx, int32_t N, int32_t P, int32_t NT, int32_t CL);
+
 /* Kernel launches issued by this context since creation (for launch accounting). */
 int64_t adscl_launch_count(const adscl_ctx *ctx);
 

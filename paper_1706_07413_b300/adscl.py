@@ -62,6 +62,9 @@ SIGNATURES = {
     "adscl_set_state": ([_VP, _I32, _VP, _VP, _I64], ctypes.c_int),
     "adscl_get_clock": ([_VP, _VP, _VP], ctypes.c_int),
     "adscl_launch_count": ([_VP], _I64),
+    "adscl_autotune": ([_VP, _I32], ctypes.c_int),
+    "adscl_get_shape": ([_VP, _I32, _VP, _VP, _VP], ctypes.c_int),
+    "adscl_set_shape": ([_VP, _I32, _I32, _I32, _I32], ctypes.c_int),
     "adscl_probe_fp64": ([_I32, _VP, _VP], ctypes.c_int),
     "adscl_exp_neg": ([_I32, _VP, _VP, _I64], ctypes.c_int),
     "adscl_evolve_noalloc": ([_I32, _VP, _I32, _I32, _VP, _VP, _F, _F, _F, _F, _VP, _VP, _VP, _VP],
@@ -264,3 +267,21 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.adscl_launch_count(self.ctx))
+
+    # -- kernel shapes and the autotuner
+    def autotune(self, trial_steps=8):
+        """Pick the fastest kernel shape for every grid size (state unchanged); returns
+        {N: (P, NT, CL)}."""
+        self._check(self.lib.adscl_autotune(self.ctx, int(trial_steps)))
+        return self.shapes()
+
+    def shape(self, inst):
+        v = [ctypes.c_int32() for _ in range(3)]
+        self._check(self.lib.adscl_get_shape(self.ctx, int(inst), *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def shapes(self):
+        return {int(n): self.shape(int(np.argmax(self.N == n))) for n in np.unique(self.N)}
+
+    def set_shape(self, N, P, NT, CL):
+        self._check(self.lib.adscl_set_shape(self.ctx, int(N), int(P), int(NT), int(CL)))

@@ -9,8 +9,10 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "adscl.h"
@@ -19,6 +21,7 @@
 #include "spectrum_tc.cuh"
 #include "adjoint.cuh"
 #include "evolve_ea.cuh"
+#include "shapes.h"
 
 using namespace adscl;
 
@@ -37,7 +40,12 @@ int cluster_of(int N)
     while (N > cl * kP * kNT + 1) cl *= 2;
     return cl;
 }
-int cl_index(int cl) { return cl == 1 ? 0 : cl == 2 ? 1 : cl == 4 ? 2 : 3; }
+// default shape of grid size N: P = 8, NT = 512 and the smallest cluster that holds the grid
+int default_shape(int N) { return shape_index(kP, kNT, cluster_of(N)); }
+
+// autotuner results of this process: (device name, SM count, N, instances of that N) -> shape
+std::map<std::tuple<std::string, int, int, int>, int> g_tuned;
+std::mutex g_tuned_mu;
 static_assert(6 * field_stride<kP>(kMaxPoints1) * 8 + 4096 <= 232448, "shared memory budget");
 
 }  // namespace
@@ -54,11 +62,14 @@ struct adscl_ctx {
     int device = 0, one_per_launch = 0, chunk = 16, direct_launch = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;     // private stream on which evolve launches are captured
-    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};   // side streams of concurrent launch groups
-    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
+    std::vector<cudaStream_t> aux;       // side streams of concurrent launch groups
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
     cudaGraphExec_t evo_exec = nullptr;    // cached executable graph of adscl_evolve's launches
     int num_sms = 0;
-    int max_units[4] = {0, 0, 0, 0};   // co-resident CTAs / clusters of 2, 4, 8 of the evolve kernel
+    std::vector<int> shape_of;         // evolve-kernel shape (index into kShapes) of every instance
+    std::map<std::pair<int, size_t>, int> units_cache;   // (shape, smem) -> co-resident units
+    std::string dev_name;
     double t_prev = 0.0;               // t_end of the last evolve call since the initial data
     int scheme = 0, reint = 0;         // ADSCL_SCHEME_*, A re-integration interval (evolved A)
     double *d_A = nullptr;             // packed evolved A (evolved-A schemes)
@@ -167,35 +178,30 @@ double step_for(int N, double cfl, double cadence)
     return cadence / std::ceil(cadence / (cfl * h));
 }
 
-template <int CL>
-adscl_status launch_group(adscl_ctx *ctx, const EvolveArgs &a, int units, cudaStream_t sm)
+// co-resident units (CTAs or clusters) of shape id with dynamic shared memory smem
+adscl_status max_units(adscl_ctx *ctx, int id, size_t smem, int *units)
 {
-    if constexpr (CL == 1) {
-        evolve_kernel<kP, kNT, 1><<<units, kNT, ctx->smem, sm>>>(a, ctx->stride);
-        CK(cudaGetLastError());
-    } else {
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(CL * units, 1, 1);
-        cfg.blockDim = dim3(kNT, 1, 1);
-        cfg.dynamicSmemBytes = ctx->smem;
-        cfg.stream = sm;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = CL;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        CK(cudaLaunchKernelEx(&cfg, evolve_kernel<kP, kNT, CL>, a, ctx->stride));
+    auto it = ctx->units_cache.find({id, smem});
+    if (it != ctx->units_cache.end()) {
+        *units = it->second;
+        return ADSCL_OK;
     }
+    int u = 0;
+    const cudaError_t e = shape_max_units(id, smem, ctx->num_sms, &u);
+    if (e != cudaSuccess || u < 1)
+        return fail(ctx, ADSCL_EUNSUPPORTED, "shape (%d, %d, %d) of the evolve kernel does not fit (%s)",
+                    kShapes[id].P, kShapes[id].NT, kShapes[id].CL, cudaGetErrorString(e));
+    ctx->units_cache[{id, smem}] = u;
+    *units = u;
     return ADSCL_OK;
 }
 
 // Launch the evolution kernel on the work list d_order[first .. first + nwork) (host copy
-// order_host[0 .. nwork)).  The list is sorted by N, largest first, so the instances that need
-// clusters of 8, 4 and 2 CTAs and those that fit one CTA form consecutive groups; each group is
-// one persistent launch with the queue control and round counters of its first list position
-// (d_ctl[first + i], d_rounds[first + i ..]), so no two launches of one call share them.
+// order_host[0 .. nwork)).  The list is sorted by N, largest first, and the kernel shape is a
+// function of N, so instances of one shape form runs; each run is one persistent launch with the
+// queue control and round counters of its first list position (d_ctl[first + i],
+// d_rounds[first + i ..]), so no two launches of one call share them.  The runs of one call are
+// launched concurrently and split the SMs in proportion to their work.
 adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
                            const int32_t *order_host, int nwork, double *outA, double *outD,
                            cudaStream_t sm)
@@ -239,7 +245,7 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
         ea.A = ctx->d_A;
         ea.order = (ctx->scheme == ADSCL_SCHEME_EVOLVED_A_RK2) ? 2 : 3;
         ea.reint = ctx->reint;
-        const int units = std::min(nwork, ctx->max_units[0]);
+        const int units = std::min(nwork, ctx->num_sms);
         queue_init_kernel<<<(nwork + 255) / 256, 256, 0, sm>>>(ea.e.ctl, ea.e.rounds, nwork, units);
         CK(cudaGetLastError());
         if (ctx->scheme == ADSCL_SCHEME_FIXED_METRIC_RK3)
@@ -250,28 +256,35 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
         ctx->launches += 2;
         return ADSCL_OK;
     }
-    // the groups (at most four) run concurrently: the first on sm, the others on side streams
-    // forked from sm and joined back into it; the block scheduler gives the SMs a group frees to
-    // the CTAs of the others still waiting to start (no group waits on another)
-    int starts[5], ng = 0;
+    // runs of equal shape, with each run's largest grid, shared memory and co-resident units
+    std::vector<int> starts, shp, nmax, units_max;
+    std::vector<size_t> smem;
     for (int i = 0; i < nwork;) {
-        const int cl = cluster_of(ctx->N[order_host[i]]);
-        int j = i + 1;
-        while (j < nwork && cluster_of(ctx->N[order_host[j]]) == cl) ++j;
-        starts[ng++] = i;
+        const int id = ctx->shape_of[order_host[i]];
+        int j = i + 1, nm = ctx->N[order_host[i]];
+        while (j < nwork && ctx->shape_of[order_host[j]] == id) nm = std::max(nm, ctx->N[order_host[j++]]);
+        starts.push_back(i);
+        shp.push_back(id);
+        nmax.push_back(nm);
+        smem.push_back(shape_smem(id, nm));
+        int u = 0;
+        adscl_status s = max_units(ctx, id, smem.back(), &u);
+        if (s != ADSCL_OK) return s;
+        units_max.push_back(u);
         i = j;
     }
-    starts[ng] = nwork;
-    // SMs per group: in proportion to the group's estimated work (N times the RK4 steps to
-    // t_end, counted from the previous call's t_end), but no more than its instances can use,
-    // so that the groups finish together
-    int units_of[4];
+    const int ng = (int)starts.size();
+    starts.push_back(nwork);
+    // SMs per run: in proportion to the run's estimated work (N times the RK4 steps to t_end,
+    // counted from the previous call's t_end), but no more than its instances can occupy, so
+    // that the runs finish together
+    std::vector<int> units_of(ng);
     {
-        double W[4] = {0, 0, 0, 0};
-        int cap[4], cls[4];
+        std::vector<double> W(ng, 0.0), cap(ng), spu(ng), sms(ng, 0.0);
+        std::vector<char> sat(ng, 0);
         for (int g = 0; g < ng; ++g) {
-            cls[g] = cluster_of(ctx->N[order_host[starts[g]]]);
-            cap[g] = std::min(starts[g + 1] - starts[g], ctx->max_units[cl_index(cls[g])]) * cls[g];
+            spu[g] = (double)ctx->num_sms / units_max[g];   // SMs one unit occupies
+            cap[g] = std::min(starts[g + 1] - starts[g], units_max[g]) * spu[g];
             for (int i = starts[g]; i < starts[g + 1]; ++i) {
                 const int b = order_host[i];
                 double steps = 1.0;
@@ -282,10 +295,8 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
                 W[g] += (double)ctx->N[b] * steps;
             }
         }
-        double sms[4] = {0, 0, 0, 0};
-        bool sat[4] = {false, false, false, false};
         double left = ctx->num_sms;
-        for (int it = 0; it < ng; ++it) {   // water-filling: saturated groups keep their cap
+        for (int it = 0; it < ng; ++it) {   // water-filling: saturated runs keep their cap
             double wsum = 0.0;
             for (int g = 0; g < ng; ++g)
                 if (!sat[g]) wsum += W[g];
@@ -296,45 +307,42 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
                 sms[g] = left * W[g] / wsum;
                 if (sms[g] >= cap[g]) {
                     sms[g] = cap[g];
-                    sat[g] = true;
+                    sat[g] = 1;
                     left -= cap[g];
                     changed = true;
                 }
             }
             if (!changed) break;
         }
-        for (int g = 0; g < ng; ++g)
-            units_of[g] = std::max(1, std::min(cap[g], (int)(sms[g] + 0.5)) / cls[g]);
+        for (int g = 0; g < ng; ++g) {
+            const int nw = starts[g + 1] - starts[g];
+            units_of[g] = (ng == 1) ? std::min(nw, units_max[g])
+                                    : std::max(1, std::min(std::min(nw, units_max[g]), (int)(sms[g] / spu[g] + 0.5)));
+        }
     }
     if (ng > 1) {
-        for (int g = 0; g < ng - 1; ++g)
-            if (!ctx->aux[g]) CK(cudaStreamCreateWithFlags(&ctx->aux[g], cudaStreamNonBlocking));
-        if (!ctx->ev_fork) {
-            CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-            for (int g = 0; g < 3; ++g) CK(cudaEventCreateWithFlags(&ctx->ev_join[g], cudaEventDisableTiming));
+        while ((int)ctx->aux.size() < ng - 1) {
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev = nullptr;
+            CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            ctx->aux.push_back(st);
+            ctx->ev_join.push_back(ev);
         }
+        if (!ctx->ev_fork) CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
         CK(cudaEventRecord(ctx->ev_fork, sm));
         for (int g = 0; g < ng - 1; ++g) CK(cudaStreamWaitEvent(ctx->aux[g], ctx->ev_fork, 0));
     }
     for (int g = 0; g < ng; ++g) {
         const int i = starts[g], j = starts[g + 1];
-        const int cl = cluster_of(ctx->N[order_host[i]]);
         const cudaStream_t gs = (g == 0) ? sm : ctx->aux[g - 1];
-        const int units = (ng > 1) ? units_of[g] : std::min(j - i, ctx->max_units[cl_index(cl)]);
         a.order = ctx->d_order + first + i;
         a.nwork = j - i;
         a.ctl = ctx->d_ctl + first + i;
         a.rounds = ctx->d_rounds + first + i;
-        queue_init_kernel<<<(a.nwork + 255) / 256, 256, 0, gs>>>(a.ctl, a.rounds, a.nwork, units);
+        queue_init_kernel<<<(a.nwork + 255) / 256, 256, 0, gs>>>(a.ctl, a.rounds, a.nwork, units_of[g]);
         CK(cudaGetLastError());
-        adscl_status s = ADSCL_OK;
-        switch (cl) {
-        case 1: s = launch_group<1>(ctx, a, units, gs); break;
-        case 2: s = launch_group<2>(ctx, a, units, gs); break;
-        case 4: s = launch_group<4>(ctx, a, units, gs); break;
-        default: s = launch_group<8>(ctx, a, units, gs); break;
-        }
-        if (s != ADSCL_OK) return s;
+        CK(shape_launch(shp[g], a, units_of[g], smem[g], shape_stride(shp[g], nmax[g]), gs));
         ctx->launches += 2;
     }
     for (int g = 0; g < ng - 1; ++g) {
@@ -782,48 +790,30 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     CK(cudaMalloc(&ctx->d_out, 3 * (size_t)ctx->B * sizeof(double)));
     CK(cudaMalloc(&ctx->d_outs, (size_t)ctx->B * sizeof(int32_t)));
 
-    // a CTA never holds more than 4096 nodes of one instance (larger grids use clusters)
+    // the evolved-A kernels: one CTA of 512 threads per instance (N <= 4097)
     ctx->stride = field_stride<kP>(std::min(ctx->Nmax, kMaxPoints1));
     ctx->smem = (size_t)6 * ctx->stride * sizeof(double);
     // the attribute is per kernel, not per context: always raise it to the largest grid
     const size_t smem_max = (size_t)6 * field_stride<kP>(kMaxPoints1) * sizeof(double);
-    CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_max));
-    CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_max));
-    CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_max));
-    CK(cudaFuncSetAttribute(evolve_kernel<kP, kNT, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_max));
+    CK(shapes_set_attributes());
     CK(cudaFuncSetAttribute(evolve_ea_kernel<kP, kNT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem_max));
     CK(cudaFuncSetAttribute(evolve_ea_kernel<kP, kNT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem_max));
-    // persistent grid sizes: one CTA per SM, and as many clusters as can be co-resident
-    ctx->max_units[0] = ctx->num_sms;
-    for (int cl = 2; cl <= kMaxCluster; cl *= 2) {
-        bool used = false;
-        for (int n : ctx->N) used |= cluster_of(n) == cl;
-        if (!used) continue;
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(cl * (ctx->num_sms / cl), 1, 1);
-        cfg.blockDim = dim3(kNT, 1, 1);
-        cfg.dynamicSmemBytes = ctx->smem;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cl;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int nc = 0;
-        cudaError_t e = cl == 2 ? cudaOccupancyMaxActiveClusters(&nc, evolve_kernel<kP, kNT, 2>, &cfg)
-                      : cl == 4 ? cudaOccupancyMaxActiveClusters(&nc, evolve_kernel<kP, kNT, 4>, &cfg)
-                                : cudaOccupancyMaxActiveClusters(&nc, evolve_kernel<kP, kNT, 8>, &cfg);
-        if (e != cudaSuccess || nc < 1)
-            return fail(ctx, ADSCL_EUNSUPPORTED, "no %d-CTA cluster of the evolve kernel fits (%s)", cl,
-                        cudaGetErrorString(e));
-        ctx->max_units[cl_index(cl)] = nc;
+    // default kernel shapes; every shape in use must fit the device
+    ctx->shape_of.resize(ctx->B);
+    for (int b = 0; b < ctx->B; ++b) {
+        ctx->shape_of[b] = default_shape(ctx->N[b]);
+        int u = 0;
+        if (ctx->scheme == ADSCL_SCHEME_RK4) {
+            adscl_status s = max_units(ctx, ctx->shape_of[b], shape_smem(ctx->shape_of[b], ctx->N[b]), &u);
+            if (s != ADSCL_OK) return s;
+        }
+    }
+    {
+        cudaDeviceProp prop{};
+        CK(cudaGetDeviceProperties(&prop, ctx->device));
+        ctx->dev_name = prop.name;
     }
     return ADSCL_OK;
 }
@@ -1184,6 +1174,141 @@ adscl_status adscl_get_clock(adscl_ctx *ctx, double *dt, int64_t *step)
 
 int64_t adscl_launch_count(const adscl_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+adscl_status adscl_get_shape(adscl_ctx *ctx, int32_t inst, int32_t *P, int32_t *NT, int32_t *CL)
+{
+    if (!ctx) return ADSCL_EINVAL;
+    if (inst < 0 || inst >= ctx->B) return fail(ctx, ADSCL_EINVAL, "bad instance %d", inst);
+    const Shape &sh = kShapes[ctx->shape_of[inst]];
+    if (P) *P = sh.P;
+    if (NT) *NT = sh.NT;
+    if (CL) *CL = sh.CL;
+    return ADSCL_OK;
+}
+
+adscl_status adscl_set_shape(adscl_ctx *ctx, int32_t N, int32_t P, int32_t NT, int32_t CL)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    const int id = shape_index(P, NT, CL);
+    if (id < 0) return fail(ctx, ADSCL_EINVAL, "shape (%d, %d, %d) is not built", P, NT, CL);
+    if (!shape_fits(id, N)) return fail(ctx, ADSCL_EINVAL, "shape (%d, %d, %d) does not fit N = %d", P, NT, CL, N);
+    int u = 0;
+    s = max_units(ctx, id, shape_smem(id, N), &u);
+    if (s != ADSCL_OK) return s;
+    bool any = false;
+    for (int b = 0; b < ctx->B; ++b)
+        if (ctx->N[b] == N) {
+            ctx->shape_of[b] = id;
+            any = true;
+        }
+    if (!any) return fail(ctx, ADSCL_EINVAL, "no instance has N = %d", N);
+    return ADSCL_OK;
+}
+
+adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    if (ctx->scheme != ADSCL_SCHEME_RK4) return ADSCL_OK;   // one shape only
+    const int trial = trial_steps > 0 ? trial_steps : 8;
+    const int B = ctx->B;
+    const size_t fb = (size_t)ctx->total * sizeof(double);
+    CK(cudaStreamSynchronize(ctx->stream));
+    // the state is saved here and restored after every trial
+    double *bPhi = nullptr, *bPi = nullptr;
+    InstState *bSt = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (bPhi) cudaFree(bPhi);
+        if (bPi) cudaFree(bPi);
+        if (bSt) cudaFree(bSt);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    auto run = [&]() -> adscl_status {
+        CK(cudaMalloc(&bPhi, fb));
+        CK(cudaMalloc(&bPi, fb));
+        CK(cudaMalloc(&bSt, B * sizeof(InstState)));
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaMemcpyAsync(bPhi, ctx->d_Phi, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(bPi, ctx->d_Pi, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(bSt, ctx->d_st, B * sizeof(InstState), cudaMemcpyDeviceToDevice, ctx->stream));
+        std::vector<InstState> st0(B), st1(B);
+        CK(cudaMemcpyAsync(st0.data(), ctx->d_st, B * sizeof(InstState), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        auto restore = [&]() -> adscl_status {
+            CK(cudaMemcpyAsync(ctx->d_Phi, bPhi, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(ctx->d_Pi, bPi, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(ctx->d_st, bSt, B * sizeof(InstState), cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaMemsetAsync(ctx->d_ctl, 0, (B + 1) * sizeof(QueueCtl), ctx->stream));
+            return ADSCL_OK;
+        };
+        const std::vector<int32_t> &ord = ctx->h_order;
+        for (int i = 0; i < B;) {   // runs of equal N in the work order
+            const int n = ctx->N[ord[i]];
+            int j = i + 1;
+            while (j < B && ctx->N[ord[j]] == n) ++j;
+            const auto key = std::make_tuple(ctx->dev_name, ctx->num_sms, n, j - i);
+            int best = -1;
+            {
+                std::lock_guard<std::mutex> lk(g_tuned_mu);
+                auto it = g_tuned.find(key);
+                if (it != g_tuned.end()) best = it->second;
+            }
+            if (best < 0) {
+                const double dt = ctx->h_desc[ord[i]].dt;
+                long long smax = 0;
+                for (int q = i; q < j; ++q) smax = std::max(smax, (long long)st0[ord[q]].step);
+                double best_rate = 0.0;
+                for (int id = 0; id < kNumShapes; ++id) {
+                    if (!shape_fits(id, n)) continue;
+                    int u = 0;
+                    if (shape_max_units(id, shape_smem(id, n), ctx->num_sms, &u) != cudaSuccess || u < 1) {
+                        (void)cudaGetLastError();
+                        continue;
+                    }
+                    for (int q = i; q < j; ++q) ctx->shape_of[ord[q]] = id;
+                    float ms = 0.0f;
+                    for (int rep = 0; rep < 2; ++rep) {   // a one-step warm-up, then the trial
+                        s = restore();
+                        if (s != ADSCL_OK) return s;
+                        const double te = (double)(smax + (rep == 0 ? 1 : trial)) * dt;
+                        CK(cudaEventRecord(e0, ctx->stream));
+                        s = launch_evolve(ctx, kModeEvolve, te, i, ord.data() + i, j - i, nullptr, nullptr,
+                                          ctx->stream);
+                        if (s != ADSCL_OK) return s;
+                        CK(cudaEventRecord(e1, ctx->stream));
+                        CK(cudaStreamSynchronize(ctx->stream));
+                        CK(cudaEventElapsedTime(&ms, e0, e1));
+                    }
+                    CK(cudaMemcpy(st1.data(), ctx->d_st, B * sizeof(InstState), cudaMemcpyDeviceToHost));
+                    double work = 0.0;
+                    for (int q = i; q < j; ++q)
+                        work += (double)n * 4.0 * (double)(st1[ord[q]].step - st0[ord[q]].step);
+                    const double rate = ms > 0.0f ? work / ms : 0.0;
+                    if (rate > best_rate) {
+                        best_rate = rate;
+                        best = id;
+                    }
+                }
+                if (best < 0) best = default_shape(n);   // nothing ran (every instance stopped)
+                std::lock_guard<std::mutex> lk(g_tuned_mu);
+                g_tuned[key] = best;
+            }
+            for (int q = i; q < j; ++q) ctx->shape_of[ord[q]] = best;
+            i = j;
+        }
+        s = restore();
+        if (s != ADSCL_OK) return s;
+        CK(cudaStreamSynchronize(ctx->stream));
+        return ADSCL_OK;
+    };
+    s = run();
+    cleanup();
+    return s;
+}
+
 const char *adscl_last_error(const adscl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 void adscl_destroy(adscl_ctx *ctx)
@@ -1204,10 +1329,8 @@ void adscl_destroy(adscl_ctx *ctx)
         if (p) cudaFree(p);
     if (ctx->evo_exec) cudaGraphExecDestroy(ctx->evo_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-    for (int g = 0; g < 3; ++g) {
-        if (ctx->aux[g]) cudaStreamDestroy(ctx->aux[g]);
-        if (ctx->ev_join[g]) cudaEventDestroy(ctx->ev_join[g]);
-    }
+    for (cudaStream_t st : ctx->aux) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : ctx->ev_join) cudaEventDestroy(ev);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     delete ctx;
 }

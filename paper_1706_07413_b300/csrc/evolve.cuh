@@ -139,7 +139,7 @@ __host__ __device__ constexpr int field_stride(int Nmax) {
     return (((Nmax + 12) + (Nmax + 12) / P + 1) + 1) & ~1;
 }
 
-__global__ void queue_init_kernel(QueueCtl *ctl, int32_t *rounds, int nwork, int grid)
+static __global__ void queue_init_kernel(QueueCtl *ctl, int32_t *rounds, int nwork, int grid)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
@@ -196,8 +196,10 @@ __device__ __forceinline__ int block_start(int r, int T) { return (r * T + CL - 
 // the node blocks block_start(r) .. block_start(r+1)-1 (at least NT/2 blocks each, so P >= 3
 // halo nodes always come from the neighbouring rank); halos, scan carries and the step-end
 // diagnostics cross between the CTAs through distributed shared memory.
+// launch bounds: 512 threads per SM worth of CTAs (one CTA of 512, two of 256, four of 128), so
+// that every shape gets the same 128 registers per thread
 template <int P, int NT, int CL = 1>
-__global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
+__global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(EvolveArgs a, int stride)
 {
     static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
     static_assert(CL == 1 || CL == 2 || CL == 4 || CL == 8, "cluster of 1, 2, 4 or 8 CTAs");
@@ -758,7 +760,7 @@ __global__ void __launch_bounds__(NT, 1) evolve_kernel(EvolveArgs a, int stride)
 
 // per-instance results of an evolve call: t_reached, t_collapse, mass, status
 // (with ctl given, the instance whose chunk wait ran out in that launch is reported as kTimeout)
-__global__ void gather_kernel(const InstDesc *desc, const InstState *st, int B, double t_end,
+static __global__ void gather_kernel(const InstDesc *desc, const InstState *st, int B, double t_end,
                               int evolve_call, const QueueCtl *ctl, const int32_t *order,
                               double *t_reached, double *t_c, double *mass, int32_t *status)
 {
