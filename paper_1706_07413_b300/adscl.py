@@ -285,3 +285,11 @@ class Solver:
 
     def set_shape(self, N, P, NT, CL):
         self._check(self.lib.adscl_set_shape(self.ctx, int(N), int(P), int(NT), int(CL)))
+
+    def apply_shapes(self, table):
+        """Apply {N: (P, NT, CL)} (e.g. a saved autotune() result; JSON keys may be strings)
+        to the grid sizes of this context that appear in it."""
+        present = set(int(n) for n in self.N)
+        for n, shp in table.items():
+            if int(n) in present:
+                self.set_shape(int(n), *shp)
