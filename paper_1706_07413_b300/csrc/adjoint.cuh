@@ -38,7 +38,10 @@ constexpr int kANW = kANT / 32;
 constexpr int kStageArrays = 6;  // stored per stage: yP, yQ, M, E, F, AL
 constexpr int kScrArrays = 20;   // CTA scratch arrays of length Nmax
 
-enum : int32_t { kAdjSegment = 0, kAdjSpectrum = 1, kAdjProject = 2 };
+// kAdjSegment: both phases of a segment; kAdjSegF / kAdjSegB: only the recomputation (phase F,
+// from the checkpoint into the stage storage) or only the backward sweep (phase B, from the
+// stage storage), so that the recomputation of one segment can run beside the sweep of the next
+enum : int32_t { kAdjSegment = 0, kAdjSpectrum = 1, kAdjProject = 2, kAdjSegF = 3, kAdjSegB = 4 };
 
 struct AdjArgs {
     const InstDesc *desc;
@@ -629,6 +632,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
         }
 
         // ================= segment: phase F (recompute and store every stage) =================
+        if (a.mode == kAdjSegment || a.mode == kAdjSegF) {
         const double *ckP = a.ckP + d.off, *ckQ = a.ckQ + d.off;
         if (act) {
 #pragma unroll
@@ -671,7 +675,10 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
             __syncthreads();
         }
 
+        }   // phase F
+
         // ================= segment: phase B (steps backwards) =================
+        if (a.mode == kAdjSegment || a.mode == kAdjSegB)
         for (int n = a.nsteps - 1; n >= 0; --n) {
             if (act) {
 #pragma unroll

@@ -107,8 +107,12 @@ struct adscl_ctx {
     // adjoint (built on first use)
     double *d_lam = nullptr;           // packed lambda: Phi part, then Pi part
     double *d_adj_scr = nullptr;       // per CTA scratch
-    double *d_adj_stage = nullptr;     // stored stages of one segment, per instance
-    size_t adj_stage_doubles = 0;
+    double *d_adj_stage = nullptr;     // stored stages of one segment, per instance (1 or 2 buffers)
+    size_t adj_stage_doubles = 0;      // doubles of one buffer
+    int adj_stage_bufs = 0;
+    cudaStream_t adj_aux = nullptr;    // stream of the recomputation beside the backward sweep
+    cudaEvent_t adj_free[2] = {nullptr, nullptr}, adj_ready[2] = {nullptr, nullptr};
+    cudaEvent_t adj_ck = nullptr;      // the last checkpoint is written
     double *d_ck = nullptr;            // checkpoints (Phi, Pi) at segment starts
     size_t ck_doubles = 0;
     double *d_adj_small = nullptr;     // E0, ET, Ebar (B x J each), J (B), dJda (B x 64)
@@ -981,12 +985,15 @@ __global__ void drift_kernel(const double *E0, const double *ET, int B, int J, d
     Jout[b] = s;
 }
 
-adscl_status launch_adjoint(adscl_ctx *ctx, AdjArgs &a)
+// one adjoint launch on stream sm; lane 0 or 1 selects the work counter and the per-CTA scratch
+// (the two lanes may run at the same time)
+adscl_status launch_adjoint(adscl_ctx *ctx, AdjArgs &a, cudaStream_t sm, int lane)
 {
     const int grid = std::min(ctx->B, ctx->num_sms);
-    CK(cudaMemsetAsync(ctx->d_adj_queue, 0, sizeof(int32_t), ctx->stream));
-    a.queue = ctx->d_adj_queue;
-    adjoint_kernel<<<grid, kANT, 0, ctx->stream>>>(a);
+    CK(cudaMemsetAsync(ctx->d_adj_queue + lane, 0, sizeof(int32_t), sm));
+    a.queue = ctx->d_adj_queue + lane;
+    a.scratch = ctx->d_adj_scr + (size_t)lane * grid * kScrArrays * ctx->Nmax;
+    adjoint_kernel<<<grid, kANT, 0, sm>>>(a);
     CK(cudaGetLastError());
     ctx->launches += 1;
     return ADSCL_OK;
@@ -1016,18 +1023,27 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     // buffers (grown on demand)
     if (!ctx->d_lam) {
         CK(cudaMalloc(&ctx->d_lam, 2 * total * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_adj_scr, (size_t)std::min(B, ctx->num_sms) * kScrArrays * ctx->Nmax * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_adj_scr, (size_t)2 * std::min(B, ctx->num_sms) * kScrArrays * ctx->Nmax * sizeof(double)));
         CK(cudaMalloc(&ctx->d_adj_small, ((size_t)B * (5 * kMaxModes + 1)) * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_adj_queue, sizeof(int32_t)));
+        CK(cudaMalloc(&ctx->d_adj_queue, 2 * sizeof(int32_t)));
     }
+    // stage storage of one segment; two of them (when memory allows) let the recomputation of
+    // segment g-1 run beside the backward sweep of segment g
     const size_t stage_need = (size_t)B * std::max(seg, 1) * 4 * kStageArrays * ctx->Nmax;
     if (ctx->adj_stage_doubles < stage_need) {
         if (ctx->d_adj_stage) CK(cudaFree(ctx->d_adj_stage));
         ctx->d_adj_stage = nullptr;
-        if (cudaMalloc(&ctx->d_adj_stage, stage_need * sizeof(double)) != cudaSuccess) {
+        ctx->adj_stage_bufs = 0;
+        if (cudaMalloc(&ctx->d_adj_stage, 2 * stage_need * sizeof(double)) == cudaSuccess) {
+            ctx->adj_stage_bufs = 2;
+        } else {
             cudaGetLastError();
-            ctx->adj_stage_doubles = 0;
-            return fail(ctx, ADSCL_ENOMEM, "adjoint stage storage (%zu MB)", stage_need * 8 >> 20);
+            if (cudaMalloc(&ctx->d_adj_stage, stage_need * sizeof(double)) != cudaSuccess) {
+                cudaGetLastError();
+                ctx->adj_stage_doubles = 0;
+                return fail(ctx, ADSCL_ENOMEM, "adjoint stage storage (%zu MB)", stage_need * 8 >> 20);
+            }
+            ctx->adj_stage_bufs = 1;
         }
         ctx->adj_stage_doubles = stage_need;
     }
@@ -1043,7 +1059,42 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     double *dJ = Jd + B;
     (void)dJ;
 
-    // forward: initial data, E(0), checkpoints every `seg` steps, E(T); no collapse stop
+    // backward arguments (the segment launches are configured below)
+    AdjArgs aa{};
+    aa.desc = ctx->d_desc;
+    aa.geo = ctx->d_geo;
+    aa.exptab = ctx->d_exptab;   // (aa.eig: the mode tables exist only after the forward pass)
+    aa.order = ctx->d_order;
+    aa.nwork = B;
+    aa.nsteps_cap = std::max(seg, 1);
+    aa.lamP = ctx->d_lam;
+    aa.lamQ = ctx->d_lam + total;
+    aa.Nmax = ctx->Nmax;
+    aa.J = Jm;
+    const size_t stN = ctx->adj_stage_doubles;
+    auto seg_args = [&](long long g, int mode) {
+        AdjArgs x = aa;
+        x.mode = mode;
+        x.ckP = ctx->d_ck + (size_t)g * 2 * total;
+        x.ckQ = x.ckP + total;
+        x.nsteps = (int32_t)(std::min(nT, (g + 1) * seg) - g * seg);
+        x.stage = ctx->d_adj_stage + (ctx->adj_stage_bufs == 2 ? (size_t)(g & 1) * stN : 0);
+        return x;
+    };
+    const bool piped = ctx->adj_stage_bufs == 2 && nseg > 1;
+    if (piped && !ctx->adj_aux) {
+        CK(cudaStreamCreateWithFlags(&ctx->adj_aux, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->adj_ck, cudaEventDisableTiming));
+        for (int k = 0; k < 2; ++k) {
+            CK(cudaEventCreateWithFlags(&ctx->adj_free[k], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&ctx->adj_ready[k], cudaEventDisableTiming));
+        }
+    }
+    const int klast = (int)((nseg - 1) & 1);
+
+    // forward: initial data, E(0), checkpoints every `seg` steps, E(T); no collapse stop.  With
+    // two stage buffers the recomputation of the last segment (phase F, side stream) runs beside
+    // the forward pass's own last segment: both start from the last checkpoint.
     const double theta = ctx->theta;
     ctx->theta = -INFINITY;
     s = adscl_set_initial_modes(ctx, a, K, ptr_is_device);
@@ -1052,6 +1103,14 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         double *ck = ctx->d_ck + (size_t)g * 2 * total;
         CK(cudaMemcpyAsync(ck, ctx->d_Phi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ck + total, ctx->d_Pi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        if (piped && g == nseg - 1) {
+            CK(cudaEventRecord(ctx->adj_ck, ctx->stream));
+            CK(cudaStreamWaitEvent(ctx->adj_aux, ctx->adj_ck, 0));
+            AdjArgs x = seg_args(g, kAdjSegF);
+            s = launch_adjoint(ctx, x, ctx->adj_aux, 1);
+            if (s != ADSCL_OK) break;
+            CK(cudaEventRecord(ctx->adj_ready[klast], ctx->adj_aux));
+        }
         const long long n1 = std::min(nT, (g + 1) * seg);
         s = launch_evolve(ctx, kModeEvolve, (double)n1 * ctx->h_desc[0].dt, 0, ctx->h_order.data(), B, nullptr, nullptr, ctx->stream);
     }
@@ -1062,45 +1121,55 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     drift_kernel<<<(B + 127) / 128, 128, 0, ctx->stream>>>(E0, ET, B, Jm, Jd, EbT, Eb0);
     CK(cudaGetLastError());
 
-    // backward
-    AdjArgs aa{};
-    aa.desc = ctx->d_desc;
-    aa.geo = ctx->d_geo;
+    // backward; the spectrum transposes use the first slot of the buffer that the last segment
+    // does not use
+    if (!ctx->d_eig) return fail(ctx, ADSCL_ECUDA, "normal-mode tables missing");
     aa.eig = ctx->d_eig;
-    aa.exptab = ctx->d_exptab;
-    aa.order = ctx->d_order;
-    aa.nwork = B;
-    aa.stage = ctx->d_adj_stage;
-    aa.nsteps_cap = std::max(seg, 1);
-    aa.lamP = ctx->d_lam;
-    aa.lamQ = ctx->d_lam + total;
-    aa.scratch = ctx->d_adj_scr;
-    aa.Nmax = ctx->Nmax;
-    aa.J = Jm;
+    aa.stage = ctx->d_adj_stage + (piped ? (size_t)(klast ^ 1) * stN : 0);
     CK(cudaMemsetAsync(ctx->d_lam, 0, 2 * total * sizeof(double), ctx->stream));
     aa.mode = kAdjSpectrum;
     aa.Ebar = EbT;
     aa.sP = ctx->d_Phi;
     aa.sQ = ctx->d_Pi;
-    s = launch_adjoint(ctx, aa);
-    for (long long g = nseg - 1; g >= 0 && s == ADSCL_OK; --g) {
-        aa.mode = kAdjSegment;
-        aa.ckP = ctx->d_ck + (size_t)g * 2 * total;
-        aa.ckQ = aa.ckP + total;
-        aa.nsteps = (int32_t)(std::min(nT, (g + 1) * seg) - g * seg);
-        s = launch_adjoint(ctx, aa);
+    s = launch_adjoint(ctx, aa, ctx->stream, 0);
+    if (s != ADSCL_OK) return s;
+    if (piped) {
+        // main stream: B(g) for g descending, each after its F(g); side stream: F(g-1) once
+        // B(g+1) (or, for the first one, the spectrum transpose) has released its buffer
+        CK(cudaEventRecord(ctx->adj_free[klast ^ 1], ctx->stream));
+        for (long long g = nseg - 1; g >= 0 && s == ADSCL_OK; --g) {
+            AdjArgs x;
+            if (g >= 1) {
+                const int k = (int)((g - 1) & 1);
+                CK(cudaStreamWaitEvent(ctx->adj_aux, ctx->adj_free[k], 0));
+                x = seg_args(g - 1, kAdjSegF);
+                s = launch_adjoint(ctx, x, ctx->adj_aux, 1);
+                if (s != ADSCL_OK) break;
+                CK(cudaEventRecord(ctx->adj_ready[k], ctx->adj_aux));
+            }
+            const int kg = (int)(g & 1);
+            CK(cudaStreamWaitEvent(ctx->stream, ctx->adj_ready[kg], 0));
+            x = seg_args(g, kAdjSegB);
+            s = launch_adjoint(ctx, x, ctx->stream, 0);
+            CK(cudaEventRecord(ctx->adj_free[kg], ctx->stream));
+        }
+    } else {
+        for (long long g = nseg - 1; g >= 0 && s == ADSCL_OK; --g) {
+            AdjArgs x = seg_args(g, kAdjSegment);
+            s = launch_adjoint(ctx, x, ctx->stream, 0);
+        }
     }
     if (s != ADSCL_OK) return s;
     aa.mode = kAdjSpectrum;
     aa.Ebar = Eb0;
     aa.sP = ctx->d_ck;
     aa.sQ = ctx->d_ck + total;
-    s = launch_adjoint(ctx, aa);
+    s = launch_adjoint(ctx, aa, ctx->stream, 0);
     if (s != ADSCL_OK) return s;
     aa.mode = kAdjProject;
     aa.J = K;
     aa.dJda = dJ;
-    s = launch_adjoint(ctx, aa);
+    s = launch_adjoint(ctx, aa, ctx->stream, 0);
     if (s != ADSCL_OK) return s;
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (J_out) CK(cudaMemcpyAsync(J_out, Jd, B * sizeof(double), kind, ctx->stream));
@@ -1330,6 +1399,12 @@ void adscl_destroy(adscl_ctx *ctx)
     if (ctx->evo_exec) cudaGraphExecDestroy(ctx->evo_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (cudaStream_t st : ctx->aux) cudaStreamDestroy(st);
+    if (ctx->adj_aux) cudaStreamDestroy(ctx->adj_aux);
+    if (ctx->adj_ck) cudaEventDestroy(ctx->adj_ck);
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->adj_free[k]) cudaEventDestroy(ctx->adj_free[k]);
+        if (ctx->adj_ready[k]) cudaEventDestroy(ctx->adj_ready[k]);
+    }
     for (cudaEvent_t ev : ctx->ev_join) cudaEventDestroy(ev);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     delete ctx;
