@@ -194,14 +194,17 @@ def workload_insts(name, rank):
     raise ValueError(name)
 
 
-def side_rate(insts, stream, local, rk_steps, flush, substeps=4, **kw):
+def side_rate(insts, stream, local, rk_steps, flush, substeps=4, tune=True, **kw):
     """Point-substeps/s of one persistent launch of rk_steps time steps on another batch
-    (substeps: Runge-Kutta stages per step of the scheme selected by kw)."""
+    (substeps: Runge-Kutta stages per step of the scheme selected by kw; kernel shapes picked by
+    the autotuner unless tune is false)."""
     import torch
     from paper_1706_07413_b300 import adscl
     sol = adscl.Solver([it.N for it in insts], ko_sigma=SIGMA_KO, collapse_threshold=THETA,
                        device=local, stream=stream.cuda_stream, **kw)
     batch_fields(insts, sol)
+    if tune:
+        sol.autotune(8)
     dt, _ = sol.clock()
     T = rk_steps * float(dt.max())
     sol.evolve(T / 8)
@@ -310,6 +313,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-others", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default kernel shapes instead of the autotuner's choice")
+    ap.add_argument("--shape", default="",
+                    help="P,NT,CL: run the timed batch with this kernel shape instead of tuning "
+                         "(for profiling, where a profiler distorts the tuner's timings)")
     ap.add_argument("--workload", default="amp_scan", choices=["amp_scan", "large", "uneven"],
                     help="batch to time (the metric's workload is amp_scan)")
     ap.add_argument("--scheme", default="rk4", choices=sorted(SCHEMES),
@@ -344,6 +352,13 @@ def main():
                        device=local, stream=stream.cuda_stream, scheme=scheme_id,
                        a_reint_every=reint)
     batch_fields(insts, sol)
+    t0 = time.perf_counter()
+    fixed_shape = [int(v) for v in args.shape.split(",")] if args.shape else None
+    if fixed_shape:
+        for n in sorted(set(it.N for it in insts)):
+            sol.set_shape(n, *fixed_shape)
+    shapes = sol.shapes() if (args.no_autotune or fixed_shape) else sol.autotune(8)
+    tune_s = time.perf_counter() - t0
     dt, _ = sol.clock()
     dstep = STEP_RK * float(dt.max())
     outs = [torch.empty(B, dtype=torch.float64, device="cuda") for _ in range(3)] + \
@@ -384,11 +399,8 @@ def main():
     collapsed = int(np.sum(st == adscl.COLLAPSED))
 
     if dist is not None:
-        tt = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ww = torch.tensor([work], dtype=torch.float64, device="cuda")
-        dist.all_reduce(ww, op=dist.ReduceOp.SUM)
-        dev_s, work_all = float(tt.item()), float(ww.item())
+        from paper_1706_07413_b300 import shard
+        dev_s, work_all = shard.reduce_timing(dev_s, work, dist, device="cuda")
     else:
         work_all = work
     value = work_all / dev_s
@@ -471,7 +483,27 @@ def main():
         Jv, gv = sa.grad(a, Ta)
         torch.cuda.synchronize()
         t_adj = time.perf_counter() - t0
+        # the same with the autotuned forward shape (64 instances: fewer than the SMs, so the
+        # tuner splits each instance over a cluster; the adjoint kernel keeps one CTA each)
+        tuned = sa.autotune(8)
+        sa.grad(a, Ta)
+        sa.set_initial_modes(a)
+        sa.evolve(Ta)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sa.set_initial_modes(a)
+        sa.evolve(Ta)
+        torch.cuda.synchronize()
+        t_fwd_t = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        sa.grad(a, Ta)
+        torch.cuda.synchronize()
+        t_adj_t = time.perf_counter() - t0
         adj = {"value": t_adj / t_fwd, "forward_ms": 1e3 * t_fwd, "grad_ms": 1e3 * t_adj,
+               "forward_shape_P_NT_CL": [8, 512, 1],
+               "tuned": {"forward_shape_P_NT_CL": list(tuned[ainst[0].N]),
+                         "forward_ms": 1e3 * t_fwd_t, "grad_ms": 1e3 * t_adj_t,
+                         "ratio": t_adj_t / t_fwd_t},
                "workload": f"64 mode-sum instances, N=4097, {ADJ_STEPS} RK4 steps of dt=2pi/32768, "
                            "checkpoint every 256 steps, J = sum_{j<32}(E_j(T)-E_j(0))^2",
                "grad_includes": "forward pass with checkpoints, E(0), E(T), per-segment recompute "
@@ -503,12 +535,18 @@ def main():
             [torch.empty(B, dtype=torch.int32).pin_memory().numpy()]
         sol_e = adscl.Solver([N] * B, ko_sigma=SIGMA_KO, collapse_threshold=THETA, device=local,
                              stream=stream.cuda_stream)
+        if fixed_shape:
+            sol_e.set_shape(N, *fixed_shape)
+        elif not args.no_autotune:
+            sol_e.autotune(8)   # warms the process cache; each timed iteration re-applies it
         ne = max(3, args.steps // 4)
         tot, work_e = 0.0, 0.0
         for k in range(ne + 1):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
+            if not (args.no_autotune or fixed_shape):
+                sol_e.autotune(8)   # cached: no timing runs, the chosen shapes are re-applied
             sol_e.set_initial(hPhi, hPi)
             st = sol_e.lib.adscl_evolve(sol_e.ctx, dstep, res[0].ctypes.data, res[1].ctypes.data,
                                         res[2].ctypes.data, res[3].ctypes.data, 0)
@@ -546,6 +584,8 @@ def main():
                        "step": f"one persistent launch = {STEP_RK} RK4 steps of every running "
                                "instance",
                        "scheme": args.scheme,
+                       "kernel_shape_P_NT_CL": {str(k): list(v) for k, v in shapes.items()},
+                       "autotune_s": round(tune_s, 3) if not (args.no_autotune or fixed_shape) else None,
                        "window_t": [round(args.warmup * dstep, 6),
                                     round((args.warmup + args.steps) * dstep, 6)],
                        "collapsed_in_window": collapsed,

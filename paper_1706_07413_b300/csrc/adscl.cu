@@ -43,8 +43,10 @@ int cluster_of(int N)
 // default shape of grid size N: P = 8, NT = 512 and the smallest cluster that holds the grid
 int default_shape(int N) { return shape_index(kP, kNT, cluster_of(N)); }
 
-// autotuner results of this process: (device name, SM count, N, instances of that N) -> shape
-std::map<std::tuple<std::string, int, int, int>, int> g_tuned;
+// autotuner results of this process: (device name, SM count, the batch's (N, instances of that
+// N) in decreasing N) -> shape of each of those N
+using TuneKey = std::tuple<std::string, int, std::vector<std::pair<int, int>>>;
+std::map<TuneKey, std::vector<int>> g_tuned;
 std::mutex g_tuned_mu;
 static_assert(6 * field_stride<kP>(kMaxPoints1) * 8 + 4096 <= 232448, "shared memory budget");
 
@@ -1314,59 +1316,104 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
             return ADSCL_OK;
         };
         const std::vector<int32_t> &ord = ctx->h_order;
-        for (int i = 0; i < B;) {   // runs of equal N in the work order
-            const int n = ctx->N[ord[i]];
+        std::vector<int> run_start;            // runs of equal N in the work order
+        std::vector<std::pair<int, int>> sig;  // (N, count) of each run
+        for (int i = 0; i < B;) {
             int j = i + 1;
-            while (j < B && ctx->N[ord[j]] == n) ++j;
-            const auto key = std::make_tuple(ctx->dev_name, ctx->num_sms, n, j - i);
-            int best = -1;
-            {
-                std::lock_guard<std::mutex> lk(g_tuned_mu);
-                auto it = g_tuned.find(key);
-                if (it != g_tuned.end()) best = it->second;
-            }
-            if (best < 0) {
-                const double dt = ctx->h_desc[ord[i]].dt;
-                long long smax = 0;
-                for (int q = i; q < j; ++q) smax = std::max(smax, (long long)st0[ord[q]].step);
-                double best_rate = 0.0;
-                for (int id = 0; id < kNumShapes; ++id) {
-                    if (!shape_fits(id, n)) continue;
-                    int u = 0;
-                    if (shape_max_units(id, shape_smem(id, n), ctx->num_sms, &u) != cudaSuccess || u < 1) {
-                        (void)cudaGetLastError();
-                        continue;
-                    }
-                    for (int q = i; q < j; ++q) ctx->shape_of[ord[q]] = id;
-                    float ms = 0.0f;
-                    for (int rep = 0; rep < 2; ++rep) {   // a one-step warm-up, then the trial
-                        s = restore();
-                        if (s != ADSCL_OK) return s;
-                        const double te = (double)(smax + (rep == 0 ? 1 : trial)) * dt;
-                        CK(cudaEventRecord(e0, ctx->stream));
-                        s = launch_evolve(ctx, kModeEvolve, te, i, ord.data() + i, j - i, nullptr, nullptr,
-                                          ctx->stream);
-                        if (s != ADSCL_OK) return s;
-                        CK(cudaEventRecord(e1, ctx->stream));
-                        CK(cudaStreamSynchronize(ctx->stream));
-                        CK(cudaEventElapsedTime(&ms, e0, e1));
-                    }
-                    CK(cudaMemcpy(st1.data(), ctx->d_st, B * sizeof(InstState), cudaMemcpyDeviceToHost));
-                    double work = 0.0;
-                    for (int q = i; q < j; ++q)
-                        work += (double)n * 4.0 * (double)(st1[ord[q]].step - st0[ord[q]].step);
-                    const double rate = ms > 0.0f ? work / ms : 0.0;
-                    if (rate > best_rate) {
-                        best_rate = rate;
-                        best = id;
-                    }
-                }
-                if (best < 0) best = default_shape(n);   // nothing ran (every instance stopped)
-                std::lock_guard<std::mutex> lk(g_tuned_mu);
-                g_tuned[key] = best;
-            }
-            for (int q = i; q < j; ++q) ctx->shape_of[ord[q]] = best;
+            while (j < B && ctx->N[ord[j]] == ctx->N[ord[i]]) ++j;
+            run_start.push_back(i);
+            sig.push_back({ctx->N[ord[i]], j - i});
             i = j;
+        }
+        run_start.push_back(B);
+        const int nr = (int)sig.size();
+        auto set_run = [&](int r, int id) {
+            for (int q = run_start[r]; q < run_start[r + 1]; ++q) ctx->shape_of[ord[q]] = id;
+        };
+        const TuneKey key{ctx->dev_name, ctx->num_sms, sig};
+        {
+            std::lock_guard<std::mutex> lk(g_tuned_mu);
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) {
+                for (int r = 0; r < nr; ++r) set_run(r, it->second[r]);
+                return restore();
+            }
+        }
+        // point-substeps per ms of the list positions [i, j) with the current shapes: a one-step
+        // warm-up, then `trial` steps, from the saved state
+        auto rate_of = [&](int i, int j, double *rate) -> adscl_status {
+            long long smax = 0;
+            double dtmax = 0.0;
+            for (int q = i; q < j; ++q) {
+                smax = std::max(smax, (long long)st0[ord[q]].step);
+                dtmax = std::max(dtmax, ctx->h_desc[ord[q]].dt);
+            }
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {
+                s = restore();
+                if (s != ADSCL_OK) return s;
+                // t_end: `trial` steps of the largest time step (every instance advances)
+                const double te = (double)smax * ctx->h_desc[ord[i]].dt + (rep == 0 ? 1 : trial) * dtmax;
+                ctx->t_prev = (double)smax * ctx->h_desc[ord[i]].dt;
+                CK(cudaEventRecord(e0, ctx->stream));
+                s = launch_evolve(ctx, kModeEvolve, te, i, ord.data() + i, j - i, nullptr, nullptr, ctx->stream);
+                if (s != ADSCL_OK) return s;
+                CK(cudaEventRecord(e1, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+            }
+            CK(cudaMemcpy(st1.data(), ctx->d_st, B * sizeof(InstState), cudaMemcpyDeviceToHost));
+            double work = 0.0;
+            for (int q = i; q < j; ++q)
+                work += (double)ctx->N[ord[q]] * 4.0 * (double)(st1[ord[q]].step - st0[ord[q]].step);
+            *rate = ms > 0.0f ? work / ms : 0.0;
+            return ADSCL_OK;
+        };
+        const double t_prev0 = ctx->t_prev;
+        std::vector<int> best(nr), dflt(nr);
+        for (int r = 0; r < nr; ++r) {   // each grid size alone
+            const int n = sig[r].first;
+            dflt[r] = default_shape(n);
+            best[r] = -1;
+            double best_rate = 0.0;
+            for (int id = 0; id < kNumShapes; ++id) {
+                if (!shape_fits(id, n)) continue;
+                int u = 0;
+                if (shape_max_units(id, shape_smem(id, n), ctx->num_sms, &u) != cudaSuccess || u < 1) {
+                    (void)cudaGetLastError();
+                    continue;
+                }
+                set_run(r, id);
+                double rate = 0.0;
+                s = rate_of(run_start[r], run_start[r + 1], &rate);
+                if (s != ADSCL_OK) return s;
+                if (rate > best_rate) {
+                    best_rate = rate;
+                    best[r] = id;
+                }
+            }
+            if (best[r] < 0) best[r] = dflt[r];   // nothing ran (every instance stopped)
+            set_run(r, best[r]);
+        }
+        if (nr > 1 && best != dflt) {
+            // the sizes run concurrently in a batch: keep the per-size choice only if the whole
+            // batch is faster with it than with the default shapes
+            double r_best = 0.0, r_dflt = 0.0;
+            s = rate_of(0, B, &r_best);
+            if (s != ADSCL_OK) return s;
+            for (int r = 0; r < nr; ++r) set_run(r, dflt[r]);
+            s = rate_of(0, B, &r_dflt);
+            if (s != ADSCL_OK) return s;
+            if (r_best > r_dflt) {
+                for (int r = 0; r < nr; ++r) set_run(r, best[r]);
+            } else {
+                best = dflt;
+            }
+        }
+        ctx->t_prev = t_prev0;
+        {
+            std::lock_guard<std::mutex> lk(g_tuned_mu);
+            g_tuned[key] = best;
         }
         s = restore();
         if (s != ADSCL_OK) return s;
