@@ -58,9 +58,9 @@ CPU_SAMPLE_STEPS = 800    # oracle sample of the cpu_baseline leg: ~10 s on 16 h
 REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
 # DRAM bytes (read + write) of one timed evolve_kernel launch of the amplitude scan, from an ncu
 # capture of this script (profiles/evolve_kernel_amp_scan.md); reported only while the kernel
-# source is the one the counters were taken on.
-TRAFFIC = {"kernel_sha256": "8bf7461a8865258a2ac0b61bd9888b067a060b3c6953a770a8f6d2f9a31fb134",
-           "dram_bytes_per_launch": 17826560 + 205086464}
+# source and the kernel shape are the ones the counters were taken on.
+TRAFFIC = {"kernel_sha256": "fd9adabd9a7828a26ff6e7672fdc7d6f1b4960ca15d10e16c9303bd41732dec8",
+           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17847552 + 227662336}
 
 
 def kernel_digest():
@@ -408,7 +408,8 @@ def main():
     # roofline of the evolution kernel (it is >99% of each timed launch)
     achieved_tflops = (work * flops_pps) / dev_s / 1e12
     traffic = None
-    if amp and args.scheme == "rk4" and kernel_digest() == TRAFFIC["kernel_sha256"]:
+    if amp and kernel_digest() == TRAFFIC["kernel_sha256"] and \
+            list(shapes.get(N_DEFAULT, ())) == TRAFFIC["shape_P_NT_CL"]:
         traffic = TRAFFIC["dram_bytes_per_launch"]
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": tflops_peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / tflops_peak, "traffic": traffic,
