@@ -87,6 +87,9 @@ typedef struct {
     int32_t a_reint_every;       /* schemes 1, 2: re-integrate A from Eq. (eq:aprime) on slices
                                     whose step index is a multiple of this (0: never; the
                                     initial slice always takes the constraint solution) */
+    int32_t adjoint_ctas;        /* CTAs per instance of the adjoint kernel (adscl_grad): 1, 2 (a
+                                    thread-block cluster), or 0 = 2 when the batch has at most
+                                    half as many instances as the GPU has SMs, else 1 */
     void *stream;                /* cudaStream_t for all work; NULL = the legacy default stream */
 } adscl_config;
 

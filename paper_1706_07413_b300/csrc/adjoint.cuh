@@ -4,8 +4,10 @@
 // projection of spectrum.cuh.  Used for gradients of mode-energy functionals with respect to
 // initial data.
 //
-// Work unit: one CTA (512 threads, 8 nodes per thread, the layout of evolve.cuh) per instance
-// and checkpoint segment.
+// Work unit: one instance and checkpoint segment, on CL = 1 CTA (512 threads, 8 nodes per
+// thread, the layout of evolve.cuh) or on a CL = 2 thread-block cluster whose two CTAs own the
+// two halves of the node blocks (for batches smaller than the SM count: each instance then
+// occupies two SMs).
 //   Phase F: from the segment's first slice, recompute its steps with the same discrete map as
 //     evolve.cuh (affine-map scan for m, suffix sum for delta, table-driven exp) and store, for
 //     every stage of every step, the stage input (Phi, Pi) and the stage's m, e^{-delta}, F and
@@ -19,9 +21,11 @@
 //   into a suffix affine scan mu_c = alpha_c mu_{c+1} + mbar_c, the delta suffix sum transposed
 //   into a prefix sum, the derivatives of the per-cell RK4 maps (alpha, beta) and of the
 //   Simpson increment, and the midpoint interpolation and rho = Phi^2 + Pi^2.
-// Neighbour values go through CTA-private global scratch arrays and __syncthreads (the kernel is
-// bound by FP64 issue, not by memory).  Instances are taken from an atomic counter; no CTA waits
-// on another.
+// Neighbour values go through global scratch arrays private to the CTA (cluster) and a barrier
+// over the CTA (cluster: barrier.cluster with release / acquire semantics, which orders the global
+// scratch accesses of both CTAs); the block scans carry the other rank's total through
+// distributed shared memory.  The kernel is bound by FP64 issue, not by memory.  Instances are
+// taken from an atomic counter by rank 0; no CTA waits on another outside its cluster.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -81,11 +85,33 @@ __device__ __forceinline__ double rv(const double *v, int N, int i) {
 
 // ------------------------------------------------------------------ block scans (512 threads)
 struct ScanShared {
-    double a[kANW], b[kANW], c[kANW], d[kANW];
+    double a[kANW], b[kANW], c[kANW], d[kANW], e[kANW];
+    double pa, pb, pd;   // total of the other rank of a 2-CTA cluster (written by it)
 };
 
-// exclusive prefix composition of affine maps x -> a x + b over threads (ascending), applied to
-// 0 at the block start: returns the b part.  Threads' own maps are (a, b).
+// node ownership of this thread for grid size N: rank r of a CL-CTA cluster owns node blocks
+// ceil(r T / CL) .. ceil((r+1) T / CL) - 1 of the T blocks of kAP nodes
+struct Own {
+    int T, i0;
+    bool act, last;
+};
+template <int CL>
+__device__ __forceinline__ Own own_of(int N)
+{
+    Own o;
+    o.T = (N - 1) / kAP;
+    const int rank = (CL > 1) ? cluster_rank() : 0;
+    const int bs = (rank * o.T + CL - 1) / CL, be = ((rank + 1) * o.T + CL - 1) / CL;
+    const int t = bs + (int)threadIdx.x;
+    o.i0 = t * kAP;
+    o.act = t < be;
+    o.last = t == o.T - 1;
+    return o;
+}
+
+// exclusive prefix composition of affine maps x -> a x + b over threads (ascending, rank 0's
+// threads first), applied to 0 at the start: returns the b part.  Threads' own maps are (a, b).
+template <int CL>
 __device__ double scan_affine_prefix(double a, double b, ScanShared &sh)
 {
     const unsigned FULL = 0xffffffffu;
@@ -106,18 +132,26 @@ __device__ double scan_affine_prefix(double a, double b, ScanShared &sh)
             const double ap = __shfl_up_sync(FULL, A, o), bp = __shfl_up_sync(FULL, B, o);
             if (lane >= o) { B = fma(A, bp, B); A = A * ap; }
         }
-        double bw = __shfl_up_sync(FULL, B, 1);
-        if (lane == 0) bw = 0.0;
-        if (lane < kANW) sh.c[lane] = bw;
+        double bw = __shfl_up_sync(FULL, B, 1), aw = __shfl_up_sync(FULL, A, 1);
+        if (lane == 0) { bw = 0.0; aw = 1.0; }
+        if (lane < kANW) { sh.c[lane] = bw; sh.e[lane] = aw; }
+        if constexpr (CL == 2) {   // rank 0's total map to rank 1
+            if (lane == kANW - 1 && cluster_rank() == 0) st_peer(&sh.pb, B, 1);
+        }
     }
-    __syncthreads();
-    const double r = fma(aEx, sh.c[wid], bEx);
-    __syncthreads();
+    csync<CL>();
+    double r = fma(aEx, sh.c[wid], bEx);
+    if constexpr (CL == 2) {
+        if (cluster_rank() == 1) r = fma(aEx * sh.e[wid], sh.pb, r);   // the maps of rank 0 first
+    }
+    csync<CL>();
     return r;
 }
 
-// exclusive suffix composition (threads descending): the thread's map is x_left = a x_right + b;
-// returns the b part of the composition of all later threads applied to 0 at the block end
+// exclusive suffix composition (threads descending, rank 1's threads first): the thread's map is
+// x_left = a x_right + b; returns the b part of the composition of all later threads applied to
+// 0 at the end
+template <int CL>
 __device__ double scan_affine_suffix(double a, double b, ScanShared &sh)
 {
     const unsigned FULL = 0xffffffffu;
@@ -138,18 +172,25 @@ __device__ double scan_affine_suffix(double a, double b, ScanShared &sh)
             const double an = __shfl_down_sync(FULL, A, o), bn = __shfl_down_sync(FULL, B, o);
             if (lane + o < kANW) { B = fma(A, bn, B); A = A * an; }
         }
-        double bw = __shfl_down_sync(FULL, B, 1);
-        if (lane + 1 >= kANW) bw = 0.0;
-        if (lane < kANW) sh.c[lane] = bw;
+        double bw = __shfl_down_sync(FULL, B, 1), aw = __shfl_down_sync(FULL, A, 1);
+        if (lane + 1 >= kANW) { bw = 0.0; aw = 1.0; }
+        if (lane < kANW) { sh.c[lane] = bw; sh.e[lane] = aw; }
+        if constexpr (CL == 2) {   // rank 1's total map to rank 0
+            if (lane == 0 && cluster_rank() == 1) st_peer(&sh.pb, B, 0);
+        }
     }
-    __syncthreads();
-    const double r = fma(aEx, sh.c[wid], bEx);
-    __syncthreads();
+    csync<CL>();
+    double r = fma(aEx, sh.c[wid], bEx);
+    if constexpr (CL == 2) {
+        if (cluster_rank() == 0) r = fma(aEx * sh.e[wid], sh.pb, r);   // the maps of rank 1 first
+    }
+    csync<CL>();
     return r;
 }
 
-// exclusive sums over threads: prefix (threads ascending) and suffix (descending)
-template <bool kSuffix>
+// exclusive sums over threads: prefix (threads ascending) and suffix (descending), over both
+// ranks of a 2-CTA cluster
+template <bool kSuffix, int CL>
 __device__ double scan_sum(double x, ScanShared &sh)
 {
     const unsigned FULL = 0xffffffffu;
@@ -183,10 +224,17 @@ __device__ double scan_sum(double x, ScanShared &sh)
         double w = kSuffix ? __shfl_down_sync(FULL, X, 1) : __shfl_up_sync(FULL, X, 1);
         if (kSuffix ? lane + 1 >= kANW : lane == 0) w = 0.0;
         if (lane < kANW) sh.c[lane] = w;
+        if constexpr (CL == 2) {   // the total of the rank that comes first to the other
+            const int from = kSuffix ? 1 : 0;
+            if (lane == (kSuffix ? 0 : kANW - 1) && cluster_rank() == from) st_peer(&sh.pd, X, 1 - from);
+        }
     }
-    __syncthreads();
-    const double r = ex + sh.c[wid];
-    __syncthreads();
+    csync<CL>();
+    double r = ex + sh.c[wid];
+    if constexpr (CL == 2) {
+        if (cluster_rank() == (kSuffix ? 0 : 1)) r += sh.pd;
+    }
+    csync<CL>();
     return r;
 }
 
@@ -295,13 +343,15 @@ __device__ __forceinline__ Scr scratch_of(double *base, int Nmax)
 // Constraint solve on the stage slice (yP, yQ) (node N-1 and all nodes written, zero at N-1);
 // stores M, E = e^{-delta}, F = A E on nodes and AL = alpha on cells; computes the fluxes into
 // scr.f, scr.u and, if kP != nullptr, the stage derivative (kP, kQ) on the thread's nodes.
+template <int CL>
 __device__ void stage_forward(const double *yP, const double *yQ, double *M, double *E, double *F, double *AL,
                               const Scr &scr, double *kP, double *kQ, const InstDesc &d, const GeoTab &g,
                               const double *tab, ScanShared &sh, bool with_rhs)
 {
-    const int N = d.N, Tn = (N - 1) / kAP, tid = threadIdx.x;
-    const bool act = tid < Tn, last = tid == Tn - 1;
-    const int i0 = tid * kAP;
+    const int N = d.N;
+    const Own o = own_of<CL>(N);
+    const bool act = o.act, last = o.last;
+    const int i0 = o.i0;
     double De[kAP], al[kAP], be[kAP];
     double aT = 1.0, bT = 0.0, SD = 0.0;
     if (act) {
@@ -316,8 +366,8 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
             else { bT = fma(cf.al, bT, cf.be); aT *= cf.al; SD += cf.De; }
         }
     }
-    const double mstart = scan_affine_prefix(aT, bT, sh);
-    const double dend = scan_sum<true>(SD, sh);
+    const double mstart = scan_affine_prefix<CL>(aT, bT, sh);
+    const double dend = scan_sum<true, CL>(SD, sh);
     double g1 = 0.0, g2 = 0.0;
     if (act) {
         double dc = dend;
@@ -347,9 +397,9 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
             scr.f[N - 1] = 0.0;
         }
     }
-    __syncthreads();
+    csync<CL>();
     if (act && last) scr.u[N - 1] = (4.0 * scr.u[N - 2] - scr.u[N - 3]) * (1.0 / 3.0);
-    __syncthreads();
+    csync<CL>();
     if (!with_rhs || !act) return;
 #pragma unroll
     for (int k = 0; k < kAP; ++k) {
@@ -378,13 +428,15 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
 // ------------------------------------------------------------------ constraint transpose
 // Given Abar-derived mbar (scr.mb, nodes) and delta_bar (scr.dlb, nodes), accumulate into
 // (yb P, yb Q) += d/d(yP, yQ) on the thread's nodes.
+template <int CL>
 __device__ void constraint_backward(const double *yP, const double *yQ, const double *M, const double *AL,
                                     const Scr &scr, double *ybP, double *ybQ, const InstDesc &d,
                                     const GeoTab &g, ScanShared &sh)
 {
-    const int N = d.N, Tn = (N - 1) / kAP, tid = threadIdx.x;
-    const bool act = tid < Tn;
-    const int i0 = tid * kAP;
+    const int N = d.N;
+    const Own o = own_of<CL>(N);
+    const bool act = o.act;
+    const int i0 = o.i0;
     // mu_c = alpha_c mu_{c+1} + mbar_c, mu_{N-1} = 0: suffix affine scan
     double aT = 1.0, bT = 0.0, SP = 0.0;
     if (act) {
@@ -398,8 +450,8 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
 #pragma unroll
         for (int k = 0; k < kAP; ++k) SP += scr.dlb[i0 + k];
     }
-    const double mu_end = scan_affine_suffix(aT, bT, sh);   // mu at node i0 + P
-    const double dpre = scan_sum<false>(SP, sh);             // sum of delta_bar over nodes < i0
+    const double mu_end = scan_affine_suffix<CL>(aT, bT, sh);   // mu at node i0 + P
+    const double dpre = scan_sum<false, CL>(SP, sh);             // sum of delta_bar over nodes < i0
     if (act) {
         double mu = mu_end;
         double mun[kAP];   // mu at node c+1 for each own cell
@@ -426,7 +478,7 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
 #pragma unroll
         for (int k = 0; k < kAP; ++k) scr.fb[i0 + k] = n0s[k];
     }
-    __syncthreads();
+    csync<CL>();
     if (act) {
 #pragma unroll
         for (int k = 0; k < kAP; ++k) {
@@ -443,19 +495,21 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
             ybQ[j] += fma(2.0 * yQ[j], rb, pQ);
         }
     }
-    __syncthreads();
+    csync<CL>();
 }
 
 // ------------------------------------------------------------------ stage backward
 // ybar = R'(y)^T kbar with kbar in (scr.vP, scr.vQ) (already restricted to rows), written to
 // (ybP, ybQ) (overwritten) on the thread's nodes.
+template <int CL>
 __device__ void stage_backward(const double *yP, const double *yQ, const double *M, const double *E,
                                const double *F, const double *AL, const Scr &scr, double *ybP, double *ybQ,
                                const InstDesc &d, const GeoTab &g, ScanShared &sh)
 {
-    const int N = d.N, Tn = (N - 1) / kAP, tid = threadIdx.x;
-    const bool act = tid < Tn, last = tid == Tn - 1;
-    const int i0 = tid * kAP;
+    const int N = d.N;
+    const Own o = own_of<CL>(N);
+    const bool act = o.act, last = o.last;
+    const int i0 = o.i0;
     const double *vP = scr.vP, *vQ = scr.vQ;
     if (act) {
         // iT12-weighted Pi-dot sensitivities for the u stencil (zero at rows 0 and N-1)
@@ -463,7 +517,7 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
         for (int k = 0; k < kAP; ++k) scr.pb[i0 + k] = __ldg(g.iT12 + i0 + k) * vQ[i0 + k];
         if (last) scr.pb[N - 1] = 0.0;
     }
-    __syncthreads();
+    csync<CL>();
     const double *v2 = scr.pb;
     auto Dr = [&](const double *v, int x) {   // raw 4th-order difference of a row-restricted array
         return (rv(v, N, x - 2) - rv(v, N, x + 2)) + 8.0 * (rv(v, N, x + 1) - rv(v, N, x - 1));
@@ -509,47 +563,59 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
         }
         if (last) { scr.dlb[N - 1] = 0.0; scr.mb[N - 1] = 0.0; }
     }
-    __syncthreads();
-    constraint_backward(yP, yQ, M, AL, scr, ybP, ybQ, d, g, sh);
+    csync<CL>();
+    constraint_backward<CL>(yP, yQ, M, AL, scr, ybP, ybQ, d, g, sh);
 }
 
 // ------------------------------------------------------------------ the kernel
+template <int CL>
 __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
 {
+    static_assert(CL == 1 || CL == 2, "one CTA or a 2-CTA cluster per instance");
     __shared__ ScanShared sh;
     __shared__ double s_tab[kExpTableSize];
     __shared__ int s_item;
     const int tid = threadIdx.x;
+    const int rank = (CL > 1) ? cluster_rank() : 0;
     for (int i = tid; i < kExpTableSize; i += kANT) s_tab[i] = a.exptab[i];
-    const Scr scr = scratch_of(a.scratch + (size_t)blockIdx.x * kScrArrays * a.Nmax, a.Nmax);
+    csync<CL>();   // every CTA of the cluster has started before any remote shared-memory store
+    // one scratch region per CTA (CL = 1) or per cluster (CL = 2: shared by both ranks)
+    const Scr scr = scratch_of(a.scratch + (size_t)(blockIdx.x / CL) * kScrArrays * a.Nmax, a.Nmax);
     const double cst[4] = {0.0, 0.5, 0.5, 1.0};
     const double wst[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(a.queue, 1);
-        __syncthreads();
+        if (tid == 0 && rank == 0) {
+            const int v = atomicAdd(a.queue, 1);
+            s_item = v;
+            if constexpr (CL == 2) st_peer(&s_item, v, 1);
+        }
+        csync<CL>();
         const int q = s_item;
-        __syncthreads();
+        csync<CL>();
         if (q >= a.nwork) break;
         const int b = a.order[q];
         const InstDesc d = a.desc[b];
         const GeoTab g = a.geo[d.geo];
-        const int N = d.N, Tn = (N - 1) / kAP;
-        const bool act = tid < Tn;
-        const int i0 = tid * kAP;
+        const int N = d.N;
+        const Own own = own_of<CL>(N);
+        const bool act = own.act;
+        const int i0 = own.i0;
         double *lamP = a.lamP + d.off, *lamQ = a.lamQ + d.off;
 
         if (a.mode == kAdjProject) {
-            const EigTab t = a.eig[d.geo];
-            const int lane = tid & 31, warp = tid >> 5;
-            for (int j = warp; j < a.J; j += kANW) {
-                double s = 0.0;
-                for (int i = lane; i < N - 1; i += 32) s = fma(lamQ[i], __ldg(t.e + (size_t)j * N + i), s);
+            if (rank == 0) {
+                const EigTab t = a.eig[d.geo];
+                const int lane = tid & 31, warp = tid >> 5;
+                for (int j = warp; j < a.J; j += kANW) {
+                    double s = 0.0;
+                    for (int i = lane; i < N - 1; i += 32) s = fma(lamQ[i], __ldg(t.e + (size_t)j * N + i), s);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) a.dJda[(size_t)b * a.J + j] = s;
+                    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    if (lane == 0) a.dJda[(size_t)b * a.J + j] = s;
+                }
             }
-            __syncthreads();
+            csync<CL>();
             continue;
         }
 
@@ -566,15 +632,15 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
             if (act) {
 #pragma unroll
                 for (int k = 0; k < kAP; ++k) { yP[i0 + k] = sP[i0 + k]; yQ[i0 + k] = sQ[i0 + k]; }
-                if (tid == Tn - 1) { yP[N - 1] = 0.0; yQ[N - 1] = 0.0; }
+                if (own.last) { yP[N - 1] = 0.0; yQ[N - 1] = 0.0; }
             }
-            __syncthreads();
-            stage_forward(yP, yQ, M, E, F, AL, scr, nullptr, nullptr, d, g, s_tab, sh, false);
-            // A = F / E on interior nodes; weights h tan^2 sqrt(A); projections per mode
+            csync<CL>();
+            stage_forward<CL>(yP, yQ, M, E, F, AL, scr, nullptr, nullptr, d, g, s_tab, sh, false);
+            // A = F / E on interior nodes; weights h tan^2 sqrt(A); projections per mode (rank 0)
             const EigTab t = a.eig[d.geo];
             const double h = 1.0 / (12.0 * d.c12);
             const int lane = tid & 31, warp = tid >> 5;
-            for (int j = warp; j < a.J; j += kANW) {
+            for (int j = warp; j < (rank == 0 ? a.J : 0); j += kANW) {
                 double sp = 0.0, sf = 0.0;
                 for (int i = 1 + lane; i < N - 1; i += 32) {
                     const double A = fma(-M[i], __ldg(g.K + i), 1.0);
@@ -593,7 +659,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                     scr.vQ[j] = 2.0 * sf * Eb / (om * om);  // Phi_j bar
                 }
             }
-            __syncthreads();
+            csync<CL>();
             if (act) {
 #pragma unroll
                 for (int k = 0; k < kAP; ++k) {
@@ -616,10 +682,10 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                     scr.mb[i] = -Ab * __ldg(g.K + i);
                     scr.dlb[i] = dlb;
                 }
-                if (tid == Tn - 1) { scr.mb[N - 1] = 0.0; scr.dlb[N - 1] = 0.0; }
+                if (own.last) { scr.mb[N - 1] = 0.0; scr.dlb[N - 1] = 0.0; }
             }
-            __syncthreads();
-            constraint_backward(yP, yQ, M, AL, scr, scr.ybP, scr.ybQ, d, g, sh);
+            csync<CL>();
+            constraint_backward<CL>(yP, yQ, M, AL, scr, scr.ybP, scr.ybQ, d, g, sh);
             if (act) {
 #pragma unroll
                 for (int k = 0; k < kAP; ++k) {
@@ -627,7 +693,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                     lamQ[i0 + k] += scr.ybQ[i0 + k];
                 }
             }
-            __syncthreads();
+            csync<CL>();
             continue;
         }
 
@@ -638,7 +704,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
 #pragma unroll
             for (int k = 0; k < kAP; ++k) { scr.uP[i0 + k] = ckP[i0 + k]; scr.uQ[i0 + k] = ckQ[i0 + k]; }
         }
-        __syncthreads();
+        csync<CL>();
         for (int n = 0; n < a.nsteps; ++n) {
             for (int s = 0; s < 4; ++s) {
                 double *yP = slot(n, s, 0), *yQ = slot(n, s, 1);
@@ -646,10 +712,10 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
 #pragma unroll
                     for (int k = 0; k < kAP; ++k) { yP[i0 + k] = scr.uP[i0 + k]; yQ[i0 + k] = scr.uQ[i0 + k]; }
                 }
-                if (act && tid == Tn - 1) { yP[N - 1] = 0.0; yQ[N - 1] = 0.0; }
-                __syncthreads();
+                if (act && own.last) { yP[N - 1] = 0.0; yQ[N - 1] = 0.0; }
+                csync<CL>();
                 double *kP = scr.vP, *kQ = scr.vQ;   // stage derivative (phase F use of the slots)
-                stage_forward(yP, yQ, slot(n, s, 2), slot(n, s, 3), slot(n, s, 4), slot(n, s, 5), scr, kP, kQ,
+                stage_forward<CL>(yP, yQ, slot(n, s, 2), slot(n, s, 3), slot(n, s, 4), slot(n, s, 5), scr, kP, kQ,
                               d, g, s_tab, sh, true);
                 if (act) {
 #pragma unroll
@@ -666,13 +732,13 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                         }
                     }
                 }
-                __syncthreads();
+                csync<CL>();
             }
             if (act) {
 #pragma unroll
                 for (int k = 0; k < kAP; ++k) { scr.uP[i0 + k] = scr.aP[i0 + k]; scr.uQ[i0 + k] = scr.aQ[i0 + k]; }
             }
-            __syncthreads();
+            csync<CL>();
         }
 
         }   // phase F
@@ -700,10 +766,10 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                         scr.vP[i] = (i == 0) ? 0.0 : kb;   // Phi-dot(0) is identically zero
                         scr.vQ[i] = kq;
                     }
-                    if (tid == Tn - 1) { scr.vP[N - 1] = 0.0; scr.vQ[N - 1] = 0.0; }
+                    if (own.last) { scr.vP[N - 1] = 0.0; scr.vQ[N - 1] = 0.0; }
                 }
-                __syncthreads();
-                stage_backward(slot(n, s, 0), slot(n, s, 1), slot(n, s, 2), slot(n, s, 3), slot(n, s, 4),
+                csync<CL>();
+                stage_backward<CL>(slot(n, s, 0), slot(n, s, 1), slot(n, s, 2), slot(n, s, 3), slot(n, s, 4),
                                slot(n, s, 5), scr, scr.ybP, scr.ybQ, d, g, sh);
                 if (act) {
 #pragma unroll
@@ -712,7 +778,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                         lamQ[i0 + k] += scr.ybQ[i0 + k];
                     }
                 }
-                __syncthreads();
+                csync<CL>();
             }
         }
     }

@@ -74,6 +74,8 @@ struct adscl_ctx {
     std::string dev_name;
     double t_prev = 0.0;               // t_end of the last evolve call since the initial data
     int scheme = 0, reint = 0;         // ADSCL_SCHEME_*, A re-integration interval (evolved A)
+    int adj_cl = 1;                    // CTAs per instance of the adjoint kernel
+    int adj_units = 0;                 // co-resident adjoint units (CTAs or 2-CTA clusters)
     double *d_A = nullptr;             // packed evolved A (evolved-A schemes)
     double *d_ea_block = nullptr;      // K2, wsim per grid size (evolved-A schemes)
     EaGeo *d_eageo = nullptr;
@@ -640,7 +642,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
         !std::isfinite(cfg->collapse_threshold) || !(cad > 0.0) || cfg->spec_J < 0 ||
         cfg->spec_J > 64 || cfg->ckpt_every < 0 || cfg->max_device_iters < 0 ||
         cfg->scheme < ADSCL_SCHEME_RK4 || cfg->scheme > ADSCL_SCHEME_FIXED_METRIC_RK3 ||
-        cfg->a_reint_every < 0)
+        cfg->a_reint_every < 0 || cfg->adjoint_ctas < 0 || cfg->adjoint_ctas > 2)
         return ADSCL_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
@@ -662,6 +664,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     ctx->direct_launch = cfg->direct_launch;
     ctx->scheme = cfg->scheme;
     ctx->reint = cfg->a_reint_every;
+    ctx->adj_cl = cfg->adjoint_ctas;   // 0: chosen at the first adscl_grad
     ctx->stream = (cudaStream_t)cfg->stream;
     *out = ctx;
 
@@ -991,12 +994,28 @@ __global__ void drift_kernel(const double *E0, const double *ET, int B, int J, d
 // (the two lanes may run at the same time)
 adscl_status launch_adjoint(adscl_ctx *ctx, AdjArgs &a, cudaStream_t sm, int lane)
 {
-    const int grid = std::min(ctx->B, ctx->num_sms);
+    const int regions = std::min(ctx->B, ctx->num_sms);   // scratch regions per lane
+    const int units = std::min(ctx->B, ctx->adj_units);
     CK(cudaMemsetAsync(ctx->d_adj_queue + lane, 0, sizeof(int32_t), sm));
     a.queue = ctx->d_adj_queue + lane;
-    a.scratch = ctx->d_adj_scr + (size_t)lane * grid * kScrArrays * ctx->Nmax;
-    adjoint_kernel<<<grid, kANT, 0, sm>>>(a);
-    CK(cudaGetLastError());
+    a.scratch = ctx->d_adj_scr + (size_t)lane * regions * kScrArrays * ctx->Nmax;
+    if (ctx->adj_cl == 2) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(2 * units, 1, 1);
+        cfg.blockDim = dim3(kANT, 1, 1);
+        cfg.stream = sm;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, adjoint_kernel<2>, a));
+    } else {
+        adjoint_kernel<1><<<units, kANT, 0, sm>>>(a);
+        CK(cudaGetLastError());
+    }
     ctx->launches += 1;
     return ADSCL_OK;
 }
@@ -1015,6 +1034,29 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     for (int n : ctx->N)
         if ((n - 1) / kAP > kANT) return fail(ctx, ADSCL_EUNSUPPORTED, "grad supports N <= %d", kAP * kANT + 1);
     const int B = ctx->B, Jm = ctx->spec_J, seg = ctx->ckpt;
+    if (ctx->adj_units == 0) {   // CTAs per instance and co-resident units of the adjoint kernel
+        if (ctx->adj_cl == 0) ctx->adj_cl = (2 * B <= ctx->num_sms) ? 2 : 1;
+        if (ctx->adj_cl == 2) {
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(2 * (ctx->num_sms / 2), 1, 1);
+            cfg.blockDim = dim3(kANT, 1, 1);
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, adjoint_kernel<2>, &cfg) != cudaSuccess || nc < 1) {
+                (void)cudaGetLastError();
+                ctx->adj_cl = 1;
+            } else {
+                ctx->adj_units = nc;
+            }
+        }
+        if (ctx->adj_cl == 1) ctx->adj_units = ctx->num_sms;
+    }
     const size_t total = (size_t)ctx->total;
     long long nT = 0;
     for (const InstDesc &d : ctx->h_desc) nT = std::max(nT, (long long)std::ceil(T / d.dt - 1e-9));

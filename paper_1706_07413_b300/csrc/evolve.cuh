@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
     int rank = 0;
     if constexpr (CL > 1) rank = cluster_rank();
     for (int i = tid; i < kExpTableSize; i += NT) s_tab[i] = a.exptab[i];
+    csync<CL>();   // every CTA of the cluster has started before any remote shared-memory store
 
     for (;;) {
         // ------------------------------------------------------------ take a ticket

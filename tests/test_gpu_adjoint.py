@@ -84,3 +84,26 @@ def test_adjoint_refinement_reduces_drift_of_qp_seeds(ad):
     h = hist.numpy()
     assert np.all(np.diff(h, axis=0) <= 0.0)
     assert np.all(h[-1] < h[0])
+
+
+@pytest.mark.parametrize("N", [257, 1025])
+def test_one_and_two_cta_adjoint_agree(ad, orc, N):
+    """The adjoint kernel on one CTA per instance and on a 2-CTA cluster (node blocks split between
+    the two CTAs, scan totals carried across) gives the same gradient up to the rounding of the
+    re-associated scans; both match the oracle's adjoint."""
+    B, K, Jm = 4, 6, 8
+    rng = np.random.default_rng(11)
+    a = rng.uniform(0.0, 0.8, (B, K)) * np.exp(-np.arange(K) / 2.0)
+    out = {}
+    for ctas in (1, 2):
+        s = ad.Solver([N] * B, ko_sigma=0.5, spec_J=Jm, ckpt_every=9, adjoint_ctas=ctas)
+        dt, _ = s.clock()
+        out[ctas] = s.grad(a, 30 * dt[0])
+        s.close()
+    J1, g1 = out[1]
+    J2, g2 = out[2]
+    assert np.abs(J1 - J2).max() <= 1e-12 * np.abs(J1).max()
+    assert np.abs(g1 - g2).max() <= 1e-11 * np.abs(g1).max()
+    Jo, go = orc.grad(a[2], N, 30, dt[0], sigma=0.5, Jm=Jm)
+    assert abs(J2[2] - Jo) <= 1e-10 * abs(Jo)
+    assert np.abs(g2[2] - go).max() <= 1e-9 * np.abs(go).max()
