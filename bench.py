@@ -59,8 +59,8 @@ REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
 # DRAM bytes (read + write) of one timed evolve_kernel launch of the amplitude scan, from an ncu
 # capture of this script (profiles/evolve_kernel_amp_scan.md); reported only while the kernel
 # source and the kernel shape are the ones the counters were taken on.
-TRAFFIC = {"kernel_sha256": "fd9adabd9a7828a26ff6e7672fdc7d6f1b4960ca15d10e16c9303bd41732dec8",
-           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17847552 + 227662336}
+TRAFFIC = {"kernel_sha256": "709f821611336044da65fe8dfaf629422dddb2c248b6f95201f94cb3e4f644fc",
+           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17725440 + 223519488}
 
 
 def kernel_digest():
