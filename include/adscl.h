@@ -44,7 +44,7 @@ typedef enum {
     ADSCL_ECUDA = 3,        /* a CUDA runtime call failed (message names it) */
     ADSCL_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
     ADSCL_ENONFINITE = 5,   /* input fields contain NaN or Inf */
-    ADSCL_EUNSUPPORTED = 6, /* valid request this build does not provide */
+    ADSCL_EUNSUPPORTED = 6, /* valid request the library does not provide */
     ADSCL_ECAPACITY = 7     /* request larger than the fixed capacity of adscl_evolve_noalloc */
 } adscl_status;
 
@@ -93,7 +93,7 @@ typedef struct {
     void *stream;                /* cudaStream_t for all work; NULL = the legacy default stream */
 } adscl_config;
 
-/* Largest grid size N one instance may use in this build: 32769.  Grids up to 4097 run on one
+/* Largest grid size N one instance may use with this library: 32769.  Grids up to 4097 run on one
  * CTA (one SM) per instance, larger ones on a thread-block cluster of 2, 4 or 8 CTAs sharing
  * the instance through distributed shared memory. */
 int32_t adscl_max_points(void);
