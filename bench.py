@@ -270,6 +270,41 @@ def autotune_report(stream, local):
     return out
 
 
+def paper_configs_report(stream, local, steps=64):
+    """The configurations the paper times (Sec. IV, Tables I and II), one instance each: N = 32769
+    with A and delta dynamical (the paper's scheme: A evolved by Eq. (eq:adot), re-integrated
+    every 64 steps, SSP-RK3; and the classic RK4 with A integrated every stage), and the fixed
+    metric A = 1, delta = 0 (the paper's Table II used N = 65537; 32769 is this solver's largest
+    grid).  A single instance occupies one 8-CTA cluster, i.e. 8 of the SMs."""
+    import torch
+    from paper_1706_07413_b300 import adscl
+    N = 32769
+    out = {}
+    for name, scheme, stages, reint in (("table1_evolved_A_rk3", 1, 3, 64), ("table1_rk4_constraint_A", 0, 4, 0),
+                                        ("table2_fixed_metric_rk3", 3, 3, 0)):
+        sol = adscl.Solver([N], ko_sigma=SIGMA_KO, collapse_threshold=THETA, device=local,
+                           stream=stream.cuda_stream, scheme=scheme, a_reint_every=reint)
+        sol.set_initial(np.zeros(N), W.gaussian_pi(N, 40.0, 1.0 / 16))
+        dt, _ = sol.clock()
+        sol.evolve(4 * dt[0])
+        torch.cuda.synchronize()
+        _, s0 = sol.clock()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            sol.evolve((4 + steps) * dt[0])
+            e1.record(stream)
+        torch.cuda.synchronize()
+        _, s1 = sol.clock()
+        ms = e0.elapsed_time(e1)
+        n = int(s1[0] - s0[0])
+        out[name] = {"N": N, "steps": n, "ms_per_step": ms / max(n, 1),
+                     "point_substeps_per_s": N * stages * n / (ms / 1e3),
+                     "wall_s_per_unit_time": ms / max(n, 1) / 1e3 / float(dt[0])}
+        sol.close()
+    return out
+
+
 def run_reference(args):
     """The reference arm: the sequential FP64 CPU oracle on the host cores."""
     ws, rank, _ = _dist()
@@ -430,6 +465,7 @@ def main():
         v = side_rate(oi, stream, local, 128, flush, substeps=3, scheme=adscl.SCHEME_EVOLVED_A_RK3,
                       a_reint_every=64)
         others["autotune"] = autotune_report(stream, local)
+        others["paper_configs"] = paper_configs_report(stream, local)
         others["amp_scan_evolved_A_rk3"] = {
             "value": v, "unit": UNIT, "rk_steps": 128,
             "workload": od + "; evolved-A scheme, SSP-RK3, A re-integrated every 64 steps",

@@ -124,8 +124,6 @@ struct adscl_ctx {
     int32_t *d_order = nullptr;
     double *d_out = nullptr;      // 3 B doubles: t_reached, t_c, mass
     int32_t *d_outs = nullptr;    // B statuses
-    int stride = 0;
-    size_t smem = 0;
 
     int64_t launches = 0;
     std::string err;
@@ -186,7 +184,79 @@ double step_for(int N, double cfl, double cadence)
     return cadence / std::ceil(cadence / (cfl * h));
 }
 
-// co-resident units (CTAs or clusters) of shape id with dynamic shared memory smem
+// the evolved-A / fixed-metric kernel of cluster size CL: its function pointer
+template <bool FIXED>
+const void *ea_kernel_of(int CL)
+{
+    switch (CL) {
+    case 1: return (const void *)evolve_ea_kernel<kP, kNT, FIXED, 1>;
+    case 2: return (const void *)evolve_ea_kernel<kP, kNT, FIXED, 2>;
+    case 4: return (const void *)evolve_ea_kernel<kP, kNT, FIXED, 4>;
+    default: return (const void *)evolve_ea_kernel<kP, kNT, FIXED, 8>;
+    }
+}
+
+template <bool FIXED, int CL>
+cudaError_t ea_launch_t(const EaArgs &ea, int units, size_t smem, int stride, cudaStream_t sm)
+{
+    if constexpr (CL == 1) {
+        evolve_ea_kernel<kP, kNT, FIXED, 1><<<units, kNT, smem, sm>>>(ea, stride);
+        return cudaGetLastError();
+    } else {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(CL * units, 1, 1);
+        cfg.blockDim = dim3(kNT, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = sm;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, evolve_ea_kernel<kP, kNT, FIXED, CL>, ea, stride);
+    }
+}
+
+template <bool FIXED>
+cudaError_t ea_launch(const EaArgs &ea, int CL, int units, size_t smem, int stride, cudaStream_t sm)
+{
+    switch (CL) {
+    case 1: return ea_launch_t<FIXED, 1>(ea, units, smem, stride, sm);
+    case 2: return ea_launch_t<FIXED, 2>(ea, units, smem, stride, sm);
+    case 4: return ea_launch_t<FIXED, 4>(ea, units, smem, stride, sm);
+    default: return ea_launch_t<FIXED, 8>(ea, units, smem, stride, sm);
+    }
+}
+
+// co-resident units of the evolved-A / fixed-metric kernel of cluster size CL
+cudaError_t ea_max_units(bool fixed, int CL, size_t smem, int num_sms, int *units)
+{
+    const void *fn = fixed ? ea_kernel_of<true>(CL) : ea_kernel_of<false>(CL);
+    *units = 0;
+    if (CL == 1) {
+        int per_sm = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kNT, smem);
+        *units = per_sm * num_sms;
+        return e;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(CL * (num_sms / CL), 1, 1);
+    cfg.blockDim = dim3(kNT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(units, fn, &cfg);
+}
+
+// co-resident units (CTAs or clusters) of shape id with dynamic shared memory smem (for the
+// context's scheme: the evolved-A / fixed-metric kernels run the default shapes)
 adscl_status max_units(adscl_ctx *ctx, int id, size_t smem, int *units)
 {
     auto it = ctx->units_cache.find({id, smem});
@@ -195,7 +265,9 @@ adscl_status max_units(adscl_ctx *ctx, int id, size_t smem, int *units)
         return ADSCL_OK;
     }
     int u = 0;
-    const cudaError_t e = shape_max_units(id, smem, ctx->num_sms, &u);
+    const cudaError_t e = (ctx->scheme == ADSCL_SCHEME_RK4)
+        ? shape_max_units(id, smem, ctx->num_sms, &u)
+        : ea_max_units(ctx->scheme == ADSCL_SCHEME_FIXED_METRIC_RK3, kShapes[id].CL, smem, ctx->num_sms, &u);
     if (e != cudaSuccess || u < 1)
         return fail(ctx, ADSCL_EUNSUPPORTED, "shape (%d, %d, %d) of the evolve kernel does not fit (%s)",
                     kShapes[id].P, kShapes[id].NT, kShapes[id].CL, cudaGetErrorString(e));
@@ -242,28 +314,6 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
     if ((long long)nwork * rounds > 0x7ffffff0LL)
         return fail(ctx, ADSCL_EINVAL, "t_end too large for one launch (%lld rounds)", rounds);
     a.max_rounds = (int32_t)rounds;
-    if (ctx->scheme != ADSCL_SCHEME_RK4) {   // evolved A: one CTA per instance (N <= 4097)
-        EaArgs ea{};
-        ea.e = a;
-        ea.e.order = ctx->d_order + first;
-        ea.e.nwork = nwork;
-        ea.e.ctl = ctx->d_ctl + first;
-        ea.e.rounds = ctx->d_rounds + first;
-        ea.eg = ctx->d_eageo;
-        ea.A = ctx->d_A;
-        ea.order = (ctx->scheme == ADSCL_SCHEME_EVOLVED_A_RK2) ? 2 : 3;
-        ea.reint = ctx->reint;
-        const int units = std::min(nwork, ctx->num_sms);
-        queue_init_kernel<<<(nwork + 255) / 256, 256, 0, sm>>>(ea.e.ctl, ea.e.rounds, nwork, units);
-        CK(cudaGetLastError());
-        if (ctx->scheme == ADSCL_SCHEME_FIXED_METRIC_RK3)
-            evolve_ea_kernel<kP, kNT, true><<<units, kNT, ctx->smem, sm>>>(ea, ctx->stride);
-        else
-            evolve_ea_kernel<kP, kNT, false><<<units, kNT, ctx->smem, sm>>>(ea, ctx->stride);
-        CK(cudaGetLastError());
-        ctx->launches += 2;
-        return ADSCL_OK;
-    }
     // runs of equal shape, with each run's largest grid, shared memory and co-resident units
     std::vector<int> starts, shp, nmax, units_max;
     std::vector<size_t> smem;
@@ -350,7 +400,20 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
         a.rounds = ctx->d_rounds + first + i;
         queue_init_kernel<<<(a.nwork + 255) / 256, 256, 0, gs>>>(a.ctl, a.rounds, a.nwork, units_of[g]);
         CK(cudaGetLastError());
-        CK(shape_launch(shp[g], a, units_of[g], smem[g], shape_stride(shp[g], nmax[g]), gs));
+        if (ctx->scheme == ADSCL_SCHEME_RK4) {
+            CK(shape_launch(shp[g], a, units_of[g], smem[g], shape_stride(shp[g], nmax[g]), gs));
+        } else {
+            EaArgs ea{};
+            ea.e = a;
+            ea.eg = ctx->d_eageo;
+            ea.A = ctx->d_A;
+            ea.order = (ctx->scheme == ADSCL_SCHEME_EVOLVED_A_RK2) ? 2 : 3;
+            ea.reint = ctx->reint;
+            const int cl = kShapes[shp[g]].CL, st = shape_stride(shp[g], nmax[g]);
+            CK(ctx->scheme == ADSCL_SCHEME_FIXED_METRIC_RK3
+                   ? ea_launch<true>(ea, cl, units_of[g], smem[g], st, gs)
+                   : ea_launch<false>(ea, cl, units_of[g], smem[g], st, gs));
+        }
         ctx->launches += 2;
     }
     for (int g = 0; g < ng - 1; ++g) {
@@ -678,9 +741,6 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
         ctx->Nmax = std::max(ctx->Nmax, ctx->N[b]);
     }
 
-    if (ctx->scheme != ADSCL_SCHEME_RK4 && ctx->Nmax > kMaxPoints1)
-        return fail(ctx, ADSCL_EUNSUPPORTED, "the evolved-A and fixed-metric schemes support N <= %d",
-                    kMaxPoints1);
 
     // geometry tables, one per distinct N
     std::map<int, int> geo_of;
@@ -799,25 +859,20 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     CK(cudaMalloc(&ctx->d_out, 3 * (size_t)ctx->B * sizeof(double)));
     CK(cudaMalloc(&ctx->d_outs, (size_t)ctx->B * sizeof(int32_t)));
 
-    // the evolved-A kernels: one CTA of 512 threads per instance (N <= 4097)
-    ctx->stride = field_stride<kP>(std::min(ctx->Nmax, kMaxPoints1));
-    ctx->smem = (size_t)6 * ctx->stride * sizeof(double);
     // the attribute is per kernel, not per context: always raise it to the largest grid
     const size_t smem_max = (size_t)6 * field_stride<kP>(kMaxPoints1) * sizeof(double);
     CK(shapes_set_attributes());
-    CK(cudaFuncSetAttribute(evolve_ea_kernel<kP, kNT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_max));
-    CK(cudaFuncSetAttribute(evolve_ea_kernel<kP, kNT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_max));
+    for (int cl = 1; cl <= kMaxCluster; cl *= 2) {
+        CK(cudaFuncSetAttribute(ea_kernel_of<false>(cl), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+        CK(cudaFuncSetAttribute(ea_kernel_of<true>(cl), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    }
     // default kernel shapes; every shape in use must fit the device
     ctx->shape_of.resize(ctx->B);
     for (int b = 0; b < ctx->B; ++b) {
         ctx->shape_of[b] = default_shape(ctx->N[b]);
         int u = 0;
-        if (ctx->scheme == ADSCL_SCHEME_RK4) {
-            adscl_status s = max_units(ctx, ctx->shape_of[b], shape_smem(ctx->shape_of[b], ctx->N[b]), &u);
-            if (s != ADSCL_OK) return s;
-        }
+        adscl_status s = max_units(ctx, ctx->shape_of[b], shape_smem(ctx->shape_of[b], ctx->N[b]), &u);
+        if (s != ADSCL_OK) return s;
     }
     {
         cudaDeviceProp prop{};
@@ -1305,6 +1360,8 @@ adscl_status adscl_set_shape(adscl_ctx *ctx, int32_t N, int32_t P, int32_t NT, i
     const int id = shape_index(P, NT, CL);
     if (id < 0) return fail(ctx, ADSCL_EINVAL, "shape (%d, %d, %d) is not built", P, NT, CL);
     if (!shape_fits(id, N)) return fail(ctx, ADSCL_EINVAL, "shape (%d, %d, %d) does not fit N = %d", P, NT, CL, N);
+    if (ctx->scheme != ADSCL_SCHEME_RK4 && id != default_shape(N))
+        return fail(ctx, ADSCL_EINVAL, "the evolved-A and fixed-metric schemes run the default shapes");
     int u = 0;
     s = max_units(ctx, id, shape_smem(id, N), &u);
     if (s != ADSCL_OK) return s;

@@ -6,7 +6,9 @@
 //   y^{(s+1)} = a_s y_n + b_s (y^{(s)} + dt L(y^{(s)})),
 //   order 2: (a, b) = (0, 1), (1/2, 1/2);  order 3: (0, 1), (3/4, 1/4), (1/3, 2/3).
 //
-// One CTA per instance (N <= P * NT + 1), the layout and the ticket queue of evolve_kernel.
+// One CTA per instance (N <= P * NT + 1) or a cluster of CL = 2, 4, 8 CTAs (N <= CL * P * NT + 1),
+// with the layout, the ticket queue and the cluster protocol of evolve_kernel (halos, scan carries
+// and slice diagnostics through distributed shared memory; control decisions by rank 0).
 // Per stage:
 //   1. cell data: the Simpson increments of delta (and, at a re-integration slice, the affine
 //      maps of the mass function, as in evolve_kernel);
@@ -45,10 +47,11 @@ struct EaArgs {
     int32_t reint;       // re-integrate A from Eq. (eq:aprime) at slices n % reint == 0 (0: never)
 };
 
-template <int P, int NT, bool FIXED = false>
+template <int P, int NT, bool FIXED = false, int CL = 1>
 __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
 {
     static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
+    static_assert(CL == 1 || CL == 2 || CL == 4 || CL == 8, "cluster of 1, 2, 4 or 8 CTAs");
     constexpr int NW = NT / 32;
     constexpr unsigned FULL = 0xffffffffu;
     const EvolveArgs &a = ea.e;
@@ -57,17 +60,23 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
     double *bufB0 = smem + 2 * stride, *bufB1 = smem + 3 * stride;  // next stage Phi, Pi
     double *sF = smem + 4 * stride, *sU = smem + 5 * stride;        // alpha/beta, then f/u
     __shared__ double s_tab[kExpTableSize];
-    __shared__ double wAl[NW], wBe[NW], wDe[NW], cM[NW], cD[NW], wMs[NW];
-    __shared__ long long wMin[NW];
-    __shared__ double s_d0;
-    __shared__ int s_cmd, s_q, s_r, s_leave;
+    __shared__ double wAl[NW], wBe[NW], wDe[NW], cM[NW], cMa[NW], cD[NW], wMs[NW];
+    __shared__ long long wMin[NW], wMinP[CL * NW];
+    __shared__ double wMsP[CL * NW];
+    __shared__ double s_d0, s_cA[CL], s_cB[CL], s_cD[CL];
+    __shared__ int s_cmd, s_q, s_r, s_leave, s_status;
+    __shared__ long long s_step;
+    __shared__ double s_tc, s_minA, s_massS, s_d0S;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int rank = 0;
+    if constexpr (CL > 1) rank = cluster_rank();
     for (int i = tid; i < kExpTableSize; i += NT) s_tab[i] = a.exptab[i];
+    csync<CL>();   // every CTA of the cluster has started before any remote shared-memory store
 
     for (;;) {
         // ------------------------------------------------------------ take a ticket
-        if (tid == 0) {
+        if (tid == 0 && rank == 0) {
             int cmd = 0, q = 0, r = 0;
             for (;;) {
                 if (ld_relaxed(&a.ctl->unfinished) == 0 || ld_relaxed(&a.ctl->error) != 0) break;
@@ -90,23 +99,49 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
                 cmd = 1;
                 break;
             }
+            InstState S{};
+            if (cmd) {
+                const InstState *sp = a.st + a.order[q];
+                S.step = __ldcg(&sp->step);
+                S.t_c = __ldcg(&sp->t_c);
+                S.minA = __ldcg(&sp->minA);
+                S.mass = __ldcg(&sp->mass);
+                S.delta0 = __ldcg(&sp->delta0);
+                S.status = __ldcg(&sp->status);
+            }
             s_cmd = cmd;
             s_q = q;
             s_r = r;
+            s_step = S.step;
+            s_tc = S.t_c;
+            s_minA = S.minA;
+            s_massS = S.mass;
+            s_d0S = S.delta0;
+            s_status = S.status;
+            if constexpr (CL > 1) {
+                st_others<CL>(&s_cmd, cmd, 0);
+                st_others<CL>(&s_q, q, 0);
+                st_others<CL>(&s_r, r, 0);
+                st_others<CL>(&s_step, (long long)S.step, 0);
+                st_others<CL>(&s_tc, S.t_c, 0);
+                st_others<CL>(&s_minA, S.minA, 0);
+                st_others<CL>(&s_massS, S.mass, 0);
+                st_others<CL>(&s_d0S, S.delta0, 0);
+                st_others<CL>(&s_status, (int)S.status, 0);
+            }
         }
-        __syncthreads();
+        csync<CL>();
         if (s_cmd == 0) break;
         const int q = s_q, rnd = s_r;
         const int b = a.order[q];
         const InstDesc d = a.desc[b];
-        const InstState *sp = a.st + b;
         InstState S;
-        S.step = __ldcg(&sp->step);
-        S.t_c = __ldcg(&sp->t_c);
-        S.minA = __ldcg(&sp->minA);
-        S.mass = __ldcg(&sp->mass);
-        S.delta0 = __ldcg(&sp->delta0);
-        S.status = __ldcg(&sp->status);
+        S.step = s_step;
+        S.t_c = s_tc;
+        S.minA = s_minA;
+        S.mass = s_massS;
+        S.delta0 = s_d0S;
+        S.status = s_status;
 
         const double dt = d.dt;
         long long n_end = S.step, n_target = S.step;
@@ -115,12 +150,19 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
             n_target = min(n_end, S.step + (long long)a.chunk);
         }
         const int N = d.N;
-        const int Tn = (N - 1) / P;
+        const int TnAll = (N - 1) / P;
+        const int bs = block_start<CL>(rank, TnAll);
+        const int Tn = block_start<CL>(rank + 1, TnAll) - bs;  // node blocks of this CTA
+        const int gb = bs * P;                                  // first node of this CTA
+        const int NLp = (rank > 0) ? (bs - block_start<CL>(rank - 1, TnAll)) * P : 0;  // nodes of rank-1
         const bool act = tid < Tn;
-        const bool tfirst = tid == 0;
-        const bool last = tid == Tn - 1;
-        const int i0 = tid * P;
-        const int tb = (P + 1) * tid;
+        const bool tfirst = rank == 0 && tid == 0;              // owns node 0
+        const bool last = (rank == CL - 1) && tid == Tn - 1;    // owns node N-2
+        const bool hl = (CL > 1) && rank < CL - 1 && tid == Tn - 1;  // pushes the left halo of rank+1
+        const bool hr = (CL > 1) && rank > 0 && tid == 0;            // pushes the right halo of rank-1
+        const int i0 = gb + tid * P;       // global node of the thread's first node
+        const int tb = (P + 1) * tid;      // thread base in the padded arrays (local nodes)
+        const int Nl = N - gb;             // local index of node N
         const GeoTab g = a.geo[d.geo];
         const EaGeo eg = ea.eg[d.geo];
         double *uPhi = a.Phi + d.off, *uPi = a.Pi + d.off, *uA = ea.A + d.off;
@@ -155,12 +197,12 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
                     if (a.mode == kModeInit) uPhi[0] = 0.0;
                 }
                 if (last) {
-                    bufA0[spos<P>(N - 1)] = 0.0;
-                    bufA1[spos<P>(N - 1)] = 0.0;
+                    bufA0[spos<P>(Nl - 1)] = 0.0;
+                    bufA1[spos<P>(Nl - 1)] = 0.0;
 #pragma unroll
                     for (int j = 1; j <= 3; ++j) {
-                        bufA0[spos<P>(N - 1 + j)] = p[P - j];
-                        bufA1[spos<P>(N - 1 + j)] = -qv[P - j];
+                        bufA0[spos<P>(Nl - 1 + j)] = p[P - j];
+                        bufA1[spos<P>(Nl - 1 + j)] = -qv[P - j];
                     }
                     if (a.mode == kModeInit) {
                         uPhi[N - 1] = 0.0;
@@ -168,8 +210,24 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
                         uA[N - 1] = 1.0;
                     }
                 }
+                if constexpr (CL > 1) {
+                    if (hl) {   // last 3 nodes -> left halo of rank+1
+#pragma unroll
+                        for (int j = 1; j <= 3; ++j) {
+                            st_peer(bufA0 + spos<P>(-j), p[P - j], rank + 1);
+                            st_peer(bufA1 + spos<P>(-j), qv[P - j], rank + 1);
+                        }
+                    }
+                    if (hr) {   // first 3 nodes -> right halo of rank-1
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            st_peer(bufA0 + spos<P>(NLp + j), p[j], rank - 1);
+                            st_peer(bufA1 + spos<P>(NLp + j), qv[j], rank - 1);
+                        }
+                    }
+                }
             }
-            __syncthreads();
+            csync<CL>();
 
             double *S0 = bufA0, *S1 = bufA1, *D0 = bufB0, *D1 = bufB1;
             bool first = true;
@@ -276,8 +334,24 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
                         if (lane == 0) bw = 0.0;
                         if (lane + 1 >= NW) dw = 0.0;
                         if (lane < NW) { cM[lane] = bw; cD[lane] = dw; }
+                        if constexpr (CL > 1) {
+                            double aw = __shfl_up_sync(FULL, A_, 1);
+                            if (lane == 0) aw = 1.0;
+                            if (lane < NW) cMa[lane] = aw;
+                            // block totals to the other ranks: the m map to higher ranks (only read
+                            // on re-integration slices), the delta sum to lower ranks
+                            if (lane == NW - 1) {
+                                for (int j = rank + 1; j < CL; ++j) {
+                                    st_peer(s_cA + rank, A_, j);
+                                    st_peer(s_cB + rank, B_, j);
+                                }
+                            }
+                            if (lane == 0) {
+                                for (int j = 0; j < rank; ++j) st_peer(s_cD + rank, D_, j);
+                            }
+                        }
                     }
-                    __syncthreads();
+                    csync<CL>();
                     }   // !FIXED
 
                     // ============ fluxes, A-dot and the A update; diagnostics of the slice ============
@@ -290,8 +364,17 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
 #pragma unroll
                             for (int k = 0; k < P; ++k) De[k] = 0.0;
                         } else {
-                            m = fma(aEx, cM[wid], bEx);
-                            double dc = dEx + cD[wid];
+                            double cm = cM[wid], dr = 0.0;
+                            if constexpr (CL > 1) {
+                                // m at this rank's first node: the maps of the ranks before it
+                                double mr = 0.0;
+                                for (int j = 0; j < rank; ++j) mr = (j == 0) ? s_cB[0] : fma(s_cA[j], mr, s_cB[j]);
+                                if (rank > 0) cm = fma(cMa[wid], mr, cm);
+                                // delta carried in from the ranks to the right
+                                for (int j = CL - 1; j > rank; --j) dr = (j == CL - 1) ? s_cD[j] : dr + s_cD[j];
+                            }
+                            m = fma(aEx, cm, bEx);
+                            double dc = dEx + cD[wid] + dr;
 #pragma unroll
                             for (int k = P - 1; k >= 0; --k) {
                                 dc = dc + De[k];
@@ -299,6 +382,7 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
                             }
                         }
                         double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0, fm1 = 0.0, fm2 = 0.0;
+                        double f0 = 0.0, f1 = 0.0, u0 = 0.0, u1 = 0.0;
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
@@ -333,7 +417,8 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
                             }
                             sF[tb + soff<P>(k)] = fi;
                             sU[tb + soff<P>(k)] = ui;
-                            if (k == 1) g1 = gi;
+                            if (k == 0) { f0 = fi; u0 = ui; }
+                            if (k == 1) { g1 = gi; f1 = fi; u1 = ui; }
                             if (k == 2) g2 = gi;
                             if (tfirst && (k == 1 || k == 2)) {
                                 sF[spos<P>(-k)] = fi;
@@ -349,17 +434,32 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
                         if (tfirst) {
                             s_d0 = De[0];
                             sF[spos<P>(-3)] = fma(16.0, g1, -2.0 * g2);
+                            if constexpr (CL > 1) st_others<CL>(&s_d0, De[0], 0);
                         }
                         if (last) {
-                            sF[spos<P>(N - 1)] = 0.0;
-                            sF[spos<P>(N)] = -fm1;
-                            sF[spos<P>(N + 1)] = -fm2;
-                            sU[spos<P>(N - 1)] = (4.0 * um1 - um2) * (1.0 / 3.0);
-                            sU[spos<P>(N)] = um1;
-                            sU[spos<P>(N + 1)] = um2;
+                            sF[spos<P>(Nl - 1)] = 0.0;
+                            sF[spos<P>(Nl)] = -fm1;
+                            sF[spos<P>(Nl + 1)] = -fm2;
+                            sU[spos<P>(Nl - 1)] = (4.0 * um1 - um2) * (1.0 / 3.0);
+                            sU[spos<P>(Nl)] = um1;
+                            sU[spos<P>(Nl + 1)] = um2;
                             if (a.outA) {
                                 a.outA[d.off + N - 1] = 1.0;
                                 a.outDelta[d.off + N - 1] = 0.0;
+                            }
+                        }
+                        if constexpr (CL > 1) {
+                            if (hl) {   // f, u at the last 2 nodes -> left halo of rank+1
+                                st_peer(sF + spos<P>(-1), fm1, rank + 1);
+                                st_peer(sF + spos<P>(-2), fm2, rank + 1);
+                                st_peer(sU + spos<P>(-1), um1, rank + 1);
+                                st_peer(sU + spos<P>(-2), um2, rank + 1);
+                            }
+                            if (hr) {   // f, u at the first 2 nodes -> right halo of rank-1
+                                st_peer(sF + spos<P>(NLp), f0, rank - 1);
+                                st_peer(sF + spos<P>(NLp + 1), f1, rank - 1);
+                                st_peer(sU + spos<P>(NLp), u0, rank - 1);
+                                st_peer(sU + spos<P>(NLp + 1), u1, rank - 1);
                             }
                         }
                     }
@@ -372,17 +472,27 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
                         if (lane == 0) {
                             wMin[wid] = kmin;
                             wMs[wid] = msum;
+                            if constexpr (CL > 1) {
+                                st_others<CL>(wMinP + rank * NW + wid, kmin, rank);
+                                st_others<CL>(wMsP + rank * NW + wid, msum, rank);
+                            }
                         }
                     }
-                    __syncthreads();
+                    csync<CL>();
 
                     if (s == 0) {
                         long long km = wMin[0];
-                        double ms = wMs[0];
+                        double ms = 0.0;
+                        // the same summation order on every rank: ranks ascending, warps ascending
+#pragma unroll 1
+                        for (int j = 0; j < CL; ++j) {
+                            const long long *wk = (j == rank) ? wMin : wMinP + j * NW;
+                            const double *wm = (j == rank) ? wMs : wMsP + j * NW;
 #pragma unroll
-                        for (int w = 1; w < NW; ++w) {
-                            km = min_ll(km, wMin[w]);
-                            ms += wMs[w];
+                            for (int w = 0; w < NW; ++w) {
+                                km = min_ll(km, wk[w]);
+                                ms = (j == 0 && w == 0) ? wm[0] : ms + wm[w];
+                            }
                         }
                         minA = order_key_inv(km);
                         mass = ms;
@@ -460,16 +570,26 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
                                 D1[spos<P>(-k)] = nq;
                             }
                             if (last && k >= P - 3) {
-                                D0[spos<P>(N - 1 + (P - k))] = np;
-                                D1[spos<P>(N - 1 + (P - k))] = -nq;
+                                D0[spos<P>(Nl - 1 + (P - k))] = np;
+                                D1[spos<P>(Nl - 1 + (P - k))] = -nq;
+                            }
+                            if constexpr (CL > 1) {
+                                if (hl && k >= P - 3) {      // -> left halo of rank+1
+                                    st_peer(D0 + spos<P>(-(P - k)), np, rank + 1);
+                                    st_peer(D1 + spos<P>(-(P - k)), nq, rank + 1);
+                                }
+                                if (hr && k < 3) {           // -> right halo of rank-1
+                                    st_peer(D0 + spos<P>(NLp + k), np, rank - 1);
+                                    st_peer(D1 + spos<P>(NLp + k), nq, rank - 1);
+                                }
                             }
                         }
                         if (last) {
-                            D0[spos<P>(N - 1)] = 0.0;
-                            D1[spos<P>(N - 1)] = 0.0;
+                            D0[spos<P>(Nl - 1)] = 0.0;
+                            D1[spos<P>(Nl - 1)] = 0.0;
                         }
                     }
-                    __syncthreads();
+                    csync<CL>();
                     double *t0 = S0, *t1 = S1;
                     S0 = D0; S1 = D1; D0 = t0; D1 = t1;
                 }
@@ -477,8 +597,8 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
             }
         }
     finish:
-        __syncthreads();
-        if (tid == 0) {
+        csync<CL>();   // all global writes of this chunk are issued, by every CTA of the cluster
+        if (tid == 0 && rank == 0) {
             if (!skip) {
                 InstState *spw = a.st + b;
                 spw->step = step;
@@ -507,8 +627,9 @@ __global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
                 }
             }
             s_leave = leave;
+            if constexpr (CL > 1) st_others<CL>(&s_leave, leave, 0);
         }
-        __syncthreads();
+        csync<CL>();
         if (s_leave) break;
     }
 }

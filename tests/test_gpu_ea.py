@@ -81,10 +81,10 @@ def test_batch_chunks_and_restarts_are_bit_identical(ad):
 
 
 def test_unsupported_requests_fail_cleanly(ad):
-    with pytest.raises(ad.AdsclError) as e:
-        ad.Solver([8193], scheme=1)
-    assert e.value.status == ad.ADSCL_EUNSUPPORTED
     s = ad.Solver([257] * 2, scheme=1)
+    with pytest.raises(ad.AdsclError) as e:
+        s.set_shape(257, 8, 256, 2)          # the evolved-A kernels run the default shapes
+    assert e.value.status == ad.ADSCL_EINVAL
     s.set_initial_modes(np.full((2, 4), 0.01))
     with pytest.raises(ad.AdsclError) as e:
         s.grad(np.full((2, 4), 0.01), 0.1)
@@ -111,3 +111,54 @@ def test_fixed_metric_matches_oracle_and_exact_mode(ad, orc, N, j):
     assert err < (1e-7 if j == 0 else 1e-5)
     assert np.all(gA == 1.0) and np.all(gd == 0.0)
     assert st[0] == ad.DONE
+
+
+# the paper's production configuration (Sec. II, Table I: N = 32K, A evolved, third order) on
+# clusters of 2, 4 and 8 CTAs, with and without re-integration
+@pytest.mark.parametrize("N,reint,steps", [(8193, 0, 6), (16385, 3, 5), (32769, 2, 4), (4105, 0, 6)])
+def test_evolved_a_on_clusters_matches_oracle(ad, orc, N, reint, steps):
+    Phi, Pi = W.smooth_random(N, seed=N % 101, amp=2.5)
+    s = ad.Solver([N], scheme=1, a_reint_every=reint, chunk_steps=3)
+    s.set_initial(Phi, Pi)
+    Ac = orc.constraints(Phi, Pi)[0]
+    assert _close(s.get_state(0)[2], Ac, 1e-12)
+    dt, _ = s.clock()
+    tr, tc, m, st = s.evolve(steps * dt[0])
+    r = orc.ea_evolve(Phi, Pi, Ac, dt[0], steps, order=3, reint=reint, sigma=0.5)
+    gP, gQ, gA, gd = s.get_state(0)
+    assert _close(gP, r.Phi, 1e-11) and _close(gQ, r.Pi, 1e-11)
+    assert _close(gA, r.A, 1e-11) and _close(gd, r.delta, 1e-11)
+    assert abs(m[0] - r.mass) <= 1e-11 * max(1.0, r.mass)
+
+
+def test_evolved_a_mixed_cluster_batch_equals_single_runs(ad):
+    Ns = [32769, 1025, 8193, 16385, 129]
+    fields = [W.smooth_random(n, seed=400 + i, amp=2.0) for i, n in enumerate(Ns)]
+    s = ad.Solver(Ns, scheme=1, a_reint_every=4, chunk_steps=3)
+    s.set_initial(W.packed([f[0] for f in fields]), W.packed([f[1] for f in fields]))
+    tb = s.evolve(0.002)
+    for i, n in enumerate(Ns):
+        one = ad.Solver([n], scheme=1, a_reint_every=4, chunk_steps=3)
+        one.set_initial(fields[i][0], fields[i][1])
+        t1 = one.evolve(0.002)
+        for x, y in zip(s.get_state(i), one.get_state(0)):
+            assert np.array_equal(x, y)
+        assert tb[2][i] == t1[2][0]
+
+
+def test_fixed_metric_on_an_eight_cta_cluster(ad, orc):
+    N, j = 32769, 2
+    a = np.zeros((1, j + 1))
+    a[0, j] = 1.0
+    s = ad.Solver([N], scheme=ad.SCHEME_FIXED_METRIC_RK3)
+    s.set_initial_modes(a)
+    dt, _ = s.clock()
+    n = 40
+    s.evolve(n * dt[0])
+    gP, gQ, gA, gd = s.get_state(0)
+    e, de = orc.eigen(N, j + 1)
+    oP, oQ = orc.fixed_evolve(np.zeros(N), e[j], dt[0], n, order=3, sigma=0.5)
+    assert np.abs(gP - oP).max() < 1e-11 and np.abs(gQ - oQ).max() < 1e-11
+    w, T = 3.0 + 2.0 * j, n * dt[0]
+    assert np.abs(gQ - np.cos(w * T) * e[j]).max() < 1e-9
+    assert np.all(gA == 1.0) and np.all(gd == 0.0)
