@@ -1440,7 +1440,7 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
         }
         // point-substeps per ms of the list positions [i, j) with the current shapes: a one-step
         // warm-up, then `trial` steps, from the saved state
-        auto rate_of = [&](int i, int j, double *rate) -> adscl_status {
+        auto rate_of = [&](int i, int j, int steps, double *rate) -> adscl_status {
             long long smax = 0;
             double dtmax = 0.0;
             for (int q = i; q < j; ++q) {
@@ -1452,7 +1452,7 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
                 s = restore();
                 if (s != ADSCL_OK) return s;
                 // t_end: `trial` steps of the largest time step (every instance advances)
-                const double te = (double)smax * ctx->h_desc[ord[i]].dt + (rep == 0 ? 1 : trial) * dtmax;
+                const double te = (double)smax * ctx->h_desc[ord[i]].dt + (rep == 0 ? 1 : steps) * dtmax;
                 ctx->t_prev = (double)smax * ctx->h_desc[ord[i]].dt;
                 CK(cudaEventRecord(e0, ctx->stream));
                 s = launch_evolve(ctx, kModeEvolve, te, i, ord.data() + i, j - i, nullptr, nullptr, ctx->stream);
@@ -1484,7 +1484,7 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
                 }
                 set_run(r, id);
                 double rate = 0.0;
-                s = rate_of(run_start[r], run_start[r + 1], &rate);
+                s = rate_of(run_start[r], run_start[r + 1], trial, &rate);
                 if (s != ADSCL_OK) return s;
                 if (rate > best_rate) {
                     best_rate = rate;
@@ -1495,15 +1495,18 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
             set_run(r, best[r]);
         }
         if (nr > 1 && best != dflt) {
-            // the sizes run concurrently in a batch: keep the per-size choice only if the whole
-            // batch is faster with it than with the default shapes
+            // the sizes run concurrently in a batch, where shapes that share an SM (two CTAs of
+            // 256 threads) and shapes that fill one do not pack as the SM split assumes: keep
+            // the per-size choice only if the whole batch, timed over a longer window, is more
+            // than 1 % faster with it than with the default shapes
+            const int bsteps = std::max(4 * trial, 32);
             double r_best = 0.0, r_dflt = 0.0;
-            s = rate_of(0, B, &r_best);
+            s = rate_of(0, B, bsteps, &r_best);
             if (s != ADSCL_OK) return s;
             for (int r = 0; r < nr; ++r) set_run(r, dflt[r]);
-            s = rate_of(0, B, &r_dflt);
+            s = rate_of(0, B, bsteps, &r_dflt);
             if (s != ADSCL_OK) return s;
-            if (r_best > r_dflt) {
+            if (r_best > 1.01 * r_dflt) {
                 for (int r = 0; r < nr; ++r) set_run(r, best[r]);
             } else {
                 best = dflt;
