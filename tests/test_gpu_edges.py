@@ -73,3 +73,21 @@ def test_many_tiny_instances_equal_single_runs(ad):
         for x, y in zip(s.get_state(i), one.get_state(0)):
             assert np.array_equal(x, y)
         assert tb[2][i] == t1[2][0]
+
+
+def test_long_run_matches_oracle(ad, orc):
+    """A weak pulse (no collapse) to t = 100 at N = 257 (32,600 RK4 steps): mass within 1e-10
+    relative and the fields within 1e-9 of the oracle, min A and delta(0) likewise."""
+    N = 257
+    Pi0 = W.gaussian_pi(N, 2.0, sigma=1.0 / 8)
+    s = ad.Solver([N], collapse_threshold=0.05)
+    s.set_initial(np.zeros(N), Pi0)
+    dt, _ = s.clock()
+    nsteps = int(round(100.0 / dt[0]))
+    tr, tc, m, st = s.evolve(100.0)
+    r = orc.evolve(np.zeros(N), Pi0, dt[0], nsteps, sigma=0.5, theta=0.05)
+    assert st[0] == ad.DONE and r.status == orc.DONE
+    assert abs(m[0] / r.mass - 1) < 1e-10
+    gP, gQ, gA, gd = s.get_state(0)
+    assert np.abs(gP - r.Phi).max() < 1e-9 and np.abs(gQ - r.Pi).max() < 1e-9
+    assert np.abs(gA - r.A).max() < 1e-9 and np.abs(gd - r.delta).max() < 1e-9
