@@ -1,9 +1,11 @@
 // evolve.cuh -- persistent FP64 method-of-lines kernel for the AdS4 Einstein-Klein-Gordon
 // system of arXiv:1706.07413, Sec. II (Eqs. (eq:phi), (eq:pi), (eq:aprime), (eq:delta)).
 //
-// One CTA evolves one instance at a time with its stage slice resident in shared memory.
-// Thread t owns the P contiguous grid nodes t*P .. t*P+P-1 and the cells to their right;
-// node N-1 (x = pi/2, where Phi = Pi = 0) is owned by nobody and written as a constant.
+// One CTA -- or a thread-block cluster of CL = 2, 4, 8 CTAs that split the node blocks between
+// them -- evolves one instance at a time with its stage slice resident in (distributed) shared
+// memory.  Thread t of a CTA owns the P contiguous grid nodes of its block and the cells to their
+// right; node N-1 (x = pi/2, where Phi = Pi = 0) is owned by nobody and written as a constant.
+// The kernel is instantiated for several (P, NT, CL) shapes; the host picks one per grid size.
 //
 // Per RK stage:
 //   1. cell data: rho at nodes and (4-point interpolated) midpoints, the Simpson increment
