@@ -543,8 +543,9 @@ def main():
                          "ratio": t_adj_t / t_fwd_t},
                "workload": f"64 mode-sum instances, N=4097, {ADJ_STEPS} RK4 steps of dt=2pi/32768, "
                            "checkpoint every 256 steps, J = sum_{j<32}(E_j(T)-E_j(0))^2",
-               "grad_includes": "forward pass with checkpoints, E(0), E(T), per-segment recompute "
-                                "with stage storage, backward sweep, projection"}
+               "grad_includes": "E(0), the forward pass (storing every stage when all segments fit "
+                                "in device memory, as here; else checkpoints and a per-segment "
+                                "recompute), E(T), the backward sweep, the projection onto the modes"}
         sa.close()
 
     # spectrum timing (current slices of the amplitude scan, 64 modes)

@@ -83,13 +83,18 @@ typedef struct {
                                     paper's production variant (Sec. II): A evolved with
                                     Eq. (eq:adot), SSP Runge-Kutta of order 3 / 2; 3 = A = 1 and
                                     delta = 0 held fixed (the paper's Table II case, the linear
-                                    wave equation on AdS4), SSP-RK3; schemes 1-3: N <= 4097 */
+                                    wave equation on AdS4), SSP-RK3 */
     int32_t a_reint_every;       /* schemes 1, 2: re-integrate A from Eq. (eq:aprime) on slices
                                     whose step index is a multiple of this (0: never; the
                                     initial slice always takes the constraint solution) */
     int32_t adjoint_ctas;        /* CTAs per instance of the adjoint kernel (adscl_grad): 1, 2 (a
                                     thread-block cluster), or 0 = 2 when the batch has at most
                                     half as many instances as the GPU has SMs, else 1 */
+    int32_t adjoint_stage_buffers; /* most checkpoint segments whose stages adscl_grad keeps in
+                                    device memory at once: 0 = as many as fit (all segments:
+                                    the forward pass stores every stage and nothing is
+                                    recomputed; else 2: recomputation of one segment beside the
+                                    backward sweep of the next; else 1) */
     void *stream;                /* cudaStream_t for all work; NULL = the legacy default stream */
 } adscl_config;
 
@@ -148,11 +153,13 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
  * Pi(x,0) = sum_{k<K} a_k e_k(x), Phi(x,0) = 0 (a: B x K row-major, K <= 64),
  *   J = sum_{j<spec_J} (E_j(T) - E_j(0))^2,
  * evolved without the collapse stop for n = ceil(T/dt) RK4 steps (the same n for every
- * instance, N <= 4097).  Outputs J_out (B) and dJda (B x K).  The forward pass keeps
- * (Phi, Pi) every ckpt_every steps; each segment is recomputed once with every stage stored in
- * device memory (B * ckpt_every * 24 * N doubles) and swept backwards through the exact
- * transpose of the discrete step (constraint scans included).  Replaces the context's state by
- * the final slice. */
+ * instance, N <= 4097).  Outputs J_out (B) and dJda (B x K).  The steps are cut into segments of
+ * ckpt_every; every stage of a segment is stored in device memory (B * ckpt_every * 24 * N
+ * doubles per segment) and swept backwards through the exact transpose of the discrete step
+ * (constraint scans included).  When every segment's stages fit (adjoint_stage_buffers), the
+ * forward pass stores them all; otherwise it keeps (Phi, Pi) at the segment starts and each
+ * segment is recomputed once before its sweep.  Replaces the context's state by the final
+ * slice (step index n). */
 adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, double *J_out,
                         double *dJda, int ptr_is_device);
 

@@ -44,6 +44,7 @@ class adscl_config(ctypes.Structure):
                 ("scheme", ctypes.c_int32),
                 ("a_reint_every", ctypes.c_int32),
                 ("adjoint_ctas", ctypes.c_int32),
+                ("adjoint_stage_buffers", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -156,7 +157,7 @@ class Solver:
     def __init__(self, N, cfl=0.5, ko_sigma=0.5, collapse_threshold=2.0 ** -7, out_dt=1.0,
                  spec_J=64, ckpt_every=256, device=0, one_per_launch=False, stream=None,
                  max_device_iters=0, chunk_steps=0, direct_launch=False, scheme=0,
-                 a_reint_every=0, adjoint_ctas=0):
+                 a_reint_every=0, adjoint_ctas=0, adjoint_stage_buffers=0):
         self.lib = load()
         self.N = np.ascontiguousarray(np.asarray(N, dtype=np.int32).ravel())
         self.B = int(self.N.size)
@@ -178,6 +179,7 @@ class Solver:
         cfg.scheme = scheme
         cfg.a_reint_every = a_reint_every
         cfg.adjoint_ctas = adjoint_ctas
+        cfg.adjoint_stage_buffers = adjoint_stage_buffers
         cfg.stream = stream
         self.stream = stream
         h = ctypes.c_void_p()

@@ -58,6 +58,7 @@ struct AdjArgs {
     int32_t mode;
     // segment mode
     const double *ckP, *ckQ;  // packed slices at the segment start
+    double *outP, *outQ;      // phase F: packed slices receiving the segment's last slice (or null)
     int32_t nsteps;           // steps of this segment
     double *stage;            // per work item: nsteps_cap * 4 stages * kStageArrays * Nmax
     int32_t nsteps_cap;
@@ -739,6 +740,12 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                 for (int k = 0; k < kAP; ++k) { scr.uP[i0 + k] = scr.aP[i0 + k]; scr.uQ[i0 + k] = scr.aQ[i0 + k]; }
             }
             csync<CL>();
+        }
+        if (a.outP && act) {   // the segment's last slice (the next segment's start)
+            double *oP = a.outP + d.off, *oQ = a.outQ + d.off;
+#pragma unroll
+            for (int k = 0; k < kAP; ++k) { oP[i0 + k] = scr.uP[i0 + k]; oQ[i0 + k] = scr.uQ[i0 + k]; }
+            if (own.last) { oP[N - 1] = 0.0; oQ[N - 1] = 0.0; }
         }
 
         }   // phase F

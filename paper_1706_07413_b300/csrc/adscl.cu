@@ -75,6 +75,7 @@ struct adscl_ctx {
     double t_prev = 0.0;               // t_end of the last evolve call since the initial data
     int scheme = 0, reint = 0;         // ADSCL_SCHEME_*, A re-integration interval (evolved A)
     int adj_cl = 1;                    // CTAs per instance of the adjoint kernel
+    int adj_bufs_cap = 0;              // most segment stage buffers the adjoint may hold (0: any)
     int adj_units = 0;                 // co-resident adjoint units (CTAs or 2-CTA clusters)
     double *d_A = nullptr;             // packed evolved A (evolved-A schemes)
     double *d_ea_block = nullptr;      // K2, wsim per grid size (evolved-A schemes)
@@ -111,9 +112,10 @@ struct adscl_ctx {
     // adjoint (built on first use)
     double *d_lam = nullptr;           // packed lambda: Phi part, then Pi part
     double *d_adj_scr = nullptr;       // per CTA scratch
-    double *d_adj_stage = nullptr;     // stored stages of one segment, per instance (1 or 2 buffers)
+    double *d_adj_stage = nullptr;     // stored stages, one buffer per segment held
     size_t adj_stage_doubles = 0;      // doubles of one buffer
     int adj_stage_bufs = 0;
+    double *d_adj_spec = nullptr;      // slots of the spectrum transposes
     cudaStream_t adj_aux = nullptr;    // stream of the recomputation beside the backward sweep
     cudaEvent_t adj_free[2] = {nullptr, nullptr}, adj_ready[2] = {nullptr, nullptr};
     cudaEvent_t adj_ck = nullptr;      // the last checkpoint is written
@@ -705,7 +707,8 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
         !std::isfinite(cfg->collapse_threshold) || !(cad > 0.0) || cfg->spec_J < 0 ||
         cfg->spec_J > 64 || cfg->ckpt_every < 0 || cfg->max_device_iters < 0 ||
         cfg->scheme < ADSCL_SCHEME_RK4 || cfg->scheme > ADSCL_SCHEME_FIXED_METRIC_RK3 ||
-        cfg->a_reint_every < 0 || cfg->adjoint_ctas < 0 || cfg->adjoint_ctas > 2)
+        cfg->a_reint_every < 0 || cfg->adjoint_ctas < 0 || cfg->adjoint_ctas > 2 ||
+        cfg->adjoint_stage_buffers < 0)
         return ADSCL_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
@@ -728,6 +731,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     ctx->scheme = cfg->scheme;
     ctx->reint = cfg->a_reint_every;
     ctx->adj_cl = cfg->adjoint_ctas;   // 0: chosen at the first adscl_grad
+    ctx->adj_bufs_cap = cfg->adjoint_stage_buffers;
     ctx->stream = (cudaStream_t)cfg->stream;
     *out = ctx;
 
@@ -1047,6 +1051,14 @@ __global__ void drift_kernel(const double *E0, const double *ET, int B, int J, d
 
 // one adjoint launch on stream sm; lane 0 or 1 selects the work counter and the per-CTA scratch
 // (the two lanes may run at the same time)
+// the step index of every instance (the forward pass of adscl_grad through the stage-storing
+// recomputation leaves the context at step nsteps)
+__global__ void set_step_kernel(InstState *st, int B, long long step)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) st[b].step = step;
+}
+
 adscl_status launch_adjoint(adscl_ctx *ctx, AdjArgs &a, cudaStream_t sm, int lane)
 {
     const int regions = std::min(ctx->B, ctx->num_sms);   // scratch regions per lane
@@ -1126,26 +1138,38 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         CK(cudaMalloc(&ctx->d_adj_small, ((size_t)B * (5 * kMaxModes + 1)) * sizeof(double)));
         CK(cudaMalloc(&ctx->d_adj_queue, 2 * sizeof(int32_t)));
     }
-    // stage storage of one segment; two of them (when memory allows) let the recomputation of
-    // segment g-1 run beside the backward sweep of segment g
+    // stage storage, one buffer per segment: with a buffer for every segment (when the device
+    // has room for them with a tenth of its memory to spare) the forward pass itself stores every
+    // stage and nothing is recomputed; with two, the recomputation of segment g-1 runs beside the
+    // backward sweep of segment g; with one, each segment recomputes, then sweeps
     const size_t stage_need = (size_t)B * std::max(seg, 1) * 4 * kStageArrays * ctx->Nmax;
-    if (ctx->adj_stage_doubles < stage_need) {
-        if (ctx->d_adj_stage) CK(cudaFree(ctx->d_adj_stage));
-        ctx->d_adj_stage = nullptr;
-        ctx->adj_stage_bufs = 0;
-        if (cudaMalloc(&ctx->d_adj_stage, 2 * stage_need * sizeof(double)) == cudaSuccess) {
-            ctx->adj_stage_bufs = 2;
-        } else {
-            cudaGetLastError();
-            if (cudaMalloc(&ctx->d_adj_stage, stage_need * sizeof(double)) != cudaSuccess) {
-                cudaGetLastError();
-                ctx->adj_stage_doubles = 0;
-                return fail(ctx, ADSCL_ENOMEM, "adjoint stage storage (%zu MB)", stage_need * 8 >> 20);
+    {
+        const int cap = ctx->adj_bufs_cap > 0 ? ctx->adj_bufs_cap : (1 << 20);
+        const int want[3] = {(int)std::min<long long>(std::min<long long>(nseg, cap), 1 << 20), std::min(2, cap), 1};
+        int have = (ctx->adj_stage_doubles >= stage_need) ? ctx->adj_stage_bufs : 0;
+        for (int w : want) {
+            if (w < 1 || have >= w) break;
+            if (ctx->d_adj_stage) CK(cudaFree(ctx->d_adj_stage));
+            ctx->d_adj_stage = nullptr;
+            ctx->adj_stage_bufs = 0;
+            ctx->adj_stage_doubles = 0;
+            size_t free_b = 0, total_b = 0;
+            CK(cudaMemGetInfo(&free_b, &total_b));
+            const double bytes = (double)w * stage_need * sizeof(double);
+            if (w > 1 && bytes > (double)free_b - 0.1 * (double)total_b) continue;
+            if (cudaMalloc(&ctx->d_adj_stage, (size_t)w * stage_need * sizeof(double)) == cudaSuccess) {
+                ctx->adj_stage_bufs = w;
+                ctx->adj_stage_doubles = stage_need;
+                have = w;
+                break;
             }
-            ctx->adj_stage_bufs = 1;
+            (void)cudaGetLastError();
         }
-        ctx->adj_stage_doubles = stage_need;
+        if (!ctx->d_adj_stage)
+            return fail(ctx, ADSCL_ENOMEM, "adjoint stage storage (%zu MB)", stage_need * 8 >> 20);
     }
+    if (!ctx->d_adj_spec)   // the spectrum transposes' one-stage slots: B x 4 x kStageArrays x Nmax
+        CK(cudaMalloc(&ctx->d_adj_spec, (size_t)B * 4 * kStageArrays * ctx->Nmax * sizeof(double)));
     const size_t ck_need = (size_t)std::max(nseg, 1LL) * 2 * total;
     if (ctx->ck_doubles < ck_need) {
         if (ctx->d_ck) CK(cudaFree(ctx->d_ck));
@@ -1177,10 +1201,16 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         x.ckP = ctx->d_ck + (size_t)g * 2 * total;
         x.ckQ = x.ckP + total;
         x.nsteps = (int32_t)(std::min(nT, (g + 1) * seg) - g * seg);
-        x.stage = ctx->d_adj_stage + (ctx->adj_stage_bufs == 2 ? (size_t)(g & 1) * stN : 0);
+        const int nb = ctx->adj_stage_bufs;
+        const bool all = nb >= nseg && (ctx->adj_bufs_cap == 0 || ctx->adj_bufs_cap >= nseg);
+        const bool two = !all && nb >= 2 && ctx->adj_bufs_cap != 1;
+        x.stage = ctx->d_adj_stage + (all ? (size_t)g : two ? (size_t)(g & 1) : 0) * stN;
+        x.outP = x.outQ = nullptr;
         return x;
     };
-    const bool piped = ctx->adj_stage_bufs == 2 && nseg > 1;
+    const bool store_all = ctx->adj_stage_bufs >= nseg &&
+                           (ctx->adj_bufs_cap == 0 || ctx->adj_bufs_cap >= nseg);
+    const bool piped = !store_all && ctx->adj_stage_bufs >= 2 && ctx->adj_bufs_cap != 1 && nseg > 1;
     if (piped && !ctx->adj_aux) {
         CK(cudaStreamCreateWithFlags(&ctx->adj_aux, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&ctx->adj_ck, cudaEventDisableTiming));
@@ -1198,7 +1228,27 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     ctx->theta = -INFINITY;
     s = adscl_set_initial_modes(ctx, a, K, ptr_is_device);
     if (s == ADSCL_OK) s = adscl_spectrum(ctx, Jm, ADSCL_PREC_FP64, E0, 1);
-    for (long long g = 0; g < nseg && s == ADSCL_OK; ++g) {
+    if (store_all && s == ADSCL_OK) {
+        // the forward pass is phase F of every segment, chained through the checkpoints; its
+        // last slice becomes the context's current slice at step nT
+        CK(cudaMemcpyAsync(ctx->d_ck, ctx->d_Phi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_ck + total, ctx->d_Pi, total * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        if (!ctx->d_eig) return fail(ctx, ADSCL_ECUDA, "normal-mode tables missing");
+        aa.eig = ctx->d_eig;
+        for (long long g = 0; g < nseg && s == ADSCL_OK; ++g) {
+            AdjArgs x = seg_args(g, kAdjSegF);
+            x.outP = (g + 1 < nseg) ? ctx->d_ck + (size_t)(g + 1) * 2 * total : ctx->d_Phi;
+            x.outQ = (g + 1 < nseg) ? x.outP + total : ctx->d_Pi;
+            s = launch_adjoint(ctx, x, ctx->stream, 0);
+        }
+        if (s == ADSCL_OK) {
+            set_step_kernel<<<(B + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_st, B, nT);
+            CK(cudaGetLastError());
+            s = launch_evolve(ctx, kModeInit, 0.0, 0, ctx->h_order.data(), ctx->B, nullptr, nullptr, ctx->stream);
+        }
+    }
+    for (long long g = 0; g < nseg && s == ADSCL_OK && !store_all; ++g) {
         double *ck = ctx->d_ck + (size_t)g * 2 * total;
         CK(cudaMemcpyAsync(ck, ctx->d_Phi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ck + total, ctx->d_Pi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1224,7 +1274,8 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     // does not use
     if (!ctx->d_eig) return fail(ctx, ADSCL_ECUDA, "normal-mode tables missing");
     aa.eig = ctx->d_eig;
-    aa.stage = ctx->d_adj_stage + (piped ? (size_t)(klast ^ 1) * stN : 0);
+    aa.stage = ctx->d_adj_spec;   // one step of slots per instance
+    aa.nsteps_cap = 1;
     CK(cudaMemsetAsync(ctx->d_lam, 0, 2 * total * sizeof(double), ctx->stream));
     aa.mode = kAdjSpectrum;
     aa.Ebar = EbT;
@@ -1232,7 +1283,13 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     aa.sQ = ctx->d_Pi;
     s = launch_adjoint(ctx, aa, ctx->stream, 0);
     if (s != ADSCL_OK) return s;
-    if (piped) {
+    aa.nsteps_cap = std::max(seg, 1);
+    if (store_all) {
+        for (long long g = nseg - 1; g >= 0 && s == ADSCL_OK; --g) {
+            AdjArgs x = seg_args(g, kAdjSegB);
+            s = launch_adjoint(ctx, x, ctx->stream, 0);
+        }
+    } else if (piped) {
         // main stream: B(g) for g descending, each after its F(g); side stream: F(g-1) once
         // B(g+1) (or, for the first one, the spectrum transpose) has released its buffer
         CK(cudaEventRecord(ctx->adj_free[klast ^ 1], ctx->stream));
@@ -1263,6 +1320,8 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     aa.Ebar = Eb0;
     aa.sP = ctx->d_ck;
     aa.sQ = ctx->d_ck + total;
+    aa.stage = ctx->d_adj_spec;
+    aa.nsteps_cap = 1;
     s = launch_adjoint(ctx, aa, ctx->stream, 0);
     if (s != ADSCL_OK) return s;
     aa.mode = kAdjProject;
@@ -1541,7 +1600,7 @@ void adscl_destroy(adscl_ctx *ctx)
                     ctx->d_eig_block, ctx->d_eig, ctx->d_modes, ctx->d_E, ctx->d_tc_rowoff,
                     ctx->d_tc_rowinst, ctx->d_tc_modeoff, ctx->d_tc_ops, ctx->d_tc_D,
                     ctx->d_tc_tasks, ctx->d_tc_err, ctx->d_lam, ctx->d_adj_scr, ctx->d_adj_stage,
-                    ctx->d_ck, ctx->d_adj_small, ctx->d_adj_queue, ctx->d_A, ctx->d_ea_block,
+                    ctx->d_ck, ctx->d_adj_small, ctx->d_adj_queue, ctx->d_A, ctx->d_ea_block, ctx->d_adj_spec,
                     ctx->d_eageo};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -107,3 +107,31 @@ def test_one_and_two_cta_adjoint_agree(ad, orc, N):
     Jo, go = orc.grad(a[2], N, 30, dt[0], sigma=0.5, Jm=Jm)
     assert abs(J2[2] - Jo) <= 1e-10 * abs(Jo)
     assert np.abs(g2[2] - go).max() <= 1e-9 * np.abs(go).max()
+
+
+@pytest.mark.parametrize("bufs", [1, 2, 0])
+def test_stage_storage_modes_agree(ad, orc, bufs):
+    """One stage buffer (recompute, then sweep, per segment), two (recomputation beside the
+    sweep) and one per segment (the forward pass stores every stage) give the oracle's gradient;
+    the context ends on the final slice at step n in every mode."""
+    N, B, K, Jm, n = 257, 3, 6, 8, 40
+    rng = np.random.default_rng(21)
+    a = rng.uniform(0.0, 0.8, (B, K)) * np.exp(-np.arange(K) / 2.0)
+    s = ad.Solver([N] * B, ko_sigma=0.5, spec_J=Jm, ckpt_every=9, adjoint_stage_buffers=bufs)
+    dt, _ = s.clock()
+    J, g = s.grad(a, n * dt[0])
+    for b in (0, 2):
+        Jo, go = orc.grad(a[b], N, n, dt[0], sigma=0.5, Jm=Jm)
+        assert abs(J[b] - Jo) <= 1e-10 * abs(Jo)
+        assert np.abs(g[b] - go).max() <= 1e-9 * np.abs(go).max()
+    assert np.all(s.clock()[1] == n)
+    # the final slice equals a plain forward evolution (to rounding)
+    ref = ad.Solver([N] * B, ko_sigma=0.5, spec_J=Jm, collapse_threshold=-1.0)
+    ref.set_initial_modes(a)
+    ref.evolve(n * dt[0])
+    for b in range(B):
+        x, y = s.get_state(b), ref.get_state(b)
+        assert np.abs(x[0] - y[0]).max() < 1e-12 and np.abs(x[1] - y[1]).max() < 1e-12
+    # and the context keeps evolving from it
+    s.evolve((n + 5) * dt[0])
+    assert np.all(s.clock()[1] == n + 5)
