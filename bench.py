@@ -59,16 +59,21 @@ REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
 # DRAM bytes (read + write) of one timed evolve_kernel launch of the amplitude scan, from an ncu
 # capture of this script (profiles/evolve_kernel_amp_scan.md); reported only while the kernel
 # source and the kernel shape are the ones the counters were taken on.
-TRAFFIC = {"kernel_sha256": "709f821611336044da65fe8dfaf629422dddb2c248b6f95201f94cb3e4f644fc",
+TRAFFIC = {"kernel_sha256": "9f96ba6ab40c1dd6e1a8641c5b14bb3371717fe6fd03389bf0624e3b27f8b4f6",
            "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17725440 + 223519488}
 
 
 def kernel_digest():
+    """SHA-256 of the evolution kernel's code (comments and blank lines removed)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("evolve.cuh", "expneg.cuh"):
-        with open(os.path.join(ROOT, "paper_1706_07413_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1706_07413_b300", "csrc", f)) as fh:
+            for line in fh:
+                code = re.sub(r"//.*", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()
 
 
