@@ -106,7 +106,8 @@ struct adscl_ctx {
     char *d_tc_ops = nullptr;          // U, V (hi, lo) per tile and mode tables (hi, lo) per group
     size_t tc_ops_bytes = 0;
     int tc_built_prec = -1;            // precision of the mode tables currently in d_tc_ops
-    float *d_tc_D = nullptr;           // 2 x tiles x 128 x 64 projections
+    float *d_tc_D = nullptr;           // 2 x tiles x tc_split x 128 x 64 partial projections
+    int tc_split = 1;                  // K splits per tile
     TcTask *d_tc_tasks = nullptr;
     int *d_tc_err = nullptr;
     // adjoint (built on first use)
@@ -501,18 +502,28 @@ adscl_status ensure_modes(adscl_ctx *ctx)
 
 int kpad_of(int N) { return (N + kTcKC - 1) / kTcKC * kTcKC; }
 
-__global__ void tc_energy_kernel(const float *Dp, const float *Df, const int32_t *rowinst, int rows,
+// E_j from the partial projections: row r of tile r / 128, partials of split q at
+// D[((proj * tiles + tile) * S + q) * 128 * 64 + (r % 128) * 64 + j], summed in FP64 over q
+__global__ void tc_energy_kernel(const float *D, int tiles, int S, const int32_t *rowinst, int rows,
                                  int J, double *E)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    // one thread per (row, mode): consecutive threads read consecutive modes of a partial row
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = idx / J, j = idx - r * J;
     if (r >= rows) return;
     const int b = rowinst[r];
     if (b < 0) return;
-    for (int j = 0; j < J; ++j) {
-        const double p = Dp[(size_t)r * kTcN + j], f = Df[(size_t)r * kTcN + j];
-        const double w = 3.0 + 2.0 * j;
-        E[(size_t)b * J + j] = fma(p, p, f * f / (w * w));
+    const int tile = r / kTcM, row = r - tile * kTcM;
+    const size_t tileSz = (size_t)kTcM * kTcN;
+    const float *Dp = D + (size_t)tile * S * tileSz + (size_t)row * kTcN + j;
+    const float *Df = D + ((size_t)tiles + tile) * S * tileSz + (size_t)row * kTcN + j;
+    double p = 0.0, f = 0.0;
+    for (int q = 0; q < S; ++q) {
+        p += (double)Dp[q * tileSz];
+        f += (double)Df[q * tileSz];
     }
+    const double w = 3.0 + 2.0 * j;
+    E[(size_t)b * J + j] = fma(p, p, f * f / (w * w));
 }
 
 // operand layout in d_tc_ops (element size 4 bytes reserved for both precisions):
@@ -555,8 +566,15 @@ adscl_status tc_prepare(adscl_ctx *ctx, int precision)
             CK(cudaMemcpy(ctx->d_tc_modeoff + (size_t)g * kTcN, moff.data(), kTcN * sizeof(int64_t),
                           cudaMemcpyHostToDevice));
         }
-        CK(cudaMalloc(&ctx->d_tc_D, 2 * (size_t)ctx->tc_tiles * kTcM * kTcN * sizeof(float)));
-        CK(cudaMalloc(&ctx->d_tc_tasks, 2 * (size_t)ctx->tc_tiles * sizeof(TcTask)));
+        // K splits: about two CTAs per SM over all tiles, no split shorter than one chunk
+        int min_chunks = 1 << 30;
+        for (int t = 0; t < ctx->tc_tiles; ++t)
+            min_chunks = std::min(min_chunks, kpad_of(ctx->geoN[ctx->tc_tile_geo[t]]) / kTcKC);
+        ctx->tc_split = std::max(1, std::min(min_chunks, (2 * ctx->num_sms + 2 * ctx->tc_tiles - 1) /
+                                                             (2 * ctx->tc_tiles)));
+        const size_t ntask = 2 * (size_t)ctx->tc_tiles * ctx->tc_split;
+        CK(cudaMalloc(&ctx->d_tc_D, ntask * kTcM * kTcN * sizeof(float)));
+        CK(cudaMalloc(&ctx->d_tc_tasks, ntask * sizeof(TcTask)));
         CK(cudaMalloc(&ctx->d_tc_err, sizeof(int)));
         const int smem = 2 * (kTcM + kTcN) * kTcKC * 4;
         CK(cudaFuncSetAttribute(spectrum_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -599,7 +617,8 @@ adscl_status tc_prepare(adscl_ctx *ctx, int precision)
         ctx->tc_built_prec = precision;
     }
     // field operands of every tile, and the task list
-    std::vector<TcTask> tasks(2 * (size_t)ctx->tc_tiles);
+    const int S = ctx->tc_split;
+    std::vector<TcTask> tasks(2 * (size_t)ctx->tc_tiles * S);
     for (int t = 0; t < ctx->tc_tiles; ++t) {
         const int g = ctx->tc_tile_geo[t], n = ctx->geoN[g], kp = kpad_of(n);
         const size_t part = (size_t)kTcM * kp * esz, bpart = (size_t)kTcN * kp * esz;
@@ -625,9 +644,15 @@ adscl_status tc_prepare(adscl_ctx *ctx, int precision)
         CK(cudaGetLastError());
         ctx->launches += 2;
         char *Bg = grpB[g];
-        tasks[2 * t] = TcTask{U, U + part, Bg, Bg + bpart, kp, ctx->d_tc_D + (size_t)t * kTcM * kTcN};
-        tasks[2 * t + 1] = TcTask{U + 2 * part, U + 3 * part, Bg + 2 * bpart, Bg + 3 * bpart, kp,
-                                  ctx->d_tc_D + ((size_t)ctx->tc_tiles + t) * kTcM * kTcN};
+        const int nch = kp / kTcKC;
+        for (int q = 0; q < S; ++q) {
+            const int k0 = (int)((long long)q * nch / S), k1 = (int)((long long)(q + 1) * nch / S);
+            const size_t dp = ((size_t)t * S + q) * kTcM * kTcN;
+            const size_t df = (((size_t)ctx->tc_tiles + t) * S + q) * kTcM * kTcN;
+            tasks[(size_t)t * S + q] = TcTask{U, U + part, Bg, Bg + bpart, kp, k0, k1, ctx->d_tc_D + dp};
+            tasks[((size_t)ctx->tc_tiles + t) * S + q] =
+                TcTask{U + 2 * part, U + 3 * part, Bg + 2 * bpart, Bg + 3 * bpart, kp, k0, k1, ctx->d_tc_D + df};
+        }
     }
     CK(cudaMemcpyAsync(ctx->d_tc_tasks, tasks.data(), tasks.size() * sizeof(TcTask), cudaMemcpyHostToDevice,
                        ctx->stream));
@@ -1008,14 +1033,15 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
         if (s != ADSCL_OK) return s;
         CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), ctx->stream));
         const int smem = 2 * (kTcM + kTcN) * kTcKC * (precision == ADSCL_PREC_TF32X3 ? 4 : 2);
+        const int ntask = 2 * ctx->tc_tiles * ctx->tc_split;
         if (precision == ADSCL_PREC_TF32X3)
-            spectrum_tc_kernel<true><<<2 * ctx->tc_tiles, 128, smem, ctx->stream>>>(ctx->d_tc_tasks, ctx->d_tc_err);
+            spectrum_tc_kernel<true><<<ntask, 128, smem, ctx->stream>>>(ctx->d_tc_tasks, ctx->d_tc_err);
         else
-            spectrum_tc_kernel<false><<<2 * ctx->tc_tiles, 128, smem, ctx->stream>>>(ctx->d_tc_tasks, ctx->d_tc_err);
+            spectrum_tc_kernel<false><<<ntask, 128, smem, ctx->stream>>>(ctx->d_tc_tasks, ctx->d_tc_err);
         CK(cudaGetLastError());
         const int rows = ctx->tc_tiles * kTcM;
-        tc_energy_kernel<<<(rows + 127) / 128, 128, 0, ctx->stream>>>(
-            ctx->d_tc_D, ctx->d_tc_D + (size_t)rows * kTcN, ctx->d_tc_rowinst, rows, J, ctx->d_E);
+        tc_energy_kernel<<<(rows * J + 255) / 256, 256, 0, ctx->stream>>>(
+            ctx->d_tc_D, ctx->tc_tiles, ctx->tc_split, ctx->d_tc_rowinst, rows, J, ctx->d_E);
         CK(cudaGetLastError());
         ctx->launches += 2;
     }

@@ -7,6 +7,11 @@
 // of each product, so the projection carries a relative error of that order on top of FP32
 // accumulation; E_j is then formed in FP64 from the FP32 projections.
 //
+// Split K: a task covers K chunks [k0, k1) of one 128 x 64 tile and writes its FP32 partial
+// product; the partials of a tile are summed in FP64, in a fixed order, by the energy kernel
+// (the grid then has about two CTAs per SM instead of one per tile, and the FP32 sums run over
+// at most a few chunks).
+//
 // Data path per CTA (128 threads): for each 64-element K chunk the four operand tiles (U hi/lo:
 // 128 rows, B hi/lo: 64 rows) are copied from global memory into shared memory in the
 // no-swizzle K-major layout of 8-row x 16-byte core matrices (K-adjacent core matrices 128 B
@@ -30,8 +35,9 @@ constexpr long long kTcSpin = 1LL << 22;
 struct TcTask {
     const void *Ahi, *Alo;  // kTcM x Kpad rows of this tile (row-major, K contiguous)
     const void *Bhi, *Blo;  // kTcN x Kpad
-    int Kpad;               // multiple of kTcKC
-    float *D;               // kTcM x kTcN output
+    int Kpad;               // row length, a multiple of kTcKC
+    int k0, k1;             // K chunks [k0, k1) of this task (k1 > k0)
+    float *D;               // kTcM x kTcN partial product over those chunks
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -123,8 +129,7 @@ __global__ void __launch_bounds__(128) spectrum_tc_kernel(const TcTask *tasks, i
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    const int nchunks = t.Kpad / kTcKC;
-    for (int kc = 0; kc < nchunks; ++kc) {
+    for (int kc = t.k0; kc < t.k1; ++kc) {
         stage_tile<ES>(sAhi, (const char *)t.Ahi, kTcM, t.Kpad, kc);
         stage_tile<ES>(sAlo, (const char *)t.Alo, kTcM, t.Kpad, kc);
         stage_tile<ES>(sBhi, (const char *)t.Bhi, kTcN, t.Kpad, kc);
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(128) spectrum_tc_kernel(const TcTask *tasks, i
 #pragma unroll
             for (int s = 0; s < kSteps; ++s) {
                 const uint32_t o = s * 256;  // two K-adjacent core matrices per instruction
-                const uint32_t acc0 = (kc > 0 || s > 0) ? 1u : 0u;
+                const uint32_t acc0 = (kc > t.k0 || s > 0) ? 1u : 0u;
                 tc_mma<kTf32>(tmem, make_smem_desc(ahi + o, 128, sboA), make_smem_desc(bhi + o, 128, sboB), kIdesc, acc0);
                 tc_mma<kTf32>(tmem, make_smem_desc(ahi + o, 128, sboA), make_smem_desc(blo + o, 128, sboB), kIdesc, 1u);
                 tc_mma<kTf32>(tmem, make_smem_desc(alo + o, 128, sboA), make_smem_desc(bhi + o, 128, sboB), kIdesc, 1u);
@@ -149,7 +154,7 @@ __global__ void __launch_bounds__(128) spectrum_tc_kernel(const TcTask *tasks, i
         }
         // every thread waits for the MMAs before the tiles are overwritten (bounded)
         long long spin = 0;
-        while (!mbar_try_wait(mbar_addr, (uint32_t)(kc & 1))) {
+        while (!mbar_try_wait(mbar_addr, (uint32_t)((kc - t.k0) & 1))) {
             if (++spin > kTcSpin) {
                 s_fail = 1;
                 break;
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(128) spectrum_tc_kernel(const TcTask *tasks, i
     if (s_fail) {
         // give the tensor core a second bounded chance to finish before the memory is freed
         long long spin = 0;
-        while (!mbar_try_wait(mbar_addr, (uint32_t)((nchunks - 1) & 1)) && ++spin < kTcSpin) {}
+        while (!mbar_try_wait(mbar_addr, (uint32_t)((t.k1 - t.k0 - 1) & 1)) && ++spin < kTcSpin) {}
         if (threadIdx.x == 0) atomicExch(err, 1);
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
