@@ -11,7 +11,7 @@ namespace adscl {
     X(4, 4, 512, 1) X(5, 4, 512, 2)                                                      \
     X(6, 8, 256, 1) X(7, 8, 256, 2) X(8, 8, 256, 4)                                      \
     X(9, 4, 256, 1) X(10, 4, 256, 2) X(11, 4, 256, 4)                                    \
-    X(12, 8, 128, 1) X(13, 4, 128, 1)
+    X(12, 8, 128, 1) X(13, 4, 128, 1) X(14, 8, 128, 2) X(15, 8, 128, 4)
 
 #define ADSCL_ROW(i, p, nt, cl) {p, nt, cl},
 const Shape kShapes[kNumShapes] = {ADSCL_SHAPES(ADSCL_ROW)};

@@ -55,7 +55,7 @@ def test_every_built_shape_matches_oracle(ad, orc):
         assert np.abs(gP - oP).max() < 1e-13 * scale and np.abs(gQ - oQ).max() < 1e-13 * scale, \
             (P, NT, CL, N)
         s.close()
-    assert built >= 14
+    assert built >= 16
 
 
 def test_mixed_shapes_batch_equals_single_runs(ad):
