@@ -541,7 +541,23 @@ def main():
         sa.grad(a, Ta)
         torch.cuda.synchronize()
         t_adj_t = time.perf_counter() - t0
+        cpu_adj = None
+        if ws == 1 and not args.no_cpu_baseline:
+            # the oracle's own gradient / forward time ratio on a bounded sample of the same
+            # problem (one instance, 64 steps; sequential C, one thread)
+            import oracle
+            oracle.build()
+            n_s = 64
+            t0 = time.perf_counter()
+            oracle.functional(a[0], ainst[0].N, n_s, dta[0], sigma=SIGMA_KO, Jm=32)
+            t_of = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            oracle.grad(a[0], ainst[0].N, n_s, dta[0], sigma=SIGMA_KO, Jm=32)
+            t_og = time.perf_counter() - t0
+            cpu_adj = {"ratio": t_og / t_of, "forward_s": t_of, "grad_s": t_og,
+                       "sample": f"1 instance, N={ainst[0].N}, {n_s} steps, oracle (1 thread)"}
         adj = {"value": t_adj / t_fwd, "forward_ms": 1e3 * t_fwd, "grad_ms": 1e3 * t_adj,
+               "cpu_oracle": cpu_adj,
                "forward_shape_P_NT_CL": [8, 512, 1],
                "tuned": {"forward_shape_P_NT_CL": list(tuned[ainst[0].N]),
                          "forward_ms": 1e3 * t_fwd_t, "grad_ms": 1e3 * t_adj_t,
