@@ -180,10 +180,13 @@ adscl_status adscl_get_clock(adscl_ctx *ctx, double *dt, int64_t *step);
  * that fits N -- P grid nodes per thread, NT threads per CTA (so 512 / NT CTAs per SM), CL CTAs
  * (a thread-block cluster) per instance -- on the context's own instances of that N for
  * trial_steps RK4 steps (0 = 8) from their current slices, keep the fastest, and restore the
- * state (the call changes no instance's slice, step or status).  With several grid sizes, which
+ * state (the call changes no instance's slice -- Phi, Pi and, under the evolved-A schemes, A --
+ * step or status).  With several grid sizes, which
  * run concurrently in a batch, the per-size choice is kept only if the whole batch (timed over
  * max(4 trial_steps, 32) steps) is more than 1 % faster with it than with the default shapes.  Results are cached for the process by (GPU name, SM count,
- * the batch's grid sizes with their instance counts); a cached entry is reused without timing.  Synchronous.  No-op for the evolved-A and fixed-metric schemes (one shape).
+ * the batch's grid sizes with their instance counts); a cached entry is reused without timing.
+ * Synchronous.  The evolved-A and fixed-metric kernels are built for the shapes (8, 512, 1/2/4/8),
+ * (8, 256, 2) and (8, 128, 2).
  * Different shapes associate the radial scans differently, so results agree with the default
  * shape to rounding, not bit for bit. */
 adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps);

@@ -43,9 +43,9 @@ int cluster_of(int N)
 // default shape of grid size N: P = 8, NT = 512 and the smallest cluster that holds the grid
 int default_shape(int N) { return shape_index(kP, kNT, cluster_of(N)); }
 
-// autotuner results of this process: (device name, SM count, the batch's (N, instances of that
-// N) in decreasing N) -> shape of each of those N
-using TuneKey = std::tuple<std::string, int, std::vector<std::pair<int, int>>>;
+// autotuner results of this process: (device name, SM count, scheme, the batch's (N, instances
+// of that N) in decreasing N) -> shape of each of those N
+using TuneKey = std::tuple<std::string, int, int, std::vector<std::pair<int, int>>>;
 std::map<TuneKey, std::vector<int>> g_tuned;
 std::mutex g_tuned_mu;
 static_assert(6 * field_stride<kP>(kMaxPoints1) * 8 + 4096 <= 232448, "shared memory budget");
@@ -187,28 +187,24 @@ double step_for(int N, double cfl, double cadence)
     return cadence / std::ceil(cadence / (cfl * h));
 }
 
-// the evolved-A / fixed-metric kernel of cluster size CL: its function pointer
-template <bool FIXED>
-const void *ea_kernel_of(int CL)
+// the evolved-A / fixed-metric kernel is built for the shapes (8, 512, 1/2/4/8), (8, 256, 2) and
+// (8, 128, 2); ea_dispatch calls f.template operator()<NT, CL>() for the shape with index id
+bool ea_shape(int id)
 {
-    switch (CL) {
-    case 1: return (const void *)evolve_ea_kernel<kP, kNT, FIXED, 1>;
-    case 2: return (const void *)evolve_ea_kernel<kP, kNT, FIXED, 2>;
-    case 4: return (const void *)evolve_ea_kernel<kP, kNT, FIXED, 4>;
-    default: return (const void *)evolve_ea_kernel<kP, kNT, FIXED, 8>;
-    }
+    const Shape &sh = kShapes[id];
+    return sh.P == 8 && ((sh.NT == 512) || (sh.NT == 256 && sh.CL == 2) || (sh.NT == 128 && sh.CL == 2));
 }
 
-template <bool FIXED, int CL>
+template <bool FIXED, int NT, int CL>
 cudaError_t ea_launch_t(const EaArgs &ea, int units, size_t smem, int stride, cudaStream_t sm)
 {
     if constexpr (CL == 1) {
-        evolve_ea_kernel<kP, kNT, FIXED, 1><<<units, kNT, smem, sm>>>(ea, stride);
+        evolve_ea_kernel<kP, NT, FIXED, 1><<<units, NT, smem, sm>>>(ea, stride);
         return cudaGetLastError();
     } else {
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(CL * units, 1, 1);
-        cfg.blockDim = dim3(kNT, 1, 1);
+        cfg.blockDim = dim3(NT, 1, 1);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = sm;
         cudaLaunchAttribute attr[1];
@@ -218,39 +214,60 @@ cudaError_t ea_launch_t(const EaArgs &ea, int units, size_t smem, int stride, cu
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, evolve_ea_kernel<kP, kNT, FIXED, CL>, ea, stride);
+        return cudaLaunchKernelEx(&cfg, evolve_ea_kernel<kP, NT, FIXED, CL>, ea, stride);
     }
+}
+
+// kernel pointer (launch = false) or launch (launch = true) of the shape with index id
+template <bool FIXED>
+cudaError_t ea_select(int id, bool launch, const void **fn, const EaArgs *ea, int units, size_t smem, int stride,
+                      cudaStream_t sm)
+{
+    const Shape &sh = kShapes[id];
+#define ADSCL_EA(NT_, CL_)                                                                  \
+    if (sh.P == 8 && sh.NT == NT_ && sh.CL == CL_) {                                        \
+        if (fn) *fn = (const void *)evolve_ea_kernel<kP, NT_, FIXED, CL_>;                  \
+        return launch ? ea_launch_t<FIXED, NT_, CL_>(*ea, units, smem, stride, sm) : cudaSuccess; \
+    }
+    ADSCL_EA(512, 1) ADSCL_EA(512, 2) ADSCL_EA(512, 4) ADSCL_EA(512, 8) ADSCL_EA(256, 2) ADSCL_EA(128, 2)
+#undef ADSCL_EA
+    return cudaErrorInvalidValue;
 }
 
 template <bool FIXED>
-cudaError_t ea_launch(const EaArgs &ea, int CL, int units, size_t smem, int stride, cudaStream_t sm)
+const void *ea_kernel_of(int id)
 {
-    switch (CL) {
-    case 1: return ea_launch_t<FIXED, 1>(ea, units, smem, stride, sm);
-    case 2: return ea_launch_t<FIXED, 2>(ea, units, smem, stride, sm);
-    case 4: return ea_launch_t<FIXED, 4>(ea, units, smem, stride, sm);
-    default: return ea_launch_t<FIXED, 8>(ea, units, smem, stride, sm);
-    }
+    const void *fn = nullptr;
+    ea_select<FIXED>(id, false, &fn, nullptr, 0, 0, 0, nullptr);
+    return fn;
 }
 
-// co-resident units of the evolved-A / fixed-metric kernel of cluster size CL
-cudaError_t ea_max_units(bool fixed, int CL, size_t smem, int num_sms, int *units)
+template <bool FIXED>
+cudaError_t ea_launch(const EaArgs &ea, int id, int units, size_t smem, int stride, cudaStream_t sm)
 {
-    const void *fn = fixed ? ea_kernel_of<true>(CL) : ea_kernel_of<false>(CL);
+    return ea_select<FIXED>(id, true, nullptr, &ea, units, smem, stride, sm);
+}
+
+// co-resident units of the evolved-A / fixed-metric kernel of shape id
+cudaError_t ea_max_units(bool fixed, int id, size_t smem, int num_sms, int *units)
+{
+    const void *fn = fixed ? ea_kernel_of<true>(id) : ea_kernel_of<false>(id);
+    const Shape &sh = kShapes[id];
     *units = 0;
-    if (CL == 1) {
+    if (!fn) return cudaErrorInvalidValue;
+    if (sh.CL == 1) {
         int per_sm = 0;
-        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kNT, smem);
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, sh.NT, smem);
         *units = per_sm * num_sms;
         return e;
     }
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(CL * (num_sms / CL), 1, 1);
-    cfg.blockDim = dim3(kNT, 1, 1);
+    cfg.gridDim = dim3(sh.CL * (num_sms / sh.CL), 1, 1);
+    cfg.blockDim = dim3(sh.NT, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.x = sh.CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -270,7 +287,7 @@ adscl_status max_units(adscl_ctx *ctx, int id, size_t smem, int *units)
     int u = 0;
     const cudaError_t e = (ctx->scheme == ADSCL_SCHEME_RK4)
         ? shape_max_units(id, smem, ctx->num_sms, &u)
-        : ea_max_units(ctx->scheme == ADSCL_SCHEME_FIXED_METRIC_RK3, kShapes[id].CL, smem, ctx->num_sms, &u);
+        : ea_max_units(ctx->scheme == ADSCL_SCHEME_FIXED_METRIC_RK3, id, smem, ctx->num_sms, &u);
     if (e != cudaSuccess || u < 1)
         return fail(ctx, ADSCL_EUNSUPPORTED, "shape (%d, %d, %d) of the evolve kernel does not fit (%s)",
                     kShapes[id].P, kShapes[id].NT, kShapes[id].CL, cudaGetErrorString(e));
@@ -412,10 +429,10 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
             ea.A = ctx->d_A;
             ea.order = (ctx->scheme == ADSCL_SCHEME_EVOLVED_A_RK2) ? 2 : 3;
             ea.reint = ctx->reint;
-            const int cl = kShapes[shp[g]].CL, st = shape_stride(shp[g], nmax[g]);
+            const int st = shape_stride(shp[g], nmax[g]);
             CK(ctx->scheme == ADSCL_SCHEME_FIXED_METRIC_RK3
-                   ? ea_launch<true>(ea, cl, units_of[g], smem[g], st, gs)
-                   : ea_launch<false>(ea, cl, units_of[g], smem[g], st, gs));
+                   ? ea_launch<true>(ea, shp[g], units_of[g], smem[g], st, gs)
+                   : ea_launch<false>(ea, shp[g], units_of[g], smem[g], st, gs));
         }
         ctx->launches += 2;
     }
@@ -891,9 +908,10 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     // the attribute is per kernel, not per context: always raise it to the largest grid
     const size_t smem_max = (size_t)6 * field_stride<kP>(kMaxPoints1) * sizeof(double);
     CK(shapes_set_attributes());
-    for (int cl = 1; cl <= kMaxCluster; cl *= 2) {
-        CK(cudaFuncSetAttribute(ea_kernel_of<false>(cl), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-        CK(cudaFuncSetAttribute(ea_kernel_of<true>(cl), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    for (int id = 0; id < kNumShapes; ++id) {
+        if (!ea_shape(id)) continue;
+        CK(cudaFuncSetAttribute(ea_kernel_of<false>(id), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+        CK(cudaFuncSetAttribute(ea_kernel_of<true>(id), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
     }
     // default kernel shapes; every shape in use must fit the device
     ctx->shape_of.resize(ctx->B);
@@ -1445,8 +1463,9 @@ adscl_status adscl_set_shape(adscl_ctx *ctx, int32_t N, int32_t P, int32_t NT, i
     const int id = shape_index(P, NT, CL);
     if (id < 0) return fail(ctx, ADSCL_EINVAL, "shape (%d, %d, %d) is not built", P, NT, CL);
     if (!shape_fits(id, N)) return fail(ctx, ADSCL_EINVAL, "shape (%d, %d, %d) does not fit N = %d", P, NT, CL, N);
-    if (ctx->scheme != ADSCL_SCHEME_RK4 && id != default_shape(N))
-        return fail(ctx, ADSCL_EINVAL, "the evolved-A and fixed-metric schemes run the default shapes");
+    if (ctx->scheme != ADSCL_SCHEME_RK4 && !ea_shape(id))
+        return fail(ctx, ADSCL_EINVAL, "the evolved-A and fixed-metric kernels are not built with shape (%d, %d, %d)",
+                    P, NT, CL);
     int u = 0;
     s = max_units(ctx, id, shape_smem(id, N), &u);
     if (s != ADSCL_OK) return s;
@@ -1464,18 +1483,19 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
 {
     adscl_status s = check_ctx(ctx);
     if (s != ADSCL_OK) return s;
-    if (ctx->scheme != ADSCL_SCHEME_RK4) return ADSCL_OK;   // one shape only
+    const bool ea_scheme = ctx->scheme != ADSCL_SCHEME_RK4;
     const int trial = trial_steps > 0 ? trial_steps : 8;
     const int B = ctx->B;
     const size_t fb = (size_t)ctx->total * sizeof(double);
     CK(cudaStreamSynchronize(ctx->stream));
     // the state is saved here and restored after every trial
-    double *bPhi = nullptr, *bPi = nullptr;
+    double *bPhi = nullptr, *bPi = nullptr, *bA = nullptr;   // bA: the evolved A (its schemes)
     InstState *bSt = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto cleanup = [&]() {
         if (bPhi) cudaFree(bPhi);
         if (bPi) cudaFree(bPi);
+        if (bA) cudaFree(bA);
         if (bSt) cudaFree(bSt);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
@@ -1489,6 +1509,10 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
         CK(cudaMemcpyAsync(bPhi, ctx->d_Phi, fb, cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(bPi, ctx->d_Pi, fb, cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(bSt, ctx->d_st, B * sizeof(InstState), cudaMemcpyDeviceToDevice, ctx->stream));
+        if (ctx->d_A) {
+            CK(cudaMalloc(&bA, fb));
+            CK(cudaMemcpyAsync(bA, ctx->d_A, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
         std::vector<InstState> st0(B), st1(B);
         CK(cudaMemcpyAsync(st0.data(), ctx->d_st, B * sizeof(InstState), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
@@ -1496,6 +1520,7 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
             CK(cudaMemcpyAsync(ctx->d_Phi, bPhi, fb, cudaMemcpyDeviceToDevice, ctx->stream));
             CK(cudaMemcpyAsync(ctx->d_Pi, bPi, fb, cudaMemcpyDeviceToDevice, ctx->stream));
             CK(cudaMemcpyAsync(ctx->d_st, bSt, B * sizeof(InstState), cudaMemcpyDeviceToDevice, ctx->stream));
+            if (bA) CK(cudaMemcpyAsync(ctx->d_A, bA, fb, cudaMemcpyDeviceToDevice, ctx->stream));
             CK(cudaMemsetAsync(ctx->d_ctl, 0, (B + 1) * sizeof(QueueCtl), ctx->stream));
             return ADSCL_OK;
         };
@@ -1514,7 +1539,7 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
         auto set_run = [&](int r, int id) {
             for (int q = run_start[r]; q < run_start[r + 1]; ++q) ctx->shape_of[ord[q]] = id;
         };
-        const TuneKey key{ctx->dev_name, ctx->num_sms, sig};
+        const TuneKey key{ctx->dev_name, ctx->num_sms, ctx->scheme, sig};
         {
             std::lock_guard<std::mutex> lk(g_tuned_mu);
             auto it = g_tuned.find(key);
@@ -1561,9 +1586,12 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
             best[r] = -1;
             double best_rate = 0.0;
             for (int id = 0; id < kNumShapes; ++id) {
-                if (!shape_fits(id, n)) continue;
+                if (!shape_fits(id, n) || (ea_scheme && !ea_shape(id))) continue;
                 int u = 0;
-                if (shape_max_units(id, shape_smem(id, n), ctx->num_sms, &u) != cudaSuccess || u < 1) {
+                const cudaError_t eu = ea_scheme
+                    ? ea_max_units(ctx->scheme == ADSCL_SCHEME_FIXED_METRIC_RK3, id, shape_smem(id, n), ctx->num_sms, &u)
+                    : shape_max_units(id, shape_smem(id, n), ctx->num_sms, &u);
+                if (eu != cudaSuccess || u < 1) {
                     (void)cudaGetLastError();
                     continue;
                 }

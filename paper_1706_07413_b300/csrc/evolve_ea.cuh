@@ -48,7 +48,7 @@ struct EaArgs {
 };
 
 template <int P, int NT, bool FIXED = false, int CL = 1>
-__global__ void __launch_bounds__(NT, 1) evolve_ea_kernel(EaArgs ea, int stride)
+__global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kernel(EaArgs ea, int stride)
 {
     static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
     static_assert(CL == 1 || CL == 2 || CL == 4 || CL == 8, "cluster of 1, 2, 4 or 8 CTAs");

@@ -83,7 +83,7 @@ def test_batch_chunks_and_restarts_are_bit_identical(ad):
 def test_unsupported_requests_fail_cleanly(ad):
     s = ad.Solver([257] * 2, scheme=1)
     with pytest.raises(ad.AdsclError) as e:
-        s.set_shape(257, 8, 256, 2)          # the evolved-A kernels run the default shapes
+        s.set_shape(257, 4, 256, 1)          # not among the evolved-A kernel's shapes
     assert e.value.status == ad.ADSCL_EINVAL
     s.set_initial_modes(np.full((2, 4), 0.01))
     with pytest.raises(ad.AdsclError) as e:
@@ -162,3 +162,41 @@ def test_fixed_metric_on_an_eight_cta_cluster(ad, orc):
     w, T = 3.0 + 2.0 * j, n * dt[0]
     assert np.abs(gQ - np.cos(w * T) * e[j]).max() < 1e-9
     assert np.all(gA == 1.0) and np.all(gd == 0.0)
+
+
+@pytest.mark.parametrize("N,shape", [(4097, (8, 256, 2)), (2049, (8, 128, 2)), (1025, (8, 256, 2))])
+@pytest.mark.parametrize("scheme", [1, 3])
+def test_evolved_a_shapes_match_oracle(ad, orc, N, shape, scheme):
+    Phi, Pi = W.smooth_random(N, seed=N + scheme, amp=2.0)
+    s = ad.Solver([N, N], scheme=scheme, a_reint_every=3, chunk_steps=2)
+    s.set_shape(N, *shape)
+    assert s.shape(0) == shape
+    s.set_initial(W.packed([Phi, Phi]), W.packed([Pi, Pi]))
+    dt, _ = s.clock()
+    s.evolve(7 * dt[0])
+    gP, gQ, gA, _ = s.get_state(1)
+    if scheme == 1:
+        r = orc.ea_evolve(Phi, Pi, orc.constraints(Phi, Pi)[0], dt[0], 7, order=3, reint=3, sigma=0.5)
+        oP, oQ, oA = r.Phi, r.Pi, r.A
+    else:
+        oP, oQ = orc.fixed_evolve(Phi, Pi, dt[0], 7, order=3, sigma=0.5)
+        oA = np.ones(N)
+    assert _close(gP, oP, 1e-11) and _close(gQ, oQ, 1e-11) and _close(gA, oA, 1e-11)
+
+
+def test_evolved_a_autotune_keeps_state(ad):
+    Ns = [2049] * 3 + [4097] * 2
+    fields = [W.smooth_random(n, seed=600 + i, amp=2.0) for i, n in enumerate(Ns)]
+    s = ad.Solver(Ns, scheme=1, a_reint_every=8)
+    s.set_initial(W.packed([f[0] for f in fields]), W.packed([f[1] for f in fields]))
+    s.evolve(0.005)
+    before = [s.get_state(b) for b in range(len(Ns))]
+    clk = s.clock()[1].copy()
+    shapes = s.autotune(trial_steps=4)
+    for n, shp in shapes.items():
+        assert shp[0] == 8 and (shp[1] == 512 or shp[2] == 2)
+    for b in range(len(Ns)):
+        after = s.get_state(b)
+        for x, y in zip(before[b][:3], after[:3]):   # Phi, Pi and the evolved A are state
+            assert np.array_equal(x, y)
+    assert np.array_equal(clk, s.clock()[1])
