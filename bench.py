@@ -60,7 +60,9 @@ REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
 # capture of this script (profiles/evolve_kernel_amp_scan.md); reported only while the kernel
 # source and the kernel shape are the ones the counters were taken on.
 TRAFFIC = {"kernel_sha256": "9f96ba6ab40c1dd6e1a8641c5b14bb3371717fe6fd03389bf0624e3b27f8b4f6",
-           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17725440 + 223519488}
+           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17725440 + 223519488,
+           # FP64 instructions (DADD + DMUL + DFMA, thread level) per point-substep, same capture
+           "fp64_instr_per_point_substep": (22380060672 + 15031607296 + 42847711232) / 1074003968}
 
 
 def kernel_digest():
@@ -447,14 +449,20 @@ def main():
 
     # roofline of the evolution kernel (it is >99% of each timed launch)
     achieved_tflops = (work * flops_pps) / dev_s / 1e12
-    traffic = None
+    traffic = issue = None
     if amp and kernel_digest() == TRAFFIC["kernel_sha256"] and \
             list(shapes.get(N_DEFAULT, ())) == TRAFFIC["shape_P_NT_CL"]:
         traffic = TRAFFIC["dram_bytes_per_launch"]
+        # FP64 issue: instructions per second against the probe's FMA rate (one FMA = 2 flops)
+        ipps = TRAFFIC["fp64_instr_per_point_substep"]
+        issue = {"fp64_instr_per_point_substep": ipps,
+                 "achieved_ginstr_per_s": work * ipps / dev_s / 1e9,
+                 "peak_ginstr_per_s": tflops_peak * 1e12 / 2 / 1e9,
+                 "frac": (work * ipps / dev_s) / (tflops_peak * 1e12 / 2)}
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": tflops_peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / tflops_peak, "traffic": traffic,
                 "peak_source": "measured FP64 FMA-chain probe on this GPU (FMA = 2 flops)",
-                "flops_per_point_substep": flops_pps}
+                "flops_per_point_substep": flops_pps, "fp64_issue": issue}
 
     # the other two batch shapes, one launch of 128 RK4 steps each (default workload only)
     others = None
