@@ -39,19 +39,20 @@ B_DEFAULT, N_DEFAULT = 256, 4097
 THETA = 2.0 ** -7
 SIGMA_KO = 0.5
 # Algorithmic FP64 flops (FMA = 2) per point-substep, tallied from the evolution kernel's
-# source for the sequential scheme it computes: cell data (rho, midpoint interpolation,
-# Simpson increment, RK4-in-x affine map) 45; sequential scans, A, the fused A e^{-delta}
-# (17, table-driven exp), fluxes 24.75; RHS stencils with dissipation 31; RK4 update 7.
-# The parallel-scan overheads (per-thread aggregates, warp shuffles, ~7 flops) are not counted.
-FLOPS_PER_POINT_SUBSTEP = 107.75
+# source for the sequential scheme it computes: cell data 40 (rho and its node factors 5,
+# midpoint interpolation, rho and factors 13, Simpson increment 3, RK4-in-x affine map
+# 19); sequential scans, A, the fused A e^{-delta} (13, table-driven exp on the argument in
+# units of ln2/256), fluxes 20.75; RHS stencils with dissipation 30; RK4 update 7.  The
+# parallel-scan overheads (per-thread aggregates, warp shuffles, ~7 flops) are not counted.
+FLOPS_PER_POINT_SUBSTEP = 97.75
 # The same tally for the evolved-A schemes (A from Eq. (eq:adot), SSP Runge-Kutta), per stage:
-# delta cell data 20, delta scan 1, fused A e^{-delta} 17, fluxes 3, A-dot 3 and the A update
-# (SSP-RK3: 4 on average over the stages), slice mass 2 (once per step), RHS 31, Phi/Pi update
+# delta cell data 20, delta scan 1, fused A e^{-delta} 13, fluxes 3, A-dot 3 and the A update
+# (SSP-RK3: 4 on average over the stages), slice mass 2 (once per step), RHS 30, Phi/Pi update
 # (SSP-RK3: 8 on average); the re-integration of A every 64 steps adds < 0.2 and is not counted.
 SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A re-integration)
     "rk4": (0, 4, FLOPS_PER_POINT_SUBSTEP, 0),
-    "evolved_a_rk3": (1, 3, 89.0, 64),
-    "evolved_a_rk2": (2, 2, 88.5, 64),
+    "evolved_a_rk3": (1, 3, 84.0, 64),
+    "evolved_a_rk2": (2, 2, 83.5, 64),
 }
 L2_FLUSH_BYTES = 512 << 20
 CPU_SAMPLE_STEPS = 800    # oracle sample of the cpu_baseline leg: ~10 s on 16 host threads

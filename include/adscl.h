@@ -211,6 +211,12 @@ adscl_status adscl_probe_fp64(int32_t device, void *stream, double *tflops);
  * Synchronous; allocates its own device buffers. */
 adscl_status adscl_exp_neg(int32_t device, const double *x, double *y, int64_t n);
 
+/* The same with the argument in units of ln2/256: y = e^{-X ln2/256} for n host values X >= 0.
+ * This is the form the evolution kernels use (they accumulate delta in these units, which makes
+ * the argument reduction exact without a two-term ln2).  Synchronous; allocates its own device
+ * buffers. */
+adscl_status adscl_exp_neg_scaled(int32_t device, const double *X, double *y, int64_t n);
+
 /* ---- evolution without device allocation ----------------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers of the library.
  *

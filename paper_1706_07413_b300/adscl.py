@@ -69,6 +69,7 @@ SIGNATURES = {
     "adscl_set_shape": ([_VP, _I32, _I32, _I32, _I32], ctypes.c_int),
     "adscl_probe_fp64": ([_I32, _VP, _VP], ctypes.c_int),
     "adscl_exp_neg": ([_I32, _VP, _VP, _I64], ctypes.c_int),
+    "adscl_exp_neg_scaled": ([_I32, _VP, _VP, _I64], ctypes.c_int),
     "adscl_evolve_noalloc": ([_I32, _VP, _I32, _I32, _VP, _VP, _F, _F, _F, _F, _VP, _VP, _VP, _VP],
                              ctypes.c_int),
     "adscl_last_error": ([_VP], ctypes.c_char_p),
@@ -117,6 +118,18 @@ def exp_neg(x, device=0):
     st = lib.adscl_exp_neg(device, x.ctypes.data, y.ctypes.data, x.size)
     if st != ADSCL_OK:
         raise AdsclError(st, "exp_neg failed")
+    return y
+
+
+def exp_neg_scaled(X, device=0):
+    """The solver's e^{-X ln2/256} (argument in units of ln2/256, as the kernels use it) on a
+    host array."""
+    lib = load()
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    y = np.empty_like(X)
+    st = lib.adscl_exp_neg_scaled(device, X.ctypes.data, y.ctypes.data, X.size)
+    if st != ADSCL_OK:
+        raise AdsclError(st, "exp_neg_scaled failed")
     return y
 
 

@@ -153,16 +153,18 @@ adscl_status fail(adscl_ctx *c, adscl_status s, const char *fmt, ...)
     } while (0)
 
 // Geometry factors of one grid size (host libm, FP64); layout: ws, wt, K, T, iT12 (N each),
-// wsm3, wtm (N-1 each).
-std::vector<double> make_geometry(int N)
+// wsm3, wtm (N-1 each), wsk, iT12k (N each; iT12k depends on the dissipation sigma).
+constexpr int kGeoTables = 9;
+std::vector<double> make_geometry(int N, double sigma)
 {
     const double h = 0.5 * M_PI / (double)(N - 1);
-    std::vector<double> t((size_t)7 * N, 0.0);
+    std::vector<double> t((size_t)kGeoTables * N, 0.0);
     double *ws = t.data(), *wt = ws + N, *K = wt + N, *T = K + N, *iT12 = T + N, *wsm3 = iT12 + N,
-           *wtm = wsm3 + N;
+           *wtm = wsm3 + N, *wsk = wtm + N, *iT12k = wsk + N;
     for (int i = 0; i < N; ++i) {
         const double x = i * h, s = std::sin(x), c = std::cos(x);
         ws[i] = h * s * c / 6.0;
+        wsk[i] = kKappa * ws[i];
         if (i < N - 1) {
             const double tn = std::tan(x);
             T[i] = tn * tn;
@@ -171,6 +173,7 @@ std::vector<double> make_geometry(int N)
         if (i > 0 && i < N - 1) {
             K[i] = c * c * c / s;
             iT12[i] = 1.0 / (12.0 * h * T[i]);
+            iT12k[i] = it12k_of(h, T[i], sigma);
         }
     }
     for (int c = 0; c < N - 1; ++c) {
@@ -797,13 +800,13 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
             geoN.push_back(n);
         }
     size_t geo_doubles = 0;
-    for (int n : geoN) geo_doubles += (size_t)7 * n;
+    for (int n : geoN) geo_doubles += (size_t)kGeoTables * n;
     CK(cudaMalloc(&ctx->d_geo_block, geo_doubles * sizeof(double)));
     std::vector<GeoTab> h_geo;
     {
         size_t pos = 0;
         for (int n : geoN) {
-            std::vector<double> t = make_geometry(n);
+            std::vector<double> t = make_geometry(n, ctx->sigma);
             CK(cudaMemcpy(ctx->d_geo_block + pos, t.data(), t.size() * sizeof(double),
                           cudaMemcpyHostToDevice));
             const double *base = ctx->d_geo_block + pos;
@@ -815,6 +818,8 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
             g.iT12 = base + 4 * (size_t)n;
             g.wsm3 = base + 5 * (size_t)n;
             g.wtm = base + 6 * (size_t)n;
+            g.wsk = base + 7 * (size_t)n;
+            g.iT12k = base + 8 * (size_t)n;
             h_geo.push_back(g);
             pos += t.size();
         }
@@ -853,18 +858,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
         d.N = n;
         d.geo = geo_of[n];
         d.off = ctx->off[b];
-        d.dt = step_for(n, cfl, cad);
-        d.dt2 = 0.5 * d.dt;
-        d.dt3 = d.dt / 3.0;
-        d.dt6 = d.dt / 6.0;
-        d.c12 = 1.0 / (12.0 * h);
-        d.c3 = 3.0 / (12.0 * h);
-        d.cko = ctx->sigma / (64.0 * h);
-        d.rko = 3.0 * ctx->sigma / 16.0;
-        d.dt6c = d.dt6 * d.c12;
-        d.dt3c = d.dt3 * d.c12;
-        d.dt2c = d.dt2 * d.c12;
-        d.dtc = d.dt * d.c12;
+        set_desc_coeffs(d, h, step_for(n, cfl, cad), ctx->sigma);
     }
     CK(cudaMalloc(&ctx->d_desc, ctx->B * sizeof(InstDesc)));
     CK(cudaMemcpy(ctx->d_desc, ctx->h_desc.data(), ctx->B * sizeof(InstDesc), cudaMemcpyHostToDevice));

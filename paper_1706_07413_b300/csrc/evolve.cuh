@@ -9,8 +9,9 @@
 //
 // Per RK stage:
 //   1. cell data: rho at nodes and (4-point interpolated) midpoints, the Simpson increment
-//      Delta_c of Eq. (eq:delta) and the RK4-in-x affine map m -> alpha_c m + beta_c of the
-//      mass-function form of Eq. (eq:aprime);
+//      Delta_c of Eq. (eq:delta) (in units of ln2/256, the reduction unit of the exponential)
+//      and the RK4-in-x affine map m -> alpha_c m + beta_c of the mass-function form of
+//      Eq. (eq:aprime);
 //   2. a block scan: delta as a suffix sum of Delta, m as a prefix composition of affine maps
 //      (per-thread serial, then warp shuffles, then one warp over the warp totals);
 //   3. A = 1 - m cos^3 x / sin x, F = A e^{-delta}, fluxes f = F Pi and u = tan^2 x F Phi;
@@ -47,6 +48,8 @@ struct GeoTab {
     const double *iT12;  // 1 / (12 h tan^2 x)       (0 at both ends)
     const double *wsm3;  // 3 h sin x cos x / (6*256) at x_{c+1/2}
     const double *wtm;   // h tan^2 x / (6*256)       at x_{c+1/2}
+    const double *wsk;   // kappa ws, kappa = 256 / ln 2 (delta is accumulated in units of ln2/256)
+    const double *iT12k; // iT12 / cq, cq = the dissipation factor of Pi-dot (sigma / (64 h), 1 if 0)
 };
 
 struct InstDesc {
@@ -59,7 +62,41 @@ struct InstDesc {
     double cko;   // sigma / (64 h)
     double rko;   // cko / c12 = 3 sigma / 16
     double dt6c, dt3c, dt2c, dtc;  // dt/6, dt/3, dt/2, dt times c12
+    double dt6q, dt3q, dt2q, dtq;  // dt/6, dt/3, dt/2, dt times cq (Pi-dot is computed divided by cq)
+    double c3q;   // c3 / cq
+    int32_t ko;   // sigma > 0: dissipation on
+    int32_t pad;
 };
+
+// the per-instance coefficients above, for grid spacing h, step dt and dissipation sigma
+__host__ inline void set_desc_coeffs(InstDesc &d, double h, double dt, double sigma)
+{
+    d.dt = dt;
+    d.dt2 = 0.5 * dt;
+    d.dt3 = dt / 3.0;
+    d.dt6 = dt / 6.0;
+    d.c12 = 1.0 / (12.0 * h);
+    d.c3 = 3.0 / (12.0 * h);
+    d.cko = sigma / (64.0 * h);
+    d.rko = 3.0 * sigma / 16.0;
+    d.dt6c = d.dt6 * d.c12;
+    d.dt3c = d.dt3 * d.c12;
+    d.dt2c = d.dt2 * d.c12;
+    d.dtc = d.dt * d.c12;
+    const double cq = sigma > 0.0 ? d.cko : 1.0;
+    d.dt6q = d.dt6 * cq;
+    d.dt3q = d.dt3 * cq;
+    d.dt2q = d.dt2 * cq;
+    d.dtq = d.dt * cq;
+    d.c3q = d.c3 / cq;
+    d.ko = sigma > 0.0 ? 1 : 0;
+    d.pad = 0;
+}
+// iT12k of one node: 1 / (12 h T cq) = 16 / (3 sigma T) for sigma > 0 (0 where iT12 is 0)
+__host__ __device__ inline double it12k_of(double h, double T, double sigma)
+{
+    return sigma > 0.0 ? 16.0 / (3.0 * sigma * T) : 1.0 / (12.0 * h * T);
+}
 
 enum : int32_t { kRunning = 0, kDone = 1, kCollapsed = 2, kNonfinite = 3, kTimeout = 4 };
 
@@ -392,13 +429,13 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                         double pm1 = Sp[soff<P>(-1)], p0 = Sp[soff<P>(0)], p1 = Sp[soff<P>(1)];
                         double qm1 = Sq[soff<P>(-1)], q0 = Sq[soff<P>(0)], q1 = Sq[soff<P>(1)];
                         const double rho0 = fma(p0, p0, q0 * q0);
-                        double qn0 = __ldg(g.ws + i0) * rho0, rn0 = __ldg(g.wt + i0) * rho0;
+                        double qn0 = __ldg(g.wsk + i0) * rho0, rn0 = __ldg(g.wt + i0) * rho0;
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int c = i0 + k;
                             const double p2 = Sp[soff<P>(k + 2)], q2 = Sq[soff<P>(k + 2)];
                             const double rho1 = fma(p1, p1, q1 * q1);
-                            const double qn1 = __ldg(g.ws + c + 1) * rho1;
+                            const double qn1 = __ldg(g.wsk + c + 1) * rho1;   // kappa q1
                             const double rn1 = __ldg(g.wt + c + 1) * rho1;
                             // 16 * (midpoint value) by the 4-point Lagrange formula
                             const double p16 = fma(9.0, p0 + p1, -(pm1 + p2));
@@ -406,24 +443,27 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             const double rm = fma(p16, p16, q16 * q16);  // 256 rho_{c+1/2}
                             const double qm3 = __ldg(g.wsm3 + c) * rm;   // 3 (h s rho / 6) at the midpoint
                             const double tm = __ldg(g.wtm + c) * rm;     // h tan^2 rho / 6 there
-                            const double s01 = qn0 + qn1;
-                            // Simpson increment of delta over the cell
-                            De[k] = fma(4.0 / 3.0, qm3, s01);
+                            const double s01 = qn0 + qn1;                     // kappa (q0 + q1)
+                            // Simpson increment of delta over the cell, in units of ln2/256
+                            De[k] = fma(kKappa * (4.0 / 3.0), qm3, s01);
                             // RK4 in x of m' = a - b m over the cell as the affine map
                             // m -> alpha m + beta (alpha: y' = -b y, y(0) = 1; beta: y' = a - b y,
-                            // y(0) = 0), with the stage values eliminated algebraically:
-                            //   alpha = 1 - q0 - q1 - 3qm [ (2/3) y2 + y3 (2/3 - 2 q1) ],
-                            //   y2 = 1 - 3 q0, y3 = 1 - 3 qm y2;
-                            //   beta = r0 + r1 + 2 w2 + w3 (2 - 6 q1),
-                            //   w2 = tm - 3 qm r0, w3 = tm - 3 qm w2,
-                            // q = h b / 6, r = h a / 6 at the cell's left end, midpoint, right end.
-                            const double y2 = fma(-3.0, qn0, 1.0);
-                            const double y3 = fma(-qm3, y2, 1.0);
-                            const double ca = fma(-2.0, qn1, 2.0 / 3.0);
-                            const double al = fma(-qm3, fma(y3, ca, fma(-2.0, qn0, 2.0 / 3.0)), 1.0 - s01);
+                            // y(0) = 0).  With q = h b / 6 and r = h a / 6 at the cell's left end
+                            // (q0, r0), midpoint (qm, tm) and right end (q1, r1), the stages give
+                            //   alpha = 1 - q0 - q1 - 2 qm (Y2 + Y3) + 6 qm q1 Y3,
+                            //   Y2 = 1 - 3 q0, Y3 = 1 - 3 qm Y2;
+                            //   beta = r0 + r1 + 2 W2 + W3 (2 - 6 q1),
+                            //   W2 = tm - 3 qm r0, W3 = tm - 3 qm W2.
+                            // Eliminating Y2 and W3 (3 qm Y2 = 1 - Y3):
+                            //   alpha = (1/3 - q0 - q1) + y3 e,   beta = (r0 + r1) + ca tm + e W2,
+                            //   y3 = Y3 / 3 = 1/3 - 3 qm (1/3 - q0), ca = 2 - 6 q1, e = 2 - 3 qm ca.
+                            const double y2 = fma(-kInvKappa, qn0, 1.0 / 3.0);       // 1/3 - q0
+                            const double y3 = fma(-qm3, y2, 1.0 / 3.0);
+                            const double ca = fma(-6.0 * kInvKappa, qn1, 2.0);       // 2 - 6 q1
+                            const double e = fma(-qm3, ca, 2.0);
+                            const double al = fma(y3, e, fma(-kInvKappa, s01, 1.0 / 3.0));
                             const double w2 = fma(-qm3, rn0, tm);
-                            const double w3 = fma(-qm3, w2, tm);
-                            const double be = fma(w3, fma(-6.0, qn1, 2.0), fma(2.0, w2, rn0 + rn1));
+                            const double be = fma(e, w2, fma(ca, tm, rn0 + rn1));
                             sF[tb + soff<P>(k)] = al;
                             sU[tb + soff<P>(k)] = be;
                             if (k == 0) {
@@ -530,7 +570,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             const double al = sF[tb + soff<P>(k)], be = sU[tb + soff<P>(k)];
                             const double Ai = fma(-m, __ldg(g.K + i), 1.0);
                             kmin = min_ll(kmin, order_key(Ai));
-                            const double Fi = a_exp_neg(Ai, De[k], s_tab);
+                            const double Fi = a_exp_neg_scaled(Ai, De[k], s_tab);
                             const double gi = Fi * Sp[soff<P>(k)];
                             const double fi = Fi * Sq[soff<P>(k)];
                             const double ui = __ldg(g.T + i) * gi;
@@ -547,16 +587,17 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             if (k == P - 2) { fm2 = fi; um2 = ui; }
                             if (a.outA) {
                                 a.outA[d.off + i] = Ai;
-                                a.outDelta[d.off + i] = De[k];
+                                a.outDelta[d.off + i] = De[k] * kInvKappa;
                             }
                             if (k < P - 1) m = fma(al, m, be);
                             else if (last) s_mass = fma(al, m, be);
                         }
                         if (tfirst) {
-                            s_d0 = De[0];
+                            const double d0n = De[0] * kInvKappa;   // delta(0)
+                            s_d0 = d0n;
                             // Pi-dot at x = 0 needs (F Phi)'(0) = (16 g_1 - 2 g_2) / (12 h)
                             sF[spos<P>(-3)] = fma(16.0, g1, -2.0 * g2);
-                            if constexpr (CL > 1) st_others<CL>(&s_d0, De[0], 0);
+                            if constexpr (CL > 1) st_others<CL>(&s_d0, d0n, 0);
                         }
                         if (last) {
                             // f odd and u even about x = pi/2; u(pi/2) by even extrapolation
@@ -639,8 +680,8 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
 
                     // ================= right-hand side and RK4 update =================
                     if (act) {
-                        const double wacc = (s == 0 || s == 3) ? d.dt6 : d.dt3;
-                        const double wst = (s == 2) ? dt : d.dt2;
+                        const double wacc = (s == 0 || s == 3) ? d.dt6q : d.dt3q;
+                        const double wst = (s == 2) ? d.dtq : d.dt2q;
                         const double waccc = (s == 0 || s == 3) ? d.dt6c : d.dt3c;
                         const double wstc = (s == 2) ? d.dtc : d.dt2c;
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
@@ -661,12 +702,14 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                                 fma(15.0, Sq[soff<P>(k - 1)] + Sq[soff<P>(k + 1)],
                                 fma(-6.0, Sq[soff<P>(k - 2)] + Sq[soff<P>(k + 2)],
                                     Sq[soff<P>(k - 3)] + Sq[soff<P>(k + 3)])));
-                            // Phi-dot = c12 (Df + rko kp): the factor c12 is folded into the RK weights
+                            // Phi-dot = c12 (Df + rko kp) and Pi-dot = cq (iT12k Du + kq): the factors
+                            // c12 and cq are folded into the RK weights
                             double Xp = fma(d.rko, kp, Df);
-                            double dQ = fma(__ldg(g.iT12 + i), Du, d.cko * kq);
+                            const double kqs = d.ko ? kq : 0.0;
+                            double dQ = fma(__ldg(g.iT12k + i), Du, kqs);
                             if (k == 0 && tfirst) {
-                                Xp = 0.0;                                      // Phi(0) = 0
-                                dQ = fma(d.c3, sF[spos<P>(-3)], d.cko * kq);  // 3 (F Phi)'(0)
+                                Xp = 0.0;                                   // Phi(0) = 0
+                                dQ = fma(d.c3q, sF[spos<P>(-3)], kqs);     // 3 (F Phi)'(0) / cq
                             }
                             const double up = __ldcg(uPhi + i), uq = __ldcg(uPi + i);
                             double ap_, aq_;

@@ -249,31 +249,31 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                         double pm1 = Sp[soff<P>(-1)], p0 = Sp[soff<P>(0)], p1 = Sp[soff<P>(1)];
                         double qm1 = Sq[soff<P>(-1)], q0 = Sq[soff<P>(0)], q1 = Sq[soff<P>(1)];
                         const double rho0 = fma(p0, p0, q0 * q0);
-                        double qn0 = __ldg(g.ws + i0) * rho0, rn0 = __ldg(g.wt + i0) * rho0;
+                        double qn0 = __ldg(g.wsk + i0) * rho0, rn0 = __ldg(g.wt + i0) * rho0;
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int c = i0 + k;
                             const double p2 = Sp[soff<P>(k + 2)], q2 = Sq[soff<P>(k + 2)];
                             const double rho1 = fma(p1, p1, q1 * q1);
-                            const double qn1 = __ldg(g.ws + c + 1) * rho1;
+                            const double qn1 = __ldg(g.wsk + c + 1) * rho1;   // kappa q1
                             const double p16 = fma(9.0, p0 + p1, -(pm1 + p2));
                             const double q16 = fma(9.0, q0 + q1, -(qm1 + q2));
                             const double rm = fma(p16, p16, q16 * q16);
                             const double qm3 = __ldg(g.wsm3 + c) * rm;
                             const double s01 = qn0 + qn1;
-                            De[k] = fma(4.0 / 3.0, qm3, s01);
+                            De[k] = fma(kKappa * (4.0 / 3.0), qm3, s01);   // units of ln2/256
                             SD = (k == 0) ? De[0] : SD + De[k];
                             if (reint) {
                                 // the affine map of the mass function over the cell (evolve_kernel)
                                 const double rn1 = __ldg(g.wt + c + 1) * rho1;
                                 const double tm = __ldg(g.wtm + c) * rm;
-                                const double y2 = fma(-3.0, qn0, 1.0);
-                                const double y3 = fma(-qm3, y2, 1.0);
-                                const double ca = fma(-2.0, qn1, 2.0 / 3.0);
-                                const double al = fma(-qm3, fma(y3, ca, fma(-2.0, qn0, 2.0 / 3.0)), 1.0 - s01);
+                                const double y2 = fma(-kInvKappa, qn0, 1.0 / 3.0);
+                                const double y3 = fma(-qm3, y2, 1.0 / 3.0);
+                                const double ca = fma(-6.0 * kInvKappa, qn1, 2.0);
+                                const double e = fma(-qm3, ca, 2.0);
+                                const double al = fma(y3, e, fma(-kInvKappa, s01, 1.0 / 3.0));
                                 const double w2 = fma(-qm3, rn0, tm);
-                                const double w3 = fma(-qm3, w2, tm);
-                                const double be = fma(w3, fma(-6.0, qn1, 2.0), fma(2.0, w2, rn0 + rn1));
+                                const double be = fma(e, w2, fma(ca, tm, rn0 + rn1));
                                 sF[tb + soff<P>(k)] = al;
                                 sU[tb + soff<P>(k)] = be;
                                 if (k == 0) {
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             } else {
                                 Ai = (s == 0) ? __ldcg(uA + i) : __ldcg(sA + i);
                             }
-                            const double Fi = FIXED ? 1.0 : a_exp_neg(Ai, De[k], s_tab);
+                            const double Fi = FIXED ? 1.0 : a_exp_neg_scaled(Ai, De[k], s_tab);
                             const double gi = FIXED ? ph : Fi * ph;
                             const double fi = FIXED ? pi : Fi * pi;
                             const double ui = __ldg(g.T + i) * gi;
@@ -428,13 +428,14 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             if (k == P - 2) { fm2 = fi; um2 = ui; }
                             if (a.outA) {
                                 a.outA[d.off + i] = Ai;
-                                a.outDelta[d.off + i] = De[k];
+                                a.outDelta[d.off + i] = De[k] * kInvKappa;
                             }
                         }
                         if (tfirst) {
-                            s_d0 = De[0];
+                            const double d0n = De[0] * kInvKappa;   // delta(0)
+                            s_d0 = d0n;
                             sF[spos<P>(-3)] = fma(16.0, g1, -2.0 * g2);
-                            if constexpr (CL > 1) st_others<CL>(&s_d0, De[0], 0);
+                            if constexpr (CL > 1) st_others<CL>(&s_d0, d0n, 0);
                         }
                         if (last) {
                             sF[spos<P>(Nl - 1)] = 0.0;
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
 
                     // ================= Phi-dot, Pi-dot and the Shu-Osher update =================
                     if (act) {
-                        const double wbdc = wb * d.dtc, wbd = wb * dt;
+                        const double wbdc = wb * d.dtc, wbd = wb * d.dtq;
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
                         const double *f = sF + tb, *u = sU + tb;
                         double *Dp = D0 + tb, *Dq = D1 + tb;
@@ -545,15 +546,16 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                 fma(-6.0, Sq[soff<P>(k - 2)] + Sq[soff<P>(k + 2)],
                                     Sq[soff<P>(k - 3)] + Sq[soff<P>(k + 3)])));
                             double Xp = fma(d.rko, kp, Df);   // Phi-dot / c12
-                            double dQ = fma(__ldg(g.iT12 + i), Du, d.cko * kq);
+                            const double kqs = d.ko ? kq : 0.0;
+                            double dQ = fma(__ldg(g.iT12k + i), Du, kqs);   // Pi-dot / cq
                             if (k == 0 && tfirst) {
                                 Xp = 0.0;
-                                dQ = fma(d.c3, sF[spos<P>(-3)], d.cko * kq);
+                                dQ = fma(d.c3q, sF[spos<P>(-3)], kqs);
                             }
                             double np, nq;
                             if (s == 0) {
                                 np = fma(d.dtc, Xp, Sp[soff<P>(k)]);
-                                nq = fma(dt, dQ, Sq[soff<P>(k)]);
+                                nq = fma(d.dtq, dQ, Sq[soff<P>(k)]);
                             } else {
                                 np = fma(wbdc, Xp, fma(wb, Sp[soff<P>(k)], wa * __ldcg(uPhi + i)));
                                 nq = fma(wbd, dQ, fma(wb, Sq[soff<P>(k)], wa * __ldcg(uPi + i)));

@@ -1,4 +1,6 @@
 // expneg.cuh -- e^{-x} for the lapse factor F = A e^{-delta} of Eqs. (eq:phi), (eq:pi).
+// Two entry points: a_exp_neg(A, x) for x in natural units, a_exp_neg_scaled(A, X) for
+// X = x * 256/ln2.
 //
 // Method: Tang's table-driven exponential (P. T. P. Tang, "Table-driven implementation of the
 // exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989), written from
@@ -44,6 +46,38 @@ __device__ __forceinline__ double a_exp_neg(double A, double x, const double *ta
     p = r * p;                         // e^r - 1
     const int j = n & (kExpTableSize - 1);
     const int m = n >> 8;              // floor(n / 256)
+    const long long tb = __double_as_longlong(tab[j]) + ((long long)m << 52);
+    double t = __longlong_as_double(tb);
+    if (n < kExpNMin) t = 0.0;
+    const double at = A * t;
+    return fma(at, p, at);
+}
+
+// A e^{-x} from its argument given in units of ln2/256, X = x * 256/ln2 (the solver accumulates
+// delta in these units, so the reduction needs no split of ln2/256): with n = round(-X), the
+// remainder z = -X - n is exact (|z| <= 1/2, Sterbenz), and
+//   e^{-x} = 2^{n/256} e^{z L},  e^{z L} - 1 = z (c1 + z (c2 + z (c3 + z c4))),  ck = L^k / k!,
+// L = ln2/256; the degree-4 remainder is below 4e-17 for |z L| <= L/2.  Nine FP64 instructions.
+// Accuracy: within 2 ulp of e^{-X L} for X in [0, 258531] (x up to 700); 0 for X in
+// (258531, 2^51); NaN for NaN.
+constexpr double kKappa = kInvLn2x256;     // 256 / ln 2
+constexpr double kInvKappa = kLn2o256Hi;   // RN(ln 2 / 256)
+constexpr double kExpC2 = 3.6655655969101062e-06;   // RN(L^2 / 2)
+constexpr double kExpC3 = 3.3083026805413713e-09;   // RN(L^3 / 6)
+constexpr double kExpC4 = 2.239395190875157e-12;    // RN(L^4 / 24)
+
+__device__ __forceinline__ double a_exp_neg_scaled(double A, double X, const double *tab)
+{
+    const double nf = kShift - X;      // kShift + round(-X): the integer n in the low bits
+    const int n = __double2loint(nf);
+    const double nd = nf - kShift;     // n, exactly
+    const double z = -X - nd;          // exact
+    double p = fma(z, kExpC4, kExpC3);
+    p = fma(z, p, kExpC2);
+    p = fma(z, p, kInvKappa);
+    p = z * p;                         // e^{z L} - 1
+    const int j = n & (kExpTableSize - 1);
+    const int m = n >> 8;
     const long long tb = __double_as_longlong(tab[j]) + ((long long)m << 52);
     double t = __longlong_as_double(tb);
     if (n < kExpNMin) t = 0.0;

@@ -37,8 +37,8 @@ constexpr int kNaMaxPts = ADSCL_NOALLOC_MAX_POINTS;       // sum of N over the b
 
 // layout of the scratch array, in doubles
 constexpr size_t kOffExp = 0;                                    // 256: 2^{j/256}
-constexpr size_t kOffGeo = 256;                                  // 7 * N geometry factors
-constexpr size_t kGeoLen = ((size_t)7 * kNaMaxN + 31) / 32 * 32;
+constexpr size_t kOffGeo = 256;                                  // 9 * N geometry factors
+constexpr size_t kGeoLen = ((size_t)9 * kNaMaxN + 31) / 32 * 32;
 constexpr size_t kPtsLen = ((size_t)kNaMaxPts + 31) / 32 * 32;
 constexpr size_t kOffAccP = kOffGeo + kGeoLen;                   // RK4 accumulator of Phi
 constexpr size_t kOffAccQ = kOffAccP + kPtsLen;                  // RK4 accumulator of Pi
@@ -68,12 +68,12 @@ DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
 
 // Geometry factors of the grid x_i = i pi / (2 (N - 1)), same layout and definitions as the
-// tables of adscl_create (ws, wt, K, T, iT12, wsm3, wtm), computed here on the device.
-__global__ void noalloc_geometry_kernel(double *t, int N)
+// tables of adscl_create (ws, wt, K, T, iT12, wsm3, wtm, wsk, iT12k), computed here on the device.
+__global__ void noalloc_geometry_kernel(double *t, int N, double sigma)
 {
     const double h = 0.5 * 3.141592653589793 / (double)(N - 1);
     double *ws = t, *wt = ws + N, *K = wt + N, *T = K + N, *iT12 = T + N, *wsm3 = iT12 + N,
-           *wtm = wsm3 + N;
+           *wtm = wsm3 + N, *wsk = wtm + N, *iT12k = wsk + N;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const double x = i * h, s = sin(x), c = cos(x);
         ws[i] = h * s * c / 6.0;
@@ -86,6 +86,8 @@ __global__ void noalloc_geometry_kernel(double *t, int N)
         wt[i] = h * Ti / 6.0;
         K[i] = (i > 0 && i < N - 1) ? c * c * c / s : 0.0;
         iT12[i] = (i > 0 && i < N - 1) ? 1.0 / (12.0 * h * Ti) : 0.0;
+        iT12k[i] = (i > 0 && i < N - 1) ? it12k_of(h, Ti, sigma) : 0.0;
+        wsk[i] = kKappa * ws[i];
         if (i < N - 1) {
             const double xm = (i + 0.5) * h, sm = sin(xm), cm = cos(xm), tm = tan(xm);
             wsm3[i] = h * sm * cm / (2.0 * 256.0);
@@ -173,18 +175,7 @@ extern "C" adscl_status adscl_evolve_noalloc(int32_t device, void *stream_, int3
         d.N = N;
         d.geo = 0;
         d.off = (int64_t)b * N;
-        d.dt = dt;
-        d.dt2 = 0.5 * dt;
-        d.dt3 = dt / 3.0;
-        d.dt6 = dt / 6.0;
-        d.c12 = 1.0 / (12.0 * h);
-        d.c3 = 3.0 / (12.0 * h);
-        d.cko = ko_sigma / (64.0 * h);
-        d.rko = 3.0 * ko_sigma / 16.0;
-        d.dt6c = d.dt6 * d.c12;
-        d.dt3c = d.dt3 * d.c12;
-        d.dt2c = d.dt2 * d.c12;
-        d.dtc = d.dt * d.c12;
+        set_desc_coeffs(d, h, dt, ko_sigma);
         order[b] = b;
     }
     GeoTab g;
@@ -195,6 +186,8 @@ extern "C" adscl_status adscl_evolve_noalloc(int32_t device, void *stream_, int3
     g.iT12 = geo + 4 * (size_t)N;
     g.wsm3 = geo + 5 * (size_t)N;
     g.wtm = geo + 6 * (size_t)N;
+    g.wsk = geo + 7 * (size_t)N;
+    g.iT12k = geo + 8 * (size_t)N;
 
 #define NA_CK(call) do { if ((call) != cudaSuccess) return ADSCL_ECUDA; } while (0)
     NA_CK(cudaMemcpyAsync(d_desc, desc, sizeof(InstDesc) * B, cudaMemcpyHostToDevice, stream));
@@ -204,7 +197,7 @@ extern "C" adscl_status adscl_evolve_noalloc(int32_t device, void *stream_, int3
     NA_CK(cudaMemsetAsync(d_st, 0, sizeof(InstState) * B, stream));
     noalloc_exptab_kernel<<<1, kExpTableSize, 0, stream>>>(base + kOffExp);
     NA_CK(cudaGetLastError());
-    noalloc_geometry_kernel<<<(N + 255) / 256, 256, 0, stream>>>(geo, N);
+    noalloc_geometry_kernel<<<(N + 255) / 256, 256, 0, stream>>>(geo, N, ko_sigma);
     NA_CK(cudaGetLastError());
 
     EvolveArgs a{};

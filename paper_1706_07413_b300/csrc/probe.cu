@@ -68,6 +68,7 @@ extern "C" adscl_status adscl_probe_fp64(int32_t device, void *stream_, double *
 
 namespace {
 
+template <bool SCALED>
 __global__ void exp_neg_kernel(const double *x, double *y, long long n, const double *tab_g)
 {
     __shared__ double tab[adscl::kExpTableSize];
@@ -75,12 +76,11 @@ __global__ void exp_neg_kernel(const double *x, double *y, long long n, const do
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        y[i] = adscl::a_exp_neg(1.0, x[i], tab);
+        y[i] = SCALED ? adscl::a_exp_neg_scaled(1.0, x[i], tab) : adscl::a_exp_neg(1.0, x[i], tab);
 }
 
-}  // namespace
-
-extern "C" adscl_status adscl_exp_neg(int32_t device, const double *x, double *y, int64_t n)
+template <bool SCALED>
+adscl_status exp_neg_host(int32_t device, const double *x, double *y, int64_t n)
 {
     if (!x || !y || n < 0) return ADSCL_EINVAL;
     if (n == 0) return ADSCL_OK;
@@ -97,7 +97,7 @@ extern "C" adscl_status adscl_exp_neg(int32_t device, const double *x, double *y
                cudaMemcpy(dt, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
         st = ADSCL_ECUDA;
     } else {
-        exp_neg_kernel<<<256, 256>>>(dx, dy, n, dt);
+        exp_neg_kernel<SCALED><<<256, 256>>>(dx, dy, n, dt);
         if (cudaGetLastError() != cudaSuccess || cudaMemcpy(y, dy, nb, cudaMemcpyDeviceToHost) != cudaSuccess)
             st = ADSCL_ECUDA;
     }
@@ -105,4 +105,16 @@ extern "C" adscl_status adscl_exp_neg(int32_t device, const double *x, double *y
     if (dy) cudaFree(dy);
     if (dt) cudaFree(dt);
     return st;
+}
+
+}  // namespace
+
+extern "C" adscl_status adscl_exp_neg(int32_t device, const double *x, double *y, int64_t n)
+{
+    return exp_neg_host<false>(device, x, y, n);
+}
+
+extern "C" adscl_status adscl_exp_neg_scaled(int32_t device, const double *X, double *y, int64_t n)
+{
+    return exp_neg_host<true>(device, X, y, n);
 }

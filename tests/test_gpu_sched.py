@@ -28,6 +28,26 @@ def test_exp_neg_within_two_ulp_of_libm(ad):
     assert np.isnan(ad.exp_neg(np.array([np.nan]))[0])
 
 
+def test_exp_neg_scaled_within_two_ulp(ad):
+    """The kernels' exp takes its argument in units of ln2/256; the reference e^{-X ln2/256} is
+    evaluated in 40-digit arithmetic (the product X ln2/256 would itself round in FP64)."""
+    from mpmath import mp, mpf, exp, log
+    rng = np.random.default_rng(1)
+    X = np.concatenate([rng.uniform(0, 400, 3000), rng.uniform(0, 25000, 3000),
+                        rng.uniform(0, 258000, 1000), rng.uniform(0, 1e-6, 200),
+                        np.arange(-3, 4) * 0.5 + 1000, [0.0, 0.5, 1.0, 1.5, 5e-324, 258531.0]])
+    y = ad.exp_neg_scaled(X)
+    with mp.workdps(40):
+        L = log(2) / 256
+        ref = np.array([float(exp(-mpf(float(v)) * L)) for v in X])
+    err = np.abs(y - ref) / np.spacing(ref)
+    assert err.max() <= 2.0, (err.max(), X[np.argmax(err)])
+    assert y[X == 0.0][0] == 1.0
+    big = ad.exp_neg_scaled(np.array([258700.0, 3.7e6]))
+    assert big[0] == 0.0 and big[1] == 0.0
+    assert np.isnan(ad.exp_neg_scaled(np.array([np.nan]))[0])
+
+
 def _batch(ad, Ns, seed, chunk, amp=3.0, t_end=0.08, **kw):
     fields = [W.smooth_random(n, seed=seed + i, amp=amp) for i, n in enumerate(Ns)]
     s = ad.Solver(Ns, ko_sigma=0.5, collapse_threshold=2.0 ** -7, chunk_steps=chunk, **kw)
