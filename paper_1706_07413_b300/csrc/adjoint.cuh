@@ -6,8 +6,8 @@
 //
 // Work unit: one instance and checkpoint segment, on CL = 1 CTA (512 threads, 8 nodes per
 // thread, the layout of evolve.cuh) or on a CL = 2 thread-block cluster whose two CTAs own the
-// two halves of the node blocks (for batches smaller than the SM count: each instance then
-// occupies two SMs).
+// two halves of the node blocks with 4 nodes per thread, so that all 2 x 512 threads carry nodes
+// at N = 4097 (for batches smaller than the SM count: each instance then occupies two SMs).
 //   Phase F: from the segment's first slice, recompute its steps with the same discrete map as
 //     evolve.cuh (affine-map scan for m, suffix sum for delta, table-driven exp) and store, for
 //     every stage of every step, the stage input (Phi, Pi) and the stage's m, e^{-delta}, F and
@@ -36,7 +36,7 @@
 
 namespace adscl {
 
-constexpr int kAP = 8;          // nodes per thread
+constexpr int kAP = 8;          // nodes per thread of a single-CTA instance (kAP / CL on a CL-CTA cluster)
 constexpr int kANT = 512;       // threads per CTA
 constexpr int kANW = kANT / 32;
 constexpr int kStageArrays = 6;  // stored per stage: yP, yQ, M, E, F, AL
@@ -91,7 +91,7 @@ struct ScanShared {
 };
 
 // node ownership of this thread for grid size N: rank r of a CL-CTA cluster owns node blocks
-// ceil(r T / CL) .. ceil((r+1) T / CL) - 1 of the T blocks of kAP nodes
+// ceil(r T / CL) .. ceil((r+1) T / CL) - 1 of the T blocks of kAP / CL nodes
 struct Own {
     int T, i0;
     bool act, last;
@@ -99,12 +99,13 @@ struct Own {
 template <int CL>
 __device__ __forceinline__ Own own_of(int N)
 {
+    constexpr int AP = kAP / CL;
     Own o;
-    o.T = (N - 1) / kAP;
+    o.T = (N - 1) / AP;
     const int rank = (CL > 1) ? cluster_rank() : 0;
     const int bs = (rank * o.T + CL - 1) / CL, be = ((rank + 1) * o.T + CL - 1) / CL;
     const int t = bs + (int)threadIdx.x;
-    o.i0 = t * kAP;
+    o.i0 = t * AP;
     o.act = t < be;
     o.last = t == o.T - 1;
     return o;
@@ -349,15 +350,16 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
                               const Scr &scr, double *kP, double *kQ, const InstDesc &d, const GeoTab &g,
                               const double *tab, ScanShared &sh, bool with_rhs)
 {
+    constexpr int AP = kAP / CL;
     const int N = d.N;
     const Own o = own_of<CL>(N);
     const bool act = o.act, last = o.last;
     const int i0 = o.i0;
-    double De[kAP], al[kAP], be[kAP];
+    double De[AP], al[AP], be[AP];
     double aT = 1.0, bT = 0.0, SD = 0.0;
     if (act) {
 #pragma unroll
-        for (int k = 0; k < kAP; ++k) {
+        for (int k = 0; k < AP; ++k) {
             const CellFwd cf = cell_fwd(yP, yQ, g, N, i0 + k);
             De[k] = cf.De;
             al[k] = cf.al;
@@ -373,10 +375,10 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
     if (act) {
         double dc = dend;
 #pragma unroll
-        for (int k = kAP - 1; k >= 0; --k) { dc += De[k]; De[k] = dc; }
+        for (int k = AP - 1; k >= 0; --k) { dc += De[k]; De[k] = dc; }
         double m = mstart;
 #pragma unroll
-        for (int k = 0; k < kAP; ++k) {
+        for (int k = 0; k < AP; ++k) {
             const int i = i0 + k;
             const double A = fma(-m, __ldg(g.K + i), 1.0);
             const double Ei = a_exp_neg(1.0, De[k], tab);
@@ -403,7 +405,7 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
     csync<CL>();
     if (!with_rhs || !act) return;
 #pragma unroll
-    for (int k = 0; k < kAP; ++k) {
+    for (int k = 0; k < AP; ++k) {
         const int i = i0 + k;
         const double Df = (gv(scr.f, N, i - 2, 1.0, -1.0) - gv(scr.f, N, i + 2, 1.0, -1.0)) +
                           8.0 * (gv(scr.f, N, i + 1, 1.0, -1.0) - gv(scr.f, N, i - 1, 1.0, -1.0));
@@ -434,6 +436,7 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
                                     const Scr &scr, double *ybP, double *ybQ, const InstDesc &d,
                                     const GeoTab &g, ScanShared &sh)
 {
+    constexpr int AP = kAP / CL;
     const int N = d.N;
     const Own o = own_of<CL>(N);
     const bool act = o.act;
@@ -442,29 +445,29 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
     double aT = 1.0, bT = 0.0, SP = 0.0;
     if (act) {
 #pragma unroll
-        for (int k = kAP - 1; k >= 0; --k) {
+        for (int k = AP - 1; k >= 0; --k) {
             const int c = i0 + k;
             const double a = AL[c];
             bT = fma(a, bT, scr.mb[c]);
             aT *= a;
         }
 #pragma unroll
-        for (int k = 0; k < kAP; ++k) SP += scr.dlb[i0 + k];
+        for (int k = 0; k < AP; ++k) SP += scr.dlb[i0 + k];
     }
     const double mu_end = scan_affine_suffix<CL>(aT, bT, sh);   // mu at node i0 + P
     const double dpre = scan_sum<false, CL>(SP, sh);             // sum of delta_bar over nodes < i0
     if (act) {
         double mu = mu_end;
-        double mun[kAP];   // mu at node c+1 for each own cell
+        double mun[AP];   // mu at node c+1 for each own cell
 #pragma unroll
-        for (int k = kAP - 1; k >= 0; --k) {
+        for (int k = AP - 1; k >= 0; --k) {
             mun[k] = mu;
             mu = fma(AL[i0 + k], mu, scr.mb[i0 + k]);
         }
         double Db = dpre;
-        double n0s[kAP];
+        double n0s[AP];
 #pragma unroll
-        for (int k = 0; k < kAP; ++k) {
+        for (int k = 0; k < AP; ++k) {
             const int c = i0 + k;
             Db += scr.dlb[c];                         // Delta_bar_c = sum_{i <= c} delta_bar_i
             const CellFwd cf = cell_fwd(yP, yQ, g, N, c);
@@ -477,12 +480,12 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
         }
         // keep the node parts in the scratch f/u slots (free in phase B)
 #pragma unroll
-        for (int k = 0; k < kAP; ++k) scr.fb[i0 + k] = n0s[k];
+        for (int k = 0; k < AP; ++k) scr.fb[i0 + k] = n0s[k];
     }
     csync<CL>();
     if (act) {
 #pragma unroll
-        for (int k = 0; k < kAP; ++k) {
+        for (int k = 0; k < AP; ++k) {
             const int j = i0 + k;
             const double rb = scr.fb[j] + (j >= 1 ? scr.r1[j - 1] : 0.0);
             // transpose of p16_c = 9 (w_c + w_{c+1}) - (w_{c-1} + w_{c+2}), cells 0 .. N-2
@@ -507,6 +510,7 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
                                const double *F, const double *AL, const Scr &scr, double *ybP, double *ybQ,
                                const InstDesc &d, const GeoTab &g, ScanShared &sh)
 {
+    constexpr int AP = kAP / CL;
     const int N = d.N;
     const Own o = own_of<CL>(N);
     const bool act = o.act, last = o.last;
@@ -515,7 +519,7 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
     if (act) {
         // iT12-weighted Pi-dot sensitivities for the u stencil (zero at rows 0 and N-1)
 #pragma unroll
-        for (int k = 0; k < kAP; ++k) scr.pb[i0 + k] = __ldg(g.iT12 + i0 + k) * vQ[i0 + k];
+        for (int k = 0; k < AP; ++k) scr.pb[i0 + k] = __ldg(g.iT12 + i0 + k) * vQ[i0 + k];
         if (last) scr.pb[N - 1] = 0.0;
     }
     csync<CL>();
@@ -530,7 +534,7 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
     if (act) {
         const double vQ0 = vQ[0];
 #pragma unroll
-        for (int k = 0; k < kAP; ++k) {
+        for (int k = 0; k < AP; ++k) {
             const int j = i0 + k;
             // transposed stencils on the extended range, ghosts folded back (parities:
             // f even/odd, u odd/even, Phi odd/even, Pi even/odd about 0 / pi/2)
@@ -572,6 +576,7 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
 template <int CL>
 __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
 {
+    constexpr int AP = kAP / CL;   // nodes per thread: a 2-CTA cluster keeps all 2 x 512 threads busy at N <= 4097
     static_assert(CL == 1 || CL == 2, "one CTA or a 2-CTA cluster per instance");
     __shared__ ScanShared sh;
     __shared__ double s_tab[kExpTableSize];
@@ -632,7 +637,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                    *F = slot(0, 0, 4), *AL = slot(0, 0, 5);
             if (act) {
 #pragma unroll
-                for (int k = 0; k < kAP; ++k) { yP[i0 + k] = sP[i0 + k]; yQ[i0 + k] = sQ[i0 + k]; }
+                for (int k = 0; k < AP; ++k) { yP[i0 + k] = sP[i0 + k]; yQ[i0 + k] = sQ[i0 + k]; }
                 if (own.last) { yP[N - 1] = 0.0; yQ[N - 1] = 0.0; }
             }
             csync<CL>();
@@ -663,7 +668,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
             csync<CL>();
             if (act) {
 #pragma unroll
-                for (int k = 0; k < kAP; ++k) {
+                for (int k = 0; k < AP; ++k) {
                     const int i = i0 + k;
                     double cP = 0.0, cQ = 0.0, Ab = 0.0, dlb = 0.0;
                     if (i >= 1 && i < N - 1) {
@@ -689,7 +694,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
             constraint_backward<CL>(yP, yQ, M, AL, scr, scr.ybP, scr.ybQ, d, g, sh);
             if (act) {
 #pragma unroll
-                for (int k = 0; k < kAP; ++k) {
+                for (int k = 0; k < AP; ++k) {
                     lamP[i0 + k] += scr.ybP[i0 + k];
                     lamQ[i0 + k] += scr.ybQ[i0 + k];
                 }
@@ -703,7 +708,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
         const double *ckP = a.ckP + d.off, *ckQ = a.ckQ + d.off;
         if (act) {
 #pragma unroll
-            for (int k = 0; k < kAP; ++k) { scr.uP[i0 + k] = ckP[i0 + k]; scr.uQ[i0 + k] = ckQ[i0 + k]; }
+            for (int k = 0; k < AP; ++k) { scr.uP[i0 + k] = ckP[i0 + k]; scr.uQ[i0 + k] = ckQ[i0 + k]; }
         }
         csync<CL>();
         for (int n = 0; n < a.nsteps; ++n) {
@@ -711,7 +716,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                 double *yP = slot(n, s, 0), *yQ = slot(n, s, 1);
                 if (s == 0 && act) {
 #pragma unroll
-                    for (int k = 0; k < kAP; ++k) { yP[i0 + k] = scr.uP[i0 + k]; yQ[i0 + k] = scr.uQ[i0 + k]; }
+                    for (int k = 0; k < AP; ++k) { yP[i0 + k] = scr.uP[i0 + k]; yQ[i0 + k] = scr.uQ[i0 + k]; }
                 }
                 if (act && own.last) { yP[N - 1] = 0.0; yQ[N - 1] = 0.0; }
                 csync<CL>();
@@ -720,7 +725,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                               d, g, s_tab, sh, true);
                 if (act) {
 #pragma unroll
-                    for (int k = 0; k < kAP; ++k) {
+                    for (int k = 0; k < AP; ++k) {
                         const int i = i0 + k;
                         const double up = scr.uP[i], uq = scr.uQ[i];
                         const double ap = (s == 0) ? fma(wst[0] * d.dt, kP[i], up) : fma(wst[s] * d.dt, kP[i], scr.aP[i]);
@@ -737,14 +742,14 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
             }
             if (act) {
 #pragma unroll
-                for (int k = 0; k < kAP; ++k) { scr.uP[i0 + k] = scr.aP[i0 + k]; scr.uQ[i0 + k] = scr.aQ[i0 + k]; }
+                for (int k = 0; k < AP; ++k) { scr.uP[i0 + k] = scr.aP[i0 + k]; scr.uQ[i0 + k] = scr.aQ[i0 + k]; }
             }
             csync<CL>();
         }
         if (a.outP && act) {   // the segment's last slice (the next segment's start)
             double *oP = a.outP + d.off, *oQ = a.outQ + d.off;
 #pragma unroll
-            for (int k = 0; k < kAP; ++k) { oP[i0 + k] = scr.uP[i0 + k]; oQ[i0 + k] = scr.uQ[i0 + k]; }
+            for (int k = 0; k < AP; ++k) { oP[i0 + k] = scr.uP[i0 + k]; oQ[i0 + k] = scr.uQ[i0 + k]; }
             if (own.last) { oP[N - 1] = 0.0; oQ[N - 1] = 0.0; }
         }
 
@@ -755,7 +760,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
         for (int n = a.nsteps - 1; n >= 0; --n) {
             if (act) {
 #pragma unroll
-                for (int k = 0; k < kAP; ++k) {
+                for (int k = 0; k < AP; ++k) {
                     scr.lo[i0 + k] = lamP[i0 + k];
                     scr.lq[i0 + k] = lamQ[i0 + k];
                 }
@@ -763,7 +768,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
             for (int s = 3; s >= 0; --s) {
                 if (act) {
 #pragma unroll
-                    for (int k = 0; k < kAP; ++k) {
+                    for (int k = 0; k < AP; ++k) {
                         const int i = i0 + k;
                         double kb = wst[s] * d.dt * scr.lo[i], kq = wst[s] * d.dt * scr.lq[i];
                         if (s < 3) {
@@ -780,7 +785,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                                slot(n, s, 5), scr, scr.ybP, scr.ybQ, d, g, sh);
                 if (act) {
 #pragma unroll
-                    for (int k = 0; k < kAP; ++k) {
+                    for (int k = 0; k < AP; ++k) {
                         lamP[i0 + k] += scr.ybP[i0 + k];
                         lamQ[i0 + k] += scr.ybQ[i0 + k];
                     }
