@@ -153,14 +153,16 @@ adscl_status fail(adscl_ctx *c, adscl_status s, const char *fmt, ...)
     } while (0)
 
 // Geometry factors of one grid size (host libm, FP64); layout: ws, wt, K, T, iT12 (N each),
-// wsm3, wtm (N-1 each), wsk, iT12k (N each; iT12k depends on the dissipation sigma).
+// wsm3, wtm (N-1 each), wsk, iT12k (N each; iT12k depends on the dissipation sigma), each table
+// geo_stride(N) doubles after the previous one.
 constexpr int kGeoTables = 9;
 std::vector<double> make_geometry(int N, double sigma)
 {
     const double h = 0.5 * M_PI / (double)(N - 1);
-    std::vector<double> t((size_t)kGeoTables * N, 0.0);
-    double *ws = t.data(), *wt = ws + N, *K = wt + N, *T = K + N, *iT12 = T + N, *wsm3 = iT12 + N,
-           *wtm = wsm3 + N, *wsk = wtm + N, *iT12k = wsk + N;
+    const int S = geo_stride(N);
+    std::vector<double> t((size_t)kGeoTables * S, 0.0);
+    double *ws = t.data(), *wt = ws + S, *K = wt + S, *T = K + S, *iT12 = T + S, *wsm3 = iT12 + S,
+           *wtm = wsm3 + S, *wsk = wtm + S, *iT12k = wsk + S;
     for (int i = 0; i < N; ++i) {
         const double x = i * h, s = std::sin(x), c = std::cos(x);
         ws[i] = h * s * c / 6.0;
@@ -800,7 +802,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
             geoN.push_back(n);
         }
     size_t geo_doubles = 0;
-    for (int n : geoN) geo_doubles += (size_t)kGeoTables * n;
+    for (int n : geoN) geo_doubles += (size_t)kGeoTables * geo_stride(n);
     CK(cudaMalloc(&ctx->d_geo_block, geo_doubles * sizeof(double)));
     std::vector<GeoTab> h_geo;
     {
@@ -810,16 +812,17 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
             CK(cudaMemcpy(ctx->d_geo_block + pos, t.data(), t.size() * sizeof(double),
                           cudaMemcpyHostToDevice));
             const double *base = ctx->d_geo_block + pos;
+            const size_t S = (size_t)geo_stride(n);
             GeoTab g;
             g.ws = base;
-            g.wt = base + n;
-            g.K = base + 2 * (size_t)n;
-            g.T = base + 3 * (size_t)n;
-            g.iT12 = base + 4 * (size_t)n;
-            g.wsm3 = base + 5 * (size_t)n;
-            g.wtm = base + 6 * (size_t)n;
-            g.wsk = base + 7 * (size_t)n;
-            g.iT12k = base + 8 * (size_t)n;
+            g.wt = base + S;
+            g.K = base + 2 * S;
+            g.T = base + 3 * S;
+            g.iT12 = base + 4 * S;
+            g.wsm3 = base + 5 * S;
+            g.wtm = base + 6 * S;
+            g.wsk = base + 7 * S;
+            g.iT12k = base + 8 * S;
             h_geo.push_back(g);
             pos += t.size();
         }
@@ -830,20 +833,21 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
         // node factors of the evolved-A schemes: K2 = -2 sin x cos x (A-dot of Eq. (eq:adot)) and
         // the composite-Simpson mass weights (h/3) w_i tan^2 x_i (0 at both ends)
         size_t tot = 0;
-        for (int n : geoN) tot += (size_t)2 * n;
+        for (int n : geoN) tot += (size_t)2 * geo_stride(n);
         CK(cudaMalloc(&ctx->d_ea_block, tot * sizeof(double)));
         std::vector<EaGeo> h_eg;
         size_t pos2 = 0;
         for (int n : geoN) {
             const double h = 0.5 * M_PI / (double)(n - 1);
-            std::vector<double> t((size_t)2 * n, 0.0);
+            const int S = geo_stride(n);
+            std::vector<double> t((size_t)2 * S, 0.0);
             for (int i = 1; i < n - 1; ++i) {
                 const double x = i * h, tn = std::tan(x);
                 t[i] = -2.0 * std::sin(x) * std::cos(x);
-                t[n + i] = h / 3.0 * ((i % 2) ? 4.0 : 2.0) * tn * tn;
+                t[S + i] = h / 3.0 * ((i % 2) ? 4.0 : 2.0) * tn * tn;
             }
             CK(cudaMemcpy(ctx->d_ea_block + pos2, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
-            h_eg.push_back(EaGeo{ctx->d_ea_block + pos2, ctx->d_ea_block + pos2 + n});
+            h_eg.push_back(EaGeo{ctx->d_ea_block + pos2, ctx->d_ea_block + pos2 + S});
             pos2 += t.size();
         }
         CK(cudaMalloc(&ctx->d_eageo, h_eg.size() * sizeof(EaGeo)));

@@ -39,7 +39,9 @@
 
 namespace adscl {
 
-// per distinct grid size: geometry factors at nodes (length N) and cell midpoints (N-1)
+// per distinct grid size: geometry factors at nodes (length N) and cell midpoints (N-1); every
+// table starts on a 16-byte boundary (tables are geo_stride(N) doubles apart), so that a thread's
+// run of P factors is read with P/2 vector loads
 struct GeoTab {
     const double *ws;    // h sin x cos x / 6
     const double *wt;    // h tan^2 x / 6            (0 at x = pi/2)
@@ -67,6 +69,21 @@ struct InstDesc {
     int32_t ko;   // sigma > 0: dissipation on
     int32_t pad;
 };
+
+// distance in doubles between consecutive tables of one grid size: N rounded up to even
+__host__ __device__ inline int geo_stride(int N) { return (N + 1) & ~1; }
+
+// P consecutive doubles from a 16-byte aligned address, by P/2 vector loads on the read-only path
+template <int P>
+__device__ __forceinline__ void ldg_run(const double *p, double *v)
+{
+#pragma unroll
+    for (int j = 0; j < P / 2; ++j) {
+        const double2 x = __ldg(reinterpret_cast<const double2 *>(p) + j);
+        v[2 * j] = x.x;
+        v[2 * j + 1] = x.y;
+    }
+}
 
 // the per-instance coefficients above, for grid spacing h, step dt and dissipation sigma
 __host__ inline void set_desc_coeffs(InstDesc &d, double h, double dt, double sigma)
@@ -428,21 +445,28 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
                         double pm1 = Sp[soff<P>(-1)], p0 = Sp[soff<P>(0)], p1 = Sp[soff<P>(1)];
                         double qm1 = Sq[soff<P>(-1)], q0 = Sq[soff<P>(0)], q1 = Sq[soff<P>(1)];
+                        // geometry of the thread's nodes i0 .. i0+P and cells i0 .. i0+P-1
+                        double gws[P + 1], gwt[P + 1], gwm[P], gtm[P];
+                        ldg_run<P>(g.wsk + i0, gws);
+                        ldg_run<P>(g.wt + i0, gwt);
+                        ldg_run<P>(g.wsm3 + i0, gwm);
+                        ldg_run<P>(g.wtm + i0, gtm);
+                        gws[P] = __ldg(g.wsk + i0 + P);
+                        gwt[P] = __ldg(g.wt + i0 + P);
                         const double rho0 = fma(p0, p0, q0 * q0);
-                        double qn0 = __ldg(g.wsk + i0) * rho0, rn0 = __ldg(g.wt + i0) * rho0;
+                        double qn0 = gws[0] * rho0, rn0 = gwt[0] * rho0;
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
-                            const int c = i0 + k;
                             const double p2 = Sp[soff<P>(k + 2)], q2 = Sq[soff<P>(k + 2)];
                             const double rho1 = fma(p1, p1, q1 * q1);
-                            const double qn1 = __ldg(g.wsk + c + 1) * rho1;   // kappa q1
-                            const double rn1 = __ldg(g.wt + c + 1) * rho1;
+                            const double qn1 = gws[k + 1] * rho1;   // kappa q1
+                            const double rn1 = gwt[k + 1] * rho1;
                             // 16 * (midpoint value) by the 4-point Lagrange formula
                             const double p16 = fma(9.0, p0 + p1, -(pm1 + p2));
                             const double q16 = fma(9.0, q0 + q1, -(qm1 + q2));
                             const double rm = fma(p16, p16, q16 * q16);  // 256 rho_{c+1/2}
-                            const double qm3 = __ldg(g.wsm3 + c) * rm;   // 3 (h s rho / 6) at the midpoint
-                            const double tm = __ldg(g.wtm + c) * rm;     // h tan^2 rho / 6 there
+                            const double qm3 = gwm[k] * rm;   // 3 (h s rho / 6) at the midpoint
+                            const double tm = gtm[k] * rm;    // h tan^2 rho / 6 there
                             const double s01 = qn0 + qn1;                     // kappa (q0 + q1)
                             // Simpson increment of delta over the cell, in units of ln2/256
                             De[k] = fma(kKappa * (4.0 / 3.0), qm3, s01);
@@ -564,16 +588,19 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                         }
                         double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0, fm1 = 0.0, fm2 = 0.0;
                         double f0 = 0.0, f1 = 0.0, u0 = 0.0, u1 = 0.0;
+                        double gK[P], gT[P];
+                        ldg_run<P>(g.K + i0, gK);
+                        ldg_run<P>(g.T + i0, gT);
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
                             const double al = sF[tb + soff<P>(k)], be = sU[tb + soff<P>(k)];
-                            const double Ai = fma(-m, __ldg(g.K + i), 1.0);
+                            const double Ai = fma(-m, gK[k], 1.0);
                             kmin = min_ll(kmin, order_key(Ai));
                             const double Fi = a_exp_neg_scaled(Ai, De[k], s_tab);
                             const double gi = Fi * Sp[soff<P>(k)];
                             const double fi = Fi * Sq[soff<P>(k)];
-                            const double ui = __ldg(g.T + i) * gi;
+                            const double ui = gT[k] * gi;
                             sF[tb + soff<P>(k)] = fi;
                             sU[tb + soff<P>(k)] = ui;
                             if (k == 0) { f0 = fi; u0 = ui; }
@@ -687,6 +714,8 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
                         const double *f = sF + tb, *u = sU + tb;
                         double *Dp = D0 + tb, *Dq = D1 + tb;
+                        double gI[P];
+                        ldg_run<P>(g.iT12k + i0, gI);
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
@@ -706,7 +735,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             // c12 and cq are folded into the RK weights
                             double Xp = fma(d.rko, kp, Df);
                             const double kqs = d.ko ? kq : 0.0;
-                            double dQ = fma(__ldg(g.iT12k + i), Du, kqs);
+                            double dQ = fma(gI[k], Du, kqs);
                             if (k == 0 && tfirst) {
                                 Xp = 0.0;                                   // Phi(0) = 0
                                 dQ = fma(d.c3q, sF[spos<P>(-3)], kqs);     // 3 (F Phi)'(0) / cq

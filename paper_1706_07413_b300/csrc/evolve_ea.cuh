@@ -34,7 +34,7 @@
 namespace adscl {
 
 // per distinct grid size: the extra node factors of this scheme
-struct EaGeo {
+struct EaGeo {            // two tables geo_stride(N) doubles apart (16-byte aligned)
     const double *K2;    // -2 sin x cos x                          (0 at both ends)
     const double *wsim;  // (h/3) w_i tan^2 x_i, w = Simpson weights (0 at both ends)
 };
@@ -248,18 +248,22 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
                         double pm1 = Sp[soff<P>(-1)], p0 = Sp[soff<P>(0)], p1 = Sp[soff<P>(1)];
                         double qm1 = Sq[soff<P>(-1)], q0 = Sq[soff<P>(0)], q1 = Sq[soff<P>(1)];
+                        double gws[P + 1], gwm[P];   // wsk at nodes i0 .. i0+P, wsm3 at cells i0 ..
+                        ldg_run<P>(g.wsk + i0, gws);
+                        ldg_run<P>(g.wsm3 + i0, gwm);
+                        gws[P] = __ldg(g.wsk + i0 + P);
                         const double rho0 = fma(p0, p0, q0 * q0);
-                        double qn0 = __ldg(g.wsk + i0) * rho0, rn0 = __ldg(g.wt + i0) * rho0;
+                        double qn0 = gws[0] * rho0, rn0 = __ldg(g.wt + i0) * rho0;
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int c = i0 + k;
                             const double p2 = Sp[soff<P>(k + 2)], q2 = Sq[soff<P>(k + 2)];
                             const double rho1 = fma(p1, p1, q1 * q1);
-                            const double qn1 = __ldg(g.wsk + c + 1) * rho1;   // kappa q1
+                            const double qn1 = gws[k + 1] * rho1;   // kappa q1
                             const double p16 = fma(9.0, p0 + p1, -(pm1 + p2));
                             const double q16 = fma(9.0, q0 + q1, -(qm1 + q2));
                             const double rm = fma(p16, p16, q16 * q16);
-                            const double qm3 = __ldg(g.wsm3 + c) * rm;
+                            const double qm3 = gwm[k] * rm;
                             const double s01 = qn0 + qn1;
                             De[k] = fma(kKappa * (4.0 / 3.0), qm3, s01);   // units of ln2/256
                             SD = (k == 0) ? De[0] : SD + De[k];
@@ -383,6 +387,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                         }
                         double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0, fm1 = 0.0, fm2 = 0.0;
                         double f0 = 0.0, f1 = 0.0, u0 = 0.0, u1 = 0.0;
+                        double gT[P], gK2[P];
+                        ldg_run<P>(g.T + i0, gT);
+                        if constexpr (!FIXED) ldg_run<P>(eg.K2 + i0, gK2);
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
@@ -401,10 +408,10 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             const double Fi = FIXED ? 1.0 : a_exp_neg_scaled(Ai, De[k], s_tab);
                             const double gi = FIXED ? ph : Fi * ph;
                             const double fi = FIXED ? pi : Fi * pi;
-                            const double ui = __ldg(g.T + i) * gi;
+                            const double ui = gT[k] * gi;
                             if constexpr (!FIXED) {
                                 // A-dot = -2 sin x cos x A (A e^{-delta} Phi) Pi, and the stage update
-                                const double dA = __ldg(eg.K2 + i) * Ai * gi * pi;
+                                const double dA = gK2[k] * Ai * gi * pi;
                                 const double An = (s == 0) ? fma(dt, dA, Ai)
                                                            : fma(wb, fma(dt, dA, Ai), wa * __ldcg(uA + i));
                                 if (s < R - 1) sA[i] = An;
@@ -530,6 +537,8 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
                         const double *f = sF + tb, *u = sU + tb;
                         double *Dp = D0 + tb, *Dq = D1 + tb;
+                        double gI[P];
+                        ldg_run<P>(g.iT12k + i0, gI);
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
@@ -547,7 +556,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                     Sq[soff<P>(k - 3)] + Sq[soff<P>(k + 3)])));
                             double Xp = fma(d.rko, kp, Df);   // Phi-dot / c12
                             const double kqs = d.ko ? kq : 0.0;
-                            double dQ = fma(__ldg(g.iT12k + i), Du, kqs);   // Pi-dot / cq
+                            double dQ = fma(gI[k], Du, kqs);   // Pi-dot / cq
                             if (k == 0 && tfirst) {
                                 Xp = 0.0;
                                 dQ = fma(d.c3q, sF[spos<P>(-3)], kqs);

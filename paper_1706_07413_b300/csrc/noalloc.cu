@@ -37,8 +37,8 @@ constexpr int kNaMaxPts = ADSCL_NOALLOC_MAX_POINTS;       // sum of N over the b
 
 // layout of the scratch array, in doubles
 constexpr size_t kOffExp = 0;                                    // 256: 2^{j/256}
-constexpr size_t kOffGeo = 256;                                  // 9 * N geometry factors
-constexpr size_t kGeoLen = ((size_t)9 * kNaMaxN + 31) / 32 * 32;
+constexpr size_t kOffGeo = 256;                                  // 9 geometry tables
+constexpr size_t kGeoLen = ((size_t)9 * ((kNaMaxN + 1) & ~1) + 31) / 32 * 32;
 constexpr size_t kPtsLen = ((size_t)kNaMaxPts + 31) / 32 * 32;
 constexpr size_t kOffAccP = kOffGeo + kGeoLen;                   // RK4 accumulator of Phi
 constexpr size_t kOffAccQ = kOffAccP + kPtsLen;                  // RK4 accumulator of Pi
@@ -72,8 +72,9 @@ std::mutex g_setup_mutex;
 __global__ void noalloc_geometry_kernel(double *t, int N, double sigma)
 {
     const double h = 0.5 * 3.141592653589793 / (double)(N - 1);
-    double *ws = t, *wt = ws + N, *K = wt + N, *T = K + N, *iT12 = T + N, *wsm3 = iT12 + N,
-           *wtm = wsm3 + N, *wsk = wtm + N, *iT12k = wsk + N;
+    const int S = geo_stride(N);
+    double *ws = t, *wt = ws + S, *K = wt + S, *T = K + S, *iT12 = T + S, *wsm3 = iT12 + S,
+           *wtm = wsm3 + S, *wsk = wtm + S, *iT12k = wsk + S;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const double x = i * h, s = sin(x), c = cos(x);
         ws[i] = h * s * c / 6.0;
@@ -178,16 +179,17 @@ extern "C" adscl_status adscl_evolve_noalloc(int32_t device, void *stream_, int3
         set_desc_coeffs(d, h, dt, ko_sigma);
         order[b] = b;
     }
+    const size_t S = (size_t)geo_stride(N);
     GeoTab g;
     g.ws = geo;
-    g.wt = geo + N;
-    g.K = geo + 2 * (size_t)N;
-    g.T = geo + 3 * (size_t)N;
-    g.iT12 = geo + 4 * (size_t)N;
-    g.wsm3 = geo + 5 * (size_t)N;
-    g.wtm = geo + 6 * (size_t)N;
-    g.wsk = geo + 7 * (size_t)N;
-    g.iT12k = geo + 8 * (size_t)N;
+    g.wt = geo + S;
+    g.K = geo + 2 * S;
+    g.T = geo + 3 * S;
+    g.iT12 = geo + 4 * S;
+    g.wsm3 = geo + 5 * S;
+    g.wtm = geo + 6 * S;
+    g.wsk = geo + 7 * S;
+    g.iT12k = geo + 8 * S;
 
 #define NA_CK(call) do { if ((call) != cudaSuccess) return ADSCL_ECUDA; } while (0)
     NA_CK(cudaMemcpyAsync(d_desc, desc, sizeof(InstDesc) * B, cudaMemcpyHostToDevice, stream));
