@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             const double tm = gtm[k] * rm;    // h tan^2 rho / 6 there
                             const double s01 = qn0 + qn1;                     // kappa (q0 + q1)
                             // Simpson increment of delta over the cell, in units of ln2/256
-                            De[k] = fma(kKappa * (4.0 / 3.0), qm3, s01);
+                            const double dek = fma(kKappa * (4.0 / 3.0), qm3, s01);
                             // RK4 in x of m' = a - b m over the cell as the affine map
                             // m -> alpha m + beta (alpha: y' = -b y, y(0) = 1; beta: y' = a - b y,
                             // y(0) = 0).  With q = h b / 6 and r = h a / 6 at the cell's left end
@@ -488,16 +488,22 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             const double al = fma(y3, e, fma(-kInvKappa, s01, 1.0 / 3.0));
                             const double w2 = fma(-qm3, rn0, tm);
                             const double be = fma(e, w2, fma(ca, tm, rn0 + rn1));
-                            sF[tb + soff<P>(k)] = al;
-                            sU[tb + soff<P>(k)] = be;
+                            // running compositions: (aT, bT) maps m at node i0 to m at node i0+k+1,
+                            // De[k] = sum of the increments of cells i0 .. i0+k-1 (k >= 1); both
+                            // let the flux phase form every node's m and delta independently
                             if (k == 0) {
                                 aT = al;
                                 bT = be;
-                                SD = De[0];
+                                SD = dek;
                             } else {
                                 bT = fma(al, bT, be);
                                 aT = aT * al;
-                                SD = SD + De[k];
+                                De[k] = SD;
+                                SD = SD + dek;
+                            }
+                            if (k < P - 1) {
+                                sF[tb + soff<P>(k + 1)] = aT;
+                                sU[tb + soff<P>(k + 1)] = bT;
                             }
                             pm1 = p0; p0 = p1; p1 = p2;
                             qm1 = q0; q0 = q1; q1 = q2;
@@ -518,9 +524,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                     }
                     double aEx = __shfl_up_sync(FULL, aT, 1);
                     double bEx = __shfl_up_sync(FULL, bT, 1);
-                    double dEx = __shfl_down_sync(FULL, SD, 1);
                     if (lane == 0) { aEx = 1.0; bEx = 0.0; }
-                    if (lane == 31) dEx = 0.0;
                     if (lane == 31) { wAl[wid] = aT; wBe[wid] = bT; }
                     if (lane == 0) wDe[wid] = SD;
                     __syncthreads();
@@ -566,7 +570,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                     long long kmin = 0x7FFFFFFFFFFFFFFFLL;
                     if (act) {
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
-                        double m, dc;
+                        // m at the warp's first node (cm) and at node i0 (m); delta at node i0 (dtop) from
+                        // the inclusive suffix sum SD of this and the warp's later lanes
+                        double m, cm, dtop;
                         if constexpr (CL > 1) {
                             // m at this rank's first node: the maps of ranks 0 .. rank-1 applied to m = 0
                             double mr = 0.0;
@@ -574,18 +580,18 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             // delta carried in from the ranks to the right
                             double dr = 0.0;
                             for (int j = CL - 1; j > rank; --j) dr = (j == CL - 1) ? s_cD[j] : dr + s_cD[j];
-                            const double cm = (rank > 0) ? fma(cMa[wid], mr, cM[wid]) : cM[wid];
-                            m = fma(aEx, cm, bEx);                                   // m at node i0
-                            dc = dEx + cD[wid] + ((rank < CL - 1) ? dr : 0.0);      // delta at node i0+P
+                            cm = (rank > 0) ? fma(cMa[wid], mr, cM[wid]) : cM[wid];
+                            m = fma(aEx, cm, bEx);
+                            dtop = SD + cD[wid] + ((rank < CL - 1) ? dr : 0.0);
                         } else {
-                            m = fma(aEx, cM[wid], bEx);
-                            dc = dEx + cD[wid];
+                            cm = cM[wid];
+                            m = fma(aEx, cm, bEx);
+                            dtop = SD + cD[wid];
                         }
+                        // delta at node i0+k: dtop minus the increments of the cells i0 .. i0+k-1
+                        De[0] = dtop;
 #pragma unroll
-                        for (int k = P - 1; k >= 0; --k) {   // delta at nodes i0 .. i0+P-1
-                            dc = dc + De[k];
-                            De[k] = dc;
-                        }
+                        for (int k = 1; k < P; ++k) De[k] = dtop - De[k];
                         double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0, fm1 = 0.0, fm2 = 0.0;
                         double f0 = 0.0, f1 = 0.0, u0 = 0.0, u1 = 0.0;
                         double gK[P], gT[P];
@@ -594,8 +600,8 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
-                            const double al = sF[tb + soff<P>(k)], be = sU[tb + soff<P>(k)];
-                            const double Ai = fma(-m, gK[k], 1.0);
+                            const double mk = (k == 0) ? m : fma(sF[tb + soff<P>(k)], m, sU[tb + soff<P>(k)]);
+                            const double Ai = fma(-mk, gK[k], 1.0);
                             kmin = min_ll(kmin, order_key(Ai));
                             const double Fi = a_exp_neg_scaled(Ai, De[k], s_tab);
                             const double gi = Fi * Sp[soff<P>(k)];
@@ -616,9 +622,8 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                                 a.outA[d.off + i] = Ai;
                                 a.outDelta[d.off + i] = De[k] * kInvKappa;
                             }
-                            if (k < P - 1) m = fma(al, m, be);
-                            else if (last) s_mass = fma(al, m, be);
                         }
+                        if (last) s_mass = fma(aT, cm, bT);   // m at node N-1: the inclusive prefix map
                         if (tfirst) {
                             const double d0n = De[0] * kInvKappa;   // delta(0)
                             s_d0 = d0n;

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                     // ================= delta (and, at a re-integration slice, m) =================
                     double De[P];
                     double aT = 1.0, bT = 0.0, SD = 0.0;
-                    double aEx = 1.0, bEx = 0.0, dEx = 0.0;
+                    double aEx = 1.0, bEx = 0.0;
                     if constexpr (!FIXED) {
                     if (act) {
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
@@ -265,8 +265,10 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             const double rm = fma(p16, p16, q16 * q16);
                             const double qm3 = gwm[k] * rm;
                             const double s01 = qn0 + qn1;
-                            De[k] = fma(kKappa * (4.0 / 3.0), qm3, s01);   // units of ln2/256
-                            SD = (k == 0) ? De[0] : SD + De[k];
+                            const double dek = fma(kKappa * (4.0 / 3.0), qm3, s01);   // units of ln2/256
+                            // De[k] (k >= 1): sum of the increments of cells i0 .. i0+k-1
+                            if (k > 0) De[k] = SD;
+                            SD = (k == 0) ? dek : SD + dek;
                             if (reint) {
                                 // the affine map of the mass function over the cell (evolve_kernel)
                                 const double rn1 = __ldg(g.wt + c + 1) * rho1;
@@ -312,9 +314,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                     }
                     aEx = __shfl_up_sync(FULL, aT, 1);
                     bEx = __shfl_up_sync(FULL, bT, 1);
-                    dEx = __shfl_down_sync(FULL, SD, 1);
                     if (lane == 0) { aEx = 1.0; bEx = 0.0; }
-                    if (lane == 31) dEx = 0.0;
                     if (lane == 31) { wAl[wid] = aT; wBe[wid] = bT; }
                     if (lane == 0) wDe[wid] = SD;
                     __syncthreads();
@@ -378,12 +378,12 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                 for (int j = CL - 1; j > rank; --j) dr = (j == CL - 1) ? s_cD[j] : dr + s_cD[j];
                             }
                             m = fma(aEx, cm, bEx);
-                            double dc = dEx + cD[wid] + dr;
+                            // delta at node i0 from the inclusive suffix sum SD, then at node i0+k
+                            // by subtracting the increments of the cells i0 .. i0+k-1
+                            const double dtop = SD + cD[wid] + dr;
+                            De[0] = dtop;
 #pragma unroll
-                            for (int k = P - 1; k >= 0; --k) {
-                                dc = dc + De[k];
-                                De[k] = dc;
-                            }
+                            for (int k = 1; k < P; ++k) De[k] = dtop - De[k];
                         }
                         double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0, fm1 = 0.0, fm2 = 0.0;
                         double f0 = 0.0, f1 = 0.0, u0 = 0.0, u1 = 0.0;
