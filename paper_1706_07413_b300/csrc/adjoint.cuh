@@ -40,7 +40,7 @@ constexpr int kAP = 8;          // nodes per thread of a single-CTA instance (kA
 constexpr int kANT = 512;       // threads per CTA
 constexpr int kANW = kANT / 32;
 constexpr int kStageArrays = 6;  // stored per stage: yP, yQ, M, E, F, AL
-constexpr int kScrArrays = 20;   // CTA scratch arrays of length Nmax
+constexpr int kScrArrays = 21;   // CTA scratch arrays of length Nmax
 
 // kAdjSegment: both phases of a segment; kAdjSegF / kAdjSegB: only the recomputation (phase F,
 // from the checkpoint into the stage storage) or only the backward sweep (phase B, from the
@@ -85,8 +85,11 @@ __device__ __forceinline__ double rv(const double *v, int N, int i) {
 }
 
 // ------------------------------------------------------------------ block scans (512 threads)
+// The affine scans and the sums use disjoint slots (a, b, c, e, pb and d, f, pd), so a sum may
+// follow an affine scan without a barrier between them; a scan's slots are written again only by
+// the next scan of its kind, which every call site separates from this one by barriers.
 struct ScanShared {
-    double a[kANW], b[kANW], c[kANW], d[kANW], e[kANW];
+    double a[kANW], b[kANW], c[kANW], d[kANW], e[kANW], f[kANW];
     double pa, pb, pd;   // total of the other rank of a 2-CTA cluster (written by it)
 };
 
@@ -146,7 +149,6 @@ __device__ double scan_affine_prefix(double a, double b, ScanShared &sh)
     if constexpr (CL == 2) {
         if (cluster_rank() == 1) r = fma(aEx * sh.e[wid], sh.pb, r);   // the maps of rank 0 first
     }
-    csync<CL>();
     return r;
 }
 
@@ -186,7 +188,6 @@ __device__ double scan_affine_suffix(double a, double b, ScanShared &sh)
     if constexpr (CL == 2) {
         if (cluster_rank() == 0) r = fma(aEx * sh.e[wid], sh.pb, r);   // the maps of rank 1 first
     }
-    csync<CL>();
     return r;
 }
 
@@ -225,18 +226,17 @@ __device__ double scan_sum(double x, ScanShared &sh)
         }
         double w = kSuffix ? __shfl_down_sync(FULL, X, 1) : __shfl_up_sync(FULL, X, 1);
         if (kSuffix ? lane + 1 >= kANW : lane == 0) w = 0.0;
-        if (lane < kANW) sh.c[lane] = w;
+        if (lane < kANW) sh.f[lane] = w;
         if constexpr (CL == 2) {   // the total of the rank that comes first to the other
             const int from = kSuffix ? 1 : 0;
             if (lane == (kSuffix ? 0 : kANW - 1) && cluster_rank() == from) st_peer(&sh.pd, X, 1 - from);
         }
     }
     csync<CL>();
-    double r = ex + sh.c[wid];
+    double r = ex + sh.f[wid];
     if constexpr (CL == 2) {
         if (cluster_rank() == (kSuffix ? 0 : 1)) r += sh.pd;
     }
-    csync<CL>();
     return r;
 }
 
@@ -327,6 +327,7 @@ struct Scr {
     double *ybP, *ybQ;   // ybar of the previous (later) stage
     double *mb;          // mbar, then mu
     double *dlb;         // delta_bar
+    double *v2;          // iT12 kbar_Pi (phase B: the Pi-dot sensitivities seen by the u stencil)
 };
 
 __device__ __forceinline__ Scr scratch_of(double *base, int Nmax)
@@ -337,7 +338,7 @@ __device__ __forceinline__ Scr scratch_of(double *base, int Nmax)
     s.f = p; p += Nmax; s.u = p; p += Nmax; s.vP = p; p += Nmax; s.vQ = p; p += Nmax;
     s.fb = p; p += Nmax; s.ub = p; p += Nmax; s.r1 = p; p += Nmax; s.pb = p; p += Nmax;
     s.qb = p; p += Nmax; s.lo = p; p += Nmax; s.lq = p; p += Nmax; s.ybP = p; p += Nmax;
-    s.ybQ = p; p += Nmax; s.mb = p; p += Nmax; s.dlb = p;
+    s.ybQ = p; p += Nmax; s.mb = p; p += Nmax; s.dlb = p; p += Nmax; s.v2 = p;
     return s;
 }
 
@@ -371,7 +372,7 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
     }
     const double mstart = scan_affine_prefix<CL>(aT, bT, sh);
     const double dend = scan_sum<true, CL>(SD, sh);
-    double g1 = 0.0, g2 = 0.0;
+    double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0;
     if (act) {
         double dc = dend;
 #pragma unroll
@@ -387,21 +388,23 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
             E[i] = Ei;
             F[i] = Fi;
             const double gi = Fi * yP[i];
+            const double ui = __ldg(g.T + i) * gi;
             scr.f[i] = Fi * yQ[i];
-            scr.u[i] = __ldg(g.T + i) * gi;
+            scr.u[i] = ui;
             if (k == 1) g1 = gi;
             if (k == 2) g2 = gi;
+            if (k == AP - 1) um1 = ui;
+            if (k == AP - 2) um2 = ui;
             m = fma(al[k], m, be[k]);
         }
-        if (last) {
+        if (last) {   // the last thread owns nodes N-3 and N-2 (AP >= 2)
             M[N - 1] = m;
             E[N - 1] = 1.0;
             F[N - 1] = 1.0;
             scr.f[N - 1] = 0.0;
+            scr.u[N - 1] = (4.0 * um1 - um2) * (1.0 / 3.0);   // u(pi/2) by even extrapolation
         }
     }
-    csync<CL>();
-    if (act && last) scr.u[N - 1] = (4.0 * scr.u[N - 2] - scr.u[N - 3]) * (1.0 / 3.0);
     csync<CL>();
     if (!with_rhs || !act) return;
 #pragma unroll
@@ -499,7 +502,8 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
             ybQ[j] += fma(2.0 * yQ[j], rb, pQ);
         }
     }
-    csync<CL>();
+    // no barrier here: every caller updates only its own nodes next and then synchronises
+    // before scr.pb, qb, r1, fb are written again
 }
 
 // ------------------------------------------------------------------ stage backward
@@ -516,14 +520,7 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
     const bool act = o.act, last = o.last;
     const int i0 = o.i0;
     const double *vP = scr.vP, *vQ = scr.vQ;
-    if (act) {
-        // iT12-weighted Pi-dot sensitivities for the u stencil (zero at rows 0 and N-1)
-#pragma unroll
-        for (int k = 0; k < AP; ++k) scr.pb[i0 + k] = __ldg(g.iT12 + i0 + k) * vQ[i0 + k];
-        if (last) scr.pb[N - 1] = 0.0;
-    }
-    csync<CL>();
-    const double *v2 = scr.pb;
+    const double *v2 = scr.v2;   // iT12-weighted Pi-dot sensitivities (zero at rows 0 and N-1)
     auto Dr = [&](const double *v, int x) {   // raw 4th-order difference of a row-restricted array
         return (rv(v, N, x - 2) - rv(v, N, x + 2)) + 8.0 * (rv(v, N, x + 1) - rv(v, N, x - 1));
     };
@@ -777,8 +774,9 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                         }
                         scr.vP[i] = (i == 0) ? 0.0 : kb;   // Phi-dot(0) is identically zero
                         scr.vQ[i] = kq;
+                        scr.v2[i] = __ldg(g.iT12 + i) * kq;
                     }
-                    if (own.last) { scr.vP[N - 1] = 0.0; scr.vQ[N - 1] = 0.0; }
+                    if (own.last) { scr.vP[N - 1] = 0.0; scr.vQ[N - 1] = 0.0; scr.v2[N - 1] = 0.0; }
                 }
                 csync<CL>();
                 stage_backward<CL>(slot(n, s, 0), slot(n, s, 1), slot(n, s, 2), slot(n, s, 3), slot(n, s, 4),
