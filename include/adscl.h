@@ -157,9 +157,11 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
  * ckpt_every; every stage of a segment is stored in device memory (B * ckpt_every * 24 * N
  * doubles per segment) and swept backwards through the exact transpose of the discrete step
  * (constraint scans included).  When every segment's stages fit (adjoint_stage_buffers), the
- * forward pass stores them all; otherwise it keeps (Phi, Pi) at the segment starts and each
- * segment is recomputed once before its sweep.  Replaces the context's state by the final
- * slice (step index n). */
+ * forward pass stores them all: through the evolution kernel itself (a variant that records
+ * every stage) when the context's kernel shapes give the batch at least one CTA per SM (see
+ * adscl_autotune), else through the adjoint kernel's recomputation; otherwise it keeps
+ * (Phi, Pi) at the segment starts and each segment is recomputed once before its sweep.
+ * Replaces the context's state by the final slice (step index n). */
 adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, double *J_out,
                         double *dJda, int ptr_is_device);
 

@@ -39,7 +39,7 @@ namespace adscl {
 constexpr int kAP = 8;          // nodes per thread of a single-CTA instance (kAP / CL on a CL-CTA cluster)
 constexpr int kANT = 512;       // threads per CTA
 constexpr int kANW = kANT / 32;
-constexpr int kStageArrays = 6;  // stored per stage: yP, yQ, M, E, F, AL
+// kStageArrays (evolve.cuh): stored per stage: yP, yQ, M, E, F, AL
 constexpr int kScrArrays = 21;   // CTA scratch arrays of length Nmax
 
 // kAdjSegment: both phases of a segment; kAdjSegF / kAdjSegB: only the recomputation (phase F,
@@ -60,7 +60,8 @@ struct AdjArgs {
     const double *ckP, *ckQ;  // packed slices at the segment start
     double *outP, *outQ;      // phase F: packed slices receiving the segment's last slice (or null)
     int32_t nsteps;           // steps of this segment
-    double *stage;            // per work item: nsteps_cap * 4 stages * kStageArrays * Nmax
+    double *stage;            // per instance: nsteps_cap * 4 stages * kStageArrays * Nmax (the
+                              // layout of the evolution kernel's stage record, stage_slot)
     int32_t nsteps_cap;
     double *lamP, *lamQ;      // packed adjoint state, updated in place
     double *scratch;          // per CTA: kScrArrays * Nmax
@@ -624,7 +625,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
 
         // per-stage storage of this work item
         const size_t stN = (size_t)a.Nmax;
-        double *stage_base = a.stage + (size_t)q * a.nsteps_cap * 4 * kStageArrays * stN;
+        double *stage_base = a.stage + (size_t)b * a.nsteps_cap * 4 * kStageArrays * stN;
         auto slot = [&](int n, int s, int arr) { return stage_base + (((size_t)n * 4 + s) * kStageArrays + arr) * stN; };
 
         if (a.mode == kAdjSpectrum) {

@@ -75,6 +75,10 @@ struct adscl_ctx {
     double t_prev = 0.0;               // t_end of the last evolve call since the initial data
     int scheme = 0, reint = 0;         // ADSCL_SCHEME_*, A re-integration interval (evolved A)
     int adj_cl = 1;                    // CTAs per instance of the adjoint kernel
+    // stage record of the evolution kernel (set by adscl_grad around its forward pass)
+    double *rec_stage = nullptr;
+    long long rec_seg_stride = 0, rec_steps = 0;
+    int rec_seg = 1;
     int adj_bufs_cap = 0;              // most segment stage buffers the adjoint may hold (0: any)
     int adj_units = 0;                 // co-resident adjoint units (CTAs or 2-CTA clusters)
     double *d_A = nullptr;             // packed evolved A (evolved-A schemes)
@@ -328,6 +332,13 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
     a.theta = ctx->theta;
     a.outA = outA;
     a.outDelta = outD;
+    if (mode == kModeEvolve && ctx->rec_stage) {
+        a.stage = ctx->rec_stage;
+        a.stage_seg_stride = ctx->rec_seg_stride;
+        a.stage_steps = ctx->rec_steps;
+        a.stage_seg = ctx->rec_seg;
+        a.stage_nmax = ctx->Nmax;
+    }
     // bound on the number of rounds: no instance needs more than ceil(n_end / chunk) chunks
     long long rounds = 1;
     if (mode == kModeEvolve) {
@@ -1091,16 +1102,16 @@ __global__ void drift_kernel(const double *E0, const double *ET, int B, int J, d
     Jout[b] = s;
 }
 
-// one adjoint launch on stream sm; lane 0 or 1 selects the work counter and the per-CTA scratch
-// (the two lanes may run at the same time)
-// the step index of every instance (the forward pass of adscl_grad through the stage-storing
-// recomputation leaves the context at step nsteps)
+// the step index of every instance (the forward pass of adscl_grad through the adjoint kernel's
+// stage-recording recomputation leaves the context at step nsteps)
 __global__ void set_step_kernel(InstState *st, int B, long long step)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < B) st[b].step = step;
 }
 
+// one adjoint launch on stream sm; lane 0 or 1 selects the work counter and the per-CTA scratch
+// (the two lanes may run at the same time)
 adscl_status launch_adjoint(adscl_ctx *ctx, AdjArgs &a, cudaStream_t sm, int lane)
 {
     const int regions = std::min(ctx->B, ctx->num_sms);   // scratch regions per lane
@@ -1252,6 +1263,12 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     };
     const bool store_all = ctx->adj_stage_bufs >= nseg &&
                            (ctx->adj_bufs_cap == 0 || ctx->adj_bufs_cap >= nseg);
+    // with every stage stored, the forward pass is the evolution kernel recording its stages when
+    // its shapes spread the batch over the whole GPU (at least one CTA per SM); otherwise the
+    // adjoint kernel's own recomputation (2-CTA clusters for small batches) records them
+    long long evo_ctas = 0;
+    for (int b = 0; b < B; ++b) evo_ctas += kShapes[ctx->shape_of[b]].CL;
+    const bool rec_evolve = store_all && evo_ctas >= ctx->num_sms;
     const bool piped = !store_all && ctx->adj_stage_bufs >= 2 && ctx->adj_bufs_cap != 1 && nseg > 1;
     if (piped && !ctx->adj_aux) {
         CK(cudaStreamCreateWithFlags(&ctx->adj_aux, cudaStreamNonBlocking));
@@ -1270,7 +1287,20 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     ctx->theta = -INFINITY;
     s = adscl_set_initial_modes(ctx, a, K, ptr_is_device);
     if (s == ADSCL_OK) s = adscl_spectrum(ctx, Jm, ADSCL_PREC_FP64, E0, 1);
-    if (store_all && s == ADSCL_OK) {
+    if (rec_evolve && s == ADSCL_OK) {
+        // the forward pass is the evolution kernel itself, recording every stage into the
+        // segment buffers as it goes (one persistent launch over all nT steps); the initial slice
+        // is kept for the transpose of E(0)
+        CK(cudaMemcpyAsync(ctx->d_ck, ctx->d_Phi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_ck + total, ctx->d_Pi, total * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        ctx->rec_stage = ctx->d_adj_stage;
+        ctx->rec_seg_stride = (long long)stN;
+        ctx->rec_steps = nT;
+        ctx->rec_seg = std::max(seg, 1);
+        s = adscl_evolve(ctx, (double)nT * ctx->h_desc[0].dt, nullptr, nullptr, nullptr, nullptr, 1);
+        ctx->rec_stage = nullptr;
+    } else if (store_all && s == ADSCL_OK) {
         // the forward pass is phase F of every segment, chained through the checkpoints; its
         // last slice becomes the context's current slice at step nT
         CK(cudaMemcpyAsync(ctx->d_ck, ctx->d_Phi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));

@@ -156,7 +156,26 @@ struct EvolveArgs {
     double t_end;
     double theta;
     double *outA, *outDelta;  // kModeSolve only: packed A, delta of the slice (may be null)
+    // kModeEvolve, optional (stage == null: off): the record of every stage of steps
+    // 0 .. stage_steps-1 that the discrete adjoint sweeps backwards (see stage_slot)
+    double *stage;
+    long long stage_seg_stride;  // doubles between the buffers of consecutive segments
+    long long stage_steps;
+    int32_t stage_seg;           // steps per segment
+    int32_t stage_nmax;          // node stride of one stored array
 };
+
+// Stage record: per stage s of step n of instance b, kStageArrays arrays of stage_nmax doubles:
+// the stage input Phi, Pi (node N-1: 0), m and e^{-delta} and F = A e^{-delta} at the nodes
+// (node N-1: M, 1, 1), alpha of the RK4-in-x map of m at the cells.  Segment g = n / stage_seg
+// holds steps g stage_seg .. (g+1) stage_seg - 1 of every instance.
+constexpr int kStageArrays = 6;
+__device__ __forceinline__ double *stage_slot(const EvolveArgs &a, int b, long long n, int s)
+{
+    const long long g = n / a.stage_seg, r = n - g * a.stage_seg;
+    return a.stage + g * a.stage_seg_stride +
+           (((long long)b * a.stage_seg + r) * 4 + s) * kStageArrays * (long long)a.stage_nmax;
+}
 
 // order-preserving map of doubles onto signed 64-bit integers (integer-pipe min)
 __device__ __forceinline__ long long order_key(double v) {
@@ -254,7 +273,8 @@ __device__ __forceinline__ int block_start(int r, int T) { return (r * T + CL - 
 // diagnostics cross between the CTAs through distributed shared memory.
 // launch bounds: 512 threads per SM worth of CTAs (one CTA of 512, two of 256, four of 128), so
 // that every shape gets the same 128 registers per thread
-template <int P, int NT, int CL = 1>
+// REC: the variant that also writes the stage record (EvolveArgs::stage) for the adjoint
+template <int P, int NT, int CL = 1, bool REC = false>
 __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(EvolveArgs a, int stride)
 {
     static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
@@ -438,10 +458,16 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
             for (;;) {
 #pragma unroll 1
                 for (int s = 0; s < 4; ++s) {
+                    // stage record for the adjoint (REC): its address is recomputed where it is
+                    // written (short live range)
+                    const bool rec = REC && step < a.stage_steps;
                     // ================= constraint solve on the stage slice =================
                     double De[P];
                     double aT = 1.0, bT = 0.0, SD = 0.0;
                     if (act) {
+                        double *stg = nullptr;
+                        if constexpr (REC) stg = rec ? stage_slot(a, b, step, s) : nullptr;
+                        const int snm = a.stage_nmax;
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
                         double pm1 = Sp[soff<P>(-1)], p0 = Sp[soff<P>(0)], p1 = Sp[soff<P>(1)];
                         double qm1 = Sq[soff<P>(-1)], q0 = Sq[soff<P>(0)], q1 = Sq[soff<P>(1)];
@@ -488,6 +514,11 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             const double al = fma(y3, e, fma(-kInvKappa, s01, 1.0 / 3.0));
                             const double w2 = fma(-qm3, rn0, tm);
                             const double be = fma(e, w2, fma(ca, tm, rn0 + rn1));
+                            if (stg) {
+                                stg[i0 + k] = p0;
+                                stg[snm + i0 + k] = q0;
+                                stg[5 * snm + i0 + k] = al;
+                            }
                             // running compositions: (aT, bT) maps m at node i0 to m at node i0+k+1,
                             // De[k] = sum of the increments of cells i0 .. i0+k-1 (k >= 1); both
                             // let the flux phase form every node's m and delta independently
@@ -508,6 +539,10 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             pm1 = p0; p0 = p1; p1 = p2;
                             qm1 = q0; q0 = q1; q1 = q2;
                             qn0 = qn1; rn0 = rn1;
+                        }
+                        if (stg && last) {
+                            stg[N - 1] = 0.0;
+                            stg[snm + N - 1] = 0.0;
                         }
                     }
                     // warp-level inclusive scans: affine prefix (lanes ascending), delta suffix sum
@@ -570,6 +605,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                     long long kmin = 0x7FFFFFFFFFFFFFFFLL;
                     if (act) {
                         const double *Sp = S0 + tb, *Sq = S1 + tb;
+                        double *stg = nullptr;
+                        if constexpr (REC) stg = rec ? stage_slot(a, b, step, s) : nullptr;
+                        const int snm = a.stage_nmax;
                         // m at the warp's first node (cm) and at node i0 (m); delta at node i0 (dtop) from
                         // the inclusive suffix sum SD of this and the warp's later lanes
                         double m, cm, dtop;
@@ -603,7 +641,13 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             const double mk = (k == 0) ? m : fma(sF[tb + soff<P>(k)], m, sU[tb + soff<P>(k)]);
                             const double Ai = fma(-mk, gK[k], 1.0);
                             kmin = min_ll(kmin, order_key(Ai));
-                            const double Fi = a_exp_neg_scaled(Ai, De[k], s_tab);
+                            const double Ei = a_exp_neg_scaled(1.0, De[k], s_tab);   // e^{-delta}
+                            const double Fi = Ai * Ei;
+                            if (stg) {
+                                stg[2 * snm + i] = mk;
+                                stg[3 * snm + i] = Ei;
+                                stg[4 * snm + i] = Fi;
+                            }
                             const double gi = Fi * Sp[soff<P>(k)];
                             const double fi = Fi * Sq[soff<P>(k)];
                             const double ui = gT[k] * gi;
@@ -623,7 +667,15 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                                 a.outDelta[d.off + i] = De[k] * kInvKappa;
                             }
                         }
-                        if (last) s_mass = fma(aT, cm, bT);   // m at node N-1: the inclusive prefix map
+                        if (last) {
+                            const double mN = fma(aT, cm, bT);   // m at node N-1: the inclusive prefix map
+                            s_mass = mN;
+                            if (stg) {
+                                stg[2 * snm + N - 1] = mN;
+                                stg[3 * snm + N - 1] = 1.0;
+                                stg[4 * snm + N - 1] = 1.0;
+                            }
+                        }
                         if (tfirst) {
                             const double d0n = De[0] * kInvKappa;   // delta(0)
                             s_d0 = d0n;

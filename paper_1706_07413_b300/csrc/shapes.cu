@@ -45,24 +45,25 @@ int local_nodes(int id, int Nmax)
     return ((T + s.CL - 1) / s.CL) * s.P + 1;
 }
 
-template <int P, int NT, int CL>
-const void *kernel_ptr() { return (const void *)evolve_kernel<P, NT, CL>; }
+template <int P, int NT, int CL, bool REC>
+const void *kernel_ptr() { return (const void *)evolve_kernel<P, NT, CL, REC>; }
 
-const void *kernel_of(int id)
+// the kernel of shape id; rec: the variant writing the adjoint's stage record
+const void *kernel_of(int id, bool rec)
 {
     switch (id) {
-#define ADSCL_CASE(i, p, nt, cl) case i: return kernel_ptr<p, nt, cl>();
+#define ADSCL_CASE(i, p, nt, cl) case i: return rec ? kernel_ptr<p, nt, cl, true>() : kernel_ptr<p, nt, cl, false>();
         ADSCL_SHAPES(ADSCL_CASE)
 #undef ADSCL_CASE
     }
     return nullptr;
 }
 
-template <int P, int NT, int CL>
+template <int P, int NT, int CL, bool REC>
 cudaError_t launch_t(const EvolveArgs &a, int units, size_t smem, int stride, cudaStream_t stream)
 {
     if constexpr (CL == 1) {
-        evolve_kernel<P, NT, 1><<<units, NT, smem, stream>>>(a, stride);
+        evolve_kernel<P, NT, 1, REC><<<units, NT, smem, stream>>>(a, stride);
         return cudaGetLastError();
     } else {
         cudaLaunchConfig_t cfg{};
@@ -77,7 +78,7 @@ cudaError_t launch_t(const EvolveArgs &a, int units, size_t smem, int stride, cu
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, evolve_kernel<P, NT, CL>, a, stride);
+        return cudaLaunchKernelEx(&cfg, evolve_kernel<P, NT, CL, REC>, a, stride);
     }
 }
 
@@ -97,9 +98,11 @@ cudaError_t shapes_set_attributes()
         const Shape &s = kShapes[id];
         // the largest grid a CTA of this shape can hold: P * NT nodes (+ the closing node)
         const size_t smem = shape_smem(id, s.P * s.NT * s.CL + 1);
-        const cudaError_t e = cudaFuncSetAttribute(kernel_of(id), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem);
-        if (e != cudaSuccess) return e;
+        for (int rec = 0; rec < 2; ++rec) {
+            const cudaError_t e = cudaFuncSetAttribute(kernel_of(id, rec != 0),
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -110,7 +113,7 @@ cudaError_t shape_max_units(int id, size_t smem, int num_sms, int *units)
     *units = 0;
     if (s.CL == 1) {
         int per_sm = 0;
-        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_of(id), s.NT, smem);
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_of(id, false), s.NT, smem);
         if (e != cudaSuccess) return e;
         *units = per_sm * num_sms;
         return cudaSuccess;
@@ -126,13 +129,17 @@ cudaError_t shape_max_units(int id, size_t smem, int num_sms, int *units)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(units, kernel_of(id), &cfg);
+    return cudaOccupancyMaxActiveClusters(units, kernel_of(id, false), &cfg);
 }
 
 cudaError_t shape_launch(int id, const EvolveArgs &a, int units, size_t smem, int stride, cudaStream_t stream)
 {
+    const bool rec = a.stage != nullptr;   // the same occupancy: 128 registers, same shared memory
     switch (id) {
-#define ADSCL_CASE(i, p, nt, cl) case i: return launch_t<p, nt, cl>(a, units, smem, stride, stream);
+#define ADSCL_CASE(i, p, nt, cl)                                                            \
+    case i:                                                                                 \
+        return rec ? launch_t<p, nt, cl, true>(a, units, smem, stride, stream)              \
+                   : launch_t<p, nt, cl, false>(a, units, smem, stride, stream);
         ADSCL_SHAPES(ADSCL_CASE)
 #undef ADSCL_CASE
     }

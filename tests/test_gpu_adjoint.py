@@ -135,3 +135,38 @@ def test_stage_storage_modes_agree(ad, orc, bufs):
     # and the context keeps evolving from it
     s.evolve((n + 5) * dt[0])
     assert np.all(s.clock()[1] == n + 5)
+
+
+def test_recording_forward_pass_for_batches_filling_the_gpu(ad, orc):
+    """A batch with at least one evolution CTA per SM takes its forward pass through the
+    evolution kernel's stage-recording variant (one launch over all steps, every segment's stages
+    written as it goes); its gradients equal those of the adjoint kernel's own recomputation
+    (one stage buffer) up to rounding and the oracle's adjoint."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    N, K, Jm, n = 129, 6, 8, 20
+    B = sms + 5
+    rng = np.random.default_rng(31)
+    a = rng.uniform(0.0, 0.8, (B, K)) * np.exp(-np.arange(K) / 2.0)
+    out = {}
+    for bufs in (0, 1):
+        s = ad.Solver([N] * B, ko_sigma=0.5, spec_J=Jm, ckpt_every=9, adjoint_stage_buffers=bufs)
+        dt, _ = s.clock()
+        out[bufs] = s.grad(a, n * dt[0])
+        assert np.all(s.clock()[1] == n)
+        if bufs == 0:   # the context ends on the final slice of a plain evolution
+            ref = ad.Solver([N] * 2, ko_sigma=0.5, spec_J=Jm, collapse_threshold=-1.0)
+            ref.set_initial_modes(a[[0, B - 1]])
+            ref.evolve(n * dt[0])
+            for k, b in enumerate((0, B - 1)):
+                x, y = s.get_state(b), ref.get_state(k)
+                assert np.abs(x[0] - y[0]).max() < 1e-13 and np.abs(x[1] - y[1]).max() < 1e-13
+            ref.close()
+        s.close()
+    (J0, g0), (J1, g1) = out[0], out[1]
+    assert np.abs(J0 - J1).max() <= 1e-12 * np.abs(J1).max()
+    assert np.abs(g0 - g1).max() <= 1e-10 * np.abs(g1).max()
+    for b in (0, B // 2, B - 1):
+        Jo, go = orc.grad(a[b], N, n, dt[0], sigma=0.5, Jm=Jm)
+        assert abs(J0[b] - Jo) <= 1e-10 * abs(Jo)
+        assert np.abs(g0[b] - go).max() <= 1e-9 * np.abs(go).max()
