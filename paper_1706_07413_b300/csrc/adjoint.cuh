@@ -242,8 +242,12 @@ __device__ double scan_sum(double x, ScanShared &sh)
 }
 
 // ------------------------------------------------------------------ per-cell RK4 map of m
+// The map in the form of the evolution kernel: with q = h b / 6, r = h a / 6 at the cell's left
+// end (q0, r0), midpoint (qm, tm; qm3 = 3 qm) and right end (q1, r1),
+//   y2 = 1/3 - q0, y3 = 1/3 - qm3 y2, ca = 2 - 6 q1, e = 2 - qm3 ca, w2 = tm - qm3 r0,
+//   alpha = (y2 - q1) + y3 e,  beta = (r0 + r1) + ca tm + e w2,  Delta = q0 + q1 + (4/3) qm3.
 struct CellFwd {
-    double qn0, qn1, rn0, rn1, p16, q16, qm3, tm, y2, y3, ca, w2, w3, al, be, De;
+    double qn0, qn1, rn0, rn1, p16, q16, qm3, tm, y2, y3, ca, e, w2, al, be, De;
 };
 
 // forward cell data of cell c from the stage slice (yP, yQ) (ghost-extended reads)
@@ -262,15 +266,14 @@ __device__ __forceinline__ CellFwd cell_fwd(const double *yP, const double *yQ, 
     const double rm = fma(r.p16, r.p16, r.q16 * r.q16);
     r.qm3 = __ldg(g.wsm3 + c) * rm;
     r.tm = __ldg(g.wtm + c) * rm;
-    const double s01 = r.qn0 + r.qn1;
-    r.De = fma(4.0 / 3.0, r.qm3, s01);
-    r.y2 = fma(-3.0, r.qn0, 1.0);
-    r.y3 = fma(-r.qm3, r.y2, 1.0);
-    r.ca = fma(-2.0, r.qn1, 2.0 / 3.0);
-    r.al = fma(-r.qm3, fma(r.y3, r.ca, fma(-2.0, r.qn0, 2.0 / 3.0)), 1.0 - s01);
+    r.De = fma(4.0 / 3.0, r.qm3, r.qn0 + r.qn1);
+    r.y2 = 1.0 / 3.0 - r.qn0;
+    r.y3 = fma(-r.qm3, r.y2, 1.0 / 3.0);
+    r.ca = fma(-6.0, r.qn1, 2.0);
+    r.e = fma(-r.qm3, r.ca, 2.0);
+    r.al = fma(r.y3, r.e, r.y2 - r.qn1);
     r.w2 = fma(-r.qm3, r.rn0, r.tm);
-    r.w3 = fma(-r.qm3, r.w2, r.tm);
-    r.be = fma(r.w3, fma(-6.0, r.qn1, 2.0), fma(2.0, r.w2, r.rn0 + r.rn1));
+    r.be = fma(r.e, r.w2, fma(r.ca, r.tm, r.rn0 + r.rn1));
     return r;
 }
 
@@ -279,36 +282,29 @@ __device__ __forceinline__ CellFwd cell_fwd(const double *yP, const double *yQ, 
 __device__ __forceinline__ void cell_bwd(const CellFwd &f, const GeoTab &g, int c, double alb, double beb,
                                          double Deb, double &n0, double &n1, double &p16b, double &q16b)
 {
-    double q0b = 0.0, q1b = 0.0, qm3b = 0.0, r0b = 0.0, r1b = 0.0, tmb = 0.0;
-    // beta = w3 (2 - 6 q1) + 2 w2 + r0 + r1
-    const double cb = fma(-6.0, f.qn1, 2.0);
-    double w3b = beb * cb, w2b = 2.0 * beb;
-    q1b += -6.0 * beb * f.w3;
-    r0b += beb;
-    r1b += beb;
-    // w3 = tm - qm3 w2
-    tmb += w3b;
-    qm3b -= w3b * f.w2;
-    w2b -= w3b * f.qm3;
+    // beta = (r0 + r1) + ca tm + e w2
+    double eb = beb * f.w2, cab = beb * f.tm, tmb = beb * f.ca, r0b = beb;
+    const double w2b = beb * f.e, r1b = beb;
+    // alpha = (y2 - q1) + y3 e
+    const double y3b = alb * f.e;
+    eb = fma(alb, f.y3, eb);
+    double y2b = alb, q1b = -alb;
     // w2 = tm - qm3 r0
     tmb += w2b;
-    qm3b -= w2b * f.rn0;
-    r0b -= w2b * f.qm3;
-    // alpha = (1 - q0 - q1) - qm3 [ (2/3 - 2 q0) + y3 ca ]
-    const double I = fma(f.y3, f.ca, fma(-2.0, f.qn0, 2.0 / 3.0));
-    qm3b -= alb * I;
-    const double Ib = -alb * f.qm3;
-    q0b -= alb;
-    q1b -= alb;
-    q0b -= 2.0 * Ib;
-    const double y3b = Ib * f.ca;
-    q1b -= 2.0 * Ib * f.y3;        // ca = 2/3 - 2 q1
-    qm3b -= y3b * f.y2;            // y3 = 1 - qm3 y2
-    q0b -= 3.0 * (-y3b * f.qm3);   // y2 = 1 - 3 q0
-    // Delta = 4/3 qm3 + q0 + q1
-    qm3b += (4.0 / 3.0) * Deb;
-    q0b += Deb;
+    double qm3b = -w2b * f.rn0;
+    r0b = fma(-w2b, f.qm3, r0b);
+    // e = 2 - qm3 ca
+    qm3b = fma(-eb, f.ca, qm3b);
+    cab = fma(-eb, f.qm3, cab);
+    // ca = 2 - 6 q1
+    q1b = fma(-6.0, cab, q1b);
+    // y3 = 1/3 - qm3 y2
+    qm3b = fma(-y3b, f.y2, qm3b);
+    y2b = fma(-y3b, f.qm3, y2b);
+    // y2 = 1/3 - q0;  Delta = q0 + q1 + (4/3) qm3
+    const double q0b = Deb - y2b;
     q1b += Deb;
+    qm3b = fma(4.0 / 3.0, Deb, qm3b);
     n0 = fma(__ldg(g.ws + c), q0b, __ldg(g.wt + c) * r0b);
     n1 = fma(__ldg(g.ws + c + 1), q1b, __ldg(g.wt + c + 1) * r1b);
     const double rmb = fma(__ldg(g.wsm3 + c), qm3b, __ldg(g.wtm + c) * tmb);
