@@ -60,10 +60,10 @@ REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
 # DRAM bytes (read + write) of one timed evolve_kernel launch of the amplitude scan, from an ncu
 # capture of this script (profiles/evolve_kernel_amp_scan.md); reported only while the kernel
 # source and the kernel shape are the ones the counters were taken on.
-TRAFFIC = {"kernel_sha256": "ab56462cc124fdeb3e752a9a8a0363f9e85fde7cce7ea98f012bad972b41e871",
-           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17851904 + 241193472,
+TRAFFIC = {"kernel_sha256": "caeb3f4fd82fb920132ccfd41d5a040a40f65d23136cdfbd7b986e865f0f088a",
+           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17203200 + 233953280,
            # FP64 instructions (DADD + DMUL + DFMA, thread level) per point-substep, same capture
-           "fp64_instr_per_point_substep": (23470579712 + 13958131712 + 38349320192) / 1074003968}
+           "fp64_instr_per_point_substep": (23334264832 + 13958131712 + 38349320192) / 1074003968}
 
 
 def kernel_digest():
