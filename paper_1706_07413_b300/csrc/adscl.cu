@@ -1515,6 +1515,31 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
     const int trial = trial_steps > 0 ? trial_steps : 8;
     const int B = ctx->B;
     const size_t fb = (size_t)ctx->total * sizeof(double);
+    const std::vector<int32_t> &ord = ctx->h_order;
+    std::vector<int> run_start;            // runs of equal N in the work order
+    std::vector<std::pair<int, int>> sig;  // (N, count) of each run
+    for (int i = 0; i < B;) {
+        int j = i + 1;
+        while (j < B && ctx->N[ord[j]] == ctx->N[ord[i]]) ++j;
+        run_start.push_back(i);
+        sig.push_back({ctx->N[ord[i]], j - i});
+        i = j;
+    }
+    run_start.push_back(B);
+    const int nr = (int)sig.size();
+    auto set_run = [&](int r, int id) {
+        for (int q = run_start[r]; q < run_start[r + 1]; ++q) ctx->shape_of[ord[q]] = id;
+    };
+    const TuneKey key{ctx->dev_name, ctx->num_sms, ctx->scheme, sig};
+    {   // a batch of this signature was tuned before in this process: apply its shapes (no device
+        // work, no allocation)
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            for (int r = 0; r < nr; ++r) set_run(r, it->second[r]);
+            return ADSCL_OK;
+        }
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     // the state is saved here and restored after every trial
     double *bPhi = nullptr, *bPi = nullptr, *bA = nullptr;   // bA: the evolved A (its schemes)
@@ -1552,30 +1577,6 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
             CK(cudaMemsetAsync(ctx->d_ctl, 0, (B + 1) * sizeof(QueueCtl), ctx->stream));
             return ADSCL_OK;
         };
-        const std::vector<int32_t> &ord = ctx->h_order;
-        std::vector<int> run_start;            // runs of equal N in the work order
-        std::vector<std::pair<int, int>> sig;  // (N, count) of each run
-        for (int i = 0; i < B;) {
-            int j = i + 1;
-            while (j < B && ctx->N[ord[j]] == ctx->N[ord[i]]) ++j;
-            run_start.push_back(i);
-            sig.push_back({ctx->N[ord[i]], j - i});
-            i = j;
-        }
-        run_start.push_back(B);
-        const int nr = (int)sig.size();
-        auto set_run = [&](int r, int id) {
-            for (int q = run_start[r]; q < run_start[r + 1]; ++q) ctx->shape_of[ord[q]] = id;
-        };
-        const TuneKey key{ctx->dev_name, ctx->num_sms, ctx->scheme, sig};
-        {
-            std::lock_guard<std::mutex> lk(g_tuned_mu);
-            auto it = g_tuned.find(key);
-            if (it != g_tuned.end()) {
-                for (int r = 0; r < nr; ++r) set_run(r, it->second[r]);
-                return restore();
-            }
-        }
         // point-substeps per ms of the list positions [i, j) with the current shapes: a one-step
         // warm-up, then `trial` steps, from the saved state
         auto rate_of = [&](int i, int j, int steps, double *rate) -> adscl_status {
