@@ -54,6 +54,11 @@ SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A
     "evolved_a_rk3": (1, 3, 84.0, 64),
     "evolved_a_rk2": (2, 2, 83.5, 64),
 }
+# FP64 instructions per point-substep of the adjoint kernel's phase F (recomputation with stage
+# record) and phase B (backward sweep) on the adjoint batch, from the ncu capture in
+# profiles/adjoint_kernel_adjoint_batch.md; used only while the kernel sources are unchanged
+ADJ_ISSUE = {"sha256": "013ec9d32a1423c08b665032850b8e2ba7b11a519df05dbae68c2609634a8656",
+             "phase_F": 21.19e9 / 268500992, "phase_B": 29.39e9 / 268500992}
 L2_FLUSH_BYTES = 512 << 20
 CPU_SAMPLE_STEPS = 800    # oracle sample of the cpu_baseline leg: ~10 s on 16 host threads
 REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
@@ -66,12 +71,12 @@ TRAFFIC = {"kernel_sha256": "caeb3f4fd82fb920132ccfd41d5a040a40f65d23136cdfbd7b9
            "fp64_instr_per_point_substep": (23334264832 + 13958131712 + 38349320192) / 1074003968}
 
 
-def kernel_digest():
+def kernel_digest(files=("evolve.cuh", "expneg.cuh")):
     """SHA-256 of the evolution kernel's code (comments and blank lines removed)."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in ("evolve.cuh", "expneg.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1706_07413_b300", "csrc", f)) as fh:
             for line in fh:
                 code = re.sub(r"//.*", "", line).rstrip()
@@ -565,8 +570,16 @@ def main():
             t_og = time.perf_counter() - t0
             cpu_adj = {"ratio": t_og / t_of, "forward_s": t_of, "grad_s": t_og,
                        "sample": f"1 instance, N={ainst[0].N}, {n_s} steps, oracle (1 thread)"}
+        adj_issue = None
+        if kernel_digest(("adjoint.cuh", "evolve.cuh", "expneg.cuh")) == ADJ_ISSUE["sha256"]:
+            # default-shape path: both phases in the adjoint kernel; FP64 instructions of the
+            # whole window against the probe's FMA issue rate (one FMA = 2 flops)
+            w_adj = len(ainst) * ainst[0].N * 4.0 * ADJ_STEPS
+            ipps = ADJ_ISSUE["phase_F"] + ADJ_ISSUE["phase_B"]
+            adj_issue = {"fp64_instr_per_point_substep": ipps,
+                         "frac": (w_adj * ipps / t_adj) / (tflops_peak * 1e12 / 2)}
         adj = {"value": t_adj / t_fwd, "forward_ms": 1e3 * t_fwd, "grad_ms": 1e3 * t_adj,
-               "cpu_oracle": cpu_adj,
+               "fp64_issue": adj_issue, "cpu_oracle": cpu_adj,
                "forward_shape_P_NT_CL": [8, 512, 1],
                "tuned": {"forward_shape_P_NT_CL": list(tuned[ainst[0].N]),
                          "forward_ms": 1e3 * t_fwd_t, "grad_ms": 1e3 * t_adj_t,
