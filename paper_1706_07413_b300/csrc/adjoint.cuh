@@ -241,6 +241,99 @@ __device__ double scan_sum(double x, ScanShared &sh)
     return r;
 }
 
+// An affine scan and a sum scan in one pass with one CTA barrier and one cluster barrier:
+// kAffSuffix = false: the exclusive affine prefix (threads ascending, as scan_affine_prefix) and
+// the exclusive suffix sum (as scan_sum<true>); kAffSuffix = true: the exclusive affine suffix
+// (as scan_affine_suffix) and the exclusive prefix sum (as scan_sum<false>).  Same slots and the
+// same association order as the separate scans.
+template <int CL, bool kAffSuffix>
+__device__ void scan_pair(double a, double b, double x, ScanShared &sh, double &raff, double &rsum)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        if (kAffSuffix) {
+            const double an = __shfl_down_sync(FULL, a, o), bn = __shfl_down_sync(FULL, b, o);
+            const double xn = __shfl_up_sync(FULL, x, o);
+            if (lane + o < 32) { b = fma(a, bn, b); a = a * an; }
+            if (lane >= o) x += xn;
+        } else {
+            const double ap = __shfl_up_sync(FULL, a, o), bp = __shfl_up_sync(FULL, b, o);
+            const double xp = __shfl_down_sync(FULL, x, o);
+            if (lane >= o) { b = fma(a, bp, b); a = a * ap; }
+            if (lane + o < 32) x += xp;
+        }
+    }
+    double aEx, bEx, ex;
+    if (kAffSuffix) {
+        aEx = __shfl_down_sync(FULL, a, 1);
+        bEx = __shfl_down_sync(FULL, b, 1);
+        ex = __shfl_up_sync(FULL, x, 1);
+        if (lane == 31) { aEx = 1.0; bEx = 0.0; }
+        if (lane == 0) { ex = 0.0; sh.a[wid] = a; sh.b[wid] = b; }
+        if (lane == 31) sh.d[wid] = x;
+    } else {
+        aEx = __shfl_up_sync(FULL, a, 1);
+        bEx = __shfl_up_sync(FULL, b, 1);
+        ex = __shfl_down_sync(FULL, x, 1);
+        if (lane == 0) { aEx = 1.0; bEx = 0.0; sh.d[wid] = x; }
+        if (lane == 31) { ex = 0.0; sh.a[wid] = a; sh.b[wid] = b; }
+    }
+    __syncthreads();
+    if (wid == 0) {
+        double A = lane < kANW ? sh.a[lane] : 1.0, B = lane < kANW ? sh.b[lane] : 0.0;
+        double X = lane < kANW ? sh.d[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < kANW; o <<= 1) {
+            if (kAffSuffix) {
+                const double an = __shfl_down_sync(FULL, A, o), bn = __shfl_down_sync(FULL, B, o);
+                const double xn = __shfl_up_sync(FULL, X, o);
+                if (lane + o < kANW) { B = fma(A, bn, B); A = A * an; }
+                if (lane >= o) X += xn;
+            } else {
+                const double ap = __shfl_up_sync(FULL, A, o), bp = __shfl_up_sync(FULL, B, o);
+                const double xp = __shfl_down_sync(FULL, X, o);
+                if (lane >= o) { B = fma(A, bp, B); A = A * ap; }
+                if (lane + o < kANW) X += xp;
+            }
+        }
+        double bw, aw, w;
+        if (kAffSuffix) {
+            bw = __shfl_down_sync(FULL, B, 1);
+            aw = __shfl_down_sync(FULL, A, 1);
+            w = __shfl_up_sync(FULL, X, 1);
+            if (lane + 1 >= kANW) { bw = 0.0; aw = 1.0; }
+            if (lane == 0) w = 0.0;
+        } else {
+            bw = __shfl_up_sync(FULL, B, 1);
+            aw = __shfl_up_sync(FULL, A, 1);
+            w = __shfl_down_sync(FULL, X, 1);
+            if (lane == 0) { bw = 0.0; aw = 1.0; }
+            if (lane + 1 >= kANW) w = 0.0;
+        }
+        if (lane < kANW) { sh.c[lane] = bw; sh.e[lane] = aw; sh.f[lane] = w; }
+        if constexpr (CL == 2) {
+            const int rk = cluster_rank();
+            if (kAffSuffix) {   // rank 1's total map to rank 0, rank 0's sum to rank 1
+                if (lane == 0 && rk == 1) st_peer(&sh.pb, B, 0);
+                if (lane == kANW - 1 && rk == 0) st_peer(&sh.pd, X, 1);
+            } else {            // rank 0's total map to rank 1, rank 1's sum to rank 0
+                if (lane == kANW - 1 && rk == 0) st_peer(&sh.pb, B, 1);
+                if (lane == 0 && rk == 1) st_peer(&sh.pd, X, 0);
+            }
+        }
+    }
+    csync<CL>();
+    raff = fma(aEx, sh.c[wid], bEx);
+    rsum = ex + sh.f[wid];
+    if constexpr (CL == 2) {
+        const int rk = cluster_rank();
+        if (rk == (kAffSuffix ? 0 : 1)) raff = fma(aEx * sh.e[wid], sh.pb, raff);   // the other rank's maps first
+        if (rk == (kAffSuffix ? 1 : 0)) rsum += sh.pd;
+    }
+}
+
 // ------------------------------------------------------------------ per-cell RK4 map of m
 // The map in the form of the evolution kernel: with q = h b / 6, r = h a / 6 at the cell's left
 // end (q0, r0), midpoint (qm, tm; qm3 = 3 qm) and right end (q1, r1),
@@ -367,8 +460,8 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
             else { bT = fma(cf.al, bT, cf.be); aT *= cf.al; SD += cf.De; }
         }
     }
-    const double mstart = scan_affine_prefix<CL>(aT, bT, sh);
-    const double dend = scan_sum<true, CL>(SD, sh);
+    double mstart, dend;   // m at node i0; the sum of Delta over the cells from node i0 + AP on
+    scan_pair<CL, false>(aT, bT, SD, sh, mstart, dend);
     double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0;
     if (act) {
         double dc = dend;
@@ -454,8 +547,8 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
 #pragma unroll
         for (int k = 0; k < AP; ++k) SP += scr.dlb[i0 + k];
     }
-    const double mu_end = scan_affine_suffix<CL>(aT, bT, sh);   // mu at node i0 + P
-    const double dpre = scan_sum<false, CL>(SP, sh);             // sum of delta_bar over nodes < i0
+    double mu_end, dpre;   // mu at node i0 + AP; the sum of delta_bar over the nodes < i0
+    scan_pair<CL, true>(aT, bT, SP, sh, mu_end, dpre);
     if (act) {
         double mu = mu_end;
         double mun[AP];   // mu at node c+1 for each own cell
@@ -562,7 +655,8 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
         }
         if (last) { scr.dlb[N - 1] = 0.0; scr.mb[N - 1] = 0.0; }
     }
-    csync<CL>();
+    // no barrier: the constraint transpose reads only this thread's mb, dlb before its scans'
+    // barriers, and vP, vQ, v2 are written again only after the next stage's first barrier
     constraint_backward<CL>(yP, yQ, M, AL, scr, ybP, ybQ, d, g, sh);
 }
 
@@ -785,7 +879,8 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                         lamQ[i0 + k] += scr.ybQ[i0 + k];
                     }
                 }
-                csync<CL>();
+                // no barrier: the next stage first touches only this thread's nodes, then
+                // synchronises before any neighbour read or before scr.pb, qb, r1, fb are rewritten
             }
         }
     }
