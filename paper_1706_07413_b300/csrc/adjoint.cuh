@@ -826,13 +826,13 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                         }
                     }
                 }
-                csync<CL>();
+                // no barrier: until the next stage's first barrier every thread touches only
+                // its own nodes (the update reads the stage derivative of its own nodes)
             }
             if (act) {
 #pragma unroll
                 for (int k = 0; k < AP; ++k) { scr.uP[i0 + k] = scr.aP[i0 + k]; scr.uQ[i0 + k] = scr.aQ[i0 + k]; }
             }
-            csync<CL>();
         }
         if (a.outP && act) {   // the segment's last slice (the next segment's start)
             double *oP = a.outP + d.off, *oQ = a.outQ + d.off;
