@@ -343,17 +343,17 @@ struct CellFwd {
     double qn0, qn1, rn0, rn1, p16, q16, qm3, tm, y2, y3, ca, e, w2, al, be, De;
 };
 
-// forward cell data of cell c from the stage slice (yP, yQ) (ghost-extended reads)
-__device__ __forceinline__ CellFwd cell_fwd(const double *yP, const double *yQ, const GeoTab &g, int N, int c)
+// forward cell data of cell c from Phi, Pi at nodes c-1 .. c+2 (ghosts by parity) and the node
+// factors q = ws rho, r = wt rho at its two ends
+__device__ __forceinline__ CellFwd cell_fwd_n(double qn0, double rn0, double qn1, double rn1, double pm1,
+                                             double p0, double p1, double p2, double qm1, double q0,
+                                             double q1, double q2, const GeoTab &g, int c)
 {
     CellFwd r;
-    const double pm1 = gv(yP, N, c - 1, -1.0, 1.0), p0 = yP[c], p1 = yP[c + 1], p2 = gv(yP, N, c + 2, -1.0, 1.0);
-    const double qm1 = gv(yQ, N, c - 1, 1.0, -1.0), q0 = yQ[c], q1 = yQ[c + 1], q2 = gv(yQ, N, c + 2, 1.0, -1.0);
-    const double rho0 = fma(p0, p0, q0 * q0), rho1 = fma(p1, p1, q1 * q1);
-    r.qn0 = __ldg(g.ws + c) * rho0;
-    r.rn0 = __ldg(g.wt + c) * rho0;
-    r.qn1 = __ldg(g.ws + c + 1) * rho1;
-    r.rn1 = __ldg(g.wt + c + 1) * rho1;
+    r.qn0 = qn0;
+    r.rn0 = rn0;
+    r.qn1 = qn1;
+    r.rn1 = rn1;
     r.p16 = fma(9.0, p0 + p1, -(pm1 + p2));
     r.q16 = fma(9.0, q0 + q1, -(qm1 + q2));
     const double rm = fma(r.p16, r.p16, r.q16 * r.q16);
@@ -368,6 +368,17 @@ __device__ __forceinline__ CellFwd cell_fwd(const double *yP, const double *yQ, 
     r.w2 = fma(-r.qm3, r.rn0, r.tm);
     r.be = fma(r.e, r.w2, fma(r.ca, r.tm, r.rn0 + r.rn1));
     return r;
+}
+
+// the same from the stage slice (yP, yQ) (ghost-extended reads)
+__device__ __forceinline__ CellFwd cell_fwd(const double *yP, const double *yQ, const GeoTab &g, int N, int c)
+{
+    const double p0 = yP[c], p1 = yP[c + 1], q0 = yQ[c], q1 = yQ[c + 1];
+    const double rho0 = fma(p0, p0, q0 * q0), rho1 = fma(p1, p1, q1 * q1);
+    return cell_fwd_n(__ldg(g.ws + c) * rho0, __ldg(g.wt + c) * rho0, __ldg(g.ws + c + 1) * rho1,
+                      __ldg(g.wt + c + 1) * rho1, gv(yP, N, c - 1, -1.0, 1.0), p0, p1,
+                      gv(yP, N, c + 2, -1.0, 1.0), gv(yQ, N, c - 1, 1.0, -1.0), q0, q1,
+                      gv(yQ, N, c + 2, 1.0, -1.0), g, c);
 }
 
 // transpose of cell_fwd from (alpha_bar, beta_bar, Delta_bar) to the node and midpoint
@@ -559,11 +570,22 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
         }
         double Db = dpre;
         double n0s[AP];
+        // the cells' forward data with the node quantities carried from cell to cell
+        double pm1 = gv(yP, N, i0 - 1, -1.0, 1.0), p0 = yP[i0], p1 = yP[i0 + 1];
+        double qm1 = gv(yQ, N, i0 - 1, 1.0, -1.0), q0 = yQ[i0], q1 = yQ[i0 + 1];
+        const double rho0 = fma(p0, p0, q0 * q0);
+        double qn0 = __ldg(g.ws + i0) * rho0, rn0 = __ldg(g.wt + i0) * rho0;
 #pragma unroll
         for (int k = 0; k < AP; ++k) {
             const int c = i0 + k;
             Db += scr.dlb[c];                         // Delta_bar_c = sum_{i <= c} delta_bar_i
-            const CellFwd cf = cell_fwd(yP, yQ, g, N, c);
+            const double p2 = gv(yP, N, c + 2, -1.0, 1.0), q2 = gv(yQ, N, c + 2, 1.0, -1.0);
+            const double rho1 = fma(p1, p1, q1 * q1);
+            const double qn1 = __ldg(g.ws + c + 1) * rho1, rn1 = __ldg(g.wt + c + 1) * rho1;
+            const CellFwd cf = cell_fwd_n(qn0, rn0, qn1, rn1, pm1, p0, p1, p2, qm1, q0, q1, q2, g, c);
+            pm1 = p0; p0 = p1; p1 = p2;
+            qm1 = q0; q0 = q1; q1 = q2;
+            qn0 = qn1; rn0 = rn1;
             double n0, n1, pb, qb;
             cell_bwd(cf, g, c, mun[k] * M[c], mun[k], Db, n0, n1, pb, qb);
             n0s[k] = n0;
