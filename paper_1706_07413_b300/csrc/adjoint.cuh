@@ -619,8 +619,9 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
 }
 
 // ------------------------------------------------------------------ stage backward
-// ybar = R'(y)^T kbar with kbar in (scr.vP, scr.vQ) (already restricted to rows), written to
-// (ybP, ybQ) (overwritten) on the thread's nodes.
+// ybar = R'(y)^T kbar with kbar in (scr.vP, scr.vQ) (already restricted to rows, and scaled by
+// c12 = 1/(12 h) and cq, the factors of Phi-dot and Pi-dot), written to (ybP, ybQ) (overwritten)
+// on the thread's nodes.
 template <int CL>
 __device__ void stage_backward(const double *yP, const double *yQ, const double *M, const double *E,
                                const double *F, const double *AL, const Scr &scr, double *ybP, double *ybQ,
@@ -663,14 +664,14 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
             }
             if (j == N - 2) ubx += (4.0 / 3.0) * (-Dr(v2, N - 1));   // u(pi/2) extrapolation
             if (j == N - 3) ubx += (-1.0 / 3.0) * (-Dr(v2, N - 1));
-            const double fb = d.c12 * fbx;
+            const double fb = fbx;   // (vP carries the factor c12, vQ the factor cq)
             double gb = __ldg(g.T + j) * ubx;
-            if (j == 1) gb = fma(16.0 * d.c3, vQ0, gb);             // Pi-dot(0) = 3 (F Phi)'(0)
-            if (j == 2) gb = fma(-2.0 * d.c3, vQ0, gb);
+            if (j == 1) gb = fma(16.0 * d.c3q, vQ0, gb);            // Pi-dot(0) = 3 (F Phi)'(0)
+            if (j == 2) gb = fma(-2.0 * d.c3q, vQ0, gb);
             const double Fj = F[j];
             const double Fb = fma(fb, yQ[j], gb * yP[j]);
-            ybQ[j] = fma(fb, Fj, d.cko * kqx);
-            ybP[j] = fma(gb, Fj, d.cko * kpx);
+            ybQ[j] = fma(fb, Fj, d.ko ? kqx : 0.0);
+            ybP[j] = fma(gb, Fj, d.rko * kpx);
             const double Ab = Fb * E[j];
             scr.dlb[j] = -Fb * Fj;
             scr.mb[j] = -Ab * __ldg(g.K + j);
@@ -880,14 +881,15 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
 #pragma unroll
                     for (int k = 0; k < AP; ++k) {
                         const int i = i0 + k;
-                        double kb = wst[s] * d.dt * scr.lo[i], kq = wst[s] * d.dt * scr.lq[i];
+                        // kbar, scaled by c12 (Phi) and cq (Pi): the factors of Phi-dot and Pi-dot
+                        double kb = wst[s] * d.dtc * scr.lo[i], kq = wst[s] * d.dtq * scr.lq[i];
                         if (s < 3) {
-                            kb = fma(cst[s + 1] * d.dt, scr.ybP[i], kb);
-                            kq = fma(cst[s + 1] * d.dt, scr.ybQ[i], kq);
+                            kb = fma(cst[s + 1] * d.dtc, scr.ybP[i], kb);
+                            kq = fma(cst[s + 1] * d.dtq, scr.ybQ[i], kq);
                         }
                         scr.vP[i] = (i == 0) ? 0.0 : kb;   // Phi-dot(0) is identically zero
                         scr.vQ[i] = kq;
-                        scr.v2[i] = __ldg(g.iT12 + i) * kq;
+                        scr.v2[i] = __ldg(g.iT12k + i) * kq;   // = iT12 kbar_Pi
                     }
                     if (own.last) { scr.vP[N - 1] = 0.0; scr.vQ[N - 1] = 0.0; scr.v2[N - 1] = 0.0; }
                 }
