@@ -170,3 +170,19 @@ def test_recording_forward_pass_for_batches_filling_the_gpu(ad, orc):
         Jo, go = orc.grad(a[b], N, n, dt[0], sigma=0.5, Jm=Jm)
         assert abs(J0[b] - Jo) <= 1e-10 * abs(Jo)
         assert np.abs(g0[b] - go).max() <= 1e-9 * np.abs(go).max()
+
+
+@pytest.mark.parametrize("ctas", [1, 2])
+def test_grad_without_dissipation_matches_oracle(ad, orc, ctas):
+    """sigma = 0: the dissipation terms of the transposed step are switched off as in the
+    forward step."""
+    N, B, K, Jm, n = 129, 2, 6, 8, 30
+    rng = np.random.default_rng(41)
+    a = rng.uniform(0.0, 0.8, (B, K)) * np.exp(-np.arange(K) / 2.0)
+    s = ad.Solver([N] * B, ko_sigma=0.0, spec_J=Jm, ckpt_every=9, adjoint_ctas=ctas)
+    dt, _ = s.clock()
+    J, g = s.grad(a, n * dt[0])
+    for b in range(B):
+        Jo, go = orc.grad(a[b], N, n, dt[0], sigma=0.0, Jm=Jm)
+        assert abs(J[b] - Jo) <= 1e-10 * abs(Jo)
+        assert np.abs(g[b] - go).max() <= 1e-9 * np.abs(go).max()

@@ -200,3 +200,22 @@ def test_evolved_a_autotune_keeps_state(ad):
         for x, y in zip(before[b][:3], after[:3]):   # Phi, Pi and the evolved A are state
             assert np.array_equal(x, y)
     assert np.array_equal(clk, s.clock()[1])
+
+
+@pytest.mark.parametrize("scheme", [1, 3])
+def test_evolved_a_and_fixed_metric_without_dissipation(ad, orc, scheme):
+    """sigma = 0 in the evolved-A and fixed-metric kernels (the dissipation term is switched off,
+    Pi-dot is not divided by a dissipation factor)."""
+    N, steps = 1025, 20
+    Phi, Pi = W.smooth_random(N, seed=77 + scheme, amp=2.0)
+    s = ad.Solver([N], scheme=scheme, a_reint_every=0, ko_sigma=0.0)
+    s.set_initial(Phi, Pi)
+    dt, _ = s.clock()
+    s.evolve(steps * dt[0])
+    gP, gQ, _, _ = s.get_state(0)
+    if scheme == 1:
+        r = orc.ea_evolve(Phi, Pi, orc.constraints(Phi, Pi)[0], dt[0], steps, order=3, reint=0, sigma=0.0)
+        oP, oQ = r.Phi, r.Pi
+    else:
+        oP, oQ = orc.fixed_evolve(Phi, Pi, dt[0], steps, order=3, sigma=0.0)
+    assert _close(gP, oP, 1e-11) and _close(gQ, oQ, 1e-11)

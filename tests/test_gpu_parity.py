@@ -63,6 +63,25 @@ def test_single_rk4_step_matches_oracle(ad, orc, N):
     assert gPhi[0] == 0.0 and gPhi[-1] == 0.0 and gPi[-1] == 0.0
 
 
+@pytest.mark.parametrize("N", [17, 4097])
+@pytest.mark.parametrize("sigma", [0.0, 0.125])
+def test_rk4_steps_match_oracle_for_other_dissipation(ad, orc, N, sigma):
+    """sigma = 0 switches the dissipation term off (Pi-dot is then not divided by a dissipation
+    factor); a second value checks that the factor folded into the weights follows sigma."""
+    Phi, Pi = W.smooth_random(N, seed=3 * N + 1, amp=2.0)
+    s = _solver(ad, [N], ko_sigma=sigma)
+    s.set_initial(Phi, Pi)
+    dt, _ = s.clock()
+    s.evolve(3 * dt[0])
+    gPhi, gPi, _, _ = s.get_state(0)
+    oPhi, oPi = Phi, Pi
+    for _ in range(3):
+        oPhi, oPi = orc.rk4_step(oPhi, oPi, dt[0], sigma=sigma)
+    scale = max(np.abs(oPhi).max(), np.abs(oPi).max())
+    assert np.abs(gPhi - oPhi).max() < 1e-13 * scale
+    assert np.abs(gPi - oPi).max() < 1e-13 * scale
+
+
 def test_single_gaussian_pulse_parity(ad, orc):
     """N = 1025, eps = 40, sigma = 1/16, RK4 with dt ~ 0.5 dx: fields agree to 1e-9 max-abs
     before collapse; the collapse (min A < 0.01) time agrees to 0.1 %."""
