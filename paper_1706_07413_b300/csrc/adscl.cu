@@ -1263,11 +1263,32 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     };
     const bool store_all = ctx->adj_stage_bufs >= nseg &&
                            (ctx->adj_bufs_cap == 0 || ctx->adj_bufs_cap >= nseg);
-    // with every stage stored, the forward pass is the evolution kernel recording its stages when
-    // its shapes spread the batch over the whole GPU (at least one CTA per SM); otherwise the
-    // adjoint kernel's own recomputation (2-CTA clusters for small batches) records them
+    // With every stage stored, the forward pass is the evolution kernel recording its stages when
+    // its shapes spread the batch over the whole GPU (at least one CTA per SM).  A batch whose
+    // shapes give fewer CTAs than SMs (a small batch on the default one-CTA shapes) runs that
+    // pass on the same thread layout split over a cluster of 2 or 4 CTAs (P = 8, NT * CL = 512),
+    // the largest that keeps the batch within two CTAs per SM; the context's shapes are restored
+    // afterwards.  Otherwise the adjoint kernel's own recomputation records the stages.
     long long evo_ctas = 0;
     for (int b = 0; b < B; ++b) evo_ctas += kShapes[ctx->shape_of[b]].CL;
+    std::vector<int> rec_shape = ctx->shape_of;
+    if (store_all && evo_ctas < ctx->num_sms) {
+        evo_ctas = 0;
+        for (int b = 0; b < B; ++b) {
+            const int cur = ctx->shape_of[b];
+            if (kShapes[cur].P == 8 && kShapes[cur].NT * kShapes[cur].CL == 512) {
+                for (int cl : {4, 2}) {
+                    const int id = shape_index(8, 512 / cl, cl);
+                    if (id >= 0 && cl > kShapes[cur].CL && shape_fits(id, ctx->N[b]) &&
+                        (long long)B * cl <= 2LL * ctx->num_sms) {
+                        rec_shape[b] = id;
+                        break;
+                    }
+                }
+            }
+            evo_ctas += kShapes[rec_shape[b]].CL;
+        }
+    }
     const bool rec_evolve = store_all && evo_ctas >= ctx->num_sms;
     const bool piped = !store_all && ctx->adj_stage_bufs >= 2 && ctx->adj_bufs_cap != 1 && nseg > 1;
     if (piped && !ctx->adj_aux) {
@@ -1298,7 +1319,9 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         ctx->rec_seg_stride = (long long)stN;
         ctx->rec_steps = nT;
         ctx->rec_seg = std::max(seg, 1);
+        std::swap(ctx->shape_of, rec_shape);
         s = adscl_evolve(ctx, (double)nT * ctx->h_desc[0].dt, nullptr, nullptr, nullptr, nullptr, 1);
+        std::swap(ctx->shape_of, rec_shape);
         ctx->rec_stage = nullptr;
     } else if (store_all && s == ADSCL_OK) {
         // the forward pass is phase F of every segment, chained through the checkpoints; its

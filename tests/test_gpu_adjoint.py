@@ -137,15 +137,17 @@ def test_stage_storage_modes_agree(ad, orc, bufs):
     assert np.all(s.clock()[1] == n + 5)
 
 
-def test_recording_forward_pass_for_batches_filling_the_gpu(ad, orc):
+@pytest.mark.parametrize("extra", [5, "quarter"])
+def test_recording_forward_pass_for_batches_filling_the_gpu(ad, orc, extra):
     """A batch with at least one evolution CTA per SM takes its forward pass through the
     evolution kernel's stage-recording variant (one launch over all steps, every segment's stages
-    written as it goes); its gradients equal those of the adjoint kernel's own recomputation
-    (one stage buffer) up to rounding and the oracle's adjoint."""
+    written as it goes); a quarter of that on the default one-CTA shapes runs the pass on 4-CTA
+    clusters.  Its gradients equal those of the adjoint kernel's own recomputation (one stage
+    buffer) up to rounding and the oracle's adjoint."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     N, K, Jm, n = 129, 6, 8, 20
-    B = sms + 5
+    B = sms + 5 if extra == 5 else sms // 4 + 3
     rng = np.random.default_rng(31)
     a = rng.uniform(0.0, 0.8, (B, K)) * np.exp(-np.arange(K) / 2.0)
     out = {}
