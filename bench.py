@@ -54,11 +54,13 @@ SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A
     "evolved_a_rk3": (1, 3, 84.0, 64),
     "evolved_a_rk2": (2, 2, 83.5, 64),
 }
-# FP64 instructions per point-substep of the adjoint kernel's phase F (recomputation with stage
-# record) and phase B (backward sweep) on the adjoint batch, from the ncu capture in
+# FP64 instructions per point-substep of the bench's adjoint batch: the forward pass recorded by
+# the evolution kernel (evolve_kernel<8, 128, 4, true> over the whole window) and the adjoint
+# kernel's backward sweep (phase B, per segment), from the ncu capture in
 # profiles/adjoint_kernel_adjoint_batch.md; used only while the kernel sources are unchanged
-ADJ_ISSUE = {"sha256": "013ec9d32a1423c08b665032850b8e2ba7b11a519df05dbae68c2609634a8656",
-             "phase_F": 21.19e9 / 268500992, "phase_B": 29.39e9 / 268500992}
+ADJ_ISSUE = {"sha256": "119fd096e22b9e1b7254041df54a75f048c6967d5a6b1ca32e3683d3f5c869e6",
+             "forward_record": 75931385856 / 1074003968,
+             "phase_B": (9518514176 + 10991304704 + 8170766336) / 268500992}
 L2_FLUSH_BYTES = 512 << 20
 CPU_SAMPLE_STEPS = 800    # oracle sample of the cpu_baseline leg: ~10 s on 16 host threads
 REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
@@ -572,10 +574,10 @@ def main():
                        "sample": f"1 instance, N={ainst[0].N}, {n_s} steps, oracle (1 thread)"}
         adj_issue = None
         if kernel_digest(("adjoint.cuh", "evolve.cuh", "expneg.cuh")) == ADJ_ISSUE["sha256"]:
-            # default-shape path: both phases in the adjoint kernel; FP64 instructions of the
-            # whole window against the probe's FMA issue rate (one FMA = 2 flops)
+            # default-shape context: the recording forward pass and the backward sweep; FP64
+            # instructions of the whole window against the probe's FMA issue rate (FMA = 2 flops)
             w_adj = len(ainst) * ainst[0].N * 4.0 * ADJ_STEPS
-            ipps = ADJ_ISSUE["phase_F"] + ADJ_ISSUE["phase_B"]
+            ipps = ADJ_ISSUE["forward_record"] + ADJ_ISSUE["phase_B"]
             adj_issue = {"fp64_instr_per_point_substep": ipps,
                          "frac": (w_adj * ipps / t_adj) / (tflops_peak * 1e12 / 2)}
         adj = {"value": t_adj / t_fwd, "forward_ms": 1e3 * t_fwd, "grad_ms": 1e3 * t_adj,
