@@ -105,10 +105,17 @@ def test_autotune_keeps_state_and_is_cached(ad, orc):
         gP, gQ, _, _ = s.get_state(b)
         scale = max(1.0, np.abs(r.Pi).max())
         assert np.abs(gP - r.Phi).max() < 1e-11 * scale and np.abs(gQ - r.Pi).max() < 1e-11 * scale
-    # a second context of the same sizes reuses the cached choice
+    # a second context of the same sizes reuses the cached choice without touching its state
     s2 = ad.Solver(Ns)
     s2.set_initial(Phi, Pi)
+    s2.evolve(0.005)
+    before2 = [s2.get_state(b)[:2] for b in range(len(Ns))]
+    clk2 = s2.clock()[1].copy()
     assert s2.autotune(trial_steps=4) == shapes
+    assert np.array_equal(clk2, s2.clock()[1])
+    for b in range(len(Ns)):
+        after = s2.get_state(b)
+        assert np.array_equal(before2[b][0], after[0]) and np.array_equal(before2[b][1], after[1])
 
 
 def test_set_shape_rejects_what_does_not_fit(ad):
