@@ -797,19 +797,31 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                                 Xp = 0.0;                                   // Phi(0) = 0
                                 dQ = fma(d.c3q, sF[spos<P>(-3)], kqs);     // 3 (F Phi)'(0) / cq
                             }
-                            const double up = __ldcg(uPhi + i), uq = __ldcg(uPi + i);
+                            // the slice u_n: the stage itself at s = 0, from global memory at
+                            // s = 1, 2, not needed at s = 3
+                            double up = 0.0, uq = 0.0;
+                            if (s == 0) {
+                                up = Sp[soff<P>(k)];
+                                uq = Sq[soff<P>(k)];
+                            } else if (s < 3) {
+                                up = __ldcg(uPhi + i);
+                                uq = __ldcg(uPi + i);
+                            }
+                            // RK4 accumulators in a node-block-interleaved layout (entry k of node
+                            // block t at k * TnAll + t), so that a warp's accesses are contiguous
+                            const int ci = k * TnAll + bs + tid;
                             double ap_, aq_;
                             if (s == 0) {
                                 ap_ = fma(waccc, Xp, up);
                                 aq_ = fma(wacc, dQ, uq);
                             } else {
-                                ap_ = fma(waccc, Xp, __ldcg(cPhi + i));
-                                aq_ = fma(wacc, dQ, __ldcg(cPi + i));
+                                ap_ = fma(waccc, Xp, __ldcg(cPhi + ci));
+                                aq_ = fma(wacc, dQ, __ldcg(cPi + ci));
                             }
                             double np, nq;
                             if (s < 3) {
-                                cPhi[i] = ap_;
-                                cPi[i] = aq_;
+                                cPhi[ci] = ap_;
+                                cPi[ci] = aq_;
                                 np = fma(wstc, Xp, up);
                                 nq = fma(wst, dQ, uq);
                             } else {
