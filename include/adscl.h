@@ -183,10 +183,12 @@ adscl_status adscl_get_clock(adscl_ctx *ctx, double *dt, int64_t *step);
  * (a thread-block cluster) per instance -- on the context's own instances of that N for
  * trial_steps RK4 steps (0 = 8) from their current slices, keep the fastest, and restore the
  * state (the call changes no instance's slice -- Phi, Pi and, under the evolved-A schemes, A --
- * step or status).  With several grid sizes, which
- * run concurrently in a batch, the per-size choice is kept only if the whole batch (timed over
- * max(4 trial_steps, 32) steps) is more than 1 % faster with it than with the default shapes.  Results are cached for the process by (GPU name, SM count,
- * the batch's grid sizes with their instance counts); a cached entry is reused without timing.
+ * step or status).  With one grid size the two fastest shapes are timed again over
+ * max(4 trial_steps, 32) steps and the faster one is kept.  With several grid sizes, which run
+ * concurrently in a batch, the per-size choice is kept only if the whole batch (timed over that
+ * longer window) is more than 1 % faster with it than with the default shapes.  Results are
+ * cached for the process by (GPU name, SM count, scheme, the batch's grid sizes with their
+ * instance counts); a cached entry is reused without timing or touching the state.
  * Synchronous.  The evolved-A and fixed-metric kernels are built for the shapes (8, 512, 1/2/4/8),
  * (8, 256, 2) and (8, 128, 2).
  * Different shapes associate the radial scans differently, so results agree with the default

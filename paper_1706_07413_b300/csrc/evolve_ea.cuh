@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
         const GeoTab g = a.geo[d.geo];
         const EaGeo eg = ea.eg[d.geo];
         double *uPhi = a.Phi + d.off, *uPi = a.Pi + d.off, *uA = ea.A + d.off;
-        double *sA = a.aPhi + d.off;   // stage A
+        double *sA = a.aPhi + d.off;   // stage A (entry k of node block t at k * TnAll + t)
         const bool skip = (a.mode == kModeEvolve) && (S.status != kRunning || S.step >= n_target);
         const int R = ea.order;
 
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                 uA[i] = Ai;   // the slice's A is the constraint solution
                                 if (k < P - 1) m = fma(al, m, be);
                             } else {
-                                Ai = (s == 0) ? __ldcg(uA + i) : __ldcg(sA + i);
+                                Ai = (s == 0) ? __ldcg(uA + i) : __ldcg(sA + k * TnAll + bs + tid);
                             }
                             const double Fi = FIXED ? 1.0 : a_exp_neg_scaled(Ai, De[k], s_tab);
                             const double gi = FIXED ? ph : Fi * ph;
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                 const double dA = gK2[k] * Ai * gi * pi;
                                 const double An = (s == 0) ? fma(dt, dA, Ai)
                                                            : fma(wb, fma(dt, dA, Ai), wa * __ldcg(uA + i));
-                                if (s < R - 1) sA[i] = An;
+                                if (s < R - 1) sA[k * TnAll + bs + tid] = An;
                                 else uA[i] = An;
                             }
                             if (s == 0) {
