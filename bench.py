@@ -58,7 +58,7 @@ SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A
 # the evolution kernel (evolve_kernel<8, 128, 4, true> over the whole window) and the adjoint
 # kernel's backward sweep (phase B, per segment), from the ncu capture in
 # profiles/adjoint_kernel_adjoint_batch.md; used only while the kernel sources are unchanged
-ADJ_ISSUE = {"sha256": "119fd096e22b9e1b7254041df54a75f048c6967d5a6b1ca32e3683d3f5c869e6",
+ADJ_ISSUE = {"sha256": "2a78f315725ae6ad25e3d55446134c234e6559d2b5b8fbf75ac9b2aa54b3e6b1",
              "forward_record": 75931385856 / 1074003968,
              "phase_B": (9518514176 + 10991304704 + 8170766336) / 268500992}
 L2_FLUSH_BYTES = 512 << 20
@@ -67,8 +67,8 @@ REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
 # DRAM bytes (read + write) of one timed evolve_kernel launch of the amplitude scan, from an ncu
 # capture of this script (profiles/evolve_kernel_amp_scan.md); reported only while the kernel
 # source and the kernel shape are the ones the counters were taken on.
-TRAFFIC = {"kernel_sha256": "caeb3f4fd82fb920132ccfd41d5a040a40f65d23136cdfbd7b986e865f0f088a",
-           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17203200 + 233953280,
+TRAFFIC = {"kernel_sha256": "691f6b869ec61cd877426dfe56545a11941d7dd356f5f956b3a6ba1fa63b221c",
+           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17722368 + 67019776,
            # FP64 instructions (DADD + DMUL + DFMA, thread level) per point-substep, same capture
            "fp64_instr_per_point_substep": (23334264832 + 13958131712 + 38349320192) / 1074003968}
 
