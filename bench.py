@@ -343,8 +343,10 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "amplitude scan, B=256 Gaussian pulses, N=4097, sigma=1/16, "
-                               "eps log-uniform [5,80], theta=2^-7 (bounded sample)",
+        "config": {"workload": workload_insts("amp_scan", 0)[1],
+                   "step": f"bounded sample of the same workload: {len(insts)} of the pulses x "
+                           f"{nsteps} RK4 steps per bench step",
+                   "scheme": "rk4",
                    "oracle": "sequential FP64 C, one instance per host thread"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
