@@ -109,14 +109,14 @@ int32_t adscl_max_points(void);
 adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out);
 
 /* Set the initial slice t = 0 of every instance from packed Phi(x,0), Pi(x,0) and solve the
- * constraints (eq:aprime), (eq:delta) for A and delta on it (Sec. II: "one must define Phi(x,0)
- * and Pi(x,0) and solve ...").  The boundary values Phi(0) = Phi(pi/2) = Pi(pi/2) = 0 are
+ * constraints (eq:aprime), (eq:delta) for A and delta on it (Sec. II: initial data are the two
+ * scalar-field functions, the metric functions follow from the constraints).  The boundary values Phi(0) = Phi(pi/2) = Pi(pi/2) = 0 are
  * imposed.  Resets every instance to step 0 with status RUNNING (or COLLAPSED at t = 0 if
  * min A already lies below the threshold).  ADSCL_ENONFINITE if an input is NaN/Inf. */
 adscl_status adscl_set_initial(adscl_ctx *ctx, const double *Phi, const double *Pi, int ptr_is_device);
 
 /* Same, with Phi(x,0) = 0 and Pi(x,0) = sum_{j<K} a_j e_j(x), e_j the AdS4 normal modes
- * (Sec. II, "We can use these normal modes to define initial data").  a: B x K row-major,
+ * (Sec. II builds initial data from sums of these modes).  a: B x K row-major,
  * K <= 64. */
 adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *a, int32_t K, int ptr_is_device);
 
@@ -134,8 +134,8 @@ adscl_status adscl_set_initial_modes(adscl_ctx *ctx, const double *a, int32_t K,
 adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, double *t_collapse,
                           double *mass, int32_t *inst_status, int ptr_is_device);
 
-/* Mode-energy spectrum of every instance's current slice (Sec. II: "the current numerical
- * solution can be decomposed into a spectrum of normal modes"): E_j = Pi_j^2 + Phi_j^2/omega_j^2,
+/* Mode-energy spectrum of every instance's current slice (Sec. II: the evolving solution is
+ * projected onto the normal modes to follow the energy in each): E_j = Pi_j^2 + Phi_j^2/omega_j^2,
  * Pi_j = (sqrt(A) Pi, e_j), Phi_j = (sqrt(A) Phi, e_j'), (u, w) = int_0^{pi/2} u w tan^2 x dx by
  * the trapezoid rule on the grid, e_j the AdS4 normal modes (omega_j = 3 + 2j), j < J <= 64.
  * Output E: B x J row-major.  A is recomputed from the current slice (no state change).

@@ -1,6 +1,6 @@
 // spectrum.cuh -- AdS4 normal modes on the grid: mode-sum initial data and the mode-energy
-// spectrum E_j = Pi_j^2 + Phi_j^2 / omega_j^2 of arXiv:1706.07413, Sec. II ("At any given time,
-// the current numerical solution can be decomposed into a spectrum of normal modes").
+// spectrum E_j = Pi_j^2 + Phi_j^2 / omega_j^2 of arXiv:1706.07413, Sec. II (the solution at
+// any time is projected onto the normal modes).
 //
 // Normal modes (the paper gives no formula; standard for a massless scalar on AdS4):
 //   e_j(x) = cos^3 x q_j(cos 2x),  omega_j = 3 + 2j,  int_0^{pi/2} e_i e_j tan^2 x dx = delta_ij,
