@@ -153,7 +153,8 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
  * Pi(x,0) = sum_{k<K} a_k e_k(x), Phi(x,0) = 0 (a: B x K row-major, K <= 64),
  *   J = sum_{j<spec_J} (E_j(T) - E_j(0))^2,
  * evolved without the collapse stop for n = ceil(T/dt) RK4 steps (the same n for every
- * instance, N <= 4097).  Outputs J_out (B) and dJda (B x K).  The steps are cut into segments of
+ * instance; N <= 8193, above 4097 on 2-CTA clusters of the adjoint kernel, so adjoint_ctas
+ * must then be 0 or 2).  Outputs J_out (B) and dJda (B x K).  The steps are cut into segments of
  * ckpt_every; every stage of a segment is stored in device memory (B * ckpt_every * 24 * N
  * doubles per segment) and swept backwards through the exact transpose of the discrete step
  * (constraint scans included).  When every segment's stages fit (adjoint_stage_buffers), the

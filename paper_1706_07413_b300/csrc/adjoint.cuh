@@ -5,9 +5,10 @@
 // initial data.
 //
 // Work unit: one instance and checkpoint segment, on CL = 1 CTA (512 threads, 8 nodes per
-// thread, the layout of evolve.cuh) or on a CL = 2 thread-block cluster whose two CTAs own the
-// two halves of the node blocks with 4 nodes per thread, so that all 2 x 512 threads carry nodes
-// at N = 4097 (for batches smaller than the SM count: each instance then occupies two SMs).
+// thread, the layout of evolve.cuh; N <= 4097) or on a CL = 2 thread-block cluster whose two
+// CTAs own the two halves of the node blocks: 4 nodes per thread for N <= 4097, so that all
+// 2 x 512 threads carry nodes (batches smaller than the SM count: each instance then occupies
+// two SMs), 8 nodes per thread for 4097 < N <= 8193.
 //   Phase F: from the segment's first slice, recompute its steps with the same discrete map as
 //     evolve.cuh (affine-map scan for m, suffix sum for delta, table-driven exp) and store, for
 //     every stage of every step, the stage input (Phi, Pi) and the stage's m, e^{-delta}, F and
@@ -36,7 +37,7 @@
 
 namespace adscl {
 
-constexpr int kAP = 8;          // nodes per thread of a single-CTA instance (kAP / CL on a CL-CTA cluster)
+constexpr int kAP = 8;          // nodes per thread of a single-CTA instance
 constexpr int kANT = 512;       // threads per CTA
 constexpr int kANW = kANT / 32;
 // kStageArrays (evolve.cuh): stored per stage: yP, yQ, M, E, F, AL
@@ -95,15 +96,14 @@ struct ScanShared {
 };
 
 // node ownership of this thread for grid size N: rank r of a CL-CTA cluster owns node blocks
-// ceil(r T / CL) .. ceil((r+1) T / CL) - 1 of the T blocks of kAP / CL nodes
+// ceil(r T / CL) .. ceil((r+1) T / CL) - 1 of the T blocks of AP nodes
 struct Own {
     int T, i0;
     bool act, last;
 };
-template <int CL>
+template <int CL, int AP>
 __device__ __forceinline__ Own own_of(int N)
 {
-    constexpr int AP = kAP / CL;
     Own o;
     o.T = (N - 1) / AP;
     const int rank = (CL > 1) ? cluster_rank() : 0;
@@ -447,14 +447,13 @@ __device__ __forceinline__ Scr scratch_of(double *base, int Nmax)
 // Constraint solve on the stage slice (yP, yQ) (node N-1 and all nodes written, zero at N-1);
 // stores M, E = e^{-delta}, F = A E on nodes and AL = alpha on cells; computes the fluxes into
 // scr.f, scr.u and, if kP != nullptr, the stage derivative (kP, kQ) on the thread's nodes.
-template <int CL>
+template <int CL, int AP>
 __device__ void stage_forward(const double *yP, const double *yQ, double *M, double *E, double *F, double *AL,
                               const Scr &scr, double *kP, double *kQ, const InstDesc &d, const GeoTab &g,
                               const double *tab, ScanShared &sh, bool with_rhs)
 {
-    constexpr int AP = kAP / CL;
     const int N = d.N;
-    const Own o = own_of<CL>(N);
+    const Own o = own_of<CL, AP>(N);
     const bool act = o.act, last = o.last;
     const int i0 = o.i0;
     double De[AP], al[AP], be[AP];
@@ -535,14 +534,13 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
 // ------------------------------------------------------------------ constraint transpose
 // Given Abar-derived mbar (scr.mb, nodes) and delta_bar (scr.dlb, nodes), accumulate into
 // (yb P, yb Q) += d/d(yP, yQ) on the thread's nodes.
-template <int CL>
+template <int CL, int AP>
 __device__ void constraint_backward(const double *yP, const double *yQ, const double *M, const double *AL,
                                     const Scr &scr, double *ybP, double *ybQ, const InstDesc &d,
                                     const GeoTab &g, ScanShared &sh)
 {
-    constexpr int AP = kAP / CL;
     const int N = d.N;
-    const Own o = own_of<CL>(N);
+    const Own o = own_of<CL, AP>(N);
     const bool act = o.act;
     const int i0 = o.i0;
     // mu_c = alpha_c mu_{c+1} + mbar_c, mu_{N-1} = 0: suffix affine scan
@@ -622,14 +620,13 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
 // ybar = R'(y)^T kbar with kbar in (scr.vP, scr.vQ) (already restricted to rows, and scaled by
 // c12 = 1/(12 h) and cq, the factors of Phi-dot and Pi-dot), written to (ybP, ybQ) (overwritten)
 // on the thread's nodes.
-template <int CL>
+template <int CL, int AP>
 __device__ void stage_backward(const double *yP, const double *yQ, const double *M, const double *E,
                                const double *F, const double *AL, const Scr &scr, double *ybP, double *ybQ,
                                const InstDesc &d, const GeoTab &g, ScanShared &sh)
 {
-    constexpr int AP = kAP / CL;
     const int N = d.N;
-    const Own o = own_of<CL>(N);
+    const Own o = own_of<CL, AP>(N);
     const bool act = o.act, last = o.last;
     const int i0 = o.i0;
     const double *vP = scr.vP, *vQ = scr.vQ;
@@ -680,14 +677,15 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
     }
     // no barrier: the constraint transpose reads only this thread's mb, dlb before its scans'
     // barriers, and vP, vQ, v2 are written again only after the next stage's first barrier
-    constraint_backward<CL>(yP, yQ, M, AL, scr, ybP, ybQ, d, g, sh);
+    constraint_backward<CL, AP>(yP, yQ, M, AL, scr, ybP, ybQ, d, g, sh);
 }
 
 // ------------------------------------------------------------------ the kernel
-template <int CL>
+// AP nodes per thread: (CL, AP) = (1, 8) and (2, 4) for N <= 4097 (on a 2-CTA cluster every
+// thread of both CTAs carries nodes), (2, 8) for N <= 8193
+template <int CL, int AP>
 __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
 {
-    constexpr int AP = kAP / CL;   // nodes per thread: a 2-CTA cluster keeps all 2 x 512 threads busy at N <= 4097
     static_assert(CL == 1 || CL == 2, "one CTA or a 2-CTA cluster per instance");
     __shared__ ScanShared sh;
     __shared__ double s_tab[kExpTableSize];
@@ -715,7 +713,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
         const InstDesc d = a.desc[b];
         const GeoTab g = a.geo[d.geo];
         const int N = d.N;
-        const Own own = own_of<CL>(N);
+        const Own own = own_of<CL, AP>(N);
         const bool act = own.act;
         const int i0 = own.i0;
         double *lamP = a.lamP + d.off, *lamQ = a.lamQ + d.off;
@@ -752,7 +750,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                 if (own.last) { yP[N - 1] = 0.0; yQ[N - 1] = 0.0; }
             }
             csync<CL>();
-            stage_forward<CL>(yP, yQ, M, E, F, AL, scr, nullptr, nullptr, d, g, s_tab, sh, false);
+            stage_forward<CL, AP>(yP, yQ, M, E, F, AL, scr, nullptr, nullptr, d, g, s_tab, sh, false);
             // A = F / E on interior nodes; weights h tan^2 sqrt(A); projections per mode (rank 0)
             const EigTab t = a.eig[d.geo];
             const double h = 1.0 / (12.0 * d.c12);
@@ -802,7 +800,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                 if (own.last) { scr.mb[N - 1] = 0.0; scr.dlb[N - 1] = 0.0; }
             }
             csync<CL>();
-            constraint_backward<CL>(yP, yQ, M, AL, scr, scr.ybP, scr.ybQ, d, g, sh);
+            constraint_backward<CL, AP>(yP, yQ, M, AL, scr, scr.ybP, scr.ybQ, d, g, sh);
             if (act) {
 #pragma unroll
                 for (int k = 0; k < AP; ++k) {
@@ -832,7 +830,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                 if (act && own.last) { yP[N - 1] = 0.0; yQ[N - 1] = 0.0; }
                 csync<CL>();
                 double *kP = scr.vP, *kQ = scr.vQ;   // stage derivative (phase F use of the slots)
-                stage_forward<CL>(yP, yQ, slot(n, s, 2), slot(n, s, 3), slot(n, s, 4), slot(n, s, 5), scr, kP, kQ,
+                stage_forward<CL, AP>(yP, yQ, slot(n, s, 2), slot(n, s, 3), slot(n, s, 4), slot(n, s, 5), scr, kP, kQ,
                               d, g, s_tab, sh, true);
                 if (act) {
 #pragma unroll
@@ -894,7 +892,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                     if (own.last) { scr.vP[N - 1] = 0.0; scr.vQ[N - 1] = 0.0; scr.v2[N - 1] = 0.0; }
                 }
                 csync<CL>();
-                stage_backward<CL>(slot(n, s, 0), slot(n, s, 1), slot(n, s, 2), slot(n, s, 3), slot(n, s, 4),
+                stage_backward<CL, AP>(slot(n, s, 0), slot(n, s, 1), slot(n, s, 2), slot(n, s, 3), slot(n, s, 4),
                                slot(n, s, 5), scr, scr.ybP, scr.ybQ, d, g, sh);
                 if (act) {
 #pragma unroll

@@ -75,6 +75,7 @@ struct adscl_ctx {
     double t_prev = 0.0;               // t_end of the last evolve call since the initial data
     int scheme = 0, reint = 0;         // ADSCL_SCHEME_*, A re-integration interval (evolved A)
     int adj_cl = 1;                    // CTAs per instance of the adjoint kernel
+    bool adj_wide = false;             // 8 nodes per thread on the 2-CTA cluster (N > 4097)
     // stage record of the evolution kernel (set by adscl_grad around its forward pass)
     double *rec_stage = nullptr;
     long long rec_seg_stride = 0, rec_steps = 0;
@@ -1131,9 +1132,10 @@ adscl_status launch_adjoint(adscl_ctx *ctx, AdjArgs &a, cudaStream_t sm, int lan
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        CK(cudaLaunchKernelEx(&cfg, adjoint_kernel<2>, a));
+        if (ctx->adj_wide) CK(cudaLaunchKernelEx(&cfg, adjoint_kernel<2, 8>, a));
+        else CK(cudaLaunchKernelEx(&cfg, adjoint_kernel<2, 4>, a));
     } else {
-        adjoint_kernel<1><<<units, kANT, 0, sm>>>(a);
+        adjoint_kernel<1, 8><<<units, kANT, 0, sm>>>(a);
         CK(cudaGetLastError());
     }
     ctx->launches += 1;
@@ -1151,11 +1153,21 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         return fail(ctx, ADSCL_EINVAL, "bad grad arguments");
     if (ctx->scheme != ADSCL_SCHEME_RK4)
         return fail(ctx, ADSCL_EUNSUPPORTED, "grad differentiates the classic RK4 scheme only");
-    for (int n : ctx->N)
-        if ((n - 1) / kAP > kANT) return fail(ctx, ADSCL_EUNSUPPORTED, "grad supports N <= %d", kAP * kANT + 1);
+    // N <= 4097: one CTA (8 nodes per thread) or a 2-CTA cluster (4 nodes per thread) per
+    // instance; 4097 < N <= 8193: a 2-CTA cluster with 8 nodes per thread
+    bool wide = false;
+    for (int n : ctx->N) {
+        if ((n - 1) / kAP > 2 * kANT)
+            return fail(ctx, ADSCL_EUNSUPPORTED, "grad supports N <= %d", 2 * kAP * kANT + 1);
+        if ((n - 1) / kAP > kANT) wide = true;
+    }
+    if (wide && ctx->adj_cl == 1)
+        return fail(ctx, ADSCL_EUNSUPPORTED, "grad at N > %d needs adjoint_ctas = 2 (or 0)", kAP * kANT + 1);
+    if (wide != ctx->adj_wide) ctx->adj_units = 0;
+    ctx->adj_wide = wide;
     const int B = ctx->B, Jm = ctx->spec_J, seg = ctx->ckpt;
     if (ctx->adj_units == 0) {   // CTAs per instance and co-resident units of the adjoint kernel
-        if (ctx->adj_cl == 0) ctx->adj_cl = (2 * B <= ctx->num_sms) ? 2 : 1;
+        if (ctx->adj_cl == 0 || wide) ctx->adj_cl = (wide || 2 * B <= ctx->num_sms) ? 2 : 1;
         if (ctx->adj_cl == 2) {
             cudaLaunchConfig_t cfg{};
             cfg.gridDim = dim3(2 * (ctx->num_sms / 2), 1, 1);
@@ -1168,8 +1180,11 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int nc = 0;
-            if (cudaOccupancyMaxActiveClusters(&nc, adjoint_kernel<2>, &cfg) != cudaSuccess || nc < 1) {
+            const cudaError_t eo = wide ? cudaOccupancyMaxActiveClusters(&nc, adjoint_kernel<2, 8>, &cfg)
+                                        : cudaOccupancyMaxActiveClusters(&nc, adjoint_kernel<2, 4>, &cfg);
+            if (eo != cudaSuccess || nc < 1) {
                 (void)cudaGetLastError();
+                if (wide) return fail(ctx, ADSCL_ECUDA, "no 2-CTA cluster of the adjoint kernel fits");
                 ctx->adj_cl = 1;
             } else {
                 ctx->adj_units = nc;

@@ -188,3 +188,41 @@ def test_grad_without_dissipation_matches_oracle(ad, orc, ctas):
         Jo, go = orc.grad(a[b], N, n, dt[0], sigma=0.0, Jm=Jm)
         assert abs(J[b] - Jo) <= 1e-10 * abs(Jo)
         assert np.abs(g[b] - go).max() <= 1e-9 * np.abs(go).max()
+
+
+def test_grad_at_8193_points_matches_oracle(ad, orc):
+    """N = 8193 (the large-grid configuration): the adjoint kernel runs each instance on a 2-CTA
+    cluster with 8 nodes per thread."""
+    # 200 steps (t = 0.019): long enough that J = sum (E_j(T) - E_j(0))^2 is not dominated by
+    # the cancellation in E_j(T) - E_j(0)
+    N, B, K, Jm, n = 8193, 2, 6, 8, 200
+    rng = np.random.default_rng(51)
+    a = rng.uniform(0.0, 0.8, (B, K)) * np.exp(-np.arange(K) / 2.0)
+    s = ad.Solver([N] * B, ko_sigma=0.5, spec_J=Jm, ckpt_every=64)
+    dt, _ = s.clock()
+    J, g = s.grad(a, n * dt[0])
+    for b in range(B):
+        Jo, go = orc.grad(a[b], N, n, dt[0], sigma=0.5, Jm=Jm)
+        assert abs(J[b] - Jo) <= 1e-10 * abs(Jo)
+        assert np.abs(g[b] - go).max() <= 1e-9 * np.abs(go).max()
+    s.close()
+    s1 = ad.Solver([N], ko_sigma=0.5, spec_J=Jm, adjoint_ctas=1)
+    with pytest.raises(ad.AdsclError) as e:
+        s1.grad(a[:1], n * dt[0])
+    assert e.value.status == ad.ADSCL_EUNSUPPORTED
+
+
+def test_qp_seed_refinement_at_8193_points(ad):
+    """The large-grid configuration's refinement: the 8 approximate quasi-periodic seeds at
+    N = 8193, a few adjoint-driven steps lower every seed's spectral drift."""
+    from paper_1706_07413_b300 import workloads as W
+    from paper_1706_07413_b300.autograd import refine_modes
+    N, K = 8193, 32
+    seeds = W.qp_seeds(N=N, K=K)
+    a0 = np.stack([it.coeffs for it in seeds])
+    s = ad.Solver([N] * len(seeds), ko_sigma=0.5, spec_J=32, ckpt_every=64)
+    dt, _ = s.clock()
+    a, hist = refine_modes(s, a0, 128 * dt[0], iters=3, step=0.02)
+    h = hist.numpy()
+    assert np.all(np.diff(h, axis=0) <= 0.0)
+    assert np.all(h[-1] < h[0])
