@@ -75,13 +75,14 @@ def test_paper_temperatures_through_the_gpu_path(ad):
 @pytest.mark.parametrize("prec,bound", [("BF16X3", 5e-5), ("TF32X3", 5e-5)])
 def test_tensor_core_spectrum_error_vs_fp64(ad, prec, bound):
     """Split-precision tensor-core projection (tcgen05, FP32 accumulation) against the FP64
-    projection on an uneven batch (three grid sizes, more than one 128-row tile for one of
-    them): max_j |E_j(TC) - E_j(FP64)| / M stays below the stated bound (measured on B300:
+    projection on an uneven batch (five grid sizes up to 8193, more than one 128-row tile for
+    one of them): max_j |E_j(TC) - E_j(FP64)| / M stays below the stated bound (measured on B300:
     BF16X3 1.1e-5, TF32X3 2.3e-5; medians 1.4e-6 and 2.9e-6 -- the FP32 accumulation over ~N
     terms dominates the operand-split error).  Small E_j (<< M) are not relatively accurate at
     this precision."""
     rng = np.random.default_rng(9)
-    Ns = [257] * 140 + [1025] * 5 + [2049] * 5   # N = 257 needs two 128-row tiles
+    # N = 257 needs two 128-row tiles; the other sizes are those of the uneven configuration
+    Ns = [257] * 140 + [1025] * 5 + [2049] * 5 + [4097] * 2 + [8193] * 2
     a = np.zeros((len(Ns), 16))
     j = np.arange(16)
     for b in range(len(Ns)):
