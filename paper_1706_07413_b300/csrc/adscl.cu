@@ -1321,6 +1321,12 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     // the forward pass's own last segment: both start from the last checkpoint.
     const double theta = ctx->theta;
     ctx->theta = -INFINITY;
+    // the collapse threshold and the stage-record pointer come back on every exit from here on
+    struct Restore {
+        adscl_ctx *c;
+        double th;
+        ~Restore() { c->theta = th; c->rec_stage = nullptr; }
+    } restore_theta{ctx, theta};
     s = adscl_set_initial_modes(ctx, a, K, ptr_is_device);
     if (s == ADSCL_OK) s = adscl_spectrum(ctx, Jm, ADSCL_PREC_FP64, E0, 1);
     if (rec_evolve && s == ADSCL_OK) {
