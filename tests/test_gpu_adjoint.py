@@ -162,7 +162,10 @@ def test_recording_forward_pass_for_batches_filling_the_gpu(ad, orc, extra):
             ref.evolve(n * dt[0])
             for k, b in enumerate((0, B - 1)):
                 x, y = s.get_state(b), ref.get_state(k)
-                assert np.abs(x[0] - y[0]).max() < 1e-13 and np.abs(x[1] - y[1]).max() < 1e-13
+                if extra == 5:   # same shape: the recording variant does the same arithmetic
+                    assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+                else:            # recorded on 4-CTA clusters: the scans associate differently
+                    assert np.abs(x[0] - y[0]).max() < 1e-13 and np.abs(x[1] - y[1]).max() < 1e-13
             ref.close()
         s.close()
     (J0, g0), (J1, g1) = out[0], out[1]
