@@ -320,6 +320,62 @@ def paper_configs_report(stream, local, steps=64):
     return out
 
 
+def run_full_job(args, sol, insts, wl_desc, stages, shapes, stream, ws, rank, dist):
+    """The whole job: every instance from t = 0 to args.full_job (or its collapse) in evolve
+    calls of one time unit; wall time on the host clock, device-resident fields.  Unless the
+    shapes are pinned, autotune is called after every unit of t: its choice is cached per
+    number of running instances (a power-of-two bucket), so it re-tunes only when collapses
+    have thinned the batch enough (the time of those tunings is part of the job)."""
+    import torch
+    B = len(insts)
+    T = args.full_job
+    outs = [torch.empty(B, dtype=torch.float64, device="cuda") for _ in range(3)] + \
+        [torch.empty(B, dtype=torch.int32, device="cuda")]
+    Ns = sol.N.astype(np.float64)
+    _, s0 = sol.clock()
+    running = []
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    t = 0.0
+    retune = not (args.no_autotune or args.shape)
+    tunes = []
+    with torch.cuda.stream(stream):
+        while t < T - 1e-12:
+            t = min(T, t + 1.0)
+            sol.evolve(t, out=outs)
+            if retune:
+                before = sol.shapes()
+                sol.autotune(8)
+                after = sol.shapes()
+                if after != before:
+                    tunes.append({"t": t, "shapes": {str(k): list(v) for k, v in after.items()}})
+            # instances still evolving (RUNNING or DONE at this t), sampled every 10 units of t
+            running.append(int((outs[3] <= 1).sum().item()) if int(t) % 10 == 0 or t >= T else None)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    _, s1 = sol.clock()
+    work = float(np.sum((s1 - s0) * Ns * stages))
+    st = outs[3].cpu().numpy()
+    collapsed = int(np.sum(st == 2))
+    if dist is not None:
+        from paper_1706_07413_b300 import shard
+        wall, work = shard.reduce_timing(wall, work, dist, device="cuda")
+        c = torch.tensor([collapsed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(c)
+        collapsed = int(c.item())
+    if rank == 0:
+        line = {"mode": "full_job", "workload": wl_desc, "t_end": T, "instances": B * ws,
+                "n_gpus": ws, "wall_s": wall, "point_substeps": work,
+                "point_substeps_per_s": work / wall, "collapsed": collapsed,
+                "running_every_10": [r for r in running if r is not None],
+                "shape_changes": tunes,
+                "kernel_shape_P_NT_CL": {str(k): list(v) for k, v in shapes.items()},
+                "note": "wall time on the host clock around all evolve calls (one per unit of t)"}
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The reference arm: the sequential FP64 CPU oracle on the host cores."""
     ws, rank, _ = _dist()
@@ -374,6 +430,10 @@ def main():
                     help="batch to time (the metric's workload is amp_scan)")
     ap.add_argument("--scheme", default="rk4", choices=sorted(SCHEMES),
                     help="time-stepping scheme (the metric's scheme is rk4)")
+    ap.add_argument("--full-job", type=float, default=0.0, metavar="T",
+                    help="instead of the bench line: evolve the whole workload to t = T (every "
+                         "instance runs until T or its collapse) and print the job's wall time, "
+                         "throughput and collapse count as one JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -411,6 +471,11 @@ def main():
             sol.set_shape(n, *fixed_shape)
     shapes = sol.shapes() if (args.no_autotune or fixed_shape) else sol.autotune(8)
     tune_s = time.perf_counter() - t0
+    if args.full_job > 0:
+        run_full_job(args, sol, insts, wl_desc, stages, shapes, stream, ws, rank, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     dt, _ = sol.clock()
     dstep = STEP_RK * float(dt.max())
     outs = [torch.empty(B, dtype=torch.float64, device="cuda") for _ in range(3)] + \

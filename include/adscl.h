@@ -182,14 +182,18 @@ adscl_status adscl_get_clock(adscl_ctx *ctx, double *dt, int64_t *step);
 /* Autotuner (classic RK4 scheme): for every grid size N of the context, time each kernel shape
  * that fits N -- P grid nodes per thread, NT threads per CTA (so 512 / NT CTAs per SM), CL CTAs
  * (a thread-block cluster) per instance -- on the context's own instances of that N for
- * trial_steps RK4 steps (0 = 8) from their current slices, keep the fastest, and restore the
+ * max(trial_steps, 4 chunk_steps) RK4 steps (trial_steps 0 = 8; at least four scheduling
+ * chunks, so that the queue's load balancing shows) from their current slices, keep the fastest,
+ * and restore the
  * state (the call changes no instance's slice -- Phi, Pi and, under the evolved-A schemes, A --
  * step or status).  With one grid size the two fastest shapes are timed again over
- * max(4 trial_steps, 32) steps and the faster one is kept.  With several grid sizes, which run
+ * four times the trial length and the faster one is kept.  With several grid sizes, which run
  * concurrently in a batch, the per-size choice is kept only if the whole batch (timed over that
  * longer window) is more than 1 % faster with it than with the default shapes.  Results are
  * cached for the process by (GPU name, SM count, scheme, the batch's grid sizes with their
- * instance counts); a cached entry is reused without timing or touching the state.
+ * instance counts, and floor(log2) of the instances of each size still running): a cached entry
+ * is reused without timing or touching the state, and calling this again after collapses have
+ * thinned a batch re-tunes for the smaller number of running instances.
  * Synchronous.  The evolved-A and fixed-metric kernels are built for the shapes (8, 512, 1/2/4/8),
  * (8, 256, 2) and (8, 128, 2).
  * Different shapes associate the radial scans differently, so results agree with the default

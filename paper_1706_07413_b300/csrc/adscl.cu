@@ -45,7 +45,9 @@ int default_shape(int N) { return shape_index(kP, kNT, cluster_of(N)); }
 
 // autotuner results of this process: (device name, SM count, scheme, the batch's (N, instances
 // of that N) in decreasing N) -> shape of each of those N
-using TuneKey = std::tuple<std::string, int, int, std::vector<std::pair<int, int>>>;
+// (GPU name, SM count, scheme, (N, instances) of each size, log2 of the running instances of each
+// size: the best shape depends on how many instances are still evolving)
+using TuneKey = std::tuple<std::string, int, int, std::vector<std::pair<int, int>>, std::vector<int>>;
 std::map<TuneKey, std::vector<int>> g_tuned;
 std::mutex g_tuned_mu;
 static_assert(6 * field_stride<kP>(kMaxPoints1) * 8 + 4096 <= 232448, "shared memory budget");
@@ -1556,7 +1558,9 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
     adscl_status s = check_ctx(ctx);
     if (s != ADSCL_OK) return s;
     const bool ea_scheme = ctx->scheme != ADSCL_SCHEME_RK4;
-    const int trial = trial_steps > 0 ? trial_steps : 8;
+    // at least four scheduling chunks per trial: shorter trials miss the chunk-level load
+    // balancing of the persistent queue and mis-rank the shapes of a thinned batch
+    const int trial = std::max(trial_steps > 0 ? trial_steps : 8, 4 * ctx->chunk);
     const int B = ctx->B;
     const size_t fb = (size_t)ctx->total * sizeof(double);
     const std::vector<int32_t> &ord = ctx->h_order;
@@ -1574,9 +1578,23 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
     auto set_run = [&](int r, int id) {
         for (int q = run_start[r]; q < run_start[r + 1]; ++q) ctx->shape_of[ord[q]] = id;
     };
-    const TuneKey key{ctx->dev_name, ctx->num_sms, ctx->scheme, sig};
-    {   // a batch of this signature was tuned before in this process: apply its shapes (no device
-        // work, no allocation)
+    // running instances of each size (the statuses of the current slices)
+    std::vector<int> rbucket(nr, -1);
+    {
+        std::vector<InstState> stc(B);
+        CK(cudaMemcpyAsync(stc.data(), ctx->d_st, B * sizeof(InstState), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int r = 0; r < nr; ++r) {
+            int run = 0;
+            for (int q = run_start[r]; q < run_start[r + 1]; ++q) run += stc[ord[q]].status == kRunning;
+            int b = -1;
+            while (run > 0) { ++b; run >>= 1; }
+            rbucket[r] = b;
+        }
+    }
+    const TuneKey key{ctx->dev_name, ctx->num_sms, ctx->scheme, sig, rbucket};
+    {   // a batch of this signature (and running-instance bucket) was tuned before in this
+        // process: apply its shapes (no allocation, no timing, the state untouched)
         std::lock_guard<std::mutex> lk(g_tuned_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
