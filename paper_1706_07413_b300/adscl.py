@@ -288,7 +288,8 @@ class Solver:
     # -- kernel shapes and the autotuner
     def autotune(self, trial_steps=8):
         """Pick the fastest kernel shape for every grid size (state unchanged); returns
-        {N: (P, NT, CL)}."""
+        {N: (P, NT, CL)}.  Cached per batch signature and number of running instances: calling
+        it again after collapses have thinned the batch re-tunes (adscl_autotune)."""
         self._check(self.lib.adscl_autotune(self.ctx, int(trial_steps)))
         return self.shapes()
 
