@@ -130,3 +130,26 @@ def test_set_shape_rejects_what_does_not_fit(ad):
     assert s.shape(1) == (8, 512, 8)
     s.set_shape(129, 8, 128, 1)
     assert s.shape(1) == (8, 128, 1)
+
+
+def test_autotune_after_collapses_keeps_state(ad):
+    """A batch thinned by collapses (some instances stopped) is tuned again for the running ones
+    (the cache is keyed by their number); the call changes no slice, step or status."""
+    N, B = 1025, 24
+    amps = np.where(np.arange(B) % 2 == 0, 40.0, 5.0)   # the strong half collapses early
+    Pi = W.packed([W.gaussian_pi(N, e, 1.0 / 16) for e in amps])
+    s = ad.Solver([N] * B, collapse_threshold=2.0 ** -7)
+    s.set_initial(np.zeros_like(Pi), Pi)
+    s.autotune(trial_steps=4)
+    tr, tc, m, st = s.evolve(6.0)
+    assert np.sum(st == ad.COLLAPSED) >= B // 2 - 2 and np.sum(st == ad.DONE) >= B // 2 - 2
+    before = [s.get_state(b)[:2] for b in range(B)]
+    clk = s.clock()[1].copy()
+    s.autotune(trial_steps=4)
+    assert np.array_equal(clk, s.clock()[1])
+    for b in range(B):
+        x = s.get_state(b)
+        assert np.array_equal(before[b][0], x[0]) and np.array_equal(before[b][1], x[1])
+    tr2, tc2, m2, st2 = s.evolve(6.5)
+    assert np.array_equal(st2 == ad.COLLAPSED, st == ad.COLLAPSED)
+    assert np.array_equal(tc2[st == ad.COLLAPSED], tc[st == ad.COLLAPSED])
