@@ -430,6 +430,9 @@ def main():
                     help="batch to time (the metric's workload is amp_scan)")
     ap.add_argument("--scheme", default="rk4", choices=sorted(SCHEMES),
                     help="time-stepping scheme (the metric's scheme is rk4)")
+    ap.add_argument("--adjoint-steps", type=int, default=1024,
+                    help="RK4 steps of the adjoint/forward-ratio window (32768 = the adjoint "
+                         "batch's whole T = 2 pi)")
     ap.add_argument("--full-job", type=float, default=0.0, metavar="T",
                     help="instead of the bench line: evolve the whole workload to t = T (every "
                          "instance runs until T or its collapse) and print the job's wall time, "
@@ -587,7 +590,7 @@ def main():
     # the window length: both passes scale with the step count)
     adj = None
     if rank == 0 and amp and not args.no_adjoint:
-        ADJ_STEPS = 1024
+        ADJ_STEPS = args.adjoint_steps
         ainst = W.adjoint_batch()
         a = np.stack([it.coeffs for it in ainst])
         sa = adscl.Solver([ainst[0].N] * len(ainst), ko_sigma=SIGMA_KO, collapse_threshold=-1.0,

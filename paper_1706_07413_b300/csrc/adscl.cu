@@ -1218,15 +1218,19 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         const int want[3] = {(int)std::min<long long>(std::min<long long>(nseg, cap), 1 << 20), std::min(2, cap), 1};
         int have = (ctx->adj_stage_doubles >= stage_need) ? ctx->adj_stage_bufs : 0;
         for (int w : want) {
-            if (w < 1 || have >= w) break;
+            if (w < 1 || have >= w) break;   // what is allocated already serves
+            // a larger count only when it fits (counting the storage it would replace) with a
+            // tenth of the device to spare; the current storage is kept otherwise
+            size_t free_b = 0, total_b = 0;
+            CK(cudaMemGetInfo(&free_b, &total_b));
+            const double cur = (double)ctx->adj_stage_bufs * ctx->adj_stage_doubles * sizeof(double);
+            const double bytes = (double)w * stage_need * sizeof(double);
+            if (w > 1 && bytes > (double)free_b + cur - 0.1 * (double)total_b) continue;
             if (ctx->d_adj_stage) CK(cudaFree(ctx->d_adj_stage));
             ctx->d_adj_stage = nullptr;
             ctx->adj_stage_bufs = 0;
             ctx->adj_stage_doubles = 0;
-            size_t free_b = 0, total_b = 0;
-            CK(cudaMemGetInfo(&free_b, &total_b));
-            const double bytes = (double)w * stage_need * sizeof(double);
-            if (w > 1 && bytes > (double)free_b - 0.1 * (double)total_b) continue;
+            have = 0;
             if (cudaMalloc(&ctx->d_adj_stage, (size_t)w * stage_need * sizeof(double)) == cudaSuccess) {
                 ctx->adj_stage_bufs = w;
                 ctx->adj_stage_doubles = stage_need;
