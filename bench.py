@@ -627,6 +627,9 @@ def main():
         sa.grad(a, Ta)
         torch.cuda.synchronize()
         t_adj_t = time.perf_counter() - t0
+        # stage storage of the whole window (6 arrays of N doubles per stage) against the device
+        stage_gb = len(ainst) * ADJ_STEPS * 4 * 6 * ainst[0].N * 8 / 1e9
+        dev_gb = torch.cuda.get_device_properties(local).total_memory / 1e9
         cpu_adj = None
         if ws == 1 and not args.no_cpu_baseline:
             # the oracle's own gradient / forward time ratio on a bounded sample of the same
@@ -659,8 +662,11 @@ def main():
                "workload": f"64 mode-sum instances, N=4097, {ADJ_STEPS} RK4 steps of dt=2pi/32768, "
                            "checkpoint every 256 steps, J = sum_{j<32}(E_j(T)-E_j(0))^2",
                "grad_includes": "E(0), the forward pass (storing every stage when all segments fit "
-                                "in device memory, as here; else checkpoints and a per-segment "
-                                "recompute), E(T), the backward sweep, the projection onto the modes"}
+                                "in device memory; else checkpoints, the last segment's stages and a "
+                                "recompute of each earlier segment beside the sweep of the next), E(T), "
+                                "the backward sweep, the projection onto the modes",
+               "stages_stored": ("all segments" if stage_gb < 0.85 * dev_gb else
+                                 "two segment buffers (recomputation)")}
         sa.close()
 
     # spectrum timing (current slices of the amplitude scan, 64 modes)

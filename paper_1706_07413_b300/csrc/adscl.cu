@@ -80,8 +80,11 @@ struct adscl_ctx {
     bool adj_wide = false;             // 8 nodes per thread on the 2-CTA cluster (N > 4097)
     // stage record of the evolution kernel (set by adscl_grad around its forward pass)
     double *rec_stage = nullptr;
-    long long rec_seg_stride = 0, rec_steps = 0;
+    long long rec_seg_stride = 0, rec_steps = 0, rec_seg0 = 0;
     int rec_seg = 1;
+    // recomputation state of adscl_grad's segment-wise modes (a second slice and its records)
+    double *d_rPhi = nullptr, *d_rPi = nullptr;
+    InstState *d_rSt = nullptr;
     int adj_bufs_cap = 0;              // most segment stage buffers the adjoint may hold (0: any)
     int adj_units = 0;                 // co-resident adjoint units (CTAs or 2-CTA clusters)
     double *d_A = nullptr;             // packed evolved A (evolved-A schemes)
@@ -338,6 +341,7 @@ adscl_status launch_evolve(adscl_ctx *ctx, int mode, double t_end, int first,
     if (mode == kModeEvolve && ctx->rec_stage) {
         a.stage = ctx->rec_stage;
         a.stage_seg_stride = ctx->rec_seg_stride;
+        a.stage_seg0 = ctx->rec_seg0;
         a.stage_steps = ctx->rec_steps;
         a.stage_seg = ctx->rec_seg;
         a.stage_nmax = ctx->Nmax;
@@ -1284,16 +1288,19 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     };
     const bool store_all = ctx->adj_stage_bufs >= nseg &&
                            (ctx->adj_bufs_cap == 0 || ctx->adj_bufs_cap >= nseg);
-    // With every stage stored, the forward pass is the evolution kernel recording its stages when
-    // its shapes spread the batch over the whole GPU (at least one CTA per SM).  A batch whose
-    // shapes give fewer CTAs than SMs (a small batch on the default one-CTA shapes) runs that
-    // pass on the same thread layout split over a cluster of 2 or 4 CTAs (P = 8, NT * CL = 512),
-    // the largest that keeps the batch within two CTAs per SM; the context's shapes are restored
-    // afterwards.  Otherwise the adjoint kernel's own recomputation records the stages.
+    // The stages are recorded by the evolution kernel itself when its shapes spread the batch
+    // over the whole GPU (at least one CTA per SM).  A batch whose shapes give fewer CTAs than
+    // SMs (a small batch on the default one-CTA shapes) runs the forward pass and the
+    // recomputations on the same thread layout split over a cluster of 2 or 4 CTAs (P = 8,
+    // NT * CL = 512), the largest that keeps the batch within two CTAs per SM; the context's
+    // shapes are restored afterwards.  With every stage stored, the forward pass records them
+    // all; otherwise it records the last segment, and each earlier segment is recomputed from its
+    // checkpoint on a second slice (the context's slice stays at step nT).  A batch that fills
+    // neither way records its stages in the adjoint kernel's own recomputation (phase F).
     long long evo_ctas = 0;
     for (int b = 0; b < B; ++b) evo_ctas += kShapes[ctx->shape_of[b]].CL;
     std::vector<int> rec_shape = ctx->shape_of;
-    if (store_all && evo_ctas < ctx->num_sms) {
+    if (evo_ctas < ctx->num_sms) {
         evo_ctas = 0;
         for (int b = 0; b < B; ++b) {
             const int cur = ctx->shape_of[b];
@@ -1311,6 +1318,12 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         }
     }
     const bool rec_evolve = store_all && evo_ctas >= ctx->num_sms;
+    const bool rec_recompute = !store_all && evo_ctas >= ctx->num_sms;
+    if (rec_recompute && !ctx->d_rSt) {
+        CK(cudaMalloc(&ctx->d_rPhi, total * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_rPi, total * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_rSt, (size_t)B * sizeof(InstState)));
+    }
     const bool piped = !store_all && ctx->adj_stage_bufs >= 2 && ctx->adj_bufs_cap != 1 && nseg > 1;
     if (piped && !ctx->adj_aux) {
         CK(cudaStreamCreateWithFlags(&ctx->adj_aux, cudaStreamNonBlocking));
@@ -1322,17 +1335,60 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     }
     const int klast = (int)((nseg - 1) & 1);
 
-    // forward: initial data, E(0), checkpoints every `seg` steps, E(T); no collapse stop.  With
-    // two stage buffers the recomputation of the last segment (phase F, side stream) runs beside
-    // the forward pass's own last segment: both start from the last checkpoint.
+    // forward: initial data, E(0), checkpoints every `seg` steps, E(T); no collapse stop.  When
+    // the evolution kernel records, the forward pass's own last segment fills that segment's
+    // buffer; otherwise, with two stage buffers, phase F of the last segment (side stream) runs
+    // beside the forward pass's last segment: both start from the last checkpoint.
     const double theta = ctx->theta;
     ctx->theta = -INFINITY;
     // the collapse threshold and the stage-record pointer come back on every exit from here on
     struct Restore {
         adscl_ctx *c;
         double th;
-        ~Restore() { c->theta = th; c->rec_stage = nullptr; }
-    } restore_theta{ctx, theta};
+        std::vector<int> *shapes;   // non-null while the recording shapes are swapped in
+        ~Restore()
+        {
+            c->theta = th;
+            c->rec_stage = nullptr;
+            c->rec_seg0 = 0;
+            if (shapes) std::swap(c->shape_of, *shapes);
+        }
+    } restore_theta{ctx, theta, nullptr};
+    // recomputation of segment g from its checkpoint on the second slice, recording its stages
+    // into stage buffer k, on stream sm; the slice, state and shapes are swapped back before
+    // returning
+    auto recompute = [&](long long g, int k, cudaStream_t sm) -> adscl_status {
+        const double *ck = ctx->d_ck + (size_t)g * 2 * total;
+        CK(cudaMemcpyAsync(ctx->d_rPhi, ck, total * sizeof(double), cudaMemcpyDeviceToDevice, sm));
+        CK(cudaMemcpyAsync(ctx->d_rPi, ck + total, total * sizeof(double), cudaMemcpyDeviceToDevice, sm));
+        CK(cudaMemcpyAsync(ctx->d_rSt, ctx->d_st, (size_t)B * sizeof(InstState), cudaMemcpyDeviceToDevice, sm));
+        set_step_kernel<<<(B + 127) / 128, 128, 0, sm>>>(ctx->d_rSt, B, g * seg);
+        CK(cudaGetLastError());
+        const double th = ctx->theta, tp = ctx->t_prev, dt0 = ctx->h_desc[0].dt;
+        const long long n1 = std::min(nT, (g + 1) * seg);
+        std::swap(ctx->d_Phi, ctx->d_rPhi);
+        std::swap(ctx->d_Pi, ctx->d_rPi);
+        std::swap(ctx->d_st, ctx->d_rSt);
+        std::swap(ctx->shape_of, rec_shape);
+        ctx->theta = -INFINITY;
+        ctx->t_prev = (double)(g * seg) * dt0;
+        ctx->rec_stage = ctx->d_adj_stage + (size_t)k * stN;
+        ctx->rec_seg_stride = (long long)stN;
+        ctx->rec_seg0 = g;
+        ctx->rec_steps = n1;
+        ctx->rec_seg = seg;
+        const adscl_status r = launch_evolve(ctx, kModeEvolve, (double)n1 * dt0, 0, ctx->h_order.data(), B,
+                                             nullptr, nullptr, sm);
+        ctx->rec_stage = nullptr;
+        ctx->rec_seg0 = 0;
+        ctx->theta = th;
+        ctx->t_prev = tp;
+        std::swap(ctx->shape_of, rec_shape);
+        std::swap(ctx->d_st, ctx->d_rSt);
+        std::swap(ctx->d_Pi, ctx->d_rPi);
+        std::swap(ctx->d_Phi, ctx->d_rPhi);
+        return r;
+    };
     s = adscl_set_initial_modes(ctx, a, K, ptr_is_device);
     if (s == ADSCL_OK) s = adscl_spectrum(ctx, Jm, ADSCL_PREC_FP64, E0, 1);
     if (rec_evolve && s == ADSCL_OK) {
@@ -1370,11 +1426,21 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
             s = launch_evolve(ctx, kModeInit, 0.0, 0, ctx->h_order.data(), ctx->B, nullptr, nullptr, ctx->stream);
         }
     }
+    if (rec_recompute && s == ADSCL_OK) {   // the forward pass runs on the recording shapes
+        std::swap(ctx->shape_of, rec_shape);
+        restore_theta.shapes = &rec_shape;
+    }
     for (long long g = 0; g < nseg && s == ADSCL_OK && !store_all; ++g) {
         double *ck = ctx->d_ck + (size_t)g * 2 * total;
         CK(cudaMemcpyAsync(ck, ctx->d_Phi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ck + total, ctx->d_Pi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-        if (piped && g == nseg - 1) {
+        if (rec_recompute && g == nseg - 1) {   // the last segment records its own stages
+            ctx->rec_stage = ctx->d_adj_stage + (size_t)(piped ? klast : 0) * stN;
+            ctx->rec_seg_stride = (long long)stN;
+            ctx->rec_seg0 = g;
+            ctx->rec_steps = nT;
+            ctx->rec_seg = seg;
+        } else if (piped && g == nseg - 1) {
             CK(cudaEventRecord(ctx->adj_ck, ctx->stream));
             CK(cudaStreamWaitEvent(ctx->adj_aux, ctx->adj_ck, 0));
             AdjArgs x = seg_args(g, kAdjSegF);
@@ -1384,7 +1450,14 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         }
         const long long n1 = std::min(nT, (g + 1) * seg);
         s = launch_evolve(ctx, kModeEvolve, (double)n1 * ctx->h_desc[0].dt, 0, ctx->h_order.data(), B, nullptr, nullptr, ctx->stream);
+        ctx->rec_stage = nullptr;
+        ctx->rec_seg0 = 0;
     }
+    if (restore_theta.shapes) {
+        std::swap(ctx->shape_of, rec_shape);
+        restore_theta.shapes = nullptr;
+    }
+    if (rec_recompute && piped && s == ADSCL_OK) CK(cudaEventRecord(ctx->adj_ready[klast], ctx->stream));
     ctx->theta = theta;
     if (s != ADSCL_OK) return s;
     s = adscl_spectrum(ctx, Jm, ADSCL_PREC_FP64, ET, 1);
@@ -1420,8 +1493,12 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
             if (g >= 1) {
                 const int k = (int)((g - 1) & 1);
                 CK(cudaStreamWaitEvent(ctx->adj_aux, ctx->adj_free[k], 0));
-                x = seg_args(g - 1, kAdjSegF);
-                s = launch_adjoint(ctx, x, ctx->adj_aux, 1);
+                if (rec_recompute) {
+                    s = recompute(g - 1, k, ctx->adj_aux);
+                } else {
+                    x = seg_args(g - 1, kAdjSegF);
+                    s = launch_adjoint(ctx, x, ctx->adj_aux, 1);
+                }
                 if (s != ADSCL_OK) break;
                 CK(cudaEventRecord(ctx->adj_ready[k], ctx->adj_aux));
             }
@@ -1433,8 +1510,15 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         }
     } else {
         for (long long g = nseg - 1; g >= 0 && s == ADSCL_OK; --g) {
-            AdjArgs x = seg_args(g, kAdjSegment);
-            s = launch_adjoint(ctx, x, ctx->stream, 0);
+            if (rec_recompute) {   // recompute (the last segment is recorded already), then sweep
+                if (g < nseg - 1) s = recompute(g, 0, ctx->stream);
+                if (s != ADSCL_OK) break;
+                AdjArgs x = seg_args(g, kAdjSegB);
+                s = launch_adjoint(ctx, x, ctx->stream, 0);
+            } else {
+                AdjArgs x = seg_args(g, kAdjSegment);
+                s = launch_adjoint(ctx, x, ctx->stream, 0);
+            }
         }
     }
     if (s != ADSCL_OK) return s;
@@ -1767,7 +1851,7 @@ void adscl_destroy(adscl_ctx *ctx)
                     ctx->d_tc_rowinst, ctx->d_tc_modeoff, ctx->d_tc_ops, ctx->d_tc_D,
                     ctx->d_tc_tasks, ctx->d_tc_err, ctx->d_lam, ctx->d_adj_scr, ctx->d_adj_stage,
                     ctx->d_ck, ctx->d_adj_small, ctx->d_adj_queue, ctx->d_A, ctx->d_ea_block, ctx->d_adj_spec,
-                    ctx->d_eageo};
+                    ctx->d_eageo, ctx->d_rPhi, ctx->d_rPi, ctx->d_rSt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ctx->evo_exec) cudaGraphExecDestroy(ctx->evo_exec);

@@ -160,6 +160,7 @@ struct EvolveArgs {
     // 0 .. stage_steps-1 that the discrete adjoint sweeps backwards (see stage_slot)
     double *stage;
     long long stage_seg_stride;  // doubles between the buffers of consecutive segments
+    long long stage_seg0;        // segment held by the first buffer
     long long stage_steps;
     int32_t stage_seg;           // steps per segment
     int32_t stage_nmax;          // node stride of one stored array
@@ -168,12 +169,12 @@ struct EvolveArgs {
 // Stage record: per stage s of step n of instance b, kStageArrays arrays of stage_nmax doubles:
 // the stage input Phi, Pi (node N-1: 0), m and e^{-delta} and F = A e^{-delta} at the nodes
 // (node N-1: M, 1, 1), alpha of the RK4-in-x map of m at the cells.  Segment g = n / stage_seg
-// holds steps g stage_seg .. (g+1) stage_seg - 1 of every instance.
+// holds steps g stage_seg .. (g+1) stage_seg - 1 of every instance, in buffer g - stage_seg0.
 constexpr int kStageArrays = 6;
 __device__ __forceinline__ double *stage_slot(const EvolveArgs &a, int b, long long n, int s)
 {
     const long long g = n / a.stage_seg, r = n - g * a.stage_seg;
-    return a.stage + g * a.stage_seg_stride +
+    return a.stage + (g - a.stage_seg0) * a.stage_seg_stride +
            (((long long)b * a.stage_seg + r) * 4 + s) * kStageArrays * (long long)a.stage_nmax;
 }
 

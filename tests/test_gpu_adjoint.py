@@ -139,11 +139,13 @@ def test_stage_storage_modes_agree(ad, orc, bufs):
 
 @pytest.mark.parametrize("extra", [5, "quarter"])
 def test_recording_forward_pass_for_batches_filling_the_gpu(ad, orc, extra):
-    """A batch with at least one evolution CTA per SM takes its forward pass through the
-    evolution kernel's stage-recording variant (one launch over all steps, every segment's stages
-    written as it goes); a quarter of that on the default one-CTA shapes runs the pass on 4-CTA
-    clusters.  Its gradients equal those of the adjoint kernel's own recomputation (one stage
-    buffer) up to rounding and the oracle's adjoint."""
+    """A batch with at least one evolution CTA per SM records its stages in the evolution
+    kernel's stage-recording variant: with a buffer per segment the forward pass writes them all
+    in one launch; with one or two buffers the forward pass writes the last segment and each
+    earlier one is recomputed from its checkpoint on a second slice (two buffers: beside the sweep
+    of the next segment).  A quarter of that on the default one-CTA shapes runs these passes on
+    4-CTA clusters.  The three storage modes give the same gradients up to rounding and the
+    oracle's adjoint, and each leaves the context on the final slice."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     N, K, Jm, n = 129, 6, 8, 20
@@ -151,26 +153,29 @@ def test_recording_forward_pass_for_batches_filling_the_gpu(ad, orc, extra):
     rng = np.random.default_rng(31)
     a = rng.uniform(0.0, 0.8, (B, K)) * np.exp(-np.arange(K) / 2.0)
     out = {}
-    for bufs in (0, 1):
+    ref = None
+    for bufs in (0, 1, 2):
         s = ad.Solver([N] * B, ko_sigma=0.5, spec_J=Jm, ckpt_every=9, adjoint_stage_buffers=bufs)
         dt, _ = s.clock()
-        out[bufs] = s.grad(a, n * dt[0])
-        assert np.all(s.clock()[1] == n)
-        if bufs == 0:   # the context ends on the final slice of a plain evolution
+        if ref is None:
             ref = ad.Solver([N] * 2, ko_sigma=0.5, spec_J=Jm, collapse_threshold=-1.0)
             ref.set_initial_modes(a[[0, B - 1]])
             ref.evolve(n * dt[0])
-            for k, b in enumerate((0, B - 1)):
-                x, y = s.get_state(b), ref.get_state(k)
-                if extra == 5:   # same shape: the recording variant does the same arithmetic
-                    assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
-                else:            # recorded on 4-CTA clusters: the scans associate differently
-                    assert np.abs(x[0] - y[0]).max() < 1e-13 and np.abs(x[1] - y[1]).max() < 1e-13
-            ref.close()
+        out[bufs] = s.grad(a, n * dt[0])
+        assert np.all(s.clock()[1] == n)
+        for k, b in enumerate((0, B - 1)):   # the context ends on the final slice
+            x, y = s.get_state(b), ref.get_state(k)
+            if extra == 5:   # same shape: the recording variant does the same arithmetic
+                assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+            else:            # recorded on 4-CTA clusters: the scans associate differently
+                assert np.abs(x[0] - y[0]).max() < 1e-13 and np.abs(x[1] - y[1]).max() < 1e-13
         s.close()
-    (J0, g0), (J1, g1) = out[0], out[1]
-    assert np.abs(J0 - J1).max() <= 1e-12 * np.abs(J1).max()
-    assert np.abs(g0 - g1).max() <= 1e-10 * np.abs(g1).max()
+    ref.close()
+    (J0, g0) = out[0]
+    for bufs in (1, 2):
+        J1, g1 = out[bufs]
+        assert np.abs(J0 - J1).max() <= 1e-12 * np.abs(J1).max()
+        assert np.abs(g0 - g1).max() <= 1e-10 * np.abs(g1).max()
     for b in (0, B // 2, B - 1):
         Jo, go = orc.grad(a[b], N, n, dt[0], sigma=0.5, Jm=Jm)
         assert abs(J0[b] - Jo) <= 1e-10 * abs(Jo)
