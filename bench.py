@@ -58,7 +58,7 @@ SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A
 # the evolution kernel (evolve_kernel<8, 128, 4, true> over the whole window) and the adjoint
 # kernel's backward sweep (phase B, per segment), from the ncu capture in
 # profiles/adjoint_kernel_adjoint_batch.md; used only while the kernel sources are unchanged
-ADJ_ISSUE = {"sha256": "e6bc238e664220463ac9c6133b43234e42edb7bbdf243517ffdb381fc9e7b5b8",
+ADJ_ISSUE = {"sha256": "b49ef8ddd58287bc68aa2f976bf0c0a3422c882778723e5618960a1ce23df2cd",
              "forward_record": 75931385856 / 1074003968,
              "phase_B": (9518514176 + 10991304704 + 8170766336) / 268500992}
 L2_FLUSH_BYTES = 512 << 20
@@ -67,8 +67,8 @@ REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
 # DRAM bytes (read + write) of one timed evolve_kernel launch of the amplitude scan, from an ncu
 # capture of this script (profiles/evolve_kernel_amp_scan.md); reported only while the kernel
 # source and the kernel shape are the ones the counters were taken on.
-TRAFFIC = {"kernel_sha256": "691f6b869ec61cd877426dfe56545a11941d7dd356f5f956b3a6ba1fa63b221c",
-           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17722368 + 67019776,
+TRAFFIC = {"kernel_sha256": "52364d26489815480a94d728709e093710313c856713ba6d8d0d930713c83fb1",
+           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17575168 + 59295232,
            # FP64 instructions (DADD + DMUL + DFMA, thread level) per point-substep, same capture
            "fp64_instr_per_point_substep": (23334264832 + 13958131712 + 38349320192) / 1074003968}
 
