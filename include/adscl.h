@@ -93,8 +93,9 @@ typedef struct {
     int32_t adjoint_stage_buffers; /* most checkpoint segments whose stages adscl_grad keeps in
                                     device memory at once: 0 = as many as fit (all segments:
                                     the forward pass stores every stage and nothing is
-                                    recomputed; else 2: recomputation of one segment beside the
-                                    backward sweep of the next; else 1) */
+                                    recomputed; else 2: the last segment stored by the forward
+                                    pass, each earlier one recomputed beside the backward sweep
+                                    of the next; else 1) */
     void *stream;                /* cudaStream_t for all work; NULL = the legacy default stream */
 } adscl_config;
 
@@ -158,11 +159,13 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
  * ckpt_every; every stage of a segment is stored in device memory (B * ckpt_every * 24 * N
  * doubles per segment) and swept backwards through the exact transpose of the discrete step
  * (constraint scans included).  When every segment's stages fit (adjoint_stage_buffers), the
- * forward pass stores them all: through the evolution kernel itself (a variant that records
- * every stage) when the context's kernel shapes give the batch at least one CTA per SM (see
- * adscl_autotune), else through the adjoint kernel's recomputation; otherwise it keeps
- * (Phi, Pi) at the segment starts and each segment is recomputed once before its sweep.
- * Replaces the context's state by the final slice (step index n). */
+ * forward pass stores them all; otherwise it keeps (Phi, Pi) at the segment starts, stores the
+ * last segment's stages and recomputes each earlier segment once before its sweep.  The
+ * recording runs in the evolution kernel itself (a variant that records every stage) when the
+ * context's kernel shapes give the batch at least one CTA per SM, directly or with a small
+ * batch's one-CTA shapes split over 2- or 4-CTA clusters for the gradient's own evolutions (see
+ * adscl_autotune); else in the adjoint kernel's recomputation.  Replaces the context's state by
+ * the final slice (step index n). */
 adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, double *J_out,
                         double *dJda, int ptr_is_device);
 
