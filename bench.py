@@ -646,11 +646,18 @@ def main():
             cpu_adj = {"ratio": t_og / t_of, "forward_s": t_of, "grad_s": t_og,
                        "sample": f"1 instance, N={ainst[0].N}, {n_s} steps, oracle (1 thread)"}
         adj_issue = None
-        if kernel_digest(("adjoint.cuh", "evolve.cuh", "expneg.cuh")) == ADJ_ISSUE["sha256"]:
-            # default-shape context: the recording forward pass and the backward sweep; FP64
+        stored_all = stage_gb < 0.85 * dev_gb
+        if (kernel_digest(("adjoint.cuh", "evolve.cuh", "expneg.cuh")) == ADJ_ISSUE["sha256"] and
+                kernel_digest() == TRAFFIC["kernel_sha256"]):
+            # default-shape context: the recording forward pass and the backward sweep (when the
+            # stages do not all fit: the plain forward pass over all but the last segment, which
+            # it records, and the recording recomputation of every other segment); FP64
             # instructions of the whole window against the probe's FMA issue rate (FMA = 2 flops)
             w_adj = len(ainst) * ainst[0].N * 4.0 * ADJ_STEPS
             ipps = ADJ_ISSUE["forward_record"] + ADJ_ISSUE["phase_B"]
+            if not stored_all:
+                nseg = -(-ADJ_STEPS // 256)
+                ipps += TRAFFIC["fp64_instr_per_point_substep"] * (1.0 - 1.0 / nseg)
             adj_issue = {"fp64_instr_per_point_substep": ipps,
                          "frac": (w_adj * ipps / t_adj) / (tflops_peak * 1e12 / 2)}
         adj = {"value": t_adj / t_fwd, "forward_ms": 1e3 * t_fwd, "grad_ms": 1e3 * t_adj,
@@ -662,11 +669,11 @@ def main():
                "workload": f"64 mode-sum instances, N=4097, {ADJ_STEPS} RK4 steps of dt=2pi/32768, "
                            "checkpoint every 256 steps, J = sum_{j<32}(E_j(T)-E_j(0))^2",
                "grad_includes": "E(0), the forward pass (storing every stage when all segments fit "
-                                "in device memory; else checkpoints, the last segment's stages and a "
-                                "recompute of each earlier segment beside the sweep of the next), E(T), "
+                                "in device memory; else checkpoints and the last segment's stages, "
+                                "each earlier segment recomputed before its sweep), E(T), "
                                 "the backward sweep, the projection onto the modes",
-               "stages_stored": ("all segments" if stage_gb < 0.85 * dev_gb else
-                                 "two segment buffers (recomputation)")}
+               "stages_stored": ("all segments" if stored_all else
+                                 "one segment buffer (recomputation)")}
         sa.close()
 
     # spectrum timing (current slices of the amplitude scan, 64 modes)

@@ -93,8 +93,9 @@ typedef struct {
     int32_t adjoint_stage_buffers; /* most checkpoint segments whose stages adscl_grad keeps in
                                     device memory at once: 0 = as many as fit (all segments:
                                     the forward pass stores every stage and nothing is
-                                    recomputed; else 2: the last segment stored by the forward
-                                    pass, each earlier one recomputed beside the backward sweep
+                                    recomputed; else segments recomputed from checkpoints, see
+                                    adscl_grad: 2 buffers let the adjoint kernel's
+                                    recomputation of one segment run beside the backward sweep
                                     of the next; else 1) */
     void *stream;                /* cudaStream_t for all work; NULL = the legacy default stream */
 } adscl_config;

@@ -128,6 +128,7 @@ struct adscl_ctx {
     int adj_stage_bufs = 0;
     double *d_adj_spec = nullptr;      // slots of the spectrum transposes
     cudaStream_t adj_aux = nullptr;    // stream of the recomputation beside the backward sweep
+    cudaStream_t adj_hi = nullptr;     // high-priority stream of that backward sweep
     cudaEvent_t adj_free[2] = {nullptr, nullptr}, adj_ready[2] = {nullptr, nullptr};
     cudaEvent_t adj_ck = nullptr;      // the last checkpoint is written
     double *d_ck = nullptr;            // checkpoints (Phi, Pi) at segment starts
@@ -1212,14 +1213,47 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         CK(cudaMalloc(&ctx->d_adj_small, ((size_t)B * (5 * kMaxModes + 1)) * sizeof(double)));
         CK(cudaMalloc(&ctx->d_adj_queue, 2 * sizeof(int32_t)));
     }
+    // The stages are recorded by the evolution kernel itself when its shapes spread the batch
+    // over the whole GPU (at least one CTA per SM).  A batch whose shapes give fewer CTAs than
+    // SMs (a small batch on the default one-CTA shapes) runs the forward pass and the
+    // recomputations on the same thread layout split over a cluster of 2 or 4 CTAs (P = 8,
+    // NT * CL = 512), the largest that keeps the batch within two CTAs per SM; the context's
+    // shapes are restored afterwards.  With every stage stored, the forward pass records them
+    // all; otherwise it records the last segment, and each earlier segment is recomputed from its
+    // checkpoint on a second slice (the context's slice stays at step nT), before the sweep of
+    // that segment: one buffer serves (the recording launch fills the GPU by itself; beside a
+    // sweep it was slower than after it).  A batch that fills neither way records its stages in
+    // the adjoint kernel's own recomputation (phase F).
+    long long evo_ctas = 0;
+    for (int b = 0; b < B; ++b) evo_ctas += kShapes[ctx->shape_of[b]].CL;
+    std::vector<int> rec_shape = ctx->shape_of;
+    if (evo_ctas < ctx->num_sms) {
+        evo_ctas = 0;
+        for (int b = 0; b < B; ++b) {
+            const int cur = ctx->shape_of[b];
+            if (kShapes[cur].P == 8 && kShapes[cur].NT * kShapes[cur].CL == 512) {
+                for (int cl : {4, 2}) {
+                    const int id = shape_index(8, 512 / cl, cl);
+                    if (id >= 0 && cl > kShapes[cur].CL && shape_fits(id, ctx->N[b]) &&
+                        (long long)B * cl <= 2LL * ctx->num_sms) {
+                        rec_shape[b] = id;
+                        break;
+                    }
+                }
+            }
+            evo_ctas += kShapes[rec_shape[b]].CL;
+        }
+    }
+    const bool fills = evo_ctas >= ctx->num_sms;
     // stage storage, one buffer per segment: with a buffer for every segment (when the device
     // has room for them with a tenth of its memory to spare) the forward pass itself stores every
-    // stage and nothing is recomputed; with two, the recomputation of segment g-1 runs beside the
-    // backward sweep of segment g; with one, each segment recomputes, then sweeps
+    // stage and nothing is recomputed; with two (phase F only), the recomputation of segment g-1
+    // runs beside the backward sweep of segment g; with one, each segment recomputes, then sweeps
     const size_t stage_need = (size_t)B * std::max(seg, 1) * 4 * kStageArrays * ctx->Nmax;
     {
         const int cap = ctx->adj_bufs_cap > 0 ? ctx->adj_bufs_cap : (1 << 20);
-        const int want[3] = {(int)std::min<long long>(std::min<long long>(nseg, cap), 1 << 20), std::min(2, cap), 1};
+        const int want[3] = {(int)std::min<long long>(std::min<long long>(nseg, cap), 1 << 20),
+                             fills ? 1 : std::min(2, cap), 1};
         int have = (ctx->adj_stage_doubles >= stage_need) ? ctx->adj_stage_bufs : 0;
         for (int w : want) {
             if (w < 1 || have >= w) break;   // what is allocated already serves
@@ -1273,59 +1307,32 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     aa.Nmax = ctx->Nmax;
     aa.J = Jm;
     const size_t stN = ctx->adj_stage_doubles;
+    const bool store_all = ctx->adj_stage_bufs >= nseg &&
+                           (ctx->adj_bufs_cap == 0 || ctx->adj_bufs_cap >= nseg);
+    const bool rec_evolve = store_all && fills;
+    const bool rec_recompute = !store_all && fills;
+    const bool piped = !store_all && !fills && ctx->adj_stage_bufs >= 2 && ctx->adj_bufs_cap != 1 && nseg > 1;
     auto seg_args = [&](long long g, int mode) {
         AdjArgs x = aa;
         x.mode = mode;
         x.ckP = ctx->d_ck + (size_t)g * 2 * total;
         x.ckQ = x.ckP + total;
         x.nsteps = (int32_t)(std::min(nT, (g + 1) * seg) - g * seg);
-        const int nb = ctx->adj_stage_bufs;
-        const bool all = nb >= nseg && (ctx->adj_bufs_cap == 0 || ctx->adj_bufs_cap >= nseg);
-        const bool two = !all && nb >= 2 && ctx->adj_bufs_cap != 1;
-        x.stage = ctx->d_adj_stage + (all ? (size_t)g : two ? (size_t)(g & 1) : 0) * stN;
+        x.stage = ctx->d_adj_stage + (store_all ? (size_t)g : piped ? (size_t)(g & 1) : 0) * stN;
         x.outP = x.outQ = nullptr;
         return x;
     };
-    const bool store_all = ctx->adj_stage_bufs >= nseg &&
-                           (ctx->adj_bufs_cap == 0 || ctx->adj_bufs_cap >= nseg);
-    // The stages are recorded by the evolution kernel itself when its shapes spread the batch
-    // over the whole GPU (at least one CTA per SM).  A batch whose shapes give fewer CTAs than
-    // SMs (a small batch on the default one-CTA shapes) runs the forward pass and the
-    // recomputations on the same thread layout split over a cluster of 2 or 4 CTAs (P = 8,
-    // NT * CL = 512), the largest that keeps the batch within two CTAs per SM; the context's
-    // shapes are restored afterwards.  With every stage stored, the forward pass records them
-    // all; otherwise it records the last segment, and each earlier segment is recomputed from its
-    // checkpoint on a second slice (the context's slice stays at step nT).  A batch that fills
-    // neither way records its stages in the adjoint kernel's own recomputation (phase F).
-    long long evo_ctas = 0;
-    for (int b = 0; b < B; ++b) evo_ctas += kShapes[ctx->shape_of[b]].CL;
-    std::vector<int> rec_shape = ctx->shape_of;
-    if (evo_ctas < ctx->num_sms) {
-        evo_ctas = 0;
-        for (int b = 0; b < B; ++b) {
-            const int cur = ctx->shape_of[b];
-            if (kShapes[cur].P == 8 && kShapes[cur].NT * kShapes[cur].CL == 512) {
-                for (int cl : {4, 2}) {
-                    const int id = shape_index(8, 512 / cl, cl);
-                    if (id >= 0 && cl > kShapes[cur].CL && shape_fits(id, ctx->N[b]) &&
-                        (long long)B * cl <= 2LL * ctx->num_sms) {
-                        rec_shape[b] = id;
-                        break;
-                    }
-                }
-            }
-            evo_ctas += kShapes[rec_shape[b]].CL;
-        }
-    }
-    const bool rec_evolve = store_all && evo_ctas >= ctx->num_sms;
-    const bool rec_recompute = !store_all && evo_ctas >= ctx->num_sms;
     if (rec_recompute && !ctx->d_rSt) {
         CK(cudaMalloc(&ctx->d_rPhi, total * sizeof(double)));
         CK(cudaMalloc(&ctx->d_rPi, total * sizeof(double)));
         CK(cudaMalloc(&ctx->d_rSt, (size_t)B * sizeof(InstState)));
     }
-    const bool piped = !store_all && ctx->adj_stage_bufs >= 2 && ctx->adj_bufs_cap != 1 && nseg > 1;
     if (piped && !ctx->adj_aux) {
+        // the sweep's CTAs are placed before the recomputation's when both wait for SMs: the
+        // recomputation then fills the SMs that the sweep leaves free instead of delaying it
+        int lo = 0, hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CK(cudaStreamCreateWithPriority(&ctx->adj_hi, cudaStreamNonBlocking, hi));
         CK(cudaStreamCreateWithFlags(&ctx->adj_aux, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&ctx->adj_ck, cudaEventDisableTiming));
         for (int k = 0; k < 2; ++k) {
@@ -1485,9 +1492,11 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
             s = launch_adjoint(ctx, x, ctx->stream, 0);
         }
     } else if (piped) {
-        // main stream: B(g) for g descending, each after its F(g); side stream: F(g-1) once
-        // B(g+1) (or, for the first one, the spectrum transpose) has released its buffer
+        // high-priority stream: B(g) for g descending, each after its F(g); side stream: F(g-1)
+        // once B(g+1) (or, for the first one, the spectrum transpose) has released its buffer;
+        // the context's stream joins after B(0)
         CK(cudaEventRecord(ctx->adj_free[klast ^ 1], ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->adj_hi, ctx->adj_free[klast ^ 1], 0));
         for (long long g = nseg - 1; g >= 0 && s == ADSCL_OK; --g) {
             AdjArgs x;
             if (g >= 1) {
@@ -1503,11 +1512,13 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
                 CK(cudaEventRecord(ctx->adj_ready[k], ctx->adj_aux));
             }
             const int kg = (int)(g & 1);
-            CK(cudaStreamWaitEvent(ctx->stream, ctx->adj_ready[kg], 0));
+            CK(cudaStreamWaitEvent(ctx->adj_hi, ctx->adj_ready[kg], 0));
             x = seg_args(g, kAdjSegB);
-            s = launch_adjoint(ctx, x, ctx->stream, 0);
-            CK(cudaEventRecord(ctx->adj_free[kg], ctx->stream));
+            s = launch_adjoint(ctx, x, ctx->adj_hi, 0);
+            CK(cudaEventRecord(ctx->adj_free[kg], ctx->adj_hi));
         }
+        CK(cudaEventRecord(ctx->adj_ck, ctx->adj_hi));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->adj_ck, 0));
     } else {
         for (long long g = nseg - 1; g >= 0 && s == ADSCL_OK; --g) {
             if (rec_recompute) {   // recompute (the last segment is recorded already), then sweep
@@ -1858,6 +1869,7 @@ void adscl_destroy(adscl_ctx *ctx)
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (cudaStream_t st : ctx->aux) cudaStreamDestroy(st);
     if (ctx->adj_aux) cudaStreamDestroy(ctx->adj_aux);
+    if (ctx->adj_hi) cudaStreamDestroy(ctx->adj_hi);
     if (ctx->adj_ck) cudaEventDestroy(ctx->adj_ck);
     for (int k = 0; k < 2; ++k) {
         if (ctx->adj_free[k]) cudaEventDestroy(ctx->adj_free[k]);

@@ -141,10 +141,9 @@ def test_stage_storage_modes_agree(ad, orc, bufs):
 def test_recording_forward_pass_for_batches_filling_the_gpu(ad, orc, extra):
     """A batch with at least one evolution CTA per SM records its stages in the evolution
     kernel's stage-recording variant: with a buffer per segment the forward pass writes them all
-    in one launch; with one or two buffers the forward pass writes the last segment and each
-    earlier one is recomputed from its checkpoint on a second slice (two buffers: beside the sweep
-    of the next segment).  A quarter of that on the default one-CTA shapes runs these passes on
-    4-CTA clusters.  The three storage modes give the same gradients up to rounding and the
+    in one launch; with a cap of one or two buffers the forward pass writes the last segment and
+    each earlier one is recomputed from its checkpoint on a second slice before its sweep.  A
+    quarter of that on the default one-CTA shapes runs these passes on 4-CTA clusters.  The three storage modes give the same gradients up to rounding and the
     oracle's adjoint, and each leaves the context on the final slice."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
