@@ -324,7 +324,7 @@ def run_full_job(args, sol, insts, wl_desc, stages, shapes, stream, ws, rank, di
     """The whole job: every instance from t = 0 to args.full_job (or its collapse) in evolve
     calls of one time unit; wall time on the host clock, device-resident fields.  Unless the
     shapes are pinned, autotune is called after every unit of t: its choice is cached per
-    number of running instances (a power-of-two bucket), so it re-tunes only when collapses
+    number of running instances (a half-octave bucket), so it re-tunes only when collapses
     have thinned the batch enough (the time of those tunings is part of the job)."""
     import torch
     B = len(insts)

@@ -195,7 +195,7 @@ adscl_status adscl_get_clock(adscl_ctx *ctx, double *dt, int64_t *step);
  * concurrently in a batch, the per-size choice is kept only if the whole batch (timed over that
  * longer window) is more than 1 % faster with it than with the default shapes.  Results are
  * cached for the process by (GPU name, SM count, scheme, the batch's grid sizes with their
- * instance counts, and floor(log2) of the instances of each size still running): a cached entry
+ * instance counts, and floor(2 log2) of the instances of each size still running): a cached entry
  * is reused without timing or touching the state, and calling this again after collapses have
  * thinned a batch re-tunes for the smaller number of running instances.
  * Synchronous.  The evolved-A and fixed-metric kernels are built for the shapes (8, 512, 1/2/4/8),

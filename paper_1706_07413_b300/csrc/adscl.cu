@@ -45,8 +45,8 @@ int default_shape(int N) { return shape_index(kP, kNT, cluster_of(N)); }
 
 // autotuner results of this process: (device name, SM count, scheme, the batch's (N, instances
 // of that N) in decreasing N) -> shape of each of those N
-// (GPU name, SM count, scheme, (N, instances) of each size, log2 of the running instances of each
-// size: the best shape depends on how many instances are still evolving)
+// (GPU name, SM count, scheme, (N, instances) of each size, the half-octave bucket of the running
+// instances of each size: the best shape depends on how many instances are still evolving)
 using TuneKey = std::tuple<std::string, int, int, std::vector<std::pair<int, int>>, std::vector<int>>;
 std::map<TuneKey, std::vector<int>> g_tuned;
 std::mutex g_tuned_mu;
@@ -1686,9 +1686,10 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
         for (int r = 0; r < nr; ++r) {
             int run = 0;
             for (int q = run_start[r]; q < run_start[r + 1]; ++q) run += stc[ord[q]].status == kRunning;
-            int b = -1;
-            while (run > 0) { ++b; run >>= 1; }
-            rbucket[r] = b;
+            // half-octave buckets: 2 floor(log2 run), plus one from run >= sqrt(2) 2^floor(log2 run)
+            int k = -1;
+            for (int x = run; x > 0; x >>= 1) ++k;
+            rbucket[r] = run > 0 ? 2 * k + ((long long)run * run >= (2LL << (2 * k)) ? 1 : 0) : -1;
         }
     }
     const TuneKey key{ctx->dev_name, ctx->num_sms, ctx->scheme, sig, rbucket};
