@@ -611,6 +611,7 @@ def main():
         Jv, gv = sa.grad(a, Ta)
         torch.cuda.synchronize()
         t_adj = time.perf_counter() - t0
+        st_bytes, st_bufs, st_segs, st_recomp = sa.adjoint_storage()
         # the same with the autotuned forward shape (64 instances: fewer than the SMs, so the
         # tuner splits each instance over a cluster; the adjoint kernel keeps one CTA each)
         tuned = sa.autotune(8)
@@ -627,9 +628,6 @@ def main():
         sa.grad(a, Ta)
         torch.cuda.synchronize()
         t_adj_t = time.perf_counter() - t0
-        # stage storage of the whole window (6 arrays of N doubles per stage) against the device
-        stage_gb = len(ainst) * ADJ_STEPS * 4 * 6 * ainst[0].N * 8 / 1e9
-        dev_gb = torch.cuda.get_device_properties(local).total_memory / 1e9
         cpu_adj = None
         if ws == 1 and not args.no_cpu_baseline:
             # the oracle's own gradient / forward time ratio on a bounded sample of the same
@@ -646,18 +644,15 @@ def main():
             cpu_adj = {"ratio": t_og / t_of, "forward_s": t_of, "grad_s": t_og,
                        "sample": f"1 instance, N={ainst[0].N}, {n_s} steps, oracle (1 thread)"}
         adj_issue = None
-        stored_all = stage_gb < 0.85 * dev_gb
         if (kernel_digest(("adjoint.cuh", "evolve.cuh", "expneg.cuh")) == ADJ_ISSUE["sha256"] and
                 kernel_digest() == TRAFFIC["kernel_sha256"]):
             # default-shape context: the recording forward pass and the backward sweep (when the
-            # stages do not all fit: the plain forward pass over all but the last segment, which
-            # it records, and the recording recomputation of every other segment); FP64
-            # instructions of the whole window against the probe's FMA issue rate (FMA = 2 flops)
+            # stages do not all fit: the plain forward pass over the segments recomputed later
+            # and the recording recomputation of those); FP64 instructions of the whole window
+            # against the probe's FMA issue rate (FMA = 2 flops)
             w_adj = len(ainst) * ainst[0].N * 4.0 * ADJ_STEPS
             ipps = ADJ_ISSUE["forward_record"] + ADJ_ISSUE["phase_B"]
-            if not stored_all:
-                nseg = -(-ADJ_STEPS // 256)
-                ipps += TRAFFIC["fp64_instr_per_point_substep"] * (1.0 - 1.0 / nseg)
+            ipps += TRAFFIC["fp64_instr_per_point_substep"] * st_recomp / max(st_segs, 1)
             adj_issue = {"fp64_instr_per_point_substep": ipps,
                          "frac": (w_adj * ipps / t_adj) / (tflops_peak * 1e12 / 2)}
         adj = {"value": t_adj / t_fwd, "forward_ms": 1e3 * t_fwd, "grad_ms": 1e3 * t_adj,
@@ -669,11 +664,11 @@ def main():
                "workload": f"64 mode-sum instances, N=4097, {ADJ_STEPS} RK4 steps of dt=2pi/32768, "
                            "checkpoint every 256 steps, J = sum_{j<32}(E_j(T)-E_j(0))^2",
                "grad_includes": "E(0), the forward pass (storing every stage when all segments fit "
-                                "in device memory; else checkpoints and the last segment's stages, "
-                                "each earlier segment recomputed before its sweep), E(T), "
-                                "the backward sweep, the projection onto the modes",
-               "stages_stored": ("all segments" if stored_all else
-                                 "one segment buffer (recomputation)")}
+                                "in device memory; else checkpoints and the stages of the last "
+                                "segments that fit, each earlier segment recomputed before its "
+                                "sweep), E(T), the backward sweep, the projection onto the modes",
+               "stage_storage": {"bytes": st_bytes, "segment_buffers": st_bufs, "segments": st_segs,
+                                 "recomputed": st_recomp}}
         sa.close()
 
     # spectrum timing (current slices of the amplitude scan, 64 modes)

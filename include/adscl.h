@@ -161,7 +161,8 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
  * doubles per segment) and swept backwards through the exact transpose of the discrete step
  * (constraint scans included).  When every segment's stages fit (adjoint_stage_buffers), the
  * forward pass stores them all; otherwise it keeps (Phi, Pi) at the segment starts, stores the
- * last segment's stages and recomputes each earlier segment once before its sweep.  The
+ * stages of as many last segments as fit and recomputes each earlier segment once before its
+ * sweep (adscl_adjoint_storage reports the buffers and the recomputed segments).  The
  * recording runs in the evolution kernel itself (a variant that records every stage) when the
  * context's kernel shapes give the batch at least one CTA per SM, directly or with a small
  * batch's one-CTA shapes split over 2- or 4-CTA clusters for the gradient's own evolutions (see
@@ -182,6 +183,14 @@ adscl_status adscl_set_state(adscl_ctx *ctx, int32_t inst, const double *Phi, co
 
 /* Per-instance time step dt and current step index (host outputs, length B, may be NULL). */
 adscl_status adscl_get_clock(adscl_ctx *ctx, double *dt, int64_t *step);
+
+/* Stage storage of adscl_grad (host outputs, each may be NULL): the device bytes the context
+ * holds for stage records (kept between calls, freed by adscl_destroy), the number of segment
+ * buffers in them, and for the last adscl_grad call its number of checkpoint segments and how
+ * many of them were recomputed from their checkpoints (0 when every stage was stored by the
+ * forward pass).  All zero before the first adscl_grad.  No device work. */
+adscl_status adscl_adjoint_storage(adscl_ctx *ctx, int64_t *bytes, int32_t *buffers, int64_t *segments,
+                                   int64_t *recomputed);
 
 /* Autotuner (classic RK4 scheme): for every grid size N of the context, time each kernel shape
  * that fits N -- P grid nodes per thread, NT threads per CTA (so 512 / NT CTAs per SM), CL CTAs

@@ -63,6 +63,7 @@ SIGNATURES = {
     "adscl_get_state": ([_VP, _I32, _VP, _VP, _VP, _VP, ctypes.c_int], ctypes.c_int),
     "adscl_set_state": ([_VP, _I32, _VP, _VP, _I64], ctypes.c_int),
     "adscl_get_clock": ([_VP, _VP, _VP], ctypes.c_int),
+    "adscl_adjoint_storage": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "adscl_launch_count": ([_VP], _I64),
     "adscl_autotune": ([_VP, _I32], ctypes.c_int),
     "adscl_get_shape": ([_VP, _I32, _VP, _VP, _VP], ctypes.c_int),
@@ -266,6 +267,14 @@ class Solver:
         step = np.empty(self.B, dtype=np.int64)
         self._check(self.lib.adscl_get_clock(self.ctx, dt.ctypes.data, step.ctypes.data))
         return dt, step
+
+    def adjoint_storage(self):
+        """(bytes, buffers, segments, recomputed) of the stage storage (adscl_adjoint_storage)."""
+        by, nb = ctypes.c_int64(), ctypes.c_int32()
+        ns, nr = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.adscl_adjoint_storage(self.ctx, ctypes.byref(by), ctypes.byref(nb),
+                                                   ctypes.byref(ns), ctypes.byref(nr)))
+        return by.value, nb.value, ns.value, nr.value
 
     def spectrum(self, J=64, precision=PREC_FP64):
         E = np.empty((self.B, J))

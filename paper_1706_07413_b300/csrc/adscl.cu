@@ -126,6 +126,7 @@ struct adscl_ctx {
     double *d_adj_stage = nullptr;     // stored stages, one buffer per segment held
     size_t adj_stage_doubles = 0;      // doubles of one buffer
     int adj_stage_bufs = 0;
+    long long adj_segments = 0, adj_recomputed = 0;   // of the last adscl_grad
     double *d_adj_spec = nullptr;      // slots of the spectrum transposes
     cudaStream_t adj_aux = nullptr;    // stream of the recomputation beside the backward sweep
     cudaStream_t adj_hi = nullptr;     // high-priority stream of that backward sweep
@@ -1247,13 +1248,23 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     const bool fills = evo_ctas >= ctx->num_sms;
     // stage storage, one buffer per segment: with a buffer for every segment (when the device
     // has room for them with a tenth of its memory to spare) the forward pass itself stores every
-    // stage and nothing is recomputed; with two (phase F only), the recomputation of segment g-1
-    // runs beside the backward sweep of segment g; with one, each segment recomputes, then sweeps
+    // stage and nothing is recomputed.  Otherwise, when the evolution kernel records, as many
+    // buffers as fit: the forward pass records the last segments into them and each earlier
+    // segment is recomputed into the first one before its sweep; for phase F on the adjoint
+    // kernel, two (the recomputation of segment g-1 beside the backward sweep of segment g)
+    // or one (each segment recomputes, then sweeps)
     const size_t stage_need = (size_t)B * std::max(seg, 1) * 4 * kStageArrays * ctx->Nmax;
     {
         const int cap = ctx->adj_bufs_cap > 0 ? ctx->adj_bufs_cap : (1 << 20);
+        size_t free0 = 0, total0 = 0;
+        CK(cudaMemGetInfo(&free0, &total0));
+        const double cur0 = (double)ctx->adj_stage_bufs * ctx->adj_stage_doubles * sizeof(double);
+        const double room = (double)free0 + cur0 - 0.1 * (double)total0;
+        const long long mfit = room > 0.0 ? (long long)(room / ((double)stage_need * sizeof(double))) : 0;
         const int want[3] = {(int)std::min<long long>(std::min<long long>(nseg, cap), 1 << 20),
-                             fills ? 1 : std::min(2, cap), 1};
+                             fills ? (int)std::max(1LL, std::min<long long>(std::min<long long>(mfit, nseg - 1), cap))
+                                   : std::min(2, cap),
+                             1};
         int have = (ctx->adj_stage_doubles >= stage_need) ? ctx->adj_stage_bufs : 0;
         for (int w : want) {
             if (w < 1 || have >= w) break;   // what is allocated already serves
@@ -1311,6 +1322,13 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
                            (ctx->adj_bufs_cap == 0 || ctx->adj_bufs_cap >= nseg);
     const bool rec_evolve = store_all && fills;
     const bool rec_recompute = !store_all && fills;
+    // recording recomputation: the last nrec segments are recorded by the forward pass
+    // (segment g >= nseg - nrec in buffer g - (nseg - nrec)), the others recomputed into buffer 0
+    const long long nrec = rec_recompute ? std::max(1LL, std::min<long long>(
+                                               std::min<long long>(ctx->adj_stage_bufs, nseg),
+                                               ctx->adj_bufs_cap > 0 ? ctx->adj_bufs_cap : nseg))
+                                         : 0;
+    const long long g_rec = nseg - nrec;   // first segment recorded by the forward pass
     const bool piped = !store_all && !fills && ctx->adj_stage_bufs >= 2 && ctx->adj_bufs_cap != 1 && nseg > 1;
     auto seg_args = [&](long long g, int mode) {
         AdjArgs x = aa;
@@ -1318,10 +1336,15 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         x.ckP = ctx->d_ck + (size_t)g * 2 * total;
         x.ckQ = x.ckP + total;
         x.nsteps = (int32_t)(std::min(nT, (g + 1) * seg) - g * seg);
-        x.stage = ctx->d_adj_stage + (store_all ? (size_t)g : piped ? (size_t)(g & 1) : 0) * stN;
+        const size_t k = store_all ? (size_t)g
+                         : piped ? (size_t)(g & 1)
+                         : (rec_recompute && g >= g_rec) ? (size_t)(g - g_rec) : 0;
+        x.stage = ctx->d_adj_stage + k * stN;
         x.outP = x.outQ = nullptr;
         return x;
     };
+    ctx->adj_segments = nseg;
+    ctx->adj_recomputed = store_all ? 0 : rec_recompute ? g_rec : nseg;
     if (rec_recompute && !ctx->d_rSt) {
         CK(cudaMalloc(&ctx->d_rPhi, total * sizeof(double)));
         CK(cudaMalloc(&ctx->d_rPi, total * sizeof(double)));
@@ -1441,10 +1464,10 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         double *ck = ctx->d_ck + (size_t)g * 2 * total;
         CK(cudaMemcpyAsync(ck, ctx->d_Phi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ck + total, ctx->d_Pi, total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-        if (rec_recompute && g == nseg - 1) {   // the last segment records its own stages
-            ctx->rec_stage = ctx->d_adj_stage + (size_t)(piped ? klast : 0) * stN;
+        if (rec_recompute && g >= g_rec) {   // the last segments record their own stages
+            ctx->rec_stage = ctx->d_adj_stage;
             ctx->rec_seg_stride = (long long)stN;
-            ctx->rec_seg0 = g;
+            ctx->rec_seg0 = g_rec;
             ctx->rec_steps = nT;
             ctx->rec_seg = seg;
         } else if (piped && g == nseg - 1) {
@@ -1464,7 +1487,6 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         std::swap(ctx->shape_of, rec_shape);
         restore_theta.shapes = nullptr;
     }
-    if (rec_recompute && piped && s == ADSCL_OK) CK(cudaEventRecord(ctx->adj_ready[klast], ctx->stream));
     ctx->theta = theta;
     if (s != ADSCL_OK) return s;
     s = adscl_spectrum(ctx, Jm, ADSCL_PREC_FP64, ET, 1);
@@ -1502,12 +1524,8 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
             if (g >= 1) {
                 const int k = (int)((g - 1) & 1);
                 CK(cudaStreamWaitEvent(ctx->adj_aux, ctx->adj_free[k], 0));
-                if (rec_recompute) {
-                    s = recompute(g - 1, k, ctx->adj_aux);
-                } else {
-                    x = seg_args(g - 1, kAdjSegF);
-                    s = launch_adjoint(ctx, x, ctx->adj_aux, 1);
-                }
+                x = seg_args(g - 1, kAdjSegF);
+                s = launch_adjoint(ctx, x, ctx->adj_aux, 1);
                 if (s != ADSCL_OK) break;
                 CK(cudaEventRecord(ctx->adj_ready[k], ctx->adj_aux));
             }
@@ -1521,8 +1539,8 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
         CK(cudaStreamWaitEvent(ctx->stream, ctx->adj_ck, 0));
     } else {
         for (long long g = nseg - 1; g >= 0 && s == ADSCL_OK; --g) {
-            if (rec_recompute) {   // recompute (the last segment is recorded already), then sweep
-                if (g < nseg - 1) s = recompute(g, 0, ctx->stream);
+            if (rec_recompute) {   // recompute (the last segments are recorded already), then sweep
+                if (g < g_rec) s = recompute(g, 0, ctx->stream);
                 if (s != ADSCL_OK) break;
                 AdjArgs x = seg_args(g, kAdjSegB);
                 s = launch_adjoint(ctx, x, ctx->stream, 0);
@@ -1617,6 +1635,18 @@ adscl_status adscl_get_clock(adscl_ctx *ctx, double *dt, int64_t *step)
 }
 
 int64_t adscl_launch_count(const adscl_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+adscl_status adscl_adjoint_storage(adscl_ctx *ctx, int64_t *bytes, int32_t *buffers, int64_t *segments,
+                                   int64_t *recomputed)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    if (bytes) *bytes = (int64_t)ctx->adj_stage_bufs * (int64_t)ctx->adj_stage_doubles * (int64_t)sizeof(double);
+    if (buffers) *buffers = ctx->adj_stage_bufs;
+    if (segments) *segments = ctx->adj_segments;
+    if (recomputed) *recomputed = ctx->adj_recomputed;
+    return ADSCL_OK;
+}
 
 adscl_status adscl_get_shape(adscl_ctx *ctx, int32_t inst, int32_t *P, int32_t *NT, int32_t *CL)
 {

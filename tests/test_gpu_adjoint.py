@@ -119,7 +119,9 @@ def test_stage_storage_modes_agree(ad, orc, bufs):
     a = rng.uniform(0.0, 0.8, (B, K)) * np.exp(-np.arange(K) / 2.0)
     s = ad.Solver([N] * B, ko_sigma=0.5, spec_J=Jm, ckpt_every=9, adjoint_stage_buffers=bufs)
     dt, _ = s.clock()
+    assert s.adjoint_storage() == (0, 0, 0, 0)
     J, g = s.grad(a, n * dt[0])
+    assert s.adjoint_storage()[2:] == (5, 0 if bufs == 0 else 5)   # phase F recomputes every segment
     for b in (0, 2):
         Jo, go = orc.grad(a[b], N, n, dt[0], sigma=0.5, Jm=Jm)
         assert abs(J[b] - Jo) <= 1e-10 * abs(Jo)
@@ -141,9 +143,9 @@ def test_stage_storage_modes_agree(ad, orc, bufs):
 def test_recording_forward_pass_for_batches_filling_the_gpu(ad, orc, extra):
     """A batch with at least one evolution CTA per SM records its stages in the evolution
     kernel's stage-recording variant: with a buffer per segment the forward pass writes them all
-    in one launch; with a cap of one or two buffers the forward pass writes the last segment and
-    each earlier one is recomputed from its checkpoint on a second slice before its sweep.  A
-    quarter of that on the default one-CTA shapes runs these passes on 4-CTA clusters.  The three storage modes give the same gradients up to rounding and the
+    in one launch; with a cap of one or two buffers the forward pass writes the last one or two
+    segments and each earlier one is recomputed from its checkpoint on a second slice before its
+    sweep.  A quarter of that on the default one-CTA shapes runs these passes on 4-CTA clusters.  The three storage modes give the same gradients up to rounding and the
     oracle's adjoint, and each leaves the context on the final slice."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -162,6 +164,9 @@ def test_recording_forward_pass_for_batches_filling_the_gpu(ad, orc, extra):
             ref.evolve(n * dt[0])
         out[bufs] = s.grad(a, n * dt[0])
         assert np.all(s.clock()[1] == n)
+        nbytes, nbuf, nseg, nrecomp = s.adjoint_storage()
+        assert nseg == 3 and nrecomp == {0: 0, 1: 2, 2: 1}[bufs]
+        assert nbuf == (3 if bufs == 0 else bufs) and nbytes == nbuf * B * 9 * 4 * 6 * N * 8
         for k, b in enumerate((0, B - 1)):   # the context ends on the final slice
             x, y = s.get_state(b), ref.get_state(k)
             if extra == 5:   # same shape: the recording variant does the same arithmetic
