@@ -63,6 +63,8 @@ def test_invalid_configs_rejected_before_device_work():
     # null context handling of the query functions
     assert lib.adscl_launch_count(None) == 0
     assert lib.adscl_last_error(None) == b"null context"
+    assert lib.adscl_adjoint_storage(None, None, None, None, None) == adscl.ADSCL_EINVAL
+    assert lib.adscl_get_clock(None, None, None) == adscl.ADSCL_EINVAL
     lib.adscl_destroy(None)
 
 
