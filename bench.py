@@ -206,6 +206,11 @@ def workload_insts(name, rank):
         return W.uneven(seed=1 + rank), (
             "uneven batch: B=192 per GPU, N uniform in {2049, 4097, 8193}, "
             "Pi = sum_{j<16} eps e^{-j/3}(1+0.05 N(0,1)) e_j, eps U[0.05,0.2]")
+    if name == "production":
+        return W.production(seed=4 + rank), (
+            "production resolution: B=15 Gaussian pulses per GPU at N=32769 (one 8-CTA cluster "
+            "each: the 15 that fit at once, 120 SMs), "
+            "sigma=1/16, eps log-uniform [5,80], early exit at min A < 2^-7")
     raise ValueError(name)
 
 
@@ -426,7 +431,7 @@ def main():
     ap.add_argument("--shape", default="",
                     help="P,NT,CL: run the timed batch with this kernel shape instead of tuning "
                          "(for profiling, where a profiler distorts the tuner's timings)")
-    ap.add_argument("--workload", default="amp_scan", choices=["amp_scan", "large", "uneven"],
+    ap.add_argument("--workload", default="amp_scan", choices=["amp_scan", "large", "uneven", "production"],
                     help="batch to time (the metric's workload is amp_scan)")
     ap.add_argument("--scheme", default="rk4", choices=sorted(SCHEMES),
                     help="time-stepping scheme (the metric's scheme is rk4)")
@@ -542,11 +547,11 @@ def main():
                 "peak_source": "measured FP64 FMA-chain probe on this GPU (FMA = 2 flops)",
                 "flops_per_point_substep": flops_pps, "fp64_issue": issue}
 
-    # the other two batch shapes, one launch of 128 RK4 steps each (default workload only)
+    # the other batch shapes, one launch of 128 RK4 steps each (default workload only)
     others = None
     if rank == 0 and amp and not args.no_others:
         others = {}
-        for name in ("large", "uneven"):
+        for name in ("large", "uneven", "production"):
             oi, od = workload_insts(name, 0)
             others[name] = {"value": side_rate(oi, stream, local, 128, flush), "unit": UNIT,
                             "workload": od, "rk_steps": 128}

@@ -111,6 +111,14 @@ def large(B: int = 148, N: int = 8193, seed: int = 3) -> list:
     return out
 
 
+def production(B: int = 15, N: int = 32769, seed: int = 4) -> list:
+    """Gaussian pulses at the paper's production resolution (its Table I grid of 2^15 + 1 points):
+    one 8-CTA cluster per instance; a B300 holds 15 such clusters at once (120 of its 148 SMs)."""
+    rng = np.random.default_rng(seed)
+    eps = np.exp(rng.uniform(math.log(5.0), math.log(80.0), size=B))
+    return [Instance(N=N, kind="gauss", eps=float(e), sigma=GAUSS_SIGMA) for e in eps]
+
+
 def qp_seeds(N: int = 8193, K: int = 32) -> list:
     out = []
     for kd in (3, 5):
