@@ -53,6 +53,10 @@ SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A
     "rk4": (0, 4, FLOPS_PER_POINT_SUBSTEP, 0),
     "evolved_a_rk3": (1, 3, 84.0, 64),
     "evolved_a_rk2": (2, 2, 83.5, 64),
+    # A = 1, delta = 0 held fixed (the paper's Table II case): per point-substep u = tan^2 x Phi
+    # (1), the RHS with dissipation (30), the Shu-Osher update (8 averaged over the 3 stages) and
+    # the step-end mass sum (5 per step)
+    "fixed_metric_rk3": (3, 3, 1.0 + 30.0 + 8.0 + 5.0 / 3.0, 0),
 }
 # FP64 instructions per point-substep of the bench's adjoint batch: the forward pass recorded by
 # the evolution kernel (evolve_kernel<8, 128, 4, true> over the whole window) and the adjoint
@@ -560,6 +564,7 @@ def main():
         oi, od = workload_insts("amp_scan", 0)
         v = side_rate(oi, stream, local, 128, flush, substeps=3, scheme=adscl.SCHEME_EVOLVED_A_RK3,
                       a_reint_every=64)
+        vf = side_rate(oi, stream, local, 128, flush, substeps=3, scheme=adscl.SCHEME_FIXED_METRIC_RK3)
         others["autotune"] = autotune_report(stream, local)
         others["paper_configs"] = paper_configs_report(stream, local)
         others["amp_scan_evolved_A_rk3"] = {
@@ -567,6 +572,10 @@ def main():
             "workload": od + "; evolved-A scheme, SSP-RK3, A re-integrated every 64 steps",
             "rk_steps_per_s": v / (3.0 * N_DEFAULT * B_DEFAULT),
             "rk4_steps_per_s_same_batch": value / (4.0 * N_DEFAULT * B_DEFAULT)}
+        others["amp_scan_fixed_metric_rk3"] = {
+            "value": vf, "unit": UNIT, "rk_steps": 128,
+            "workload": od + "; fixed metric A = 1, delta = 0 (no constraints), SSP-RK3",
+            "rk_steps_per_s": vf / (3.0 * N_DEFAULT * B_DEFAULT)}
 
     # one instance per launch, same workload, for the batched-vs-one-per-launch comparison
     opl = None
