@@ -168,3 +168,26 @@ def test_more_clusters_than_fit_chunk_invariance(ad):
     for a, b in zip(res[0][1], res[1][1]):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+def test_production_batch_sampled_matches_oracle(ad, orc):
+    """The bench's production-resolution batch (15 pulses at N = 32769, one 8-CTA cluster each,
+    the default chunking and shape) after 12 RK4 steps: sampled instances match the oracle."""
+    insts = W.production()
+    n = insts[0].N
+    Pi0 = W.packed([W.gaussian_pi(it.N, it.eps, it.sigma) for it in insts])
+    s = ad.Solver([it.N for it in insts], ko_sigma=0.5, collapse_threshold=2.0 ** -7)
+    assert s.shape(0) == (8, 512, 8)
+    s.set_initial(np.zeros_like(Pi0), Pi0)
+    dt, _ = s.clock()
+    tr, tc, m, st = s.evolve(12 * dt[0])
+    assert np.all(s.clock()[1] == 12)
+    for b in (0, 7, len(insts) - 1):
+        r = orc.evolve(np.zeros(n), W.gaussian_pi(n, insts[b].eps, insts[b].sigma), dt[0], 12,
+                       sigma=0.5, theta=2.0 ** -7)
+        gP, gQ, gA, gd = s.get_state(b)
+        scale = max(1.0, np.abs(r.Pi).max())
+        assert np.abs(gP - r.Phi).max() <= 1e-11 * scale and np.abs(gQ - r.Pi).max() <= 1e-11 * scale
+        assert np.abs(gA - r.A).max() <= 1e-11 and np.abs(gd - r.delta).max() <= 1e-11 * max(1.0, r.delta0)
+        assert abs(m[b] / r.mass - 1) < 1e-11
+    s.close()
