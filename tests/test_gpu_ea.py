@@ -219,3 +219,25 @@ def test_evolved_a_and_fixed_metric_without_dissipation(ad, orc, scheme):
     else:
         oP, oQ = orc.fixed_evolve(Phi, Pi, dt[0], steps, order=3, sigma=0.0)
     assert _close(gP, oP, 1e-11) and _close(gQ, oQ, 1e-11)
+
+
+def test_fixed_metric_amp_scan_full_size_sampled(ad, orc):
+    """The bench's fixed-metric line in its launch configuration: the 256-pulse amplitude scan at
+    N = 4097 on the (8, 256, 2) shape, 16 SSP-RK3 steps; sampled instances match the oracle."""
+    insts = W.amp_scan()
+    n = insts[0].N
+    Pi0 = W.packed([W.gaussian_pi(it.N, it.eps, it.sigma) for it in insts])
+    s = ad.Solver([n] * len(insts), scheme=ad.SCHEME_FIXED_METRIC_RK3, collapse_threshold=2.0 ** -7)
+    s.set_shape(n, 8, 256, 2)
+    s.set_initial(np.zeros_like(Pi0), Pi0)
+    dt, _ = s.clock()
+    s.evolve(16 * dt[0])
+    assert np.all(s.clock()[1] == 16)
+    for b in (0, 131, len(insts) - 1):
+        oP, oQ = orc.fixed_evolve(np.zeros(n), W.gaussian_pi(n, insts[b].eps, insts[b].sigma), dt[0], 16,
+                                  order=3, sigma=0.5)
+        gP, gQ, gA, gd = s.get_state(b)
+        scale = max(1.0, np.abs(oQ).max())
+        assert np.abs(gP - oP).max() <= 1e-11 * scale and np.abs(gQ - oQ).max() <= 1e-11 * scale
+        assert np.all(gA == 1.0) and np.all(gd == 0.0)
+    s.close()
