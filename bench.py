@@ -60,17 +60,18 @@ SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A
 }
 # FP64 instructions per point-substep of the bench's adjoint batch: the forward pass recorded by
 # the evolution kernel (evolve_kernel<8, 128, 4, true> over the whole window) and the adjoint
-# kernel's backward sweep (phase B, per segment), from the ncu capture in
-# profiles/adjoint_kernel_adjoint_batch.md; used only while the kernel sources are unchanged
+# kernel's backward sweep (phase B, per segment): ncu's smsp__sass_thread_inst_executed_op_d{add,
+# mul,fma}_pred_on.sum of those launches divided by their point-substeps, captured on this
+# script's adjoint leg; used only while the kernel sources are unchanged
 ADJ_ISSUE = {"sha256": "b49ef8ddd58287bc68aa2f976bf0c0a3422c882778723e5618960a1ce23df2cd",
              "forward_record": 75931385856 / 1074003968,
              "phase_B": (9518514176 + 10991304704 + 8170766336) / 268500992}
 L2_FLUSH_BYTES = 512 << 20
 CPU_SAMPLE_STEPS = 800    # oracle sample of the cpu_baseline leg: ~10 s on 16 host threads
 REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
-# DRAM bytes (read + write) of one timed evolve_kernel launch of the amplitude scan, from an ncu
-# capture of this script (profiles/evolve_kernel_amp_scan.md); reported only while the kernel
-# source and the kernel shape are the ones the counters were taken on.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one timed evolve_kernel launch of
+# the amplitude scan, from an ncu capture of this script's headline launch; reported only while
+# the kernel source and the kernel shape are the ones the counters were taken on.
 TRAFFIC = {"kernel_sha256": "52364d26489815480a94d728709e093710313c856713ba6d8d0d930713c83fb1",
            "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17575168 + 59295232,
            # FP64 instructions (DADD + DMUL + DFMA, thread level) per point-substep, same capture

@@ -253,11 +253,25 @@ adscl_status adscl_exp_neg_scaled(int32_t device, const double *X, double *y, in
  * The caller provides, as device pointers: Phi and Pi (packed B x N doubles; on entry the
  * initial slice Phi(x,0), Pi(x,0); on return the slice at t_reached), and four outputs of
  * length B (t_reached, t_collapse, mass, inst_status) with the meaning of adscl_evolve.
- * cfl, ko_sigma and collapse_threshold as in adscl_config (out_dt is 1).  All other working
- * storage is one fixed array in device memory that the library holds on every GPU where it is
- * loaded (about 1.3 MB, until the process exits), hence the limits: B <= 64 instances,
- * N <= 4097, B * N <= 65552 (16 instances of N = 4097); larger requests return
- * ADSCL_ECAPACITY and launch nothing.
+ * cfl, ko_sigma and collapse_threshold as in adscl_config (out_dt is 1).  N must satisfy the
+ * same rule as adscl_config.N: N >= 17 with (N - 1) a multiple of 8 (so N = 1001 is refused
+ * with ADSCL_EINVAL, N = 1025 is accepted).  All other working storage is one fixed array in
+ * device memory that the library holds on every GPU where it is loaded (about 1.3 MB, until the
+ * process exits), hence the limits: B <= 64 instances, N <= 4097, B * N <= 65552 (16 instances
+ * of N = 4097); larger requests return ADSCL_ECAPACITY.
+ *
+ * Every argument check (ADSCL_EINVAL, ADSCL_ECAPACITY) happens before anything is queued: a
+ * refused call leaves Phi, Pi and the outputs untouched.  ADSCL_EINVAL covers a null pointer,
+ * a bad device ordinal, N outside the rule above, cfl outside (0, 2], ko_sigma outside
+ * [0, 10), a non-finite threshold, and t_end negative, non-finite or so long that the step
+ * count overflows the 32-bit work queue (beyond about 2^27 / B RK4 steps).
+ *
+ * Differences from the allocating path: the geometry tables are computed on the device with
+ * CUDA's sin, cos and tan (adscl_create computes them on the host with the C library), so the
+ * two paths can differ in the last bit of a table entry and the fields agree to rounding rather
+ * than bit for bit.  An instance whose initial slice holds NaN or Inf (adscl_set_initial
+ * rejects such a batch with ADSCL_ENONFINITE) is reported here with inst_status
+ * ADSCL_INST_NONFINITE at t_reached = 0, and the other instances evolve normally.
  *
  * The work is queued on `stream` (a cudaStream_t, NULL = legacy default) and the call returns
  * without waiting; read the outputs after synchronising that stream.  The first call on a

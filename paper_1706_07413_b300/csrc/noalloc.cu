@@ -100,6 +100,30 @@ __global__ void noalloc_geometry_kernel(double *t, int N, double sigma)
     }
 }
 
+// The per-call records, written on the device from values passed by value (no host copy):
+// instance b of the batch is the template `d` at offset b N; work item b runs instance b; the
+// instance records start at zero (step 0, status RUNNING); one geometry table set.
+__global__ void noalloc_records_kernel(InstDesc d, GeoTab g, int B, int N, InstDesc *desc,
+                                       int32_t *order, GeoTab *geo, InstState *st)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0) *geo = g;
+    if (b >= B) return;
+    InstDesc e = d;
+    e.off = (int64_t)b * N;
+    desc[b] = e;
+    order[b] = b;
+    InstState z;
+    z.step = 0;
+    z.t_c = 0.0;
+    z.minA = 0.0;
+    z.mass = 0.0;
+    z.delta0 = 0.0;
+    z.status = kRunning;
+    z.pad = 0;
+    st[b] = z;
+}
+
 __global__ void noalloc_exptab_kernel(double *tab)
 {
     const int j = threadIdx.x;
@@ -146,6 +170,17 @@ extern "C" adscl_status adscl_evolve_noalloc(int32_t device, void *stream_, int3
         return ADSCL_EINVAL;
     // fixed capacity of the scratch array
     if (B < 1 || B > kNaMaxB || N > kNaMaxN || (long long)B * N > kNaMaxPts) return ADSCL_ECAPACITY;
+    // time step and the queue's round count, checked in floating point before any integer
+    // conversion and before anything is queued (a t_end too long for the 32-bit ticket counter
+    // is rejected here)
+    constexpr int kChunk = 16;
+    const double h = 0.5 * M_PI / (double)(N - 1);
+    const double cad = 1.0;
+    const double dt = cad / std::ceil(cad / (lam * h));
+    const double n_end_d = std::ceil(t_end / dt - 1e-9);
+    const double rounds_d = std::floor(n_end_d / kChunk) + 2.0;
+    if (!(rounds_d * (double)B <= (double)0x7ffffff0)) return ADSCL_EINVAL;
+    const int32_t rounds = (int32_t)rounds_d;
 
     double *base = nullptr;
     adscl_status st = setup_device(device, &base);
@@ -165,20 +200,12 @@ extern "C" adscl_status adscl_evolve_noalloc(int32_t device, void *stream_, int3
     int32_t *d_order = (int32_t *)(rec + kRecOrder);
     double *geo = base + kOffGeo;
 
-    // small host records (stack only), copied into the scratch array on the caller's stream
-    const double h = 0.5 * M_PI / (double)(N - 1);
-    const double cad = 1.0;
-    const double dt = cad / std::ceil(cad / (lam * h));
-    InstDesc desc[kNaMaxB];
-    int32_t order[kNaMaxB];
-    for (int b = 0; b < B; ++b) {
-        InstDesc &d = desc[b];
-        d.N = N;
-        d.geo = 0;
-        d.off = (int64_t)b * N;
-        set_desc_coeffs(d, h, dt, ko_sigma);
-        order[b] = b;
-    }
+    // the instance template (every instance of the batch has the same grid and step)
+    InstDesc desc{};
+    desc.N = N;
+    desc.geo = 0;
+    desc.off = 0;
+    set_desc_coeffs(desc, h, dt, ko_sigma);
     const size_t S = (size_t)geo_stride(N);
     GeoTab g;
     g.ws = geo;
@@ -192,11 +219,8 @@ extern "C" adscl_status adscl_evolve_noalloc(int32_t device, void *stream_, int3
     g.iT12k = geo + 8 * S;
 
 #define NA_CK(call) do { if ((call) != cudaSuccess) return ADSCL_ECUDA; } while (0)
-    NA_CK(cudaMemcpyAsync(d_desc, desc, sizeof(InstDesc) * B, cudaMemcpyHostToDevice, stream));
-    NA_CK(cudaMemcpyAsync(d_order, order, sizeof(int32_t) * B, cudaMemcpyHostToDevice, stream));
-    NA_CK(cudaMemcpyAsync(d_geo, &g, sizeof g, cudaMemcpyHostToDevice, stream));
-    // the instance records start at zero: step 0, status RUNNING
-    NA_CK(cudaMemsetAsync(d_st, 0, sizeof(InstState) * B, stream));
+    noalloc_records_kernel<<<1, kNaMaxB, 0, stream>>>(desc, g, B, N, d_desc, d_order, d_geo, d_st);
+    NA_CK(cudaGetLastError());
     noalloc_exptab_kernel<<<1, kExpTableSize, 0, stream>>>(base + kOffExp);
     NA_CK(cudaGetLastError());
     noalloc_geometry_kernel<<<(N + 255) / 256, 256, 0, stream>>>(geo, N, ko_sigma);
@@ -213,7 +237,7 @@ extern "C" adscl_status adscl_evolve_noalloc(int32_t device, void *stream_, int3
     a.aPi = base + kOffAccQ;
     a.order = d_order;
     a.nwork = B;
-    a.chunk = 16;
+    a.chunk = kChunk;
     a.ctl = d_ctl;
     a.rounds = d_rounds;
     a.max_spin = (long long)1 << 24;
@@ -234,10 +258,7 @@ extern "C" adscl_status adscl_evolve_noalloc(int32_t device, void *stream_, int3
     NA_CK(cudaGetLastError());
     // 2) evolution to t_end or collapse (as adscl_evolve)
     a.mode = kModeEvolve;
-    const long long n_end = (long long)std::ceil(t_end / dt - 1e-9);
-    const long long rounds = n_end / a.chunk + 2;
-    if ((long long)B * rounds > 0x7ffffff0LL) return ADSCL_EINVAL;
-    a.max_rounds = (int32_t)rounds;
+    a.max_rounds = rounds;
     queue_init_kernel<<<1, 256, 0, stream>>>(d_ctl, d_rounds, B, grid);
     NA_CK(cudaGetLastError());
     evolve_kernel<kNaP, kNaNT><<<grid, kNaNT, smem, stream>>>(a, stride);

@@ -98,3 +98,42 @@ def test_noalloc_rejects_requests_beyond_its_capacity(ad):
         assert rc == ad.ADSCL_ECAPACITY
         torch.cuda.synchronize()
         assert float(Pi.min()) == 1.0 and float(Phi.abs().max()) == 0.0   # nothing ran
+
+
+def test_noalloc_refuses_bad_arguments_before_queuing_anything(ad):
+    """A refused call (bad N, or a t_end whose step count the work queue cannot hold) returns
+    ADSCL_EINVAL with the caller's fields and outputs untouched."""
+    import torch
+    dev = torch.device("cuda", 0)
+    for B, N, t_end in ((4, 1001, 0.1), (4, 129, 1e300), (64, 4097 // 8 + 1, 4.0e6), (2, 129, -1.0),
+                        (2, 129, float("nan"))):
+        Phi = torch.zeros(B * N, dtype=torch.float64, device=dev)
+        Pi = torch.ones(B * N, dtype=torch.float64, device=dev)
+        outs = [torch.full((B,), 7.0, dtype=torch.float64, device=dev) for _ in range(3)]
+        outs.append(torch.full((B,), 7, dtype=torch.int32, device=dev))
+        torch.cuda.synchronize()
+        rc = ad.evolve_noalloc(Phi, Pi, N, t_end, *outs)
+        assert rc == ad.ADSCL_EINVAL, (B, N, t_end, rc)
+        torch.cuda.synchronize()
+        assert float(Pi.min()) == 1.0 and float(Pi.max()) == 1.0 and float(Phi.abs().max()) == 0.0
+        for o in outs:
+            assert bool((o == 7).all())
+
+
+def test_noalloc_reports_a_nonfinite_instance_and_evolves_the_others(ad):
+    """An instance whose initial slice holds a NaN is reported NONFINITE at t = 0; the other
+    instances of the batch match the allocating path run without it."""
+    N = 513
+    fields = [W.smooth_random(N, seed=900 + i, amp=2.0) for i in range(3)]
+    Phi0 = W.packed([f[0] for f in fields])
+    Pi0 = W.packed([f[1] for f in fields])
+    t_end = 0.5
+    ref = _allocating_path(ad, N, Phi0, Pi0, t_end)
+    bad_Pi = Pi0.copy()
+    bad_Pi[N + N // 3] = np.nan                          # instance 1, an interior node
+    got = _noalloc_path(ad, N, Phi0, bad_Pi, t_end)
+    assert got[3][1] == ad.NONFINITE and got[0][1] == 0.0
+    keep = [0, 2]
+    sl = np.concatenate([np.arange(b * N, (b + 1) * N) for b in keep])
+    _compare(tuple(x[keep] for x in ref[:4]) + (ref[4][sl], ref[5][sl]),
+             tuple(x[keep] for x in got[:4]) + (got[4][sl], got[5][sl]))
