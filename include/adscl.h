@@ -98,6 +98,9 @@ typedef struct {
                                     recomputation of one segment run beside the backward sweep
                                     of the next; else 1) */
     void *stream;                /* cudaStream_t for all work; NULL = the legacy default stream */
+    int32_t spectrum_chunks;     /* tensor-core spectrum: 64-point K chunks per FP32
+                                    accumulation run (one CTA task); 0 = 1, the most accurate
+                                    (see adscl_spectrum for the error bound) */
 } adscl_config;
 
 /* Largest grid size N one instance may use with this library: 32769.  Grids up to 4097 run on one
@@ -143,12 +146,42 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
  * Output E: B x J row-major.  A is recomputed from the current slice (no state change).
  * precision: ADSCL_PREC_FP64 (FP64 CUDA cores), ADSCL_PREC_BF16X3 or ADSCL_PREC_TF32X3: the
  * projections on the tensor cores (tcgen05) with each operand split into a rounded high part
- * and a rounded remainder (BF16 or TF32), three products hi*hi + hi*lo + lo*hi, FP32
- * accumulation.  Accuracy: max_j |E_j - E_j(FP64)| <= 5e-5 M (measured ~1e-5 M); small E_j are
- * not relatively accurate.  ADSCL_ETIMEOUT if a bounded wait of the tensor-core kernel ran out
- * (host pointers only). */
+ * and a rounded remainder (BF16 or TF32), three products hi*hi + hi*lo + lo*hi, hi*hi and the
+ * two corrections accumulated in FP32 in separate accumulators over runs of
+ * cfg.spectrum_chunks x 64 grid points, partial sums added in FP64.  Accuracy (derived, M the
+ * mass of the slice): max_j |E_j - E_j(FP64)| <= 2 eps M with
+ * eps = 3 2^-2p (1 + 2^-p) + c n 2^-23 (1 + 2^{1-p}), p = 8 (BF16) or 11 (TF32) bits, n = 4
+ * (BF16) or 8 (TF32) MMA instructions per 64 points, c = spectrum_chunks: at c = 1,
+ * 9.3e-5 M (BF16x3) and 3.4e-6 M (TF32x3).  Small E_j are not relatively accurate.
+ * ADSCL_ETIMEOUT if a bounded wait of the tensor-core kernel ran out (host pointers only). */
 enum { ADSCL_PREC_FP64 = 0, ADSCL_PREC_BF16X3 = 1, ADSCL_PREC_TF32X3 = 2 };
 adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E, int ptr_is_device);
+
+/* Two of the three quantities the two-time-framework (TTF) equations conserve, from the mode
+ * energies E_j (j < J) of every instance's current slice (Sec. II: the normal-mode decomposition
+ * provides the conserved quantities of the TTF formalism; the temperature quoted for the
+ * quasi-periodic data after Eq. (eq:approxQP) is their ratio):
+ *   ttf[3b + 0] = E = sum_{j<J} E_j          (total energy; equals the mass M as J grows),
+ *   ttf[3b + 1] = N = sum_{j<J} E_j / omega_j (particle number, omega_j = 3 + 2j),
+ *   ttf[3b + 2] = T = E / N                   (temperature),
+ * summed in order of j in FP64 from the E_j of adscl_spectrum with the same J and precision.
+ * The third conserved quantity, the TTF Hamiltonian, needs interaction coefficients that the
+ * paper does not give; it is not provided.  E: optional (NULL or B x J), receives the mode
+ * energies.  Errors as adscl_spectrum. */
+adscl_status adscl_ttf(adscl_ctx *ctx, int32_t J, int precision, double *ttf, double *E, int ptr_is_device);
+
+/* Track the spectrum in time (Sec. II: the evolving solution is decomposed into normal modes at
+ * any time): for k = 0 .. n_snap-1, evolve to t_k = t_first + k cadence exactly as adscl_evolve
+ * does (per-instance stop at collapse), then take the mode energies (adscl_spectrum) and the TTF
+ * quantities (adscl_ttf) of every instance's current slice.  Outputs (each optional, row k of
+ * snapshot k): t_hist (n_snap x B) the time of the slice each instance is on (an instance that
+ * collapsed stays on its last slice), ttf_hist (n_snap x B x 3), E_hist (n_snap x B x J).  Steps
+ * land on the snapshot times when cadence is a multiple of the context's out_dt.  With host
+ * pointers the history is gathered in a temporary device buffer, copied once at the end, and
+ * the call reports ADSCL_ETIMEOUT if a device wait ran out (as adscl_evolve). */
+adscl_status adscl_track(adscl_ctx *ctx, double t_first, double cadence, int32_t n_snap, int32_t J,
+                         int precision, double *t_hist, double *ttf_hist, double *E_hist,
+                         int ptr_is_device);
 
 /* Discrete-adjoint gradient of the mode-energy drift functional (Sec. II spectrum; the
  * functional and the adjoint are not in the paper):  for every instance, with

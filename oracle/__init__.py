@@ -13,6 +13,11 @@ it with gcc and marshals numpy arrays through ctypes.  Parity status of each fun
 - ``eigen``, ``spectrum``, ``synthesize``: pinned by the hypergeometric closed form at high
   precision, Gauss-Legendre orthonormality, the eigen-equation and the paper's printed
   temperatures (tests/test_oracle_eigen.py).
+- ``ttf`` (total energy, particle number, temperature): pinned by single-mode data
+  (T = omega_j), the paper's printed temperatures reached through synthesis, constraint solve
+  and spectrum, the total energy equal to the mass, exact conservation of every mode energy by
+  the linear (fixed-metric) evolution up to truncation error, and the O(eps^2) drift of the
+  particle number under the full scheme (tests/test_oracle_ttf.py).
 - collapse time: the detection rule is pinned by invariants; the value itself is
   "parity unpinned" (the paper prints no collapse time).
 """
@@ -64,6 +69,8 @@ def lib():
         _lib.orc_eigen.restype = None
         _lib.orc_spectrum.argtypes = [I, I, D, D, D, D, D, D]
         _lib.orc_spectrum.restype = None
+        _lib.orc_ttf.argtypes = [I, D, D]
+        _lib.orc_ttf.restype = None
         _lib.orc_synthesize.argtypes = [I, I, D, D, D]
         _lib.orc_synthesize.restype = None
         _lib.orc_constraints_vjp.argtypes = [I, D, D, D, D, D, D]
@@ -238,6 +245,16 @@ def spectrum(Phi, Pi, A, J):
     return E, pj, fj
 
 
+def ttf(E):
+    """(E, N, T) of one slice from its mode energies E_j: total energy, particle number
+    sum_j E_j / omega_j and temperature E / N (the two TTF conserved quantities fixed by the
+    spectrum, and their ratio)."""
+    E = _f64(E)
+    out = np.empty(3)
+    lib().orc_ttf(E.size, _p(E), _p(out))
+    return out
+
+
 def synthesize(N, a):
     """Pi(x,0) = sum_j a_j e_j(x), Phi(x,0) = 0."""
     a = _f64(a)
@@ -303,10 +320,9 @@ def functional(a, N, nsteps, dt, sigma=0.5, Jm=32):
 
 
 def temperature_from_energies(E):
-    """T = sum_j E_j / sum_j (E_j / omega_j): energy over particle number of the modes."""
-    E = np.asarray(E, dtype=np.float64)
-    w = omega(np.arange(E.size))
-    return float(E.sum() / (E / w).sum())
+    """T = sum_j E_j / sum_j (E_j / omega_j): energy over particle number of the modes
+    (the third output of ttf)."""
+    return float(ttf(E)[2])
 
 
 def momentum_residual(A_levels, dt, Phi, Pi, A, delta):

@@ -544,6 +544,31 @@ void orc_spectrum(int N, int J, const double *Phi, const double *Pi, const doubl
     free(de);
 }
 
+/*
+ * Two of the three quantities that the two-time-framework (TTF) equations conserve (Sec. II:
+ * the normal-mode decomposition connects the evolution with perturbation theory and its three
+ * conserved quantities), written out from the mode energies of one slice:
+ *   total energy      E = sum_{j<J} E_j,
+ *   particle number   N = sum_{j<J} E_j / omega_j,   omega_j = 3 + 2j,
+ * and the temperature T = E / N, the quantity the paper quotes for its quasi-periodic initial
+ * data (it depends only on how the energy is distributed over the modes).  E_j is the energy of
+ * mode j, so E_j / omega_j is its number of quanta.  The third conserved quantity, the TTF
+ * Hamiltonian, needs the interaction coefficients of the resonant system, which the paper does
+ * not give; it is not computed.  out[0..2] = E, N, T.
+ */
+void orc_ttf(int J, const double *E, double *out)
+{
+    double e_tot = 0.0, n_tot = 0.0;
+    int j;
+    for (j = 0; j < J; ++j) {
+        e_tot += E[j];
+        n_tot += E[j] / (3.0 + 2.0 * j);
+    }
+    out[0] = e_tot;
+    out[1] = n_tot;
+    out[2] = e_tot / n_tot;
+}
+
 /* Pi(x,0) = sum_j a_j e_j(x), Phi(x,0) = 0, with the boundary values of Sec. II imposed */
 void orc_synthesize(int N, int K, const double *a, double *Phi, double *Pi)
 {

@@ -45,7 +45,8 @@ class adscl_config(ctypes.Structure):
                 ("a_reint_every", ctypes.c_int32),
                 ("adjoint_ctas", ctypes.c_int32),
                 ("adjoint_stage_buffers", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p),
+                ("spectrum_chunks", ctypes.c_int32)]
 
 
 # exported symbols and their signatures (kept in one table so tests can check the .so)
@@ -59,6 +60,8 @@ SIGNATURES = {
     "adscl_set_initial_modes": ([_VP, _VP, _I32, ctypes.c_int], ctypes.c_int),
     "adscl_evolve": ([_VP, _F, _VP, _VP, _VP, _VP, ctypes.c_int], ctypes.c_int),
     "adscl_spectrum": ([_VP, _I32, ctypes.c_int, _VP, ctypes.c_int], ctypes.c_int),
+    "adscl_ttf": ([_VP, _I32, ctypes.c_int, _VP, _VP, ctypes.c_int], ctypes.c_int),
+    "adscl_track": ([_VP, _F, _F, _I32, _I32, ctypes.c_int, _VP, _VP, _VP, ctypes.c_int], ctypes.c_int),
     "adscl_grad": ([_VP, _VP, _I32, _F, _VP, _VP, ctypes.c_int], ctypes.c_int),
     "adscl_get_state": ([_VP, _I32, _VP, _VP, _VP, _VP, ctypes.c_int], ctypes.c_int),
     "adscl_set_state": ([_VP, _I32, _VP, _VP, _I64], ctypes.c_int),
@@ -171,7 +174,7 @@ class Solver:
     def __init__(self, N, cfl=0.5, ko_sigma=0.5, collapse_threshold=2.0 ** -7, out_dt=1.0,
                  spec_J=64, ckpt_every=256, device=0, one_per_launch=False, stream=None,
                  max_device_iters=0, chunk_steps=0, direct_launch=False, scheme=0,
-                 a_reint_every=0, adjoint_ctas=0, adjoint_stage_buffers=0):
+                 a_reint_every=0, adjoint_ctas=0, adjoint_stage_buffers=0, spectrum_chunks=0):
         self.lib = load()
         self.N = np.ascontiguousarray(np.asarray(N, dtype=np.int32).ravel())
         self.B = int(self.N.size)
@@ -195,6 +198,7 @@ class Solver:
         cfg.adjoint_ctas = adjoint_ctas
         cfg.adjoint_stage_buffers = adjoint_stage_buffers
         cfg.stream = stream
+        cfg.spectrum_chunks = spectrum_chunks
         self.stream = stream
         h = ctypes.c_void_p()
         st = self.lib.adscl_create(ctypes.byref(cfg), ctypes.byref(h))
@@ -280,6 +284,27 @@ class Solver:
         E = np.empty((self.B, J))
         self._check(self.lib.adscl_spectrum(self.ctx, J, precision, E.ctypes.data, 0))
         return E
+
+    def ttf(self, J=64, precision=PREC_FP64, with_energies=False):
+        """(E, N, T) per instance (B x 3): total energy, particle number and temperature of the
+        current slices (adscl_ttf); with_energies also returns the mode energies (B x J)."""
+        q = np.empty((self.B, 3))
+        E = np.empty((self.B, J)) if with_energies else None
+        self._check(self.lib.adscl_ttf(self.ctx, J, precision, q.ctypes.data,
+                                       E.ctypes.data if E is not None else None, 0))
+        return (q, E) if with_energies else q
+
+    def track(self, t_first, cadence, n_snap, J=64, precision=PREC_FP64, energies=False):
+        """Evolve to t_first + k cadence, k < n_snap, with the spectrum and the TTF quantities of
+        every slice reached (adscl_track).  Returns (t_hist (n_snap x B), ttf_hist
+        (n_snap x B x 3), E_hist (n_snap x B x J) or None)."""
+        th = np.empty((n_snap, self.B))
+        qh = np.empty((n_snap, self.B, 3))
+        Eh = np.empty((n_snap, self.B, J)) if energies else None
+        self._check(self.lib.adscl_track(self.ctx, float(t_first), float(cadence), int(n_snap), J,
+                                         precision, th.ctypes.data, qh.ctypes.data,
+                                         Eh.ctypes.data if Eh is not None else None, 0))
+        return th, qh, Eh
 
     def grad(self, a, T):
         """(J, dJ/da) of J = sum_{j<spec_J} (E_j(T) - E_j(0))^2 for Pi(x,0) = sum_k a_k e_k."""

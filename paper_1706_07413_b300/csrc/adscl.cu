@@ -116,8 +116,11 @@ struct adscl_ctx {
     char *d_tc_ops = nullptr;          // U, V (hi, lo) per tile and mode tables (hi, lo) per group
     size_t tc_ops_bytes = 0;
     int tc_built_prec = -1;            // precision of the mode tables currently in d_tc_ops
-    float *d_tc_D = nullptr;           // 2 x tiles x tc_split x 128 x 64 partial projections
-    int tc_split = 1;                  // K splits per tile
+    double *d_tc_D = nullptr;          // 2 x tc_tasks_proj x 128 x 64 partial projections
+    int tc_chunks = 1;                 // K chunks (64 grid points each) per tensor-core task
+    int tc_tasks_proj = 0;             // tasks of one projection: sum over tiles of their splits
+    int32_t *d_tc_tile = nullptr;      // per tile: number of K splits, index of its first task
+    std::vector<int> tc_tile_split, tc_tile_first;
     TcTask *d_tc_tasks = nullptr;
     int *d_tc_err = nullptr;
     // adjoint (built on first use)
@@ -544,10 +547,11 @@ adscl_status ensure_modes(adscl_ctx *ctx)
 
 int kpad_of(int N) { return (N + kTcKC - 1) / kTcKC * kTcKC; }
 
-// E_j from the partial projections: row r of tile r / 128, partials of split q at
-// D[((proj * tiles + tile) * S + q) * 128 * 64 + (r % 128) * 64 + j], summed in FP64 over q
-__global__ void tc_energy_kernel(const float *D, int tiles, int S, const int32_t *rowinst, int rows,
-                                 int J, double *E)
+// E_j from the partial projections: row r of tile t = r / 128 has its partials (one per K split q
+// of that tile) at D[((proj * tasks_proj + first_t + q) * 128 + r % 128) * 64 + j], summed in FP64
+// in the order of q; tile[2t] = splits of tile t, tile[2t + 1] = first_t
+__global__ void tc_energy_kernel(const double *D, const int32_t *tile, int tasks_proj,
+                                 const int32_t *rowinst, int rows, int J, double *E)
 {
     // one thread per (row, mode): consecutive threads read consecutive modes of a partial row
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -555,14 +559,15 @@ __global__ void tc_energy_kernel(const float *D, int tiles, int S, const int32_t
     if (r >= rows) return;
     const int b = rowinst[r];
     if (b < 0) return;
-    const int tile = r / kTcM, row = r - tile * kTcM;
+    const int t = r / kTcM, row = r - t * kTcM;
+    const int S = tile[2 * t], first = tile[2 * t + 1];
     const size_t tileSz = (size_t)kTcM * kTcN;
-    const float *Dp = D + (size_t)tile * S * tileSz + (size_t)row * kTcN + j;
-    const float *Df = D + ((size_t)tiles + tile) * S * tileSz + (size_t)row * kTcN + j;
+    const double *Dp = D + (size_t)first * tileSz + (size_t)row * kTcN + j;
+    const double *Df = D + ((size_t)tasks_proj + first) * tileSz + (size_t)row * kTcN + j;
     double p = 0.0, f = 0.0;
     for (int q = 0; q < S; ++q) {
-        p += (double)Dp[q * tileSz];
-        f += (double)Df[q * tileSz];
+        p += Dp[q * tileSz];
+        f += Df[q * tileSz];
     }
     const double w = 3.0 + 2.0 * j;
     E[(size_t)b * J + j] = fma(p, p, f * f / (w * w));
@@ -608,14 +613,25 @@ adscl_status tc_prepare(adscl_ctx *ctx, int precision)
             CK(cudaMemcpy(ctx->d_tc_modeoff + (size_t)g * kTcN, moff.data(), kTcN * sizeof(int64_t),
                           cudaMemcpyHostToDevice));
         }
-        // K splits: about two CTAs per SM over all tiles, no split shorter than one chunk
-        int min_chunks = 1 << 30;
-        for (int t = 0; t < ctx->tc_tiles; ++t)
-            min_chunks = std::min(min_chunks, kpad_of(ctx->geoN[ctx->tc_tile_geo[t]]) / kTcKC);
-        ctx->tc_split = std::max(1, std::min(min_chunks, (2 * ctx->num_sms + 2 * ctx->tc_tiles - 1) /
-                                                             (2 * ctx->tc_tiles)));
-        const size_t ntask = 2 * (size_t)ctx->tc_tiles * ctx->tc_split;
-        CK(cudaMalloc(&ctx->d_tc_D, ntask * kTcM * kTcN * sizeof(float)));
+        // K splits: tasks of ctx->tc_chunks chunks each (the last one of a tile may be shorter)
+        ctx->tc_tile_split.assign(ctx->tc_tiles, 0);
+        ctx->tc_tile_first.assign(ctx->tc_tiles, 0);
+        std::vector<int32_t> tinfo(2 * (size_t)ctx->tc_tiles);
+        int first = 0;
+        for (int t = 0; t < ctx->tc_tiles; ++t) {
+            const int nch = kpad_of(ctx->geoN[ctx->tc_tile_geo[t]]) / kTcKC;
+            const int S = (nch + ctx->tc_chunks - 1) / ctx->tc_chunks;
+            ctx->tc_tile_split[t] = S;
+            ctx->tc_tile_first[t] = first;
+            tinfo[2 * t] = S;
+            tinfo[2 * t + 1] = first;
+            first += S;
+        }
+        ctx->tc_tasks_proj = first;
+        CK(cudaMalloc(&ctx->d_tc_tile, tinfo.size() * sizeof(int32_t)));
+        CK(cudaMemcpy(ctx->d_tc_tile, tinfo.data(), tinfo.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        const size_t ntask = 2 * (size_t)ctx->tc_tasks_proj;
+        CK(cudaMalloc(&ctx->d_tc_D, ntask * kTcM * kTcN * sizeof(double)));
         CK(cudaMalloc(&ctx->d_tc_tasks, ntask * sizeof(TcTask)));
         CK(cudaMalloc(&ctx->d_tc_err, sizeof(int)));
         const int smem = 2 * (kTcM + kTcN) * kTcKC * 4;
@@ -659,8 +675,8 @@ adscl_status tc_prepare(adscl_ctx *ctx, int precision)
         ctx->tc_built_prec = precision;
     }
     // field operands of every tile, and the task list
-    const int S = ctx->tc_split;
-    std::vector<TcTask> tasks(2 * (size_t)ctx->tc_tiles * S);
+    const size_t TP = ctx->tc_tasks_proj;
+    std::vector<TcTask> tasks(2 * TP);
     for (int t = 0; t < ctx->tc_tiles; ++t) {
         const int g = ctx->tc_tile_geo[t], n = ctx->geoN[g], kp = kpad_of(n);
         const size_t part = (size_t)kTcM * kp * esz, bpart = (size_t)kTcN * kp * esz;
@@ -686,14 +702,13 @@ adscl_status tc_prepare(adscl_ctx *ctx, int precision)
         CK(cudaGetLastError());
         ctx->launches += 2;
         char *Bg = grpB[g];
-        const int nch = kp / kTcKC;
+        const int nch = kp / kTcKC, S = ctx->tc_tile_split[t];
         for (int q = 0; q < S; ++q) {
-            const int k0 = (int)((long long)q * nch / S), k1 = (int)((long long)(q + 1) * nch / S);
-            const size_t dp = ((size_t)t * S + q) * kTcM * kTcN;
-            const size_t df = (((size_t)ctx->tc_tiles + t) * S + q) * kTcM * kTcN;
-            tasks[(size_t)t * S + q] = TcTask{U, U + part, Bg, Bg + bpart, kp, k0, k1, ctx->d_tc_D + dp};
-            tasks[((size_t)ctx->tc_tiles + t) * S + q] =
-                TcTask{U + 2 * part, U + 3 * part, Bg + 2 * bpart, Bg + 3 * bpart, kp, k0, k1, ctx->d_tc_D + df};
+            const int k0 = q * ctx->tc_chunks, k1 = std::min(nch, (q + 1) * ctx->tc_chunks);
+            const size_t ip = (size_t)ctx->tc_tile_first[t] + q, iF = TP + ip;
+            tasks[ip] = TcTask{U, U + part, Bg, Bg + bpart, kp, k0, k1, ctx->d_tc_D + ip * kTcM * kTcN};
+            tasks[iF] = TcTask{U + 2 * part, U + 3 * part, Bg + 2 * bpart, Bg + 3 * bpart, kp, k0, k1,
+                               ctx->d_tc_D + iF * kTcM * kTcN};
         }
     }
     CK(cudaMemcpyAsync(ctx->d_tc_tasks, tasks.data(), tasks.size() * sizeof(TcTask), cudaMemcpyHostToDevice,
@@ -775,7 +790,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
         cfg->spec_J > 64 || cfg->ckpt_every < 0 || cfg->max_device_iters < 0 ||
         cfg->scheme < ADSCL_SCHEME_RK4 || cfg->scheme > ADSCL_SCHEME_FIXED_METRIC_RK3 ||
         cfg->a_reint_every < 0 || cfg->adjoint_ctas < 0 || cfg->adjoint_ctas > 2 ||
-        cfg->adjoint_stage_buffers < 0)
+        cfg->adjoint_stage_buffers < 0 || cfg->spectrum_chunks < 0)
         return ADSCL_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
@@ -799,6 +814,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     ctx->reint = cfg->a_reint_every;
     ctx->adj_cl = cfg->adjoint_ctas;   // 0: chosen at the first adscl_grad
     ctx->adj_bufs_cap = cfg->adjoint_stage_buffers;
+    ctx->tc_chunks = cfg->spectrum_chunks > 0 ? cfg->spectrum_chunks : 1;
     ctx->stream = (cudaStream_t)cfg->stream;
     *out = ctx;
 
@@ -1041,14 +1057,18 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
     return ADSCL_OK;
 }
 
-adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E, int ptr_is_device)
+}  // extern "C"
+
+namespace {
+
+// Mode energies of every instance's current slice into ctx->d_E (B x J, row stride J), queued
+// on the context's stream; no copy to the caller.
+adscl_status spectrum_dev(adscl_ctx *ctx, int32_t J, int precision)
 {
-    adscl_status s = check_ctx(ctx);
-    if (s != ADSCL_OK) return s;
-    if (!E || J < 1 || J > kMaxModes) return fail(ctx, ADSCL_EINVAL, "need 1 <= J <= %d", kMaxModes);
+    if (J < 1 || J > kMaxModes) return fail(ctx, ADSCL_EINVAL, "need 1 <= J <= %d", kMaxModes);
     if (precision != ADSCL_PREC_FP64 && precision != ADSCL_PREC_BF16X3 && precision != ADSCL_PREC_TF32X3)
         return fail(ctx, ADSCL_EINVAL, "unknown precision %d", precision);
-    s = ensure_modes(ctx);
+    adscl_status s = ensure_modes(ctx);
     if (s != ADSCL_OK) return s;
     // A on the current slices (one constraint solve of every instance, no state change)
     s = launch_evolve(ctx, kModeSolve, 0.0, 0, ctx->h_order.data(), ctx->B, ctx->d_scratchA, ctx->d_scratchD, ctx->stream);
@@ -1069,7 +1089,7 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
         if (s != ADSCL_OK) return s;
         CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), ctx->stream));
         const int smem = 2 * (kTcM + kTcN) * kTcKC * (precision == ADSCL_PREC_TF32X3 ? 4 : 2);
-        const int ntask = 2 * ctx->tc_tiles * ctx->tc_split;
+        const int ntask = 2 * ctx->tc_tasks_proj;
         if (precision == ADSCL_PREC_TF32X3)
             spectrum_tc_kernel<true><<<ntask, 128, smem, ctx->stream>>>(ctx->d_tc_tasks, ctx->d_tc_err);
         else
@@ -1077,21 +1097,124 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
         CK(cudaGetLastError());
         const int rows = ctx->tc_tiles * kTcM;
         tc_energy_kernel<<<(rows * J + 255) / 256, 256, 0, ctx->stream>>>(
-            ctx->d_tc_D, ctx->tc_tiles, ctx->tc_split, ctx->d_tc_rowinst, rows, J, ctx->d_E);
+            ctx->d_tc_D, ctx->d_tc_tile, ctx->tc_tasks_proj, ctx->d_tc_rowinst, rows, J, ctx->d_E);
         CK(cudaGetLastError());
         ctx->launches += 2;
     }
+    return ADSCL_OK;
+}
+
+// after the stream has finished: did a bounded wait of the tensor-core projection run out?
+adscl_status check_tc_wait(adscl_ctx *ctx, int precision)
+{
+    if (precision == ADSCL_PREC_FP64 || !ctx->d_tc_err) return ADSCL_OK;
+    int err = 0;
+    CK(cudaMemcpy(&err, ctx->d_tc_err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) return fail(ctx, ADSCL_ETIMEOUT, "tensor-core projection: a wait ran out");
+    return ADSCL_OK;
+}
+
+// TTF quantities (E, N, T per instance, B x 3) of the energies in ctx->d_E into out (device)
+adscl_status ttf_dev(adscl_ctx *ctx, int32_t J, double *out)
+{
+    ttf_kernel<<<(ctx->B + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_E, ctx->B, J, out);
+    CK(cudaGetLastError());
+    ctx->launches += 1;
+    return ADSCL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E, int ptr_is_device)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    if (!E) return fail(ctx, ADSCL_EINVAL, "E is null");
+    s = spectrum_dev(ctx, J, precision);
+    if (s != ADSCL_OK) return s;
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CK(cudaMemcpyAsync(E, ctx->d_E, (size_t)ctx->B * J * sizeof(double), kind, ctx->stream));
     if (!ptr_is_device) {
         CK(cudaStreamSynchronize(ctx->stream));
-        if (precision != ADSCL_PREC_FP64) {
-            int err = 0;
-            CK(cudaMemcpy(&err, ctx->d_tc_err, sizeof err, cudaMemcpyDeviceToHost));
-            if (err) return fail(ctx, ADSCL_ETIMEOUT, "tensor-core projection: a wait ran out");
-        }
+        return check_tc_wait(ctx, precision);
     }
     return ADSCL_OK;
+}
+
+adscl_status adscl_ttf(adscl_ctx *ctx, int32_t J, int precision, double *ttf, double *E, int ptr_is_device)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    if (!ttf) return fail(ctx, ADSCL_EINVAL, "ttf is null");
+    s = spectrum_dev(ctx, J, precision);
+    if (s != ADSCL_OK) return s;
+    const size_t B = ctx->B;
+    double *dst = ttf;
+    if (!ptr_is_device) dst = ctx->d_out;   // 3 B doubles, free between evolve calls
+    s = ttf_dev(ctx, J, dst);
+    if (s != ADSCL_OK) return s;
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (!ptr_is_device) CK(cudaMemcpyAsync(ttf, dst, 3 * B * sizeof(double), kind, ctx->stream));
+    if (E) CK(cudaMemcpyAsync(E, ctx->d_E, B * J * sizeof(double), kind, ctx->stream));
+    if (!ptr_is_device) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        return check_tc_wait(ctx, precision);
+    }
+    return ADSCL_OK;
+}
+
+adscl_status adscl_track(adscl_ctx *ctx, double t_first, double cadence, int32_t n_snap, int32_t J,
+                         int precision, double *t_hist, double *ttf_hist, double *E_hist, int ptr_is_device)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    if (n_snap < 1 || !std::isfinite(t_first) || t_first < 0.0 || !std::isfinite(cadence) || cadence < 0.0 ||
+        (n_snap > 1 && !(cadence > 0.0)) || !std::isfinite(t_first + (n_snap - 1) * cadence))
+        return fail(ctx, ADSCL_EINVAL, "need n_snap >= 1, finite t_first >= 0 and cadence > 0");
+    if (J < 1 || J > kMaxModes) return fail(ctx, ADSCL_EINVAL, "need 1 <= J <= %d", kMaxModes);
+    if (precision != ADSCL_PREC_FP64 && precision != ADSCL_PREC_BF16X3 && precision != ADSCL_PREC_TF32X3)
+        return fail(ctx, ADSCL_EINVAL, "unknown precision %d", precision);
+    const size_t B = ctx->B;
+    const size_t nT = t_hist ? (size_t)n_snap * B : 0, nQ = ttf_hist ? (size_t)n_snap * B * 3 : 0,
+                 nE = E_hist ? (size_t)n_snap * B * J : 0;
+    // host outputs: the history is gathered in one device buffer and copied once at the end
+    double *stage = nullptr;
+    if (!ptr_is_device && nT + nQ + nE > 0) CK(cudaMalloc(&stage, (nT + nQ + nE) * sizeof(double)));
+    double *dT = ptr_is_device ? t_hist : stage, *dQ = ptr_is_device ? ttf_hist : stage + nT,
+           *dE = ptr_is_device ? E_hist : stage + nT + nQ;
+    for (int32_t k = 0; k < n_snap && s == ADSCL_OK; ++k) {
+        const double tk = t_first + k * cadence;
+        s = adscl_evolve(ctx, tk, t_hist ? dT + (size_t)k * B : nullptr, nullptr, nullptr, nullptr, 1);
+        if (s == ADSCL_OK) s = spectrum_dev(ctx, J, precision);
+        if (s == ADSCL_OK && ttf_hist) s = ttf_dev(ctx, J, dQ + (size_t)k * B * 3);
+        if (s == ADSCL_OK && E_hist) {
+            if (cudaMemcpyAsync(dE + (size_t)k * B * J, ctx->d_E, B * J * sizeof(double),
+                                cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+                s = fail(ctx, ADSCL_ECUDA, "history copy failed");
+        }
+    }
+    if (!ptr_is_device) {
+        // one copy per history the caller asked for
+        if (s == ADSCL_OK && nT && cudaMemcpyAsync(t_hist, dT, nT * sizeof(double), cudaMemcpyDeviceToHost,
+                                                   ctx->stream) != cudaSuccess)
+            s = fail(ctx, ADSCL_ECUDA, "history copy failed");
+        if (s == ADSCL_OK && nQ && cudaMemcpyAsync(ttf_hist, dQ, nQ * sizeof(double), cudaMemcpyDeviceToHost,
+                                                   ctx->stream) != cudaSuccess)
+            s = fail(ctx, ADSCL_ECUDA, "history copy failed");
+        if (s == ADSCL_OK && nE && cudaMemcpyAsync(E_hist, dE, nE * sizeof(double), cudaMemcpyDeviceToHost,
+                                                   ctx->stream) != cudaSuccess)
+            s = fail(ctx, ADSCL_ECUDA, "history copy failed");
+        const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (stage) cudaFree(stage);
+        if (s != ADSCL_OK) return s;
+        if (e != cudaSuccess) return fail(ctx, ADSCL_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+        s = check_tc_wait(ctx, precision);
+        if (s != ADSCL_OK) return s;
+        return check_timeout(ctx);
+    }
+    return s;
 }
 
 namespace {
@@ -1893,7 +2016,7 @@ void adscl_destroy(adscl_ctx *ctx)
                     ctx->d_tc_rowinst, ctx->d_tc_modeoff, ctx->d_tc_ops, ctx->d_tc_D,
                     ctx->d_tc_tasks, ctx->d_tc_err, ctx->d_lam, ctx->d_adj_scr, ctx->d_adj_stage,
                     ctx->d_ck, ctx->d_adj_small, ctx->d_adj_queue, ctx->d_A, ctx->d_ea_block, ctx->d_adj_spec,
-                    ctx->d_eageo, ctx->d_rPhi, ctx->d_rPi, ctx->d_rSt};
+                    ctx->d_eageo, ctx->d_rPhi, ctx->d_rPi, ctx->d_rSt, ctx->d_tc_tile};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ctx->evo_exec) cudaGraphExecDestroy(ctx->evo_exec);

@@ -88,4 +88,26 @@ __global__ void spectrum_fp64_kernel(const InstDesc *desc, const EigTab *eig, co
     }
 }
 
+// Two of the three quantities conserved by the two-time-framework (TTF) equations, from the
+// mode energies of each instance (one thread per instance): the total energy E = sum_j E_j and
+// the particle number N = sum_j E_j / omega_j (E_j / omega_j: the quanta in mode j), with the
+// temperature T = E / N (Sec. II quotes T for its quasi-periodic data).  Summed in order of j.
+// out[3b + 0..2] = E, N, T.  The third TTF quantity needs interaction coefficients the paper
+// does not give.
+__global__ void ttf_kernel(const double *E, int B, int J, double *out)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double *e = E + (size_t)b * J;
+    double et = 0.0, nt = 0.0;
+    for (int j = 0; j < J; ++j) {
+        const double v = e[j];
+        et += v;
+        nt += v / (3.0 + 2.0 * j);
+    }
+    out[3 * b] = et;
+    out[3 * b + 1] = nt;
+    out[3 * b + 2] = et / nt;
+}
+
 }  // namespace adscl

@@ -2,15 +2,27 @@
 // of spectrum.cuh on the 5th-generation tensor cores (tcgen05), as dense products
 //   D[instance, j] = sum_k U[instance, k] B[j, k],   128 instances x 64 modes per CTA,
 // with split operands: each FP64 value is written as hi + lo (hi = the value rounded to BF16 or
-// TF32, lo = the rounded remainder) and D = Uhi Bhi + Uhi Blo + Ulo Bhi, accumulated in FP32 in
-// tensor memory.  The dropped term Ulo Blo and the remainders are ~2^-16 (BF16) or ~2^-22 (TF32)
-// of each product, so the projection carries a relative error of that order on top of FP32
-// accumulation; E_j is then formed in FP64 from the FP32 projections.
+// TF32, lo = the rounded remainder), and D = Uhi Bhi + (Uhi Blo + Ulo Bhi).  The two parts are
+// accumulated in FP32 in two separate tensor-memory accumulators (columns 0..63: hi*hi; columns
+// 64..127: the two correction products) and added in FP64 in the epilogue.
 //
-// Split K: a task covers K chunks [k0, k1) of one 128 x 64 tile and writes its FP32 partial
-// product; the partials of a tile are summed in FP64, in a fixed order, by the energy kernel
-// (the grid then has about two CTAs per SM instead of one per tile, and the FP32 sums run over
-// at most a few chunks).
+// Error of one projection P = sum_k u_k b_k over the K range of a task (p = 8 bits for BF16,
+// 11 for TF32; L1 = sum_k |u_k b_k|):
+//   - split: u = hi + lo + d with |d| <= 2^-2p |u|; the dropped terms lo*lo, hi*db, lo*db, du*b
+//     add at most 3 2^-2p |u_k b_k| per term, 3 2^-2p L1 in all;
+//   - accumulation: every MMA instruction adds its products to an FP32 accumulator; each such
+//     accumulation is taken to err by at most one unit in the last place of the running sum
+//     (2^-23 relative: the tensor cores' FP32 accumulation is not guaranteed to round to
+//     nearest).  The hi*hi accumulator takes n_hh = (64 / k) accumulations per 64-element chunk
+//     (k = 16 per BF16 instruction, 8 per TF32 instruction), so it errs by <= n_hh 2^-23 L1; the
+//     correction accumulator holds values ~2^-p smaller and errs by <= 2 n_hh 2^{-p-23} L1.
+//   One accumulator for all three products, as an earlier version had, takes 3 n_hh FP32
+//   accumulations of the full-size sum per chunk; with several chunks per task that error grows
+//   with the run length and dominated: it is why TF32 x3 (twice the instructions per chunk)
+//   measured worse than BF16 x3 in that version.
+// Split K: every task covers `chunks` 64-element K chunks of one 128 x 64 tile (1 by default,
+// the shortest FP32 run) and writes its FP64 partial product; the partials of a tile are summed
+// in FP64, in a fixed order, by the energy kernel.
 //
 // Data path per CTA (128 threads): for each 64-element K chunk the four operand tiles (U hi/lo:
 // 128 rows, B hi/lo: 64 rows) are copied from global memory into shared memory in the
@@ -37,7 +49,7 @@ struct TcTask {
     const void *Bhi, *Blo;  // kTcN x Kpad
     int Kpad;               // row length, a multiple of kTcKC
     int k0, k1;             // K chunks [k0, k1) of this task (k1 > k0)
-    float *D;               // kTcM x kTcN partial product over those chunks
+    double *D;              // kTcM x kTcN partial product over those chunks
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -82,6 +94,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
     return ok != 0;
 }
 
+// 16 consecutive FP32 accumulator columns of this warp's 32 lanes (completed by tcgen05.wait::ld)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+
 // copy rows [0, rows) x K chunk kc of a row-major operand into the core-matrix layout
 template <int ES>
 __device__ __forceinline__ void stage_tile(char *dst, const char *src, int rows, int Kpad, int kc) {
@@ -119,9 +141,9 @@ __global__ void __launch_bounds__(128) spectrum_tc_kernel(const TcTask *tasks, i
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar_addr) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 0) {   // two accumulators of kTcN columns: hi*hi, and the corrections
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&tmem_slot)), "r"(kTcN) : "memory");
+                     :: "r"(smem_u32(&tmem_slot)), "r"(2 * kTcN) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -146,8 +168,8 @@ __global__ void __launch_bounds__(128) spectrum_tc_kernel(const TcTask *tasks, i
                 const uint32_t o = s * 256;  // two K-adjacent core matrices per instruction
                 const uint32_t acc0 = (kc > t.k0 || s > 0) ? 1u : 0u;
                 tc_mma<kTf32>(tmem, make_smem_desc(ahi + o, 128, sboA), make_smem_desc(bhi + o, 128, sboB), kIdesc, acc0);
-                tc_mma<kTf32>(tmem, make_smem_desc(ahi + o, 128, sboA), make_smem_desc(blo + o, 128, sboB), kIdesc, 1u);
-                tc_mma<kTf32>(tmem, make_smem_desc(alo + o, 128, sboA), make_smem_desc(bhi + o, 128, sboB), kIdesc, 1u);
+                tc_mma<kTf32>(tmem + kTcN, make_smem_desc(ahi + o, 128, sboA), make_smem_desc(blo + o, 128, sboB), kIdesc, acc0);
+                tc_mma<kTf32>(tmem + kTcN, make_smem_desc(alo + o, 128, sboA), make_smem_desc(bhi + o, 128, sboB), kIdesc, 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(mbar_addr) : "memory");
@@ -170,28 +192,26 @@ __global__ void __launch_bounds__(128) spectrum_tc_kernel(const TcTask *tasks, i
         if (threadIdx.x == 0) atomicExch(err, 1);
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // warp w reads accumulator lanes 32w .. 32w+31 (= tile rows), columns 0 .. 63
+        // warp w reads accumulator lanes 32w .. 32w+31 (= tile rows), columns 0 .. 63 of both
+        // accumulators, and writes their sum in FP64
         const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16);
-        float *drow = t.D + (size_t)(32 * warp + lane) * kTcN;
+        double *drow = t.D + (size_t)(32 * warp + lane) * kTcN;
 #pragma unroll
         for (int c = 0; c < kTcN; c += 16) {
-            uint32_t r[16];
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                           "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                           "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                         : "r"(base + c));
+            uint32_t r[16], q2[16];
+            tc_ld16(base + c, r);
+            tc_ld16(base + kTcN + c, q2);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int q = 0; q < 16; ++q) drow[c + q] = __uint_as_float(r[q]);
+            for (int q = 0; q < 16; ++q)
+                drow[c + q] = (double)__uint_as_float(r[q]) + (double)__uint_as_float(q2[q]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * kTcN) : "memory");
     }
 }
 
