@@ -10,8 +10,10 @@ actually taken, over the device time of the timed launches).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun every rank evolves its own batch (seed = rank): weak scaling, no collective on
-the data path; rank 0 prints the max-over-ranks timing.
+Under torchrun the workload is one batch of B x world instances (one seed), split over the ranks
+by longest-processing-time first on the estimated work (N x RK4 steps to the job's end): every
+rank evolves its share (B instances of the amplitude scan), no collective on the data path
+(weak scaling); rank 0 gathers the per-instance results and prints the max-over-ranks timing.
 """
 from __future__ import annotations
 
@@ -196,27 +198,36 @@ def batch_fields(insts, sol):
         sol.set_initial(np.zeros_like(Pi0), Pi0)
 
 
-def workload_insts(name, rank):
-    if name == "amp_scan":
-        return W.amp_scan(B=B_DEFAULT, N=N_DEFAULT, seed=rank), (
-            f"amplitude scan: B={B_DEFAULT} Gaussian pulses per GPU, N={N_DEFAULT}, sigma=1/16, "
-            "eps log-uniform [5,80], RK4 dt=0.5dx, constraints every substep, early exit at "
-            "min A < 2^-7")
-    if name == "large":
-        return W.large(seed=3 + rank), (
-            "large grids: B=148 per GPU at N=8193 (2-CTA clusters), half Gaussian pulses "
-            "(sigma U[1/32,1/8], eps log-uniform [5,80]), half two-mode data, early exit at "
-            "min A < 2^-7")
-    if name == "uneven":
-        return W.uneven(seed=1 + rank), (
-            "uneven batch: B=192 per GPU, N uniform in {2049, 4097, 8193}, "
-            "Pi = sum_{j<16} eps e^{-j/3}(1+0.05 N(0,1)) e_j, eps U[0.05,0.2]")
-    if name == "production":
-        return W.production(seed=4 + rank), (
-            "production resolution: B=15 Gaussian pulses per GPU at N=32769 (one 8-CTA cluster "
-            "each: the 15 that fit at once, 120 SMs), "
-            "sigma=1/16, eps log-uniform [5,80], early exit at min A < 2^-7")
-    raise ValueError(name)
+# per-GPU batch of every workload: (generator, instances per GPU, seed, job end time t_end)
+WORKLOADS = {"amp_scan": (W.amp_scan, B_DEFAULT, 0, 100.0), "large": (W.large, 148, 3, 200.0),
+             "uneven": (W.uneven, 192, 1, 200.0), "production": (W.production, 15, 4, 500.0)}
+
+
+def workload_insts(name, rank, world=1):
+    """This rank's share of the workload's global batch (B x world instances, one seed), the
+    share's indices in the global batch, and the workload's description."""
+    from paper_1706_07413_b300 import shard
+    gen, B, seed, t_end = WORKLOADS[name]
+    glob = gen(B=B * world, seed=seed)
+    if world == 1:
+        idx = list(range(len(glob)))
+    else:
+        idx = shard.partition(shard.instance_work([it.N for it in glob], t_end), world)[rank]
+    insts = [glob[i] for i in idx]
+    desc = {
+        "amp_scan": (f"amplitude scan: B={B_DEFAULT} Gaussian pulses per GPU, N={N_DEFAULT}, "
+                     "sigma=1/16, eps log-uniform [5,80], RK4 dt=0.5dx, constraints every "
+                     "substep, early exit at min A < 2^-7"),
+        "large": ("large grids: B=148 per GPU at N=8193 (2-CTA clusters), half Gaussian pulses "
+                  "(sigma U[1/32,1/8], eps log-uniform [5,80]), half two-mode data, early exit "
+                  "at min A < 2^-7"),
+        "uneven": ("uneven batch: B=192 per GPU, N uniform in {2049, 4097, 8193}, "
+                   "Pi = sum_{j<16} eps e^{-j/3}(1+0.05 N(0,1)) e_j, eps U[0.05,0.2]"),
+        "production": ("production resolution: B=15 Gaussian pulses per GPU at N=32769 (one "
+                       "8-CTA cluster each: the 15 that fit at once, 120 SMs), sigma=1/16, eps "
+                       "log-uniform [5,80], early exit at min A < 2^-7"),
+    }[name]
+    return insts, idx, desc
 
 
 def side_rate(insts, stream, local, rk_steps, flush, substeps=4, tune=True, **kw):
@@ -330,15 +341,13 @@ def paper_configs_report(stream, local, steps=64):
     return out
 
 
-def run_full_job(args, sol, insts, wl_desc, stages, shapes, stream, ws, rank, dist):
-    """The whole job: every instance from t = 0 to args.full_job (or its collapse) in evolve
-    calls of one time unit; wall time on the host clock, device-resident fields.  Unless the
-    shapes are pinned, autotune is called after every unit of t: its choice is cached per
-    number of running instances (a half-octave bucket), so it re-tunes only when collapses
-    have thinned the batch enough (the time of those tunings is part of the job)."""
+def full_job(sol, B, stages, stream, T, retune, dist=None):
+    """The whole job: every instance from its current slice to t = T (or its collapse) in evolve
+    calls of one time unit; wall time on the host clock, device-resident fields.  With retune,
+    autotune is called after every unit of t: its choice is cached per number of running
+    instances (a half-octave bucket), so it re-tunes only when collapses have thinned the batch
+    enough (the time of those tunings is part of the job)."""
     import torch
-    B = len(insts)
-    T = args.full_job
     outs = [torch.empty(B, dtype=torch.float64, device="cuda") for _ in range(3)] + \
         [torch.empty(B, dtype=torch.int32, device="cuda")]
     Ns = sol.N.astype(np.float64)
@@ -349,7 +358,6 @@ def run_full_job(args, sol, insts, wl_desc, stages, shapes, stream, ws, rank, di
         dist.barrier()
     t0 = time.perf_counter()
     t = 0.0
-    retune = not (args.no_autotune or args.shape)
     tunes = []
     with torch.cuda.stream(stream):
         while t < T - 1e-12:
@@ -375,15 +383,92 @@ def run_full_job(args, sol, insts, wl_desc, stages, shapes, stream, ws, rank, di
         c = torch.tensor([collapsed], dtype=torch.float64, device="cuda")
         dist.all_reduce(c)
         collapsed = int(c.item())
+    return {"t_end": T, "wall_s": wall, "point_substeps": work, "point_substeps_per_s": work / wall,
+            "collapsed": collapsed, "running_every_10": [r for r in running if r is not None],
+            "shape_changes": tunes,
+            "note": "wall time on the host clock around all evolve calls (one per unit of t)"}
+
+
+def run_full_job(args, sol, insts, wl_desc, stages, shapes, stream, ws, rank, dist):
+    """--full-job T: the whole job instead of the bench line (one JSON line)."""
+    res = full_job(sol, len(insts), stages, stream, args.full_job,
+                   not (args.no_autotune or args.shape), dist)
     if rank == 0:
-        line = {"mode": "full_job", "workload": wl_desc, "t_end": T, "instances": B * ws,
-                "n_gpus": ws, "wall_s": wall, "point_substeps": work,
-                "point_substeps_per_s": work / wall, "collapsed": collapsed,
-                "running_every_10": [r for r in running if r is not None],
-                "shape_changes": tunes,
-                "kernel_shape_P_NT_CL": {str(k): list(v) for k, v in shapes.items()},
-                "note": "wall time on the host clock around all evolve calls (one per unit of t)"}
+        line = {"mode": "full_job", "workload": wl_desc, "instances": len(insts) * ws,
+                "n_gpus": ws, **res,
+                "kernel_shape_P_NT_CL": {str(k): list(v) for k, v in shapes.items()}}
         print(json.dumps(line), flush=True)
+
+
+def job_amp_scan(stream, local, T=100.0):
+    """The amplitude-scan job from t = 0 to T (every pulse to T or its collapse), as one side
+    figure of the default bench: the autotuner's start-up choice and its re-tunes are included."""
+    from paper_1706_07413_b300 import adscl
+    insts, _, desc = workload_insts("amp_scan", 0)
+    sol = adscl.Solver([it.N for it in insts], ko_sigma=SIGMA_KO, collapse_threshold=THETA,
+                       device=local, stream=stream.cuda_stream)
+    batch_fields(insts, sol)
+    t0 = time.perf_counter()
+    sol.autotune(8)
+    tune0 = time.perf_counter() - t0
+    res = full_job(sol, len(insts), 4, stream, T, True)
+    res["wall_s_with_first_tune"] = res["wall_s"] + tune0
+    res["workload"] = desc
+    sol.close()
+    return res
+
+
+def job_uneven_spectra(stream, local, T=10.0, precision_name="BF16X3"):
+    """The uneven batch with its spectra (192 instances, N in {2049, 4097, 8193}, mode-sum data)
+    from t = 0 to T: evolve one unit of t, then the 64 mode energies of every instance on the
+    tensor cores and the TTF quantities (adscl_track), timed as one job on the host clock; the
+    spectrum's share is the time of the same number of spectrum calls on the final slices, timed
+    alone with CUDA events.  Also: the tensor-core energies against the FP64 projection on the
+    last slice, and how far the particle number and the total energy moved over the job."""
+    import torch
+    from paper_1706_07413_b300 import adscl
+    insts, _, desc = workload_insts("uneven", 0)
+    prec = getattr(adscl, "PREC_" + precision_name)
+    sol = adscl.Solver([it.N for it in insts], ko_sigma=SIGMA_KO, collapse_threshold=THETA,
+                       out_dt=1.0, device=local, stream=stream.cuda_stream)
+    batch_fields(insts, sol)
+    t0 = time.perf_counter()
+    shapes = sol.autotune(8)
+    tune_s = time.perf_counter() - t0
+    n_snap = int(round(T)) + 1
+    sol.spectrum(64, prec)          # builds the split mode tables once (outside the job)
+    torch.cuda.synchronize()
+    _, s0 = sol.clock()
+    t0 = time.perf_counter()
+    th, qh, Eh = sol.track(0.0, 1.0, n_snap, 64, prec, energies=True)
+    wall = time.perf_counter() - t0
+    _, s1 = sol.clock()
+    work = float(np.sum((s1 - s0) * sol.N.astype(np.float64) * 4.0))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    E = torch.empty((len(insts), 64), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(n_snap):
+            sol.lib.adscl_spectrum(sol.ctx, 64, prec, E.data_ptr(), 1)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    spec_s = e0.elapsed_time(e1) / 1e3
+    E64 = sol.spectrum(64, adscl.PREC_FP64)
+    _, _, mass, _ = sol.evolve(T)
+    tc_err = float((np.abs(Eh[-1] - E64).max(axis=1) / mass).max())
+    dN = np.abs(qh[:, :, 1] / qh[0, :, 1] - 1.0).max(axis=0)
+    dE = np.abs(qh[:, :, 0] / qh[0, :, 0] - 1.0).max(axis=0)
+    sol.close()
+    return {"t_end": T, "snapshots": n_snap, "workload": desc + f"; spectra every unit of t ({precision_name})",
+            "wall_s": wall, "point_substeps_per_s": work / wall, "autotune_s": tune_s,
+            "kernel_shape_P_NT_CL": {str(k): list(v) for k, v in shapes.items()},
+            "spectrum_s": spec_s, "spectrum_share": spec_s / wall,
+            "tc_vs_fp64_max_dE_over_M": tc_err,
+            "ttf": {"particle_number_max_rel_change": {"median": float(np.median(dN)), "max": float(dN.max())},
+                    "total_energy_max_rel_change": {"median": float(np.median(dE)), "max": float(dE.max())},
+                    "temperature_range": [float(qh[:, :, 2].min()), float(qh[:, :, 2].max())]},
+            "note": "wall time on the host clock around one adscl_track call (evolve + spectrum + "
+                    "TTF per unit of t, history copied to the host at the end)"}
 
 
 def run_reference(args):
@@ -409,7 +494,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_insts("amp_scan", 0)[1],
+        "config": {"workload": workload_insts("amp_scan", 0)[2],
                    "step": f"bounded sample of the same workload: {len(insts)} of the pulses x "
                            f"{nsteps} RK4 steps per bench step",
                    "scheme": "rk4",
@@ -431,6 +516,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-others", action="store_true")
+    ap.add_argument("--no-jobs", action="store_true",
+                    help="skip the whole-job side figures (amplitude scan to t = 100, uneven batch "
+                         "with spectra to t = 10)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel shapes instead of the autotuner's choice")
     ap.add_argument("--shape", default="",
@@ -461,9 +549,10 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        host_group = dist.new_group(backend="gloo")
 
     stream = torch.cuda.Stream()
-    insts, wl_desc = workload_insts(args.workload, rank)
+    insts, glob_idx, wl_desc = workload_insts(args.workload, rank, ws)
     B = len(insts)
     N = insts[0].N
     amp = args.workload == "amp_scan" and args.scheme == "rk4"
@@ -531,6 +620,11 @@ def main():
     if dist is not None:
         from paper_1706_07413_b300 import shard
         dev_s, work_all = shard.reduce_timing(dev_s, work, dist, device="cuda")
+        # per-instance results of the whole batch on rank 0 (host data over a gloo group)
+        res = shard.gather_results(np.stack([st.astype(np.float64), tc, m], axis=1), glob_idx,
+                                   B * ws, dist, group=host_group)
+        if rank == 0:
+            collapsed = int(np.sum(res[:, 0] == adscl.COLLAPSED))
     else:
         work_all = work
     value = work_all / dev_s
@@ -557,12 +651,12 @@ def main():
     if rank == 0 and amp and not args.no_others:
         others = {}
         for name in ("large", "uneven", "production"):
-            oi, od = workload_insts(name, 0)
+            oi, _, od = workload_insts(name, 0)
             others[name] = {"value": side_rate(oi, stream, local, 128, flush), "unit": UNIT,
                             "workload": od, "rk_steps": 128}
         # the paper's production scheme on the amplitude scan: A evolved with Eq. (eq:adot),
         # re-integrated every 64 steps, SSP-RK3 (3 substeps per step)
-        oi, od = workload_insts("amp_scan", 0)
+        oi, _, od = workload_insts("amp_scan", 0)
         v = side_rate(oi, stream, local, 128, flush, substeps=3, scheme=adscl.SCHEME_EVOLVED_A_RK3,
                       a_reint_every=64)
         vf = side_rate(oi, stream, local, 128, flush, substeps=3, scheme=adscl.SCHEME_FIXED_METRIC_RK3)
@@ -577,6 +671,12 @@ def main():
             "value": vf, "unit": UNIT, "rk_steps": 128,
             "workload": od + "; fixed metric A = 1, delta = 0 (no constraints), SSP-RK3",
             "rk_steps_per_s": vf / (3.0 * N_DEFAULT * B_DEFAULT)}
+
+    # whole jobs of the configurations (default run on one GPU only)
+    jobs = None
+    if rank == 0 and ws == 1 and amp and not args.no_jobs:
+        jobs = {"amp_scan_to_t100": job_amp_scan(stream, local, 100.0),
+                "uneven_spectra_to_t10": job_uneven_spectra(stream, local, 10.0)}
 
     # one instance per launch, same workload, for the batched-vs-one-per-launch comparison
     opl = None
@@ -670,12 +770,13 @@ def main():
             ipps += TRAFFIC["fp64_instr_per_point_substep"] * st_recomp / max(st_segs, 1)
             adj_issue = {"fp64_instr_per_point_substep": ipps,
                          "frac": (w_adj * ipps / t_adj) / (tflops_peak * 1e12 / 2)}
-        adj = {"value": t_adj / t_fwd, "forward_ms": 1e3 * t_fwd, "grad_ms": 1e3 * t_adj,
-               "fp64_issue": adj_issue, "cpu_oracle": cpu_adj,
-               "forward_shape_P_NT_CL": [8, 512, 1],
-               "tuned": {"forward_shape_P_NT_CL": list(tuned[ainst[0].N]),
-                         "forward_ms": 1e3 * t_fwd_t, "grad_ms": 1e3 * t_adj_t,
-                         "ratio": t_adj_t / t_fwd_t},
+        adj = {"value": t_adj_t / t_fwd_t, "forward_ms": 1e3 * t_fwd_t, "grad_ms": 1e3 * t_adj_t,
+               "forward_shape_P_NT_CL": list(tuned[ainst[0].N]),
+               "against": "the autotuned forward pass of the same batch",
+               "cpu_oracle": cpu_adj,
+               "default_shapes": {"forward_shape_P_NT_CL": [8, 512, 1], "forward_ms": 1e3 * t_fwd,
+                                  "grad_ms": 1e3 * t_adj, "ratio": t_adj / t_fwd,
+                                  "fp64_issue": adj_issue},
                "workload": f"64 mode-sum instances, N=4097, {ADJ_STEPS} RK4 steps of dt=2pi/32768, "
                            "checkpoint every 256 steps, J = sum_{j<32}(E_j(T)-E_j(0))^2",
                "grad_includes": "E(0), the forward pass (storing every stage when all segments fit "
@@ -768,7 +869,10 @@ def main():
                                     round((args.warmup + args.steps) * dstep, 6)],
                        "collapsed_in_window": collapsed,
                        "l2": "flushed (512 MB write) before every timed launch",
-                       "parallelism": f"instances sharded over {ws} GPU(s), no collective"},
+                       "instances_total": B * ws,
+                       "parallelism": (f"one batch of {B * ws} instances split over {ws} GPU(s) "
+                                       "by longest-processing-time first, no collective on the "
+                                       "data path; per-instance results gathered on rank 0")},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -778,6 +882,7 @@ def main():
             "adjoint_forward_ratio": adj,
             "spectrum": spec,
             "other_workloads": others,
+            "jobs": jobs,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

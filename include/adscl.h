@@ -287,7 +287,7 @@ adscl_status adscl_exp_neg_scaled(int32_t device, const double *X, double *y, in
  * initial slice Phi(x,0), Pi(x,0); on return the slice at t_reached), and four outputs of
  * length B (t_reached, t_collapse, mass, inst_status) with the meaning of adscl_evolve.
  * cfl, ko_sigma and collapse_threshold as in adscl_config (out_dt is 1).  N must satisfy the
- * same rule as adscl_config.N: N >= 17 with (N - 1) a multiple of 8 (so N = 1001 is refused
+ * same rule as adscl_config.N: N >= 17 with (N - 1) a multiple of 8 (so N = 1003 is refused
  * with ADSCL_EINVAL, N = 1025 is accepted).  All other working storage is one fixed array in
  * device memory that the library holds on every GPU where it is loaded (about 1.3 MB, until the
  * process exits), hence the limits: B <= 64 instances, N <= 4097, B * N <= 65552 (16 instances

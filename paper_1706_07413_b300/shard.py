@@ -36,24 +36,24 @@ def partition(work, world):
     return [sorted(p) for p in parts]
 
 
-def gather_results(local, indices, B, dist, dtype=np.float64):
+def gather_results(local, indices, B, dist, dtype=np.float64, group=None):
     """Reassemble per-instance results (local: array of this rank's instances, in the order of
-    `indices`) into the global order on rank 0 (None elsewhere).  Host tensors over the process
-    group's backend (gloo for host data)."""
+    `indices`) into the global order on rank 0 (None elsewhere).  Host tensors over `group`
+    (default: the default process group), which must have a host backend (gloo)."""
     import torch
-    world = dist.get_world_size()
-    rank = dist.get_rank()
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
     payload = np.concatenate([np.asarray(indices, dtype=np.float64)[:, None],
                               np.asarray(local, dtype=np.float64).reshape(len(indices), -1)], axis=1)
     width = payload.shape[1]
     counts = torch.zeros(world, dtype=torch.int64)
     counts[rank] = len(indices)
-    dist.all_reduce(counts)
+    dist.all_reduce(counts, group=group)
     nmax = int(counts.max())
     buf = torch.zeros((nmax, width), dtype=torch.float64)
     buf[: len(indices)] = torch.from_numpy(payload)
     out = [torch.zeros_like(buf) for _ in range(world)] if rank == 0 else None
-    dist.gather(buf, out, dst=0)
+    dist.gather(buf, out, dst=0, group=group)
     if rank != 0:
         return None
     res = np.zeros((B, width - 1))

@@ -1,5 +1,5 @@
-"""Collapse-time parity at the headline workload: the 8 strongest pulses of the 256-instance,
-N = 4097 amplitude scan, evolved inside the full batch to their collapse (min A < 2^-7, the
+"""Collapse-time parity at the headline workload: the 8 earliest-collapsing pulses of the
+256-instance, N = 4097 amplitude scan, evolved inside the full batch to their collapse (min A < 2^-7, the
 criterion of Sec. II with the scan's threshold) on each kernel shape the bench runs, against
 the CPU oracle run to the same slices on host threads.
 
@@ -7,8 +7,8 @@ Bars (the solver's stated tolerances): collapse time within 0.1 %; the same fina
 within 1e-10 relative on the last slice before the earliest collapse and on each collapse slice;
 Phi, Pi, A, delta within 1e-9 max-abs on a slice just before the earliest collapse.
 
-Oracle cost: about 6,600 RK4 steps at N = 4097 per pulse, ~18 s each on one host core; the 8
-pulses run on up to 8 host threads (ctypes releases the GIL)."""
+Oracle cost: about 6,000-6,600 RK4 steps at N = 4097 per pulse, ~18 s each on one host core;
+the 8 pulses run on up to 8 host threads (ctypes releases the GIL)."""
 import os
 from concurrent.futures import ThreadPoolExecutor
 
@@ -42,16 +42,17 @@ def _batch(ad, insts, shape=None):
 
 @pytest.fixture(scope="module")
 def reference(ad, orc):
-    """GPU collapse times on the default shape fix the comparison slice n_pre (95 % of the
-    earliest collapse); the oracle then runs every pulse to n_pre and on to its collapse."""
+    """A run of the batch on the default shape picks the 8 pulses that collapse first and the
+    comparison slice n_pre (95 % of the earliest collapse, before any instance of the batch has
+    collapsed); the oracle then runs those pulses to n_pre and on to their collapse."""
     insts = W.amp_scan()
     N = insts[0].N
-    strongest = [int(b) for b in np.argsort([-it.eps for it in insts])[:8]]
     s = _batch(ad, insts)
     dt = s.clock()[0][0]
     _, tc, _, st = s.evolve(2.0)
+    strongest = [int(b) for b in np.argsort(tc)[:8]]
     assert all(st[b] == ad.COLLAPSED for b in strongest)
-    n_pre = int(0.95 * min(tc[b] for b in strongest) / dt)
+    n_pre = int(0.95 * tc.min() / dt)
     s.close()
 
     def run(b):

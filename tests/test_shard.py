@@ -49,7 +49,7 @@ def _worker(rank, world, port, q):
         mine = parts[rank]
         # every rank "computes" per-instance results: 10 * index + rank marker in column 2
         local = np.stack([10.0 * np.asarray(mine), np.full(len(mine), float(rank))], axis=1)
-        res = shard.gather_results(local, mine, work.size, dist)
+        res = shard.gather_results(local, mine, work.size, dist, group=dist.new_group(backend="gloo"))
         t, w = shard.reduce_timing(0.5 + rank, float(work[mine].sum()), dist)
         q.put((rank, None if res is None else res.tolist(), t, w))
     finally:
@@ -78,3 +78,23 @@ def test_gather_and_timing_over_gloo_world_size_2():
     for r in range(2):
         assert np.all(res[parts[r], 1] == r)
         assert out[r][1] == 1.5 and out[r][2] == work.sum()
+
+
+def test_bench_splits_one_global_batch_over_the_ranks():
+    """bench.py under torchrun: each rank's share of a workload is a piece of one global batch of
+    B x world instances (one seed), the shares partition it, and one rank gets the N = 1 batch."""
+    import importlib.util
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    one, idx1, _ = bench.workload_insts("amp_scan", 0, 1)
+    assert idx1 == list(range(256)) and [it.eps for it in one] == [it.eps for it in bench.W.amp_scan()]
+    for name in ("amp_scan", "uneven"):
+        shares = [bench.workload_insts(name, r, 2) for r in range(2)]
+        allidx = sorted(i for s in shares for i in s[1])
+        assert allidx == list(range(2 * len(one if name == "amp_scan" else bench.W.uneven())))
+        assert abs(len(shares[0][0]) - len(shares[1][0])) <= (0 if name == "amp_scan" else 40)
+        glob = bench.WORKLOADS[name][0](B=len(allidx), seed=bench.WORKLOADS[name][2])
+        for insts, idx, _ in shares:
+            assert [it.N for it in insts] == [glob[i].N for i in idx]

@@ -105,7 +105,7 @@ def test_noalloc_refuses_bad_arguments_before_queuing_anything(ad):
     ADSCL_EINVAL with the caller's fields and outputs untouched."""
     import torch
     dev = torch.device("cuda", 0)
-    for B, N, t_end in ((4, 1001, 0.1), (4, 129, 1e300), (64, 4097 // 8 + 1, 4.0e6), (2, 129, -1.0),
+    for B, N, t_end in ((4, 1003, 0.1), (4, 129, 1e300), (64, 4097 // 8 + 1, 4.0e6), (2, 129, -1.0),
                         (2, 129, float("nan"))):
         Phi = torch.zeros(B * N, dtype=torch.float64, device=dev)
         Pi = torch.ones(B * N, dtype=torch.float64, device=dev)
