@@ -309,15 +309,15 @@ def autotune_report(stream, local):
 def paper_configs_report(stream, local, steps=64):
     """The configurations the paper times (Sec. IV, Tables I and II), one instance each: N = 32769
     with A and delta dynamical (the paper's scheme: A evolved by Eq. (eq:adot), re-integrated
-    every 64 steps, SSP-RK3; and the classic RK4 with A integrated every stage), and the fixed
-    metric A = 1, delta = 0 (the paper's Table II used N = 65537; 32769 is this solver's largest
-    grid).  A single instance occupies one 8-CTA cluster, i.e. 8 of the SMs."""
+    every 64 steps, SSP-RK3; and the classic RK4 with A integrated every stage) on one 8-CTA
+    cluster (8 of the SMs), and the fixed metric A = 1, delta = 0 at the Table II grid N = 65537
+    on one 16-CTA cluster."""
     import torch
     from paper_1706_07413_b300 import adscl
-    N = 32769
     out = {}
-    for name, scheme, stages, reint in (("table1_evolved_A_rk3", 1, 3, 64), ("table1_rk4_constraint_A", 0, 4, 0),
-                                        ("table2_fixed_metric_rk3", 3, 3, 0)):
+    for name, N, scheme, stages, reint in (("table1_evolved_A_rk3", 32769, 1, 3, 64),
+                                           ("table1_rk4_constraint_A", 32769, 0, 4, 0),
+                                           ("table2_fixed_metric_rk3", 65537, 3, 3, 0)):
         sol = adscl.Solver([N], ko_sigma=SIGMA_KO, collapse_threshold=THETA, device=local,
                            stream=stream.cuda_stream, scheme=scheme, a_reint_every=reint)
         sol.set_initial(np.zeros(N), W.gaussian_pi(N, 40.0, 1.0 / 16))

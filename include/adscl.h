@@ -103,9 +103,11 @@ typedef struct {
                                     (see adscl_spectrum for the error bound) */
 } adscl_config;
 
-/* Largest grid size N one instance may use with this library: 32769.  Grids up to 4097 run on one
- * CTA (one SM) per instance, larger ones on a thread-block cluster of 2, 4 or 8 CTAs sharing
- * the instance through distributed shared memory. */
+/* Largest grid size N one instance may use with this library: 65537 (the paper's Table II
+ * grid).  Grids up to 4097 run on one CTA (one SM) per instance, larger ones on a thread-block
+ * cluster of 2, 4, 8 or 16 CTAs sharing the instance through distributed shared memory (16 CTAs,
+ * for N > 32769, is a non-portable cluster size: on a device that cannot place such a cluster,
+ * adscl_create returns ADSCL_EUNSUPPORTED for those grids). */
 int32_t adscl_max_points(void);
 
 /* Create a context: validates cfg (ADSCL_EINVAL before any allocation or launch), builds the
@@ -240,7 +242,7 @@ adscl_status adscl_adjoint_storage(adscl_ctx *ctx, int64_t *bytes, int32_t *buff
  * instance counts, and floor(2 log2) of the instances of each size still running): a cached entry
  * is reused without timing or touching the state, and calling this again after collapses have
  * thinned a batch re-tunes for the smaller number of running instances.
- * Synchronous.  The evolved-A and fixed-metric kernels are built for the shapes (8, 512, 1/2/4/8),
+ * Synchronous.  The evolved-A and fixed-metric kernels are built for the shapes (8, 512, 1/2/4/8/16),
  * (8, 256, 2) and (8, 128, 2).
  * Different shapes associate the radial scans differently, so results agree with the default
  * shape to rounding, not bit for bit. */

@@ -30,8 +30,8 @@ namespace {
 constexpr int kP = 8;      // grid nodes per thread
 constexpr int kNT = 512;   // threads per CTA
 constexpr int kMaxPoints1 = kP * kNT + 1;      // 4097: one CTA per instance
-constexpr int kMaxCluster = 8;                 // larger grids: clusters of 2, 4 or 8 CTAs
-constexpr int kMaxPoints = kMaxCluster * kP * kNT + 1;   // 32769
+constexpr int kMaxCluster = 16;                // larger grids: clusters of 2, 4, 8 or 16 CTAs
+constexpr int kMaxPoints = kMaxCluster * kP * kNT + 1;   // 65537
 
 // CTAs per instance of grid size N: the smallest power of two whose CTAs hold the N - 1 cells
 int cluster_of(int N)
@@ -207,7 +207,7 @@ double step_for(int N, double cfl, double cadence)
     return cadence / std::ceil(cadence / (cfl * h));
 }
 
-// the evolved-A / fixed-metric kernel is built for the shapes (8, 512, 1/2/4/8), (8, 256, 2) and
+// the evolved-A / fixed-metric kernel is built for the shapes (8, 512, 1/2/4/8/16), (8, 256, 2) and
 // (8, 128, 2); ea_dispatch calls f.template operator()<NT, CL>() for the shape with index id
 bool ea_shape(int id)
 {
@@ -249,7 +249,8 @@ cudaError_t ea_select(int id, bool launch, const void **fn, const EaArgs *ea, in
         if (fn) *fn = (const void *)evolve_ea_kernel<kP, NT_, FIXED, CL_>;                  \
         return launch ? ea_launch_t<FIXED, NT_, CL_>(*ea, units, smem, stride, sm) : cudaSuccess; \
     }
-    ADSCL_EA(512, 1) ADSCL_EA(512, 2) ADSCL_EA(512, 4) ADSCL_EA(512, 8) ADSCL_EA(256, 2) ADSCL_EA(128, 2)
+    ADSCL_EA(512, 1) ADSCL_EA(512, 2) ADSCL_EA(512, 4) ADSCL_EA(512, 8) ADSCL_EA(512, 16) ADSCL_EA(256, 2)
+    ADSCL_EA(128, 2)
 #undef ADSCL_EA
     return cudaErrorInvalidValue;
 }
@@ -946,6 +947,10 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
         if (!ea_shape(id)) continue;
         CK(cudaFuncSetAttribute(ea_kernel_of<false>(id), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
         CK(cudaFuncSetAttribute(ea_kernel_of<true>(id), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+        if (kShapes[id].CL > 8) {   // 16 CTAs: beyond the portable cluster size
+            CK(cudaFuncSetAttribute(ea_kernel_of<false>(id), cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            CK(cudaFuncSetAttribute(ea_kernel_of<true>(id), cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        }
     }
     // default kernel shapes; every shape in use must fit the device
     ctx->shape_of.resize(ctx->B);

@@ -1,7 +1,7 @@
 // evolve.cuh -- persistent FP64 method-of-lines kernel for the AdS4 Einstein-Klein-Gordon
 // system of arXiv:1706.07413, Sec. II (Eqs. (eq:phi), (eq:pi), (eq:aprime), (eq:delta)).
 //
-// One CTA -- or a thread-block cluster of CL = 2, 4, 8 CTAs that split the node blocks between
+// One CTA -- or a thread-block cluster of CL = 2, 4, 8, 16 CTAs that split the node blocks between
 // them -- evolves one instance at a time with its stage slice resident in (distributed) shared
 // memory.  Thread t of a CTA owns the P contiguous grid nodes of its block and the cells to their
 // right; node N-1 (x = pi/2, where Phi = Pi = 0) is owned by nobody and written as a constant.
@@ -268,7 +268,8 @@ __device__ __forceinline__ void st_others(T *p, T v, int rank) {
 template <int CL>
 __device__ __forceinline__ int block_start(int r, int T) { return (r * T + CL - 1) / CL; }
 
-// CL = 1: one CTA per instance.  CL = 2, 4, 8: a cluster of CL CTAs per instance, rank r owning
+// CL = 1: one CTA per instance.  CL = 2, 4, 8, 16: a cluster of CL CTAs per instance (16: a
+// non-portable cluster size, allowed per kernel by the host), rank r owning
 // the node blocks block_start(r) .. block_start(r+1)-1 (at least NT/2 blocks each, so P >= 3
 // halo nodes always come from the neighbouring rank); halos, scan carries and the step-end
 // diagnostics cross between the CTAs through distributed shared memory.
@@ -279,7 +280,7 @@ template <int P, int NT, int CL = 1, bool REC = false>
 __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(EvolveArgs a, int stride)
 {
     static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
-    static_assert(CL == 1 || CL == 2 || CL == 4 || CL == 8, "cluster of 1, 2, 4 or 8 CTAs");
+    static_assert(CL == 1 || CL == 2 || CL == 4 || CL == 8 || CL == 16, "cluster of 1, 2, 4, 8 or 16 CTAs");
     constexpr int NW = NT / 32;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ double smem[];

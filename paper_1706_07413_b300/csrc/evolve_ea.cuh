@@ -6,7 +6,7 @@
 //   y^{(s+1)} = a_s y_n + b_s (y^{(s)} + dt L(y^{(s)})),
 //   order 2: (a, b) = (0, 1), (1/2, 1/2);  order 3: (0, 1), (3/4, 1/4), (1/3, 2/3).
 //
-// One CTA per instance (N <= P * NT + 1) or a cluster of CL = 2, 4, 8 CTAs (N <= CL * P * NT + 1),
+// One CTA per instance (N <= P * NT + 1) or a cluster of CL = 2, 4, 8, 16 CTAs (N <= CL * P * NT + 1),
 // with the layout, the ticket queue and the cluster protocol of evolve_kernel (halos, scan carries
 // and slice diagnostics through distributed shared memory; control decisions by rank 0).
 // Per stage:
@@ -51,7 +51,7 @@ template <int P, int NT, bool FIXED = false, int CL = 1>
 __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kernel(EaArgs ea, int stride)
 {
     static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
-    static_assert(CL == 1 || CL == 2 || CL == 4 || CL == 8, "cluster of 1, 2, 4 or 8 CTAs");
+    static_assert(CL == 1 || CL == 2 || CL == 4 || CL == 8 || CL == 16, "cluster of 1, 2, 4, 8 or 16 CTAs");
     constexpr int NW = NT / 32;
     constexpr unsigned FULL = 0xffffffffu;
     const EvolveArgs &a = ea.e;

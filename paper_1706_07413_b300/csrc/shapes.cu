@@ -11,7 +11,8 @@ namespace adscl {
     X(4, 4, 512, 1) X(5, 4, 512, 2)                                                      \
     X(6, 8, 256, 1) X(7, 8, 256, 2) X(8, 8, 256, 4)                                      \
     X(9, 4, 256, 1) X(10, 4, 256, 2) X(11, 4, 256, 4)                                    \
-    X(12, 8, 128, 1) X(13, 4, 128, 1) X(14, 8, 128, 2) X(15, 8, 128, 4)
+    X(12, 8, 128, 1) X(13, 4, 128, 1) X(14, 8, 128, 2) X(15, 8, 128, 4)                  \
+    X(16, 8, 512, 16)
 
 #define ADSCL_ROW(i, p, nt, cl) {p, nt, cl},
 const Shape kShapes[kNumShapes] = {ADSCL_SHAPES(ADSCL_ROW)};
@@ -99,8 +100,10 @@ cudaError_t shapes_set_attributes()
         // the largest grid a CTA of this shape can hold: P * NT nodes (+ the closing node)
         const size_t smem = shape_smem(id, s.P * s.NT * s.CL + 1);
         for (int rec = 0; rec < 2; ++rec) {
-            const cudaError_t e = cudaFuncSetAttribute(kernel_of(id, rec != 0),
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = cudaFuncSetAttribute(kernel_of(id, rec != 0),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess && s.CL > 8)   // 16 CTAs: beyond the portable cluster size
+                e = cudaFuncSetAttribute(kernel_of(id, rec != 0), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return e;
         }
     }

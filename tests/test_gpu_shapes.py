@@ -22,7 +22,7 @@ def _candidates():
     out = []
     for P, NT, CL in itertools.product((4, 8), (128, 256, 512), (1, 2, 4, 8)):
         nmax = P * NT * CL + 1
-        if nmax > 32769:
+        if nmax > 65537 or CL > 8:   # the 16-CTA shape: tests/test_gpu_grid65537.py
             continue
         out.append((P, NT, CL, nmax))
         small = 8 * CL * 3 + 1          # three node blocks of 8 per CTA, several tiles short
