@@ -60,22 +60,23 @@ SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A
     # the step-end mass sum (5 per step)
     "fixed_metric_rk3": (3, 3, 1.0 + 30.0 + 8.0 + 5.0 / 3.0, 0),
 }
-# FP64 instructions per point-substep of the bench's adjoint batch: the forward pass recorded by
-# the evolution kernel (evolve_kernel<8, 128, 4, true> over the whole window) and the adjoint
-# kernel's backward sweep (phase B, per segment): ncu's smsp__sass_thread_inst_executed_op_d{add,
-# mul,fma}_pred_on.sum of those launches divided by their point-substeps, captured on this
-# script's adjoint leg; used only while the kernel sources are unchanged
-ADJ_ISSUE = {"sha256": "b49ef8ddd58287bc68aa2f976bf0c0a3422c882778723e5618960a1ce23df2cd",
-             "forward_record": 75931385856 / 1074003968,
-             "phase_B": (9518514176 + 10991304704 + 8170766336) / 268500992}
+# FP64 instructions per point-substep of the adjoint: the forward pass recorded by the evolution
+# kernel (evolve_kernel<8, 128, 4, true>) and the adjoint kernel's backward sweep (phase B, per
+# segment): ncu's smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum of those launches
+# divided by their point-substeps, captured on a reduced adjoint batch (38 instances at N = 4097,
+# 96 steps in two 48-step segments; per point-substep the same instruction mix as the bench's
+# 64-instance batch); used only while the kernel sources are unchanged
+ADJ_ISSUE = {"sha256": "289191c0b5d3adb207820c4f9b541176d5ba63fea2ff06c66d12e7ef3bc93538",
+             "forward_record": (1305519336 + 777914796 + 2143215276) / (38 * 4097 * 96 * 4),
+             "phase_B": (1059678336 + 909699328 + 1223641344) / (38 * 4097 * 48 * 4)}
 L2_FLUSH_BYTES = 512 << 20
 CPU_SAMPLE_STEPS = 800    # oracle sample of the cpu_baseline leg: ~10 s on 16 host threads
 REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one timed evolve_kernel launch of
 # the amplitude scan, from an ncu capture of this script's headline launch; reported only while
 # the kernel source and the kernel shape are the ones the counters were taken on.
-TRAFFIC = {"kernel_sha256": "52364d26489815480a94d728709e093710313c856713ba6d8d0d930713c83fb1",
-           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17575168 + 59295232,
+TRAFFIC = {"kernel_sha256": "ccc4175475c9dfb9eb5757f76274debb11128dce1a2aa1ac6d41c1c6b13aa4cc",
+           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17731840 + 67287040,
            # FP64 instructions (DADD + DMUL + DFMA, thread level) per point-substep, same capture
            "fp64_instr_per_point_substep": (23334264832 + 13958131712 + 38349320192) / 1074003968}
 
@@ -528,6 +529,11 @@ def main():
                     help="batch to time (the metric's workload is amp_scan)")
     ap.add_argument("--scheme", default="rk4", choices=sorted(SCHEMES),
                     help="time-stepping scheme (the metric's scheme is rk4)")
+    ap.add_argument("--adjoint-batch", type=int, default=64,
+                    help="instances of the adjoint leg (64: the adjoint configuration; fewer for "
+                         "counter captures of a few GB)")
+    ap.add_argument("--adjoint-ckpt", type=int, default=256,
+                    help="checkpoint interval of the adjoint leg in steps")
     ap.add_argument("--adjoint-steps", type=int, default=1024,
                     help="RK4 steps of the adjoint/forward-ratio window (32768 = the adjoint "
                          "batch's whole T = 2 pi)")
@@ -706,10 +712,10 @@ def main():
     adj = None
     if rank == 0 and amp and not args.no_adjoint:
         ADJ_STEPS = args.adjoint_steps
-        ainst = W.adjoint_batch()
+        ainst = W.adjoint_batch(B=args.adjoint_batch)
         a = np.stack([it.coeffs for it in ainst])
         sa = adscl.Solver([ainst[0].N] * len(ainst), ko_sigma=SIGMA_KO, collapse_threshold=-1.0,
-                          out_dt=2 * math.pi, spec_J=32, ckpt_every=256, device=local,
+                          out_dt=2 * math.pi, spec_J=32, ckpt_every=args.adjoint_ckpt, device=local,
                           stream=stream.cuda_stream)
         dta, _ = sa.clock()
         Ta = ADJ_STEPS * dta[0]
@@ -777,8 +783,9 @@ def main():
                "default_shapes": {"forward_shape_P_NT_CL": [8, 512, 1], "forward_ms": 1e3 * t_fwd,
                                   "grad_ms": 1e3 * t_adj, "ratio": t_adj / t_fwd,
                                   "fp64_issue": adj_issue},
-               "workload": f"64 mode-sum instances, N=4097, {ADJ_STEPS} RK4 steps of dt=2pi/32768, "
-                           "checkpoint every 256 steps, J = sum_{j<32}(E_j(T)-E_j(0))^2",
+               "workload": f"{len(ainst)} mode-sum instances, N=4097, {ADJ_STEPS} RK4 steps of "
+                           f"dt=2pi/32768, checkpoint every {args.adjoint_ckpt} steps, "
+                           "J = sum_{j<32}(E_j(T)-E_j(0))^2",
                "grad_includes": "E(0), the forward pass (storing every stage when all segments fit "
                                 "in device memory; else checkpoints and the stages of the last "
                                 "segments that fit, each earlier segment recomputed before its "

@@ -106,3 +106,4 @@ def test_sixteen_cta_instances_in_a_mixed_batch_equal_single_runs(ad):
         for x, y in zip(s.get_state(i), one.get_state(0)):
             assert np.array_equal(x, y)
         assert tb[2][i] == t1[2][0]
+
