@@ -19,7 +19,7 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference"
     assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["higher_is_better"] is True and line["value"] > 0
-    assert line["config"]["workload"] == bench.workload_insts("amp_scan", 0)[1]
+    assert line["config"]["workload"] == bench.workload_insts("amp_scan", 0)[2]
     for k in ("n_gpus", "steps", "warmup", "ms_per_step", "scaling", "dtype", "data", "cpu_baseline",
               "e2e"):
         assert k in line
