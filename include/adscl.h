@@ -166,7 +166,8 @@ adscl_status adscl_spectrum(adscl_ctx *ctx, int32_t J, int precision, double *E,
  *   ttf[3b + 0] = E = sum_{j<J} E_j          (total energy; equals the mass M as J grows),
  *   ttf[3b + 1] = N = sum_{j<J} E_j / omega_j (particle number, omega_j = 3 + 2j),
  *   ttf[3b + 2] = T = E / N                   (temperature),
- * summed in order of j in FP64 from the E_j of adscl_spectrum with the same J and precision.
+ * summed in order of j in FP64 from the E_j of adscl_spectrum with the same J and precision
+ * (an instance with no energy in these modes, e.g. static AdS, gets E = N = 0 and T = NaN).
  * The third conserved quantity, the TTF Hamiltonian, needs interaction coefficients that the
  * paper does not give; it is not provided.  E: optional (NULL or B x J), receives the mode
  * energies.  Errors as adscl_spectrum. */

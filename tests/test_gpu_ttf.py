@@ -116,3 +116,15 @@ def test_track_rejects_bad_arguments(ad):
         assert e.value.status == ad.ADSCL_EINVAL
     with pytest.raises(ad.AdsclError):
         s.track(0.0, 0.5, 2, J=65)
+
+
+def test_ttf_of_static_ads_is_zero_energy_and_undefined_temperature(ad, orc):
+    """Static AdS (Phi = Pi = 0): every mode energy is 0, so E = N = 0 and T = 0/0 = NaN, as in
+    the oracle; a normal mode beside it in the same batch is unaffected."""
+    s = ad.Solver([129, 129], ko_sigma=0.5)
+    Phi1, Pi1 = orc.synthesize(129, np.array([0.0, 0.02]))
+    s.set_initial(np.concatenate([np.zeros(129), Phi1]), np.concatenate([np.zeros(129), Pi1]))
+    q = s.ttf(16)
+    assert q[0, 0] == 0.0 and q[0, 1] == 0.0 and np.isnan(q[0, 2])
+    assert np.isnan(orc.ttf(np.zeros(16))[2])
+    assert abs(q[1, 2] - 5.0) < 1e-6                       # single mode j = 1: T = omega_1
