@@ -128,3 +128,28 @@ def test_ttf_of_static_ads_is_zero_energy_and_undefined_temperature(ad, orc):
     assert q[0, 0] == 0.0 and q[0, 1] == 0.0 and np.isnan(q[0, 2])
     assert np.isnan(orc.ttf(np.zeros(16))[2])
     assert abs(q[1, 2] - 5.0) < 1e-6                       # single mode j = 1: T = omega_1
+
+
+@pytest.mark.parametrize("prec", ["BF16X3", "TF32X3"])
+def test_track_on_tensor_cores_within_the_derived_bound(ad, prec):
+    """A tracked job of an uneven batch with the tensor-core spectrum: every snapshot's mode
+    energies agree with those of the same job tracked with the FP64 projection within the derived
+    bound of the split-precision projection (tests/test_gpu_spectrum.py tc_bound), relative to the
+    slice's mass; the TTF quantities follow."""
+    from test_gpu_spectrum import tc_bound
+    rng = np.random.default_rng(12)
+    Ns = [2049] * 3 + [4097] * 2 + [1025] * 4
+    a = np.stack([rng.uniform(0.05, 0.2) * np.exp(-np.arange(16) / 3.0) for _ in Ns])
+    res = {}
+    for p in ("FP64", prec):
+        s = ad.Solver(Ns, ko_sigma=0.5, out_dt=0.25)
+        s.set_initial_modes(a)
+        res[p] = s.track(0.0, 0.25, 4, 64, getattr(ad, "PREC_" + p), energies=True)
+        s.close()
+    (t0, q0, E0), (t1, q1, E1) = res["FP64"], res[prec]
+    assert np.array_equal(t0, t1)
+    bound = tc_bound(prec, 1)
+    for k in range(4):
+        rel = np.abs(E1[k] - E0[k]).max(axis=1) / q0[k, :, 0]
+        assert rel.max() <= bound, (k, rel.max(), bound)
+        assert np.all(np.abs(q1[k, :, 0] - q0[k, :, 0]) <= 64 * bound * q0[k, :, 0])
