@@ -472,6 +472,57 @@ def job_uneven_spectra(stream, local, T=10.0, precision_name="BF16X3"):
                     "TTF per unit of t, history copied to the host at the end)"}
 
 
+def job_large_spectra_refine(stream, local, T=4.0, refine_iters=3, refine_steps=256):
+    """The large-grid configuration as a bounded job: 148 instances at N = 8193 (2-CTA clusters;
+    half Gaussian pulses, half two-mode data) from t = 0 to T with the 64 mode energies on the
+    tensor cores (BF16x3) and the TTF quantities every unit of t (one adscl_track call, host
+    clock), and the adjoint-driven refinement of the 8 approximate quasi-periodic seeds at the
+    same resolution (refine_iters gradient steps, each gradient over refine_steps RK4 steps)."""
+    import torch
+    from paper_1706_07413_b300 import adscl
+    from paper_1706_07413_b300.autograd import refine_modes
+    insts, _, desc = workload_insts("large", 0)
+    sol = adscl.Solver([it.N for it in insts], ko_sigma=SIGMA_KO, collapse_threshold=THETA,
+                       out_dt=1.0, device=local, stream=stream.cuda_stream)
+    batch_fields(insts, sol)
+    shapes = sol.autotune(8)
+    n_snap = int(round(T)) + 1
+    sol.spectrum(64, adscl.PREC_BF16X3)
+    torch.cuda.synchronize()
+    _, s0 = sol.clock()
+    t0 = time.perf_counter()
+    th, qh, _ = sol.track(0.0, 1.0, n_snap, 64, adscl.PREC_BF16X3)
+    wall = time.perf_counter() - t0
+    _, s1 = sol.clock()
+    work = float(np.sum((s1 - s0) * sol.N.astype(np.float64) * 4.0))
+    tr, tc, m, st = sol.evolve(T)
+    collapsed = int(np.sum(st == adscl.COLLAPSED))
+    sol.close()
+    seeds = W.qp_seeds(N=8193, K=32)
+    a0 = np.stack([it.coeffs for it in seeds])
+    sr = adscl.Solver([8193] * len(seeds), ko_sigma=SIGMA_KO, spec_J=32, ckpt_every=64, device=local,
+                      stream=stream.cuda_stream)
+    dt = float(sr.clock()[0][0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, hist = refine_modes(sr, a0, refine_steps * dt, iters=refine_iters, step=0.02)
+    torch.cuda.synchronize()
+    refine_s = time.perf_counter() - t0
+    h = hist.numpy()
+    sr.close()
+    return {"t_end": T, "snapshots": n_snap, "workload": desc + "; spectra (BF16x3) and TTF every unit of t",
+            "wall_s": wall, "point_substeps_per_s": work / wall, "collapsed": collapsed,
+            "kernel_shape_P_NT_CL": {str(k): list(v) for k, v in shapes.items()},
+            "refinement": {"seeds": len(seeds), "N": 8193, "iterations": refine_iters,
+                           "gradient_window_steps": refine_steps, "wall_s": refine_s,
+                           "gradients": refine_iters + 1,
+                           "drift_J_last_over_first": {"median": float(np.median(h[-1] / h[0])),
+                                                       "max": float(np.max(h[-1] / h[0]))}},
+            "note": "wall time on the host clock around one adscl_track call, and around the "
+                    "refinement (its gradients, each a forward pass, checkpoint recomputation "
+                    "and backward sweep)"}
+
+
 def run_reference(args):
     """The reference arm: the sequential FP64 CPU oracle on the host cores."""
     ws, rank, _ = _dist()
@@ -519,7 +570,8 @@ def main():
     ap.add_argument("--no-others", action="store_true")
     ap.add_argument("--no-jobs", action="store_true",
                     help="skip the whole-job side figures (amplitude scan to t = 100, uneven batch "
-                         "with spectra to t = 10)")
+                         "with spectra to t = 10, large grids with spectra to t = 4 and the "
+                         "refinement of the quasi-periodic seeds)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel shapes instead of the autotuner's choice")
     ap.add_argument("--shape", default="",
@@ -682,7 +734,8 @@ def main():
     jobs = None
     if rank == 0 and ws == 1 and amp and not args.no_jobs:
         jobs = {"amp_scan_to_t100": job_amp_scan(stream, local, 100.0),
-                "uneven_spectra_to_t10": job_uneven_spectra(stream, local, 10.0)}
+                "uneven_spectra_to_t10": job_uneven_spectra(stream, local, 10.0),
+                "large_spectra_refine_to_t4": job_large_spectra_refine(stream, local, 4.0)}
 
     # one instance per launch, same workload, for the batched-vs-one-per-launch comparison
     opl = None
