@@ -115,137 +115,12 @@ __device__ __forceinline__ Own own_of(int N)
     return o;
 }
 
-// exclusive prefix composition of affine maps x -> a x + b over threads (ascending, rank 0's
-// threads first), applied to 0 at the start: returns the b part.  Threads' own maps are (a, b).
-template <int CL>
-__device__ double scan_affine_prefix(double a, double b, ScanShared &sh)
-{
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double ap = __shfl_up_sync(FULL, a, o), bp = __shfl_up_sync(FULL, b, o);
-        if (lane >= o) { b = fma(a, bp, b); a = a * ap; }
-    }
-    double aEx = __shfl_up_sync(FULL, a, 1), bEx = __shfl_up_sync(FULL, b, 1);
-    if (lane == 0) { aEx = 1.0; bEx = 0.0; }
-    if (lane == 31) { sh.a[wid] = a; sh.b[wid] = b; }
-    __syncthreads();
-    if (wid == 0) {
-        double A = lane < kANW ? sh.a[lane] : 1.0, B = lane < kANW ? sh.b[lane] : 0.0;
-#pragma unroll
-        for (int o = 1; o < kANW; o <<= 1) {
-            const double ap = __shfl_up_sync(FULL, A, o), bp = __shfl_up_sync(FULL, B, o);
-            if (lane >= o) { B = fma(A, bp, B); A = A * ap; }
-        }
-        double bw = __shfl_up_sync(FULL, B, 1), aw = __shfl_up_sync(FULL, A, 1);
-        if (lane == 0) { bw = 0.0; aw = 1.0; }
-        if (lane < kANW) { sh.c[lane] = bw; sh.e[lane] = aw; }
-        if constexpr (CL == 2) {   // rank 0's total map to rank 1
-            if (lane == kANW - 1 && cluster_rank() == 0) st_peer(&sh.pb, B, 1);
-        }
-    }
-    csync<CL>();
-    double r = fma(aEx, sh.c[wid], bEx);
-    if constexpr (CL == 2) {
-        if (cluster_rank() == 1) r = fma(aEx * sh.e[wid], sh.pb, r);   // the maps of rank 0 first
-    }
-    return r;
-}
-
-// exclusive suffix composition (threads descending, rank 1's threads first): the thread's map is
-// x_left = a x_right + b; returns the b part of the composition of all later threads applied to
-// 0 at the end
-template <int CL>
-__device__ double scan_affine_suffix(double a, double b, ScanShared &sh)
-{
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double an = __shfl_down_sync(FULL, a, o), bn = __shfl_down_sync(FULL, b, o);
-        if (lane + o < 32) { b = fma(a, bn, b); a = a * an; }
-    }
-    double aEx = __shfl_down_sync(FULL, a, 1), bEx = __shfl_down_sync(FULL, b, 1);
-    if (lane == 31) { aEx = 1.0; bEx = 0.0; }
-    if (lane == 0) { sh.a[wid] = a; sh.b[wid] = b; }
-    __syncthreads();
-    if (wid == 0) {
-        double A = lane < kANW ? sh.a[lane] : 1.0, B = lane < kANW ? sh.b[lane] : 0.0;
-#pragma unroll
-        for (int o = 1; o < kANW; o <<= 1) {
-            const double an = __shfl_down_sync(FULL, A, o), bn = __shfl_down_sync(FULL, B, o);
-            if (lane + o < kANW) { B = fma(A, bn, B); A = A * an; }
-        }
-        double bw = __shfl_down_sync(FULL, B, 1), aw = __shfl_down_sync(FULL, A, 1);
-        if (lane + 1 >= kANW) { bw = 0.0; aw = 1.0; }
-        if (lane < kANW) { sh.c[lane] = bw; sh.e[lane] = aw; }
-        if constexpr (CL == 2) {   // rank 1's total map to rank 0
-            if (lane == 0 && cluster_rank() == 1) st_peer(&sh.pb, B, 0);
-        }
-    }
-    csync<CL>();
-    double r = fma(aEx, sh.c[wid], bEx);
-    if constexpr (CL == 2) {
-        if (cluster_rank() == 0) r = fma(aEx * sh.e[wid], sh.pb, r);   // the maps of rank 1 first
-    }
-    return r;
-}
-
-// exclusive sums over threads: prefix (threads ascending) and suffix (descending), over both
-// ranks of a 2-CTA cluster
-template <bool kSuffix, int CL>
-__device__ double scan_sum(double x, ScanShared &sh)
-{
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        if (kSuffix) {
-            const double n = __shfl_down_sync(FULL, x, o);
-            if (lane + o < 32) x += n;
-        } else {
-            const double n = __shfl_up_sync(FULL, x, o);
-            if (lane >= o) x += n;
-        }
-    }
-    double ex = kSuffix ? __shfl_down_sync(FULL, x, 1) : __shfl_up_sync(FULL, x, 1);
-    if (kSuffix ? lane == 31 : lane == 0) ex = 0.0;
-    if (kSuffix ? lane == 0 : lane == 31) sh.d[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        double X = lane < kANW ? sh.d[lane] : 0.0;
-#pragma unroll
-        for (int o = 1; o < kANW; o <<= 1) {
-            if (kSuffix) {
-                const double n = __shfl_down_sync(FULL, X, o);
-                if (lane + o < kANW) X += n;
-            } else {
-                const double n = __shfl_up_sync(FULL, X, o);
-                if (lane >= o) X += n;
-            }
-        }
-        double w = kSuffix ? __shfl_down_sync(FULL, X, 1) : __shfl_up_sync(FULL, X, 1);
-        if (kSuffix ? lane + 1 >= kANW : lane == 0) w = 0.0;
-        if (lane < kANW) sh.f[lane] = w;
-        if constexpr (CL == 2) {   // the total of the rank that comes first to the other
-            const int from = kSuffix ? 1 : 0;
-            if (lane == (kSuffix ? 0 : kANW - 1) && cluster_rank() == from) st_peer(&sh.pd, X, 1 - from);
-        }
-    }
-    csync<CL>();
-    double r = ex + sh.f[wid];
-    if constexpr (CL == 2) {
-        if (cluster_rank() == (kSuffix ? 0 : 1)) r += sh.pd;
-    }
-    return r;
-}
-
-// An affine scan and a sum scan in one pass with one CTA barrier and one cluster barrier:
-// kAffSuffix = false: the exclusive affine prefix (threads ascending, as scan_affine_prefix) and
-// the exclusive suffix sum (as scan_sum<true>); kAffSuffix = true: the exclusive affine suffix
-// (as scan_affine_suffix) and the exclusive prefix sum (as scan_sum<false>).  Same slots and the
-// same association order as the separate scans.
+// An affine scan and a sum scan in one pass with one CTA barrier and one cluster barrier, over
+// the threads of both ranks of a 2-CTA cluster.  The affine maps x -> a x + b compose in thread
+// order and the scan returns the b part of the exclusive composition applied to 0; the sums are
+// exclusive.  kAffSuffix = false: the affine prefix (threads ascending, rank 0's threads first)
+// and the suffix sum; kAffSuffix = true: the affine suffix (threads descending, rank 1's threads
+// first; the thread's map is x_left = a x_right + b) and the prefix sum.
 template <int CL, bool kAffSuffix>
 __device__ void scan_pair(double a, double b, double x, ScanShared &sh, double &raff, double &rsum)
 {
@@ -256,13 +131,13 @@ __device__ void scan_pair(double a, double b, double x, ScanShared &sh, double &
         if (kAffSuffix) {
             const double an = __shfl_down_sync(FULL, a, o), bn = __shfl_down_sync(FULL, b, o);
             const double xn = __shfl_up_sync(FULL, x, o);
-            if (lane + o < 32) { b = fma(a, bn, b); a = a * an; }
-            if (lane >= o) x += xn;
+            if (lane + o < 32) { b = fma(a, bn, b); a = mul_f(a, an); }
+            if (lane >= o) x = add_f(x, xn);
         } else {
             const double ap = __shfl_up_sync(FULL, a, o), bp = __shfl_up_sync(FULL, b, o);
             const double xp = __shfl_down_sync(FULL, x, o);
-            if (lane >= o) { b = fma(a, bp, b); a = a * ap; }
-            if (lane + o < 32) x += xp;
+            if (lane >= o) { b = fma(a, bp, b); a = mul_f(a, ap); }
+            if (lane + o < 32) x = add_f(x, xp);
         }
     }
     double aEx, bEx, ex;
@@ -289,13 +164,13 @@ __device__ void scan_pair(double a, double b, double x, ScanShared &sh, double &
             if (kAffSuffix) {
                 const double an = __shfl_down_sync(FULL, A, o), bn = __shfl_down_sync(FULL, B, o);
                 const double xn = __shfl_up_sync(FULL, X, o);
-                if (lane + o < kANW) { B = fma(A, bn, B); A = A * an; }
-                if (lane >= o) X += xn;
+                if (lane + o < kANW) { B = fma(A, bn, B); A = mul_f(A, an); }
+                if (lane >= o) X = add_f(X, xn);
             } else {
                 const double ap = __shfl_up_sync(FULL, A, o), bp = __shfl_up_sync(FULL, B, o);
                 const double xp = __shfl_down_sync(FULL, X, o);
-                if (lane >= o) { B = fma(A, bp, B); A = A * ap; }
-                if (lane + o < kANW) X += xp;
+                if (lane >= o) { B = fma(A, bp, B); A = mul_f(A, ap); }
+                if (lane + o < kANW) X = add_f(X, xp);
             }
         }
         double bw, aw, w;
@@ -326,11 +201,11 @@ __device__ void scan_pair(double a, double b, double x, ScanShared &sh, double &
     }
     csync<CL>();
     raff = fma(aEx, sh.c[wid], bEx);
-    rsum = ex + sh.f[wid];
+    rsum = add_f(ex, sh.f[wid]);
     if constexpr (CL == 2) {
         const int rk = cluster_rank();
-        if (rk == (kAffSuffix ? 0 : 1)) raff = fma(aEx * sh.e[wid], sh.pb, raff);   // the other rank's maps first
-        if (rk == (kAffSuffix ? 1 : 0)) rsum += sh.pd;
+        if (rk == (kAffSuffix ? 0 : 1)) raff = fma(mul_f(aEx, sh.e[wid]), sh.pb, raff);   // the other rank's maps first
+        if (rk == (kAffSuffix ? 1 : 0)) rsum = add_f(rsum, sh.pd);
     }
 }
 
@@ -354,19 +229,19 @@ __device__ __forceinline__ CellFwd cell_fwd_n(double qn0, double rn0, double qn1
     r.rn0 = rn0;
     r.qn1 = qn1;
     r.rn1 = rn1;
-    r.p16 = fma(9.0, p0 + p1, -(pm1 + p2));
-    r.q16 = fma(9.0, q0 + q1, -(qm1 + q2));
-    const double rm = fma(r.p16, r.p16, r.q16 * r.q16);
-    r.qm3 = __ldg(g.wsm3 + c) * rm;
-    r.tm = __ldg(g.wtm + c) * rm;
-    r.De = fma(4.0 / 3.0, r.qm3, r.qn0 + r.qn1);
-    r.y2 = 1.0 / 3.0 - r.qn0;
+    r.p16 = fma(9.0, add_f(p0, p1), -add_f(pm1, p2));
+    r.q16 = fma(9.0, add_f(q0, q1), -add_f(qm1, q2));
+    const double rm = fma(r.p16, r.p16, mul_f(r.q16, r.q16));
+    r.qm3 = mul_f(__ldg(g.wsm3 + c), rm);
+    r.tm = mul_f(__ldg(g.wtm + c), rm);
+    r.De = fma(4.0 / 3.0, r.qm3, add_f(r.qn0, r.qn1));
+    r.y2 = add_f(-r.qn0, 1.0 / 3.0);
     r.y3 = fma(-r.qm3, r.y2, 1.0 / 3.0);
     r.ca = fma(-6.0, r.qn1, 2.0);
     r.e = fma(-r.qm3, r.ca, 2.0);
-    r.al = fma(r.y3, r.e, r.y2 - r.qn1);
+    r.al = fma(r.y3, r.e, add_f(r.y2, -r.qn1));
     r.w2 = fma(-r.qm3, r.rn0, r.tm);
-    r.be = fma(r.e, r.w2, fma(r.ca, r.tm, r.rn0 + r.rn1));
+    r.be = fma(r.e, r.w2, fma(r.ca, r.tm, add_f(r.rn0, r.rn1)));
     return r;
 }
 
@@ -374,9 +249,9 @@ __device__ __forceinline__ CellFwd cell_fwd_n(double qn0, double rn0, double qn1
 __device__ __forceinline__ CellFwd cell_fwd(const double *yP, const double *yQ, const GeoTab &g, int N, int c)
 {
     const double p0 = yP[c], p1 = yP[c + 1], q0 = yQ[c], q1 = yQ[c + 1];
-    const double rho0 = fma(p0, p0, q0 * q0), rho1 = fma(p1, p1, q1 * q1);
-    return cell_fwd_n(__ldg(g.ws + c) * rho0, __ldg(g.wt + c) * rho0, __ldg(g.ws + c + 1) * rho1,
-                      __ldg(g.wt + c + 1) * rho1, gv(yP, N, c - 1, -1.0, 1.0), p0, p1,
+    const double rho0 = fma(p0, p0, mul_f(q0, q0)), rho1 = fma(p1, p1, mul_f(q1, q1));
+    return cell_fwd_n(mul_f(__ldg(g.ws + c), rho0), mul_f(__ldg(g.wt + c), rho0), mul_f(__ldg(g.ws + c + 1), rho1),
+                      mul_f(__ldg(g.wt + c + 1), rho1), gv(yP, N, c - 1, -1.0, 1.0), p0, p1,
                       gv(yP, N, c + 2, -1.0, 1.0), gv(yQ, N, c - 1, 1.0, -1.0), q0, q1,
                       gv(yQ, N, c + 2, 1.0, -1.0), g, c);
 }
@@ -387,15 +262,15 @@ __device__ __forceinline__ void cell_bwd(const CellFwd &f, const GeoTab &g, int 
                                          double Deb, double &n0, double &n1, double &p16b, double &q16b)
 {
     // beta = (r0 + r1) + ca tm + e w2
-    double eb = beb * f.w2, cab = beb * f.tm, tmb = beb * f.ca, r0b = beb;
-    const double w2b = beb * f.e, r1b = beb;
+    double eb = mul_f(beb, f.w2), cab = mul_f(beb, f.tm), tmb = mul_f(beb, f.ca), r0b = beb;
+    const double w2b = mul_f(beb, f.e), r1b = beb;
     // alpha = (y2 - q1) + y3 e
-    const double y3b = alb * f.e;
+    const double y3b = mul_f(alb, f.e);
     eb = fma(alb, f.y3, eb);
     double y2b = alb, q1b = -alb;
     // w2 = tm - qm3 r0
-    tmb += w2b;
-    double qm3b = -w2b * f.rn0;
+    tmb = add_f(tmb, w2b);
+    double qm3b = mul_f(-w2b, f.rn0);
     r0b = fma(-w2b, f.qm3, r0b);
     // e = 2 - qm3 ca
     qm3b = fma(-eb, f.ca, qm3b);
@@ -406,14 +281,16 @@ __device__ __forceinline__ void cell_bwd(const CellFwd &f, const GeoTab &g, int 
     qm3b = fma(-y3b, f.y2, qm3b);
     y2b = fma(-y3b, f.qm3, y2b);
     // y2 = 1/3 - q0;  Delta = q0 + q1 + (4/3) qm3
-    const double q0b = Deb - y2b;
-    q1b += Deb;
+    const double q0b = add_f(Deb, -y2b);
+    q1b = add_f(q1b, Deb);
     qm3b = fma(4.0 / 3.0, Deb, qm3b);
-    n0 = fma(__ldg(g.ws + c), q0b, __ldg(g.wt + c) * r0b);
-    n1 = fma(__ldg(g.ws + c + 1), q1b, __ldg(g.wt + c + 1) * r1b);
-    const double rmb = fma(__ldg(g.wsm3 + c), qm3b, __ldg(g.wtm + c) * tmb);
-    p16b = 2.0 * f.p16 * rmb;
-    q16b = 2.0 * f.q16 * rmb;
+    n0 = fma(__ldg(g.ws + c), q0b, mul_f(__ldg(g.wt + c), r0b));
+    n1 = fma(__ldg(g.ws + c + 1), q1b, mul_f(__ldg(g.wt + c + 1), r1b));
+    const double rmb = fma(__ldg(g.wsm3 + c), qm3b, mul_f(__ldg(g.wtm + c), tmb));
+    // rho_m = (p16^2 + q16^2) / 256, the 1/256 folded into wsm3 and wtm; 2 rmb is exact
+    const double rmb2 = add_f(rmb, rmb);
+    p16b = mul_f(f.p16, rmb2);
+    q16b = mul_f(f.q16, rmb2);
 }
 
 // ------------------------------------------------------------------ CTA scratch layout
@@ -467,7 +344,7 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
             be[k] = cf.be;
             AL[i0 + k] = cf.al;
             if (k == 0) { aT = cf.al; bT = cf.be; SD = cf.De; }
-            else { bT = fma(cf.al, bT, cf.be); aT *= cf.al; SD += cf.De; }
+            else { bT = fma(cf.al, bT, cf.be); aT = mul_f(aT, cf.al); SD = add_f(SD, cf.De); }
         }
     }
     double mstart, dend;   // m at node i0; the sum of Delta over the cells from node i0 + AP on
@@ -476,20 +353,20 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
     if (act) {
         double dc = dend;
 #pragma unroll
-        for (int k = AP - 1; k >= 0; --k) { dc += De[k]; De[k] = dc; }
+        for (int k = AP - 1; k >= 0; --k) { dc = add_f(dc, De[k]); De[k] = dc; }
         double m = mstart;
 #pragma unroll
         for (int k = 0; k < AP; ++k) {
             const int i = i0 + k;
             const double A = fma(-m, __ldg(g.K + i), 1.0);
             const double Ei = a_exp_neg(1.0, De[k], tab);
-            const double Fi = A * Ei;
+            const double Fi = mul_f(A, Ei);
             M[i] = m;
             E[i] = Ei;
             F[i] = Fi;
-            const double gi = Fi * yP[i];
-            const double ui = __ldg(g.T + i) * gi;
-            scr.f[i] = Fi * yQ[i];
+            const double gi = mul_f(Fi, yP[i]);
+            const double ui = mul_f(__ldg(g.T + i), gi);
+            scr.f[i] = mul_f(Fi, yQ[i]);
             scr.u[i] = ui;
             if (k == 1) g1 = gi;
             if (k == 2) g2 = gi;
@@ -510,18 +387,18 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
 #pragma unroll
     for (int k = 0; k < AP; ++k) {
         const int i = i0 + k;
-        const double Df = (gv(scr.f, N, i - 2, 1.0, -1.0) - gv(scr.f, N, i + 2, 1.0, -1.0)) +
-                          8.0 * (gv(scr.f, N, i + 1, 1.0, -1.0) - gv(scr.f, N, i - 1, 1.0, -1.0));
-        const double Du = (gv(scr.u, N, i - 2, -1.0, 1.0) - gv(scr.u, N, i + 2, -1.0, 1.0)) +
-                          8.0 * (gv(scr.u, N, i + 1, -1.0, 1.0) - gv(scr.u, N, i - 1, -1.0, 1.0));
-        const double kp = fma(-20.0, yP[i], fma(15.0, gv(yP, N, i - 1, -1, 1) + gv(yP, N, i + 1, -1, 1),
-                          fma(-6.0, gv(yP, N, i - 2, -1, 1) + gv(yP, N, i + 2, -1, 1),
-                              gv(yP, N, i - 3, -1, 1) + gv(yP, N, i + 3, -1, 1))));
-        const double kq = fma(-20.0, yQ[i], fma(15.0, gv(yQ, N, i - 1, 1, -1) + gv(yQ, N, i + 1, 1, -1),
-                          fma(-6.0, gv(yQ, N, i - 2, 1, -1) + gv(yQ, N, i + 2, 1, -1),
-                              gv(yQ, N, i - 3, 1, -1) + gv(yQ, N, i + 3, 1, -1))));
-        double dP = fma(d.c12, Df, d.cko * kp);
-        double dQ = fma(__ldg(g.iT12 + i), Du, d.cko * kq);
+        const double Df = fma(8.0, add_f(gv(scr.f, N, i + 1, 1.0, -1.0), -gv(scr.f, N, i - 1, 1.0, -1.0)),
+                              add_f(gv(scr.f, N, i - 2, 1.0, -1.0), -gv(scr.f, N, i + 2, 1.0, -1.0)));
+        const double Du = fma(8.0, add_f(gv(scr.u, N, i + 1, -1.0, 1.0), -gv(scr.u, N, i - 1, -1.0, 1.0)),
+                              add_f(gv(scr.u, N, i - 2, -1.0, 1.0), -gv(scr.u, N, i + 2, -1.0, 1.0)));
+        const double kp = fma(-20.0, yP[i], fma(15.0, add_f(gv(yP, N, i - 1, -1, 1), gv(yP, N, i + 1, -1, 1)),
+                          fma(-6.0, add_f(gv(yP, N, i - 2, -1, 1), gv(yP, N, i + 2, -1, 1)),
+                              add_f(gv(yP, N, i - 3, -1, 1), gv(yP, N, i + 3, -1, 1)))));
+        const double kq = fma(-20.0, yQ[i], fma(15.0, add_f(gv(yQ, N, i - 1, 1, -1), gv(yQ, N, i + 1, 1, -1)),
+                          fma(-6.0, add_f(gv(yQ, N, i - 2, 1, -1), gv(yQ, N, i + 2, 1, -1)),
+                              add_f(gv(yQ, N, i - 3, 1, -1), gv(yQ, N, i + 3, 1, -1)))));
+        double dP = fma(d.c12, Df, mul_f(d.cko, kp));
+        double dQ = fma(__ldg(g.iT12 + i), Du, mul_f(d.cko, kq));
         if (i == 0) {
             dP = 0.0;
             dQ = fma(d.c3, fma(16.0, g1, -2.0 * g2), d.cko * kq);
@@ -551,10 +428,10 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
             const int c = i0 + k;
             const double a = AL[c];
             bT = fma(a, bT, scr.mb[c]);
-            aT *= a;
+            aT = mul_f(aT, a);
         }
 #pragma unroll
-        for (int k = 0; k < AP; ++k) SP += scr.dlb[i0 + k];
+        for (int k = 0; k < AP; ++k) SP = add_f(SP, scr.dlb[i0 + k]);
     }
     double mu_end, dpre;   // mu at node i0 + AP; the sum of delta_bar over the nodes < i0
     scan_pair<CL, true>(aT, bT, SP, sh, mu_end, dpre);
@@ -571,21 +448,21 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
         // the cells' forward data with the node quantities carried from cell to cell
         double pm1 = gv(yP, N, i0 - 1, -1.0, 1.0), p0 = yP[i0], p1 = yP[i0 + 1];
         double qm1 = gv(yQ, N, i0 - 1, 1.0, -1.0), q0 = yQ[i0], q1 = yQ[i0 + 1];
-        const double rho0 = fma(p0, p0, q0 * q0);
-        double qn0 = __ldg(g.ws + i0) * rho0, rn0 = __ldg(g.wt + i0) * rho0;
+        const double rho0 = fma(p0, p0, mul_f(q0, q0));
+        double qn0 = mul_f(__ldg(g.ws + i0), rho0), rn0 = mul_f(__ldg(g.wt + i0), rho0);
 #pragma unroll
         for (int k = 0; k < AP; ++k) {
             const int c = i0 + k;
-            Db += scr.dlb[c];                         // Delta_bar_c = sum_{i <= c} delta_bar_i
+            Db = add_f(Db, scr.dlb[c]);               // Delta_bar_c = sum_{i <= c} delta_bar_i
             const double p2 = gv(yP, N, c + 2, -1.0, 1.0), q2 = gv(yQ, N, c + 2, 1.0, -1.0);
-            const double rho1 = fma(p1, p1, q1 * q1);
-            const double qn1 = __ldg(g.ws + c + 1) * rho1, rn1 = __ldg(g.wt + c + 1) * rho1;
+            const double rho1 = fma(p1, p1, mul_f(q1, q1));
+            const double qn1 = mul_f(__ldg(g.ws + c + 1), rho1), rn1 = mul_f(__ldg(g.wt + c + 1), rho1);
             const CellFwd cf = cell_fwd_n(qn0, rn0, qn1, rn1, pm1, p0, p1, p2, qm1, q0, q1, q2, g, c);
             pm1 = p0; p0 = p1; p1 = p2;
             qm1 = q0; q0 = q1; q1 = q2;
             qn0 = qn1; rn0 = rn1;
             double n0, n1, pb, qb;
-            cell_bwd(cf, g, c, mun[k] * M[c], mun[k], Db, n0, n1, pb, qb);
+            cell_bwd(cf, g, c, mul_f(mun[k], M[c]), mun[k], Db, n0, n1, pb, qb);
             n0s[k] = n0;
             scr.r1[c] = n1;
             scr.pb[c] = pb;
@@ -600,16 +477,17 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
 #pragma unroll
         for (int k = 0; k < AP; ++k) {
             const int j = i0 + k;
-            const double rb = scr.fb[j] + (j >= 1 ? scr.r1[j - 1] : 0.0);
+            const double rb = add_f(scr.fb[j], j >= 1 ? scr.r1[j - 1] : 0.0);
             // transpose of p16_c = 9 (w_c + w_{c+1}) - (w_{c-1} + w_{c+2}), cells 0 .. N-2
             auto itp = [&](const double *b, int x) {
-                return 9.0 * (rv(b, N - 1, x) + rv(b, N - 1, x - 1)) - (rv(b, N - 1, x + 1) + rv(b, N - 1, x - 2));
+                return fma(9.0, add_f(rv(b, N - 1, x), rv(b, N - 1, x - 1)),
+                           -add_f(rv(b, N - 1, x + 1), rv(b, N - 1, x - 2)));
             };
             double pP = itp(scr.pb, j), pQ = itp(scr.qb, j);
             if (j == 1) { pP += -itp(scr.pb, -1); pQ += itp(scr.qb, -1); }                    // ghost -1
             if (j == N - 2) { pP += itp(scr.pb, N); pQ += -itp(scr.qb, N); }                  // ghost N
-            ybP[j] += fma(2.0 * yP[j], rb, pP);
-            ybQ[j] += fma(2.0 * yQ[j], rb, pQ);
+            ybP[j] = add_f(ybP[j], fma(add_f(yP[j], yP[j]), rb, pP));
+            ybQ[j] = add_f(ybQ[j], fma(add_f(yQ[j], yQ[j]), rb, pQ));
         }
     }
     // no barrier here: every caller updates only its own nodes next and then synchronises
@@ -632,11 +510,11 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
     const double *vP = scr.vP, *vQ = scr.vQ;
     const double *v2 = scr.v2;   // iT12-weighted Pi-dot sensitivities (zero at rows 0 and N-1)
     auto Dr = [&](const double *v, int x) {   // raw 4th-order difference of a row-restricted array
-        return (rv(v, N, x - 2) - rv(v, N, x + 2)) + 8.0 * (rv(v, N, x + 1) - rv(v, N, x - 1));
+        return fma(8.0, add_f(rv(v, N, x + 1), -rv(v, N, x - 1)), add_f(rv(v, N, x - 2), -rv(v, N, x + 2)));
     };
     auto KOr = [&](const double *v, int x) {  // raw dissipation stencil of a row-restricted array
-        return fma(-20.0, rv(v, N, x), fma(15.0, rv(v, N, x - 1) + rv(v, N, x + 1),
-               fma(-6.0, rv(v, N, x - 2) + rv(v, N, x + 2), rv(v, N, x - 3) + rv(v, N, x + 3))));
+        return fma(-20.0, rv(v, N, x), fma(15.0, add_f(rv(v, N, x - 1), rv(v, N, x + 1)),
+               fma(-6.0, add_f(rv(v, N, x - 2), rv(v, N, x + 2)), add_f(rv(v, N, x - 3), rv(v, N, x + 3)))));
     };
     if (act) {
         const double vQ0 = vQ[0];
@@ -662,16 +540,16 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
             if (j == N - 2) ubx += (4.0 / 3.0) * (-Dr(v2, N - 1));   // u(pi/2) extrapolation
             if (j == N - 3) ubx += (-1.0 / 3.0) * (-Dr(v2, N - 1));
             const double fb = fbx;   // (vP carries the factor c12, vQ the factor cq)
-            double gb = __ldg(g.T + j) * ubx;
+            double gb = mul_f(__ldg(g.T + j), ubx);
             if (j == 1) gb = fma(16.0 * d.c3q, vQ0, gb);            // Pi-dot(0) = 3 (F Phi)'(0)
             if (j == 2) gb = fma(-2.0 * d.c3q, vQ0, gb);
             const double Fj = F[j];
-            const double Fb = fma(fb, yQ[j], gb * yP[j]);
+            const double Fb = fma(fb, yQ[j], mul_f(gb, yP[j]));
             ybQ[j] = fma(fb, Fj, d.ko ? kqx : 0.0);
-            ybP[j] = fma(gb, Fj, d.rko * kpx);
-            const double Ab = Fb * E[j];
-            scr.dlb[j] = -Fb * Fj;
-            scr.mb[j] = -Ab * __ldg(g.K + j);
+            ybP[j] = fma(gb, Fj, mul_f(d.rko, kpx));
+            const double Ab = mul_f(Fb, E[j]);
+            scr.dlb[j] = mul_f(-Fb, Fj);
+            scr.mb[j] = mul_f(-Ab, __ldg(g.K + j));
         }
         if (last) { scr.dlb[N - 1] = 0.0; scr.mb[N - 1] = 0.0; }
     }
@@ -880,14 +758,14 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                     for (int k = 0; k < AP; ++k) {
                         const int i = i0 + k;
                         // kbar, scaled by c12 (Phi) and cq (Pi): the factors of Phi-dot and Pi-dot
-                        double kb = wst[s] * d.dtc * scr.lo[i], kq = wst[s] * d.dtq * scr.lq[i];
+                        double kb = mul_f(wst[s] * d.dtc, scr.lo[i]), kq = mul_f(wst[s] * d.dtq, scr.lq[i]);
                         if (s < 3) {
                             kb = fma(cst[s + 1] * d.dtc, scr.ybP[i], kb);
                             kq = fma(cst[s + 1] * d.dtq, scr.ybQ[i], kq);
                         }
                         scr.vP[i] = (i == 0) ? 0.0 : kb;   // Phi-dot(0) is identically zero
                         scr.vQ[i] = kq;
-                        scr.v2[i] = __ldg(g.iT12k + i) * kq;   // = iT12 kbar_Pi
+                        scr.v2[i] = mul_f(__ldg(g.iT12k + i), kq);   // = iT12 kbar_Pi
                     }
                     if (own.last) { scr.vP[N - 1] = 0.0; scr.vQ[N - 1] = 0.0; scr.v2[N - 1] = 0.0; }
                 }
@@ -897,8 +775,8 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                 if (act) {
 #pragma unroll
                     for (int k = 0; k < AP; ++k) {
-                        lamP[i0 + k] += scr.ybP[i0 + k];
-                        lamQ[i0 + k] += scr.ybQ[i0 + k];
+                        lamP[i0 + k] = add_f(lamP[i0 + k], scr.ybP[i0 + k]);
+                        lamQ[i0 + k] = add_f(lamQ[i0 + k], scr.ybQ[i0 + k]);
                     }
                 }
                 // no barrier: the next stage first touches only this thread's nodes, then

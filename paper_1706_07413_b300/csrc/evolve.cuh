@@ -481,21 +481,21 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                         ldg_run<P>(g.wtm + i0, gtm);
                         gws[P] = __ldg(g.wsk + i0 + P);
                         gwt[P] = __ldg(g.wt + i0 + P);
-                        const double rho0 = fma(p0, p0, q0 * q0);
-                        double qn0 = gws[0] * rho0, rn0 = gwt[0] * rho0;
+                        const double rho0 = fma(p0, p0, mul_f(q0, q0));
+                        double qn0 = mul_f(gws[0], rho0), rn0 = mul_f(gwt[0], rho0);
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const double p2 = Sp[soff<P>(k + 2)], q2 = Sq[soff<P>(k + 2)];
-                            const double rho1 = fma(p1, p1, q1 * q1);
-                            const double qn1 = gws[k + 1] * rho1;   // kappa q1
-                            const double rn1 = gwt[k + 1] * rho1;
+                            const double rho1 = fma(p1, p1, mul_f(q1, q1));
+                            const double qn1 = mul_f(gws[k + 1], rho1);   // kappa q1
+                            const double rn1 = mul_f(gwt[k + 1], rho1);
                             // 16 * (midpoint value) by the 4-point Lagrange formula
-                            const double p16 = fma(9.0, p0 + p1, -(pm1 + p2));
-                            const double q16 = fma(9.0, q0 + q1, -(qm1 + q2));
-                            const double rm = fma(p16, p16, q16 * q16);  // 256 rho_{c+1/2}
-                            const double qm3 = gwm[k] * rm;   // 3 (h s rho / 6) at the midpoint
-                            const double tm = gtm[k] * rm;    // h tan^2 rho / 6 there
-                            const double s01 = qn0 + qn1;                     // kappa (q0 + q1)
+                            const double p16 = fma(9.0, add_f(p0, p1), -add_f(pm1, p2));
+                            const double q16 = fma(9.0, add_f(q0, q1), -add_f(qm1, q2));
+                            const double rm = fma(p16, p16, mul_f(q16, q16));  // 256 rho_{c+1/2}
+                            const double qm3 = mul_f(gwm[k], rm);   // 3 (h s rho / 6) at the midpoint
+                            const double tm = mul_f(gtm[k], rm);    // h tan^2 rho / 6 there
+                            const double s01 = add_f(qn0, qn1);               // kappa (q0 + q1)
                             // Simpson increment of delta over the cell, in units of ln2/256
                             const double dek = fma(kKappa * (4.0 / 3.0), qm3, s01);
                             // RK4 in x of m' = a - b m over the cell as the affine map
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             const double e = fma(-qm3, ca, 2.0);
                             const double al = fma(y3, e, fma(-kInvKappa, s01, 1.0 / 3.0));
                             const double w2 = fma(-qm3, rn0, tm);
-                            const double be = fma(e, w2, fma(ca, tm, rn0 + rn1));
+                            const double be = fma(e, w2, fma(ca, tm, add_f(rn0, rn1)));
                             if (stg) {
                                 stg[i0 + k] = p0;
                                 stg[snm + i0 + k] = q0;
@@ -530,9 +530,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                                 SD = dek;
                             } else {
                                 bT = fma(al, bT, be);
-                                aT = aT * al;
+                                aT = mul_f(aT, al);
                                 De[k] = SD;
-                                SD = SD + dek;
+                                SD = add_f(SD, dek);
                             }
                             if (k < P - 1) {
                                 sF[tb + soff<P>(k + 1)] = aT;
@@ -555,9 +555,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                         const double dn = __shfl_down_sync(FULL, SD, o);
                         if (lane >= o) {
                             bT = fma(aT, bp, bT);
-                            aT = aT * ap;
+                            aT = mul_f(aT, ap);
                         }
-                        if (lane + o < 32) SD = SD + dn;
+                        if (lane + o < 32) SD = add_f(SD, dn);
                     }
                     double aEx = __shfl_up_sync(FULL, aT, 1);
                     double bEx = __shfl_up_sync(FULL, bT, 1);
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                         // delta at node i0+k: dtop minus the increments of the cells i0 .. i0+k-1
                         De[0] = dtop;
 #pragma unroll
-                        for (int k = 1; k < P; ++k) De[k] = dtop - De[k];
+                        for (int k = 1; k < P; ++k) De[k] = add_f(dtop, -De[k]);
                         double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0, fm1 = 0.0, fm2 = 0.0;
                         double f0 = 0.0, f1 = 0.0, u0 = 0.0, u1 = 0.0;
                         double gK[P], gT[P];
@@ -644,15 +644,15 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             const double Ai = fma(-mk, gK[k], 1.0);
                             kmin = min_ll(kmin, order_key(Ai));
                             const double Ei = a_exp_neg_scaled(1.0, De[k], s_tab);   // e^{-delta}
-                            const double Fi = Ai * Ei;
+                            const double Fi = mul_f(Ai, Ei);
                             if (stg) {
                                 stg[2 * snm + i] = mk;
                                 stg[3 * snm + i] = Ei;
                                 stg[4 * snm + i] = Fi;
                             }
-                            const double gi = Fi * Sp[soff<P>(k)];
-                            const double fi = Fi * Sq[soff<P>(k)];
-                            const double ui = gT[k] * gi;
+                            const double gi = mul_f(Fi, Sp[soff<P>(k)]);
+                            const double fi = mul_f(Fi, Sq[soff<P>(k)]);
+                            const double ui = mul_f(gT[k], gi);
                             sF[tb + soff<P>(k)] = fi;
                             sU[tb + soff<P>(k)] = ui;
                             if (k == 0) { f0 = fi; u0 = ui; }
@@ -778,18 +778,18 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
-                            const double Df = (f[soff<P>(k - 2)] - f[soff<P>(k + 2)]) +
-                                              8.0 * (f[soff<P>(k + 1)] - f[soff<P>(k - 1)]);
-                            const double Du = (u[soff<P>(k - 2)] - u[soff<P>(k + 2)]) +
-                                              8.0 * (u[soff<P>(k + 1)] - u[soff<P>(k - 1)]);
+                            const double Df = fma(8.0, add_f(f[soff<P>(k + 1)], -f[soff<P>(k - 1)]),
+                                                  add_f(f[soff<P>(k - 2)], -f[soff<P>(k + 2)]));
+                            const double Du = fma(8.0, add_f(u[soff<P>(k + 1)], -u[soff<P>(k - 1)]),
+                                                  add_f(u[soff<P>(k - 2)], -u[soff<P>(k + 2)]));
                             const double kp = fma(-20.0, Sp[soff<P>(k)],
-                                fma(15.0, Sp[soff<P>(k - 1)] + Sp[soff<P>(k + 1)],
-                                fma(-6.0, Sp[soff<P>(k - 2)] + Sp[soff<P>(k + 2)],
-                                    Sp[soff<P>(k - 3)] + Sp[soff<P>(k + 3)])));
+                                fma(15.0, add_f(Sp[soff<P>(k - 1)], Sp[soff<P>(k + 1)]),
+                                fma(-6.0, add_f(Sp[soff<P>(k - 2)], Sp[soff<P>(k + 2)]),
+                                    add_f(Sp[soff<P>(k - 3)], Sp[soff<P>(k + 3)]))));
                             const double kq = fma(-20.0, Sq[soff<P>(k)],
-                                fma(15.0, Sq[soff<P>(k - 1)] + Sq[soff<P>(k + 1)],
-                                fma(-6.0, Sq[soff<P>(k - 2)] + Sq[soff<P>(k + 2)],
-                                    Sq[soff<P>(k - 3)] + Sq[soff<P>(k + 3)])));
+                                fma(15.0, add_f(Sq[soff<P>(k - 1)], Sq[soff<P>(k + 1)]),
+                                fma(-6.0, add_f(Sq[soff<P>(k - 2)], Sq[soff<P>(k + 2)]),
+                                    add_f(Sq[soff<P>(k - 3)], Sq[soff<P>(k + 3)]))));
                             // Phi-dot = c12 (Df + rko kp) and Pi-dot = cq (iT12k Du + kq): the factors
                             // c12 and cq are folded into the RK weights
                             double Xp = fma(d.rko, kp, Df);

@@ -252,34 +252,34 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                         ldg_run<P>(g.wsk + i0, gws);
                         ldg_run<P>(g.wsm3 + i0, gwm);
                         gws[P] = __ldg(g.wsk + i0 + P);
-                        const double rho0 = fma(p0, p0, q0 * q0);
-                        double qn0 = gws[0] * rho0, rn0 = __ldg(g.wt + i0) * rho0;
+                        const double rho0 = fma(p0, p0, mul_f(q0, q0));
+                        double qn0 = mul_f(gws[0], rho0), rn0 = mul_f(__ldg(g.wt + i0), rho0);
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int c = i0 + k;
                             const double p2 = Sp[soff<P>(k + 2)], q2 = Sq[soff<P>(k + 2)];
-                            const double rho1 = fma(p1, p1, q1 * q1);
-                            const double qn1 = gws[k + 1] * rho1;   // kappa q1
-                            const double p16 = fma(9.0, p0 + p1, -(pm1 + p2));
-                            const double q16 = fma(9.0, q0 + q1, -(qm1 + q2));
-                            const double rm = fma(p16, p16, q16 * q16);
-                            const double qm3 = gwm[k] * rm;
-                            const double s01 = qn0 + qn1;
+                            const double rho1 = fma(p1, p1, mul_f(q1, q1));
+                            const double qn1 = mul_f(gws[k + 1], rho1);   // kappa q1
+                            const double p16 = fma(9.0, add_f(p0, p1), -add_f(pm1, p2));
+                            const double q16 = fma(9.0, add_f(q0, q1), -add_f(qm1, q2));
+                            const double rm = fma(p16, p16, mul_f(q16, q16));
+                            const double qm3 = mul_f(gwm[k], rm);
+                            const double s01 = add_f(qn0, qn1);
                             const double dek = fma(kKappa * (4.0 / 3.0), qm3, s01);   // units of ln2/256
                             // De[k] (k >= 1): sum of the increments of cells i0 .. i0+k-1
                             if (k > 0) De[k] = SD;
-                            SD = (k == 0) ? dek : SD + dek;
+                            SD = (k == 0) ? dek : add_f(SD, dek);
                             if (reint) {
                                 // the affine map of the mass function over the cell (evolve_kernel)
-                                const double rn1 = __ldg(g.wt + c + 1) * rho1;
-                                const double tm = __ldg(g.wtm + c) * rm;
+                                const double rn1 = mul_f(__ldg(g.wt + c + 1), rho1);
+                                const double tm = mul_f(__ldg(g.wtm + c), rm);
                                 const double y2 = fma(-kInvKappa, qn0, 1.0 / 3.0);
                                 const double y3 = fma(-qm3, y2, 1.0 / 3.0);
                                 const double ca = fma(-6.0 * kInvKappa, qn1, 2.0);
                                 const double e = fma(-qm3, ca, 2.0);
                                 const double al = fma(y3, e, fma(-kInvKappa, s01, 1.0 / 3.0));
                                 const double w2 = fma(-qm3, rn0, tm);
-                                const double be = fma(e, w2, fma(ca, tm, rn0 + rn1));
+                                const double be = fma(e, w2, fma(ca, tm, add_f(rn0, rn1)));
                                 sF[tb + soff<P>(k)] = al;
                                 sU[tb + soff<P>(k)] = be;
                                 if (k == 0) {
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                     bT = be;
                                 } else {
                                     bT = fma(al, bT, be);
-                                    aT = aT * al;
+                                    aT = mul_f(aT, al);
                                 }
                                 rn0 = rn1;
                             }
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const double dn = __shfl_down_sync(FULL, SD, o);
-                        if (lane + o < 32) SD = SD + dn;
+                        if (lane + o < 32) SD = add_f(SD, dn);
                     }
                     if (reint) {
 #pragma unroll
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             const double bp = __shfl_up_sync(FULL, bT, o);
                             if (lane >= o) {
                                 bT = fma(aT, bp, bT);
-                                aT = aT * ap;
+                                aT = mul_f(aT, ap);
                             }
                         }
                     }
@@ -329,9 +329,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             const double dn = __shfl_down_sync(FULL, D_, o);
                             if (lane >= o) {
                                 B_ = fma(A_, bp, B_);
-                                A_ = A_ * ap;
+                                A_ = mul_f(A_, ap);
                             }
-                            if (lane + o < NW) D_ = D_ + dn;
+                            if (lane + o < NW) D_ = add_f(D_, dn);
                         }
                         double bw = __shfl_up_sync(FULL, B_, 1);
                         double dw = __shfl_down_sync(FULL, D_, 1);
@@ -380,10 +380,10 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             m = fma(aEx, cm, bEx);
                             // delta at node i0 from the inclusive suffix sum SD, then at node i0+k
                             // by subtracting the increments of the cells i0 .. i0+k-1
-                            const double dtop = SD + cD[wid] + dr;
+                            const double dtop = add_f(add_f(SD, cD[wid]), dr);
                             De[0] = dtop;
 #pragma unroll
-                            for (int k = 1; k < P; ++k) De[k] = dtop - De[k];
+                            for (int k = 1; k < P; ++k) De[k] = add_f(dtop, -De[k]);
                         }
                         double g1 = 0.0, g2 = 0.0, um1 = 0.0, um2 = 0.0, fm1 = 0.0, fm2 = 0.0;
                         double f0 = 0.0, f1 = 0.0, u0 = 0.0, u1 = 0.0;
@@ -406,21 +406,21 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                 Ai = (s == 0) ? __ldcg(uA + i) : __ldcg(sA + k * TnAll + bs + tid);
                             }
                             const double Fi = FIXED ? 1.0 : a_exp_neg_scaled(Ai, De[k], s_tab);
-                            const double gi = FIXED ? ph : Fi * ph;
-                            const double fi = FIXED ? pi : Fi * pi;
-                            const double ui = gT[k] * gi;
+                            const double gi = FIXED ? ph : mul_f(Fi, ph);
+                            const double fi = FIXED ? pi : mul_f(Fi, pi);
+                            const double ui = mul_f(gT[k], gi);
                             if constexpr (!FIXED) {
                                 // A-dot = -2 sin x cos x A (A e^{-delta} Phi) Pi, and the stage update
-                                const double dA = gK2[k] * Ai * gi * pi;
+                                const double dA = mul_f(mul_f(mul_f(gK2[k], Ai), gi), pi);
                                 const double An = (s == 0) ? fma(dt, dA, Ai)
-                                                           : fma(wb, fma(dt, dA, Ai), wa * __ldcg(uA + i));
+                                                           : fma(wb, fma(dt, dA, Ai), mul_f(wa, __ldcg(uA + i)));
                                 if (s < R - 1) sA[k * TnAll + bs + tid] = An;
                                 else uA[i] = An;
                             }
                             if (s == 0) {
                                 kmin = min_ll(kmin, order_key(Ai));
-                                msum = FIXED ? fma(__ldg(eg.wsim + i), fma(ph, ph, pi * pi), msum)
-                                             : fma(__ldg(eg.wsim + i) * Ai, fma(ph, ph, pi * pi), msum);
+                                msum = FIXED ? fma(__ldg(eg.wsim + i), fma(ph, ph, mul_f(pi, pi)), msum)
+                                             : fma(mul_f(__ldg(eg.wsim + i), Ai), fma(ph, ph, mul_f(pi, pi)), msum);
                             }
                             sF[tb + soff<P>(k)] = fi;
                             sU[tb + soff<P>(k)] = ui;
@@ -542,18 +542,18 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
-                            const double Df = (f[soff<P>(k - 2)] - f[soff<P>(k + 2)]) +
-                                              8.0 * (f[soff<P>(k + 1)] - f[soff<P>(k - 1)]);
-                            const double Du = (u[soff<P>(k - 2)] - u[soff<P>(k + 2)]) +
-                                              8.0 * (u[soff<P>(k + 1)] - u[soff<P>(k - 1)]);
+                            const double Df = fma(8.0, add_f(f[soff<P>(k + 1)], -f[soff<P>(k - 1)]),
+                                                  add_f(f[soff<P>(k - 2)], -f[soff<P>(k + 2)]));
+                            const double Du = fma(8.0, add_f(u[soff<P>(k + 1)], -u[soff<P>(k - 1)]),
+                                                  add_f(u[soff<P>(k - 2)], -u[soff<P>(k + 2)]));
                             const double kp = fma(-20.0, Sp[soff<P>(k)],
-                                fma(15.0, Sp[soff<P>(k - 1)] + Sp[soff<P>(k + 1)],
-                                fma(-6.0, Sp[soff<P>(k - 2)] + Sp[soff<P>(k + 2)],
-                                    Sp[soff<P>(k - 3)] + Sp[soff<P>(k + 3)])));
+                                fma(15.0, add_f(Sp[soff<P>(k - 1)], Sp[soff<P>(k + 1)]),
+                                fma(-6.0, add_f(Sp[soff<P>(k - 2)], Sp[soff<P>(k + 2)]),
+                                    add_f(Sp[soff<P>(k - 3)], Sp[soff<P>(k + 3)]))));
                             const double kq = fma(-20.0, Sq[soff<P>(k)],
-                                fma(15.0, Sq[soff<P>(k - 1)] + Sq[soff<P>(k + 1)],
-                                fma(-6.0, Sq[soff<P>(k - 2)] + Sq[soff<P>(k + 2)],
-                                    Sq[soff<P>(k - 3)] + Sq[soff<P>(k + 3)])));
+                                fma(15.0, add_f(Sq[soff<P>(k - 1)], Sq[soff<P>(k + 1)]),
+                                fma(-6.0, add_f(Sq[soff<P>(k - 2)], Sq[soff<P>(k + 2)]),
+                                    add_f(Sq[soff<P>(k - 3)], Sq[soff<P>(k + 3)]))));
                             double Xp = fma(d.rko, kp, Df);   // Phi-dot / c12
                             const double kqs = d.ko ? kq : 0.0;
                             double dQ = fma(gI[k], Du, kqs);   // Pi-dot / cq
@@ -566,8 +566,8 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                 np = fma(d.dtc, Xp, Sp[soff<P>(k)]);
                                 nq = fma(d.dtq, dQ, Sq[soff<P>(k)]);
                             } else {
-                                np = fma(wbdc, Xp, fma(wb, Sp[soff<P>(k)], wa * __ldcg(uPhi + i)));
-                                nq = fma(wbd, dQ, fma(wb, Sq[soff<P>(k)], wa * __ldcg(uPi + i)));
+                                np = fma(wbdc, Xp, fma(wb, Sp[soff<P>(k)], mul_f(wa, __ldcg(uPhi + i))));
+                                nq = fma(wbd, dQ, fma(wb, Sq[soff<P>(k)], mul_f(wa, __ldcg(uPi + i))));
                             }
                             if (k == 0 && tfirst) np = 0.0;
                             if (s == R - 1) {
