@@ -34,6 +34,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "expneg.cuh"
 
@@ -775,6 +776,10 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                         double *Dp = D0 + tb, *Dq = D1 + tb;
                         double gI[P];
                         ldg_run<P>(g.iT12k + i0, gI);
+                        // the node loop, compiled once per stage kind (first, middle, last) so that no stage
+                        // issues another's FP64 work with its lanes predicated off
+                        auto update_nodes = [&](auto stage_kind) {
+                        constexpr int KIND = decltype(stage_kind)::value;
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
@@ -802,10 +807,10 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             // the slice u_n: the stage itself at s = 0, from global memory at
                             // s = 1, 2, not needed at s = 3
                             double up = 0.0, uq = 0.0;
-                            if (s == 0) {
+                            if constexpr (KIND == 0) {
                                 up = Sp[soff<P>(k)];
                                 uq = Sq[soff<P>(k)];
-                            } else if (s < 3) {
+                            } else if constexpr (KIND == 1) {
                                 up = __ldcg(uPhi + i);
                                 uq = __ldcg(uPi + i);
                             }
@@ -813,7 +818,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             // block t at k * TnAll + t), so that a warp's accesses are contiguous
                             const int ci = k * TnAll + bs + tid;
                             double ap_, aq_;
-                            if (s == 0) {
+                            if constexpr (KIND == 0) {
                                 ap_ = fma(waccc, Xp, up);
                                 aq_ = fma(wacc, dQ, uq);
                             } else {
@@ -821,7 +826,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                                 aq_ = fma(wacc, dQ, __ldcg(cPi + ci));
                             }
                             double np, nq;
-                            if (s < 3) {
+                            if constexpr (KIND < 2) {
                                 cPhi[ci] = ap_;
                                 cPi[ci] = aq_;
                                 np = fma(wstc, Xp, up);
@@ -853,6 +858,10 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                                 }
                             }
                         }
+                        };
+                        if (s == 0) update_nodes(std::integral_constant<int, 0>{});
+                        else if (s < 3) update_nodes(std::integral_constant<int, 1>{});
+                        else update_nodes(std::integral_constant<int, 2>{});
                         if (last) {
                             D0[spos<P>(Nl - 1)] = 0.0;
                             D1[spos<P>(Nl - 1)] = 0.0;

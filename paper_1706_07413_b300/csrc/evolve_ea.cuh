@@ -28,6 +28,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "evolve.cuh"
 
@@ -254,6 +255,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                         gws[P] = __ldg(g.wsk + i0 + P);
                         const double rho0 = fma(p0, p0, mul_f(q0, q0));
                         double qn0 = mul_f(gws[0], rho0), rn0 = mul_f(__ldg(g.wt + i0), rho0);
+                        // compiled once with the mass map (re-integration slices) and once without
+                        auto cell_nodes = [&](auto with_map) {
+                        constexpr bool REINT = decltype(with_map)::value;
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int c = i0 + k;
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             // De[k] (k >= 1): sum of the increments of cells i0 .. i0+k-1
                             if (k > 0) De[k] = SD;
                             SD = (k == 0) ? dek : add_f(SD, dek);
-                            if (reint) {
+                            if constexpr (REINT) {
                                 // the affine map of the mass function over the cell (evolve_kernel)
                                 const double rn1 = mul_f(__ldg(g.wt + c + 1), rho1);
                                 const double tm = mul_f(__ldg(g.wtm + c), rm);
@@ -295,6 +299,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             qm1 = q0; q0 = q1; q1 = q2;
                             qn0 = qn1;
                         }
+                        };
+                        if (reint) cell_nodes(std::true_type{});
+                        else cell_nodes(std::false_type{});
                     }
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
@@ -390,6 +397,10 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                         double gT[P], gK2[P];
                         ldg_run<P>(g.T + i0, gT);
                         if constexpr (!FIXED) ldg_run<P>(eg.K2 + i0, gK2);
+                        // the node loop, compiled once for the first stage of a step and once for the later
+                        // stages, so that no stage issues the other's FP64 work with its lanes predicated off
+                        auto flux_nodes = [&](auto first_stage) {
+                        constexpr bool FIRST = decltype(first_stage)::value;
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
@@ -397,13 +408,13 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             double Ai;
                             if (FIXED) {
                                 Ai = 1.0;
-                            } else if (reint) {
+                            } else if (FIRST && reint) {   // re-integration slices are first stages
                                 const double al = sF[tb + soff<P>(k)], be = sU[tb + soff<P>(k)];
                                 Ai = fma(-m, __ldg(g.K + i), 1.0);
                                 uA[i] = Ai;   // the slice's A is the constraint solution
                                 if (k < P - 1) m = fma(al, m, be);
                             } else {
-                                Ai = (s == 0) ? __ldcg(uA + i) : __ldcg(sA + k * TnAll + bs + tid);
+                                Ai = FIRST ? __ldcg(uA + i) : __ldcg(sA + k * TnAll + bs + tid);
                             }
                             const double Fi = FIXED ? 1.0 : a_exp_neg_scaled(Ai, De[k], s_tab);
                             const double gi = FIXED ? ph : mul_f(Fi, ph);
@@ -412,12 +423,12 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             if constexpr (!FIXED) {
                                 // A-dot = -2 sin x cos x A (A e^{-delta} Phi) Pi, and the stage update
                                 const double dA = mul_f(mul_f(mul_f(gK2[k], Ai), gi), pi);
-                                const double An = (s == 0) ? fma(dt, dA, Ai)
+                                const double An = FIRST ? fma(dt, dA, Ai)
                                                            : fma(wb, fma(dt, dA, Ai), mul_f(wa, __ldcg(uA + i)));
                                 if (s < R - 1) sA[k * TnAll + bs + tid] = An;
                                 else uA[i] = An;
                             }
-                            if (s == 0) {
+                            if constexpr (FIRST) {
                                 kmin = min_ll(kmin, order_key(Ai));
                                 msum = FIXED ? fma(__ldg(eg.wsim + i), fma(ph, ph, mul_f(pi, pi)), msum)
                                              : fma(mul_f(__ldg(eg.wsim + i), Ai), fma(ph, ph, mul_f(pi, pi)), msum);
@@ -438,6 +449,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                 a.outDelta[d.off + i] = De[k] * kInvKappa;
                             }
                         }
+                        };
+                        if (s == 0) flux_nodes(std::true_type{});
+                        else flux_nodes(std::false_type{});
                         if (tfirst) {
                             const double d0n = De[0] * kInvKappa;   // delta(0)
                             s_d0 = d0n;
@@ -539,6 +553,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                         double *Dp = D0 + tb, *Dq = D1 + tb;
                         double gI[P];
                         ldg_run<P>(g.iT12k + i0, gI);
+                        // compiled per stage kind as the flux loop
+                        auto update_nodes = [&](auto first_stage) {
+                        constexpr bool FIRST = decltype(first_stage)::value;
 #pragma unroll
                         for (int k = 0; k < P; ++k) {
                             const int i = i0 + k;
@@ -562,7 +579,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                 dQ = fma(d.c3q, sF[spos<P>(-3)], kqs);
                             }
                             double np, nq;
-                            if (s == 0) {
+                            if constexpr (FIRST) {
                                 np = fma(d.dtc, Xp, Sp[soff<P>(k)]);
                                 nq = fma(d.dtq, dQ, Sq[soff<P>(k)]);
                             } else {
@@ -595,6 +612,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                 }
                             }
                         }
+                        };
+                        if (s == 0) update_nodes(std::true_type{});
+                        else update_nodes(std::false_type{});
                         if (last) {
                             D0[spos<P>(Nl - 1)] = 0.0;
                             D1[spos<P>(Nl - 1)] = 0.0;
