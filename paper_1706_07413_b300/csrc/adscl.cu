@@ -1247,6 +1247,13 @@ __global__ void set_step_kernel(InstState *st, int B, long long step)
     if (b < B) st[b].step = step;
 }
 
+// delta from the solve mode's units of ln2/256 to natural units
+__global__ void delta_units_kernel(double *delta, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) delta[i] *= kInvKappa;
+}
+
 // one adjoint launch on stream sm; lane 0 or 1 selects the work counter and the per-CTA scratch
 // (the two lanes may run at the same time)
 adscl_status launch_adjoint(adscl_ctx *ctx, AdjArgs &a, cudaStream_t sm, int lane)
@@ -1716,7 +1723,13 @@ adscl_status adscl_get_state(adscl_ctx *ctx, int32_t inst, double *Phi, double *
                           ctx->stream);
         if (s != ADSCL_OK) return s;
         if (A) CK(cudaMemcpyAsync(A, ctx->d_scratchA + off, nb, kind, ctx->stream));
-        if (delta) CK(cudaMemcpyAsync(delta, ctx->d_scratchD + off, nb, kind, ctx->stream));
+        if (delta) {
+            const int n = ctx->N[inst];
+            delta_units_kernel<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_scratchD + off, n);
+            CK(cudaGetLastError());
+            ctx->launches += 1;
+            CK(cudaMemcpyAsync(delta, ctx->d_scratchD + off, nb, kind, ctx->stream));
+        }
     }
     if (Phi) CK(cudaMemcpyAsync(Phi, ctx->d_Phi + off, nb, kind, ctx->stream));
     if (Pi) CK(cudaMemcpyAsync(Pi, ctx->d_Pi + off, nb, kind, ctx->stream));

@@ -156,7 +156,9 @@ struct EvolveArgs {
     long long max_spin;    // iteration limit of a wait
     double t_end;
     double theta;
-    double *outA, *outDelta;  // kModeSolve only: packed A, delta of the slice (may be null)
+    // kModeSolve only: packed A and delta of the slice (may be null); delta in units of ln2/256,
+    // scaled by the caller, so that the node loop issues no multiplication for it
+    double *outA, *outDelta;
     // kModeEvolve, optional (stage == null: off): the record of every stage of steps
     // 0 .. stage_steps-1 that the discrete adjoint sweeps backwards (see stage_slot)
     double *stage;
@@ -667,7 +669,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             if (k == P - 2) { fm2 = fi; um2 = ui; }
                             if (a.outA) {
                                 a.outA[d.off + i] = Ai;
-                                a.outDelta[d.off + i] = De[k] * kInvKappa;
+                                a.outDelta[d.off + i] = De[k];   // in units of ln2/256 (no FP64 work here)
                             }
                         }
                         if (last) {
@@ -797,13 +799,12 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                                     add_f(Sq[soff<P>(k - 3)], Sq[soff<P>(k + 3)]))));
                             // Phi-dot = c12 (Df + rko kp) and Pi-dot = cq (iT12k Du + kq): the factors
                             // c12 and cq are folded into the RK weights
-                            double Xp = fma(d.rko, kp, Df);
+                            // at node 0: Phi(0) = 0 and Pi-dot = 3 (F Phi)'(0) / cq, chosen by operand
+                            // and result selects so that no thread issues a predicated-off FMA
+                            const bool origin = (k == 0) && tfirst;
                             const double kqs = d.ko ? kq : 0.0;
-                            double dQ = fma(gI[k], Du, kqs);
-                            if (k == 0 && tfirst) {
-                                Xp = 0.0;                                   // Phi(0) = 0
-                                dQ = fma(d.c3q, sF[spos<P>(-3)], kqs);     // 3 (F Phi)'(0) / cq
-                            }
+                            const double Xp = origin ? 0.0 : fma(d.rko, kp, Df);
+                            const double dQ = fma(origin ? d.c3q : gI[k], origin ? sF[spos<P>(-3)] : Du, kqs);
                             // the slice u_n: the stage itself at s = 0, from global memory at
                             // s = 1, 2, not needed at s = 3
                             double up = 0.0, uq = 0.0;

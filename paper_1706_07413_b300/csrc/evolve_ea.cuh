@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             if (k == P - 2) { fm2 = fi; um2 = ui; }
                             if (a.outA) {
                                 a.outA[d.off + i] = Ai;
-                                a.outDelta[d.off + i] = De[k] * kInvKappa;
+                                a.outDelta[d.off + i] = De[k];   // in units of ln2/256 (no FP64 work here)
                             }
                         }
                         };
