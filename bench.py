@@ -225,8 +225,8 @@ def workload_insts(name, rank, world=1):
         "uneven": ("uneven batch: B=192 per GPU, N uniform in {2049, 4097, 8193}, "
                    "Pi = sum_{j<16} eps e^{-j/3}(1+0.05 N(0,1)) e_j, eps U[0.05,0.2]"),
         "production": ("production resolution: B=15 Gaussian pulses per GPU at N=32769 (one "
-                       "8-CTA cluster each: the 15 that fit at once, 120 SMs), sigma=1/16, eps "
-                       "log-uniform [5,80], early exit at min A < 2^-7"),
+                       "cluster each: the 15 clusters of 8 or 9 CTAs that fit at once), "
+                       "sigma=1/16, eps log-uniform [5,80], early exit at min A < 2^-7"),
     }[name]
     return insts, idx, desc
 

@@ -104,10 +104,12 @@ typedef struct {
 } adscl_config;
 
 /* Largest grid size N one instance may use with this library: 65537 (the paper's Table II
- * grid).  Grids up to 4097 run on one CTA (one SM) per instance, larger ones on a thread-block
- * cluster of 2, 4, 8 or 16 CTAs sharing the instance through distributed shared memory (16 CTAs,
- * for N > 32769, is a non-portable cluster size: on a device that cannot place such a cluster,
- * adscl_create returns ADSCL_EUNSUPPORTED for those grids). */
+ * grid).  Grids up to 4097 run on one CTA (one SM) per instance by default, larger ones on a
+ * thread-block cluster of 2, 4, 8 or 16 CTAs sharing the instance through distributed shared
+ * memory (16 CTAs, for N > 32769, is a non-portable cluster size: on a device that cannot place
+ * such a cluster, adscl_create returns ADSCL_EUNSUPPORTED for those grids).  adscl_autotune and
+ * adscl_set_shape may also choose a 9-CTA cluster (P = 8, NT = 512) for 73 <= N <= 36865, also
+ * non-portable: on a B300 15 such clusters are co-resident (135 SMs) against 15 of 8 CTAs. */
 int32_t adscl_max_points(void);
 
 /* Create a context: validates cfg (ADSCL_EINVAL before any allocation or launch), builds the

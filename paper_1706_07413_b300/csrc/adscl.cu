@@ -207,7 +207,7 @@ double step_for(int N, double cfl, double cadence)
     return cadence / std::ceil(cadence / (cfl * h));
 }
 
-// the evolved-A / fixed-metric kernel is built for the shapes (8, 512, 1/2/4/8/16), (8, 256, 2) and
+// the evolved-A / fixed-metric kernel is built for the shapes (8, 512, 1/2/4/8/9/16), (8, 256, 2) and
 // (8, 128, 2); ea_dispatch calls f.template operator()<NT, CL>() for the shape with index id
 bool ea_shape(int id)
 {
@@ -249,7 +249,8 @@ cudaError_t ea_select(int id, bool launch, const void **fn, const EaArgs *ea, in
         if (fn) *fn = (const void *)evolve_ea_kernel<kP, NT_, FIXED, CL_>;                  \
         return launch ? ea_launch_t<FIXED, NT_, CL_>(*ea, units, smem, stride, sm) : cudaSuccess; \
     }
-    ADSCL_EA(512, 1) ADSCL_EA(512, 2) ADSCL_EA(512, 4) ADSCL_EA(512, 8) ADSCL_EA(512, 16) ADSCL_EA(256, 2)
+    ADSCL_EA(512, 1) ADSCL_EA(512, 2) ADSCL_EA(512, 4) ADSCL_EA(512, 8) ADSCL_EA(512, 9) ADSCL_EA(512, 16)
+    ADSCL_EA(256, 2)
     ADSCL_EA(128, 2)
 #undef ADSCL_EA
     return cudaErrorInvalidValue;
@@ -947,7 +948,7 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
         if (!ea_shape(id)) continue;
         CK(cudaFuncSetAttribute(ea_kernel_of<false>(id), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
         CK(cudaFuncSetAttribute(ea_kernel_of<true>(id), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-        if (kShapes[id].CL > 8) {   // 16 CTAs: beyond the portable cluster size
+        if (kShapes[id].CL > 8) {   // 9 or 16 CTAs: beyond the portable cluster size
             CK(cudaFuncSetAttribute(ea_kernel_of<false>(id), cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
             CK(cudaFuncSetAttribute(ea_kernel_of<true>(id), cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         }

@@ -271,8 +271,8 @@ __device__ __forceinline__ void st_others(T *p, T v, int rank) {
 template <int CL>
 __device__ __forceinline__ int block_start(int r, int T) { return (r * T + CL - 1) / CL; }
 
-// CL = 1: one CTA per instance.  CL = 2, 4, 8, 16: a cluster of CL CTAs per instance (16: a
-// non-portable cluster size, allowed per kernel by the host), rank r owning
+// CL = 1: one CTA per instance.  CL > 1: a cluster of CL CTAs per instance (built for 2, 4, 8, 9
+// and 16; 9 and 16 are non-portable cluster sizes, allowed per kernel by the host), rank r owning
 // the node blocks block_start(r) .. block_start(r+1)-1 (at least NT/2 blocks each, so P >= 3
 // halo nodes always come from the neighbouring rank); halos, scan carries and the step-end
 // diagnostics cross between the CTAs through distributed shared memory.
@@ -283,7 +283,7 @@ template <int P, int NT, int CL = 1, bool REC = false>
 __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(EvolveArgs a, int stride)
 {
     static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
-    static_assert(CL == 1 || CL == 2 || CL == 4 || CL == 8 || CL == 16, "cluster of 1, 2, 4, 8 or 16 CTAs");
+    static_assert(CL >= 1 && CL <= 16, "cluster of 1 to 16 CTAs");
     constexpr int NW = NT / 32;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ double smem[];

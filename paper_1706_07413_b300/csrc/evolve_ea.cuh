@@ -52,7 +52,7 @@ template <int P, int NT, bool FIXED = false, int CL = 1>
 __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kernel(EaArgs ea, int stride)
 {
     static_assert(P >= 4 && (P & (P - 1)) == 0, "P: power of two >= 4");
-    static_assert(CL == 1 || CL == 2 || CL == 4 || CL == 8 || CL == 16, "cluster of 1, 2, 4, 8 or 16 CTAs");
+    static_assert(CL >= 1 && CL <= 16, "cluster of 1 to 16 CTAs");
     constexpr int NW = NT / 32;
     constexpr unsigned FULL = 0xffffffffu;
     const EvolveArgs &a = ea.e;

@@ -12,7 +12,7 @@ namespace adscl {
     X(6, 8, 256, 1) X(7, 8, 256, 2) X(8, 8, 256, 4)                                      \
     X(9, 4, 256, 1) X(10, 4, 256, 2) X(11, 4, 256, 4)                                    \
     X(12, 8, 128, 1) X(13, 4, 128, 1) X(14, 8, 128, 2) X(15, 8, 128, 4)                  \
-    X(16, 8, 512, 16)
+    X(16, 8, 512, 16) X(17, 8, 512, 9)
 
 #define ADSCL_ROW(i, p, nt, cl) {p, nt, cl},
 const Shape kShapes[kNumShapes] = {ADSCL_SHAPES(ADSCL_ROW)};
@@ -102,7 +102,7 @@ cudaError_t shapes_set_attributes()
         for (int rec = 0; rec < 2; ++rec) {
             cudaError_t e = cudaFuncSetAttribute(kernel_of(id, rec != 0),
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess && s.CL > 8)   // 16 CTAs: beyond the portable cluster size
+            if (e == cudaSuccess && s.CL > 8)   // 9 or 16 CTAs: beyond the portable cluster size
                 e = cudaFuncSetAttribute(kernel_of(id, rec != 0), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return e;
         }

@@ -14,7 +14,7 @@ struct Shape {
     int P, NT, CL;
 };
 
-constexpr int kNumShapes = 17;
+constexpr int kNumShapes = 18;
 extern const Shape kShapes[kNumShapes];
 
 // index of the shape (P, NT, CL) in kShapes, or -1

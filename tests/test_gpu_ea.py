@@ -164,7 +164,8 @@ def test_fixed_metric_on_an_eight_cta_cluster(ad, orc):
     assert np.all(gA == 1.0) and np.all(gd == 0.0)
 
 
-@pytest.mark.parametrize("N,shape", [(4097, (8, 256, 2)), (2049, (8, 128, 2)), (1025, (8, 256, 2))])
+@pytest.mark.parametrize("N,shape", [(4097, (8, 256, 2)), (2049, (8, 128, 2)), (1025, (8, 256, 2)),
+                                     (36865, (8, 512, 9)), (4105, (8, 512, 9))])
 @pytest.mark.parametrize("scheme", [1, 3])
 def test_evolved_a_shapes_match_oracle(ad, orc, N, shape, scheme):
     Phi, Pi = W.smooth_random(N, seed=N + scheme, amp=2.0)

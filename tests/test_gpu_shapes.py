@@ -20,10 +20,9 @@ def ad():
 
 def _candidates():
     out = []
-    for P, NT, CL in itertools.product((4, 8), (128, 256, 512), (1, 2, 4, 8)):
+    # the 16-CTA shape is tested in tests/test_gpu_grid65537.py
+    for P, NT, CL in itertools.product((4, 8), (128, 256, 512), (1, 2, 4, 8, 9)):
         nmax = P * NT * CL + 1
-        if nmax > 65537 or CL > 8:   # the 16-CTA shape: tests/test_gpu_grid65537.py
-            continue
         out.append((P, NT, CL, nmax))
         small = 8 * CL * 3 + 1          # three node blocks of 8 per CTA, several tiles short
         if small < nmax:
@@ -55,7 +54,7 @@ def test_every_built_shape_matches_oracle(ad, orc):
         assert np.abs(gP - oP).max() < 1e-13 * scale and np.abs(gQ - oQ).max() < 1e-13 * scale, \
             (P, NT, CL, N)
         s.close()
-    assert built >= 16
+    assert built >= 17
 
 
 def test_mixed_shapes_batch_equals_single_runs(ad):
