@@ -186,6 +186,38 @@ def test_recording_forward_pass_for_batches_filling_the_gpu(ad, orc, extra):
         assert np.abs(g0[b] - go).max() <= 1e-9 * np.abs(go).max()
 
 
+@pytest.mark.parametrize("shape", [(8, 512, 9), (8, 512, 16)])
+def test_recording_on_non_portable_cluster_shapes(ad, orc, shape):
+    """The stage-recording variant of the evolution kernel on the 9- and 16-CTA clusters: a batch
+    set to that shape spreads over every SM, so its forward pass records the stages, with one
+    buffer per segment or with one buffer and the earlier segments recomputed; both match the
+    oracle's adjoint."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    N, K, Jm, n = 289, 6, 8, 20
+    B = -(-sms // shape[2])   # enough clusters for one CTA per SM
+    rng = np.random.default_rng(37)
+    a = rng.uniform(0.0, 0.8, (B, K)) * np.exp(-np.arange(K) / 2.0)
+    grads = {}
+    for bufs in (0, 1):
+        s = ad.Solver([N] * B, ko_sigma=0.5, spec_J=Jm, ckpt_every=9, adjoint_stage_buffers=bufs)
+        s.set_shape(N, *shape)
+        dt, _ = s.clock()
+        grads[bufs] = s.grad(a, n * dt[0])
+        assert np.all(s.clock()[1] == n)
+        _, nbuf, nseg, nrecomp = s.adjoint_storage()
+        assert nseg == 3 and nrecomp == (0 if bufs == 0 else 2)
+        assert s.shape(0) == shape   # the context's shape is kept
+        s.close()
+    (J0, g0), (J1, g1) = grads[0], grads[1]
+    assert np.abs(J0 - J1).max() <= 1e-12 * np.abs(J1).max()
+    assert np.abs(g0 - g1).max() <= 1e-10 * np.abs(g1).max()
+    for b in (0, B - 1):
+        Jo, go = orc.grad(a[b], N, n, dt[0], sigma=0.5, Jm=Jm)
+        assert abs(J0[b] - Jo) <= 1e-10 * abs(Jo)
+        assert np.abs(g0[b] - go).max() <= 1e-9 * np.abs(go).max()
+
+
 @pytest.mark.parametrize("ctas", [1, 2])
 def test_grad_without_dissipation_matches_oracle(ad, orc, ctas):
     """sigma = 0: the dissipation terms of the transposed step are switched off as in the
