@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             if (k == 2) g2 = gi;
                             if (tfirst && (k == 1 || k == 2)) {
                                 sF[spos<P>(-k)] = fi;   // f = F Pi: even about x = 0
-                                sU[spos<P>(-k)] = -ui;  // u = tan^2 F Phi: odd about x = 0
+                                sU[spos<P>(-k)] = neg_bits(ui);  // u = tan^2 F Phi: odd about x = 0
                             }
                             if (k == P - 1) { fm1 = fi; um1 = ui; }
                             if (k == P - 2) { fm2 = fi; um2 = ui; }
@@ -672,6 +672,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                                 a.outDelta[d.off + i] = De[k];   // in units of ln2/256 (no FP64 work here)
                             }
                         }
+                        // the grid's two ends, in a branch that only their warps take (a vote result is
+                        // uniform over the warp), so the other warps issue none of this FP64 work
+                        if (__any_sync(__activemask(), tfirst || last)) {
                         if (last) {
                             const double mN = fma(aT, cm, bT);   // m at node N-1: the inclusive prefix map
                             s_mass = mN;
@@ -691,8 +694,8 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                         if (last) {
                             // f odd and u even about x = pi/2; u(pi/2) by even extrapolation
                             sF[spos<P>(Nl - 1)] = 0.0;
-                            sF[spos<P>(Nl)] = -fm1;
-                            sF[spos<P>(Nl + 1)] = -fm2;
+                            sF[spos<P>(Nl)] = neg_bits(fm1);
+                            sF[spos<P>(Nl + 1)] = neg_bits(fm2);
                             sU[spos<P>(Nl - 1)] = (4.0 * um1 - um2) * (1.0 / 3.0);
                             sU[spos<P>(Nl)] = um1;
                             sU[spos<P>(Nl + 1)] = um2;
@@ -701,6 +704,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                                 a.outDelta[d.off + N - 1] = 0.0;
                             }
                             if constexpr (CL > 1) st_others<CL>(&s_mass, s_mass, CL - 1);
+                        }
                         }
                         if constexpr (CL > 1) {
                             if (hl) {   // f, u at the last 2 nodes -> left halo of rank+1
@@ -841,12 +845,12 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_kernel(
                             Dp[soff<P>(k)] = np;
                             Dq[soff<P>(k)] = nq;
                             if (tfirst && k >= 1 && k <= 3) {
-                                D0[spos<P>(-k)] = -np;  // Phi odd about x = 0
+                                D0[spos<P>(-k)] = neg_bits(np);  // Phi odd about x = 0
                                 D1[spos<P>(-k)] = nq;   // Pi even about x = 0
                             }
                             if (last && k >= P - 3) {
                                 D0[spos<P>(Nl - 1 + (P - k))] = np;   // Phi even about pi/2
-                                D1[spos<P>(Nl - 1 + (P - k))] = -nq;  // Pi odd about pi/2
+                                D1[spos<P>(Nl - 1 + (P - k))] = neg_bits(nq);  // Pi odd about pi/2
                             }
                             if constexpr (CL > 1) {
                                 if (hl && k >= P - 3) {      // -> left halo of rank+1

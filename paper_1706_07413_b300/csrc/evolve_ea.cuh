@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             if (k == 2) g2 = gi;
                             if (tfirst && (k == 1 || k == 2)) {
                                 sF[spos<P>(-k)] = fi;
-                                sU[spos<P>(-k)] = -ui;
+                                sU[spos<P>(-k)] = neg_bits(ui);
                             }
                             if (k == P - 1) { fm1 = fi; um1 = ui; }
                             if (k == P - 2) { fm2 = fi; um2 = ui; }
@@ -452,6 +452,8 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                         };
                         if (s == 0) flux_nodes(std::true_type{});
                         else flux_nodes(std::false_type{});
+                        // the grid's two ends, in a branch that only their warps take
+                        if (__any_sync(__activemask(), tfirst || last)) {
                         if (tfirst) {
                             const double d0n = De[0] * kInvKappa;   // delta(0)
                             s_d0 = d0n;
@@ -460,8 +462,8 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                         }
                         if (last) {
                             sF[spos<P>(Nl - 1)] = 0.0;
-                            sF[spos<P>(Nl)] = -fm1;
-                            sF[spos<P>(Nl + 1)] = -fm2;
+                            sF[spos<P>(Nl)] = neg_bits(fm1);
+                            sF[spos<P>(Nl + 1)] = neg_bits(fm2);
                             sU[spos<P>(Nl - 1)] = (4.0 * um1 - um2) * (1.0 / 3.0);
                             sU[spos<P>(Nl)] = um1;
                             sU[spos<P>(Nl + 1)] = um2;
@@ -469,6 +471,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                                 a.outA[d.off + N - 1] = 1.0;
                                 a.outDelta[d.off + N - 1] = 0.0;
                             }
+                        }
                         }
                         if constexpr (CL > 1) {
                             if (hl) {   // f, u at the last 2 nodes -> left halo of rank+1
@@ -594,12 +597,12 @@ __global__ void __launch_bounds__(NT, (NT >= 512) ? 1 : 512 / NT) evolve_ea_kern
                             Dp[soff<P>(k)] = np;
                             Dq[soff<P>(k)] = nq;
                             if (tfirst && k >= 1 && k <= 3) {
-                                D0[spos<P>(-k)] = -np;
+                                D0[spos<P>(-k)] = neg_bits(np);
                                 D1[spos<P>(-k)] = nq;
                             }
                             if (last && k >= P - 3) {
                                 D0[spos<P>(Nl - 1 + (P - k))] = np;
-                                D1[spos<P>(Nl - 1 + (P - k))] = -nq;
+                                D1[spos<P>(Nl - 1 + (P - k))] = neg_bits(nq);
                             }
                             if constexpr (CL > 1) {
                                 if (hl && k >= P - 3) {      // -> left halo of rank+1

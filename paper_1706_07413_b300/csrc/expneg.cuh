@@ -31,6 +31,12 @@ static __constant__ double c_fp_one = 1.0;
 static __constant__ double c_fp_negzero = -0.0;
 __device__ __forceinline__ double add_f(double x, double y) { return fma(x, c_fp_one, y); }
 __device__ __forceinline__ double mul_f(double x, double y) { return fma(x, y, c_fp_negzero); }
+// -x by flipping the sign bit on the integer pipe (IEEE negation, NaN payloads included), for the
+// parity ghosts that only a few threads write: no FP64 instruction that every lane would issue
+__device__ __forceinline__ double neg_bits(double x)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
 
 constexpr int kExpTableSize = 256;
 
