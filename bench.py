@@ -66,7 +66,7 @@ SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A
 # divided by their point-substeps, captured on a reduced adjoint batch (38 instances at N = 4097,
 # 96 steps in two 48-step segments; per point-substep the same instruction mix as the bench's
 # 64-instance batch); used only while the kernel sources are unchanged
-ADJ_ISSUE = {"sha256": "bf5249b26e51b564e4f3eef4af5a264d2e83215619be4ea63fdf170823214273",
+ADJ_ISSUE = {"sha256": "635d0f4e0aef810b30da1ae20e6b85b740caa82d35f5073dc42a772ce0f878c7",
              "forward_record": (24925416 + 3955116 + 4205327532) / (38 * 4097 * 96 * 4),
              "phase_B": (67458816 + 59890432 + 3080728704) / (38 * 4097 * 48 * 4)}
 L2_FLUSH_BYTES = 512 << 20
@@ -75,8 +75,8 @@ REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one timed evolve_kernel launch of
 # the amplitude scan, from an ncu capture of this script's headline launch; reported only while
 # the kernel source and the kernel shape are the ones the counters were taken on.
-TRAFFIC = {"kernel_sha256": "8c23bd34952d1678afb25bcc6b56cb8c1f50f6b316f51d2441b110f7a0ac581d",
-           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17625344 + 62251520,
+TRAFFIC = {"kernel_sha256": "ca296d6613958823a02695a1cacccc351e232a7f9d64edbcb3234f81141078f6",
+           "shape_P_NT_CL": [8, 256, 2], "dram_bytes_per_launch": 17760000 + 64856320,
            # FP64 instructions (DADD + DMUL + DFMA, thread level) per point-substep, same capture
            "fp64_instr_per_point_substep": (328507392 + 54013952 + 75394985984) / 1074003968}
 
