@@ -170,14 +170,19 @@ def test_more_clusters_than_fit_chunk_invariance(ad):
             assert np.array_equal(x, y)
 
 
-def test_production_batch_sampled_matches_oracle(ad, orc):
-    """The bench's production-resolution batch (15 pulses at N = 32769, one 8-CTA cluster each,
-    the default chunking and shape) after 12 RK4 steps: sampled instances match the oracle."""
+@pytest.mark.parametrize("shape", [None, (8, 512, 9)])
+def test_production_batch_sampled_matches_oracle(ad, orc, shape):
+    """The bench's production-resolution batch (15 pulses at N = 32769, one cluster each, the
+    default chunking) after 12 RK4 steps on the default 8-CTA shape and on the 9-CTA shape the
+    autotuner picks for it: sampled instances match the oracle."""
     insts = W.production()
     n = insts[0].N
     Pi0 = W.packed([W.gaussian_pi(it.N, it.eps, it.sigma) for it in insts])
     s = ad.Solver([it.N for it in insts], ko_sigma=0.5, collapse_threshold=2.0 ** -7)
     assert s.shape(0) == (8, 512, 8)
+    if shape:
+        s.set_shape(n, *shape)
+        assert s.shape(0) == shape
     s.set_initial(np.zeros_like(Pi0), Pi0)
     dt, _ = s.clock()
     tr, tc, m, st = s.evolve(12 * dt[0])
