@@ -31,6 +31,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "evolve.cuh"
 #include "spectrum.cuh"
@@ -85,6 +86,19 @@ __device__ __forceinline__ double gv(const double *u, int N, int i, double p0, d
 __device__ __forceinline__ double rv(const double *v, int N, int i) {
     return (i < 0 || i > N - 1) ? 0.0 : v[i];
 }
+// the same for a thread whose reads all lie inside the grid (INT): a plain load, no range tests
+template <bool INT>
+__device__ __forceinline__ double gvi(const double *u, int N, int i, double p0, double p1) {
+    if constexpr (INT) return u[i]; else return gv(u, N, i, p0, p1);
+}
+template <bool INT>
+__device__ __forceinline__ double rvi(const double *v, int N, int i) {
+    if constexpr (INT) return v[i]; else return rv(v, N, i);
+}
+// every node this thread reads in the transposed stencils and cell maps (its AP nodes and three
+// on each side, ghost folds included) is an interior node
+template <int AP>
+__device__ __forceinline__ bool reads_interior(int i0, int N) { return i0 >= 4 && i0 + AP + 4 <= N - 1; }
 
 // ------------------------------------------------------------------ block scans (512 threads)
 // The affine scans and the sums use disjoint slots (a, b, c, e, pb and d, f, pd), so a sum may
@@ -445,16 +459,20 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
         }
         double Db = dpre;
         double n0s[AP];
+        // the cell loop, compiled once with plain loads (warps whose threads read only interior
+        // nodes: all but the two at the ends of the grid) and once with the parity ghosts
+        auto cells = [&](auto interior) {
+        constexpr bool INT = decltype(interior)::value;
         // the cells' forward data with the node quantities carried from cell to cell
-        double pm1 = gv(yP, N, i0 - 1, -1.0, 1.0), p0 = yP[i0], p1 = yP[i0 + 1];
-        double qm1 = gv(yQ, N, i0 - 1, 1.0, -1.0), q0 = yQ[i0], q1 = yQ[i0 + 1];
+        double pm1 = gvi<INT>(yP, N, i0 - 1, -1.0, 1.0), p0 = yP[i0], p1 = yP[i0 + 1];
+        double qm1 = gvi<INT>(yQ, N, i0 - 1, 1.0, -1.0), q0 = yQ[i0], q1 = yQ[i0 + 1];
         const double rho0 = fma(p0, p0, mul_f(q0, q0));
         double qn0 = mul_f(__ldg(g.ws + i0), rho0), rn0 = mul_f(__ldg(g.wt + i0), rho0);
 #pragma unroll
         for (int k = 0; k < AP; ++k) {
             const int c = i0 + k;
             Db = add_f(Db, scr.dlb[c]);               // Delta_bar_c = sum_{i <= c} delta_bar_i
-            const double p2 = gv(yP, N, c + 2, -1.0, 1.0), q2 = gv(yQ, N, c + 2, 1.0, -1.0);
+            const double p2 = gvi<INT>(yP, N, c + 2, -1.0, 1.0), q2 = gvi<INT>(yQ, N, c + 2, 1.0, -1.0);
             const double rho1 = fma(p1, p1, mul_f(q1, q1));
             const double qn1 = mul_f(__ldg(g.ws + c + 1), rho1), rn1 = mul_f(__ldg(g.wt + c + 1), rho1);
             const CellFwd cf = cell_fwd_n(qn0, rn0, qn1, rn1, pm1, p0, p1, p2, qm1, q0, q1, q2, g, c);
@@ -468,27 +486,38 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
             scr.pb[c] = pb;
             scr.qb[c] = qb;
         }
+        };
+        if (__all_sync(__activemask(), reads_interior<AP>(i0, N))) cells(std::true_type{});
+        else cells(std::false_type{});
         // keep the node parts in the scratch f/u slots (free in phase B)
 #pragma unroll
         for (int k = 0; k < AP; ++k) scr.fb[i0 + k] = n0s[k];
     }
     csync<CL>();
     if (act) {
+        // compiled with and without range tests, as the cell loop
+        auto nodes = [&](auto interior) {
+        constexpr bool INT = decltype(interior)::value;
 #pragma unroll
         for (int k = 0; k < AP; ++k) {
             const int j = i0 + k;
-            const double rb = add_f(scr.fb[j], j >= 1 ? scr.r1[j - 1] : 0.0);
+            const double rb = add_f(scr.fb[j], (INT || j >= 1) ? scr.r1[j - 1] : 0.0);
             // transpose of p16_c = 9 (w_c + w_{c+1}) - (w_{c-1} + w_{c+2}), cells 0 .. N-2
             auto itp = [&](const double *b, int x) {
-                return fma(9.0, add_f(rv(b, N - 1, x), rv(b, N - 1, x - 1)),
-                           -add_f(rv(b, N - 1, x + 1), rv(b, N - 1, x - 2)));
+                return fma(9.0, add_f(rvi<INT>(b, N - 1, x), rvi<INT>(b, N - 1, x - 1)),
+                           -add_f(rvi<INT>(b, N - 1, x + 1), rvi<INT>(b, N - 1, x - 2)));
             };
             double pP = itp(scr.pb, j), pQ = itp(scr.qb, j);
-            if (j == 1) { pP += -itp(scr.pb, -1); pQ += itp(scr.qb, -1); }                    // ghost -1
-            if (j == N - 2) { pP += itp(scr.pb, N); pQ += -itp(scr.qb, N); }                  // ghost N
+            if constexpr (!INT) {
+                if (j == 1) { pP += -itp(scr.pb, -1); pQ += itp(scr.qb, -1); }                // ghost -1
+                if (j == N - 2) { pP += itp(scr.pb, N); pQ += -itp(scr.qb, N); }              // ghost N
+            }
             ybP[j] = add_f(ybP[j], fma(add_f(yP[j], yP[j]), rb, pP));
             ybQ[j] = add_f(ybQ[j], fma(add_f(yQ[j], yQ[j]), rb, pQ));
         }
+        };
+        if (__all_sync(__activemask(), reads_interior<AP>(i0, N))) nodes(std::true_type{});
+        else nodes(std::false_type{});
     }
     // no barrier here: every caller updates only its own nodes next and then synchronises
     // before scr.pb, qb, r1, fb are written again
@@ -509,40 +538,50 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
     const int i0 = o.i0;
     const double *vP = scr.vP, *vQ = scr.vQ;
     const double *v2 = scr.v2;   // iT12-weighted Pi-dot sensitivities (zero at rows 0 and N-1)
-    auto Dr = [&](const double *v, int x) {   // raw 4th-order difference of a row-restricted array
-        return fma(8.0, add_f(rv(v, N, x + 1), -rv(v, N, x - 1)), add_f(rv(v, N, x - 2), -rv(v, N, x + 2)));
-    };
-    auto KOr = [&](const double *v, int x) {  // raw dissipation stencil of a row-restricted array
-        return fma(-20.0, rv(v, N, x), fma(15.0, add_f(rv(v, N, x - 1), rv(v, N, x + 1)),
-               fma(-6.0, add_f(rv(v, N, x - 2), rv(v, N, x + 2)), add_f(rv(v, N, x - 3), rv(v, N, x + 3)))));
-    };
     if (act) {
         const double vQ0 = vQ[0];
+        // the node loop, compiled once with plain loads (warps whose threads read only interior
+        // nodes) and once with the range tests and the ghost folds of the grid's two ends
+        auto nodes = [&](auto interior) {
+        constexpr bool INT = decltype(interior)::value;
+        auto Dr = [&](const double *v, int x) {   // raw 4th-order difference of a row-restricted array
+            return fma(8.0, add_f(rvi<INT>(v, N, x + 1), -rvi<INT>(v, N, x - 1)),
+                       add_f(rvi<INT>(v, N, x - 2), -rvi<INT>(v, N, x + 2)));
+        };
+        auto KOr = [&](const double *v, int x) {  // raw dissipation stencil of a row-restricted array
+            return fma(-20.0, rvi<INT>(v, N, x), fma(15.0, add_f(rvi<INT>(v, N, x - 1), rvi<INT>(v, N, x + 1)),
+                   fma(-6.0, add_f(rvi<INT>(v, N, x - 2), rvi<INT>(v, N, x + 2)),
+                       add_f(rvi<INT>(v, N, x - 3), rvi<INT>(v, N, x + 3)))));
+        };
 #pragma unroll
         for (int k = 0; k < AP; ++k) {
             const int j = i0 + k;
             // transposed stencils on the extended range, ghosts folded back (parities:
             // f even/odd, u odd/even, Phi odd/even, Pi even/odd about 0 / pi/2)
             double fbx = -Dr(vP, j), ubx = -Dr(v2, j), kpx = KOr(vP, j), kqx = KOr(vQ, j);
-            if (j >= 1 && j <= 3) {
-                fbx += -Dr(vP, -j);
-                ubx -= -Dr(v2, -j);
-                kpx -= KOr(vP, -j);
-                kqx += KOr(vQ, -j);
+            if constexpr (!INT) {
+                if (j >= 1 && j <= 3) {
+                    fbx += -Dr(vP, -j);
+                    ubx -= -Dr(v2, -j);
+                    kpx -= KOr(vP, -j);
+                    kqx += KOr(vQ, -j);
+                }
+                if (j >= N - 4 && j <= N - 2) {
+                    const int x = 2 * (N - 1) - j;
+                    fbx -= -Dr(vP, x);
+                    ubx += -Dr(v2, x);
+                    kpx += KOr(vP, x);
+                    kqx -= KOr(vQ, x);
+                }
+                if (j == N - 2) ubx += (4.0 / 3.0) * (-Dr(v2, N - 1));   // u(pi/2) extrapolation
+                if (j == N - 3) ubx += (-1.0 / 3.0) * (-Dr(v2, N - 1));
             }
-            if (j >= N - 4 && j <= N - 2) {
-                const int x = 2 * (N - 1) - j;
-                fbx -= -Dr(vP, x);
-                ubx += -Dr(v2, x);
-                kpx += KOr(vP, x);
-                kqx -= KOr(vQ, x);
-            }
-            if (j == N - 2) ubx += (4.0 / 3.0) * (-Dr(v2, N - 1));   // u(pi/2) extrapolation
-            if (j == N - 3) ubx += (-1.0 / 3.0) * (-Dr(v2, N - 1));
             const double fb = fbx;   // (vP carries the factor c12, vQ the factor cq)
             double gb = mul_f(__ldg(g.T + j), ubx);
-            if (j == 1) gb = fma(16.0 * d.c3q, vQ0, gb);            // Pi-dot(0) = 3 (F Phi)'(0)
-            if (j == 2) gb = fma(-2.0 * d.c3q, vQ0, gb);
+            if constexpr (!INT) {
+                if (j == 1) gb = fma(16.0 * d.c3q, vQ0, gb);            // Pi-dot(0) = 3 (F Phi)'(0)
+                if (j == 2) gb = fma(-2.0 * d.c3q, vQ0, gb);
+            }
             const double Fj = F[j];
             const double Fb = fma(fb, yQ[j], mul_f(gb, yP[j]));
             ybQ[j] = fma(fb, Fj, d.ko ? kqx : 0.0);
@@ -551,6 +590,9 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
             scr.dlb[j] = mul_f(-Fb, Fj);
             scr.mb[j] = mul_f(-Ab, __ldg(g.K + j));
         }
+        };
+        if (__all_sync(__activemask(), reads_interior<AP>(i0, N))) nodes(std::true_type{});
+        else nodes(std::false_type{});
         if (last) { scr.dlb[N - 1] = 0.0; scr.mb[N - 1] = 0.0; }
     }
     // no barrier: the constraint transpose reads only this thread's mb, dlb before its scans'
