@@ -42,7 +42,11 @@ constexpr int kAP = 8;          // nodes per thread of a single-CTA instance
 constexpr int kANT = 512;       // threads per CTA
 constexpr int kANW = kANT / 32;
 // kStageArrays (evolve.cuh): stored per stage: yP, yQ, M, E, F, AL
-constexpr int kScrArrays = 21;   // CTA scratch arrays of length Nmax
+constexpr int kScrArrays = 21;   // CTA scratch arrays
+// length of every scratch array: a compile-time stride (the adjoint's largest grid, 8193 points,
+// rounded up), so that each array is the scratch base plus a constant and a thread's accesses
+// are one base register plus immediate offsets
+constexpr int kScrStride = 2 * kAP * kANT + 8;
 
 // kAdjSegment: both phases of a segment; kAdjSegF / kAdjSegB: only the recomputation (phase F,
 // from the checkpoint into the stage storage) or only the backward sweep (phase B, from the
@@ -66,7 +70,7 @@ struct AdjArgs {
                               // layout of the evolution kernel's stage record, stage_slot)
     int32_t nsteps_cap;
     double *lamP, *lamQ;      // packed adjoint state, updated in place
-    double *scratch;          // per CTA: kScrArrays * Nmax
+    double *scratch;          // per CTA (cluster): kScrArrays * kScrStride
     int32_t Nmax;
     // spectrum mode: lambda += d(sum_j Ebar_j E_j)/d(slice)
     const double *Ebar;       // B x J
@@ -322,15 +326,15 @@ struct Scr {
     double *v2;          // iT12 kbar_Pi (phase B: the Pi-dot sensitivities seen by the u stencil)
 };
 
-__device__ __forceinline__ Scr scratch_of(double *base, int Nmax)
+__device__ __forceinline__ Scr scratch_of(double *base)
 {
+    constexpr int L = kScrStride;
     Scr s;
-    double *p = base;
-    s.uP = p; p += Nmax; s.uQ = p; p += Nmax; s.aP = p; p += Nmax; s.aQ = p; p += Nmax;
-    s.f = p; p += Nmax; s.u = p; p += Nmax; s.vP = p; p += Nmax; s.vQ = p; p += Nmax;
-    s.fb = p; p += Nmax; s.ub = p; p += Nmax; s.r1 = p; p += Nmax; s.pb = p; p += Nmax;
-    s.qb = p; p += Nmax; s.lo = p; p += Nmax; s.lq = p; p += Nmax; s.ybP = p; p += Nmax;
-    s.ybQ = p; p += Nmax; s.mb = p; p += Nmax; s.dlb = p; p += Nmax; s.v2 = p;
+    s.uP = base; s.uQ = base + L; s.aP = base + 2 * L; s.aQ = base + 3 * L;
+    s.f = base + 4 * L; s.u = base + 5 * L; s.vP = base + 6 * L; s.vQ = base + 7 * L;
+    s.fb = base + 8 * L; s.ub = base + 9 * L; s.r1 = base + 10 * L; s.pb = base + 11 * L;
+    s.qb = base + 12 * L; s.lo = base + 13 * L; s.lq = base + 14 * L; s.ybP = base + 15 * L;
+    s.ybQ = base + 16 * L; s.mb = base + 17 * L; s.dlb = base + 18 * L; s.v2 = base + 19 * L;
     return s;
 }
 
@@ -615,7 +619,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
     for (int i = tid; i < kExpTableSize; i += kANT) s_tab[i] = a.exptab[i];
     csync<CL>();   // every CTA of the cluster has started before any remote shared-memory store
     // one scratch region per CTA (CL = 1) or per cluster (CL = 2: shared by both ranks)
-    const Scr scr = scratch_of(a.scratch + (size_t)(blockIdx.x / CL) * kScrArrays * a.Nmax, a.Nmax);
+    const Scr scr = scratch_of(a.scratch + (size_t)(blockIdx.x / CL) * kScrArrays * kScrStride);
     const double cst[4] = {0.0, 0.5, 0.5, 1.0};
     const double wst[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
 

@@ -1263,7 +1263,7 @@ adscl_status launch_adjoint(adscl_ctx *ctx, AdjArgs &a, cudaStream_t sm, int lan
     const int units = std::min(ctx->B, ctx->adj_units);
     CK(cudaMemsetAsync(ctx->d_adj_queue + lane, 0, sizeof(int32_t), sm));
     a.queue = ctx->d_adj_queue + lane;
-    a.scratch = ctx->d_adj_scr + (size_t)lane * regions * kScrArrays * ctx->Nmax;
+    a.scratch = ctx->d_adj_scr + (size_t)lane * regions * kScrArrays * kScrStride;
     if (ctx->adj_cl == 2) {
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(2 * units, 1, 1);
@@ -1346,7 +1346,7 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     // buffers (grown on demand)
     if (!ctx->d_lam) {
         CK(cudaMalloc(&ctx->d_lam, 2 * total * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_adj_scr, (size_t)2 * std::min(B, ctx->num_sms) * kScrArrays * ctx->Nmax * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_adj_scr, (size_t)2 * std::min(B, ctx->num_sms) * kScrArrays * kScrStride * sizeof(double)));
         CK(cudaMalloc(&ctx->d_adj_small, ((size_t)B * (5 * kMaxModes + 1)) * sizeof(double)));
         CK(cudaMalloc(&ctx->d_adj_queue, 2 * sizeof(int32_t)));
     }
