@@ -263,18 +263,7 @@ __device__ __forceinline__ CellFwd cell_fwd_n(double qn0, double rn0, double qn1
     return r;
 }
 
-// the same from the stage slice (yP, yQ) (ghost-extended reads)
-__device__ __forceinline__ CellFwd cell_fwd(const double *yP, const double *yQ, const GeoTab &g, int N, int c)
-{
-    const double p0 = yP[c], p1 = yP[c + 1], q0 = yQ[c], q1 = yQ[c + 1];
-    const double rho0 = fma(p0, p0, mul_f(q0, q0)), rho1 = fma(p1, p1, mul_f(q1, q1));
-    return cell_fwd_n(mul_f(__ldg(g.ws + c), rho0), mul_f(__ldg(g.wt + c), rho0), mul_f(__ldg(g.ws + c + 1), rho1),
-                      mul_f(__ldg(g.wt + c + 1), rho1), gv(yP, N, c - 1, -1.0, 1.0), p0, p1,
-                      gv(yP, N, c + 2, -1.0, 1.0), gv(yQ, N, c - 1, 1.0, -1.0), q0, q1,
-                      gv(yQ, N, c + 2, 1.0, -1.0), g, c);
-}
-
-// transpose of cell_fwd from (alpha_bar, beta_bar, Delta_bar) to the node and midpoint
+// transpose of cell_fwd_n from (alpha_bar, beta_bar, Delta_bar) to the node and midpoint
 // sensitivities: rho_bar at node c (n0) and c+1 (n1), and (p16_bar, q16_bar)
 __device__ __forceinline__ void cell_bwd(const CellFwd &f, const GeoTab &g, int c, double alb, double beb,
                                          double Deb, double &n0, double &n1, double &p16b, double &q16b)
@@ -354,16 +343,34 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
     double De[AP], al[AP], be[AP];
     double aT = 1.0, bT = 0.0, SD = 0.0;
     if (act) {
+        // the cell maps with the node quantities carried from cell to cell, compiled with plain
+        // loads for warps whose threads read only interior nodes and with the parity ghosts
+        auto cells = [&](auto interior) {
+        constexpr bool INT = decltype(interior)::value;
+        double pm1 = gvi<INT>(yP, N, i0 - 1, -1.0, 1.0), p0 = yP[i0], p1 = yP[i0 + 1];
+        double qm1 = gvi<INT>(yQ, N, i0 - 1, 1.0, -1.0), q0 = yQ[i0], q1 = yQ[i0 + 1];
+        const double rho0 = fma(p0, p0, mul_f(q0, q0));
+        double qn0 = mul_f(__ldg(g.ws + i0), rho0), rn0 = mul_f(__ldg(g.wt + i0), rho0);
 #pragma unroll
         for (int k = 0; k < AP; ++k) {
-            const CellFwd cf = cell_fwd(yP, yQ, g, N, i0 + k);
+            const int c = i0 + k;
+            const double p2 = gvi<INT>(yP, N, c + 2, -1.0, 1.0), q2 = gvi<INT>(yQ, N, c + 2, 1.0, -1.0);
+            const double rho1 = fma(p1, p1, mul_f(q1, q1));
+            const double qn1 = mul_f(__ldg(g.ws + c + 1), rho1), rn1 = mul_f(__ldg(g.wt + c + 1), rho1);
+            const CellFwd cf = cell_fwd_n(qn0, rn0, qn1, rn1, pm1, p0, p1, p2, qm1, q0, q1, q2, g, c);
+            pm1 = p0; p0 = p1; p1 = p2;
+            qm1 = q0; q0 = q1; q1 = q2;
+            qn0 = qn1; rn0 = rn1;
             De[k] = cf.De;
             al[k] = cf.al;
             be[k] = cf.be;
-            AL[i0 + k] = cf.al;
+            AL[c] = cf.al;
             if (k == 0) { aT = cf.al; bT = cf.be; SD = cf.De; }
             else { bT = fma(cf.al, bT, cf.be); aT = mul_f(aT, cf.al); SD = add_f(SD, cf.De); }
         }
+        };
+        if (__all_sync(__activemask(), reads_interior<AP>(i0, N))) cells(std::true_type{});
+        else cells(std::false_type{});
     }
     double mstart, dend;   // m at node i0; the sum of Delta over the cells from node i0 + AP on
     scan_pair<CL, false>(aT, bT, SD, sh, mstart, dend);
@@ -402,28 +409,34 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
     }
     csync<CL>();
     if (!with_rhs || !act) return;
+    // the stage derivative, compiled with and without range tests as the cell maps
+    auto rhs = [&](auto interior) {
+    constexpr bool INT = decltype(interior)::value;
 #pragma unroll
     for (int k = 0; k < AP; ++k) {
         const int i = i0 + k;
-        const double Df = fma(8.0, add_f(gv(scr.f, N, i + 1, 1.0, -1.0), -gv(scr.f, N, i - 1, 1.0, -1.0)),
-                              add_f(gv(scr.f, N, i - 2, 1.0, -1.0), -gv(scr.f, N, i + 2, 1.0, -1.0)));
-        const double Du = fma(8.0, add_f(gv(scr.u, N, i + 1, -1.0, 1.0), -gv(scr.u, N, i - 1, -1.0, 1.0)),
-                              add_f(gv(scr.u, N, i - 2, -1.0, 1.0), -gv(scr.u, N, i + 2, -1.0, 1.0)));
-        const double kp = fma(-20.0, yP[i], fma(15.0, add_f(gv(yP, N, i - 1, -1, 1), gv(yP, N, i + 1, -1, 1)),
-                          fma(-6.0, add_f(gv(yP, N, i - 2, -1, 1), gv(yP, N, i + 2, -1, 1)),
-                              add_f(gv(yP, N, i - 3, -1, 1), gv(yP, N, i + 3, -1, 1)))));
-        const double kq = fma(-20.0, yQ[i], fma(15.0, add_f(gv(yQ, N, i - 1, 1, -1), gv(yQ, N, i + 1, 1, -1)),
-                          fma(-6.0, add_f(gv(yQ, N, i - 2, 1, -1), gv(yQ, N, i + 2, 1, -1)),
-                              add_f(gv(yQ, N, i - 3, 1, -1), gv(yQ, N, i + 3, 1, -1)))));
+        const double Df = fma(8.0, add_f(gvi<INT>(scr.f, N, i + 1, 1.0, -1.0), -gvi<INT>(scr.f, N, i - 1, 1.0, -1.0)),
+                              add_f(gvi<INT>(scr.f, N, i - 2, 1.0, -1.0), -gvi<INT>(scr.f, N, i + 2, 1.0, -1.0)));
+        const double Du = fma(8.0, add_f(gvi<INT>(scr.u, N, i + 1, -1.0, 1.0), -gvi<INT>(scr.u, N, i - 1, -1.0, 1.0)),
+                              add_f(gvi<INT>(scr.u, N, i - 2, -1.0, 1.0), -gvi<INT>(scr.u, N, i + 2, -1.0, 1.0)));
+        const double kp = fma(-20.0, yP[i], fma(15.0, add_f(gvi<INT>(yP, N, i - 1, -1, 1), gvi<INT>(yP, N, i + 1, -1, 1)),
+                          fma(-6.0, add_f(gvi<INT>(yP, N, i - 2, -1, 1), gvi<INT>(yP, N, i + 2, -1, 1)),
+                              add_f(gvi<INT>(yP, N, i - 3, -1, 1), gvi<INT>(yP, N, i + 3, -1, 1)))));
+        const double kq = fma(-20.0, yQ[i], fma(15.0, add_f(gvi<INT>(yQ, N, i - 1, 1, -1), gvi<INT>(yQ, N, i + 1, 1, -1)),
+                          fma(-6.0, add_f(gvi<INT>(yQ, N, i - 2, 1, -1), gvi<INT>(yQ, N, i + 2, 1, -1)),
+                              add_f(gvi<INT>(yQ, N, i - 3, 1, -1), gvi<INT>(yQ, N, i + 3, 1, -1)))));
         double dP = fma(d.c12, Df, mul_f(d.cko, kp));
         double dQ = fma(__ldg(g.iT12 + i), Du, mul_f(d.cko, kq));
-        if (i == 0) {
+        if (!INT && i == 0) {
             dP = 0.0;
             dQ = fma(d.c3, fma(16.0, g1, -2.0 * g2), d.cko * kq);
         }
         kP[i] = dP;
         kQ[i] = dQ;
     }
+    };
+    if (__all_sync(__activemask(), reads_interior<AP>(i0, N))) rhs(std::true_type{});
+    else rhs(std::false_type{});
 }
 
 // ------------------------------------------------------------------ constraint transpose
