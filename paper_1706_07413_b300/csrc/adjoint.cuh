@@ -619,8 +619,10 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
 
 // ------------------------------------------------------------------ the kernel
 // AP nodes per thread: (CL, AP) = (1, 8) and (2, 4) for N <= 4097 (on a 2-CTA cluster every
-// thread of both CTAs carries nodes), (2, 8) for N <= 8193
-template <int CL, int AP>
+// thread of both CTAs carries nodes), (2, 8) for N <= 8193.  SWEEP = true compiles the backward
+// sweep alone (mode kAdjSegB only): its registers are then allocated for that path, not for the
+// longest-lived values of the recomputation and the spectrum transpose.
+template <int CL, int AP, bool SWEEP>
 __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
 {
     static_assert(CL == 1 || CL == 2, "one CTA or a 2-CTA cluster per instance");
@@ -629,7 +631,8 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
     __shared__ int s_item;
     const int tid = threadIdx.x;
     const int rank = (CL > 1) ? cluster_rank() : 0;
-    for (int i = tid; i < kExpTableSize; i += kANT) s_tab[i] = a.exptab[i];
+    if constexpr (!SWEEP)   // the exponential is evaluated only in the forward stages
+        for (int i = tid; i < kExpTableSize; i += kANT) s_tab[i] = a.exptab[i];
     csync<CL>();   // every CTA of the cluster has started before any remote shared-memory store
     // one scratch region per CTA (CL = 1) or per cluster (CL = 2: shared by both ranks)
     const Scr scr = scratch_of(a.scratch + (size_t)(blockIdx.x / CL) * kScrArrays * kScrStride);
@@ -655,7 +658,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
         const int i0 = own.i0;
         double *lamP = a.lamP + d.off, *lamQ = a.lamQ + d.off;
 
-        if (a.mode == kAdjProject) {
+        if (!SWEEP && a.mode == kAdjProject) {
             if (rank == 0) {
                 const EigTab t = a.eig[d.geo];
                 const int lane = tid & 31, warp = tid >> 5;
@@ -676,7 +679,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
         double *stage_base = a.stage + (size_t)b * a.nsteps_cap * 4 * kStageArrays * stN;
         auto slot = [&](int n, int s, int arr) { return stage_base + (((size_t)n * 4 + s) * kStageArrays + arr) * stN; };
 
-        if (a.mode == kAdjSpectrum) {
+        if (!SWEEP && a.mode == kAdjSpectrum) {
             // constraint solve of the slice, projections, then the transpose into lambda
             const double *sP = a.sP + d.off, *sQ = a.sQ + d.off;
             double *yP = slot(0, 0, 0), *yQ = slot(0, 0, 1), *M = slot(0, 0, 2), *E = slot(0, 0, 3),
@@ -750,7 +753,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
         }
 
         // ================= segment: phase F (recompute and store every stage) =================
-        if (a.mode == kAdjSegment || a.mode == kAdjSegF) {
+        if (!SWEEP && (a.mode == kAdjSegment || a.mode == kAdjSegF)) {
         const double *ckP = a.ckP + d.off, *ckQ = a.ckQ + d.off;
         if (act) {
 #pragma unroll
@@ -802,7 +805,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
         }   // phase F
 
         // ================= segment: phase B (steps backwards) =================
-        if (a.mode == kAdjSegment || a.mode == kAdjSegB)
+        if (SWEEP || a.mode == kAdjSegment || a.mode == kAdjSegB)
         for (int n = a.nsteps - 1; n >= 0; --n) {
             if (act) {
 #pragma unroll

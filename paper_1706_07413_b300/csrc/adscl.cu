@@ -1276,10 +1276,13 @@ adscl_status launch_adjoint(adscl_ctx *ctx, AdjArgs &a, cudaStream_t sm, int lan
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (ctx->adj_wide) CK(cudaLaunchKernelEx(&cfg, adjoint_kernel<2, 8>, a));
-        else CK(cudaLaunchKernelEx(&cfg, adjoint_kernel<2, 4>, a));
+        // the backward sweep on its own instantiation (registers allocated for that path alone)
+        const bool sweep = a.mode == kAdjSegB;
+        if (ctx->adj_wide) CK(cudaLaunchKernelEx(&cfg, sweep ? adjoint_kernel<2, 8, true> : adjoint_kernel<2, 8, false>, a));
+        else CK(cudaLaunchKernelEx(&cfg, sweep ? adjoint_kernel<2, 4, true> : adjoint_kernel<2, 4, false>, a));
     } else {
-        adjoint_kernel<1, 8><<<units, kANT, 0, sm>>>(a);
+        if (a.mode == kAdjSegB) adjoint_kernel<1, 8, true><<<units, kANT, 0, sm>>>(a);
+        else adjoint_kernel<1, 8, false><<<units, kANT, 0, sm>>>(a);
         CK(cudaGetLastError());
     }
     ctx->launches += 1;
@@ -1324,8 +1327,8 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int nc = 0;
-            const cudaError_t eo = wide ? cudaOccupancyMaxActiveClusters(&nc, adjoint_kernel<2, 8>, &cfg)
-                                        : cudaOccupancyMaxActiveClusters(&nc, adjoint_kernel<2, 4>, &cfg);
+            const cudaError_t eo = wide ? cudaOccupancyMaxActiveClusters(&nc, adjoint_kernel<2, 8, false>, &cfg)
+                                        : cudaOccupancyMaxActiveClusters(&nc, adjoint_kernel<2, 4, false>, &cfg);
             if (eo != cudaSuccess || nc < 1) {
                 (void)cudaGetLastError();
                 if (wide) return fail(ctx, ADSCL_ECUDA, "no 2-CTA cluster of the adjoint kernel fits");
