@@ -47,15 +47,30 @@ constexpr int kScrArrays = 21;   // CTA scratch arrays
 // rounded up), so that each array is the scratch base plus a constant and a thread's accesses
 // are one base register plus immediate offsets
 constexpr int kScrStride = 2 * kAP * kANT + 8;
+// table t of the sweep's geometry block at index i (read-only path)
+__device__ __forceinline__ double agv(const double *ag, int t, int i) { return __ldg(ag + t * kScrStride + i); }
 
 // kAdjSegment: both phases of a segment; kAdjSegF / kAdjSegB: only the recomputation (phase F,
 // from the checkpoint into the stage storage) or only the backward sweep (phase B, from the
 // stage storage), so that the recomputation of one segment can run beside the sweep of the next
 enum : int32_t { kAdjSegment = 0, kAdjSpectrum = 1, kAdjProject = 2, kAdjSegF = 3, kAdjSegB = 4 };
 
+// The backward sweep's geometry (per grid size N <= 8193): kAgTables tables kScrStride doubles
+// apart, so that one base pointer and immediate offsets reach all of them.  The first seven are
+// copies of GeoTab's ws, wt, K, T, wsm3, wtm and iT12k; the others are scaled copies for the cell
+// transpose: at the nodes 2 ws, 2 wt and 6 ws, at the cell midpoints 2 wsm3, 2 wtm and (8/3) wsm3.
+// With them the transpose forms twice the node and midpoint sensitivities of rho directly (the
+// factor 2 of d rho = 2 Phi dPhi + 2 Pi dPi) and the forward quantities y2 = 1/3 - ws rho and
+// ca = 2 - 6 ws rho in one FMA each.
+enum : int {
+    kAgWs = 0, kAgWt, kAgK, kAgT, kAgWsm3, kAgWtm, kAgIT12k,
+    kAgWs2, kAgWt2, kAgWs6, kAgWsm3x2, kAgWtm2, kAgWsm3x83, kAgTables
+};
+
 struct AdjArgs {
     const InstDesc *desc;
     const GeoTab *geo;
+    const double *const *ageo;   // per grid size: the sweep's geometry block (null for N > 8193)
     const EigTab *eig;
     const double *exptab;
     const int32_t *order;
@@ -263,43 +278,6 @@ __device__ __forceinline__ CellFwd cell_fwd_n(double qn0, double rn0, double qn1
     return r;
 }
 
-// transpose of cell_fwd_n from (alpha_bar, beta_bar, Delta_bar) to the node and midpoint
-// sensitivities: rho_bar at node c (n0) and c+1 (n1), and (p16_bar, q16_bar)
-__device__ __forceinline__ void cell_bwd(const CellFwd &f, const GeoTab &g, int c, double alb, double beb,
-                                         double Deb, double &n0, double &n1, double &p16b, double &q16b)
-{
-    // beta = (r0 + r1) + ca tm + e w2
-    double eb = mul_f(beb, f.w2), cab = mul_f(beb, f.tm), tmb = mul_f(beb, f.ca), r0b = beb;
-    const double w2b = mul_f(beb, f.e), r1b = beb;
-    // alpha = (y2 - q1) + y3 e
-    const double y3b = mul_f(alb, f.e);
-    eb = fma(alb, f.y3, eb);
-    double y2b = alb, q1b = -alb;
-    // w2 = tm - qm3 r0
-    tmb = add_f(tmb, w2b);
-    double qm3b = mul_f(-w2b, f.rn0);
-    r0b = fma(-w2b, f.qm3, r0b);
-    // e = 2 - qm3 ca
-    qm3b = fma(-eb, f.ca, qm3b);
-    cab = fma(-eb, f.qm3, cab);
-    // ca = 2 - 6 q1
-    q1b = fma(-6.0, cab, q1b);
-    // y3 = 1/3 - qm3 y2
-    qm3b = fma(-y3b, f.y2, qm3b);
-    y2b = fma(-y3b, f.qm3, y2b);
-    // y2 = 1/3 - q0;  Delta = q0 + q1 + (4/3) qm3
-    const double q0b = add_f(Deb, -y2b);
-    q1b = add_f(q1b, Deb);
-    qm3b = fma(4.0 / 3.0, Deb, qm3b);
-    n0 = fma(__ldg(g.ws + c), q0b, mul_f(__ldg(g.wt + c), r0b));
-    n1 = fma(__ldg(g.ws + c + 1), q1b, mul_f(__ldg(g.wt + c + 1), r1b));
-    const double rmb = fma(__ldg(g.wsm3 + c), qm3b, mul_f(__ldg(g.wtm + c), tmb));
-    // rho_m = (p16^2 + q16^2) / 256, the 1/256 folded into wsm3 and wtm; 2 rmb is exact
-    const double rmb2 = add_f(rmb, rmb);
-    p16b = mul_f(f.p16, rmb2);
-    q16b = mul_f(f.q16, rmb2);
-}
-
 // ------------------------------------------------------------------ CTA scratch layout
 struct Scr {
     double *uP, *uQ;     // current slice u_n (phase F)
@@ -445,7 +423,7 @@ __device__ void stage_forward(const double *yP, const double *yQ, double *M, dou
 template <int CL, int AP>
 __device__ void constraint_backward(const double *yP, const double *yQ, const double *M, const double *AL,
                                     const Scr &scr, double *ybP, double *ybQ, const InstDesc &d,
-                                    const GeoTab &g, ScanShared &sh)
+                                    const double *ag, ScanShared &sh)
 {
     const int N = d.N;
     const Own o = own_of<CL, AP>(N);
@@ -453,16 +431,19 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
     const int i0 = o.i0;
     // mu_c = alpha_c mu_{c+1} + mbar_c, mu_{N-1} = 0: suffix affine scan
     double aT = 1.0, bT = 0.0, SP = 0.0;
-    if (act) {
+    if (act) {   // seeded with the last cell's map and the first node's value
+        aT = AL[i0 + AP - 1];
+        bT = scr.mb[i0 + AP - 1];
 #pragma unroll
-        for (int k = AP - 1; k >= 0; --k) {
+        for (int k = AP - 2; k >= 0; --k) {
             const int c = i0 + k;
             const double a = AL[c];
             bT = fma(a, bT, scr.mb[c]);
             aT = mul_f(aT, a);
         }
+        SP = scr.dlb[i0];
 #pragma unroll
-        for (int k = 0; k < AP; ++k) SP = add_f(SP, scr.dlb[i0 + k]);
+        for (int k = 1; k < AP; ++k) SP = add_f(SP, scr.dlb[i0 + k]);
     }
     double mu_end, dpre;   // mu at node i0 + AP; the sum of delta_bar over the nodes < i0
     scan_pair<CL, true>(aT, bT, SP, sh, mu_end, dpre);
@@ -477,31 +458,59 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
         double Db = dpre;
         double n0s[AP];
         // the cell loop, compiled once with plain loads (warps whose threads read only interior
-        // nodes: all but the two at the ends of the grid) and once with the parity ghosts
+        // nodes: all but the two at the ends of the grid) and once with the parity ghosts.
+        // Per cell c: the forward quantities of the m map (the linearisation point; rho and the
+        // node factor r carried from cell to cell), then the transpose of
+        //   alpha = (y2 - q1) + y3 e,  beta = (r0 + r1) + ca tm + e w2,  Delta = q0 + q1 + (4/3) qm3
+        // with y2 = 1/3 - q0, y3 = 1/3 - qm3 y2, ca = 2 - 6 q1, e = 2 - qm3 ca, w2 = tm - qm3 r0,
+        // at alpha_bar = mu m_c, beta_bar = mu (mu = mu_{c+1}), Delta_bar = Db.  Its partial
+        // derivatives give, with u = 1 - e qm3:
+        //   r0_bar = mu u,  q0_bar = Db - mu m_c u,  r1_bar = mu,  tm_bar = mu (ca + e),
+        //   q1_bar = mu (m_c (6 qm3 y3 - 1) + 6 (qm3 w2 - tm)) + Db,
+        //   qm3_bar = (4/3) Db - mu (m_c (e y2 + y3 ca) + (w2 ca + e r0)),
+        // and, through q = ws rho, r = wt rho at the nodes and qm3 = wsm3 rm, tm = wtm rm at the
+        // midpoint, twice the rho sensitivities:
+        //   2 rho_bar(node c) = mu u (2 wt - 2 ws m_c) + 2 ws Db  (cell c's left node),
+        //   2 rho_bar(node c+1) = 2 ws q1_bar + 2 wt mu          (its right node),
+        //   2 rm_bar = mu (2 wtm (ca + e) - 2 wsm3 (...)) + (8/3) wsm3 Db.
         auto cells = [&](auto interior) {
         constexpr bool INT = decltype(interior)::value;
-        // the cells' forward data with the node quantities carried from cell to cell
         double pm1 = gvi<INT>(yP, N, i0 - 1, -1.0, 1.0), p0 = yP[i0], p1 = yP[i0 + 1];
         double qm1 = gvi<INT>(yQ, N, i0 - 1, 1.0, -1.0), q0 = yQ[i0], q1 = yQ[i0 + 1];
-        const double rho0 = fma(p0, p0, mul_f(q0, q0));
-        double qn0 = mul_f(__ldg(g.ws + i0), rho0), rn0 = mul_f(__ldg(g.wt + i0), rho0);
+        double rho0 = fma(p0, p0, mul_f(q0, q0));
+        double r0 = mul_f(agv(ag, kAgWt, i0), rho0);
 #pragma unroll
         for (int k = 0; k < AP; ++k) {
             const int c = i0 + k;
             Db = add_f(Db, scr.dlb[c]);               // Delta_bar_c = sum_{i <= c} delta_bar_i
             const double p2 = gvi<INT>(yP, N, c + 2, -1.0, 1.0), q2 = gvi<INT>(yQ, N, c + 2, 1.0, -1.0);
             const double rho1 = fma(p1, p1, mul_f(q1, q1));
-            const double qn1 = mul_f(__ldg(g.ws + c + 1), rho1), rn1 = mul_f(__ldg(g.wt + c + 1), rho1);
-            const CellFwd cf = cell_fwd_n(qn0, rn0, qn1, rn1, pm1, p0, p1, p2, qm1, q0, q1, q2, g, c);
+            const double y2 = fma(-agv(ag, kAgWs, c), rho0, 1.0 / 3.0);
+            const double ca = fma(-agv(ag, kAgWs6, c + 1), rho1, 2.0);
+            const double p16 = fma(9.0, add_f(p0, p1), -add_f(pm1, p2));
+            const double q16 = fma(9.0, add_f(q0, q1), -add_f(qm1, q2));
+            const double rm = fma(p16, p16, mul_f(q16, q16));
+            const double qm3 = mul_f(agv(ag, kAgWsm3, c), rm);
+            const double tm = mul_f(agv(ag, kAgWtm, c), rm);
+            const double y3 = fma(-qm3, y2, 1.0 / 3.0);
+            const double e = fma(-qm3, ca, 2.0);
+            const double w2 = fma(-qm3, r0, tm);
+            const double r1 = mul_f(agv(ag, kAgWt, c + 1), rho1);
+            const double mc = mun[k], m = M[c];
+            const double u = fma(-e, qm3, 1.0);
+            n0s[k] = fma(mul_f(mc, u), fma(-agv(ag, kAgWs2, c), m, agv(ag, kAgWt2, c)), mul_f(agv(ag, kAgWs2, c), Db));
+            const double q6 = mul_f(6.0, qm3);
+            const double q1b = fma(mc, fma(m, fma(q6, y3, -1.0), fma(q6, w2, mul_f(-6.0, tm))), Db);
+            scr.r1[c] = fma(agv(ag, kAgWs2, c + 1), q1b, mul_f(agv(ag, kAgWt2, c + 1), mc));
+            const double inner = fma(m, fma(e, y2, mul_f(y3, ca)), fma(w2, ca, mul_f(e, r0)));
+            const double X = fma(-agv(ag, kAgWsm3x2, c), inner, mul_f(agv(ag, kAgWtm2, c), add_f(ca, e)));
+            const double rmb2 = fma(mc, X, mul_f(agv(ag, kAgWsm3x83, c), Db));   // 2 rm_bar
+            // rho_m = (p16^2 + q16^2) / 256, the 1/256 folded into wsm3 and wtm
+            scr.pb[c] = mul_f(p16, rmb2);
+            scr.qb[c] = mul_f(q16, rmb2);
             pm1 = p0; p0 = p1; p1 = p2;
             qm1 = q0; q0 = q1; q1 = q2;
-            qn0 = qn1; rn0 = rn1;
-            double n0, n1, pb, qb;
-            cell_bwd(cf, g, c, mul_f(mun[k], M[c]), mun[k], Db, n0, n1, pb, qb);
-            n0s[k] = n0;
-            scr.r1[c] = n1;
-            scr.pb[c] = pb;
-            scr.qb[c] = qb;
+            rho0 = rho1; r0 = r1;
         }
         };
         if (__all_sync(__activemask(), reads_interior<AP>(i0, N))) cells(std::true_type{});
@@ -518,6 +527,7 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
 #pragma unroll
         for (int k = 0; k < AP; ++k) {
             const int j = i0 + k;
+            // twice rho_bar at node j: the left-node part of cell j and the right-node part of cell j-1
             const double rb = add_f(scr.fb[j], (INT || j >= 1) ? scr.r1[j - 1] : 0.0);
             // transpose of p16_c = 9 (w_c + w_{c+1}) - (w_{c-1} + w_{c+2}), cells 0 .. N-2
             auto itp = [&](const double *b, int x) {
@@ -529,8 +539,8 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
                 if (j == 1) { pP += -itp(scr.pb, -1); pQ += itp(scr.qb, -1); }                // ghost -1
                 if (j == N - 2) { pP += itp(scr.pb, N); pQ += -itp(scr.qb, N); }              // ghost N
             }
-            ybP[j] = add_f(ybP[j], fma(add_f(yP[j], yP[j]), rb, pP));
-            ybQ[j] = add_f(ybQ[j], fma(add_f(yQ[j], yQ[j]), rb, pQ));
+            ybP[j] = add_f(ybP[j], fma(yP[j], rb, pP));   // d rho = 2 Phi dPhi + 2 Pi dPi
+            ybQ[j] = add_f(ybQ[j], fma(yQ[j], rb, pQ));
         }
         };
         if (__all_sync(__activemask(), reads_interior<AP>(i0, N))) nodes(std::true_type{});
@@ -547,7 +557,7 @@ __device__ void constraint_backward(const double *yP, const double *yQ, const do
 template <int CL, int AP>
 __device__ void stage_backward(const double *yP, const double *yQ, const double *M, const double *E,
                                const double *F, const double *AL, const Scr &scr, double *ybP, double *ybQ,
-                               const InstDesc &d, const GeoTab &g, ScanShared &sh)
+                               const InstDesc &d, const double *ag, ScanShared &sh)
 {
     const int N = d.N;
     const Own o = own_of<CL, AP>(N);
@@ -594,7 +604,7 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
                 if (j == N - 3) ubx += (-1.0 / 3.0) * (-Dr(v2, N - 1));
             }
             const double fb = fbx;   // (vP carries the factor c12, vQ the factor cq)
-            double gb = mul_f(__ldg(g.T + j), ubx);
+            double gb = mul_f(agv(ag, kAgT, j), ubx);
             if constexpr (!INT) {
                 if (j == 1) gb = fma(16.0 * d.c3q, vQ0, gb);            // Pi-dot(0) = 3 (F Phi)'(0)
                 if (j == 2) gb = fma(-2.0 * d.c3q, vQ0, gb);
@@ -605,7 +615,7 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
             ybP[j] = fma(gb, Fj, mul_f(d.rko, kpx));
             const double Ab = mul_f(Fb, E[j]);
             scr.dlb[j] = mul_f(-Fb, Fj);
-            scr.mb[j] = mul_f(-Ab, __ldg(g.K + j));
+            scr.mb[j] = mul_f(-Ab, agv(ag, kAgK, j));
         }
         };
         if (__all_sync(__activemask(), reads_interior<AP>(i0, N))) nodes(std::true_type{});
@@ -614,7 +624,7 @@ __device__ void stage_backward(const double *yP, const double *yQ, const double 
     }
     // no barrier: the constraint transpose reads only this thread's mb, dlb before its scans'
     // barriers, and vP, vQ, v2 are written again only after the next stage's first barrier
-    constraint_backward<CL, AP>(yP, yQ, M, AL, scr, ybP, ybQ, d, g, sh);
+    constraint_backward<CL, AP>(yP, yQ, M, AL, scr, ybP, ybQ, d, ag, sh);
 }
 
 // ------------------------------------------------------------------ the kernel
@@ -629,6 +639,9 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
     __shared__ ScanShared sh;
     __shared__ double s_tab[kExpTableSize];
     __shared__ int s_item;
+    // phase B's factors of stage s for the current work item: w_s dt c12, w_s dt cq, c_{s+1} dt c12,
+    // c_{s+1} dt cq (computed once per work item instead of by every thread in every stage)
+    __shared__ double s_kc[4][4];
     const int tid = threadIdx.x;
     const int rank = (CL > 1) ? cluster_rank() : 0;
     if constexpr (!SWEEP)   // the exponential is evaluated only in the forward stages
@@ -647,11 +660,22 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
         }
         csync<CL>();
         const int q = s_item;
-        csync<CL>();
+        if (tid == 0 && q < a.nwork) {
+            const InstDesc dq = a.desc[a.order[q]];
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+                s_kc[st][0] = wst[st] * dq.dtc;
+                s_kc[st][1] = wst[st] * dq.dtq;
+                s_kc[st][2] = st < 3 ? cst[st + 1] * dq.dtc : 0.0;
+                s_kc[st][3] = st < 3 ? cst[st + 1] * dq.dtq : 0.0;
+            }
+        }
+        csync<CL>();   // also publishes s_kc (its previous readers passed the barrier above)
         if (q >= a.nwork) break;
         const int b = a.order[q];
         const InstDesc d = a.desc[b];
         const GeoTab g = a.geo[d.geo];
+        const double *ag = a.ageo[d.geo];
         const int N = d.N;
         const Own own = own_of<CL, AP>(N);
         const bool act = own.act;
@@ -740,7 +764,7 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                 if (own.last) { scr.mb[N - 1] = 0.0; scr.dlb[N - 1] = 0.0; }
             }
             csync<CL>();
-            constraint_backward<CL, AP>(yP, yQ, M, AL, scr, scr.ybP, scr.ybQ, d, g, sh);
+            constraint_backward<CL, AP>(yP, yQ, M, AL, scr, scr.ybP, scr.ybQ, d, ag, sh);
             if (act) {
 #pragma unroll
                 for (int k = 0; k < AP; ++k) {
@@ -820,20 +844,20 @@ __global__ void __launch_bounds__(kANT, 1) adjoint_kernel(AdjArgs a)
                     for (int k = 0; k < AP; ++k) {
                         const int i = i0 + k;
                         // kbar, scaled by c12 (Phi) and cq (Pi): the factors of Phi-dot and Pi-dot
-                        double kb = mul_f(wst[s] * d.dtc, scr.lo[i]), kq = mul_f(wst[s] * d.dtq, scr.lq[i]);
+                        double kb = mul_f(s_kc[s][0], scr.lo[i]), kq = mul_f(s_kc[s][1], scr.lq[i]);
                         if (s < 3) {
-                            kb = fma(cst[s + 1] * d.dtc, scr.ybP[i], kb);
-                            kq = fma(cst[s + 1] * d.dtq, scr.ybQ[i], kq);
+                            kb = fma(s_kc[s][2], scr.ybP[i], kb);
+                            kq = fma(s_kc[s][3], scr.ybQ[i], kq);
                         }
                         scr.vP[i] = (i == 0) ? 0.0 : kb;   // Phi-dot(0) is identically zero
                         scr.vQ[i] = kq;
-                        scr.v2[i] = mul_f(__ldg(g.iT12k + i), kq);   // = iT12 kbar_Pi
+                        scr.v2[i] = mul_f(agv(ag, kAgIT12k, i), kq);   // = iT12 kbar_Pi
                     }
                     if (own.last) { scr.vP[N - 1] = 0.0; scr.vQ[N - 1] = 0.0; scr.v2[N - 1] = 0.0; }
                 }
                 csync<CL>();
                 stage_backward<CL, AP>(slot(n, s, 0), slot(n, s, 1), slot(n, s, 2), slot(n, s, 3), slot(n, s, 4),
-                               slot(n, s, 5), scr, scr.ybP, scr.ybQ, d, g, sh);
+                               slot(n, s, 5), scr, scr.ybP, scr.ybQ, d, ag, sh);
                 if (act) {
 #pragma unroll
                     for (int k = 0; k < AP; ++k) {

@@ -98,6 +98,8 @@ struct adscl_ctx {
     QueueCtl *d_ctl = nullptr;
     int32_t *d_rounds = nullptr;
     GeoTab *d_geo = nullptr;
+    double *d_ageo_block = nullptr;   // the backward sweep's geometry blocks (kAgTables tables each)
+    const double **d_ageo = nullptr;  // per grid size: its block, or null for N > kScrStride
     InstDesc *d_desc = nullptr;
     InstState *d_st = nullptr;
     double *d_Phi = nullptr, *d_Pi = nullptr, *d_aPhi = nullptr, *d_aPi = nullptr;
@@ -843,10 +845,34 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     for (int n : geoN) geo_doubles += (size_t)kGeoTables * geo_stride(n);
     CK(cudaMalloc(&ctx->d_geo_block, geo_doubles * sizeof(double)));
     std::vector<GeoTab> h_geo;
+    std::vector<double> h_ageo_tabs;   // kAdjGeoTables tables per grid size, geo_stride(N) apart
     {
         size_t pos = 0;
         for (int n : geoN) {
             std::vector<double> t = make_geometry(n, ctx->sigma);
+            if (n <= kScrStride) {   // the backward sweep's block: GeoTab copies and scaled weights
+                const size_t S = (size_t)geo_stride(n), L = kScrStride;
+                const double *ws = t.data(), *wt = ws + S, *K = ws + 2 * S, *T = ws + 3 * S, *wsm3 = ws + 5 * S,
+                             *wtm = ws + 6 * S, *iT12k = ws + 8 * S;
+                const size_t a0 = h_ageo_tabs.size();
+                h_ageo_tabs.resize(a0 + kAgTables * L, 0.0);
+                double *o = h_ageo_tabs.data() + a0;
+                for (size_t i = 0; i < (size_t)n; ++i) {
+                    o[kAgWs * L + i] = ws[i];
+                    o[kAgWt * L + i] = wt[i];
+                    o[kAgK * L + i] = K[i];
+                    o[kAgT * L + i] = T[i];
+                    o[kAgWsm3 * L + i] = wsm3[i];
+                    o[kAgWtm * L + i] = wtm[i];
+                    o[kAgIT12k * L + i] = iT12k[i];
+                    o[kAgWs2 * L + i] = 2.0 * ws[i];
+                    o[kAgWt2 * L + i] = 2.0 * wt[i];
+                    o[kAgWs6 * L + i] = 6.0 * ws[i];
+                    o[kAgWsm3x2 * L + i] = 2.0 * wsm3[i];
+                    o[kAgWtm2 * L + i] = 2.0 * wtm[i];
+                    o[kAgWsm3x83 * L + i] = (8.0 / 3.0) * wsm3[i];
+                }
+            }
             CK(cudaMemcpy(ctx->d_geo_block + pos, t.data(), t.size() * sizeof(double),
                           cudaMemcpyHostToDevice));
             const double *base = ctx->d_geo_block + pos;
@@ -867,6 +893,21 @@ adscl_status adscl_create(const adscl_config *cfg, adscl_ctx **out)
     }
     CK(cudaMalloc(&ctx->d_geo, h_geo.size() * sizeof(GeoTab)));
     CK(cudaMemcpy(ctx->d_geo, h_geo.data(), h_geo.size() * sizeof(GeoTab), cudaMemcpyHostToDevice));
+    {
+        if (!h_ageo_tabs.empty()) {
+            CK(cudaMalloc(&ctx->d_ageo_block, h_ageo_tabs.size() * sizeof(double)));
+            CK(cudaMemcpy(ctx->d_ageo_block, h_ageo_tabs.data(), h_ageo_tabs.size() * sizeof(double),
+                          cudaMemcpyHostToDevice));
+        }
+        std::vector<const double *> h_ageo;
+        size_t pos = 0;
+        for (int n : geoN) {
+            h_ageo.push_back(n <= kScrStride ? ctx->d_ageo_block + pos : nullptr);
+            if (n <= kScrStride) pos += (size_t)kAgTables * kScrStride;
+        }
+        CK(cudaMalloc(&ctx->d_ageo, h_ageo.size() * sizeof(const double *)));
+        CK(cudaMemcpy(ctx->d_ageo, h_ageo.data(), h_ageo.size() * sizeof(const double *), cudaMemcpyHostToDevice));
+    }
     if (ctx->scheme != ADSCL_SCHEME_RK4) {
         // node factors of the evolved-A schemes: K2 = -2 sin x cos x (A-dot of Eq. (eq:adot)) and
         // the composite-Simpson mass weights (h/3) w_i tan^2 x_i (0 at both ends)
@@ -1448,6 +1489,7 @@ adscl_status adscl_grad(adscl_ctx *ctx, const double *a, int32_t K, double T, do
     AdjArgs aa{};
     aa.desc = ctx->d_desc;
     aa.geo = ctx->d_geo;
+    aa.ageo = ctx->d_ageo;
     aa.exptab = ctx->d_exptab;   // (aa.eig: the mode tables exist only after the forward pass)
     aa.order = ctx->d_order;
     aa.nwork = B;
@@ -2032,7 +2074,7 @@ void adscl_destroy(adscl_ctx *ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
-    void *ptrs[] = {ctx->d_geo_block, ctx->d_geo, ctx->d_desc, ctx->d_st, ctx->d_Phi, ctx->d_Pi,
+    void *ptrs[] = {ctx->d_geo_block, ctx->d_geo, ctx->d_ageo_block, (void *)ctx->d_ageo, ctx->d_desc, ctx->d_st, ctx->d_Phi, ctx->d_Pi,
                     ctx->d_aPhi, ctx->d_aPi, ctx->d_scratchA, ctx->d_scratchD, ctx->d_order,
                     ctx->d_ctl, ctx->d_rounds, ctx->d_exptab, ctx->d_out, ctx->d_outs,
                     ctx->d_eig_block, ctx->d_eig, ctx->d_modes, ctx->d_E, ctx->d_tc_rowoff,
