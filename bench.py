@@ -66,9 +66,9 @@ SCHEMES = {   # name: (config value, stages per step, flops per point-substep, A
 # divided by their point-substeps, captured on a reduced adjoint batch (38 instances at N = 4097,
 # 96 steps in two 48-step segments; per point-substep the same instruction mix as the bench's
 # 64-instance batch); used only while the kernel sources are unchanged
-ADJ_ISSUE = {"sha256": "6e940d62290630fa8685de8baa1b07afcf8b6b7ad4dbb19d1bc65372132c4c90",
+ADJ_ISSUE = {"sha256": "647182ea36803fad5233ec8fbc9159e2263c8bd13a710fae2f524ca4085b6e8d",
              "forward_record": (24925416 + 3955116 + 4205327532) / (38 * 4097 * 96 * 4),
-             "phase_B": (11425536 + 59890432 + 3067625088) / (38 * 4097 * 48 * 4)}
+             "phase_B": (3954432 + 122056 + 2894894720) / (38 * 4097 * 48 * 4)}
 L2_FLUSH_BYTES = 512 << 20
 CPU_SAMPLE_STEPS = 800    # oracle sample of the cpu_baseline leg: ~10 s on 16 host threads
 REF_SAMPLE_STEPS = 100    # oracle sample per bench step of the reference arm
