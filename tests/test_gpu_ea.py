@@ -164,8 +164,10 @@ def test_fixed_metric_on_an_eight_cta_cluster(ad, orc):
     assert np.all(gA == 1.0) and np.all(gd == 0.0)
 
 
+# (32769, (8, 512, 16)): the paper's Table I grid on the 16-CTA cluster the autotuner picks for
+# a single instance
 @pytest.mark.parametrize("N,shape", [(4097, (8, 256, 2)), (2049, (8, 128, 2)), (1025, (8, 256, 2)),
-                                     (36865, (8, 512, 9)), (4105, (8, 512, 9))])
+                                     (36865, (8, 512, 9)), (4105, (8, 512, 9)), (32769, (8, 512, 16))])
 @pytest.mark.parametrize("scheme", [1, 3])
 def test_evolved_a_shapes_match_oracle(ad, orc, N, shape, scheme):
     Phi, Pi = W.smooth_random(N, seed=N + scheme, amp=2.0)

@@ -40,6 +40,28 @@ def test_sixteen_cta_constraints_and_step(ad, orc, n):
     assert np.abs(gP - oP).max() < 1e-13 * scale and np.abs(gQ - oQ).max() < 1e-13 * scale
 
 
+def test_table1_grid_on_sixteen_ctas_matches_oracle(ad, orc):
+    """N = 32769 (the paper's Table I grid) on the 16-CTA cluster the autotuner picks for a single
+    instance instead of its default 8-CTA cluster: constraint solve and two RK4 steps."""
+    n = 32769
+    Phi, Pi = W.smooth_random(n, seed=77, amp=3.0)
+    s = ad.Solver([n])
+    assert s.shape(0) == (8, 512, 8)
+    s.set_shape(n, 8, 512, 16)
+    assert s.shape(0) == (8, 512, 16)
+    s.set_initial(Phi, Pi)
+    _, _, A, dl = s.get_state(0)
+    Ao, dlo, _, _ = orc.constraints(Phi, Pi)
+    assert np.abs(A - Ao).max() < 1e-12 * max(1.0, np.abs(Ao).max())
+    assert np.abs(dl - dlo).max() < 1e-12 * max(1.0, np.abs(dlo).max())
+    dt, _ = s.clock()
+    s.evolve(2 * dt[0])
+    gP, gQ, _, _ = s.get_state(0)
+    oP, oQ = orc.rk4_step(*orc.rk4_step(Phi, Pi, dt[0], sigma=0.5), dt[0], sigma=0.5)
+    scale = max(np.abs(oP).max(), np.abs(oQ).max())
+    assert np.abs(gP - oP).max() < 1e-13 * scale and np.abs(gQ - oQ).max() < 1e-13 * scale
+
+
 def test_sixteen_cta_pulse_evolution_matches_oracle(ad, orc):
     n = 65537
     Pi0 = W.gaussian_pi(n, 30.0, sigma=1.0 / 16)
