@@ -2034,21 +2034,57 @@ adscl_status adscl_autotune(adscl_ctx *ctx, int32_t trial_steps)
             }
             set_run(r, best[r]);
         }
-        if (nr > 1 && best != dflt) {
-            // the sizes run concurrently in a batch, where shapes that share an SM (two CTAs of
-            // 256 threads) and shapes that fill one do not pack as the SM split assumes: keep
-            // the per-size choice only if the whole batch, timed over a longer window, is more
-            // than 1 % faster with it than with the default shapes
-            double r_best = 0.0, r_dflt = 0.0;
-            s = rate_of(0, B, bsteps, &r_best);
-            if (s != ADSCL_OK) return s;
-            for (int r = 0; r < nr; ++r) set_run(r, dflt[r]);
-            s = rate_of(0, B, bsteps, &r_dflt);
-            if (s != ADSCL_OK) return s;
-            if (r_best > 1.01 * r_dflt) {
+        if (nr > 1) {
+            // The sizes run concurrently in a batch, where shapes that share an SM (two CTAs of
+            // 256 threads) and shapes that fill one do not pack as the SM split assumes.  So the
+            // whole batch is timed over a longer window with the defaults, with the per-size
+            // choices, and with each family of P = 8 shapes of one CTA size (the smallest cluster
+            // that holds each grid size: all CTAs alike, e.g. (8, 256, 1/2/4) for N = 2049, 4097,
+            // 8193, which ran the uneven batch at 6.95e9 against 6.88e9 for the defaults), and a
+            // candidate is kept only when it is more than 1 % faster than the defaults.
+            std::vector<std::vector<int>> cands;
+            if (best != dflt) cands.push_back(best);
+            for (int nt : {128, 256}) {
+                std::vector<int> fam(nr, -1);
+                bool ok = true;
+                for (int r = 0; r < nr && ok; ++r) {
+                    const int n = sig[r].first;
+                    for (int id = 0; id < kNumShapes; ++id) {
+                        const Shape &sh = kShapes[id];
+                        if (sh.P != 8 || sh.NT != nt || !shape_fits(id, n) || (ea_scheme && !ea_shape(id))) continue;
+                        if (fam[r] >= 0 && sh.CL >= kShapes[fam[r]].CL) continue;
+                        int u = 0;
+                        const cudaError_t eu = ea_scheme
+                            ? ea_max_units(ctx->scheme == ADSCL_SCHEME_FIXED_METRIC_RK3, id, shape_smem(id, n), ctx->num_sms, &u)
+                            : shape_max_units(id, shape_smem(id, n), ctx->num_sms, &u);
+                        if (eu != cudaSuccess || u < 1) {
+                            (void)cudaGetLastError();
+                            continue;
+                        }
+                        fam[r] = id;
+                    }
+                    ok = fam[r] >= 0;
+                }
+                if (ok && fam != dflt && fam != best) cands.push_back(fam);
+            }
+            if (!cands.empty()) {
+                double r_dflt = 0.0, r_top = 0.0;
+                int top = -1;
+                for (int r = 0; r < nr; ++r) set_run(r, dflt[r]);
+                s = rate_of(0, B, bsteps, &r_dflt);
+                if (s != ADSCL_OK) return s;
+                for (int c = 0; c < (int)cands.size(); ++c) {
+                    for (int r = 0; r < nr; ++r) set_run(r, cands[c][r]);
+                    double rate = 0.0;
+                    s = rate_of(0, B, bsteps, &rate);
+                    if (s != ADSCL_OK) return s;
+                    if (rate > r_top) {
+                        r_top = rate;
+                        top = c;
+                    }
+                }
+                best = (top >= 0 && r_top > 1.01 * r_dflt) ? cands[top] : dflt;
                 for (int r = 0; r < nr; ++r) set_run(r, best[r]);
-            } else {
-                best = dflt;
             }
         }
         ctx->t_prev = t_prev0;
