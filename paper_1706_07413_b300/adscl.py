@@ -59,6 +59,7 @@ SIGNATURES = {
     "adscl_set_initial": ([_VP, _VP, _VP, ctypes.c_int], ctypes.c_int),
     "adscl_set_initial_modes": ([_VP, _VP, _I32, ctypes.c_int], ctypes.c_int),
     "adscl_evolve": ([_VP, _F, _VP, _VP, _VP, _VP, ctypes.c_int], ctypes.c_int),
+    "adscl_evolve_wide": ([_VP, _F, _VP, _VP, _VP, _VP, ctypes.c_int], ctypes.c_int),
     "adscl_spectrum": ([_VP, _I32, ctypes.c_int, _VP, ctypes.c_int], ctypes.c_int),
     "adscl_ttf": ([_VP, _I32, ctypes.c_int, _VP, _VP, ctypes.c_int], ctypes.c_int),
     "adscl_track": ([_VP, _F, _F, _I32, _I32, ctypes.c_int, _VP, _VP, _VP, ctypes.c_int], ctypes.c_int),
@@ -252,6 +253,21 @@ class Solver:
         ptrs = [_ptr(x)[0] for x in out]
         dev = _ptr(out[0])[1]
         self._check(self.lib.adscl_evolve(self.ctx, float(t_end), *ptrs, dev))
+        return out
+
+    def evolve_wide(self, t_end, out=None):
+        """adscl_evolve_wide: evolve the context's single fixed-metric instance to t_end on the
+        whole GPU (one cooperative launch, a grid-wide barrier per stage).  Same outputs as
+        evolve."""
+        if out is None:
+            tr, tc, m = np.empty(self.B), np.empty(self.B), np.empty(self.B)
+            s = np.empty(self.B, dtype=np.int32)
+            self._check(self.lib.adscl_evolve_wide(self.ctx, float(t_end), tr.ctypes.data, tc.ctypes.data,
+                                                   m.ctypes.data, s.ctypes.data, 0))
+            return tr, tc, m, s
+        ptrs = [_ptr(x)[0] for x in out]
+        dev = _ptr(out[0])[1]
+        self._check(self.lib.adscl_evolve_wide(self.ctx, float(t_end), *ptrs, dev))
         return out
 
     def get_state(self, inst):

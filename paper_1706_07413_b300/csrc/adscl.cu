@@ -21,6 +21,7 @@
 #include "spectrum_tc.cuh"
 #include "adjoint.cuh"
 #include "evolve_ea.cuh"
+#include "fixed_wide.cuh"
 #include "shapes.h"
 
 using namespace adscl;
@@ -89,6 +90,7 @@ struct adscl_ctx {
     int adj_units = 0;                 // co-resident adjoint units (CTAs or 2-CTA clusters)
     double *d_A = nullptr;             // packed evolved A (evolved-A schemes)
     double *d_ea_block = nullptr;      // K2, wsim per grid size (evolved-A schemes)
+    double *d_wide = nullptr;          // adscl_evolve_wide: stage slices, partial sums, barrier words
     EaGeo *d_eageo = nullptr;
 
     std::vector<InstDesc> h_desc;
@@ -1100,6 +1102,73 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
     if (!ptr_is_device) {
         CK(cudaStreamSynchronize(ctx->stream));
         return check_timeout(ctx);
+    }
+    return ADSCL_OK;
+}
+
+adscl_status adscl_evolve_wide(adscl_ctx *ctx, double t_end, double *t_reached, double *t_collapse,
+                               double *mass, int32_t *inst_status, int ptr_is_device)
+{
+    adscl_status s = check_ctx(ctx);
+    if (s != ADSCL_OK) return s;
+    if (!std::isfinite(t_end) || t_end < 0.0) return fail(ctx, ADSCL_EINVAL, "bad t_end");
+    if (ctx->B != 1) return fail(ctx, ADSCL_EUNSUPPORTED, "adscl_evolve_wide evolves a context of one instance");
+    if (ctx->scheme != ADSCL_SCHEME_FIXED_METRIC_RK3)
+        return fail(ctx, ADSCL_EUNSUPPORTED, "adscl_evolve_wide runs the fixed-metric scheme only");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(ctx->stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(ctx, ADSCL_EUNSUPPORTED, "adscl_evolve_wide is not for use inside a stream capture");
+    const int N = ctx->N[0];
+    const int G = (N + kWideNT - 1) / kWideNT;
+    int coop = 0, per_sm = 0;
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fixed_wide_kernel, kWideNT, 0));
+    if (!coop || per_sm * ctx->num_sms < G)
+        return fail(ctx, ADSCL_EUNSUPPORTED, "the %d CTAs of N = %d do not fit one cooperative launch", G, N);
+    // scratch: y_1, y_2 (Phi, Pi), u twice, the per-CTA partial sums, then the barrier words
+    const size_t nd = (size_t)6 * N + G;
+    if (!ctx->d_wide) CK(cudaMalloc(&ctx->d_wide, nd * sizeof(double) + 64));
+    const size_t S = (size_t)geo_stride(N);   // one grid size: its tables start each block
+    WideArgs w{};
+    w.d = ctx->h_desc[0];
+    w.T = ctx->d_geo_block + 3 * S;
+    w.iT12 = ctx->d_geo_block + 4 * S;
+    w.wsim = ctx->d_ea_block + S;
+    w.Phi = ctx->d_Phi;
+    w.Pi = ctx->d_Pi;
+    w.Y1P = ctx->d_wide;
+    w.Y1Q = w.Y1P + N;
+    w.Y2P = w.Y1Q + N;
+    w.Y2Q = w.Y2P + N;
+    w.U0 = w.Y2Q + N;
+    w.U1 = w.U0 + N;
+    w.part = w.U1 + N;
+    w.bar = reinterpret_cast<unsigned *>(ctx->d_wide + nd);
+    w.flag = reinterpret_cast<int *>(w.bar + 2);
+    w.st = ctx->d_st;
+    w.n_end = (long long)std::ceil(t_end / w.d.dt - 1e-9);
+    w.max_spin = ctx->max_iters;
+    CK(cudaMemsetAsync(w.bar, 0, 4 * sizeof(int32_t), ctx->stream));
+    void *args[] = {&w};
+    CK(cudaLaunchCooperativeKernel((const void *)fixed_wide_kernel, dim3(G), dim3(kWideNT), args, 0, ctx->stream));
+    double *o = ctx->d_out;
+    CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(QueueCtl), ctx->stream));
+    gather_kernel<<<1, 128, 0, ctx->stream>>>(ctx->d_desc, ctx->d_st, 1, t_end, 1, nullptr, nullptr, o, o + 1,
+                                              o + 2, ctx->d_outs);
+    CK(cudaGetLastError());
+    ctx->launches += 2;
+    ctx->t_prev = t_end;
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (t_reached) CK(cudaMemcpyAsync(t_reached, o, sizeof(double), kind, ctx->stream));
+    if (t_collapse) CK(cudaMemcpyAsync(t_collapse, o + 1, sizeof(double), kind, ctx->stream));
+    if (mass) CK(cudaMemcpyAsync(mass, o + 2, sizeof(double), kind, ctx->stream));
+    if (inst_status) CK(cudaMemcpyAsync(inst_status, ctx->d_outs, sizeof(int32_t), kind, ctx->stream));
+    if (!ptr_is_device) {
+        int32_t fl[2] = {0, 0};
+        CK(cudaMemcpyAsync(fl, w.flag, sizeof fl, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (fl[1]) return fail(ctx, ADSCL_ETIMEOUT, "a grid barrier wait ran out");
     }
     return ADSCL_OK;
 }
@@ -2117,7 +2186,7 @@ void adscl_destroy(adscl_ctx *ctx)
                     ctx->d_tc_rowinst, ctx->d_tc_modeoff, ctx->d_tc_ops, ctx->d_tc_D,
                     ctx->d_tc_tasks, ctx->d_tc_err, ctx->d_lam, ctx->d_adj_scr, ctx->d_adj_stage,
                     ctx->d_ck, ctx->d_adj_small, ctx->d_adj_queue, ctx->d_A, ctx->d_ea_block, ctx->d_adj_spec,
-                    ctx->d_eageo, ctx->d_rPhi, ctx->d_rPi, ctx->d_rSt, ctx->d_tc_tile};
+                    ctx->d_eageo, ctx->d_rPhi, ctx->d_rPi, ctx->d_rSt, ctx->d_tc_tile, ctx->d_wide};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ctx->evo_exec) cudaGraphExecDestroy(ctx->evo_exec);
