@@ -43,33 +43,48 @@ struct WideArgs {
     long long max_spin;       // iteration limit of a barrier wait
 };
 
+// gpu-scope acquire load, acquire-release atomic add and release add (PTX memory model)
+__device__ __forceinline__ unsigned wide_ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned wide_atom_add_acq_rel(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void wide_red_release(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier of a cooperative launch: every CTA's writes before it are visible to every
-// CTA after it.  Returns false if this CTA's wait ran out (flag[1] is then set).
+// CTA after it.  The CTA barrier orders the CTA's writes before thread 0's arrival, a release at
+// gpu scope (cumulative); the last arrival resets the count and releases the next generation,
+// which the others acquire.  Returns false if this CTA's wait ran out (flag[1] is then set).
 __device__ __forceinline__ bool wide_barrier(unsigned *bar, int *flag, long long max_spin)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();   // the CTA's writes (ordered before by the CTA barrier) before arriving
+        const unsigned g = wide_ld_acquire(bar + 1);
         int ok = 1;
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);   // reset for the next barrier before releasing the others
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        if (wide_atom_add_acq_rel(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);          // ordered before the release below
+            wide_red_release(bar + 1, 1u);
         } else {
             long long it = 0;
-            while (*gen == g) {
+            while (wide_ld_acquire(bar + 1) == g) {
                 if (++it > max_spin) {
                     atomicExch(flag + 1, 1);
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
             }
         }
-        __threadfence();
         s_ok = ok && (*(volatile int *)(flag + 1) == 0);
     }
     __syncthreads();
