@@ -312,7 +312,8 @@ def paper_configs_report(stream, local, steps=64):
     with A and delta dynamical (the paper's scheme: A evolved by Eq. (eq:adot), re-integrated
     every 64 steps, SSP-RK3; and the classic RK4 with A integrated every stage), and the fixed
     metric A = 1, delta = 0 at the Table II grid N = 65537; each on the cluster shape the
-    autotuner picks for the single instance (a 16-CTA cluster for both grids)."""
+    autotuner picks for the single instance (a 16-CTA cluster for both grids); the fixed metric
+    also on the whole GPU (adscl_evolve_wide)."""
     import torch
     from paper_1706_07413_b300 import adscl
     out = {}
@@ -339,6 +340,23 @@ def paper_configs_report(stream, local, steps=64):
         out[name] = {"N": N, "steps": n, "kernel_shape_P_NT_CL": list(shape), "ms_per_step": ms / max(n, 1),
                      "point_substeps_per_s": N * stages * n / (ms / 1e3),
                      "wall_s_per_unit_time": ms / max(n, 1) / 1e3 / float(dt[0])}
+        if scheme == 3:
+            # the same single instance on the whole GPU (adscl_evolve_wide: one cooperative
+            # launch of ceil(N / 512) CTAs, a grid-wide barrier per stage)
+            sol.evolve_wide((8 + steps) * dt[0])
+            torch.cuda.synchronize()
+            _, s0 = sol.clock()
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                sol.evolve_wide((8 + 2 * steps) * dt[0])
+                e1.record(stream)
+            torch.cuda.synchronize()
+            _, s1 = sol.clock()
+            ms = e0.elapsed_time(e1)
+            n = int(s1[0] - s0[0])
+            out[name]["whole_gpu"] = {"ctas": -(-N // 512), "ms_per_step": ms / max(n, 1),
+                                      "point_substeps_per_s": N * stages * n / (ms / 1e3),
+                                      "wall_s_per_unit_time": ms / max(n, 1) / 1e3 / float(dt[0])}
         sol.close()
     return out
 
