@@ -145,17 +145,18 @@ adscl_status adscl_evolve(adscl_ctx *ctx, double t_end, double *t_reached, doubl
 
 /* adscl_evolve for a context of ONE instance under ADSCL_SCHEME_FIXED_METRIC_RK3 (the paper's
  * Table II case, Sec. IV: A = 1 and delta = 0 held fixed, Eqs. (eq:phi), (eq:pi) with SSP-RK3),
- * spread over the whole GPU: one cooperative launch of ceil(N / 512) CTAs, one grid node per
- * thread, meeting at one grid-wide barrier per Runge-Kutta stage (adscl_evolve gives one
- * instance at most one 16-CTA cluster).  Same discretisation and readings as adscl_evolve, so
+ * spread over the whole GPU: one cooperative launch of ceil(N / 500) CTAs of 512 threads, each
+ * owning 500 grid nodes and forming the three Runge-Kutta stages of a step on them and on a
+ * 9-node halo, meeting at one grid-wide barrier per step (adscl_evolve gives one instance at
+ * most one 16-CTA cluster).  Same discretisation and readings as adscl_evolve, so
  * the slices agree with it to rounding; same outputs and per-instance statuses (length 1),
  * same step counter and slice diagnostics (mass: the composite Simpson rule), so calls of the
  * two may follow each other.  The barrier waits are bounded by cfg.max_device_iters: if one
  * runs out the instance is reported TIMEOUT (and a synchronous call returns ADSCL_ETIMEOUT).
- * Scratch of 6 N + ceil(N / 512) doubles is allocated at the first call and kept by the context.
+ * Scratch of 2 N + ceil(N / 500) doubles is allocated at the first call and kept by the context.
  * The launch is issued directly on the context's stream; not for use inside a stream capture
  * (ADSCL_EUNSUPPORTED).  ADSCL_EUNSUPPORTED also for contexts of more than one instance, other
- * schemes, or a grid whose CTAs do not fit one cooperative launch (N above 512 x the SM count). */
+ * schemes, or a grid whose CTAs do not fit one cooperative launch (N above 500 x the SM count). */
 adscl_status adscl_evolve_wide(adscl_ctx *ctx, double t_end, double *t_reached, double *t_collapse,
                                double *mass, int32_t *inst_status, int ptr_is_device);
 

@@ -1120,14 +1120,14 @@ adscl_status adscl_evolve_wide(adscl_ctx *ctx, double t_end, double *t_reached, 
     if (cap != cudaStreamCaptureStatusNone)
         return fail(ctx, ADSCL_EUNSUPPORTED, "adscl_evolve_wide is not for use inside a stream capture");
     const int N = ctx->N[0];
-    const int G = (N + kWideNT - 1) / kWideNT;
+    const int G = (N + kWideNodes - 1) / kWideNodes;
     int coop = 0, per_sm = 0;
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fixed_wide_kernel, kWideNT, 0));
     if (!coop || per_sm * ctx->num_sms < G)
         return fail(ctx, ADSCL_EUNSUPPORTED, "the %d CTAs of N = %d do not fit one cooperative launch", G, N);
-    // scratch: y_1, y_2 (Phi, Pi), u twice, the per-CTA partial sums, then the barrier words
-    const size_t nd = (size_t)6 * N + G;
+    // scratch: the second slice (Phi, Pi), the per-CTA partial sums, then the barrier words
+    const size_t nd = (size_t)2 * N + G;
     if (!ctx->d_wide) CK(cudaMalloc(&ctx->d_wide, nd * sizeof(double) + 64));
     const size_t S = (size_t)geo_stride(N);   // one grid size: its tables start each block
     WideArgs w{};
@@ -1137,13 +1137,9 @@ adscl_status adscl_evolve_wide(adscl_ctx *ctx, double t_end, double *t_reached, 
     w.wsim = ctx->d_ea_block + S;
     w.Phi = ctx->d_Phi;
     w.Pi = ctx->d_Pi;
-    w.Y1P = ctx->d_wide;
-    w.Y1Q = w.Y1P + N;
-    w.Y2P = w.Y1Q + N;
-    w.Y2Q = w.Y2P + N;
-    w.U0 = w.Y2Q + N;
-    w.U1 = w.U0 + N;
-    w.part = w.U1 + N;
+    w.BP = ctx->d_wide;
+    w.BQ = w.BP + N;
+    w.part = w.BQ + N;
     w.bar = reinterpret_cast<unsigned *>(ctx->d_wide + nd);
     w.flag = reinterpret_cast<int *>(w.bar + 2);
     w.st = ctx->d_st;
