@@ -1,6 +1,6 @@
 """adscl_evolve_wide: one fixed-metric instance (the paper's Table II case, Sec. IV: A = 1,
-delta = 0, SSP-RK3) spread over the whole GPU, one cooperative launch with a grid-wide barrier
-per stage.  Against the oracle's discrete map, against the cluster path of adscl_evolve, and the
+delta = 0, SSP-RK3) spread over the whole GPU, one cooperative launch of 500-node blocks with a
+grid-wide barrier per step.  Against the oracle's discrete map, against the cluster path of adscl_evolve, and the
 state protocol shared with it (step counter, slice mass, statuses)."""
 import numpy as np
 import pytest
@@ -23,8 +23,8 @@ def _solver(ad, n, Phi, Pi):
     return s
 
 
-# 65537: the paper's Table II grid (129 CTAs, the last with one node); 4105: a ragged last CTA
-# (9 nodes); 129: a single CTA
+# 65537: the paper's Table II grid (132 CTAs, the last with 37 nodes); 4105: a ragged last CTA
+# (105 nodes); 129: a single CTA holding both ends of the grid
 @pytest.mark.parametrize("n,nst", [(65537, 6), (4105, 40), (129, 40)])
 def test_wide_matches_oracle(ad, orc, n, nst):
     Phi, Pi = W.smooth_random(n, seed=n % 97, amp=2.0)
